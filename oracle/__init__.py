@@ -1,0 +1,294 @@
+"""FP64 CPU oracle for the Octree-GS LOD renderer hot path — TEST INFRASTRUCTURE ONLY.
+
+Only the test-suite, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg may
+import this package.  It shares no code with the CUDA path (``paper_2403_17898_gb300``) and
+imports nothing from it.  The C library ``ogs_oracle.c`` holds the arithmetic; this module
+only converts arrays to float64 / int64, calls it and composes the stages in the paper's order
+(Sec. 4.1.3 selection -> Sec. 3.2 decode -> Sec. 3.1 projection, tile lists and blending).
+
+Parity status of each function (what pins it) is stated in its docstring; every function
+here is pinned by a ``-m "not gpu"`` test in ``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ogs_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+TILE = 16
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP over pixels)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = C.CDLL(_LIB)
+        _declare(_lib)
+    return _lib
+
+
+_P = C.c_void_p
+
+
+def _declare(L):
+    L.orc_lod_select.restype = C.c_long
+    L.orc_lod_select.argtypes = [C.c_long, _P, _P, _P, C.c_int, _P, C.c_int, _P, _P, _P]
+    L.orc_decode.restype = None
+    L.orc_decode.argtypes = [C.c_long, _P, _P, _P, _P, C.c_int, _P, _P, C.c_int,
+                             _P, _P, C.c_int, _P, _P, _P, _P, _P, _P, _P,
+                             _P, _P, _P, _P, _P, _P]
+    L.orc_project.restype = None
+    L.orc_project.argtypes = [C.c_long] + [_P] * 12
+    L.orc_tile_lists.restype = C.c_long
+    L.orc_tile_lists.argtypes = [C.c_long, _P, _P, C.c_int, C.c_int, _P, _P, C.c_long, _P]
+    L.orc_blend.restype = None
+    L.orc_blend.argtypes = [C.c_int, C.c_int] + [_P] * 13
+    L.orc_blend_bwd.restype = None
+    L.orc_blend_bwd.argtypes = [C.c_int, C.c_int] + [_P] * 12
+    L.orc_project_bwd.restype = None
+    L.orc_project_bwd.argtypes = [C.c_long] + [_P] * 10
+    L.orc_decode_bwd.restype = None
+    L.orc_decode_bwd.argtypes = ([C.c_long, _P, _P, _P, _P, C.c_int, _P, _P, C.c_int,
+                                  _P, _P, C.c_int, _P, _P, _P, _P, _P, _P, _P]
+                                 + [_P] * 16)
+
+
+def _d(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def cam_array(cam) -> np.ndarray:
+    """Camera as 22 float64 (R[9], campos[3], fx, fy, cx, cy, W, H, znear, d_max, s, pad),
+    upcast exactly from the float32 values both paths receive."""
+    if hasattr(cam, "as_floats"):
+        cam = cam.as_floats()
+    return _d(np.asarray(cam, np.float32))
+
+
+def grid(W, H):
+    return (W + TILE - 1) // TILE, (H + TILE - 1) // TILE
+
+
+# ----------------------------------------------------------------------------------------
+# stages
+# ----------------------------------------------------------------------------------------
+
+def lod_select(pos, level, dL, NL, cam, infer):
+    """Sec. 4.1.3 (Eq. for L_hat): selected anchor indices (ascending), weights, and the
+    per-anchor decision margin.  Pinned by hand cases at d = d_max/2^m +- eps, cumulativity,
+    monotonicity in distance and the s <-> distance equivalence (tests/test_oracle_select)."""
+    pos, dL = _d(pos), _d(dL)
+    level = np.ascontiguousarray(level, np.int32)
+    N = pos.shape[0]
+    idx = np.zeros(N, np.int64)
+    w = np.zeros(N, np.float64)
+    margin = np.zeros(N, np.float64)
+    M = lib().orc_lod_select(N, _p(pos), _p(level), _p(dL), int(NL), _p(cam_array(cam)),
+                             int(bool(infer)), _p(idx), _p(w), _p(margin))
+    return idx[:M].copy(), w[:M].copy(), margin
+
+
+def decode(sel_idx, sel_w, scene, mlp, cam):
+    """Sec. 3.2 (Eq. offsets, Eq. mlp).  Gaussian g = rank*k + i.  Pinned by closed forms with
+    zeroed second layers, the affine collapse when every hidden unit is active, and position
+    offsets (tests/test_oracle_decode)."""
+    sel_idx = np.ascontiguousarray(sel_idx, np.int64)
+    sel_w = _d(sel_w)
+    M = sel_idx.shape[0]
+    k = scene.k
+    F = scene.feat.shape[1]
+    Hd = mlp.w1.shape[1]
+    G = M * k
+    out = dict(means=np.zeros((G, 3)), scales=np.zeros((G, 3)), quats=np.zeros((G, 4)),
+               opac=np.zeros(G), colors=np.zeros((G, 3)), op_margin=np.zeros(G))
+    ws = [_d(a) for a in mlp.arrays()]
+    lib().orc_decode(M, _p(sel_idx), _p(sel_w), _p(_d(scene.pos)), _p(_d(scene.feat)), F,
+                     _p(_d(scene.offs)), _p(_d(scene.lv)), k, _p(ws[0]), _p(ws[1]), Hd,
+                     _p(ws[2]), _p(ws[3]), _p(ws[4]), _p(ws[5]), _p(ws[6]), _p(ws[7]),
+                     _p(cam_array(cam)), _p(out["means"]), _p(out["scales"]),
+                     _p(out["quats"]), _p(out["opac"]), _p(out["colors"]),
+                     _p(out["op_margin"]))
+    return out
+
+
+def project(means, scales, quats, opac, cam):
+    """Sec. 3.1 (Eq. 1 and the EWA projection).  Pinned by the on-axis axis-aligned closed
+    form, the 90-degree-about-z swap, radius/rect hand cases (tests/test_oracle_project)."""
+    means, scales, quats, opac = _d(means), _d(scales), _d(quats), _d(opac)
+    G = means.shape[0]
+    o = dict(uv=np.zeros((G, 2)), conic=np.zeros((G, 3)), depth=np.zeros(G),
+             radius=np.zeros(G), rect=np.zeros((G, 4), np.int32), mz=np.zeros(G),
+             mpx=np.zeros(G))
+    lib().orc_project(G, _p(means), _p(scales), _p(quats), _p(opac), _p(cam_array(cam)),
+                      _p(o["uv"]), _p(o["conic"]), _p(o["depth"]), _p(o["radius"]),
+                      _p(o["rect"]), _p(o["mz"]), _p(o["mpx"]))
+    return o
+
+
+def tile_lists(rect, depth, gx, gy):
+    """Sec. 3.1: per tile, Gaussians whose rect covers it, ordered by (depth, id).  Pinned by
+    permutation/ordering invariants and a brute-force rebuild (tests/test_oracle_lists)."""
+    rect = np.ascontiguousarray(rect, np.int32)
+    depth = _d(depth)
+    G = rect.shape[0]
+    T = gx * gy
+    start = np.zeros(T + 1, np.int64)
+    tie = np.zeros(T, np.float64)
+    spans = np.maximum(rect[:, 2] - rect[:, 0], 0) * np.maximum(rect[:, 3] - rect[:, 1], 0)
+    cap = int(spans.sum())
+    lst = np.zeros(max(cap, 1), np.int64)
+    P = lib().orc_tile_lists(G, _p(rect), _p(depth), int(gx), int(gy), _p(start), _p(lst),
+                             cap, _p(tie))
+    assert P == cap
+    return start, lst[:P].copy(), tie
+
+
+def blend(W, H, start, lst, uv, conic, opac, colors, bg=(0.0, 0.0, 0.0), anchor_of=None,
+          n_anchors=0):
+    """Sec. 3.1 Eq. 2 with the rasterizer conventions.  Pinned by the single- and
+    two-Gaussian closed forms, the clamp/skip/stop hand cases, monotone transmittance and
+    input-order invariance (tests/test_oracle_blend)."""
+    uv, conic, opac, colors = _d(uv), _d(conic), _d(opac), _d(colors)
+    bg = _d(bg)
+    img = np.zeros((3, H, W))
+    T = np.zeros((H, W))
+    last = np.zeros((H, W), np.int32)
+    m = np.zeros((H, W))
+    maxc = None
+    if anchor_of is not None:
+        anchor_of = np.ascontiguousarray(anchor_of, np.int64)
+        maxc = np.zeros(n_anchors)
+    lib().orc_blend(int(W), int(H), _p(start), _p(lst), _p(uv), _p(conic), _p(opac),
+                    _p(colors), _p(bg), _p(img), _p(T), _p(last), _p(m), _p(anchor_of),
+                    _p(maxc))
+    return dict(img=img, T=T, last=last, px_margin=m, maxc=maxc)
+
+
+def blend_bwd(W, H, start, lst, uv, conic, opac, colors, bg, dimg):
+    """Analytic backward of Eq. 2 (back-to-front replay).  Pinned by central finite
+    differences of ``blend`` (tests/test_oracle_grad)."""
+    uv, conic, opac, colors = _d(uv), _d(conic), _d(opac), _d(colors)
+    G = uv.shape[0]
+    o = dict(duv=np.zeros((G, 2)), dconic=np.zeros((G, 3)), dopac=np.zeros(G),
+             dcolors=np.zeros((G, 3)))
+    lib().orc_blend_bwd(int(W), int(H), _p(start), _p(lst), _p(uv), _p(conic), _p(opac),
+                        _p(colors), _p(_d(bg)), _p(_d(dimg)), _p(o["duv"]), _p(o["dconic"]),
+                        _p(o["dopac"]), _p(o["dcolors"]))
+    return o
+
+
+def project_bwd(means, scales, quats, rect, cam, duv, dconic):
+    """Analytic backward of the EWA projection.  Pinned by finite differences."""
+    means, scales, quats = _d(means), _d(scales), _d(quats)
+    G = means.shape[0]
+    o = dict(dmeans=np.zeros((G, 3)), dscales=np.zeros((G, 3)), dquats=np.zeros((G, 4)))
+    lib().orc_project_bwd(G, _p(means), _p(scales), _p(quats),
+                          _p(np.ascontiguousarray(rect, np.int32)), _p(cam_array(cam)),
+                          _p(_d(duv)), _p(_d(dconic)), _p(o["dmeans"]), _p(o["dscales"]),
+                          _p(o["dquats"]))
+    return o
+
+
+def decode_bwd(sel_idx, sel_w, scene, mlp, cam, g):
+    """Analytic backward of the decoders.  Pinned by finite differences."""
+    sel_idx = np.ascontiguousarray(sel_idx, np.int64)
+    sel_w = _d(sel_w)
+    M = sel_idx.shape[0]
+    k = scene.k
+    N, F = scene.feat.shape
+    Hd = mlp.w1.shape[1]
+    ws = [_d(a) for a in mlp.arrays()]
+    o = dict(dfeat=np.zeros((N, F)), doffs=np.zeros((N, k, 3)), dlv=np.zeros((N, 3)))
+    names = ["dw1", "db1", "dw2_op", "db2_op", "dw2_col", "db2_col", "dw2_cov", "db2_cov"]
+    for n, a in zip(names, mlp.arrays()):
+        o[n] = np.zeros(a.shape)
+    lib().orc_decode_bwd(M, _p(sel_idx), _p(sel_w), _p(_d(scene.pos)), _p(_d(scene.feat)), F,
+                         _p(_d(scene.offs)), _p(_d(scene.lv)), k, _p(ws[0]), _p(ws[1]), Hd,
+                         _p(ws[2]), _p(ws[3]), _p(ws[4]), _p(ws[5]), _p(ws[6]), _p(ws[7]),
+                         _p(cam_array(cam)), _p(_d(g["dmeans"])), _p(_d(g["dscales"])),
+                         _p(_d(g["dquats"])), _p(_d(g["dopac"])), _p(_d(g["dcolors"])),
+                         _p(o["dfeat"]), _p(o["doffs"]), _p(o["dlv"]),
+                         *[_p(o[n]) for n in names])
+    return o
+
+
+def stable_sort_pairs(keys, vals):
+    """Stable sort of (key, value) pairs by key: a library sort is the whole definition.
+    Pinned by ordering/permutation/stability properties (tests/test_oracle_lists)."""
+    order = np.argsort(np.asarray(keys), kind="stable")
+    return np.asarray(keys)[order], np.asarray(vals)[order]
+
+
+# ----------------------------------------------------------------------------------------
+# composed forward / backward
+# ----------------------------------------------------------------------------------------
+
+@dataclass
+class Frame:
+    sel_idx: np.ndarray
+    sel_w: np.ndarray
+    sel_margin: np.ndarray
+    gauss: dict
+    proj: dict
+    start: np.ndarray
+    lst: np.ndarray
+    tie: np.ndarray
+    out: dict
+    gx: int
+    gy: int
+
+
+def render(scene, mlp, cam, infer=True, bg=(0.0, 0.0, 0.0), want_maxc=False):
+    """The whole forward pass of one view, stage by stage."""
+    sel_idx, sel_w, margin = lod_select(scene.pos, scene.level, scene.dL, scene.NL, cam, infer)
+    g = decode(sel_idx, sel_w, scene, mlp, cam)
+    pr = project(g["means"], g["scales"], g["quats"], g["opac"], cam)
+    gx, gy = grid(cam.W, cam.H)
+    start, lst, tie = tile_lists(pr["rect"], pr["depth"], gx, gy)
+    anchor_of = np.repeat(sel_idx, scene.k) if want_maxc else None
+    out = blend(cam.W, cam.H, start, lst, pr["uv"], pr["conic"], g["opac"], g["colors"], bg,
+                anchor_of=anchor_of, n_anchors=scene.N)
+    return Frame(sel_idx, sel_w, margin, g, pr, start, lst, tie, out, gx, gy)
+
+
+def render_grad(scene, mlp, cam, fr: Frame, dimg, bg=(0.0, 0.0, 0.0)):
+    """Backward of ``render`` for a given dL/dimage: blend -> projection -> decoders."""
+    g, pr = fr.gauss, fr.proj
+    gb = blend_bwd(cam.W, cam.H, fr.start, fr.lst, pr["uv"], pr["conic"], g["opac"],
+                   g["colors"], bg, dimg)
+    pb = project_bwd(g["means"], g["scales"], g["quats"], pr["rect"], cam, gb["duv"],
+                     gb["dconic"])
+    per_g = dict(dmeans=pb["dmeans"], dscales=pb["dscales"], dquats=pb["dquats"],
+                 dopac=gb["dopac"], dcolors=gb["dcolors"])
+    db = decode_bwd(fr.sel_idx, fr.sel_w, scene, mlp, cam, per_g)
+    db.update(per_gauss=per_g, blend=gb)
+    return db
+
+
+def l1_loss(img, target):
+    """Mean absolute error over all channels and pixels, and its gradient."""
+    diff = _d(img) - _d(target)
+    return float(np.abs(diff).mean()), np.sign(diff) / diff.size
