@@ -1,0 +1,226 @@
+/*
+ * ogs.h — C ABI of the GB300 (sm_103a) Octree-GS LOD renderer hot path.
+ *
+ * One view (or one training step) runs as a chain of stream-ordered calls:
+ *
+ *   ogs_lod_select   anchors -> selected anchor indices + opacity weights   (Sec. 4.1.3)
+ *   ogs_decode       selected anchors -> k neural Gaussians each            (Sec. 3.2)
+ *   ogs_project_bin  Gaussians -> 2D screen records, depth keys, tile rects (Sec. 3.1)
+ *   ogs_sort         per-tile Gaussian lists in front-to-back order         (Sec. 3.1)
+ *   ogs_blend_fwd    per-pixel front-to-back alpha blending                 (Sec. 3.1, Eq. 2)
+ *   ogs_blend_bwd, ogs_project_bwd, ogs_decode_bwd   analytic backward (training)
+ *
+ * Conventions shared by every entry point
+ *   - Every pointer argument is a DEVICE pointer unless its comment says "host".  All device
+ *     memory is owned by the caller; the library never allocates or frees device memory and
+ *     keeps no global state.  Scratch space is passed in by the caller; its size comes from
+ *     the matching *_scratch_bytes() query.
+ *   - `stream` is a cudaStream_t passed as void*.  Every call only enqueues work on it and
+ *     returns without synchronising; outputs are valid once the stream reaches that point.
+ *   - Counts produced on the device (selected anchors, Gaussians, pairs) stay on the device in
+ *     an ogs_counts record that later calls read, so a frame needs no host round trip.  Buffer
+ *     capacities are passed from the host; a count that exceeds its capacity sets a bit in
+ *     ogs_counts.overflow, records the size that would have been needed, and the affected
+ *     stage writes only what fits (the caller grows the buffer and reruns the frame).
+ *   - Return value: OGS_OK, or OGS_ERR_ARG for a null pointer / bad size / misaligned pointer
+ *     detected on the host before anything is enqueued, or OGS_ERR_CUDA when a launch fails.
+ *     No call throws, traps or exits.
+ *   - Arrays are C-contiguous; "f32[N][3]" means N rows of 3 floats.
+ *
+ * Camera model: world point p has camera coordinates R (p - campos) (x right, y down, z
+ * forward); its pixel is (fx x/z + cx, fy y/z + cy) with pixel (i, j) centred on integer
+ * coordinates.  Tiles are 16x16 pixels; the tile grid is ceil(W/16) x ceil(H/16).
+ */
+#ifndef OGS_H
+#define OGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ogs_status {
+    OGS_OK = 0,
+    OGS_ERR_ARG = 1,       /* invalid argument, nothing enqueued */
+    OGS_ERR_CAPACITY = 2,  /* reserved for host-side capacity checks */
+    OGS_ERR_TIMEOUT = 3,   /* a bounded device-side wait expired (see ogs_counts.timeout) */
+    OGS_ERR_CUDA = 4       /* a CUDA launch or API call failed */
+} ogs_status;
+
+/* Host-side camera, passed by pointer and copied at call time. */
+typedef struct ogs_camera {
+    float R[9];        /* world -> camera rotation, row-major */
+    float campos[3];   /* camera centre, world */
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float znear;       /* near plane, camera z (0.2 by convention) */
+    float d_max;       /* reference distance of the LOD rule */
+    float s;           /* focal scale factor of the LOD rule */
+    float pad;
+} ogs_camera;
+
+/* Device-resident counters of one frame.  The caller zeroes the record before
+ * ogs_lod_select (cudaMemsetAsync); the kernels fill it in. */
+typedef struct ogs_counts {
+    uint32_t n_selected;       /* M, anchors kept by ogs_lod_select (<= its capacity) */
+    uint32_t n_gaussians;      /* M * k */
+    uint32_t n_pairs;          /* P, (tile, Gaussian) pairs (<= pair capacity) */
+    uint32_t overflow;         /* bit 0: selection capacity, bit 1: pair capacity */
+    uint32_t need_selected;    /* selection size that was needed */
+    uint32_t need_pairs;       /* pair count that was needed */
+    uint32_t timeout;          /* nonzero if a bounded wait expired */
+    uint32_t n_visible;        /* Gaussians with a non-empty tile rectangle */
+} ogs_counts;
+
+/* Decoder weights (device, f32), layout of the paper's three attribute MLPs (Sec. 3.2,
+ * Eq. mlp): input z = [f_v (F), (x_v - campos)/|x_v - campos| (3), |x_v - campos| (1)],
+ * Din = F + 4, hidden H = 32, ReLU.
+ *   w1  f32[3][H][Din], b1 f32[3][H]   (0 = opacity, 1 = colour, 2 = covariance)
+ *   w2_op  f32[k][H],   b2_op  f32[k]    opacity_i  = w * tanh(.)   (dropped if <= 0)
+ *   w2_col f32[3k][H],  b2_col f32[3k]   colour_i   = sigmoid(rows 3i..3i+2)
+ *   w2_cov f32[7k][H],  b2_cov f32[7k]   scale_i    = l_v * sigmoid(rows 7i..7i+2),
+ *                                        quat_i (w,x,y,z) = normalise(rows 7i+3..7i+6) */
+typedef struct ogs_mlp {
+    const float* w1;
+    const float* b1;
+    const float* w2_op;
+    const float* b2_op;
+    const float* w2_col;
+    const float* b2_col;
+    const float* w2_cov;
+    const float* b2_cov;
+    int32_t F;          /* feature width (32) */
+    int32_t H;          /* hidden width, must be 32 */
+    int32_t k;          /* Gaussians per anchor (1..16) */
+    int32_t pad;
+} ogs_mlp;
+
+/* Neural-Gaussian structure of arrays (device, f32); Gaussian g = r*k + i belongs to the r-th
+ * selected anchor.  means are CAMERA-RELATIVE (mu - campos, world axes) when written by
+ * ogs_decode: subtracting the camera centre before rounding keeps FP32 positions accurate at
+ * city scale. */
+typedef struct ogs_gaussians {
+    float* means;    /* f32[G][3] */
+    float* scales;   /* f32[G][3] */
+    float* quats;    /* f32[G][4] unit quaternion (w, x, y, z) */
+    float* opac;     /* f32[G]    opacity; <= 0 marks a dropped Gaussian */
+    float* colors;   /* f32[G][3] */
+} ogs_gaussians;
+
+/* Screen-space record of one Gaussian (48 bytes, 16-byte aligned), written by
+ * ogs_project_bin:  {u, v, conic_a, conic_b}, {conic_c, opacity, r, g}, {b, depth, radius, 0}.
+ * The 2D falloff at pixel offset (dx, dy) = (u - px, v - py) is
+ * exp(-0.5 (a dx^2 + c dy^2) - b dx dy). */
+typedef struct ogs_rec2d {
+    float u, v, ca, cb;
+    float cc, o, cr, cg;
+    float cbl, depth, radius, pad;
+} ogs_rec2d;
+
+/* ---------------------------------------------------------------------------------------
+ * ogs_lod_select — Sec. 4.1.3, Eq. for L_hat and the inference-time opacity blending.
+ * For each anchor j: d = |pos_j - campos|, L* = clamp(log2(d_max/(d s)) + dL_j, 0, NL-1),
+ * L_hat = floor(L*).  The anchor is kept with weight 1 if level_j <= L_hat; with infer != 0
+ * it is also kept with weight L* - L_hat if level_j == L_hat + 1 and that weight is > 0.
+ * Only anchors whose centre is in front of the near plane and within 1.3x the half field of
+ * view are considered.  Output is order-preserving: sel_idx ascending.
+ *   pos f32[N][3], level u8[N], dL f32[N]      anchor SoA (inputs)
+ *   sel_idx u32[sel_cap], sel_w f32[sel_cap]   outputs; counts->n_selected = M,
+ *                                              counts->n_gaussians = M * k
+ *   scratch: ogs_lod_select_scratch_bytes(N) bytes, 16-byte aligned.
+ * ------------------------------------------------------------------------------------- */
+size_t ogs_lod_select_scratch_bytes(int64_t N);
+ogs_status ogs_lod_select(const float* pos, const uint8_t* level, const float* dL, int64_t N,
+                          int32_t NL, int32_t k, const ogs_camera* cam /* host */,
+                          int32_t infer, uint32_t* sel_idx, float* sel_w, int64_t sel_cap,
+                          ogs_counts* counts, void* scratch, size_t scratch_bytes,
+                          void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * ogs_decode — Sec. 3.2, Eq. offsets (mu_i = x_v + O_i * l_v, elementwise) and Eq. mlp.
+ * FP32 arithmetic.  Reads M from counts->n_selected; writes Gaussians 0 .. M*k-1.
+ *   pos f32[N][3], feat f32[N][F], offs f32[N][k][3], lv f32[N][3]   anchor SoA
+ *   sel_idx/sel_w from ogs_lod_select; sel_cap = their capacity
+ *   out: Gaussian SoA with room for sel_cap * k Gaussians (means camera-relative)
+ * ------------------------------------------------------------------------------------- */
+ogs_status ogs_decode(const float* pos, const float* feat, const float* offs, const float* lv,
+                      int64_t N, const ogs_mlp* mlp /* host struct of device ptrs */,
+                      const ogs_camera* cam /* host */, const uint32_t* sel_idx,
+                      const float* sel_w, int64_t sel_cap, const ogs_counts* counts,
+                      const ogs_gaussians* out /* host struct of device ptrs */, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * ogs_project_bin — Sec. 3.1: Sigma = R(q) S S^T R(q)^T (Eq. 1), EWA projection
+ * Sigma' = J W Sigma W^T J^T + 0.3 I (J with x/z, y/z clamped to 1.3x the half-fov),
+ * conic = Sigma'^-1, radius r = 3 sqrt(lambda_max), lambda_max = mid + sqrt(max(0.1,
+ * mid^2 - det)), tile rectangle of the tiles holding a pixel centre inside [u-r, u+r] x
+ * [v-r, v+r].  A Gaussian is culled (rect empty, tiles 0, depth key 0xFFFFFFFF) when its
+ * opacity is <= 0, its depth is <= znear, det <= 0 or its rectangle is empty.
+ *   g: Gaussian SoA; count = counts->n_gaussians if counts != NULL else n_gauss
+ *   means_relative: 1 if means are camera-relative (as written by ogs_decode), 0 if world
+ *   rec ogs_rec2d[G], depth_key u32[G] (float bits of depth), rect u32[G][2]
+ *   (x0 | y0 << 16, x1 | y1 << 16), tiles u32[G] (number of tiles covered)
+ * ------------------------------------------------------------------------------------- */
+ogs_status ogs_project_bin(const ogs_gaussians* g /* host struct */, int64_t n_gauss,
+                           int32_t means_relative, const ogs_camera* cam /* host */,
+                           ogs_rec2d* rec, uint32_t* depth_key, uint32_t* rect,
+                           uint32_t* tiles, ogs_counts* counts, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * ogs_sort — Sec. 3.1: for every tile, the Gaussians whose rectangle covers it, in
+ * front-to-back order (ascending depth, ties by Gaussian id).  Built as: stable radix sort
+ * of Gaussians by depth key; exclusive scan of their tile counts in that order; emission of
+ * (tile, Gaussian) pairs in depth order; stable radix sort of the pairs by tile.
+ *   depth_key/rect/tiles from ogs_project_bin; count = counts->n_gaussians (or n_gauss)
+ *   pair_gauss u32[pair_cap]: Gaussian id of each pair, tile-major, front-to-back
+ *   tile_range u32[n_tiles][2]: [start, end) of each tile in pair_gauss
+ *   counts->n_pairs = P; if P > pair_cap, overflow bit 1 is set, need_pairs = P and only
+ *   tile_range is left empty.
+ *   scratch: ogs_sort_scratch_bytes(g_cap, pair_cap, n_tiles) bytes, 16-byte aligned.
+ * ------------------------------------------------------------------------------------- */
+size_t ogs_sort_scratch_bytes(int64_t g_cap, int64_t pair_cap, int32_t n_tiles);
+ogs_status ogs_sort(const uint32_t* depth_key, const uint32_t* rect, const uint32_t* tiles,
+                    int64_t g_cap, int64_t n_gauss, int32_t grid_x, int32_t grid_y,
+                    uint32_t* pair_gauss, uint32_t* tile_range, int64_t pair_cap,
+                    ogs_counts* counts, void* scratch, size_t scratch_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * ogs_radix_sort_pairs — the stable LSD radix sort used by ogs_sort, exposed on its own:
+ * sorts (key, value) pairs by bits [bit_lo, bit_hi) of the key, equal keys keeping their
+ * input order.  n = *n_dev if n_dev != NULL (device count, <= n_cap) else n_cap.  Result
+ * replaces keys/vals in place.
+ *   scratch: ogs_radix_sort_scratch_bytes(n_cap) bytes, 16-byte aligned.
+ * ------------------------------------------------------------------------------------- */
+size_t ogs_radix_sort_scratch_bytes(int64_t n_cap);
+ogs_status ogs_radix_sort_pairs(uint32_t* keys, uint32_t* vals, const uint32_t* n_dev,
+                                int64_t n_cap, int32_t bit_lo, int32_t bit_hi, void* scratch,
+                                size_t scratch_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * ogs_blend_fwd — Sec. 3.1, Eq. 2: per pixel, over its tile's list front to back:
+ * alpha = min(0.99, o exp(power)); skip power > 0 or alpha < 1/255; stop before a Gaussian
+ * that would bring T below 1e-4; C += c alpha T; T *= 1 - alpha.  Finally C += T bg.
+ *   rec, pair_gauss, tile_range from the calls above
+ *   bg: host float[3]
+ *   img f32[3][H][W], T_final f32[H][W], n_last u32[H][W] (list entries up to and
+ *   including the last blended one)
+ *   maxc (optional, may be NULL): u32[N_anchors], float bits of the largest T*alpha of any
+ *   blended Gaussian of each anchor (atomic max; caller zeroes); anchor of Gaussian g is
+ *   sel_idx[g / k].
+ * ------------------------------------------------------------------------------------- */
+ogs_status ogs_blend_fwd(const ogs_rec2d* rec, const uint32_t* pair_gauss,
+                         const uint32_t* tile_range, int32_t width, int32_t height,
+                         const float* bg /* host float[3] */, float* img, float* T_final,
+                         uint32_t* n_last, const uint32_t* sel_idx, int32_t k, uint32_t* maxc,
+                         void* stream);
+
+/* Library version string (host). */
+const char* ogs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OGS_H */

@@ -61,7 +61,7 @@ def _declare(L):
     L.orc_tile_lists.restype = C.c_long
     L.orc_tile_lists.argtypes = [C.c_long, _P, _P, C.c_int, C.c_int, _P, _P, C.c_long, _P]
     L.orc_blend.restype = None
-    L.orc_blend.argtypes = [C.c_int, C.c_int] + [_P] * 13
+    L.orc_blend.argtypes = [C.c_int, C.c_int] + [_P] * 15
     L.orc_blend_bwd.restype = None
     L.orc_blend_bwd.argtypes = [C.c_int, C.c_int] + [_P] * 12
     L.orc_project_bwd.restype = None
@@ -167,7 +167,7 @@ def tile_lists(rect, depth, gx, gy):
 
 
 def blend(W, H, start, lst, uv, conic, opac, colors, bg=(0.0, 0.0, 0.0), anchor_of=None,
-          n_anchors=0):
+          n_anchors=0, depth=None):
     """Sec. 3.1 Eq. 2 with the rasterizer conventions.  Pinned by the single- and
     two-Gaussian closed forms, the clamp/skip/stop hand cases, monotone transmittance and
     input-order invariance (tests/test_oracle_blend)."""
@@ -178,13 +178,17 @@ def blend(W, H, start, lst, uv, conic, opac, colors, bg=(0.0, 0.0, 0.0), anchor_
     last = np.zeros((H, W), np.int32)
     m = np.zeros((H, W))
     maxc = None
+    tie = None
+    if depth is not None:
+        depth = _d(depth)
+        tie = np.zeros((H, W))
     if anchor_of is not None:
         anchor_of = np.ascontiguousarray(anchor_of, np.int64)
         maxc = np.zeros(n_anchors)
     lib().orc_blend(int(W), int(H), _p(start), _p(lst), _p(uv), _p(conic), _p(opac),
                     _p(colors), _p(bg), _p(img), _p(T), _p(last), _p(m), _p(anchor_of),
-                    _p(maxc))
-    return dict(img=img, T=T, last=last, px_margin=m, maxc=maxc)
+                    _p(maxc), _p(depth), _p(tie))
+    return dict(img=img, T=T, last=last, px_margin=m, maxc=maxc, px_tie=tie)
 
 
 def blend_bwd(W, H, start, lst, uv, conic, opac, colors, bg, dimg):
@@ -270,7 +274,7 @@ def render(scene, mlp, cam, infer=True, bg=(0.0, 0.0, 0.0), want_maxc=False):
     start, lst, tie = tile_lists(pr["rect"], pr["depth"], gx, gy)
     anchor_of = np.repeat(sel_idx, scene.k) if want_maxc else None
     out = blend(cam.W, cam.H, start, lst, pr["uv"], pr["conic"], g["opac"], g["colors"], bg,
-                anchor_of=anchor_of, n_anchors=scene.N)
+                anchor_of=anchor_of, n_anchors=scene.N, depth=pr["depth"])
     return Frame(sel_idx, sel_w, margin, g, pr, start, lst, tie, out, gx, gy)
 
 

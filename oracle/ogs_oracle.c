@@ -281,7 +281,8 @@ static int project_one(const cam_t* k, const double* mu, const double* s, const 
 }
 
 /* uv: pixel coordinates of the centre; conic = inverse 2D covariance (a, b, c); rect =
- * [x0, y0, x1, y1) tiles, all zero when culled.  mz: relative margin of the near-plane test,
+ * [x0, y0, x1, y1) tiles, all zero when culled (uv and radius are still reported when only
+ * the rectangle is empty).  mz: relative margin of the near-plane test,
  * mpx: pixel distance of the four extent edges to a value that changes the tile rectangle. */
 void orc_project(long G, const double* means, const double* scales, const double* quats,
                  const double* opac, const double* camp, double* uv, double* conic,
@@ -320,11 +321,12 @@ void orc_project(long G, const double* means, const double* scales, const double
             m = dmin(m, grid_dist(v + r, 0.0));
             mpx[g] = m;
         }
-        if (x0 >= x1 || y0 >= y1) continue;
+        /* centre and extent are reported even when the rectangle is empty */
         uv[2 * g] = u; uv[2 * g + 1] = v;
+        radius[g] = r;
+        if (x0 >= x1 || y0 >= y1) continue;
         conic[3 * g] = c / det; conic[3 * g + 1] = -b / det; conic[3 * g + 2] = a / det;
         depth[g] = t.pc[2];
-        radius[g] = r;
         rc[0] = (int32_t)x0; rc[1] = (int32_t)y0; rc[2] = (int32_t)x1; rc[3] = (int32_t)y1;
     }
 }
@@ -401,17 +403,20 @@ static double eval_alpha(const double* uv, const double* conic, const double* op
 /* img[3][H][W], Tfinal[H][W], last[H][W] = number of list entries up to and including the
  * last blended one.  px_margin: smallest relative distance of an alpha-skip or stop test to
  * its threshold at that pixel.  If anchor_of and maxc are given, maxc[anchor] is raised to
- * the largest T_i alpha_i of any blended Gaussian of that anchor. */
+ * the largest T_i alpha_i of any blended Gaussian of that anchor.  If depth and px_tie are
+ * given, px_tie is the smallest relative depth gap between consecutive Gaussians that take
+ * part at the pixel (blended ones and the one that stops it): only such pairs change the
+ * pixel when their order flips. */
 void orc_blend(int W, int H, const int64_t* tile_start, const int64_t* list, const double* uv,
                const double* conic, const double* opac, const double* colors, const double* bg,
                double* img, double* Tfinal, int32_t* last, double* px_margin,
-               const int64_t* anchor_of, double* maxc) {
+               const int64_t* anchor_of, double* maxc, const double* depth, double* px_tie) {
     int gx = (W + ORC_TILE - 1) / ORC_TILE;
 #pragma omp parallel for schedule(dynamic, 64)
     for (long pix = 0; pix < (long)W * H; ++pix) {
         int px = (int)(pix % W), py = (int)(pix / W);
         long t = (long)(py / ORC_TILE) * gx + px / ORC_TILE;
-        double T = 1.0, C[3] = {0, 0, 0}, m = INFINITY;
+        double T = 1.0, C[3] = {0, 0, 0}, m = INFINITY, tie = INFINITY, prev_z = -1.0;
         int32_t n_last = 0;
         for (int64_t e = tile_start[t]; e < tile_start[t + 1]; ++e) {
             long g = list[e];
@@ -420,6 +425,10 @@ void orc_blend(int W, int H, const int64_t* tile_start, const int64_t* list, con
             if (power > 0) continue;
             if (raw < ORC_ALPHA_MAX) m = dmin(m, fabs(raw - ORC_ALPHA_MIN) / ORC_ALPHA_MIN);
             if (alpha < ORC_ALPHA_MIN) continue;
+            if (depth) {
+                if (prev_z >= 0) tie = dmin(tie, fabs(depth[g] - prev_z) / dmax(prev_z, 1e-300));
+                prev_z = depth[g];
+            }
             double Tn = T * (1.0 - alpha);
             m = dmin(m, fabs(Tn - ORC_T_MIN) / ORC_T_MIN);
             if (Tn < ORC_T_MIN) break;
@@ -437,6 +446,7 @@ void orc_blend(int W, int H, const int64_t* tile_start, const int64_t* list, con
         Tfinal[pix] = T;
         last[pix] = n_last;
         if (px_margin) px_margin[pix] = m;
+        if (px_tie) px_tie[pix] = tie;
     }
 }
 

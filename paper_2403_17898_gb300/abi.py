@@ -1,0 +1,214 @@
+"""Thin Python binding of the C ABI in ``include/ogs.h`` (argument marshalling only).
+
+Every function here has the name of its C entry point without the ``ogs_`` prefix, takes
+CUDA tensors (device memory) plus plain numbers, and enqueues the call on the current torch
+stream (or ``stream``).  All arithmetic happens in ``libogs.so``; if the library is missing
+the import fails with an error instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libogs.so")
+
+STATUS = {0: "OGS_OK", 1: "OGS_ERR_ARG", 2: "OGS_ERR_CAPACITY", 3: "OGS_ERR_TIMEOUT",
+          4: "OGS_ERR_CUDA"}
+
+
+class OgsError(RuntimeError):
+    pass
+
+
+class Camera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("campos", C.c_float * 3), ("fx", C.c_float),
+                ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int32),
+                ("height", C.c_int32), ("znear", C.c_float), ("d_max", C.c_float),
+                ("s", C.c_float), ("pad", C.c_float)]
+
+
+class Counts(C.Structure):
+    _fields_ = [(n, C.c_uint32) for n in ("n_selected", "n_gaussians", "n_pairs", "overflow",
+                                          "need_selected", "need_pairs", "timeout", "n_visible")]
+
+
+COUNT_FIELDS = [f[0] for f in Counts._fields_]
+
+
+class MLP(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("w1", "b1", "w2_op", "b2_op", "w2_col", "b2_col",
+                                          "w2_cov", "b2_cov")] + \
+               [("F", C.c_int32), ("H", C.c_int32), ("k", C.c_int32), ("pad", C.c_int32)]
+
+
+class Gaussians(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("means", "scales", "quats", "opac", "colors")]
+
+
+_P = C.c_void_p
+_I64 = C.c_int64
+_I32 = C.c_int32
+_SZ = C.c_size_t
+
+_SIGS = {
+    "ogs_lod_select_scratch_bytes": (_SZ, [_I64]),
+    "ogs_lod_select": (C.c_int, [_P, _P, _P, _I64, _I32, _I32, C.POINTER(Camera), _I32, _P, _P,
+                                 _I64, _P, _P, _SZ, _P]),
+    "ogs_decode": (C.c_int, [_P, _P, _P, _P, _I64, C.POINTER(MLP), C.POINTER(Camera), _P, _P,
+                             _I64, _P, C.POINTER(Gaussians), _P]),
+    "ogs_project_bin": (C.c_int, [C.POINTER(Gaussians), _I64, _I32, C.POINTER(Camera), _P, _P,
+                                  _P, _P, _P, _P]),
+    "ogs_sort_scratch_bytes": (_SZ, [_I64, _I64, _I32]),
+    "ogs_sort": (C.c_int, [_P, _P, _P, _I64, _I64, _I32, _I32, _P, _P, _I64, _P, _P, _SZ, _P]),
+    "ogs_radix_sort_scratch_bytes": (_SZ, [_I64]),
+    "ogs_radix_sort_pairs": (C.c_int, [_P, _P, _P, _I64, _I32, _I32, _P, _SZ, _P]),
+    "ogs_blend_fwd": (C.c_int, [_P, _P, _P, _I32, _I32, C.POINTER(C.c_float * 3), _P, _P, _P,
+                                _P, _I32, _P, _P]),
+    "ogs_version": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libogs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OgsError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_2403_17898_gb300.build` (needs nvcc)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(st, what):
+    if st != 0:
+        raise OgsError(f"{what} failed: {STATUS.get(st, st)}")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise OgsError("expected a CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def camera(cam) -> Camera:
+    """synth.Camera (or any object with the same fields) -> ogs_camera."""
+    c = Camera()
+    R = np.asarray(cam.R, np.float32).reshape(9)
+    p = np.asarray(cam.campos, np.float32).reshape(3)
+    for i in range(9):
+        c.R[i] = float(R[i])
+    for i in range(3):
+        c.campos[i] = float(p[i])
+    c.fx, c.fy, c.cx, c.cy = (float(np.float32(v)) for v in (cam.fx, cam.fy, cam.cx, cam.cy))
+    c.width, c.height = int(cam.W), int(cam.H)
+    c.znear, c.d_max, c.s = (float(np.float32(v)) for v in (cam.znear, cam.d_max, cam.s))
+    return c
+
+
+def mlp_struct(t, k=10, F=32, H=32) -> MLP:
+    """Decoder weights (dict of CUDA float32 tensors named like synth.DecoderMLP)."""
+    m = MLP()
+    for n in ("w1", "b1", "w2_op", "b2_op", "w2_col", "b2_col", "w2_cov", "b2_cov"):
+        setattr(m, n, t[n].data_ptr())
+    m.F, m.H, m.k = F, H, k
+    return m
+
+
+def gaussians_struct(t) -> Gaussians:
+    g = Gaussians()
+    for n in ("means", "scales", "quats", "opac", "colors"):
+        setattr(g, n, t[n].data_ptr())
+    return g
+
+
+# ---------------------------------------------------------------------------------------
+# entry points
+# ---------------------------------------------------------------------------------------
+
+def lod_select_scratch_bytes(N):
+    return int(lib().ogs_lod_select_scratch_bytes(int(N)))
+
+
+def lod_select(pos, level, dL, N, NL, k, cam, infer, sel_idx, sel_w, sel_cap, counts,
+               scratch, stream=None):
+    c = cam if isinstance(cam, Camera) else camera(cam)
+    _check(lib().ogs_lod_select(_ptr(pos), _ptr(level), _ptr(dL), int(N), int(NL), int(k),
+                                C.byref(c), int(bool(infer)), _ptr(sel_idx), _ptr(sel_w),
+                                int(sel_cap), _ptr(counts), _ptr(scratch), scratch.numel(),
+                                _stream(stream)), "ogs_lod_select")
+
+
+def decode(pos, feat, offs, lv, N, mlp, cam, sel_idx, sel_w, sel_cap, counts, out,
+           stream=None):
+    c = cam if isinstance(cam, Camera) else camera(cam)
+    m = mlp if isinstance(mlp, MLP) else mlp_struct(mlp)
+    g = out if isinstance(out, Gaussians) else gaussians_struct(out)
+    _check(lib().ogs_decode(_ptr(pos), _ptr(feat), _ptr(offs), _ptr(lv), int(N), C.byref(m),
+                            C.byref(c), _ptr(sel_idx), _ptr(sel_w), int(sel_cap), _ptr(counts),
+                            C.byref(g), _stream(stream)), "ogs_decode")
+
+
+def project_bin(g, n_gauss, means_relative, cam, rec, depth_key, rect, tiles, counts=None,
+                stream=None):
+    c = cam if isinstance(cam, Camera) else camera(cam)
+    gs = g if isinstance(g, Gaussians) else gaussians_struct(g)
+    _check(lib().ogs_project_bin(C.byref(gs), int(n_gauss), int(means_relative), C.byref(c),
+                                 _ptr(rec), _ptr(depth_key), _ptr(rect), _ptr(tiles),
+                                 _ptr(counts), _stream(stream)), "ogs_project_bin")
+
+
+def sort_scratch_bytes(g_cap, pair_cap, n_tiles):
+    return int(lib().ogs_sort_scratch_bytes(int(g_cap), int(pair_cap), int(n_tiles)))
+
+
+def sort(depth_key, rect, tiles, g_cap, n_gauss, grid_x, grid_y, pair_gauss, tile_range,
+         pair_cap, counts, scratch, stream=None):
+    _check(lib().ogs_sort(_ptr(depth_key), _ptr(rect), _ptr(tiles), int(g_cap), int(n_gauss),
+                          int(grid_x), int(grid_y), _ptr(pair_gauss), _ptr(tile_range),
+                          int(pair_cap), _ptr(counts), _ptr(scratch), scratch.numel(),
+                          _stream(stream)), "ogs_sort")
+
+
+def radix_sort_scratch_bytes(n_cap):
+    return int(lib().ogs_radix_sort_scratch_bytes(int(n_cap)))
+
+
+def radix_sort_pairs(keys, vals, n_dev, n_cap, bit_lo, bit_hi, scratch, stream=None):
+    _check(lib().ogs_radix_sort_pairs(_ptr(keys), _ptr(vals), _ptr(n_dev), int(n_cap),
+                                      int(bit_lo), int(bit_hi), _ptr(scratch), scratch.numel(),
+                                      _stream(stream)), "ogs_radix_sort_pairs")
+
+
+def blend_fwd(rec, pair_gauss, tile_range, width, height, bg, img, T_final, n_last,
+              sel_idx=None, k=10, maxc=None, stream=None):
+    b = (C.c_float * 3)(*[float(x) for x in bg])
+    _check(lib().ogs_blend_fwd(_ptr(rec), _ptr(pair_gauss), _ptr(tile_range), int(width),
+                               int(height), C.byref(b), _ptr(img), _ptr(T_final), _ptr(n_last),
+                               _ptr(sel_idx), int(k), _ptr(maxc), _stream(stream)),
+           "ogs_blend_fwd")
+
+
+def version():
+    return lib().ogs_version().decode()

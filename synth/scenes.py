@@ -243,15 +243,19 @@ def cube_scene(seed=0, N=4096, NL=3, extent=10.0, k=K_GAUSS, F=F_DIM) -> Scene:
 
 
 def _city_boxes(rng, extent, block=100.0, street=20.0, plaza=40.0):
-    """Boxes (x0, y0, x1, y1, h) on a street grid; the grid is centred on the origin and a
-    plaza of radius ``plaza`` around the centre is kept free of buildings."""
+    """Boxes (x0, y0, x1, y1, h) on a street grid centred on the origin, 1-4 per 100 m block
+    (footprint and height U[10, 60] m); a plaza of radius ``plaza`` around the centre is kept
+    free of buildings.  Also returns a [nb, nb, 4] table of each block's box indices (-1 =
+    none) for fast point-in-footprint queries."""
     pitch = block + street
     nb = int(math.ceil(extent / pitch))
     boxes = []
+    table = -np.ones((nb, nb, 4), np.int64)
     for bi in range(nb):
         for bj in range(nb):
             bx0 = -extent / 2 + bi * pitch + street / 2
             by0 = -extent / 2 + bj * pitch + street / 2
+            slot = 0
             for _ in range(int(rng.integers(1, 5))):
                 wx, wy, h = rng.uniform(10.0, 60.0, size=3)
                 x0 = bx0 + rng.uniform(0.0, block - wx)
@@ -259,24 +263,31 @@ def _city_boxes(rng, extent, block=100.0, street=20.0, plaza=40.0):
                 cxb, cyb = x0 + wx / 2, y0 + wy / 2
                 if math.hypot(cxb, cyb) < plaza + max(wx, wy) / 2:
                     continue
+                table[bi, bj, slot] = len(boxes)
+                slot += 1
                 boxes.append((x0, y0, x0 + wx, y0 + wy, h))
-    return np.asarray(boxes, np.float64)
+    return np.asarray(boxes, np.float64).reshape(-1, 5), table, pitch
 
 
-def _sample_surface(rng, boxes, half, n):
+def _sample_surface(rng, city, extent, half, n):
     """n points uniformly (by area) on the ground square [-half, half]^2 (outside box
     footprints) and on the top and side faces of the boxes, restricted to |x|,|y| <= half."""
+    boxes, table, pitch = city
     x0, y0, x1, y1, h = boxes.T
     wx, wy = x1 - x0, y1 - y0
-    # faces: ground, then per box: top, -x, +x, -y, +y
-    areas = [4 * half * half]
-    areas += list(wx * wy) + list(wy * h) + list(wy * h) + list(wx * h) + list(wx * h)
-    areas = np.asarray(areas)
-    nbx = len(boxes)
-    out = np.empty((0, 3))
-    while out.shape[0] < n:
-        m = int((n - out.shape[0]) * 1.6) + 64
-        face = rng.choice(len(areas), size=m, p=areas / areas.sum())
+    # only boxes that reach into the square can receive samples
+    near = (x1 >= -half) & (x0 <= half) & (y1 >= -half) & (y0 <= half)
+    bidx = np.nonzero(near)[0]
+    nbx = len(bidx)
+    # faces: ground, then per nearby box: top, -x, +x, -y, +y
+    areas = np.concatenate([[4 * half * half], (wx * wy)[bidx], (wy * h)[bidx], (wy * h)[bidx],
+                            (wx * h)[bidx], (wx * h)[bidx]])
+    prob = areas / areas.sum()
+    out = []
+    have = 0
+    while have < n:
+        m = int((n - have) * 1.3) + 64
+        face = rng.choice(len(areas), size=m, p=prob)
         u, v = rng.uniform(size=m), rng.uniform(size=m)
         P = np.zeros((m, 3))
         g = face == 0
@@ -285,7 +296,7 @@ def _sample_surface(rng, boxes, half, n):
         fb = face - 1
         for kind in range(5):
             sel = (fb >= kind * nbx) & (fb < (kind + 1) * nbx) & ~g
-            b = fb[sel] - kind * nbx
+            b = bidx[fb[sel] - kind * nbx]
             uu, vv = u[sel], v[sel]
             if kind == 0:
                 P[sel] = np.stack([x0[b] + uu * wx[b], y0[b] + vv * wy[b], h[b]], 1)
@@ -298,30 +309,36 @@ def _sample_surface(rng, boxes, half, n):
             else:
                 P[sel] = np.stack([x0[b] + uu * wx[b], y1[b], vv * h[b]], 1)
         keep = (np.abs(P[:, 0]) <= half) & (np.abs(P[:, 1]) <= half)
-        if nbx:
-            # ground points under a footprint are hidden: drop them
-            inside = np.zeros(m, bool)
+        if len(boxes):
+            # ground points under a footprint are hidden: drop them (block-table lookup)
             gi = np.nonzero(g)[0]
-            for s in range(0, nbx, 256):
-                bb = boxes[s:s + 256]
-                px, py = P[gi, 0:1], P[gi, 1:2]
-                inside[gi] |= ((px >= bb[:, 0]) & (px <= bb[:, 2]) &
-                               (py >= bb[:, 1]) & (py <= bb[:, 3])).any(1)
-            keep &= ~inside
-        out = np.concatenate([out, P[keep]])
-    return out[:n]
+            nbk = table.shape[0]
+            bi = np.clip(((P[gi, 0] + extent / 2) // pitch).astype(np.int64), 0, nbk - 1)
+            bj = np.clip(((P[gi, 1] + extent / 2) // pitch).astype(np.int64), 0, nbk - 1)
+            inside = np.zeros(len(gi), bool)
+            for slot in range(4):
+                k = table[bi, bj, slot]
+                has = k >= 0
+                kk = np.where(has, k, 0)
+                inside |= has & (P[gi, 0] >= x0[kk]) & (P[gi, 0] <= x1[kk]) & \
+                    (P[gi, 1] >= y0[kk]) & (P[gi, 1] <= y1[kk])
+            keep[gi[inside]] = False
+        P = P[keep]
+        out.append(P)
+        have += len(P)
+    return np.concatenate(out)[:n]
 
 
-def city_scene(seed=0, N=2_000_000, NL=8, extent=2000.0, c0=4.0, gamma=0.85,
+def city_scene(seed=0, N=2_000_000, NL=8, extent=2000.0, c0=4.0, gamma=0.55,
                k=K_GAUSS, F=F_DIM) -> Scene:
     """Street-grid city of side ``extent`` (blocks 100 m, streets 20 m, 1-4 boxes per block
     with footprint and height U[10, 60] m) plus ground.  Level-L anchors are voxel centres
-    (cell c0/2^L) of surface samples inside a centred square of half-width
+    (cell c0/2^L, Eq. for V_L) of surface samples inside a centred square of half-width
     (extent/2)·2^(-gamma·L): fine levels concentrate where a zoom-out path starts, as in
     multi-scale captures.  Per-level counts follow the number of cells that square holds,
     (2^((1-gamma)·L))^2, scaled to N; duplicates within a level are removed."""
     rng = np.random.default_rng(seed)
-    boxes = _city_boxes(rng, extent)
+    city = _city_boxes(rng, extent)
     w = np.array([4.0 ** ((1.0 - gamma) * L) for L in range(NL)])
     counts = np.floor(N * w / w.sum()).astype(np.int64)
     counts[-1] += N - counts.sum()
@@ -330,26 +347,25 @@ def city_scene(seed=0, N=2_000_000, NL=8, extent=2000.0, c0=4.0, gamma=0.85,
     for L in range(NL):
         half = (extent / 2) * 2.0 ** (-gamma * L)
         need = int(counts[L])
-        got = np.empty((0, 3))
-        keys_seen = np.empty(0, np.int64)
-        tries = 0
-        while got.shape[0] < need:
-            tries += 1
-            if tries > 40:
-                raise RuntimeError(f"level {L}: only {got.shape[0]} of {need} free cells")
-            P = _sample_surface(rng, boxes, half, int((need - got.shape[0]) * 1.3) + 16)
-            V = np.round(P / cell[L])                     # Eq. V_L voxelisation
+        keys = np.empty(0, np.int64)
+        V_all = np.empty((0, 3))
+        batch = int(need * 1.5) + 64
+        for _ in range(40):
+            P = _sample_surface(rng, city, extent, half, batch)
+            V = np.round(P / cell[L])
             key = ((V[:, 0].astype(np.int64) + (1 << 20)) << 42) | \
                   ((V[:, 1].astype(np.int64) + (1 << 20)) << 21) | \
                   (V[:, 2].astype(np.int64) + (1 << 20))
-            _, first = np.unique(key, return_index=True)
-            first = np.sort(first)
-            key, V = key[first], V[first]
-            fresh = ~np.isin(key, keys_seen)
-            key, V = key[fresh], V[fresh]
-            keys_seen = np.concatenate([keys_seen, key])
-            got = np.concatenate([got, V * cell[L]])
-        pos.append(got[:need])
+            keys = np.concatenate([keys, key])
+            V_all = np.concatenate([V_all, V])
+            _, first = np.unique(keys, return_index=True)
+            if len(first) >= need:
+                break
+            batch = int((need - len(first)) * 3) + 64
+        else:
+            raise RuntimeError(f"level {L}: only {len(first)} of {need} free cells")
+        first = np.sort(first)[:need]
+        pos.append(V_all[first] * cell[L])
         lev.append(np.full(need, L, np.uint8))
     pos = np.concatenate(pos).astype(np.float32)
     level = np.concatenate(lev)
@@ -359,7 +375,7 @@ def city_scene(seed=0, N=2_000_000, NL=8, extent=2000.0, c0=4.0, gamma=0.85,
     return Scene(pos=np.ascontiguousarray(pos), level=level, dL=dL, feat=feat, offs=offs,
                  lv=lv, NL=NL, k=k, meta={"kind": "city", "extent": extent, "c0": c0,
                                            "gamma": gamma, "counts": counts.tolist(),
-                                           "n_boxes": int(len(boxes))})
+                                           "n_boxes": int(len(city[0]))})
 
 
 # --------------------------------------------------------------------------------------
@@ -391,8 +407,9 @@ def random_gaussians(seed, G, cam: Camera, depth=(2.0, 30.0), scale=(0.05, 0.8),
 
 
 def random_records(seed, G, W, H, sigma=(0.6, 12.0), opac=(0.05, 0.99)):
-    """Random screen-space Gaussians: centre (u, v), 2x2 covariance from random axes, opacity,
-    colour and a strictly positive depth, spread over a W x H image (with a margin)."""
+    """Random screen-space Gaussians: centre (u, v), 2x2 covariance from random axes and its
+    inverse (conic), opacity, colour and a strictly positive depth, spread over a W x H image
+    (with a margin)."""
     rng = np.random.default_rng(seed)
     u = rng.uniform(-0.1 * W, 1.1 * W, size=G)
     v = rng.uniform(-0.1 * H, 1.1 * H, size=G)
@@ -406,9 +423,14 @@ def random_records(seed, G, W, H, sigma=(0.6, 12.0), opac=(0.05, 0.99)):
     o = rng.uniform(*opac, size=G)
     col = rng.uniform(0, 1, size=(G, 3))
     depth = rng.uniform(1.0, 50.0, size=G)
+    # inverse of [[a, b], [b, d]] from the same axes: R diag(1/s1^2, 1/s2^2) R^T
+    ia = c * c / (s1 * s1) + s * s / (s2 * s2)
+    ib = c * s * (1 / (s1 * s1) - 1 / (s2 * s2))
+    idd = s * s / (s1 * s1) + c * c / (s2 * s2)
     f = np.float32
     return dict(u=u.astype(f), v=v.astype(f), cov=np.stack([a, b, d], 1).astype(f),
-                opac=o.astype(f), colors=col.astype(f), depth=depth.astype(f))
+                conic=np.stack([ia, ib, idd], 1).astype(f), opac=o.astype(f),
+                colors=col.astype(f), depth=depth.astype(f))
 
 
 def random_rects_depths(seed, G, gx, gy, max_span=6, equal_depth_frac=0.05):

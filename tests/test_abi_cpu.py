@@ -1,0 +1,69 @@
+"""Host-side checks of the C-ABI library that need no GPU: it builds for sm_103a, loads, and
+exports every entry point that include/ogs.h declares (no compute call is made)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(ogs_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2403_17898_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_entry_points():
+    d = _declared()
+    for n in ("ogs_lod_select", "ogs_decode", "ogs_project_bin", "ogs_sort", "ogs_blend_fwd",
+              "ogs_radix_sort_pairs"):
+        assert n in d
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2403_17898_gb300 import abi
+    assert set(_declared()) <= set(abi.exported_symbols())
+
+
+def test_host_argument_checks_without_gpu(lib):
+    """Invalid arguments are rejected on the host before anything is enqueued."""
+    lib.ogs_lod_select_scratch_bytes.restype = ctypes.c_size_t
+    lib.ogs_lod_select_scratch_bytes.argtypes = [ctypes.c_int64]
+    assert lib.ogs_lod_select_scratch_bytes(4096) >= 4
+    from paper_2403_17898_gb300 import abi
+    L = abi.lib()
+    cam = abi.Camera()
+    cam.width, cam.height, cam.d_max, cam.s = 64, 64, 10.0, 1.0
+    # null anchor pointers -> OGS_ERR_ARG (1), no CUDA call made
+    st = L.ogs_lod_select(None, None, None, 10, 3, 10, ctypes.byref(cam), 1, None, None, 10,
+                          None, None, 0, None)
+    assert st == 1
+    st = L.ogs_radix_sort_pairs(None, None, None, 10, 0, 32, None, 0, None)
+    assert st == 1
+    assert abi.version().startswith("ogs-gb300")
+
+
+def test_product_path_fails_loudly_without_library(tmp_path, monkeypatch):
+    from paper_2403_17898_gb300 import abi
+    monkeypatch.setattr(abi, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(abi, "_lib", None)
+    with pytest.raises(abi.OgsError):
+        abi.lib()
