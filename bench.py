@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark: 1080p frames/s of the Octree-GS LOD renderer hot path on GB300.
+
+Workload (default): 2M anchors over 8 octree levels on a 2 km synthetic city grid, k = 10
+neural Gaussians per anchor, 1920x1080, a 120-pose zoom-out from 10 m to 2 km altitude.  A
+step is one view through the whole forward hot path (LOD selection, decoding, projection and
+binning, sorting, blending); step i renders pose (rank + i * world) mod 120.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on the host
+cores instead (rank 0 only), each step a 1/16 sub-view of a frame.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "city2M_1080p"
+WORKLOAD_DESC = ("2M anchors / 8 levels / 2 km synthetic city grid, k=10, 1920x1080, "
+                 "120-pose zoom-out 10 m -> 2 km, FP32 decode")
+METRIC = "1080p FPS (frames/s)"
+# FP32 operations of one (pixel, Gaussian) blend evaluation of Eq. 2 with the rasterizer
+# conventions: offset (2), quadratic form (7), exp (2), clamp/skip (3), transmittance and
+# stop (3), weight and colour (4)
+OPS_PER_EVAL = 21
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        reasons = set()
+        for _, _, flags in rows:
+            for n, v in zip(names[1:], flags[1:]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload():
+    import synth
+    return synth.CONFIGS[WORKLOAD]()
+
+
+# ---------------------------------------------------------------------------------------
+# algorithmic bytes per stage (inputs read once, outputs written once)
+# ---------------------------------------------------------------------------------------
+
+def stage_bytes(N, M, G, P, n_tiles, pixels, k=10):
+    return {
+        "lod_select": N * (12 + 1 + 4) + M * 8,
+        "decode": M * (8 + 12 + 128 + 12 * k + 12) + G * 56,
+        "project_bin": G * 56 + G * (48 + 4 + 8 + 4),
+        "sort": G * (4 + 8 + 4) + P * 4 + n_tiles * 8,
+        "blend_fwd": P * (36 + 4) + n_tiles * 8 + pixels * (12 + 4 + 4),
+    }
+
+
+# ---------------------------------------------------------------------------------------
+# CPU oracle timing
+# ---------------------------------------------------------------------------------------
+
+def oracle_frame(sc, mlp, cam):
+    import oracle
+    oracle.render(sc, mlp, cam, infer=True)
+
+
+def sub_view(cam, i, nx=4, ny=4):
+    """Camera for the i-th of nx*ny windows of a frame: same centre and focal length, optical
+    axis through the window centre, window-sized image."""
+    import synth
+    W, H = cam.W // nx, cam.H // ny
+    wx, wy = i % nx, i // nx
+    u = (wx + 0.5) * W - 0.5
+    v = (wy + 0.5) * H - 0.5
+    d_cam = np.array([(u - cam.cx) / cam.fx, (v - cam.cy) / cam.fy, 1.0])
+    d_world = cam.R.astype(np.float64).T @ d_cam
+    c = cam.campos.astype(np.float64)
+    up = -cam.R[1].astype(np.float64)
+    sv = synth.look_at_camera(c, c + d_world, W, H, up=tuple(up), d_max=cam.d_max)
+    sv.fx = sv.fy = float(np.float32(cam.fx))
+    return sv
+
+
+def cpu_baseline(sc, mlp, cams, frames=8):
+    idx = np.linspace(0, len(cams) - 1, frames).round().astype(int)
+    oracle_frame(sc, mlp, cams[int(idx[0])])          # builds the library, warms caches
+    t0 = time.perf_counter()
+    for i in idx:
+        oracle_frame(sc, mlp, cams[int(i)])
+    dt = time.perf_counter() - t0
+    return {"value": frames / dt, "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{frames} full 1920x1080 frames at poses {idx.tolist()} of the "
+                      f"120-pose path ({dt:.1f} s, FP64 C oracle, OpenMP in blending)"}
+
+
+def _as_f64(sc, mlp):
+    """One-time float64 copies so the oracle's per-call conversions are no-ops."""
+    import synth
+    sc64 = synth.Scene(pos=sc.pos.astype(np.float64), level=sc.level.astype(np.int32),
+                       dL=sc.dL.astype(np.float64), feat=sc.feat.astype(np.float64),
+                       offs=sc.offs.astype(np.float64), lv=sc.lv.astype(np.float64),
+                       NL=sc.NL, k=sc.k, meta=sc.meta)
+    mlp64 = synth.DecoderMLP(*[a.astype(np.float64) for a in mlp.arrays()])
+    return sc64, mlp64
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    sc, mlp, cams = _workload()
+    sc, mlp = _as_f64(sc, mlp)
+    n = len(cams)
+    views = lambda step: sub_view(cams[(step // 16) % n], step % 16)
+    oracle_frame(sc, mlp, views(0))
+    for s in range(args.warmup):
+        oracle_frame(sc, mlp, views(s))
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        oracle_frame(sc, mlp, views(args.warmup + s))
+    dt = time.perf_counter() - t0
+    fps = (args.steps / 16.0) / dt
+    sample = ("each step renders one 480x270 sub-view (1/16 of the pixels, same focal length, "
+              "axis through the window centre) of a 1080p frame; 16 steps = 1 frame")
+    line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC},
+            "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------
+
+# kernels each ABI call launches per frame (radix passes: 4 depth + 2 tile, 3 kernels each)
+LAUNCHES = {"lod_select": 3, "decode": 1, "project_bin": 1,
+            "sort": 1 + 3 * 4 + 3 + 3 * 2 + 1, "blend_fwd": 1}
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2403_17898_gb300 import build as _b
+    _b.build()
+    from paper_2403_17898_gb300.render import Renderer
+
+    sc, mlp, cams = _workload()
+    n = len(cams)
+    W, H = cams[0].W, cams[0].H
+    rd = Renderer(sc, mlp, W, H, sel_cap=200_000, pair_cap=4_000_000)
+    # size buffers over the whole path, record per-pose work
+    per_pose = []
+    n_eval = torch.zeros(H, W, dtype=torch.int32, device="cuda")
+    for cam in cams:
+        c = rd.render(cam)
+        rd.enqueue(cam, n_eval=n_eval)
+        ev = int(n_eval.sum().item())
+        per_pose.append((c.n_selected, c.n_gaussians, c.n_pairs, ev))
+    pose = lambda i: (rank + i * ws) % n
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 126 MB L2
+    for i in range(args.warmup):
+        flush.zero_()
+        rd.enqueue(cams[pose(i)])
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    timers = {}
+    steps = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            rd.enqueue(cams[pose(args.warmup + i)], timers=timers)
+            e1.record()
+            steps.append((e0, e1))
+        torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in steps]
+    total_s = sum(step_ms) / 1e3
+    stage_ms = {k: [a.elapsed_time(b) for a, b in v] for k, v in timers.items()}
+    c = rd.counts()
+    assert c.overflow == 0, "buffers overflowed during the timed steps"
+    t_max = total_s
+    if ws > 1:
+        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    fps = ws * args.steps / t_max
+
+    # end-to-end through the public call: render + image to pinned host memory, per step
+    host = torch.empty(3, H, W, dtype=torch.float32, pin_memory=True)
+    n_e2e = min(args.steps, 600)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for i in range(n_e2e):
+        rd.render_to_host(cams[pose(i)], host)
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_fps = ws * n_e2e / e2e_s
+
+    if rank != 0:
+        dist.destroy_process_group() if ws > 1 else None
+        return 0
+
+    # roofline of the dominant stage, from the timed steps
+    peaks, src = _peaks()
+    clocks = clk.summary()
+    timed_poses = [pose(args.warmup + i) for i in range(args.steps)]
+    mean_ms = {k: float(np.mean(v)) for k, v in stage_ms.items()}
+    dominant = max(mean_ms, key=mean_ms.get)
+    evals = float(np.mean([per_pose[p][3] for p in timed_poses]))
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12          # Tops/s
+    stages = {}
+    for k, v in mean_ms.items():
+        b = float(np.mean([stage_bytes(sc.N, per_pose[p][0], per_pose[p][1], per_pose[p][2],
+                                       rd.gx * rd.gy, W * H)[k] for p in timed_poses]))
+        stages[k] = {"ms": v, "algorithmic_GB_per_s": b / (v * 1e-3) / 1e9,
+                     "hbm_frac": b / (v * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+    if dominant == "blend_fwd":
+        ach = evals * OPS_PER_EVAL / (mean_ms["blend_fwd"] * 1e-3) / 1e12
+        roof = {"kernel": "blend_fwd", "bound": "alu", "achieved": ach, "peak": alu_peak,
+                "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": None,
+                "work": f"{evals:.4g} (pixel, Gaussian) evaluations x {OPS_PER_EVAL} FP32 ops",
+                "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                               f"{sm_max:.0f} MHz ({src} sm_max_mhz)"}
+    else:
+        gbs = stages[dominant]["algorithmic_GB_per_s"]
+        roof = {"kernel": dominant, "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": f"{src} hbm_gbs"}
+
+    line = {
+        "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "anchors": sc.N, "levels": sc.NL,
+                   "resolution": f"{W}x{H}", "poses": n, "parallelism": f"replicas x{ws}",
+                   "l2": "256 MB buffer written between timed steps (L2 is 126 MB)",
+                   "mean_selected_anchors": float(np.mean([per_pose[p][0] for p in timed_poses])),
+                   "mean_gaussians": float(np.mean([per_pose[p][1] for p in timed_poses])),
+                   "mean_pairs": float(np.mean([per_pose[p][2] for p in timed_poses])),
+                   "mean_evaluations": evals},
+        "roofline": roof,
+        "stages_ms": {k: round(v, 5) for k, v in mean_ms.items()},
+        "stages": stages,
+        "clocks": clocks,
+        "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": 88,
+                "d2h_bytes_per_step": 3 * W * H * 4, "steps": n_e2e,
+                "call": "Renderer.render_to_host (render + image to pinned host memory)"},
+        "gpu_launches": args.steps * sum(LAUNCHES.values()),
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(*_as_f64(sc, mlp), cams)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

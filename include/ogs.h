@@ -176,8 +176,9 @@ ogs_status ogs_project_bin(const ogs_gaussians* g /* host struct */, int64_t n_g
  *   depth_key/rect/tiles from ogs_project_bin; count = counts->n_gaussians (or n_gauss)
  *   pair_gauss u32[pair_cap]: Gaussian id of each pair, tile-major, front-to-back
  *   tile_range u32[n_tiles][2]: [start, end) of each tile in pair_gauss
- *   counts->n_pairs = P; if P > pair_cap, overflow bit 1 is set, need_pairs = P and only
- *   tile_range is left empty.
+ *   counts->n_pairs = P; if P > pair_cap, overflow bit 1 is set, need_pairs = P and
+ *   no pair is emitted (every tile range is empty).
+ *   n_gauss < 0 takes the Gaussian count from counts->n_gaussians (as written by ogs_decode).
  *   scratch: ogs_sort_scratch_bytes(g_cap, pair_cap, n_tiles) bytes, 16-byte aligned.
  * ------------------------------------------------------------------------------------- */
 size_t ogs_sort_scratch_bytes(int64_t g_cap, int64_t pair_cap, int32_t n_tiles);
@@ -206,6 +207,8 @@ ogs_status ogs_radix_sort_pairs(uint32_t* keys, uint32_t* vals, const uint32_t* 
  *   bg: host float[3]
  *   img f32[3][H][W], T_final f32[H][W], n_last u32[H][W] (list entries up to and
  *   including the last blended one)
+ *   n_eval (optional, may be NULL): u32[H][W], list entries the pixel evaluated before it
+ *   saturated or ran out (the blend's unit of work)
  *   maxc (optional, may be NULL): u32[N_anchors], float bits of the largest T*alpha of any
  *   blended Gaussian of each anchor (atomic max; caller zeroes); anchor of Gaussian g is
  *   sel_idx[g / k].
@@ -213,8 +216,73 @@ ogs_status ogs_radix_sort_pairs(uint32_t* keys, uint32_t* vals, const uint32_t* 
 ogs_status ogs_blend_fwd(const ogs_rec2d* rec, const uint32_t* pair_gauss,
                          const uint32_t* tile_range, int32_t width, int32_t height,
                          const float* bg /* host float[3] */, float* img, float* T_final,
-                         uint32_t* n_last, const uint32_t* sel_idx, int32_t k, uint32_t* maxc,
-                         void* stream);
+                         uint32_t* n_last, uint32_t* n_eval, const uint32_t* sel_idx, int32_t k,
+                         uint32_t* maxc, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * ogs_blend_bwd — backward of ogs_blend_fwd (Sec. 3.1, Eq. 2).  With C = sum_i c_i a_i T_i +
+ * T_{n+1} bg: dC/dc_i = a_i T_i, dC/da_i = T_i (c_i - S_i) with S the colour behind i.  Each
+ * pixel replays its list back to front from n_last, recovering T_i = T_{i+1}/(1 - a_i) from
+ * T_final (no per-pair storage); a = min(0.99, o G) has zero derivative where clamped.
+ *   rec, pair_gauss, tile_range, T_final, n_last: as produced by the forward
+ *   bg: host float[3];  dimg f32[3][H][W] = dL/dimage
+ *   drec f32[G][9] (ACCUMULATED, caller zeroes): dL/d(u, v, conic a, conic b, conic c,
+ *   opacity, r, g, b) per Gaussian.  Atomic accumulation: float summation order varies.
+ * ------------------------------------------------------------------------------------- */
+ogs_status ogs_blend_bwd(const ogs_rec2d* rec, const uint32_t* pair_gauss,
+                         const uint32_t* tile_range, int32_t width, int32_t height,
+                         const float* bg /* host float[3] */, const float* T_final,
+                         const uint32_t* n_last, const float* dimg, float* drec, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * ogs_project_bwd — backward of the EWA projection of ogs_project_bin (Sec. 3.1, Eq. 1):
+ * d(u, v, conic) -> d(mean, scale, unit quaternion).  Gaussians with an empty rect get 0.
+ *   g, means_relative, cam: as given to ogs_project_bin; rect from it; drec from
+ *   ogs_blend_bwd; count = counts->n_gaussians if counts != NULL else n_gauss
+ *   dmeans f32[G][3], dscales f32[G][3], dquats f32[G][4] (written, not accumulated)
+ * ------------------------------------------------------------------------------------- */
+ogs_status ogs_project_bwd(const ogs_gaussians* g /* host struct */, int64_t n_gauss,
+                           int32_t means_relative, const ogs_camera* cam /* host */,
+                           const uint32_t* rect, const float* drec, float* dmeans,
+                           float* dscales, float* dquats, const ogs_counts* counts,
+                           void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * ogs_decode_bwd — backward of ogs_decode (Sec. 3.2, Eq. offsets and Eq. mlp): per selected
+ * anchor, recomputes the three decoders and chains the per-Gaussian gradients (dmeans,
+ * dscales, dquats from ogs_project_bwd; opacity and colour gradients from drec) into
+ *   dfeat f32[N][F], doffs f32[N][k][3], dlv f32[N][3]   (ACCUMULATED: +=)
+ *   dmlp: decoder weight gradients, same layout as ogs_mlp  (ACCUMULATED: +=)
+ * Anchor positions, LOD bias and the selection are constants.  Weight gradients are summed
+ * per block and then across blocks in a fixed order.
+ *   scratch: ogs_decode_bwd_scratch_bytes() bytes, 16-byte aligned.
+ * ------------------------------------------------------------------------------------- */
+size_t ogs_decode_bwd_scratch_bytes(void);
+ogs_status ogs_decode_bwd(const float* pos, const float* feat, const float* offs, const float* lv,
+                          int64_t N, const ogs_mlp* mlp /* host struct */,
+                          const ogs_camera* cam /* host */, const uint32_t* sel_idx,
+                          const float* sel_w, const ogs_counts* counts, const float* dmeans,
+                          const float* dscales, const float* dquats, const float* drec,
+                          float* dfeat, float* doffs, float* dlv,
+                          const ogs_mlp* dmlp /* host struct of device ptrs, written */,
+                          void* scratch, size_t scratch_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * ogs_loss_l1 — photometric L1 term of Sec. 5.1.5: loss = mean |img - target| over n
+ * values; dimg = sign(img - target) / n (written); *loss += the mean (device float, caller
+ * zeroes; may be NULL).
+ * ------------------------------------------------------------------------------------- */
+ogs_status ogs_loss_l1(const float* img, const float* target, int64_t n, float* dimg,
+                       float* loss, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * ogs_adam — one Adam step over n parameters (step >= 1 is the 1-based step count used for
+ * bias correction):  m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
+ * p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).  zero_grad != 0 clears g.
+ * ------------------------------------------------------------------------------------- */
+ogs_status ogs_adam(float* param, float* grad, float* m, float* v, int64_t n, float lr,
+                    float beta1, float beta2, float eps, int32_t step, int32_t zero_grad,
+                    void* stream);
 
 /* Library version string (host). */
 const char* ogs_version(void);

@@ -296,3 +296,14 @@ def l1_loss(img, target):
     """Mean absolute error over all channels and pixels, and its gradient."""
     diff = _d(img) - _d(target)
     return float(np.abs(diff).mean()), np.sign(diff) / diff.size
+
+
+def adam(param, grad, m, v, lr, beta1, beta2, eps, step):
+    """One Adam update (the optimiser of the training loop; FP64): returns new (param, m, v).
+    Pinned by its first-step closed form p - lr * g / (|g| + eps') (tests/test_oracle_train)."""
+    param, grad, m, v = _d(param), _d(grad), _d(m), _d(v)
+    m = beta1 * m + (1 - beta1) * grad
+    v = beta2 * v + (1 - beta2) * grad * grad
+    mh = m / (1 - beta1 ** step)
+    vh = v / (1 - beta2 ** step)
+    return param - lr * mh / (np.sqrt(vh) + eps), m, v

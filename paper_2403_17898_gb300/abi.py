@@ -66,7 +66,17 @@ _SIGS = {
     "ogs_radix_sort_scratch_bytes": (_SZ, [_I64]),
     "ogs_radix_sort_pairs": (C.c_int, [_P, _P, _P, _I64, _I32, _I32, _P, _SZ, _P]),
     "ogs_blend_fwd": (C.c_int, [_P, _P, _P, _I32, _I32, C.POINTER(C.c_float * 3), _P, _P, _P,
-                                _P, _I32, _P, _P]),
+                                _P, _P, _I32, _P, _P]),
+    "ogs_blend_bwd": (C.c_int, [_P, _P, _P, _I32, _I32, C.POINTER(C.c_float * 3), _P, _P, _P,
+                                _P, _P]),
+    "ogs_project_bwd": (C.c_int, [C.POINTER(Gaussians), _I64, _I32, C.POINTER(Camera), _P, _P,
+                                  _P, _P, _P, _P, _P]),
+    "ogs_decode_bwd_scratch_bytes": (_SZ, []),
+    "ogs_decode_bwd": (C.c_int, [_P, _P, _P, _P, _I64, C.POINTER(MLP), C.POINTER(Camera), _P, _P,
+                                 _P, _P, _P, _P, _P, _P, _P, _P, C.POINTER(MLP), _P, _SZ, _P]),
+    "ogs_loss_l1": (C.c_int, [_P, _P, _I64, _P, _P, _P]),
+    "ogs_adam": (C.c_int, [_P, _P, _P, _P, _I64, C.c_float, C.c_float, C.c_float, C.c_float,
+                           _I32, _I32, _P]),
     "ogs_version": (C.c_char_p, []),
 }
 
@@ -202,12 +212,56 @@ def radix_sort_pairs(keys, vals, n_dev, n_cap, bit_lo, bit_hi, scratch, stream=N
 
 
 def blend_fwd(rec, pair_gauss, tile_range, width, height, bg, img, T_final, n_last,
-              sel_idx=None, k=10, maxc=None, stream=None):
+              sel_idx=None, k=10, maxc=None, n_eval=None, stream=None):
     b = (C.c_float * 3)(*[float(x) for x in bg])
     _check(lib().ogs_blend_fwd(_ptr(rec), _ptr(pair_gauss), _ptr(tile_range), int(width),
                                int(height), C.byref(b), _ptr(img), _ptr(T_final), _ptr(n_last),
-                               _ptr(sel_idx), int(k), _ptr(maxc), _stream(stream)),
-           "ogs_blend_fwd")
+                               _ptr(n_eval), _ptr(sel_idx), int(k), _ptr(maxc),
+                               _stream(stream)), "ogs_blend_fwd")
+
+
+def blend_bwd(rec, pair_gauss, tile_range, width, height, bg, T_final, n_last, dimg, drec,
+              stream=None):
+    b = (C.c_float * 3)(*[float(x) for x in bg])
+    _check(lib().ogs_blend_bwd(_ptr(rec), _ptr(pair_gauss), _ptr(tile_range), int(width),
+                               int(height), C.byref(b), _ptr(T_final), _ptr(n_last), _ptr(dimg),
+                               _ptr(drec), _stream(stream)), "ogs_blend_bwd")
+
+
+def project_bwd(g, n_gauss, means_relative, cam, rect, drec, dmeans, dscales, dquats,
+                counts=None, stream=None):
+    c = cam if isinstance(cam, Camera) else camera(cam)
+    gs = g if isinstance(g, Gaussians) else gaussians_struct(g)
+    _check(lib().ogs_project_bwd(C.byref(gs), int(n_gauss), int(means_relative), C.byref(c),
+                                 _ptr(rect), _ptr(drec), _ptr(dmeans), _ptr(dscales),
+                                 _ptr(dquats), _ptr(counts), _stream(stream)), "ogs_project_bwd")
+
+
+def decode_bwd_scratch_bytes():
+    return int(lib().ogs_decode_bwd_scratch_bytes())
+
+
+def decode_bwd(pos, feat, offs, lv, N, mlp, cam, sel_idx, sel_w, counts, dmeans, dscales,
+               dquats, drec, dfeat, doffs, dlv, dmlp, scratch, stream=None):
+    c = cam if isinstance(cam, Camera) else camera(cam)
+    m = mlp if isinstance(mlp, MLP) else mlp_struct(mlp)
+    dm = dmlp if isinstance(dmlp, MLP) else mlp_struct(dmlp)
+    _check(lib().ogs_decode_bwd(_ptr(pos), _ptr(feat), _ptr(offs), _ptr(lv), int(N), C.byref(m),
+                                C.byref(c), _ptr(sel_idx), _ptr(sel_w), _ptr(counts),
+                                _ptr(dmeans), _ptr(dscales), _ptr(dquats), _ptr(drec),
+                                _ptr(dfeat), _ptr(doffs), _ptr(dlv), C.byref(dm), _ptr(scratch),
+                                scratch.numel(), _stream(stream)), "ogs_decode_bwd")
+
+
+def loss_l1(img, target, n, dimg, loss=None, stream=None):
+    _check(lib().ogs_loss_l1(_ptr(img), _ptr(target), int(n), _ptr(dimg), _ptr(loss),
+                             _stream(stream)), "ogs_loss_l1")
+
+
+def adam(param, grad, m, v, n, lr, beta1, beta2, eps, step, zero_grad=True, stream=None):
+    _check(lib().ogs_adam(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), int(n), float(lr),
+                          float(beta1), float(beta2), float(eps), int(step), int(bool(zero_grad)),
+                          _stream(stream)), "ogs_adam")
 
 
 def version():

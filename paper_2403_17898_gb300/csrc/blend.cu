@@ -16,7 +16,8 @@ __global__ void __launch_bounds__(kBlendThreads) blend_fwd_kernel(
     const float4* __restrict__ rec, const uint32_t* __restrict__ pair_gauss,
     const uint2* __restrict__ tile_range, int W, int H, int gx, float bg0, float bg1, float bg2,
     float* __restrict__ img, float* __restrict__ T_final, uint32_t* __restrict__ n_last,
-    const uint32_t* __restrict__ sel_idx, int k, uint32_t* __restrict__ maxc) {
+    uint32_t* __restrict__ n_eval, const uint32_t* __restrict__ sel_idx, int k,
+    uint32_t* __restrict__ maxc) {
     __shared__ float4 s_a[kBlendThreads];   // u, v, conic a, conic b
     __shared__ float4 s_b[kBlendThreads];   // conic c, opacity, r, g
     __shared__ float s_c[kBlendThreads];    // b
@@ -104,6 +105,7 @@ __global__ void __launch_bounds__(kBlendThreads) blend_fwd_kernel(
         img[2 * plane + pix] = C2 + T * bg2;
         T_final[pix] = T;
         n_last[pix] = last;
+        if (n_eval) n_eval[pix] = contributor;
     }
 }
 
@@ -115,8 +117,8 @@ using namespace ogs;
 extern "C" ogs_status ogs_blend_fwd(const ogs_rec2d* rec, const uint32_t* pair_gauss,
                                     const uint32_t* tile_range, int32_t width, int32_t height,
                                     const float* bg, float* img, float* T_final,
-                                    uint32_t* n_last, const uint32_t* sel_idx, int32_t k,
-                                    uint32_t* maxc, void* stream) {
+                                    uint32_t* n_last, uint32_t* n_eval, const uint32_t* sel_idx,
+                                    int32_t k, uint32_t* maxc, void* stream) {
     if (!rec || !pair_gauss || !tile_range || !bg || !img || !T_final || !n_last) return OGS_ERR_ARG;
     if (width <= 0 || height <= 0 || !aligned(rec, 16) || !aligned(tile_range, 8)) return OGS_ERR_ARG;
     if (maxc && (!sel_idx || k <= 0)) return OGS_ERR_ARG;
@@ -127,10 +129,10 @@ extern "C" ogs_status ogs_blend_fwd(const ogs_rec2d* rec, const uint32_t* pair_g
     if (maxc)
         blend_fwd_kernel<true><<<gx * gy, kBlendThreads, 0, st>>>(
             r, pair_gauss, tr, width, height, gx, bg[0], bg[1], bg[2], img, T_final, n_last,
-            sel_idx, k, maxc);
+            n_eval, sel_idx, k, maxc);
     else
         blend_fwd_kernel<false><<<gx * gy, kBlendThreads, 0, st>>>(
             r, pair_gauss, tr, width, height, gx, bg[0], bg[1], bg[2], img, T_final, n_last,
-            nullptr, 1, nullptr);
+            n_eval, nullptr, 1, nullptr);
     return launch_status();
 }

@@ -90,27 +90,54 @@ class Renderer:
         return self.sel_cap * self.k
 
     # -- one view --------------------------------------------------------------------------
-    def enqueue(self, cam, infer=True, bg=(0.0, 0.0, 0.0), maxc=None, stream=None):
-        """Enqueues the whole forward pass of one view (no host synchronisation)."""
+    def enqueue(self, cam, infer=True, bg=(0.0, 0.0, 0.0), maxc=None, stream=None, timers=None,
+                n_eval=None):
+        """Enqueues the whole forward pass of one view (no host synchronisation).  If
+        ``timers`` is a dict, a CUDA event pair is recorded around every stage under its name
+        (on the launching stream)."""
         assert int(cam.W) == self.W and int(cam.H) == self.H
         c = abi.camera(cam)
+        st = stream if stream is not None else torch.cuda.current_stream()
+
+        def stage(name, fn):
+            if timers is None:
+                fn()
+                return
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            fn()
+            e1.record(st)
+            timers.setdefault(name, []).append((e0, e1))
+
         self.counts_t.zero_()
-        abi.lod_select(self.pos, self.level, self.dL, self.N, self.NL, self.k, c, infer,
-                       self.sel_idx, self.sel_w, self.sel_cap, self.counts_t, self.sel_scratch,
-                       stream)
-        abi.decode(self.pos, self.feat, self.offs, self.lv, self.N, self._mlp_struct, c,
-                   self.sel_idx, self.sel_w, self.sel_cap, self.counts_t, self._g_struct, stream)
-        abi.project_bin(self._g_struct, self.g_cap, 1, c, self.rec, self.depth_key, self.rect,
-                        self.tiles, self.counts_t, stream)
-        abi.sort(self.depth_key, self.rect, self.tiles, self.g_cap, -1, self.gx, self.gy,
-                 self.pair_gauss, self.tile_range, self.pair_cap, self.counts_t,
-                 self.sort_scratch, stream)
-        abi.blend_fwd(self.rec, self.pair_gauss, self.tile_range, self.W, self.H, bg, self.img,
-                      self.T, self.n_last, self.sel_idx, self.k, maxc, stream)
+        stage("lod_select", lambda: abi.lod_select(
+            self.pos, self.level, self.dL, self.N, self.NL, self.k, c, infer, self.sel_idx,
+            self.sel_w, self.sel_cap, self.counts_t, self.sel_scratch, st))
+        stage("decode", lambda: abi.decode(
+            self.pos, self.feat, self.offs, self.lv, self.N, self._mlp_struct, c, self.sel_idx,
+            self.sel_w, self.sel_cap, self.counts_t, self._g_struct, st))
+        stage("project_bin", lambda: abi.project_bin(
+            self._g_struct, self.g_cap, 1, c, self.rec, self.depth_key, self.rect, self.tiles,
+            self.counts_t, st))
+        stage("sort", lambda: abi.sort(
+            self.depth_key, self.rect, self.tiles, self.g_cap, -1, self.gx, self.gy,
+            self.pair_gauss, self.tile_range, self.pair_cap, self.counts_t, self.sort_scratch,
+            st))
+        stage("blend_fwd", lambda: abi.blend_fwd(
+            self.rec, self.pair_gauss, self.tile_range, self.W, self.H, bg, self.img, self.T,
+            self.n_last, self.sel_idx, self.k, maxc, n_eval, st))
 
     def counts(self) -> FrameCounts:
         v = self.counts_t.cpu().numpy().view(np.uint32)
         return FrameCounts(*[int(x) for x in v])
+
+    def render_to_host(self, cam, host_img, infer=True, bg=(0.0, 0.0, 0.0)):
+        """The end-to-end call: render one view and copy the image into ``host_img`` (a pinned
+        float32 [3, H, W] CPU tensor); returns when the image is on the host."""
+        self.enqueue(cam, infer, bg)
+        host_img.copy_(self.img, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return host_img
 
     def render(self, cam, infer=True, bg=(0.0, 0.0, 0.0), maxc=None, check=True):
         """Renders one view; with ``check`` it synchronises, grows overflowing buffers and
@@ -130,3 +157,85 @@ class Renderer:
             if maxc is not None:
                 maxc.zero_()
         raise abi.OgsError("buffers kept overflowing")
+
+
+class Trainer(Renderer):
+    """One optimisation step over a batch of views: for each view the training-mode forward
+    (no next-level anchors), the L1 loss against its target, and the backward chain
+    blend_bwd -> project_bwd -> decode_bwd accumulating anchor and decoder gradients; then one
+    fused Adam update of features, offsets, scalings and decoder weights."""
+
+    PARAMS = ("feat", "offs", "lv")
+
+    def __init__(self, scene, mlp, W, H, lr=1e-3, betas=(0.9, 0.999), eps=1e-15, **kw):
+        super().__init__(scene, mlp, W, H, **kw)
+        self.lr, self.betas, self.eps = lr, betas, eps
+        self.step_count = 0
+        dev = "cuda"
+        self.grads = {n: torch.zeros_like(getattr(self, n)) for n in self.PARAMS}
+        self.dmlp = {n: torch.zeros_like(t) for n, t in self.mlp.items()}
+        self._dmlp_struct = abi.mlp_struct(self.dmlp, k=self.k)
+        self.adam_m = {n: torch.zeros_like(getattr(self, n)) for n in self.PARAMS}
+        self.adam_v = {n: torch.zeros_like(getattr(self, n)) for n in self.PARAMS}
+        for n, t in self.mlp.items():
+            self.adam_m["mlp." + n] = torch.zeros_like(t)
+            self.adam_v["mlp." + n] = torch.zeros_like(t)
+        self.dimg = torch.zeros(3, self.H, self.W, device=dev)
+        self.loss = torch.zeros(1, device=dev)
+        self.db_scratch = torch.empty(abi.decode_bwd_scratch_bytes(), dtype=torch.uint8,
+                                      device=dev)
+        self._alloc_grad()
+
+    def _alloc(self):
+        super()._alloc()
+        if hasattr(self, "grads"):
+            self._alloc_grad()
+
+    def _alloc_grad(self):
+        G = self.g_cap
+        dev = "cuda"
+        self.drec = torch.zeros(G, 9, device=dev)
+        self.dmeans = torch.empty(G, 3, device=dev)
+        self.dscales = torch.empty(G, 3, device=dev)
+        self.dquats = torch.empty(G, 4, device=dev)
+
+    def backward_view(self, cam, target, bg=(0.0, 0.0, 0.0), stream=None):
+        """Loss and backward of the view last enqueued (its forward must have run in
+        training mode with ``cam``); gradients accumulate."""
+        c = abi.camera(cam)
+        st = stream if stream is not None else torch.cuda.current_stream()
+        abi.loss_l1(self.img, target, self.img.numel(), self.dimg, self.loss, st)
+        self.drec.zero_()
+        abi.blend_bwd(self.rec, self.pair_gauss, self.tile_range, self.W, self.H, bg, self.T,
+                      self.n_last, self.dimg, self.drec, st)
+        abi.project_bwd(self._g_struct, self.g_cap, 1, c, self.rect, self.drec, self.dmeans,
+                        self.dscales, self.dquats, self.counts_t, st)
+        abi.decode_bwd(self.pos, self.feat, self.offs, self.lv, self.N, self._mlp_struct, c,
+                       self.sel_idx, self.sel_w, self.counts_t, self.dmeans, self.dscales,
+                       self.dquats, self.drec, self.grads["feat"], self.grads["offs"],
+                       self.grads["lv"], self._dmlp_struct, self.db_scratch, st)
+
+    def zero_grad(self):
+        for t in self.grads.values():
+            t.zero_()
+        for t in self.dmlp.values():
+            t.zero_()
+
+    def optimizer_step(self, stream=None):
+        self.step_count += 1
+        b1, b2 = self.betas
+        pairs = [(getattr(self, n), self.grads[n], n) for n in self.PARAMS]
+        pairs += [(self.mlp[n], self.dmlp[n], "mlp." + n) for n in self.mlp]
+        for p, g, n in pairs:
+            abi.adam(p, g, self.adam_m[n], self.adam_v[n], p.numel(), self.lr, b1, b2, self.eps,
+                     self.step_count, True, stream)
+
+    def train_step(self, cams, targets, bg=(0.0, 0.0, 0.0), update=True):
+        """Forward + backward over the views, then (optionally) the Adam update; returns
+        nothing (the summed mean-L1 of the views is left in ``self.loss``)."""
+        self.loss.zero_()
+        for cam, tgt in zip(cams, targets):
+            self.enqueue(cam, infer=False, bg=bg)
+            self.backward_view(cam, tgt, bg)
+        if update:
+            self.optimizer_step()

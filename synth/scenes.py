@@ -464,6 +464,7 @@ def random_sort_keys(seed, n, bits=32, dup_frac=0.2):
 # --------------------------------------------------------------------------------------
 
 def _cfg1():
+    """4,096 anchors, 3 levels, 10 m cube, one camera 12 m from the centre, 128x128."""
     sc = cube_scene(seed=0)
     d_max = 30.0
     cam = look_at_camera(np.array([3.0, -4.0, 10.5]) * (12.0 / np.linalg.norm([3.0, -4.0, 10.5])),
@@ -472,6 +473,50 @@ def _cfg1():
     return sc, mlp, [cam]
 
 
+def _city_cfg(N, NL, extent, c0, n_poses, h0, h1, W, H, seed=0, yaw_jitter=0.0, pose_seed=None):
+    sc = city_scene(seed=seed, N=N, NL=NL, extent=extent, c0=c0)
+    cams = zoom_out_path(n_poses, h0, h1, (0.0, 0.0, 0.0), W, H, yaw_jitter_deg=yaw_jitter,
+                         seed=pose_seed)
+    d_max, d_min = trajectory_d_max(sc, cams)
+    for c in cams:
+        c.d_max = float(np.float32(d_max))
+    sc.meta.update(d_max=d_max, d_min=d_min, NL_eqK=int(round(math.log2(d_max / d_min))) + 1)
+    mlp = decoder_mlp(seed=seed, dist_scale=1.0 / d_max)
+    return sc, mlp, cams
+
+
+def _cfg2():
+    """500k anchors, 6 levels, 600 m street grid, 30-pose zoom-out 8 m -> 250 m, 1600x900."""
+    return _city_cfg(500_000, 6, 600.0, 2.0, 30, 8.0, 250.0, 1600, 900)
+
+
+def _cfg3():
+    """2M anchors, 8 levels, 2 km city grid, 120-pose zoom-out 10 m -> 2 km, 1920x1080."""
+    return _city_cfg(2_000_000, 8, 2000.0, 4.0, 120, 10.0, 2000.0, 1920, 1080)
+
+
+def _cfg3_train_poses():
+    """Config-3 scene with 200 zoom-out poses with yaw jitter (proposal-net training views)."""
+    return _city_cfg(2_000_000, 8, 2000.0, 4.0, 200, 10.0, 2000.0, 1920, 1080,
+                     yaw_jitter=40.0, pose_seed=2)
+
+
+def _cfg3_heldout_poses():
+    """Config-3 scene with 60 held-out zoom-out poses (different yaw jitter seed)."""
+    return _city_cfg(2_000_000, 8, 2000.0, 4.0, 60, 10.0, 2000.0, 1920, 1080,
+                     yaw_jitter=40.0, pose_seed=3)
+
+
+def _cfg5():
+    """8M anchors, 10 levels, 4 km city grid, zoom-out 8 m -> 4 km (16 views per step), 1080p."""
+    return _city_cfg(8_000_000, 10, 4000.0, 6.0, 64, 8.0, 4000.0, 1920, 1080)
+
+
 CONFIGS = {
     "cube4k_128": _cfg1,
+    "street500k_1600x900": _cfg2,
+    "city2M_1080p": _cfg3,
+    "city2M_1080p_train200": _cfg3_train_poses,
+    "city2M_1080p_heldout60": _cfg3_heldout_poses,
+    "city8M_1080p": _cfg5,
 }

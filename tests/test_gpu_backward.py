@@ -1,0 +1,240 @@
+"""GPU parity of the training path: blend/project/decode backward, L1 loss and Adam against
+the FP64 oracle, the whole-chain gradient of a training view, and a finite-difference check
+through the GPU forward at the 500k-anchor street-grid scale."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_helpers import cuda, lib_ready, to_np_u32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def abi():
+    return lib_ready()
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    return t
+
+
+def _close_frac(got, ref, rel=1e-3, floor_frac=1e-3):
+    """Fraction of entries within rel of the reference, with an absolute floor of
+    floor_frac x the reference's RMS (gradients near zero)."""
+    got, ref = np.asarray(got, np.float64).ravel(), np.asarray(ref, np.float64).ravel()
+    floor = floor_frac * np.sqrt(np.mean(ref ** 2)) + 1e-30
+    return float(np.mean(np.abs(got - ref) <= rel * np.abs(ref) + floor))
+
+
+def test_blend_bwd_matches_oracle(abi, torch):
+    W, H, gx, gy = 72, 40, 5, 3
+    r = synth.random_records(3, 300, W, H, sigma=(0.8, 10.0), opac=(0.05, 0.95))
+    G = 300
+    order = np.argsort(r["depth"], kind="stable")
+    T = gx * gy
+    lst = np.tile(order, T).astype(np.int64)
+    start = np.arange(T + 1, dtype=np.int64) * G
+    uv = np.stack([r["u"], r["v"]], 1)
+    bg = (0.05, 0.1, 0.2)
+    dimg = np.random.default_rng(5).normal(size=(3, H, W)).astype(np.float32)
+    ref = oracle.blend_bwd(W, H, start, lst, uv, r["conic"], r["opac"], r["colors"], bg, dimg)
+    rec = np.zeros((G, 12), np.float32)
+    rec[:, 0], rec[:, 1] = r["u"], r["v"]
+    rec[:, 2:4] = r["conic"][:, 0:2]
+    rec[:, 4], rec[:, 5] = r["conic"][:, 2], r["opac"]
+    rec[:, 6:9] = r["colors"]
+    tr = cuda(np.stack([start[:-1], start[1:]], 1).astype(np.int32))
+    img = torch.zeros(3, H, W, device="cuda")
+    Tf = torch.zeros(H, W, device="cuda")
+    nl = torch.zeros(H, W, dtype=torch.int32, device="cuda")
+    rec_t, lst_t = cuda(rec), cuda(lst.astype(np.int32))
+    abi.blend_fwd(rec_t, lst_t, tr, W, H, bg, img, Tf, nl)
+    drec = torch.zeros(G, 9, device="cuda")
+    abi.blend_bwd(rec_t, lst_t, tr, W, H, bg, Tf, nl, cuda(dimg), drec)
+    torch.cuda.synchronize()
+    d = drec.cpu().numpy()
+    assert _close_frac(d[:, 0:2], ref["duv"]) > 0.99
+    assert _close_frac(d[:, 2:5], ref["dconic"]) > 0.99
+    assert _close_frac(d[:, 5], ref["dopac"]) > 0.99
+    assert _close_frac(d[:, 6:9], ref["dcolors"]) > 0.99
+    # aggregate agreement over everything
+    for a, b in ((d[:, 0:2], ref["duv"]), (d[:, 5], ref["dopac"]), (d[:, 6:9], ref["dcolors"])):
+        assert np.linalg.norm(a - b) <= 1e-3 * np.linalg.norm(b)
+
+
+def test_project_bwd_matches_oracle(abi, torch):
+    W, H = 160, 120
+    cam = synth.look_at_camera(np.array([1.0, -8.0, 3.0]), np.zeros(3), W, H, d_max=30.0)
+    g = synth.random_gaussians(7, 5000, cam, depth=(1.0, 30.0), scale=(0.02, 1.0))
+    ref_p = oracle.project(g["means"], g["scales"], g["quats"], g["opac"], cam)
+    G = 5000
+    gt = {k: cuda(v) for k, v in g.items()}
+    rec = torch.zeros(G, 12, device="cuda")
+    dk = torch.zeros(G, dtype=torch.int32, device="cuda")
+    rect = torch.zeros(G, 2, dtype=torch.int32, device="cuda")
+    tiles = torch.zeros(G, dtype=torch.int32, device="cuda")
+    abi.project_bin(gt, G, 0, cam, rec, dk, rect, tiles)
+    rng = np.random.default_rng(8)
+    drec = rng.normal(size=(G, 9)).astype(np.float32)
+    drec[:, 2:5] *= 20.0
+    dm = torch.zeros(G, 3, device="cuda")
+    ds = torch.zeros(G, 3, device="cuda")
+    dq = torch.zeros(G, 4, device="cuda")
+    abi.project_bwd(gt, G, 0, cam, rect, cuda(drec), dm, ds, dq)
+    torch.cuda.synchronize()
+    vis = (ref_p["rect"][:, 2] > ref_p["rect"][:, 0]) & (ref_p["mpx"] > 1e-3)
+    ref = oracle.project_bwd(g["means"], g["scales"], g["quats"], ref_p["rect"], cam,
+                             drec[:, 0:2], drec[:, 2:5])
+    for got, want in ((dm, ref["dmeans"]), (ds, ref["dscales"]), (dq, ref["dquats"])):
+        a = got.cpu().numpy()[vis]
+        b = want[vis]
+        assert _close_frac(a, b, rel=2e-3) > 0.995
+        assert np.linalg.norm(a - b) <= 2e-3 * np.linalg.norm(b)
+    culled = (ref_p["rect"][:, 2] <= ref_p["rect"][:, 0]) & (ref_p["mpx"] > 1e-3)
+    assert np.all(dm.cpu().numpy()[culled] == 0)
+
+
+def _mlp_tensors(mlp):
+    names = ("w1", "b1", "w2_op", "b2_op", "w2_col", "b2_col", "w2_cov", "b2_cov")
+    return {n: cuda(a) for n, a in zip(names, mlp.arrays())}, names
+
+
+def test_decode_bwd_matches_oracle(abi, torch):
+    sc, mlp, cams = synth.CONFIGS["cube4k_128"]()
+    cam = cams[0]
+    rng = np.random.default_rng(2)
+    M = 900
+    sel = np.sort(rng.choice(sc.N, size=M, replace=False)).astype(np.int64)
+    w = rng.uniform(0.05, 1.0, size=M).astype(np.float32)
+    G = M * 10
+    grads = dict(dmeans=rng.normal(size=(G, 3)), dscales=rng.normal(size=(G, 3)),
+                 dquats=rng.normal(size=(G, 4)), dopac=rng.normal(size=G),
+                 dcolors=rng.normal(size=(G, 3)))
+    grads = {k: v.astype(np.float32) for k, v in grads.items()}
+    ref = oracle.decode_bwd(sel, w, sc, mlp, cam, grads)
+    counts = np.zeros(8, np.uint32)
+    counts[0], counts[1] = M, G
+    drec = np.zeros((G, 9), np.float32)
+    drec[:, 5] = grads["dopac"]
+    drec[:, 6:9] = grads["dcolors"]
+    mt, names = _mlp_tensors(mlp)
+    dmlp = {n: torch.zeros_like(t) for n, t in mt.items()}
+    dfeat = torch.zeros(sc.N, 32, device="cuda")
+    doffs = torch.zeros(sc.N, 10, 3, device="cuda")
+    dlv = torch.zeros(sc.N, 3, device="cuda")
+    scr = torch.empty(abi.decode_bwd_scratch_bytes(), dtype=torch.uint8, device="cuda")
+    abi.decode_bwd(cuda(sc.pos), cuda(sc.feat), cuda(sc.offs), cuda(sc.lv), sc.N, mt, cam,
+                   cuda(sel.astype(np.int32)), cuda(w), cuda(counts.view(np.int32)),
+                   cuda(grads["dmeans"]), cuda(grads["dscales"]), cuda(grads["dquats"]),
+                   cuda(drec), dfeat, doffs, dlv, dmlp, scr)
+    torch.cuda.synchronize()
+    # opacity-sign knife edges would drop a Gaussian's opacity gradient on one side only
+    dec = oracle.decode(sel, w, sc, mlp, cam)
+    assert dec["op_margin"].min() > 1e-5
+    for name, got in (("dfeat", dfeat), ("doffs", doffs), ("dlv", dlv)):
+        a, b = got.cpu().numpy(), ref[name]
+        assert np.linalg.norm(a - b) <= 1e-4 * np.linalg.norm(b), name
+    for n in names:
+        a, b = dmlp[n].cpu().numpy(), ref["d" + n]
+        assert np.linalg.norm(a - b) <= 1e-4 * np.linalg.norm(b), n
+    # a second call accumulates
+    abi.decode_bwd(cuda(sc.pos), cuda(sc.feat), cuda(sc.offs), cuda(sc.lv), sc.N, mt, cam,
+                   cuda(sel.astype(np.int32)), cuda(w), cuda(counts.view(np.int32)),
+                   cuda(grads["dmeans"]), cuda(grads["dscales"]), cuda(grads["dquats"]),
+                   cuda(drec), dfeat, doffs, dlv, dmlp, scr)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(dmlp["w1"].cpu().numpy(), 2 * ref["dw1"], rtol=1e-3, atol=1e-6)
+
+
+def test_loss_and_adam_match_oracle(abi, torch):
+    rng = np.random.default_rng(3)
+    img = rng.uniform(size=(3, 40, 50)).astype(np.float32)
+    tgt = rng.uniform(size=(3, 40, 50)).astype(np.float32)
+    dimg = torch.zeros(3, 40, 50, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    abi.loss_l1(cuda(img), cuda(tgt), img.size, dimg, loss)
+    torch.cuda.synchronize()
+    L, g = oracle.l1_loss(img, tgt)
+    assert abs(loss.item() - L) <= 1e-6
+    np.testing.assert_allclose(dimg.cpu().numpy(), g, rtol=1e-6)
+    p = rng.normal(size=1000).astype(np.float32)
+    m = np.zeros(1000, np.float32)
+    v = np.zeros(1000, np.float32)
+    pt, mt_, vt = cuda(p), cuda(m), cuda(v)
+    po, mo, vo = p.astype(np.float64), m.astype(np.float64), v.astype(np.float64)
+    for step in range(1, 6):
+        gr = rng.normal(size=1000).astype(np.float32)
+        gt = cuda(gr)
+        abi.adam(pt, gt, mt_, vt, 1000, 1e-2, 0.9, 0.999, 1e-8, step, True)
+        po, mo, vo = oracle.adam(po, gr, mo, vo, 1e-2, 0.9, 0.999, 1e-8, step)
+        torch.cuda.synchronize()
+        assert np.all(gt.cpu().numpy() == 0)
+    np.testing.assert_allclose(pt.cpu().numpy(), po, rtol=1e-5, atol=1e-6)
+
+
+def test_training_view_gradient_matches_oracle(abi, torch):
+    """Whole chain for one training view of the 4k-anchor cube (L1 against a seeded target)."""
+    from paper_2403_17898_gb300.render import Trainer
+    sc, mlp, cams = synth.CONFIGS["cube4k_128"]()
+    cam = cams[0]
+    target = np.random.default_rng(1).uniform(size=(3, 128, 128)).astype(np.float32)
+    tr = Trainer(sc, mlp, 128, 128)
+    c = tr.render(cam, infer=False)
+    assert c.overflow == 0
+    tr.zero_grad()
+    tr.backward_view(cam, cuda(target))
+    torch.cuda.synchronize()
+    fr = oracle.render(sc, mlp, cam, infer=False)
+    L, dimg = oracle.l1_loss(fr.out["img"], target)
+    assert abs(tr.loss.item() - L) <= 1e-5
+    ref = oracle.render_grad(sc, mlp, cam, fr, dimg)
+    pairs = [("dfeat", tr.grads["feat"]), ("doffs", tr.grads["offs"]), ("dlv", tr.grads["lv"])]
+    pairs += [("d" + n, tr.dmlp[n]) for n in tr.mlp]
+    for name, got in pairs:
+        a, b = got.cpu().numpy(), ref[name]
+        err = np.linalg.norm(a - b) / np.linalg.norm(b)
+        assert err <= 5e-3, (name, err)
+    # per-anchor feature gradients agree almost everywhere
+    assert _close_frac(tr.grads["feat"].cpu().numpy(), ref["dfeat"], rel=1e-2) > 0.98
+
+
+def test_finite_difference_through_gpu_street_scale(abi, torch):
+    """FD check of decoder-weight gradients through the FP32 GPU forward at the 500k-anchor,
+    1600x900 street-grid scale (central differences, relative step 1e-2 of the weight)."""
+    from paper_2403_17898_gb300.render import Trainer
+    sc, mlp, cams = synth.CONFIGS["street500k_1600x900"]()
+    cam = cams[10]
+    target = cuda(np.random.default_rng(1).uniform(size=(3, cam.H, cam.W)).astype(np.float32))
+    tr = Trainer(sc, mlp, cam.W, cam.H, sel_cap=200_000, pair_cap=4_000_000)
+    c = tr.render(cam, infer=False)
+    assert c.overflow == 0 and c.n_selected > 1000
+    tr.zero_grad()
+    tr.loss.zero_()
+    tr.backward_view(cam, target)
+    torch.cuda.synchronize()
+
+    def loss_at():
+        tr.enqueue(cam, infer=False)
+        tr.loss.zero_()
+        abi.loss_l1(tr.img, target, tr.img.numel(), tr.dimg, tr.loss)
+        torch.cuda.synchronize()
+        return float(tr.loss.item())
+
+    checks = [("b2_op", (3,)), ("b2_col", (4,)), ("b2_col", (17,)), ("b1", (0, 5)),
+              ("b2_cov", (2,)), ("w2_col", (5, 7))]
+    for name, ix in checks:
+        p = tr.mlp[name]
+        g = float(tr.dmlp[name][ix].item())
+        x0 = float(p[ix].item())
+        h = 1e-2 * max(abs(x0), 0.1)
+        p[ix] = x0 + h
+        lp = loss_at()
+        p[ix] = x0 - h
+        lm = loss_at()
+        p[ix] = x0
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g) <= 0.05 * abs(g) + 2e-7, (name, ix, g, fd)
