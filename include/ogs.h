@@ -284,6 +284,28 @@ ogs_status ogs_adam(float* param, float* grad, float* m, float* v, int64_t n, fl
                     float beta1, float beta2, float eps, int32_t step, int32_t zero_grad,
                     void* stream);
 
+/* ---------------------------------------------------------------------------------------
+ * ogs_radix_sort_pairs_noalloc — the same stable LSD radix sort as ogs_radix_sort_pairs, for
+ * callers that cannot allocate device memory (an embedding host application that owns the
+ * device heap and offers no allocator, or a real-time frame loop that must not call
+ * cudaMalloc/cudaFree because they synchronise the device).  The paper has no counterpart:
+ * this is a deployment variant of the sort.
+ *   Scratch is a fixed array inside the library image (about 8.3 MB), reserved on every GPU
+ *   that loads the library until the process exits; no allocation of any kind is made.
+ *   n_cap must be <= ogs_radix_sort_pairs_noalloc_max_items() (2^20); larger requests return
+ *   OGS_ERR_CAPACITY and enqueue nothing.
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ *   which may load the module): make that first call before any stream capture.
+ *   All calls share the one array, so calls that overlap on the GPU (different streams
+ *   without ordering, or different host threads) race; serialise them.  The array keeps the
+ *   last call's contents; every word is written before it is read, so nothing is cleared.
+ *   Other arguments and the result are as for ogs_radix_sort_pairs.
+ * ------------------------------------------------------------------------------------- */
+int64_t ogs_radix_sort_pairs_noalloc_max_items(void);
+ogs_status ogs_radix_sort_pairs_noalloc(uint32_t* keys, uint32_t* vals, const uint32_t* n_dev,
+                                        int64_t n_cap, int32_t bit_lo, int32_t bit_hi,
+                                        void* stream);
+
 /* Library version string (host). */
 const char* ogs_version(void);
 

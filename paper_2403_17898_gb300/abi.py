@@ -77,6 +77,8 @@ _SIGS = {
     "ogs_loss_l1": (C.c_int, [_P, _P, _I64, _P, _P, _P]),
     "ogs_adam": (C.c_int, [_P, _P, _P, _P, _I64, C.c_float, C.c_float, C.c_float, C.c_float,
                            _I32, _I32, _P]),
+    "ogs_radix_sort_pairs_noalloc_max_items": (_I64, []),
+    "ogs_radix_sort_pairs_noalloc": (C.c_int, [_P, _P, _P, _I64, _I32, _I32, _P]),
     "ogs_version": (C.c_char_p, []),
 }
 
@@ -262,6 +264,18 @@ def adam(param, grad, m, v, n, lr, beta1, beta2, eps, step, zero_grad=True, stre
     _check(lib().ogs_adam(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), int(n), float(lr),
                           float(beta1), float(beta2), float(eps), int(step), int(bool(zero_grad)),
                           _stream(stream)), "ogs_adam")
+
+
+def radix_sort_pairs_noalloc_max_items():
+    return int(lib().ogs_radix_sort_pairs_noalloc_max_items())
+
+
+def radix_sort_pairs_noalloc(keys, vals, n_dev, n_cap, bit_lo, bit_hi, stream=None):
+    """Allocation-free sort: for callers that cannot give the library any scratch memory (see
+    ogs_radix_sort_pairs_noalloc in include/ogs.h); calls overlapping on the GPU race."""
+    _check(lib().ogs_radix_sort_pairs_noalloc(_ptr(keys), _ptr(vals), _ptr(n_dev), int(n_cap),
+                                              int(bit_lo), int(bit_hi), _stream(stream)),
+           "ogs_radix_sort_pairs_noalloc")
 
 
 def version():

@@ -15,6 +15,8 @@
 // The radix sort is a classic three-kernel LSD pass (per-block digit histograms -> per-digit
 // scan over blocks -> stable block-local multisplit and coalesced scatter) with 8-bit digits;
 // every item count is read on the device, so no host synchronisation is needed.
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace ogs {
@@ -494,4 +496,68 @@ extern "C" ogs_status ogs_sort(const uint32_t* depth_key, const uint32_t* rect, 
     tile_ranges<<<stride_grid(pair_cap, 256, 8), 256, 0, st>>>(s.pkey, counts,
                                                                 reinterpret_cast<uint2*>(tile_range));
     return launch_status();
+}
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free variant of ogs_radix_sort_pairs.
+//
+// Some callers cannot hand this library a scratch buffer: a renderer embedded as a plugin in
+// a host application that owns the whole device heap and offers no allocator, or a real-time
+// frame loop that must never call cudaMalloc/cudaFree because they synchronise the device
+// and stall the frame.  For them the sort's scratch lives in a fixed device array that is
+// part of the library image: it is reserved on every GPU that loads the library and stays
+// reserved until the process exits.
+// ---------------------------------------------------------------------------------------
+
+namespace ogs {
+namespace {
+
+constexpr int64_t kNoAllocMaxItems = (int64_t)1 << 20;   // largest n_cap accepted
+constexpr int64_t kNoAllocBlocks = (kNoAllocMaxItems + kRsTile - 1) / kRsTile;
+// alt keys + alt values + per-block digit histograms + digit totals, each 256-byte aligned
+constexpr size_t kNoAllocBytes =
+    2 * (size_t)kNoAllocMaxItems * sizeof(uint32_t) + 256 +
+    (size_t)kNoAllocBlocks * kRsBins * sizeof(uint32_t) + 256 + kRsBins * sizeof(uint32_t) + 512;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Device address of g_noalloc_scratch per device (host code only ever sees the symbol's
+// host-side stand-in, never usable as a pointer).  Filled once per device.
+constexpr int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+ogs_status noalloc_scratch(void** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return OGS_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return OGS_ERR_CUDA;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return OGS_OK;
+}
+
+}  // namespace
+}  // namespace ogs
+
+extern "C" int64_t ogs_radix_sort_pairs_noalloc_max_items(void) { return kNoAllocMaxItems; }
+
+extern "C" ogs_status ogs_radix_sort_pairs_noalloc(uint32_t* keys, uint32_t* vals,
+                                                   const uint32_t* n_dev, int64_t n_cap,
+                                                   int32_t bit_lo, int32_t bit_hi, void* stream) {
+    if (!keys || !vals || n_cap < 0) return OGS_ERR_ARG;
+    if (bit_lo < 0 || bit_hi > 32 || bit_lo >= bit_hi) return OGS_ERR_ARG;
+    if (n_cap > kNoAllocMaxItems) return OGS_ERR_CAPACITY;
+    if (n_cap == 0) return OGS_OK;
+    void* base = nullptr;
+    ogs_status st = noalloc_scratch(&base);
+    if (st != OGS_OK) return st;
+    // every scratch word is written before it is read in each pass: nothing to clear
+    RsScratch s;
+    rs_layout(n_cap, base, &s);
+    return radix_sort(keys, vals, n_dev, n_cap, bit_lo, bit_hi, s, (cudaStream_t)stream)
+               ? OGS_OK : OGS_ERR_CUDA;
 }
