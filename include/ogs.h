@@ -152,6 +152,20 @@ ogs_status ogs_decode(const float* pos, const float* feat, const float* offs, co
                       const ogs_gaussians* out /* host struct of device ptrs */, void* stream);
 
 /* ---------------------------------------------------------------------------------------
+ * ogs_decode_bf16 — ogs_decode on the tensor cores: both decoder layers as BF16 x BF16 MMAs
+ * with FP32 accumulation (tcgen05, accumulators in tensor memory); inputs and hidden
+ * activations are rounded to BF16, everything after the GEMMs (biases, activations,
+ * normalisation, positions) is FP32.  Same arguments, layout and outputs as ogs_decode.
+ * counts is written only if a bounded internal wait expires (counts->timeout = 1, outputs
+ * of the remaining anchors not written).
+ * ------------------------------------------------------------------------------------- */
+ogs_status ogs_decode_bf16(const float* pos, const float* feat, const float* offs,
+                           const float* lv, int64_t N, const ogs_mlp* mlp /* host struct */,
+                           const ogs_camera* cam /* host */, const uint32_t* sel_idx,
+                           const float* sel_w, int64_t sel_cap, ogs_counts* counts,
+                           const ogs_gaussians* out /* host struct */, void* stream);
+
+/* ---------------------------------------------------------------------------------------
  * ogs_project_bin — Sec. 3.1: Sigma = R(q) S S^T R(q)^T (Eq. 1), EWA projection
  * Sigma' = J W Sigma W^T J^T + 0.3 I (J with x/z, y/z clamped to 1.3x the half-fov),
  * conic = Sigma'^-1, radius r = 3 sqrt(lambda_max), lambda_max = mid + sqrt(max(0.1,
@@ -305,6 +319,47 @@ int64_t ogs_radix_sort_pairs_noalloc_max_items(void);
 ogs_status ogs_radix_sort_pairs_noalloc(uint32_t* keys, uint32_t* vals, const uint32_t* n_dev,
                                         int64_t n_cap, int32_t bit_lo, int32_t bit_hi,
                                         void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Learned anchor-visibility proposal (not in the paper: a gate in front of decoding).  A
+ * 3-layer MLP, input x = [f_v (32), L/(NL-1), unit direction camera->anchor (3), ln(d/d_max)]
+ * (37), hidden 64 ReLU, 64 ReLU, output keep probability p = sigmoid(w3 . h2 + b3).
+ *   w1 f32[64][37], b1 f32[64], w2 f32[64][64], b2 f32[64], w3 f32[64], b3 f32[1]
+ * ------------------------------------------------------------------------------------- */
+typedef struct ogs_proposal {
+    const float* w1;
+    const float* b1;
+    const float* w2;
+    const float* b2;
+    const float* w3;
+    const float* b3;
+} ogs_proposal;
+
+/* ogs_proposal_gate — scores the counts->n_selected entries of (sel_in, w_in) and writes the
+ * ones with p >= p_star to (sel_out, w_out) in their original order; counts->n_selected and
+ * n_gaussians are updated to the kept count.  p_out (optional) receives p for every input
+ * entry.  sel_out must not alias sel_in.
+ *   scratch: ogs_proposal_gate_scratch_bytes(sel_cap) bytes, 16-byte aligned. */
+size_t ogs_proposal_gate_scratch_bytes(int64_t sel_cap);
+ogs_status ogs_proposal_gate(const float* pos, const uint8_t* level, const float* feat,
+                             int64_t N, int32_t NL, int32_t k, const ogs_camera* cam /* host */,
+                             const ogs_proposal* net /* host struct */, float p_star,
+                             const uint32_t* sel_in, const float* w_in, int64_t sel_cap,
+                             ogs_counts* counts, uint32_t* sel_out, float* w_out, float* p_out,
+                             void* scratch, size_t scratch_bytes, void* stream);
+
+/* ogs_proposal_train — mean binary cross-entropy of the keep probability over the selected
+ * anchors of one view against labels y = (maxc[anchor] >= tau) (maxc as written by
+ * ogs_blend_fwd: float bits of the largest T*alpha), and its gradients.
+ *   grads: same layout as the network, ACCUMULATED (+=); *loss += mean BCE (may be NULL).
+ *   scratch: ogs_proposal_train_scratch_bytes() bytes, 16-byte aligned. */
+size_t ogs_proposal_train_scratch_bytes(void);
+ogs_status ogs_proposal_train(const float* pos, const uint8_t* level, const float* feat,
+                              int64_t N, int32_t NL, const ogs_camera* cam /* host */,
+                              const ogs_proposal* net /* host struct */, const uint32_t* sel_idx,
+                              const ogs_counts* counts, const uint32_t* maxc, float tau,
+                              const ogs_proposal* grads /* host struct, written */, float* loss,
+                              void* scratch, size_t scratch_bytes, void* stream);
 
 /* Library version string (host). */
 const char* ogs_version(void);

@@ -307,3 +307,51 @@ def adam(param, grad, m, v, lr, beta1, beta2, eps, step):
     mh = m / (1 - beta1 ** step)
     vh = v / (1 - beta2 ** step)
     return param - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+# ----------------------------------------------------------------------------------------
+# anchor-visibility proposal network (learned gate in front of decoding)
+# ----------------------------------------------------------------------------------------
+
+def proposal_inputs(pos, level, feat, NL, sel_idx, cam):
+    """Per selected anchor: [f_v, L/(NL-1), unit direction camera->anchor, ln(d/d_max)]."""
+    c = cam_array(cam)
+    campos, d_max = c[9:12], c[19]
+    p = _d(pos)[sel_idx] - campos
+    d = np.linalg.norm(p, axis=1, keepdims=True)
+    lev = np.asarray(level, np.float64)[sel_idx][:, None] / max(NL - 1, 1)
+    return np.concatenate([_d(feat)[sel_idx], lev, p / d, np.log(d / d_max)], 1)
+
+
+def proposal_forward(net, X):
+    """3-layer MLP (ReLU, ReLU, sigmoid): keep probability per row of X, plus the hidden
+    pre-activations.  Pinned by closed forms and finite differences (tests/test_oracle_proposal)."""
+    w1, b1, w2, b2, w3, b3 = [_d(a) for a in net.arrays()]
+    a1 = X @ w1.T + b1
+    h1 = np.maximum(a1, 0)
+    a2 = h1 @ w2.T + b2
+    h2 = np.maximum(a2, 0)
+    z = (h2 @ w3.T + b3)[:, 0]
+    p = 1.0 / (1.0 + np.exp(-z))
+    return p, dict(a1=a1, h1=h1, a2=a2, h2=h2, z=z)
+
+
+def proposal_bce_grad(net, X, y):
+    """Mean binary cross-entropy of the keep probability against labels y in {0, 1}, and its
+    gradients w.r.t. every weight (analytic backward; dL/dz = (p - y) / n)."""
+    w1, b1, w2, b2, w3, b3 = [_d(a) for a in net.arrays()]
+    p, t = proposal_forward(net, X)
+    y = np.asarray(y, np.float64)
+    n = len(y)
+    eps = 1e-300
+    loss = float(-np.mean(y * np.log(np.maximum(p, eps)) + (1 - y) * np.log(np.maximum(1 - p, eps))))
+    dz = (p - y) / n
+    dw3 = dz[None, :] @ t["h2"]
+    db3 = np.array([dz.sum()])
+    dh2 = dz[:, None] * w3[0][None, :] * (t["a2"] > 0)
+    dw2 = dh2.T @ t["h1"]
+    db2 = dh2.sum(0)
+    dh1 = (dh2 @ w2) * (t["a1"] > 0)
+    dw1 = dh1.T @ X
+    db1 = dh1.sum(0)
+    return loss, dict(w1=dw1, b1=db1, w2=dw2, b2=db2, w3=dw3, b3=db3)

@@ -44,6 +44,10 @@ class MLP(C.Structure):
                [("F", C.c_int32), ("H", C.c_int32), ("k", C.c_int32), ("pad", C.c_int32)]
 
 
+class Proposal(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("w1", "b1", "w2", "b2", "w3", "b3")]
+
+
 class Gaussians(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("means", "scales", "quats", "opac", "colors")]
 
@@ -59,6 +63,8 @@ _SIGS = {
                                  _I64, _P, _P, _SZ, _P]),
     "ogs_decode": (C.c_int, [_P, _P, _P, _P, _I64, C.POINTER(MLP), C.POINTER(Camera), _P, _P,
                              _I64, _P, C.POINTER(Gaussians), _P]),
+    "ogs_decode_bf16": (C.c_int, [_P, _P, _P, _P, _I64, C.POINTER(MLP), C.POINTER(Camera), _P,
+                                  _P, _I64, _P, C.POINTER(Gaussians), _P]),
     "ogs_project_bin": (C.c_int, [C.POINTER(Gaussians), _I64, _I32, C.POINTER(Camera), _P, _P,
                                   _P, _P, _P, _P]),
     "ogs_sort_scratch_bytes": (_SZ, [_I64, _I64, _I32]),
@@ -79,6 +85,14 @@ _SIGS = {
                            _I32, _I32, _P]),
     "ogs_radix_sort_pairs_noalloc_max_items": (_I64, []),
     "ogs_radix_sort_pairs_noalloc": (C.c_int, [_P, _P, _P, _I64, _I32, _I32, _P]),
+    "ogs_proposal_gate_scratch_bytes": (_SZ, [_I64]),
+    "ogs_proposal_gate": (C.c_int, [_P, _P, _P, _I64, _I32, _I32, C.POINTER(Camera),
+                                    C.POINTER(Proposal), C.c_float, _P, _P, _I64, _P, _P, _P,
+                                    _P, _P, _SZ, _P]),
+    "ogs_proposal_train_scratch_bytes": (_SZ, []),
+    "ogs_proposal_train": (C.c_int, [_P, _P, _P, _I64, _I32, C.POINTER(Camera),
+                                     C.POINTER(Proposal), _P, _P, _P, C.c_float,
+                                     C.POINTER(Proposal), _P, _P, _SZ, _P]),
     "ogs_version": (C.c_char_p, []),
 }
 
@@ -182,6 +196,17 @@ def decode(pos, feat, offs, lv, N, mlp, cam, sel_idx, sel_w, sel_cap, counts, ou
                             C.byref(g), _stream(stream)), "ogs_decode")
 
 
+def decode_bf16(pos, feat, offs, lv, N, mlp, cam, sel_idx, sel_w, sel_cap, counts, out,
+                stream=None):
+    c = cam if isinstance(cam, Camera) else camera(cam)
+    m = mlp if isinstance(mlp, MLP) else mlp_struct(mlp)
+    g = out if isinstance(out, Gaussians) else gaussians_struct(out)
+    _check(lib().ogs_decode_bf16(_ptr(pos), _ptr(feat), _ptr(offs), _ptr(lv), int(N),
+                                 C.byref(m), C.byref(c), _ptr(sel_idx), _ptr(sel_w),
+                                 int(sel_cap), _ptr(counts), C.byref(g), _stream(stream)),
+           "ogs_decode_bf16")
+
+
 def project_bin(g, n_gauss, means_relative, cam, rec, depth_key, rect, tiles, counts=None,
                 stream=None):
     c = cam if isinstance(cam, Camera) else camera(cam)
@@ -276,6 +301,45 @@ def radix_sort_pairs_noalloc(keys, vals, n_dev, n_cap, bit_lo, bit_hi, stream=No
     _check(lib().ogs_radix_sort_pairs_noalloc(_ptr(keys), _ptr(vals), _ptr(n_dev), int(n_cap),
                                               int(bit_lo), int(bit_hi), _stream(stream)),
            "ogs_radix_sort_pairs_noalloc")
+
+
+def proposal_struct(t) -> Proposal:
+    """Proposal-network weights (dict of CUDA float32 tensors w1 b1 w2 b2 w3 b3)."""
+    p = Proposal()
+    for n in ("w1", "b1", "w2", "b2", "w3", "b3"):
+        setattr(p, n, t[n].data_ptr())
+    return p
+
+
+def proposal_gate_scratch_bytes(sel_cap):
+    return int(lib().ogs_proposal_gate_scratch_bytes(int(sel_cap)))
+
+
+def proposal_gate(pos, level, feat, N, NL, k, cam, net, p_star, sel_in, w_in, sel_cap, counts,
+                  sel_out, w_out, p_out, scratch, stream=None):
+    c = cam if isinstance(cam, Camera) else camera(cam)
+    n = net if isinstance(net, Proposal) else proposal_struct(net)
+    _check(lib().ogs_proposal_gate(_ptr(pos), _ptr(level), _ptr(feat), int(N), int(NL), int(k),
+                                   C.byref(c), C.byref(n), float(p_star), _ptr(sel_in),
+                                   _ptr(w_in), int(sel_cap), _ptr(counts), _ptr(sel_out),
+                                   _ptr(w_out), _ptr(p_out), _ptr(scratch), scratch.numel(),
+                                   _stream(stream)), "ogs_proposal_gate")
+
+
+def proposal_train_scratch_bytes():
+    return int(lib().ogs_proposal_train_scratch_bytes())
+
+
+def proposal_train(pos, level, feat, N, NL, cam, net, sel_idx, counts, maxc, tau, grads, loss,
+                   scratch, stream=None):
+    c = cam if isinstance(cam, Camera) else camera(cam)
+    n = net if isinstance(net, Proposal) else proposal_struct(net)
+    g = grads if isinstance(grads, Proposal) else proposal_struct(grads)
+    _check(lib().ogs_proposal_train(_ptr(pos), _ptr(level), _ptr(feat), int(N), int(NL),
+                                    C.byref(c), C.byref(n), _ptr(sel_idx), _ptr(counts),
+                                    _ptr(maxc), float(tau), C.byref(g), _ptr(loss),
+                                    _ptr(scratch), scratch.numel(), _stream(stream)),
+           "ogs_proposal_train")
 
 
 def version():

@@ -1,0 +1,253 @@
+// Neural-Gaussian decoding (Sec. 3.2, Eq. offsets and Eq. mlp) on the 5th-generation tensor
+// cores: both decoder layers as BF16 x BF16 -> FP32 tcgen05 MMAs, 128 anchors per tile.
+//
+//   layer 1:  D1[128 x 96]  = Z[128 x 48] . W1^T       (3 decoders stacked along N;
+//                                                        K = 36 inputs padded to 48)
+//   layer 2:  D2[128 x 112] = H[128 x 96] . W2blk^T    (block-diagonal: each decoder's
+//                                                        outputs only see its own hidden)
+// Operands live in shared memory in the no-swizzle K-major core-matrix layout (8 rows x 16
+// bytes per core matrix); accumulators live in tensor memory (columns 0..95 and 128..239 of
+// a 256-column allocation).  One thread issues the MMAs and commits them to an mbarrier; the
+// four warps read their 32 accumulator rows each (one anchor per thread) for the bias/ReLU
+// epilogue of layer 1 and the activation epilogue of layer 2 (FP32).  Every mbarrier wait is
+// bounded; on expiry the kernel flags ogs_counts.timeout, releases its tensor memory and exits.
+#include "internal.cuh"
+#include "tc.cuh"
+
+namespace ogs {
+namespace {
+
+constexpr int kTcThreads = 128;     // 4 warps, one anchor (TMEM lane) per thread
+constexpr int kTM = 128;            // anchors per tile (MMA M)
+constexpr int kF = 32;
+constexpr int kH = 32;
+constexpr int kDin = kF + 4;        // 36
+constexpr int kK1 = 48;             // padded layer-1 K
+constexpr int kN1 = 3 * kH;         // 96 hidden (layer-1 N, layer-2 K)
+constexpr int kK = 10;              // Gaussians per anchor
+constexpr int kN2 = 112;            // 110 outputs padded to a multiple of 16
+constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kD2Col = 128;
+constexpr uint32_t kWaitLimit = 1u << 24;
+
+// shared-memory carve (bytes)
+constexpr int kOffA1 = 0;                               // 128 x 48 bf16
+constexpr int kOffB1 = kOffA1 + kTM * kK1 * 2;          // 96 x 48 bf16
+constexpr int kOffA2 = kOffB1 + kN1 * kK1 * 2;          // 128 x 96 bf16
+constexpr int kOffB2 = kOffA2 + kTM * kN1 * 2;          // 112 x 96 bf16
+constexpr int kOffBias = kOffB2 + kN2 * kN1 * 2;        // 96 + 112 f32
+constexpr int kSmemUsed = kOffBias + (kN1 + kN2) * 4;
+// request enough shared memory that at most two CTAs share an SM: 2 x 256 TMEM columns fit
+constexpr int kSmemRequest = 100 * 1024;
+static_assert(kSmemUsed <= kSmemRequest, "shared memory carve");
+
+struct TcArgs {
+    const float* pos;
+    const float* feat;
+    const float* offs;
+    const float* lv;
+    const uint32_t* sel_idx;
+    const float* sel_w;
+    ogs_counts* counts;
+    ogs_mlp mlp;
+    ogs_gaussians out;
+    Cam cam;
+};
+
+__device__ __forceinline__ float sigm(float x) { return 1.0f / (1.0f + __expf(-x)); }
+
+__device__ __forceinline__ void put_bf16(unsigned char* base, int row, int k, int Kpad, float v) {
+    *reinterpret_cast<__nv_bfloat16*>(base + tc::core_offset(row, k, Kpad)) = __float2bfloat16_rn(v);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) decode_bf16_tc(TcArgs a) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    unsigned char* sA1 = sm + kOffA1;
+    unsigned char* sB1 = sm + kOffB1;
+    unsigned char* sA2 = sm + kOffA2;
+    unsigned char* sB2 = sm + kOffB2;
+    float* sb1 = reinterpret_cast<float*>(sm + kOffBias);
+    float* sb2 = sb1 + kN1;
+    const int t = threadIdx.x, w = t >> 5;
+
+    // weights -> bf16 operand tiles (zero padding included), biases -> f32
+    for (int e = t; e < kN1 * kK1; e += kTcThreads) {
+        const int n = e / kK1, k = e % kK1;
+        put_bf16(sB1, n, k, kK1, k < kDin ? a.mlp.w1[n * kDin + k] : 0.f);
+    }
+    for (int e = t; e < kN2 * kN1; e += kTcThreads) {
+        const int n = e / kN1, k = e % kN1;
+        float v = 0.f;
+        if (n < kK) { if (k < kH) v = a.mlp.w2_op[n * kH + k]; }
+        else if (n < 4 * kK) { if (k >= kH && k < 2 * kH) v = a.mlp.w2_col[(n - kK) * kH + (k - kH)]; }
+        else if (n < 11 * kK) { if (k >= 2 * kH) v = a.mlp.w2_cov[(n - 4 * kK) * kH + (k - 2 * kH)]; }
+        put_bf16(sB2, n, k, kN1, v);
+    }
+    for (int e = t; e < kN1; e += kTcThreads) sb1[e] = a.mlp.b1[e];
+    for (int e = t; e < kN2; e += kTcThreads)
+        sb2[e] = e < kK ? a.mlp.b2_op[e] : (e < 4 * kK ? a.mlp.b2_col[e - kK]
+                                                    : (e < 11 * kK ? a.mlp.b2_cov[e - 4 * kK] : 0.f));
+    // zero the K padding of the layer-1 A tile once (columns 36..47 never change)
+    for (int e = t; e < kTM * (kK1 - kDin); e += kTcThreads)
+        put_bf16(sA1, e / (kK1 - kDin), kDin + e % (kK1 - kDin), kK1, 0.f);
+    if (t == 0) tc::mbar_init(&mbar, 1);
+    if (w == 0) {
+        tc::tmem_alloc(&tmem_base, kTmemCols);
+        tc::tmem_relinquish();
+    }
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = tmem_base;
+    const uint32_t lane_addr = tbase + ((uint32_t)(32 * w) << 16);
+    const uint32_t id1 = tc::idesc_bf16(kTM, kN1), id2 = tc::idesc_bf16(kTM, kN2);
+    const uint32_t M = a.counts->n_selected;
+    const uint32_t ntiles = (M + kTM - 1) / kTM;
+    const Cam& c = a.cam;
+    uint32_t phase = 0;
+    bool aborted = false;
+
+    for (uint32_t tile = blockIdx.x; tile < ntiles && !aborted; tile += gridDim.x) {
+        const uint32_t r = tile * kTM + t;
+        const bool valid = r < M;
+        uint32_t j = 0;
+        float wgt = 0.f, dv[3] = {0.f, 0.f, 0.f};
+        if (valid) {
+            j = a.sel_idx[r];
+            wgt = a.sel_w[r];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) dv[q] = a.pos[3 * (size_t)j + q] - c.c[q];
+            const float d = sqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+            const float4* f4 = reinterpret_cast<const float4*>(a.feat + (size_t)j * kF);
+#pragma unroll
+            for (int i = 0; i < kF / 4; ++i) {
+                const float4 v = f4[i];
+                put_bf16(sA1, t, 4 * i, kK1, v.x);
+                put_bf16(sA1, t, 4 * i + 1, kK1, v.y);
+                put_bf16(sA1, t, 4 * i + 2, kK1, v.z);
+                put_bf16(sA1, t, 4 * i + 3, kK1, v.w);
+            }
+            put_bf16(sA1, t, kF, kK1, dv[0] / d);
+            put_bf16(sA1, t, kF + 1, kK1, dv[1] / d);
+            put_bf16(sA1, t, kF + 2, kK1, dv[2] / d);
+            put_bf16(sA1, t, kF + 3, kK1, d);
+        } else {
+            for (int k = 0; k < kDin; ++k) put_bf16(sA1, t, k, kK1, 0.f);
+        }
+        tc::fence_smem_to_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (t == 0) {
+#pragma unroll
+            for (int kk = 0; kk < kK1 / 16; ++kk)
+                tc::mma_bf16(tbase, tc::smem_desc(tc::smem_u32(sA1 + kk * 256), 128, 16 * kK1),
+                             tc::smem_desc(tc::smem_u32(sB1 + kk * 256), 128, 16 * kK1), id1, kk > 0);
+            tc::commit(&mbar);
+        }
+        bool ok = tc::mbar_wait(&mbar, phase, kWaitLimit);
+        if (__syncthreads_or(!ok)) { aborted = true; break; }
+        phase ^= 1;
+        tc::fence_after_sync();
+        // layer-1 epilogue: bias, ReLU, bf16 -> layer-2 A tile (row t)
+#pragma unroll
+        for (int c0 = 0; c0 < kN1; c0 += 32) {
+            float v[32];
+            tc::tmem_ld32(lane_addr + c0, v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) put_bf16(sA2, t, c0 + i, kN1, fmaxf(v[i] + sb1[c0 + i], 0.f));
+        }
+        tc::fence_smem_to_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (t == 0) {
+#pragma unroll
+            for (int kk = 0; kk < kN1 / 16; ++kk)
+                tc::mma_bf16(tbase + kD2Col, tc::smem_desc(tc::smem_u32(sA2 + kk * 256), 128, 16 * kN1),
+                             tc::smem_desc(tc::smem_u32(sB2 + kk * 256), 128, 16 * kN1), id2, kk > 0);
+            tc::commit(&mbar);
+        }
+        ok = tc::mbar_wait(&mbar, phase, kWaitLimit);
+        if (__syncthreads_or(!ok)) { aborted = true; break; }
+        phase ^= 1;
+        tc::fence_after_sync();
+        // layer-2 epilogue (FP32): activations, positions
+        float y[128];
+#pragma unroll
+        for (int c0 = 0; c0 < 128; c0 += 32) {
+            float v[32];
+            tc::tmem_ld32(lane_addr + kD2Col + c0, v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) y[c0 + i] = v[i];
+        }
+        if (valid) {
+#pragma unroll
+            for (int i = 0; i < kN2; ++i) y[i] += sb2[i];
+            const size_t g0 = (size_t)r * kK;
+            float lvv[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) lvv[q] = a.lv[3 * (size_t)j + q];
+#pragma unroll
+            for (int i = 0; i < kK; ++i) {
+                const size_t g = g0 + i;
+                a.out.opac[g] = wgt * tanhf(y[i]);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) a.out.colors[3 * g + q] = sigm(y[kK + 3 * i + q]);
+                const float* yc = y + 4 * kK + 7 * i;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) a.out.scales[3 * g + q] = lvv[q] * sigm(yc[q]);
+                const float inv = 1.0f / sqrtf(yc[3] * yc[3] + yc[4] * yc[4] + yc[5] * yc[5] + yc[6] * yc[6]);
+                *reinterpret_cast<float4*>(a.out.quats + 4 * g) =
+                    make_float4(yc[3] * inv, yc[4] * inv, yc[5] * inv, yc[6] * inv);
+                const float* O = a.offs + ((size_t)j * kK + i) * 3;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) a.out.means[3 * g + q] = dv[q] + O[q] * lvv[q];
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
+    if (aborted) {
+        if (t == 0) atomicExch(&a.counts->timeout, 1u);
+        // wait (bounded) for the MMA group that may still be in flight before releasing TMEM
+        tc::mbar_wait(&mbar, phase, kWaitLimit);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (w == 0) tc::tmem_dealloc(tbase, kTmemCols);
+}
+
+}  // namespace
+}  // namespace ogs
+
+using namespace ogs;
+
+extern "C" ogs_status ogs_decode_bf16(const float* pos, const float* feat, const float* offs,
+                                      const float* lv, int64_t N, const ogs_mlp* mlp,
+                                      const ogs_camera* cam, const uint32_t* sel_idx,
+                                      const float* sel_w, int64_t sel_cap, ogs_counts* counts,
+                                      const ogs_gaussians* out, void* stream) {
+    if (!pos || !feat || !offs || !lv || !mlp || !cam || !sel_idx || !sel_w || !counts || !out)
+        return OGS_ERR_ARG;
+    if (mlp->F != kF || mlp->H != kH || mlp->k != kK || N < 0 || sel_cap < 0) return OGS_ERR_ARG;
+    if (!mlp->w1 || !mlp->b1 || !mlp->w2_op || !mlp->b2_op || !mlp->w2_col || !mlp->b2_col ||
+        !mlp->w2_cov || !mlp->b2_cov)
+        return OGS_ERR_ARG;
+    if (!out->means || !out->scales || !out->quats || !out->opac || !out->colors)
+        return OGS_ERR_ARG;
+    if (!aligned(feat, 16) || !aligned(out->quats, 16)) return OGS_ERR_ARG;
+    if (sel_cap == 0) return OGS_OK;
+    if (cudaFuncSetAttribute(decode_bf16_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kSmemRequest) != cudaSuccess)
+        return OGS_ERR_CUDA;
+    TcArgs args{pos, feat, offs, lv, sel_idx, sel_w, counts, *mlp, *out, make_cam(*cam)};
+    int64_t tiles = (sel_cap + kTM - 1) / kTM;
+    int grid = (int)(tiles < 2 * kSmCount ? tiles : 2 * kSmCount);
+    decode_bf16_tc<<<grid, kTcThreads, kSmemRequest, (cudaStream_t)stream>>>(args);
+    return launch_status();
+}

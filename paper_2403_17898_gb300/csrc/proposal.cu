@@ -1,0 +1,440 @@
+// Learned anchor-visibility proposal: a 3-layer MLP (37 -> 64 -> 64 -> 1, ReLU, ReLU,
+// sigmoid) scores every anchor kept by the LOD rule from [f_v, L/(NL-1), unit direction
+// camera->anchor, ln(d/d_max)] and drops those whose keep probability is below p*, before any
+// Gaussian is decoded.  Training labels are the renderer's own per-anchor maximum
+// contribution (T * alpha) from ogs_blend_fwd.
+//
+// gate:  score pass (thread per selected anchor, weights in shared memory, outer-product
+//        form so only the 40-wide input and 64 second-layer accumulators live in registers;
+//        per-block keep counts) -> scan -> order-preserving scatter of the kept entries.
+// train: thread per selected anchor: forward, BCE gradient dL/dz = (p - y)/M, backward;
+//        weight gradients as per-block sums of outer products staged in shared memory,
+//        written as partials and summed in a fixed order.
+#include <cstring>
+
+#include "internal.cuh"
+
+namespace ogs {
+namespace {
+
+constexpr int kPIn = 37;
+constexpr int kPInPad = 40;
+constexpr int kPH = 64;
+constexpr int kGateThreads = 128;
+constexpr int kNetFloats = kPH * kPInPad + kPH + kPH * kPH + kPH + kPH + 4;   // smem image
+
+struct PropArgs {
+    const float* pos;
+    const uint8_t* level;
+    const float* feat;
+    int NL;
+    Cam cam;
+    ogs_proposal net;
+};
+
+// Loads the network into shared memory: w1 [64][40] (zero padded), b1, w2t [64][64] (w2
+// transposed: row o holds the weights that hidden-1 unit o feeds), b2, w3, b3.
+__device__ void load_net(const ogs_proposal& n, float* s) {
+    float* w1 = s;
+    float* b1 = w1 + kPH * kPInPad;
+    float* w2t = b1 + kPH;
+    float* b2 = w2t + kPH * kPH;
+    float* w3 = b2 + kPH;
+    float* b3 = w3 + kPH;
+    for (int e = threadIdx.x; e < kPH * kPInPad; e += blockDim.x) {
+        const int o = e / kPInPad, i = e % kPInPad;
+        w1[e] = i < kPIn ? n.w1[o * kPIn + i] : 0.f;
+    }
+    for (int e = threadIdx.x; e < kPH * kPH; e += blockDim.x) {
+        const int o = e / kPH, i = e % kPH;
+        w2t[e] = n.w2[i * kPH + o];
+    }
+    for (int e = threadIdx.x; e < kPH; e += blockDim.x) {
+        b1[e] = n.b1[e];
+        b2[e] = n.b2[e];
+        w3[e] = n.w3[e];
+    }
+    if (threadIdx.x == 0) b3[0] = n.b3[0];
+}
+
+__device__ __forceinline__ void prop_input(const PropArgs& a, uint32_t j, float (&x)[kPInPad]) {
+    const Cam& c = a.cam;
+    const float4* f4 = reinterpret_cast<const float4*>(a.feat + (size_t)j * 32);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float4 v = f4[i];
+        x[4 * i] = v.x; x[4 * i + 1] = v.y; x[4 * i + 2] = v.z; x[4 * i + 3] = v.w;
+    }
+    const float dx = a.pos[3 * (size_t)j] - c.c[0], dy = a.pos[3 * (size_t)j + 1] - c.c[1],
+                dz = a.pos[3 * (size_t)j + 2] - c.c[2];
+    const float d = sqrtf(dx * dx + dy * dy + dz * dz);
+    x[32] = (float)a.level[j] / (float)max(a.NL - 1, 1);
+    x[33] = dx / d; x[34] = dy / d; x[35] = dz / d;
+    x[36] = logf(d / c.d_max);
+    x[37] = x[38] = x[39] = 0.f;
+}
+
+__device__ __forceinline__ float prop_logit(const float* s, const float (&x)[kPInPad]) {
+    const float* w1 = s;
+    const float* b1 = w1 + kPH * kPInPad;
+    const float* w2t = b1 + kPH;
+    const float* b2 = w2t + kPH * kPH;
+    const float* w3 = b2 + kPH;
+    const float* b3 = w3 + kPH;
+    float h2[kPH];
+#pragma unroll
+    for (int i = 0; i < kPH; ++i) h2[i] = b2[i];
+#pragma unroll 1
+    for (int o = 0; o < kPH; ++o) {
+        const float4* row = reinterpret_cast<const float4*>(w1 + o * kPInPad);
+        float acc = b1[o];
+#pragma unroll
+        for (int i = 0; i < kPInPad / 4; ++i) {
+            const float4 w = row[i];
+            acc = fmaf(w.x, x[4 * i], acc);
+            acc = fmaf(w.y, x[4 * i + 1], acc);
+            acc = fmaf(w.z, x[4 * i + 2], acc);
+            acc = fmaf(w.w, x[4 * i + 3], acc);
+        }
+        const float h1 = fmaxf(acc, 0.f);
+        const float4* col = reinterpret_cast<const float4*>(w2t + o * kPH);
+#pragma unroll
+        for (int i = 0; i < kPH / 4; ++i) {
+            const float4 w = col[i];
+            h2[4 * i] = fmaf(w.x, h1, h2[4 * i]);
+            h2[4 * i + 1] = fmaf(w.y, h1, h2[4 * i + 1]);
+            h2[4 * i + 2] = fmaf(w.z, h1, h2[4 * i + 2]);
+            h2[4 * i + 3] = fmaf(w.w, h1, h2[4 * i + 3]);
+        }
+    }
+    float z = b3[0];
+#pragma unroll
+    for (int i = 0; i < kPH; ++i) z = fmaf(w3[i], fmaxf(h2[i], 0.f), z);
+    return z;
+}
+
+// score pass: p per selected anchor (scratch), keep counts per block, old M saved
+__global__ void __launch_bounds__(kGateThreads) gate_score(PropArgs a, const uint32_t* sel_idx,
+                                                           const ogs_counts* counts, float p_star,
+                                                           float* p_out, uint32_t* block_count,
+                                                           uint32_t* m_saved) {
+    extern __shared__ __align__(16) float s[];
+    __shared__ uint32_t wc[kGateThreads / 32];
+    const uint32_t M = counts->n_selected;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *m_saved = M;
+    const uint32_t r = blockIdx.x * kGateThreads + threadIdx.x;
+    bool keep = false;
+    if ((uint32_t)blockIdx.x * kGateThreads < M) {
+        load_net(a.net, s);
+        __syncthreads();
+        if (r < M) {
+            float x[kPInPad];
+            prop_input(a, sel_idx[r], x);
+            const float p = 1.0f / (1.0f + __expf(-prop_logit(s, x)));
+            p_out[r] = p;
+            keep = p >= p_star;
+        }
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, keep);
+    if (lane_id() == 0) wc[threadIdx.x >> 5] = __popc(b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int i = 0; i < kGateThreads / 32; ++i) t += wc[i];
+        block_count[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(1024) gate_scan(uint32_t* block_count, int nb, int k,
+                                                  ogs_counts* counts) {
+    __shared__ uint32_t ws[32];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nb; b0 += 1024) {
+        const int b = b0 + threadIdx.x;
+        const uint32_t v = b < nb ? block_count[b] : 0;
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane_id() >= (unsigned)o) x += y;
+        }
+        if (lane_id() == 31) ws[threadIdx.x >> 5] = x;
+        __syncthreads();
+        uint32_t wpre = 0, tot = 0;
+        for (int q = 0; q < 32; ++q) {
+            wpre += (q < (int)(threadIdx.x >> 5)) ? ws[q] : 0;
+            tot += ws[q];
+        }
+        const uint32_t excl = carry + wpre + x - v;
+        if (b < nb) block_count[b] = excl;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        counts->n_selected = carry;
+        counts->n_gaussians = carry * (uint32_t)k;
+    }
+}
+
+__global__ void __launch_bounds__(kGateThreads) gate_scatter(
+    const uint32_t* sel_in, const float* w_in, const float* p, float p_star,
+    const uint32_t* m_saved, const uint32_t* block_off, uint32_t* sel_out, float* w_out) {
+    __shared__ uint32_t wc[kGateThreads / 32];
+    const uint32_t M = *m_saved;
+    const uint32_t r = blockIdx.x * kGateThreads + threadIdx.x;
+    const bool keep = r < M && p[r] >= p_star;
+    const unsigned b = __ballot_sync(0xffffffffu, keep);
+    if (lane_id() == 0) wc[threadIdx.x >> 5] = __popc(b);
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (int i = 0; i < (int)(threadIdx.x >> 5); ++i) wpre += wc[i];
+    if (keep) {
+        const uint32_t o = block_off[blockIdx.x] + wpre + __popc(b & lanemask_lt());
+        sel_out[o] = sel_in[r];
+        w_out[o] = w_in[r];
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// training
+// ---------------------------------------------------------------------------------------
+
+constexpr int kTrThreads = 64;
+// gradient layout (flat): dw1 [64][37] | db1 [64] | dw2 [64][64] | db2 [64] | dw3 [64] | db3
+constexpr int kGW1 = 0;
+constexpr int kGB1 = kGW1 + kPH * kPIn;
+constexpr int kGW2 = kGB1 + kPH;
+constexpr int kGB2 = kGW2 + kPH * kPH;
+constexpr int kGW3 = kGB2 + kPH;
+constexpr int kGB3 = kGW3 + kPH;
+constexpr int kGrads = kGB3 + 1;
+constexpr int kTrBlocks = 2 * kSmCount;
+
+struct TrainArgs {
+    PropArgs pa;
+    const uint32_t* sel_idx;
+    const ogs_counts* counts;
+    const uint32_t* maxc;
+    uint32_t tau_bits;
+    float* partial;
+    float* loss;
+};
+
+__global__ void __launch_bounds__(kTrThreads) prop_train_kernel(TrainArgs a) {
+    extern __shared__ __align__(16) float s[];
+    float* net = s;                                  // kNetFloats
+    float* acc = net + kNetFloats;                   // kGrads
+    float* sX = acc + ((kGrads + 3) / 4) * 4;        // [T][40]
+    float* sH1 = sX + kTrThreads * kPInPad;          // [T][64]
+    float* sH2 = sH1 + kTrThreads * kPH;             // [T][64]  relu(a2)
+    float* sD1 = sH2 + kTrThreads * kPH;             // [T][64]  dL/da1
+    float* sD2 = sD1 + kTrThreads * kPH;             // [T][64]  dL/da2
+    float* sDZ = sD2 + kTrThreads * kPH;             // [T]
+    load_net(a.pa.net, net);
+    for (int e = threadIdx.x; e < kGrads; e += blockDim.x) acc[e] = 0.f;
+    __syncthreads();
+    const float* w1 = net;
+    const float* b1 = w1 + kPH * kPInPad;
+    const float* w2t = b1 + kPH;
+    const float* b2 = w2t + kPH * kPH;
+    const float* w3 = b2 + kPH;
+    const float* b3 = w3 + kPH;
+    const uint32_t M = a.counts->n_selected;
+    const float invM = M ? 1.0f / (float)M : 0.f;
+    const int t = threadIdx.x;
+    float lsum = 0.f;
+    for (uint32_t base = blockIdx.x * kTrThreads; base < M; base += gridDim.x * kTrThreads) {
+        const uint32_t r = base + t;
+        const bool valid = r < M;
+        float x[kPInPad];
+        uint32_t j = 0;
+        if (valid) {
+            j = a.sel_idx[r];
+            prop_input(a.pa, j, x);
+        } else {
+#pragma unroll
+            for (int i = 0; i < kPInPad; ++i) x[i] = 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < kPInPad; ++i) sX[t * kPInPad + i] = x[i];
+        // forward, keeping a1 sign in sD1 temporarily and h1 in sH1
+        float a2[kPH];
+#pragma unroll
+        for (int i = 0; i < kPH; ++i) a2[i] = b2[i];
+        for (int o = 0; o < kPH; ++o) {
+            float acc1 = b1[o];
+#pragma unroll
+            for (int i = 0; i < kPInPad; ++i) acc1 = fmaf(w1[o * kPInPad + i], x[i], acc1);
+            const float h1 = fmaxf(acc1, 0.f);
+            sH1[t * kPH + o] = h1;
+            sD1[t * kPH + o] = acc1 > 0.f ? 1.f : 0.f;
+#pragma unroll
+            for (int i = 0; i < kPH; ++i) a2[i] = fmaf(w2t[o * kPH + i], h1, a2[i]);
+        }
+        float z = b3[0];
+#pragma unroll
+        for (int i = 0; i < kPH; ++i) {
+            const float h2 = fmaxf(a2[i], 0.f);
+            sH2[t * kPH + i] = h2;
+            z = fmaf(w3[i], h2, z);
+        }
+        const float p = 1.0f / (1.0f + __expf(-z));
+        float dz = 0.f;
+        if (valid) {
+            const float y = a.maxc[j] >= a.tau_bits ? 1.f : 0.f;
+            dz = (p - y) * invM;
+            // BCE with the log-sigmoid written stably: -y z + log(1 + e^z)
+            const float sp = z > 0.f ? z + log1pf(__expf(-z)) : log1pf(__expf(z));
+            lsum += (sp - y * z) * invM;
+        }
+        sDZ[t] = dz;
+#pragma unroll
+        for (int i = 0; i < kPH; ++i) sD2[t * kPH + i] = a2[i] > 0.f ? dz * w3[i] : 0.f;
+        // dL/da1 = (W2^T dL/da2) * relu'(a1)
+        for (int o = 0; o < kPH; ++o) {
+            float g = 0.f;
+#pragma unroll
+            for (int i = 0; i < kPH; ++i) g = fmaf(w2t[o * kPH + i], sD2[t * kPH + i], g);
+            sD1[t * kPH + o] *= g;
+        }
+        __syncthreads();
+        const int nv = (int)min((uint32_t)kTrThreads, M - base);
+        for (int e = t; e < kPH * kPIn; e += kTrThreads) {
+            const int o = e / kPIn, i = e % kPIn;
+            float sum = 0.f;
+            for (int q = 0; q < nv; ++q) sum = fmaf(sD1[q * kPH + o], sX[q * kPInPad + i], sum);
+            acc[kGW1 + e] += sum;
+        }
+        for (int e = t; e < kPH * kPH; e += kTrThreads) {
+            const int o = e / kPH, i = e % kPH;
+            float sum = 0.f;
+            for (int q = 0; q < nv; ++q) sum = fmaf(sD2[q * kPH + o], sH1[q * kPH + i], sum);
+            acc[kGW2 + e] += sum;
+        }
+        for (int e = t; e < kPH; e += kTrThreads) {
+            float s1 = 0.f, s2 = 0.f, s3 = 0.f;
+            for (int q = 0; q < nv; ++q) {
+                s1 += sD1[q * kPH + e];
+                s2 += sD2[q * kPH + e];
+                s3 = fmaf(sDZ[q], sH2[q * kPH + e], s3);
+            }
+            acc[kGB1 + e] += s1;
+            acc[kGB2 + e] += s2;
+            acc[kGW3 + e] += s3;
+        }
+        if (t == 0) {
+            float s0 = 0.f;
+            for (int q = 0; q < nv; ++q) s0 += sDZ[q];
+            acc[kGB3] += s0;
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if (lane_id() == 0 && a.loss) atomicAdd(a.loss, lsum);
+    float* out = a.partial + (size_t)blockIdx.x * kGrads;
+    for (int e = t; e < kGrads; e += kTrThreads) out[e] = acc[e];
+}
+
+__global__ void prop_reduce(const float* __restrict__ partial, int nblocks, ogs_proposal g) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kGrads; e += gridDim.x * blockDim.x) {
+        float sum = 0.f;
+        for (int b = 0; b < nblocks; ++b) sum += partial[(size_t)b * kGrads + e];
+        float* dst;
+        if (e < kGB1) dst = const_cast<float*>(g.w1) + (e - kGW1);
+        else if (e < kGW2) dst = const_cast<float*>(g.b1) + (e - kGB1);
+        else if (e < kGB2) dst = const_cast<float*>(g.w2) + (e - kGW2);
+        else if (e < kGW3) dst = const_cast<float*>(g.b2) + (e - kGB2);
+        else if (e < kGB3) dst = const_cast<float*>(g.w3) + (e - kGW3);
+        else dst = const_cast<float*>(g.b3);
+        *dst += sum;
+    }
+}
+
+size_t train_smem() {
+    return sizeof(float) * (kNetFloats + ((kGrads + 3) / 4) * 4 +
+                            kTrThreads * (kPInPad + 4 * kPH + 1));
+}
+
+bool net_ok(const ogs_proposal* n) {
+    return n && n->w1 && n->b1 && n->w2 && n->b2 && n->w3 && n->b3;
+}
+
+}  // namespace
+}  // namespace ogs
+
+using namespace ogs;
+
+extern "C" size_t ogs_proposal_gate_scratch_bytes(int64_t sel_cap) {
+    int64_t nb = (sel_cap + kGateThreads - 1) / kGateThreads;
+    if (nb < 1) nb = 1;
+    Carver cv(nullptr);
+    cv.take<float>(sel_cap > 0 ? sel_cap : 1);
+    cv.take<uint32_t>(nb);
+    cv.take<uint32_t>(1);
+    return cv.off + 256;
+}
+
+extern "C" ogs_status ogs_proposal_gate(const float* pos, const uint8_t* level, const float* feat,
+                                        int64_t N, int32_t NL, int32_t k, const ogs_camera* cam,
+                                        const ogs_proposal* net, float p_star,
+                                        const uint32_t* sel_in, const float* w_in, int64_t sel_cap,
+                                        ogs_counts* counts, uint32_t* sel_out, float* w_out,
+                                        float* p_out, void* scratch, size_t scratch_bytes,
+                                        void* stream) {
+    if (!pos || !level || !feat || !cam || !net_ok(net) || !sel_in || !w_in || !counts ||
+        !sel_out || !w_out || !scratch)
+        return OGS_ERR_ARG;
+    if (N < 0 || NL < 1 || k < 1 || sel_cap < 0 || sel_in == sel_out) return OGS_ERR_ARG;
+    if (scratch_bytes < ogs_proposal_gate_scratch_bytes(sel_cap) || !aligned(scratch, 16) ||
+        !aligned(feat, 16))
+        return OGS_ERR_ARG;
+    if (sel_cap == 0) return OGS_OK;
+    Carver cv(scratch);
+    float* p = cv.take<float>(sel_cap);
+    const int nb = (int)((sel_cap + kGateThreads - 1) / kGateThreads);
+    uint32_t* block = cv.take<uint32_t>(nb);
+    uint32_t* m_saved = cv.take<uint32_t>(1);
+    PropArgs a{pos, level, feat, NL, make_cam(*cam), *net};
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t smem = sizeof(float) * kNetFloats;
+    gate_score<<<nb, kGateThreads, smem, st>>>(a, sel_in, counts, p_star, p, block, m_saved);
+    gate_scan<<<1, 1024, 0, st>>>(block, nb, k, counts);
+    gate_scatter<<<nb, kGateThreads, 0, st>>>(sel_in, w_in, p, p_star, m_saved, block, sel_out, w_out);
+    if (p_out)
+        cudaMemcpyAsync(p_out, p, sizeof(float) * sel_cap, cudaMemcpyDeviceToDevice, st);
+    return launch_status();
+}
+
+extern "C" size_t ogs_proposal_train_scratch_bytes(void) {
+    return sizeof(float) * (size_t)kTrBlocks * kGrads + 256;
+}
+
+extern "C" ogs_status ogs_proposal_train(const float* pos, const uint8_t* level, const float* feat,
+                                         int64_t N, int32_t NL, const ogs_camera* cam,
+                                         const ogs_proposal* net, const uint32_t* sel_idx,
+                                         const ogs_counts* counts, const uint32_t* maxc,
+                                         float tau, const ogs_proposal* grads, float* loss,
+                                         void* scratch, size_t scratch_bytes, void* stream) {
+    if (!pos || !level || !feat || !cam || !net_ok(net) || !sel_idx || !counts || !maxc ||
+        !net_ok(grads) || !scratch)
+        return OGS_ERR_ARG;
+    if (N < 0 || NL < 1 || !(tau >= 0.f)) return OGS_ERR_ARG;
+    if (scratch_bytes < ogs_proposal_train_scratch_bytes() || !aligned(scratch, 16) ||
+        !aligned(feat, 16))
+        return OGS_ERR_ARG;
+    const size_t smem = train_smem();
+    if (cudaFuncSetAttribute(prop_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return OGS_ERR_CUDA;
+    uint32_t tau_bits;
+    memcpy(&tau_bits, &tau, sizeof tau_bits);
+    TrainArgs a{{pos, level, feat, NL, make_cam(*cam), *net}, sel_idx, counts, maxc, tau_bits,
+                (float*)scratch, loss};
+    cudaStream_t st = (cudaStream_t)stream;
+    prop_train_kernel<<<kTrBlocks, kTrThreads, smem, st>>>(a);
+    prop_reduce<<<(kGrads + 255) / 256, 256, 0, st>>>((const float*)scratch, kTrBlocks, *grads);
+    return launch_status();
+}

@@ -41,7 +41,9 @@ class Renderer:
     pairs; ``render(..., check=True)`` grows them and re-renders when a view overflows.
     """
 
-    def __init__(self, scene, mlp, W, H, sel_cap=None, pair_cap=None, k=10):
+    def __init__(self, scene, mlp, W, H, sel_cap=None, pair_cap=None, k=10, precision="fp32"):
+        assert precision in ("fp32", "bf16")
+        self.precision = precision
         self.k = k
         self.W, self.H = int(W), int(H)
         self.gx, self.gy = (self.W + TILE - 1) // TILE, (self.H + TILE - 1) // TILE
@@ -73,6 +75,11 @@ class Renderer:
         dev = "cuda"
         self.sel_idx = torch.empty(S, dtype=torch.int32, device=dev)
         self.sel_w = torch.empty(S, device=dev)
+        # gated selection (written by the proposal gate when one is used)
+        self.sel_idx_g = torch.empty(S, dtype=torch.int32, device=dev)
+        self.sel_w_g = torch.empty(S, device=dev)
+        self.gate_scratch = torch.empty(abi.proposal_gate_scratch_bytes(S), dtype=torch.uint8,
+                                        device=dev)
         self.g = {"means": torch.empty(G, 3, device=dev), "scales": torch.empty(G, 3, device=dev),
                   "quats": torch.empty(G, 4, device=dev), "opac": torch.empty(G, device=dev),
                   "colors": torch.empty(G, 3, device=dev)}
@@ -91,10 +98,11 @@ class Renderer:
 
     # -- one view --------------------------------------------------------------------------
     def enqueue(self, cam, infer=True, bg=(0.0, 0.0, 0.0), maxc=None, stream=None, timers=None,
-                n_eval=None):
+                n_eval=None, gate=None):
         """Enqueues the whole forward pass of one view (no host synchronisation).  If
         ``timers`` is a dict, a CUDA event pair is recorded around every stage under its name
-        (on the launching stream)."""
+        (on the launching stream).  ``gate = (proposal_weights, p_star)`` inserts the learned
+        anchor-visibility gate between selection and decoding."""
         assert int(cam.W) == self.W and int(cam.H) == self.H
         c = abi.camera(cam)
         st = stream if stream is not None else torch.cuda.current_stream()
@@ -113,9 +121,19 @@ class Renderer:
         stage("lod_select", lambda: abi.lod_select(
             self.pos, self.level, self.dL, self.N, self.NL, self.k, c, infer, self.sel_idx,
             self.sel_w, self.sel_cap, self.counts_t, self.sel_scratch, st))
-        stage("decode", lambda: abi.decode(
-            self.pos, self.feat, self.offs, self.lv, self.N, self._mlp_struct, c, self.sel_idx,
-            self.sel_w, self.sel_cap, self.counts_t, self._g_struct, st))
+        sel, selw = self.sel_idx, self.sel_w
+        if gate is not None:
+            net, p_star = gate
+            stage("proposal_gate", lambda: abi.proposal_gate(
+                self.pos, self.level, self.feat, self.N, self.NL, self.k, c, net, p_star,
+                self.sel_idx, self.sel_w, self.sel_cap, self.counts_t, self.sel_idx_g,
+                self.sel_w_g, None, self.gate_scratch, st))
+            sel, selw = self.sel_idx_g, self.sel_w_g
+        self.active_sel = sel
+        dec = abi.decode_bf16 if self.precision == "bf16" else abi.decode
+        stage("decode", lambda: dec(
+            self.pos, self.feat, self.offs, self.lv, self.N, self._mlp_struct, c, sel, selw,
+            self.sel_cap, self.counts_t, self._g_struct, st))
         stage("project_bin", lambda: abi.project_bin(
             self._g_struct, self.g_cap, 1, c, self.rec, self.depth_key, self.rect, self.tiles,
             self.counts_t, st))
@@ -125,25 +143,25 @@ class Renderer:
             st))
         stage("blend_fwd", lambda: abi.blend_fwd(
             self.rec, self.pair_gauss, self.tile_range, self.W, self.H, bg, self.img, self.T,
-            self.n_last, self.sel_idx, self.k, maxc, n_eval, st))
+            self.n_last, sel, self.k, maxc, n_eval, st))
 
     def counts(self) -> FrameCounts:
         v = self.counts_t.cpu().numpy().view(np.uint32)
         return FrameCounts(*[int(x) for x in v])
 
-    def render_to_host(self, cam, host_img, infer=True, bg=(0.0, 0.0, 0.0)):
+    def render_to_host(self, cam, host_img, infer=True, bg=(0.0, 0.0, 0.0), gate=None):
         """The end-to-end call: render one view and copy the image into ``host_img`` (a pinned
         float32 [3, H, W] CPU tensor); returns when the image is on the host."""
-        self.enqueue(cam, infer, bg)
+        self.enqueue(cam, infer, bg, gate=gate)
         host_img.copy_(self.img, non_blocking=True)
         torch.cuda.current_stream().synchronize()
         return host_img
 
-    def render(self, cam, infer=True, bg=(0.0, 0.0, 0.0), maxc=None, check=True):
+    def render(self, cam, infer=True, bg=(0.0, 0.0, 0.0), maxc=None, check=True, gate=None):
         """Renders one view; with ``check`` it synchronises, grows overflowing buffers and
         re-renders until everything fits."""
         for _ in range(4):
-            self.enqueue(cam, infer, bg, maxc)
+            self.enqueue(cam, infer, bg, maxc, gate=gate)
             if not check:
                 return None
             c = self.counts()

@@ -204,11 +204,20 @@ def test_training_view_gradient_matches_oracle(abi, torch):
 
 def test_finite_difference_through_gpu_street_scale(abi, torch):
     """FD check of decoder-weight gradients through the FP32 GPU forward at the 500k-anchor,
-    1600x900 street-grid scale (central differences, relative step 1e-2 of the weight)."""
+    1600x900 street-grid scale.  The target is black, so L1 is the mean intensity: no pixel
+    sits on the |.| kink and the FD quotient is not a cancelling sum of signs; the loss for
+    the FD is summed in float64 on the host to keep accumulation noise below the signal.
+
+    Only colour-decoder parameters are perturbed: they never move alpha.  Opacity and
+    geometry parameters push (pixel, Gaussian) pairs across the alpha >= 1/255 skip and the
+    T < 1e-4 stop; at this scale the resulting jumps (which the analytic gradient omits by
+    definition) move a finite difference by several percent.  Those chains are checked
+    against the oracle's analytic gradient instead (and the oracle against FD on scenes with
+    no decision near a threshold)."""
     from paper_2403_17898_gb300.render import Trainer
     sc, mlp, cams = synth.CONFIGS["street500k_1600x900"]()
     cam = cams[10]
-    target = cuda(np.random.default_rng(1).uniform(size=(3, cam.H, cam.W)).astype(np.float32))
+    target = torch.zeros(3, cam.H, cam.W, device="cuda")
     tr = Trainer(sc, mlp, cam.W, cam.H, sel_cap=200_000, pair_cap=4_000_000)
     c = tr.render(cam, infer=False)
     assert c.overflow == 0 and c.n_selected > 1000
@@ -219,22 +228,22 @@ def test_finite_difference_through_gpu_street_scale(abi, torch):
 
     def loss_at():
         tr.enqueue(cam, infer=False)
-        tr.loss.zero_()
-        abi.loss_l1(tr.img, target, tr.img.numel(), tr.dimg, tr.loss)
         torch.cuda.synchronize()
-        return float(tr.loss.item())
+        return float(tr.img.double().mean().item())
 
-    checks = [("b2_op", (3,)), ("b2_col", (4,)), ("b2_col", (17,)), ("b1", (0, 5)),
-              ("b2_cov", (2,)), ("w2_col", (5, 7))]
+    assert abs(loss_at() - tr.loss.item()) <= 1e-5 * abs(loss_at())
+    checks = [("b2_col", (4,)), ("b2_col", (17,)), ("b1", (1, 5)), ("b1", (1, 9)),
+              ("w2_col", (5, 7)), ("w2_col", (22, 30)), ("w1", (1, 3, 4)), ("w1", (1, 10, 33))]
     for name, ix in checks:
         p = tr.mlp[name]
         g = float(tr.dmlp[name][ix].item())
         x0 = float(p[ix].item())
-        h = 1e-2 * max(abs(x0), 0.1)
+        # first-layer parameters move ReLU kinks: a smaller step keeps the quotient local
+        h = 2e-3 if name in ("b1", "w1") else 0.02
         p[ix] = x0 + h
         lp = loss_at()
         p[ix] = x0 - h
         lm = loss_at()
         p[ix] = x0
         fd = (lp - lm) / (2 * h)
-        assert abs(fd - g) <= 0.05 * abs(g) + 2e-7, (name, ix, g, fd)
+        assert abs(fd - g) <= 0.03 * abs(g) + 1e-6, (name, ix, g, fd)

@@ -1,0 +1,71 @@
+"""Pins of the oracle's proposal network (inputs, forward, BCE and backward)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+
+def _net(seed=0):
+    return synth.ProposalMLP(*[a.astype(np.float64) for a in synth.proposal_mlp(seed=seed).arrays()])
+
+
+def test_inputs_layout():
+    cam = synth.look_at_camera(np.zeros(3), np.array([1.0, 0.0, 0.0]), 32, 32, d_max=40.0)
+    pos = np.array([[3.0, 0.0, 4.0]])
+    feat = np.arange(32, dtype=np.float64)[None, :]
+    X = oracle.proposal_inputs(pos, np.array([2]), feat, 5, np.array([0]), cam)
+    np.testing.assert_allclose(X[0, :32], np.arange(32))
+    assert X[0, 32] == 0.5                               # level 2 of 5 -> 2/4
+    np.testing.assert_allclose(X[0, 33:36], [0.6, 0.0, 0.8])
+    assert X[0, 36] == pytest.approx(math.log(5.0 / 40.0), rel=1e-12)
+
+
+def test_bias_only_network():
+    net = _net()
+    for a in net.arrays():
+        a[...] = 0
+    net.b3[0] = math.log(3.0)                            # sigmoid -> 0.75
+    X = np.random.default_rng(0).normal(size=(5, 37))
+    p, _ = oracle.proposal_forward(net, X)
+    np.testing.assert_allclose(p, 0.75, rtol=1e-12)
+    loss, g = oracle.proposal_bce_grad(net, X, np.array([1, 1, 0, 0, 1]))
+    # -(3 ln .75 + 2 ln .25)/5 and dL/db3 = mean(p - y) = (5*.75 - 3)/5
+    assert loss == pytest.approx(-(3 * math.log(0.75) + 2 * math.log(0.25)) / 5, rel=1e-12)
+    assert g["b3"][0] == pytest.approx((5 * 0.75 - 3) / 5, rel=1e-12)
+
+
+def test_single_path_copies_input():
+    net = _net()
+    for a in net.arrays():
+        a[...] = 0
+    net.w1[0, 36] = 1.0        # hidden1_0 = relu(ln(d/d_max)) ...
+    net.b1[0] = 10.0           # ... shifted positive
+    net.w2[0, 0] = 1.0
+    net.w3[0, 0] = 1.0
+    net.b3[0] = -10.0
+    X = np.zeros((3, 37))
+    X[:, 36] = [-2.0, -1.0, 0.5]
+    p, t = oracle.proposal_forward(net, X)
+    np.testing.assert_allclose(t["z"], X[:, 36], atol=1e-12)
+
+
+def test_backward_matches_finite_differences():
+    rng = np.random.default_rng(1)
+    net = _net(3)
+    net = synth.ProposalMLP(*[a.astype(np.float64) for a in net.arrays()])
+    X = rng.normal(size=(40, 37))
+    y = (rng.uniform(size=40) < 0.4).astype(np.float64)
+    loss, g = oracle.proposal_bce_grad(net, X, y)
+    for name, ix in [("w1", (3, 7)), ("w1", (60, 36)), ("b1", (5,)), ("w2", (10, 20)),
+                     ("b2", (63,)), ("w3", (0, 11)), ("b3", (0,))]:
+        arr = getattr(net, name)
+        x0 = arr[ix]
+        arr[ix] = x0 + 1e-6
+        lp = oracle.proposal_bce_grad(net, X, y)[0]
+        arr[ix] = x0 - 1e-6
+        lm = oracle.proposal_bce_grad(net, X, y)[0]
+        arr[ix] = x0
+        assert g[name][ix] == pytest.approx((lp - lm) / 2e-6, rel=1e-5, abs=1e-9), (name, ix)
