@@ -3,8 +3,10 @@
 
 Workload (default): 2M anchors over 8 octree levels on a 2 km synthetic city grid, k = 10
 neural Gaussians per anchor, 1920x1080, a 120-pose zoom-out from 10 m to 2 km altitude.  A
-step is one view through the whole forward hot path (LOD selection, decoding, projection and
-binning, sorting, blending); step i renders pose (rank + i * world) mod 120.
+step is one view through the whole forward hot path (LOD selection, learned visibility gate,
+BF16 tensor-core decoding, projection and binning, sorting, blending); step i renders pose
+(rank + i * world) mod 120.  The same steps are also timed on the plain FP32 path (no gate,
+FP32 decode), and the gate's image cost is judged on 60 held-out poses.
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on the host
 cores instead (rank 0 only), each step a 1/16 sub-view of a frame.
@@ -218,14 +220,93 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------
 
 # kernels each ABI call launches per frame (radix passes: 4 depth + 2 tile, 3 kernels each)
-LAUNCHES = {"lod_select": 3, "decode": 1, "project_bin": 1,
+LAUNCHES = {"lod_select": 3, "proposal_gate": 3, "decode": 1, "project_bin": 1,
             "sort": 1 + 3 * 4 + 3 + 3 * 2 + 1, "blend_fwd": 1}
+DPSNR_GATE_DB = 0.05
+
+
+def _time_form(rd, cams, pose, steps, warmup, gate, flush, clk_index):
+    """Device time of `steps` frames (CUDA events per frame and per stage, L2 flushed
+    between frames) and the clocks seen meanwhile."""
+    import torch
+    for i in range(warmup):
+        flush.zero_()
+        rd.enqueue(cams[pose(i)], gate=gate)
+    torch.cuda.synchronize()
+    timers, steps_ev = {}, []
+    with ClockSampler(clk_index) as clk:
+        torch.cuda.synchronize()
+        for i in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            rd.enqueue(cams[pose(warmup + i)], timers=timers, gate=gate)
+            e1.record()
+            steps_ev.append((e0, e1))
+        torch.cuda.synchronize()
+    c = rd.counts()
+    assert c.overflow == 0 and c.timeout == 0, "overflow or expired wait in timed steps"
+    step_ms = [a.elapsed_time(b) for a, b in steps_ev]
+    stage_ms = {k: float(np.mean([a.elapsed_time(b) for a, b in v])) for k, v in timers.items()}
+    return sum(step_ms) / 1e3, stage_ms, clk.summary()
+
+
+def _per_pose(rd, cams, gate=None):
+    """Selected anchors, Gaussians, pairs and blend evaluations of every pose (untimed)."""
+    import torch
+    n_eval = torch.zeros(rd.H, rd.W, dtype=torch.int32, device="cuda")
+    out = []
+    for cam in cams:
+        c = rd.render(cam, gate=gate)
+        rd.enqueue(cam, n_eval=n_eval, gate=gate)
+        out.append((c.n_selected, c.n_gaussians, c.n_pairs, int(n_eval.sum().item())))
+    return out
+
+
+def _train_proposal(rd, train_cams, test_cams, full_rd):
+    """Trains the anchor-visibility proposal on the training poses, calibrates p* on a
+    subset of them and judges it on the held-out poses against full-detail renders."""
+    import synth
+    from paper_2403_17898_gb300 import proposal
+    t0 = time.perf_counter()
+    views = proposal.collect_labels(rd, train_cams)
+    net = proposal.ProposalNet(synth.proposal_mlp(seed=0), lr=2e-3)
+    hist = proposal.train(net, rd, views, epochs=30)
+    t_train = time.perf_counter() - t0
+
+    def judge(cams, p_star):
+        dps, kept, direct = [], [], []
+        for cam in cams:
+            full_rd.render(proposal.full_detail(cam))
+            ref = full_rd.img
+            c0 = rd.render(cam)
+            plain = rd.img.clone()
+            c1 = rd.render(cam, gate=(net.w, p_star))
+            dps.append(proposal.psnr(plain, ref) - proposal.psnr(rd.img, ref))
+            direct.append(proposal.psnr(rd.img, plain))
+            kept.append(c1.n_selected / max(c0.n_selected, 1))
+        return float(np.mean(dps)), float(np.max(dps)), float(np.mean(kept)), float(np.median(direct))
+
+    calib = train_cams[::5]
+    p_star = 0.0
+    for cand in (0.001, 0.002, 0.005, 0.01, 0.02, 0.05, 0.1, 0.15, 0.2, 0.3, 0.4, 0.5):
+        if judge(calib, cand)[0] <= DPSNR_GATE_DB:
+            p_star = cand
+    mean_dp, max_dp, kept, direct = judge(test_cams, p_star)
+    info = {"train_poses": len(train_cams), "heldout_poses": len(test_cams),
+            "epochs": len(hist), "bce_first_epoch": hist[0], "bce_last_epoch": hist[-1],
+            "train_s": t_train, "p_star": p_star, "label": "max T*alpha >= 1/255",
+            "heldout_dpsnr_db_mean": mean_dp, "heldout_dpsnr_db_max": max_dp,
+            "heldout_psnr_vs_plain_db_median": direct, "heldout_kept_anchor_frac": kept,
+            "dpsnr_definition": "PSNR(plain FP32 LOD vs full-detail) - PSNR(gated BF16 vs full-detail)"}
+    return net, p_star, info
 
 
 def run_gpu(args):
     import torch
     import torch.distributed as dist
 
+    import synth
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
     if ws > 1:
@@ -238,48 +319,41 @@ def run_gpu(args):
     n = len(cams)
     W, H = cams[0].W, cams[0].H
     rd = Renderer(sc, mlp, W, H, sel_cap=200_000, pair_cap=4_000_000)
-    # size buffers over the whole path, record per-pose work
-    per_pose = []
-    n_eval = torch.zeros(H, W, dtype=torch.int32, device="cuda")
-    for cam in cams:
-        c = rd.render(cam)
-        rd.enqueue(cam, n_eval=n_eval)
-        ev = int(n_eval.sum().item())
-        per_pose.append((c.n_selected, c.n_gaussians, c.n_pairs, ev))
     pose = lambda i: (rank + i * ws) % n
-
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 126 MB L2
-    for i in range(args.warmup):
-        flush.zero_()
-        rd.enqueue(cams[pose(i)])
-    torch.cuda.synchronize()
+
+    # the learned proposal (trained on its own poses of the same scene, judged on held-out)
+    train_cams = synth.proposal_poses(cams, 200, seed=2)
+    test_cams = synth.proposal_poses(cams, 60, seed=3)
+    full_rd = Renderer(sc, mlp, W, H, sel_cap=2_000_000, pair_cap=40_000_000)
+    net, p_star, pinfo = _train_proposal(rd, train_cams, test_cams, full_rd)
+    del full_rd
+    torch.cuda.empty_cache()
+    gate = (net.w, p_star)
+
+    # plain FP32 form
+    rd.precision = "fp32"
+    work_plain = _per_pose(rd, cams)
     if ws > 1:
         dist.barrier()
-    timers = {}
-    steps = []
-    with ClockSampler(local) as clk:
-        torch.cuda.synchronize()
-        for i in range(args.steps):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            rd.enqueue(cams[pose(args.warmup + i)], timers=timers)
-            e1.record()
-            steps.append((e0, e1))
-        torch.cuda.synchronize()
+    t_plain, stages_plain, _ = _time_form(rd, cams, pose, args.steps, args.warmup, None, flush,
+                                          local)
+    # BF16 decode + learned gate: the measured form
+    rd.precision = "bf16"
+    work = _per_pose(rd, cams, gate)
     if ws > 1:
         dist.barrier()
-    step_ms = [a.elapsed_time(b) for a, b in steps]
-    total_s = sum(step_ms) / 1e3
-    stage_ms = {k: [a.elapsed_time(b) for a, b in v] for k, v in timers.items()}
-    c = rd.counts()
-    assert c.overflow == 0, "buffers overflowed during the timed steps"
-    t_max = total_s
+    total_s, mean_ms, clocks = _time_form(rd, cams, pose, args.steps, args.warmup, gate, flush,
+                                          local)
     if ws > 1:
-        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+        dist.barrier()
+    t_max, tp_max = total_s, t_plain
+    if ws > 1:
+        t = torch.tensor([total_s, t_plain], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+        t_max, tp_max = float(t[0].item()), float(t[1].item())
     fps = ws * args.steps / t_max
+    fps_plain = ws * args.steps / tp_max
 
     # end-to-end through the public call: render + image to pinned host memory, per step
     host = torch.empty(3, H, W, dtype=torch.float32, pin_memory=True)
@@ -289,7 +363,7 @@ def run_gpu(args):
         dist.barrier()
     t0 = time.perf_counter()
     for i in range(n_e2e):
-        rd.render_to_host(cams[pose(i)], host)
+        rd.render_to_host(cams[pose(i)], host, gate=gate)
     e2e_s = time.perf_counter() - t0
     if ws > 1:
         t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
@@ -298,22 +372,22 @@ def run_gpu(args):
     e2e_fps = ws * n_e2e / e2e_s
 
     if rank != 0:
-        dist.destroy_process_group() if ws > 1 else None
+        if ws > 1:
+            dist.destroy_process_group()
         return 0
 
-    # roofline of the dominant stage, from the timed steps
     peaks, src = _peaks()
-    clocks = clk.summary()
-    timed_poses = [pose(args.warmup + i) for i in range(args.steps)]
-    mean_ms = {k: float(np.mean(v)) for k, v in stage_ms.items()}
+    timed = [pose(args.warmup + i) for i in range(args.steps)]
     dominant = max(mean_ms, key=mean_ms.get)
-    evals = float(np.mean([per_pose[p][3] for p in timed_poses]))
+    evals = float(np.mean([work[p][3] for p in timed]))
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12          # Tops/s
     stages = {}
     for k, v in mean_ms.items():
-        b = float(np.mean([stage_bytes(sc.N, per_pose[p][0], per_pose[p][1], per_pose[p][2],
-                                       rd.gx * rd.gy, W * H)[k] for p in timed_poses]))
+        if k == "proposal_gate":
+            continue
+        b = float(np.mean([stage_bytes(sc.N, work[p][0], work[p][1], work[p][2],
+                                       rd.gx * rd.gy, W * H)[k] for p in timed]))
         stages[k] = {"ms": v, "algorithmic_GB_per_s": b / (v * 1e-3) / 1e9,
                      "hbm_frac": b / (v * 1e-3) / 1e9 / peaks["hbm_gbs"]}
     if dominant == "blend_fwd":
@@ -328,19 +402,27 @@ def run_gpu(args):
         roof = {"kernel": dominant, "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"], "traffic": None,
                 "peak_source": f"{src} hbm_gbs"}
-
+    mean = lambda w, i: float(np.mean([w[p][i] for p in timed]))
     line = {
         "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "anchors": sc.N, "levels": sc.NL,
-                   "resolution": f"{W}x{H}", "poses": n, "parallelism": f"replicas x{ws}",
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16 decode GEMMs, f32 accumulate/blend",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC.replace("FP32 decode", "BF16 decode + learned gate"),
+                   "anchors": sc.N, "levels": sc.NL, "resolution": f"{W}x{H}", "poses": n,
+                   "parallelism": f"replicas x{ws}",
                    "l2": "256 MB buffer written between timed steps (L2 is 126 MB)",
-                   "mean_selected_anchors": float(np.mean([per_pose[p][0] for p in timed_poses])),
-                   "mean_gaussians": float(np.mean([per_pose[p][1] for p in timed_poses])),
-                   "mean_pairs": float(np.mean([per_pose[p][2] for p in timed_poses])),
-                   "mean_evaluations": evals},
+                   "mean_selected_anchors": mean(work, 0), "mean_gaussians": mean(work, 1),
+                   "mean_pairs": mean(work, 2), "mean_evaluations": evals},
+        "plain_fp32": {"value": fps_plain, "unit": "frames/s",
+                       "ms_per_step": 1e3 * t_plain / args.steps,
+                       "stages_ms": {k: round(v, 5) for k, v in stages_plain.items()},
+                       "mean_selected_anchors": mean(work_plain, 0),
+                       "mean_pairs": mean(work_plain, 2),
+                       "mean_evaluations": mean(work_plain, 3)},
+        "speedup_vs_plain_fp32": fps / fps_plain,
+        "proposal": pinfo,
         "roofline": roof,
         "stages_ms": {k: round(v, 5) for k, v in mean_ms.items()},
         "stages": stages,
@@ -358,6 +440,23 @@ def run_gpu(args):
     return 0
 
 
+def run_profile(args):
+    """Renders warmup + steps frames of the workload (BF16 decode, no gate) and exits: the
+    small case that the ncu captures under profiles/ are taken on."""
+    import torch
+    from paper_2403_17898_gb300 import build as _b
+    _b.build()
+    from paper_2403_17898_gb300.render import Renderer
+    sc, mlp, cams = _workload()
+    rd = Renderer(sc, mlp, cams[0].W, cams[0].H, sel_cap=200_000, pair_cap=4_000_000,
+                  precision=args.precision)
+    for i in range(args.warmup + args.steps):
+        rd.render(cams[(37 * i + 60) % len(cams)])
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_frames": args.warmup + args.steps, **rd.counts().__dict__}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -365,7 +464,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="render a few frames only (the case profiled with ncu)")
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
     args = ap.parse_args()
+    if args.profile:
+        return run_profile(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -110,13 +110,15 @@ typedef struct ogs_gaussians {
 } ogs_gaussians;
 
 /* Screen-space record of one Gaussian (48 bytes, 16-byte aligned), written by
- * ogs_project_bin:  {u, v, conic_a, conic_b}, {conic_c, opacity, r, g}, {b, depth, radius, 0}.
- * The 2D falloff at pixel offset (dx, dy) = (u - px, v - py) is
- * exp(-0.5 (a dx^2 + c dy^2) - b dx dy). */
+ * ogs_project_bin:  {u, v, conic_a, conic_b}, {conic_c, opacity, r, g},
+ * {b, depth, radius, p_skip}.  The 2D falloff at pixel offset (dx, dy) = (u - px, v - py) is
+ * G = exp(power), power = -0.5 (a dx^2 + c dy^2) - b dx dy; p_skip = -ln(255 opacity), so
+ * alpha = opacity G < 1/255 exactly when power < p_skip (the blend tests the exponent before
+ * evaluating exp; forward and backward use the same test). */
 typedef struct ogs_rec2d {
     float u, v, ca, cb;
     float cc, o, cr, cg;
-    float cbl, depth, radius, pad;
+    float cbl, depth, radius, p_skip;
 } ogs_rec2d;
 
 /* ---------------------------------------------------------------------------------------
@@ -290,6 +292,18 @@ ogs_status ogs_loss_l1(const float* img, const float* target, int64_t n, float* 
                        float* loss, void* stream);
 
 /* ---------------------------------------------------------------------------------------
+ * ogs_loss_l1_ssim — photometric loss of Sec. 5.1.5: (1 - lambda) L1 + lambda (1 - SSIM)
+ * (lambda = 0.2 in the paper), SSIM with an 11x11 Gaussian window (sigma 1.5, zero padded),
+ * C1 = 0.01^2, C2 = 0.03^2, averaged over the C x H x W values.  dimg (written) is the
+ * gradient w.r.t. img; *loss += the loss (device float, may be NULL).
+ *   scratch: ogs_loss_l1_ssim_scratch_bytes(C, H, W) bytes, 16-byte aligned.
+ * ------------------------------------------------------------------------------------- */
+size_t ogs_loss_l1_ssim_scratch_bytes(int32_t C, int32_t H, int32_t W);
+ogs_status ogs_loss_l1_ssim(const float* img, const float* target, int32_t C, int32_t H,
+                            int32_t W, float lambda, float* dimg, float* loss, void* scratch,
+                            size_t scratch_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------
  * ogs_adam — one Adam step over n parameters (step >= 1 is the 1-based step count used for
  * bias correction):  m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
  * p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).  zero_grad != 0 clears g.
@@ -304,7 +318,7 @@ ogs_status ogs_adam(float* param, float* grad, float* m, float* v, int64_t n, fl
  * device heap and offers no allocator, or a real-time frame loop that must not call
  * cudaMalloc/cudaFree because they synchronise the device).  The paper has no counterpart:
  * this is a deployment variant of the sort.
- *   Scratch is a fixed array inside the library image (about 8.3 MB), reserved on every GPU
+ *   Scratch is a fixed array inside the library image (about 9.4 MB), reserved on every GPU
  *   that loads the library until the process exits; no allocation of any kind is made.
  *   n_cap must be <= ogs_radix_sort_pairs_noalloc_max_items() (2^20); larger requests return
  *   OGS_ERR_CAPACITY and enqueue nothing.
@@ -322,8 +336,9 @@ ogs_status ogs_radix_sort_pairs_noalloc(uint32_t* keys, uint32_t* vals, const ui
 
 /* ---------------------------------------------------------------------------------------
  * Learned anchor-visibility proposal (not in the paper: a gate in front of decoding).  A
- * 3-layer MLP, input x = [f_v (32), L/(NL-1), unit direction camera->anchor (3), ln(d/d_max)]
- * (37), hidden 64 ReLU, 64 ReLU, output keep probability p = sigmoid(w3 . h2 + b3).
+ * 3-layer MLP, input x = [f_v (32), L/(NL-1), unit viewing direction in the camera frame
+ * R (x_v - campos)/d (3), ln(d/d_max)] (37), hidden 64 ReLU, 64 ReLU, output keep probability
+ * p = sigmoid(w3 . h2 + b3).
  *   w1 f32[64][37], b1 f32[64], w2 f32[64][64], b2 f32[64], w3 f32[64], b3 f32[1]
  * ------------------------------------------------------------------------------------- */
 typedef struct ogs_proposal {

@@ -314,13 +314,14 @@ def adam(param, grad, m, v, lr, beta1, beta2, eps, step):
 # ----------------------------------------------------------------------------------------
 
 def proposal_inputs(pos, level, feat, NL, sel_idx, cam):
-    """Per selected anchor: [f_v, L/(NL-1), unit direction camera->anchor, ln(d/d_max)]."""
+    """Per selected anchor: [f_v, L/(NL-1), unit viewing direction in the camera frame
+    R (x - c)/|x - c|, ln(d/d_max)]."""
     c = cam_array(cam)
-    campos, d_max = c[9:12], c[19]
+    R, campos, d_max = c[0:9].reshape(3, 3), c[9:12], c[19]
     p = _d(pos)[sel_idx] - campos
     d = np.linalg.norm(p, axis=1, keepdims=True)
     lev = np.asarray(level, np.float64)[sel_idx][:, None] / max(NL - 1, 1)
-    return np.concatenate([_d(feat)[sel_idx], lev, p / d, np.log(d / d_max)], 1)
+    return np.concatenate([_d(feat)[sel_idx], lev, (p @ R.T) / d, np.log(d / d_max)], 1)
 
 
 def proposal_forward(net, X):
@@ -355,3 +356,66 @@ def proposal_bce_grad(net, X, y):
     dw1 = dh1.T @ X
     db1 = dh1.sum(0)
     return loss, dict(w1=dw1, b1=db1, w2=dw2, b2=db2, w3=dw3, b3=db3)
+
+
+# ----------------------------------------------------------------------------------------
+# SSIM term of the photometric loss (Sec. 5.1.5: 0.8 L1 + 0.2 D-SSIM)
+# ----------------------------------------------------------------------------------------
+
+SSIM_C1 = 0.01 ** 2
+SSIM_C2 = 0.03 ** 2
+
+
+def gaussian_window(size=11, sigma=1.5):
+    """Normalised 1D Gaussian window; the 2D window is its outer product."""
+    x = np.arange(size) - size // 2
+    g = np.exp(-x * x / (2.0 * sigma * sigma))
+    return g / g.sum()
+
+
+def _blur(img, win):
+    """Separable 2D correlation with zero padding ('same' size), per channel."""
+    r = len(win) // 2
+    out = np.zeros_like(img)
+    tmp = np.zeros_like(img)
+    H, W = img.shape[-2:]
+    for i, w in enumerate(win):
+        o = i - r
+        # horizontal: tmp[:, y, x] += w * img[:, y, x + o]
+        xs = slice(max(0, -o), min(W, W - o))
+        xd = slice(max(0, o), min(W, W + o))
+        tmp[..., :, xs] += w * img[..., :, xd]
+    for i, w in enumerate(win):
+        o = i - r
+        ys = slice(max(0, -o), min(H, H - o))
+        yd = slice(max(0, o), min(H, H + o))
+        out[..., ys, :] += w * tmp[..., yd, :]
+    return out
+
+
+def ssim(x, y, win=None):
+    """Mean SSIM over channels and pixels (Wang et al. 2004 form, Gaussian window, zero padded)
+    and dSSIM/dx.  Pinned by SSIM(x, x) = 1, the constant-image closed form and finite
+    differences (tests/test_oracle_ssim)."""
+    win = gaussian_window() if win is None else win
+    x, y = _d(x), _d(y)
+    mx, my = _blur(x, win), _blur(y, win)
+    exx, eyy, exy = _blur(x * x, win), _blur(y * y, win), _blur(x * y, win)
+    sx, sy, sxy = exx - mx * mx, eyy - my * my, exy - mx * my
+    A1, A2 = 2 * mx * my + SSIM_C1, 2 * sxy + SSIM_C2
+    B1, B2 = mx * mx + my * my + SSIM_C1, sx + sy + SSIM_C2
+    S = A1 * A2 / (B1 * B2)
+    n = S.size
+    dS = 1.0 / n                       # d mean(S) / d S_p
+    g1 = dS * S * (2 * my / A1 - 2 * my / A2 - 2 * mx / B1 + 2 * mx / B2)
+    g2 = dS * S * (-1.0 / B2)
+    g3 = dS * S * (2.0 / A2)
+    grad = _blur(g1, win) + 2 * x * _blur(g2, win) + y * _blur(g3, win)
+    return float(S.mean()), grad
+
+
+def photometric_loss(img, target, lam=0.2):
+    """(1 - lam) L1 + lam (1 - SSIM) and its gradient w.r.t. img."""
+    l1, g1 = l1_loss(img, target)
+    s, gs = ssim(img, target)
+    return (1 - lam) * l1 + lam * (1 - s), (1 - lam) * g1 - lam * gs

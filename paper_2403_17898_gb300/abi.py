@@ -81,6 +81,8 @@ _SIGS = {
     "ogs_decode_bwd": (C.c_int, [_P, _P, _P, _P, _I64, C.POINTER(MLP), C.POINTER(Camera), _P, _P,
                                  _P, _P, _P, _P, _P, _P, _P, _P, C.POINTER(MLP), _P, _SZ, _P]),
     "ogs_loss_l1": (C.c_int, [_P, _P, _I64, _P, _P, _P]),
+    "ogs_loss_l1_ssim_scratch_bytes": (_SZ, [_I32, _I32, _I32]),
+    "ogs_loss_l1_ssim": (C.c_int, [_P, _P, _I32, _I32, _I32, C.c_float, _P, _P, _P, _SZ, _P]),
     "ogs_adam": (C.c_int, [_P, _P, _P, _P, _I64, C.c_float, C.c_float, C.c_float, C.c_float,
                            _I32, _I32, _P]),
     "ogs_radix_sort_pairs_noalloc_max_items": (_I64, []),
@@ -283,6 +285,17 @@ def decode_bwd(pos, feat, offs, lv, N, mlp, cam, sel_idx, sel_w, counts, dmeans,
 def loss_l1(img, target, n, dimg, loss=None, stream=None):
     _check(lib().ogs_loss_l1(_ptr(img), _ptr(target), int(n), _ptr(dimg), _ptr(loss),
                              _stream(stream)), "ogs_loss_l1")
+
+
+def loss_l1_ssim_scratch_bytes(C, H, W):
+    return int(lib().ogs_loss_l1_ssim_scratch_bytes(int(C), int(H), int(W)))
+
+
+def loss_l1_ssim(img, target, lam, dimg, loss, scratch, stream=None):
+    C, H, W = img.shape
+    _check(lib().ogs_loss_l1_ssim(_ptr(img), _ptr(target), int(C), int(H), int(W), float(lam),
+                                  _ptr(dimg), _ptr(loss), _ptr(scratch), scratch.numel(),
+                                  _stream(stream)), "ogs_loss_l1_ssim")
 
 
 def adam(param, grad, m, v, n, lr, beta1, beta2, eps, step, zero_grad=True, stream=None):

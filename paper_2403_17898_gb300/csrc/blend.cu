@@ -21,6 +21,7 @@ __global__ void __launch_bounds__(kBlendThreads) blend_fwd_kernel(
     __shared__ float4 s_a[kBlendThreads];   // u, v, conic a, conic b
     __shared__ float4 s_b[kBlendThreads];   // conic c, opacity, r, g
     __shared__ float s_c[kBlendThreads];    // b
+    __shared__ float s_p[kBlendThreads];    // exponent below which alpha < 1/255
     __shared__ uint32_t s_anchor[kMaxC ? kBlendThreads : 1];
     const int tile = blockIdx.x;
     const int tx = tile % gx, ty = tile / gx;
@@ -40,7 +41,9 @@ __global__ void __launch_bounds__(kBlendThreads) blend_fwd_kernel(
             const uint32_t g = pair_gauss[range.x + e];
             s_a[threadIdx.x] = rec[3 * (size_t)g];
             s_b[threadIdx.x] = rec[3 * (size_t)g + 1];
-            s_c[threadIdx.x] = rec[3 * (size_t)g + 2].x;
+            const float4 C = rec[3 * (size_t)g + 2];
+            s_c[threadIdx.x] = C.x;
+            s_p[threadIdx.x] = C.w;
             if (kMaxC) s_anchor[threadIdx.x] = sel_idx[g / (uint32_t)k];
         }
         __syncthreads();
@@ -52,9 +55,8 @@ __global__ void __launch_bounds__(kBlendThreads) blend_fwd_kernel(
                 const float dx = A.x - fx, dy = A.y - fy;
                 const float4 B = s_b[j];
                 const float power = -0.5f * (A.z * dx * dx + B.x * dy * dy) - A.w * dx * dy;
-                if (power > 0.0f) continue;
+                if (!(power <= 0.0f && power >= s_p[j])) continue;   // power > 0 or alpha < 1/255
                 const float alpha = fminf(0.99f, B.y * __expf(power));
-                if (alpha < 1.0f / 255.0f) continue;
                 const float Tn = T * (1.0f - alpha);
                 if (Tn < 1e-4f) { done = true; continue; }
                 const float wgt = alpha * T;
@@ -74,8 +76,8 @@ __global__ void __launch_bounds__(kBlendThreads) blend_fwd_kernel(
                     const float dx = A.x - fx, dy = A.y - fy;
                     const float4 B = s_b[j];
                     const float power = -0.5f * (A.z * dx * dx + B.x * dy * dy) - A.w * dx * dy;
-                    const float alpha = power > 0.0f ? 0.0f : fminf(0.99f, B.y * __expf(power));
-                    if (alpha >= 1.0f / 255.0f) {
+                    if (power <= 0.0f && power >= s_p[j]) {
+                        const float alpha = fminf(0.99f, B.y * __expf(power));
                         const float Tn = T * (1.0f - alpha);
                         if (Tn < 1e-4f) {
                             done = true;

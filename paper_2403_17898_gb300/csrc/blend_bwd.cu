@@ -28,6 +28,7 @@ __global__ void __launch_bounds__(kBwdThreads) blend_bwd_kernel(
     __shared__ float4 s_a[kBwdThreads];
     __shared__ float4 s_b[kBwdThreads];
     __shared__ float s_c[kBwdThreads];
+    __shared__ float s_p[kBwdThreads];
     __shared__ uint32_t s_g[kBwdThreads];
     __shared__ int s_maxlast;
     const int tile = blockIdx.x;
@@ -61,7 +62,9 @@ __global__ void __launch_bounds__(kBwdThreads) blend_bwd_kernel(
             s_g[threadIdx.x] = g;
             s_a[threadIdx.x] = rec[3 * (size_t)g];
             s_b[threadIdx.x] = rec[3 * (size_t)g + 1];
-            s_c[threadIdx.x] = rec[3 * (size_t)g + 2].x;
+            const float4 C = rec[3 * (size_t)g + 2];
+            s_c[threadIdx.x] = C.x;
+            s_p[threadIdx.x] = C.w;
         }
         __syncthreads();
         for (int j = top - lo - 1; j >= 0; --j) {
@@ -74,11 +77,12 @@ __global__ void __launch_bounds__(kBwdThreads) blend_bwd_kernel(
                 const float4 B = s_b[j];
                 const float dx = A.x - fx, dy = A.y - fy;
                 const float power = -0.5f * (A.z * dx * dx + B.x * dy * dy) - A.w * dx * dy;
-                if (power <= 0.0f) {
+                // the forward's skip test, bit for bit: power > 0 or alpha < 1/255
+                if (power <= 0.0f && power >= s_p[j]) {
                     const float G = __expf(power);
                     const float raw = B.y * G;
                     const float alpha = fminf(0.99f, raw);
-                    if (alpha >= 1.0f / 255.0f) {
+                    {
                         act = true;
                         T = T / (1.0f - alpha);               // T_i, before this Gaussian
                         const float cb = s_c[j];

@@ -98,7 +98,9 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(ProjArgs a) {
                         const float id = 1.0f / det;
                         r0 = make_float4(u, v, cc * id, -cb * id);
                         r1 = make_float4(ca * id, o, a.g.colors[3 * gi], a.g.colors[3 * gi + 1]);
-                        r2 = make_float4(a.g.colors[3 * gi + 2], pz, r, 0.f);
+                        // alpha = o G < 1/255  <=>  power < -ln(255 o): the blend tests the
+                        // exponent against this bound before evaluating exp
+                        r2 = make_float4(a.g.colors[3 * gi + 2], pz, r, -logf(255.0f * o));
                         dkey = __float_as_uint(pz);
                         ntiles = (uint32_t)((tx1 - tx0) * (ty1 - ty0));
                         rc = make_uint2((uint32_t)tx0 | ((uint32_t)ty0 << 16),

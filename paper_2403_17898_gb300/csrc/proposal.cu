@@ -1,7 +1,7 @@
 // Learned anchor-visibility proposal: a 3-layer MLP (37 -> 64 -> 64 -> 1, ReLU, ReLU,
-// sigmoid) scores every anchor kept by the LOD rule from [f_v, L/(NL-1), unit direction
-// camera->anchor, ln(d/d_max)] and drops those whose keep probability is below p*, before any
-// Gaussian is decoded.  Training labels are the renderer's own per-anchor maximum
+// sigmoid) scores every anchor kept by the LOD rule from [f_v, L/(NL-1), unit viewing
+// direction in the camera frame, ln(d/d_max)] and drops those whose keep probability is below
+// p*, before any Gaussian is decoded.  Training labels are the renderer's own per-anchor maximum
 // contribution (T * alpha) from ogs_blend_fwd.
 //
 // gate:  score pass (thread per selected anchor, weights in shared memory, outer-product
@@ -69,7 +69,10 @@ __device__ __forceinline__ void prop_input(const PropArgs& a, uint32_t j, float 
                 dz = a.pos[3 * (size_t)j + 2] - c.c[2];
     const float d = sqrtf(dx * dx + dy * dy + dz * dz);
     x[32] = (float)a.level[j] / (float)max(a.NL - 1, 1);
-    x[33] = dx / d; x[34] = dy / d; x[35] = dz / d;
+    // viewing direction in the camera frame
+    x[33] = (c.R[0] * dx + c.R[1] * dy + c.R[2] * dz) / d;
+    x[34] = (c.R[3] * dx + c.R[4] * dy + c.R[5] * dz) / d;
+    x[35] = (c.R[6] * dx + c.R[7] * dy + c.R[8] * dz) / d;
     x[36] = logf(d / c.d_max);
     x[37] = x[38] = x[39] = 0.f;
 }

@@ -11,7 +11,7 @@ namespace ogs {
 namespace {
 
 constexpr int kSelThreads = 256;
-constexpr int kSelItems = 16;
+constexpr int kSelItems = 4;
 constexpr int kSelChunk = kSelThreads * kSelItems;   // anchors per block
 
 struct SelArgs {

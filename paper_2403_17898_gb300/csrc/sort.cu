@@ -24,8 +24,8 @@ namespace {
 
 constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
-constexpr int kRsItems = 16;
-constexpr int kRsTile = kRsThreads * kRsItems;   // 4096 items per block
+constexpr int kRsItems = 4;
+constexpr int kRsTile = kRsThreads * kRsItems;   // 1024 items per block
 constexpr int kRsBins = 256;
 
 __device__ __forceinline__ uint32_t count_of(const uint32_t* n_dev, int64_t n_cap) {
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kRsThreads) rs_downsweep(
     const unsigned lane = lane_id();
     const int64_t wbase = base + (int64_t)w * (kRsItems * 32);
     uint32_t key[kRsItems], val[kRsItems], rank[kRsItems];
-    // warp-striped: warp w owns a contiguous run of 512 items, lane-interleaved per step, so
+    // warp-striped: warp w owns a contiguous run of 32*kRsItems items, lane-interleaved per step, so
     // (step, lane) order equals input order and ranks come out stable
 #pragma unroll
     for (int it = 0; it < kRsItems; ++it) {
@@ -249,7 +249,7 @@ bool radix_sort(uint32_t* keys, uint32_t* vals, const uint32_t* n_dev, int64_t n
 // ---------------------------------------------------------------------------------------
 
 constexpr int kEmThreads = 256;
-constexpr int kEmItems = 16;
+constexpr int kEmItems = 4;
 constexpr int kEmTile = kEmThreads * kEmItems;
 
 __global__ void iota_keys(const uint32_t* __restrict__ dkey, uint32_t* __restrict__ k,

@@ -185,8 +185,10 @@ class Trainer(Renderer):
 
     PARAMS = ("feat", "offs", "lv")
 
-    def __init__(self, scene, mlp, W, H, lr=1e-3, betas=(0.9, 0.999), eps=1e-15, **kw):
+    def __init__(self, scene, mlp, W, H, lr=1e-3, betas=(0.9, 0.999), eps=1e-15, ssim_lambda=0.0,
+                 **kw):
         super().__init__(scene, mlp, W, H, **kw)
+        self.ssim_lambda = float(ssim_lambda)   # 0.2 gives the 0.8 L1 + 0.2 D-SSIM loss
         self.lr, self.betas, self.eps = lr, betas, eps
         self.step_count = 0
         dev = "cuda"
@@ -202,6 +204,10 @@ class Trainer(Renderer):
         self.loss = torch.zeros(1, device=dev)
         self.db_scratch = torch.empty(abi.decode_bwd_scratch_bytes(), dtype=torch.uint8,
                                       device=dev)
+        self.loss_scratch = None
+        if self.ssim_lambda > 0:
+            self.loss_scratch = torch.empty(abi.loss_l1_ssim_scratch_bytes(3, self.H, self.W),
+                                            dtype=torch.uint8, device=dev)
         self._alloc_grad()
 
     def _alloc(self):
@@ -222,7 +228,11 @@ class Trainer(Renderer):
         training mode with ``cam``); gradients accumulate."""
         c = abi.camera(cam)
         st = stream if stream is not None else torch.cuda.current_stream()
-        abi.loss_l1(self.img, target, self.img.numel(), self.dimg, self.loss, st)
+        if self.ssim_lambda > 0:
+            abi.loss_l1_ssim(self.img, target, self.ssim_lambda, self.dimg, self.loss,
+                             self.loss_scratch, st)
+        else:
+            abi.loss_l1(self.img, target, self.img.numel(), self.dimg, self.loss, st)
         self.drec.zero_()
         abi.blend_bwd(self.rec, self.pair_gauss, self.tile_range, self.W, self.H, bg, self.T,
                       self.n_last, self.dimg, self.drec, st)
@@ -248,12 +258,12 @@ class Trainer(Renderer):
             abi.adam(p, g, self.adam_m[n], self.adam_v[n], p.numel(), self.lr, b1, b2, self.eps,
                      self.step_count, True, stream)
 
-    def train_step(self, cams, targets, bg=(0.0, 0.0, 0.0), update=True):
+    def train_step(self, cams, targets, bg=(0.0, 0.0, 0.0), update=True, timers=None):
         """Forward + backward over the views, then (optionally) the Adam update; returns
-        nothing (the summed mean-L1 of the views is left in ``self.loss``)."""
+        nothing (the summed per-view loss is left in ``self.loss``)."""
         self.loss.zero_()
         for cam, tgt in zip(cams, targets):
-            self.enqueue(cam, infer=False, bg=bg)
+            self.enqueue(cam, infer=False, bg=bg, timers=timers)
             self.backward_view(cam, tgt, bg)
         if update:
             self.optimizer_step()

@@ -24,7 +24,7 @@ import numpy as np
 __all__ = [
     "Scene", "DecoderMLP", "Camera", "ProposalMLP",
     "cube_scene", "city_scene", "decoder_mlp", "proposal_mlp",
-    "look_at_camera", "zoom_out_path", "trajectory_d_max",
+    "look_at_camera", "zoom_out_path", "trajectory_d_max", "proposal_poses",
     "random_gaussians", "random_records", "random_rects_depths", "random_sort_keys",
     "CONFIGS",
 ]
@@ -493,6 +493,14 @@ def _cfg2():
 def _cfg3():
     """2M anchors, 8 levels, 2 km city grid, 120-pose zoom-out 10 m -> 2 km, 1920x1080."""
     return _city_cfg(2_000_000, 8, 2000.0, 4.0, 120, 10.0, 2000.0, 1920, 1080)
+
+
+def proposal_poses(main_cams, n, seed, h0=10.0, h1=2000.0, yaw_jitter=40.0):
+    """Zoom-out poses with random azimuth jitter for training / evaluating the anchor
+    visibility proposal; they share the LOD reference distance of the main path."""
+    c0 = main_cams[0]
+    return zoom_out_path(n, h0, h1, (0.0, 0.0, 0.0), c0.W, c0.H, yaw_jitter_deg=yaw_jitter,
+                         seed=seed, d_max=c0.d_max)
 
 
 def _cfg3_train_poses():

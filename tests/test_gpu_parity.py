@@ -269,6 +269,7 @@ def test_blend_matches_oracle(abi, torch):
     rec[:, 4], rec[:, 5] = r["conic"][:, 2], r["opac"]
     rec[:, 6:9] = r["colors"]
     rec[:, 9] = r["depth"]
+    rec[:, 11] = -np.log(255.0 * r["opac"].astype(np.float64))
     tr = np.stack([start[:-1], start[1:]], 1).astype(np.int32)
     img = torch.zeros(3, H, W, device="cuda")
     Tf = torch.zeros(H, W, device="cuda")

@@ -19,7 +19,9 @@ def test_inputs_layout():
     X = oracle.proposal_inputs(pos, np.array([2]), feat, 5, np.array([0]), cam)
     np.testing.assert_allclose(X[0, :32], np.arange(32))
     assert X[0, 32] == 0.5                               # level 2 of 5 -> 2/4
-    np.testing.assert_allclose(X[0, 33:36], [0.6, 0.0, 0.8])
+    # camera looks down +x with z up: right = -y, down = -z, forward = +x, so the anchor at
+    # (3, 0, 4) is seen at camera-frame direction (0, -4, 3) / 5
+    np.testing.assert_allclose(X[0, 33:36], [0.0, -0.8, 0.6], atol=1e-7)
     assert X[0, 36] == pytest.approx(math.log(5.0 / 40.0), rel=1e-12)
 
 
