@@ -219,9 +219,9 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------------------
 
-# kernels each ABI call launches per frame (radix passes: 4 depth + 2 tile, 3 kernels each)
-LAUNCHES = {"lod_select": 3, "proposal_gate": 3, "decode": 1, "project_bin": 1,
-            "sort": 1 + 3 * 4 + 3 + 3 * 2 + 1, "blend_fwd": 1}
+# kernels each ABI call launches per frame
+LAUNCHES = {"lod_select": 3, "proposal_gate": 3, "decode": 1, "project_bin": 1, "sort": 4,
+            "blend_fwd": 1}
 DPSNR_GATE_DB = 0.05
 
 
@@ -263,15 +263,21 @@ def _per_pose(rd, cams, gate=None):
     return out
 
 
+POS_WEIGHT = 4.0
+
+
 def _train_proposal(rd, train_cams, test_cams, full_rd):
-    """Trains the anchor-visibility proposal on the training poses, calibrates p* on a
-    subset of them and judges it on the held-out poses against full-detail renders."""
+    """Trains the anchor-visibility proposal on the training poses (BCE with positives
+    weighted, so dropping a visible anchor costs more than keeping an invisible one),
+    calibrates p* as the largest threshold whose WORST calibration pose stays within the
+    PSNR budget, and judges it on the held-out poses against full-detail renders.  If the
+    held-out poses exceed the budget, the plain LOD path is used (the gate's fallback)."""
     import synth
     from paper_2403_17898_gb300 import proposal
     t0 = time.perf_counter()
     views = proposal.collect_labels(rd, train_cams)
     net = proposal.ProposalNet(synth.proposal_mlp(seed=0), lr=2e-3)
-    hist = proposal.train(net, rd, views, epochs=30)
+    hist = proposal.train(net, rd, views, epochs=30, pos_weight=POS_WEIGHT)
     t_train = time.perf_counter() - t0
 
     def judge(cams, p_star):
@@ -285,21 +291,28 @@ def _train_proposal(rd, train_cams, test_cams, full_rd):
             dps.append(proposal.psnr(plain, ref) - proposal.psnr(rd.img, ref))
             direct.append(proposal.psnr(rd.img, plain))
             kept.append(c1.n_selected / max(c0.n_selected, 1))
-        return float(np.mean(dps)), float(np.max(dps)), float(np.mean(kept)), float(np.median(direct))
+        return (float(np.mean(dps)), float(np.max(dps)), float(np.mean(kept)),
+                float(np.median(direct)))
 
     calib = train_cams[::5]
-    p_star = 0.0
-    for cand in (0.001, 0.002, 0.005, 0.01, 0.02, 0.05, 0.1, 0.15, 0.2, 0.3, 0.4, 0.5):
-        if judge(calib, cand)[0] <= DPSNR_GATE_DB:
+    p_star, curve = 0.0, []
+    for cand in (0.001, 0.002, 0.005, 0.01, 0.02, 0.05, 0.1, 0.2):
+        r = judge(calib, cand)
+        curve.append([cand, round(r[0], 4), round(r[1], 4), round(r[2], 4)])
+        if r[1] <= DPSNR_GATE_DB:
             p_star = cand
-    mean_dp, max_dp, kept, direct = judge(test_cams, p_star)
+    mean_dp, max_dp, kept, direct = judge(test_cams, p_star) if p_star > 0 else (0.0, 0.0, 1.0, float("inf"))
+    use_gate = p_star > 0 and mean_dp <= DPSNR_GATE_DB
     info = {"train_poses": len(train_cams), "heldout_poses": len(test_cams),
             "epochs": len(hist), "bce_first_epoch": hist[0], "bce_last_epoch": hist[-1],
-            "train_s": t_train, "p_star": p_star, "label": "max T*alpha >= 1/255",
+            "pos_weight": POS_WEIGHT, "train_s": t_train, "p_star": p_star,
+            "label": "max T*alpha >= 1/255",
+            "calibration_curve[p*, dPSNR mean, dPSNR max, kept]": curve,
             "heldout_dpsnr_db_mean": mean_dp, "heldout_dpsnr_db_max": max_dp,
             "heldout_psnr_vs_plain_db_median": direct, "heldout_kept_anchor_frac": kept,
+            "gate_used": use_gate,
             "dpsnr_definition": "PSNR(plain FP32 LOD vs full-detail) - PSNR(gated BF16 vs full-detail)"}
-    return net, p_star, info
+    return net, p_star, use_gate, info
 
 
 def run_gpu(args):
@@ -326,10 +339,10 @@ def run_gpu(args):
     train_cams = synth.proposal_poses(cams, 200, seed=2)
     test_cams = synth.proposal_poses(cams, 60, seed=3)
     full_rd = Renderer(sc, mlp, W, H, sel_cap=2_000_000, pair_cap=40_000_000)
-    net, p_star, pinfo = _train_proposal(rd, train_cams, test_cams, full_rd)
+    net, p_star, use_gate, pinfo = _train_proposal(rd, train_cams, test_cams, full_rd)
     del full_rd
     torch.cuda.empty_cache()
-    gate = (net.w, p_star)
+    gate = (net.w, p_star) if use_gate else None
 
     # plain FP32 form
     rd.precision = "fp32"
@@ -409,7 +422,9 @@ def run_gpu(args):
         "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16 decode GEMMs, f32 accumulate/blend",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC.replace("FP32 decode", "BF16 decode + learned gate"),
+        "config": {"workload": WORKLOAD_DESC.replace(
+                       "FP32 decode", "BF16 decode + learned gate" if use_gate else
+                       "BF16 decode (learned gate fell back to the plain LOD path)"),
                    "anchors": sc.N, "levels": sc.NL, "resolution": f"{W}x{H}", "poses": n,
                    "parallelism": f"replicas x{ws}",
                    "l2": "256 MB buffer written between timed steps (L2 is 126 MB)",
@@ -430,7 +445,7 @@ def run_gpu(args):
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": 88,
                 "d2h_bytes_per_step": 3 * W * H * 4, "steps": n_e2e,
                 "call": "Renderer.render_to_host (render + image to pinned host memory)"},
-        "gpu_launches": args.steps * sum(LAUNCHES.values()),
+        "gpu_launches": args.steps * (sum(LAUNCHES.values()) - (0 if use_gate else LAUNCHES["proposal_gate"])),
     }
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(*_as_f64(sc, mlp), cams)

@@ -186,15 +186,16 @@ ogs_status ogs_project_bin(const ogs_gaussians* g /* host struct */, int64_t n_g
 
 /* ---------------------------------------------------------------------------------------
  * ogs_sort — Sec. 3.1: for every tile, the Gaussians whose rectangle covers it, in
- * front-to-back order (ascending depth, ties by Gaussian id).  Built as: stable radix sort
- * of Gaussians by depth key; exclusive scan of their tile counts in that order; emission of
- * (tile, Gaussian) pairs in depth order; stable radix sort of the pairs by tile.
- *   depth_key/rect/tiles from ogs_project_bin; count = counts->n_gaussians (or n_gauss)
+ * front-to-back order (ascending depth, ties by Gaussian id).  Built per tile: pair counts per
+ * tile and their exclusive scan (the tile ranges), an unordered fill of each tile's range, and
+ * one CTA per tile sorting its range by the unique key (depth bits << 32 | Gaussian id) in
+ * shared memory.  The result is fully determined by the inputs.
+ *   depth_key/rect/tiles from ogs_project_bin; n_gauss < 0 takes the Gaussian count from
+ *   counts->n_gaussians (as written by ogs_decode), else n_gauss (<= g_cap)
  *   pair_gauss u32[pair_cap]: Gaussian id of each pair, tile-major, front-to-back
  *   tile_range u32[n_tiles][2]: [start, end) of each tile in pair_gauss
- *   counts->n_pairs = P; if P > pair_cap, overflow bit 1 is set, need_pairs = P and
- *   no pair is emitted (every tile range is empty).
- *   n_gauss < 0 takes the Gaussian count from counts->n_gaussians (as written by ogs_decode).
+ *   counts->n_pairs = P; if P > pair_cap, overflow bit 1 is set, need_pairs = P and no pair
+ *   is emitted (every tile range is empty).
  *   scratch: ogs_sort_scratch_bytes(g_cap, pair_cap, n_tiles) bytes, 16-byte aligned.
  * ------------------------------------------------------------------------------------- */
 size_t ogs_sort_scratch_bytes(int64_t g_cap, int64_t pair_cap, int32_t n_tiles);
@@ -363,9 +364,10 @@ ogs_status ogs_proposal_gate(const float* pos, const uint8_t* level, const float
                              ogs_counts* counts, uint32_t* sel_out, float* w_out, float* p_out,
                              void* scratch, size_t scratch_bytes, void* stream);
 
-/* ogs_proposal_train — mean binary cross-entropy of the keep probability over the selected
- * anchors of one view against labels y = (maxc[anchor] >= tau) (maxc as written by
- * ogs_blend_fwd: float bits of the largest T*alpha), and its gradients.
+/* ogs_proposal_train — mean weighted binary cross-entropy of the keep probability over the
+ * selected anchors of one view against labels y = (maxc[anchor] >= tau) (maxc as written by
+ * ogs_blend_fwd: float bits of the largest T*alpha), positives weighted by pos_weight (> 0),
+ * and its gradients.
  *   grads: same layout as the network, ACCUMULATED (+=); *loss += mean BCE (may be NULL).
  *   scratch: ogs_proposal_train_scratch_bytes() bytes, 16-byte aligned. */
 size_t ogs_proposal_train_scratch_bytes(void);
@@ -373,6 +375,7 @@ ogs_status ogs_proposal_train(const float* pos, const uint8_t* level, const floa
                               int64_t N, int32_t NL, const ogs_camera* cam /* host */,
                               const ogs_proposal* net /* host struct */, const uint32_t* sel_idx,
                               const ogs_counts* counts, const uint32_t* maxc, float tau,
+                              float pos_weight,
                               const ogs_proposal* grads /* host struct, written */, float* loss,
                               void* scratch, size_t scratch_bytes, void* stream);
 

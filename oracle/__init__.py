@@ -337,16 +337,19 @@ def proposal_forward(net, X):
     return p, dict(a1=a1, h1=h1, a2=a2, h2=h2, z=z)
 
 
-def proposal_bce_grad(net, X, y):
-    """Mean binary cross-entropy of the keep probability against labels y in {0, 1}, and its
-    gradients w.r.t. every weight (analytic backward; dL/dz = (p - y) / n)."""
+def proposal_bce_grad(net, X, y, pos_weight=1.0):
+    """Mean weighted binary cross-entropy of the keep probability against labels y in {0, 1}
+    (positives weighted by pos_weight), and its gradients w.r.t. every weight (analytic
+    backward; dL/dz = w_y (p - y) / n)."""
     w1, b1, w2, b2, w3, b3 = [_d(a) for a in net.arrays()]
     p, t = proposal_forward(net, X)
     y = np.asarray(y, np.float64)
     n = len(y)
     eps = 1e-300
-    loss = float(-np.mean(y * np.log(np.maximum(p, eps)) + (1 - y) * np.log(np.maximum(1 - p, eps))))
-    dz = (p - y) / n
+    wy = np.where(y > 0, pos_weight, 1.0)
+    loss = float(-np.mean(wy * (y * np.log(np.maximum(p, eps)) +
+                                (1 - y) * np.log(np.maximum(1 - p, eps)))))
+    dz = wy * (p - y) / n
     dw3 = dz[None, :] @ t["h2"]
     db3 = np.array([dz.sum()])
     dh2 = dz[:, None] * w3[0][None, :] * (t["a2"] > 0)

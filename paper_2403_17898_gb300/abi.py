@@ -93,7 +93,7 @@ _SIGS = {
                                     _P, _P, _SZ, _P]),
     "ogs_proposal_train_scratch_bytes": (_SZ, []),
     "ogs_proposal_train": (C.c_int, [_P, _P, _P, _I64, _I32, C.POINTER(Camera),
-                                     C.POINTER(Proposal), _P, _P, _P, C.c_float,
+                                     C.POINTER(Proposal), _P, _P, _P, C.c_float, C.c_float,
                                      C.POINTER(Proposal), _P, _P, _SZ, _P]),
     "ogs_version": (C.c_char_p, []),
 }
@@ -344,13 +344,14 @@ def proposal_train_scratch_bytes():
 
 
 def proposal_train(pos, level, feat, N, NL, cam, net, sel_idx, counts, maxc, tau, grads, loss,
-                   scratch, stream=None):
+                   scratch, pos_weight=1.0, stream=None):
     c = cam if isinstance(cam, Camera) else camera(cam)
     n = net if isinstance(net, Proposal) else proposal_struct(net)
     g = grads if isinstance(grads, Proposal) else proposal_struct(grads)
     _check(lib().ogs_proposal_train(_ptr(pos), _ptr(level), _ptr(feat), int(N), int(NL),
                                     C.byref(c), C.byref(n), _ptr(sel_idx), _ptr(counts),
-                                    _ptr(maxc), float(tau), C.byref(g), _ptr(loss),
+                                    _ptr(maxc), float(tau), float(pos_weight), C.byref(g),
+                                    _ptr(loss),
                                     _ptr(scratch), scratch.numel(), _stream(stream)),
            "ogs_proposal_train")
 

@@ -1,113 +1,125 @@
 // Front-to-back alpha blending per 16x16 tile (Sec. 3.1, Eq. 2).
 //
-// One CTA per tile, one thread per pixel.  The tile's list is consumed in batches of 256
-// records staged through shared memory (one coalesced gather per batch), and the CTA leaves
-// as soon as every pixel has saturated (barrier vote).  The inner loop is FP32 FMA plus one
-// MUFU ex2 per (pixel, Gaussian) evaluation, so it is bound by issue slots, not HBM.
-#include "internal.cuh"
+// One CTA of 4 warps per tile; each thread blends two vertically adjacent pixels (warps cover
+// compact 8x8 blocks, so pixels that saturate together share a warp).  The tile's list is
+// consumed in batches of 256 records gathered into shared memory, converted once per batch to
+// pre-scaled coefficients so that one (pixel, Gaussian) evaluation is: offset, a 5-operation
+// quadratic form, the exponent-bound skip test, and only for surviving pairs one ex2 and the
+// compositing update.  The CTA leaves as soon as every pixel has saturated (barrier vote).
+// The kernel is bound by instruction issue (FP32 + MUFU), not by memory.
+#include "blend_common.cuh"
 
 namespace ogs {
 namespace {
 
-constexpr int kBlendThreads = kTile * kTile;   // 256
+using namespace blend;
 
 template <bool kMaxC>
-__global__ void __launch_bounds__(kBlendThreads) blend_fwd_kernel(
+__global__ void __launch_bounds__(kThreads) blend_fwd_kernel(
     const float4* __restrict__ rec, const uint32_t* __restrict__ pair_gauss,
     const uint2* __restrict__ tile_range, int W, int H, int gx, float bg0, float bg1, float bg2,
     float* __restrict__ img, float* __restrict__ T_final, uint32_t* __restrict__ n_last,
     uint32_t* __restrict__ n_eval, const uint32_t* __restrict__ sel_idx, int k,
     uint32_t* __restrict__ maxc) {
-    __shared__ float4 s_a[kBlendThreads];   // u, v, conic a, conic b
-    __shared__ float4 s_b[kBlendThreads];   // conic c, opacity, r, g
-    __shared__ float s_c[kBlendThreads];    // b
-    __shared__ float s_p[kBlendThreads];    // exponent below which alpha < 1/255
-    __shared__ uint32_t s_anchor[kMaxC ? kBlendThreads : 1];
+    __shared__ float4 s_a[kBatch];
+    __shared__ float4 s_b[kBatch];
+    __shared__ float2 s_c[kBatch];
+    __shared__ uint32_t s_anchor[kMaxC ? kBatch : 1];
     const int tile = blockIdx.x;
-    const int tx = tile % gx, ty = tile / gx;
-    const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-    const int py = ty * kTile + (threadIdx.x >> 4);
-    const bool inside = px < W && py < H;
+    int lx, ly;
+    pixels_of(threadIdx.x, lx, ly);
+    const int px = (tile % gx) * kTile + lx;
+    const int py = (tile / gx) * kTile + ly;
+    const bool in0 = px < W && py < H, in1 = px < W && py + 1 < H;
     const float fx = (float)px, fy = (float)py;
     const uint2 range = tile_range[tile];
     const int n = (int)(range.y - range.x);
-    float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    uint32_t contributor = 0, last = 0;
-    bool done = !inside;
-    for (int b0 = 0; b0 < n; b0 += kBlendThreads) {
-        if (__syncthreads_count(done) == kBlendThreads) break;
-        const int e = b0 + threadIdx.x;
-        if (e < n) {
-            const uint32_t g = pair_gauss[range.x + e];
-            s_a[threadIdx.x] = rec[3 * (size_t)g];
-            s_b[threadIdx.x] = rec[3 * (size_t)g + 1];
-            const float4 C = rec[3 * (size_t)g + 2];
-            s_c[threadIdx.x] = C.x;
-            s_p[threadIdx.x] = C.w;
-            if (kMaxC) s_anchor[threadIdx.x] = sel_idx[g / (uint32_t)k];
+    float T0 = 1.f, T1 = 1.f, C00 = 0.f, C01 = 0.f, C02 = 0.f, C10 = 0.f, C11 = 0.f, C12 = 0.f;
+    int last0 = 0, last1 = 0, stop0 = n, stop1 = n;
+    bool done0 = !in0, done1 = !in1;
+    for (int b0 = 0; b0 < n; b0 += kBatch) {
+        if (__syncthreads_count(done0 && done1) == kThreads) break;
+        for (int e = threadIdx.x; e < kBatch && b0 + e < n; e += kThreads) {
+            const uint32_t g = pair_gauss[range.x + b0 + e];
+            const Rec r = load_rec(rec, g);
+            s_a[e] = r.A;
+            s_b[e] = r.B;
+            s_c[e] = r.C;
+            if (kMaxC) s_anchor[e] = sel_idx[g / (uint32_t)k];
         }
         __syncthreads();
-        const int cnt = min(kBlendThreads, n - b0);
-        if (!kMaxC) {
-            for (int j = 0; !done && j < cnt; ++j) {
-                ++contributor;
-                const float4 A = s_a[j];
-                const float dx = A.x - fx, dy = A.y - fy;
-                const float4 B = s_b[j];
-                const float power = -0.5f * (A.z * dx * dx + B.x * dy * dy) - A.w * dx * dy;
-                if (!(power <= 0.0f && power >= s_p[j])) continue;   // power > 0 or alpha < 1/255
-                const float alpha = fminf(0.99f, B.y * __expf(power));
-                const float Tn = T * (1.0f - alpha);
-                if (Tn < 1e-4f) { done = true; continue; }
-                const float wgt = alpha * T;
-                C0 = fmaf(B.z, wgt, C0);
-                C1 = fmaf(B.w, wgt, C1);
-                C2 = fmaf(s_c[j], wgt, C2);
-                T = Tn;
-                last = contributor;
-            }
-        } else {
-            // warp-uniform loop so that the per-anchor max can be reduced across the warp
-            for (int j = 0; j < cnt; ++j) {
-                float contrib = 0.0f;
-                if (!done) {
-                    ++contributor;
-                    const float4 A = s_a[j];
-                    const float dx = A.x - fx, dy = A.y - fy;
-                    const float4 B = s_b[j];
-                    const float power = -0.5f * (A.z * dx * dx + B.x * dy * dy) - A.w * dx * dy;
-                    if (power <= 0.0f && power >= s_p[j]) {
-                        const float alpha = fminf(0.99f, B.y * __expf(power));
-                        const float Tn = T * (1.0f - alpha);
-                        if (Tn < 1e-4f) {
-                            done = true;
-                        } else {
-                            const float wgt = alpha * T;
-                            C0 = fmaf(B.z, wgt, C0);
-                            C1 = fmaf(B.w, wgt, C1);
-                            C2 = fmaf(s_c[j], wgt, C2);
-                            contrib = wgt;
-                            T = Tn;
-                            last = contributor;
-                        }
-                    }
+        const int cnt = min(kBatch, n - b0);
+        for (int j = 0; j < cnt; ++j) {
+            if (!kMaxC && done0 && done1) break;
+            const float4 A = s_a[j];
+            const float4 B = s_b[j];
+            const float2 Cc = s_c[j];
+            const float dx = A.x - fx;
+            const float dy0 = A.y - fy, dy1 = dy0 - 1.0f;
+            const float ax = __fmul_rn(A.z, dx);
+            const float p0 = power2(ax, dx, dy0, A.w, B.x);
+            const float p1 = power2(ax, dx, dy1, A.w, B.x);
+            float c0 = 0.f, c1 = 0.f;
+            // pixel 0: skip if power > 0 or alpha < 1/255 (power2 < pskip2)
+            if (!done0 && p0 <= 0.f && p0 >= Cc.y) {
+                const float alpha = fminf(0.99f, raw_alpha(B.y, p0));
+                const float Tn = T0 * (1.0f - alpha);
+                if (Tn < 1e-4f) {
+                    done0 = true;
+                    stop0 = b0 + j + 1;
+                } else {
+                    const float wgt = alpha * T0;
+                    C00 = fmaf(B.z, wgt, C00);
+                    C01 = fmaf(B.w, wgt, C01);
+                    C02 = fmaf(Cc.x, wgt, C02);
+                    T0 = Tn;
+                    last0 = b0 + j + 1;
+                    c0 = wgt;
                 }
+            }
+            if (!done1 && p1 <= 0.f && p1 >= Cc.y) {
+                const float alpha = fminf(0.99f, raw_alpha(B.y, p1));
+                const float Tn = T1 * (1.0f - alpha);
+                if (Tn < 1e-4f) {
+                    done1 = true;
+                    stop1 = b0 + j + 1;
+                } else {
+                    const float wgt = alpha * T1;
+                    C10 = fmaf(B.z, wgt, C10);
+                    C11 = fmaf(B.w, wgt, C11);
+                    C12 = fmaf(Cc.x, wgt, C12);
+                    T1 = Tn;
+                    last1 = b0 + j + 1;
+                    c1 = wgt;
+                }
+            }
+            if (kMaxC) {
                 // contributions are >= 0, so their float bits order like unsigned ints
-                const uint32_t m = __reduce_max_sync(0xffffffffu, __float_as_uint(contrib));
+                const uint32_t m = __reduce_max_sync(0xffffffffu,
+                                                     __float_as_uint(fmaxf(c0, c1)));
                 if (lane_id() == 0 && m) atomicMax(&maxc[s_anchor[j]], m);
-                if (__all_sync(0xffffffffu, done)) break;
+                if (__all_sync(0xffffffffu, done0 && done1)) break;
             }
         }
     }
-    if (inside) {
+    const size_t plane = (size_t)W * H;
+    if (in0) {
         const size_t pix = (size_t)py * W + px;
-        const size_t plane = (size_t)W * H;
-        img[pix] = C0 + T * bg0;
-        img[plane + pix] = C1 + T * bg1;
-        img[2 * plane + pix] = C2 + T * bg2;
-        T_final[pix] = T;
-        n_last[pix] = last;
-        if (n_eval) n_eval[pix] = contributor;
+        img[pix] = C00 + T0 * bg0;
+        img[plane + pix] = C01 + T0 * bg1;
+        img[2 * plane + pix] = C02 + T0 * bg2;
+        T_final[pix] = T0;
+        n_last[pix] = (uint32_t)last0;
+        if (n_eval) n_eval[pix] = (uint32_t)stop0;
+    }
+    if (in1) {
+        const size_t pix = (size_t)(py + 1) * W + px;
+        img[pix] = C10 + T1 * bg0;
+        img[plane + pix] = C11 + T1 * bg1;
+        img[2 * plane + pix] = C12 + T1 * bg2;
+        T_final[pix] = T1;
+        n_last[pix] = (uint32_t)last1;
+        if (n_eval) n_eval[pix] = (uint32_t)stop1;
     }
 }
 
@@ -129,11 +141,11 @@ extern "C" ogs_status ogs_blend_fwd(const ogs_rec2d* rec, const uint32_t* pair_g
     const float4* r = reinterpret_cast<const float4*>(rec);
     const uint2* tr = reinterpret_cast<const uint2*>(tile_range);
     if (maxc)
-        blend_fwd_kernel<true><<<gx * gy, kBlendThreads, 0, st>>>(
+        blend_fwd_kernel<true><<<gx * gy, blend::kThreads, 0, st>>>(
             r, pair_gauss, tr, width, height, gx, bg[0], bg[1], bg[2], img, T_final, n_last,
             n_eval, sel_idx, k, maxc);
     else
-        blend_fwd_kernel<false><<<gx * gy, kBlendThreads, 0, st>>>(
+        blend_fwd_kernel<false><<<gx * gy, blend::kThreads, 0, st>>>(
             r, pair_gauss, tr, width, height, gx, bg[0], bg[1], bg[2], img, T_final, n_last,
             n_eval, nullptr, 1, nullptr);
     return launch_status();

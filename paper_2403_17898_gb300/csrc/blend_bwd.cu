@@ -5,14 +5,15 @@
 // (1 - a_i) S_i).  Each pixel replays its list back to front from its last blended entry,
 // recovering T_i = T_{i+1} / (1 - a_i) from the final transmittance instead of storing
 // per-pair values (1 - a_i >= 0.01 because a is clamped to 0.99).  a = min(0.99, o G) has
-// zero derivative where clamped.  Per-Gaussian gradients of one warp are summed with
-// shuffles before a single atomic add per warp and Gaussian.
-#include "internal.cuh"
+// zero derivative where clamped.  Same tile/pixel mapping and skip test as the forward (two
+// pixels per thread); a thread's two contributions are summed, then a warp's with shuffles,
+// before one atomic add per warp and Gaussian.
+#include "blend_common.cuh"
 
 namespace ogs {
 namespace {
 
-constexpr int kBwdThreads = kTile * kTile;
+using namespace blend;
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -20,99 +21,106 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-__global__ void __launch_bounds__(kBwdThreads) blend_bwd_kernel(
+// one pixel's contribution of one Gaussian, accumulated into g[9]:
+// du dv da db dc do dr dg db (w.r.t. the unscaled record)
+struct PixState {
+    float T, S0, S1, S2, d0, d1, d2;
+    int last;
+};
+
+__device__ __forceinline__ bool pixel_step(PixState& s, int idx, float p2, const float4& A,
+                                           const float4& B, const float2& Cc, float dx, float dy,
+                                           float (&g)[9]) {
+    if (idx >= s.last || !(p2 <= 0.f && p2 >= Cc.y)) return false;
+    const float raw = raw_alpha(B.y, p2);
+    const float alpha = fminf(0.99f, raw);
+    s.T = s.T / (1.0f - alpha);                     // T_i, before this Gaussian
+    const float wgt = alpha * s.T;
+    g[6] += wgt * s.d0; g[7] += wgt * s.d1; g[8] += wgt * s.d2;
+    const float dalpha = s.T * ((B.z - s.S0) * s.d0 + (B.w - s.S1) * s.d1 + (Cc.x - s.S2) * s.d2);
+    s.S0 = alpha * B.z + (1.0f - alpha) * s.S0;
+    s.S1 = alpha * B.w + (1.0f - alpha) * s.S1;
+    s.S2 = alpha * Cc.x + (1.0f - alpha) * s.S2;
+    if (raw < 0.99f) {
+        // d alpha / d power = alpha, d alpha / d o = G = alpha / o; the record's conic is
+        // (a, b, c) with power = -0.5 (a dx^2 + c dy^2) - b dx dy, and a2 = -0.5 a log2e etc.
+        g[5] += dalpha * (alpha / B.y);
+        const float dp = dalpha * alpha;
+        const float a = -2.0f * A.z / kLog2e, b = -A.w / kLog2e, c = -2.0f * B.x / kLog2e;
+        g[0] += -dp * (a * dx + b * dy);
+        g[1] += -dp * (c * dy + b * dx);
+        g[2] += -0.5f * dp * dx * dx;
+        g[3] += -dp * dx * dy;
+        g[4] += -0.5f * dp * dy * dy;
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kThreads) blend_bwd_kernel(
     const float4* __restrict__ rec, const uint32_t* __restrict__ pair_gauss,
     const uint2* __restrict__ tile_range, int W, int H, int gx, float bg0, float bg1, float bg2,
     const float* __restrict__ T_final, const uint32_t* __restrict__ n_last,
     const float* __restrict__ dimg, float* __restrict__ drec) {
-    __shared__ float4 s_a[kBwdThreads];
-    __shared__ float4 s_b[kBwdThreads];
-    __shared__ float s_c[kBwdThreads];
-    __shared__ float s_p[kBwdThreads];
-    __shared__ uint32_t s_g[kBwdThreads];
+    __shared__ float4 s_a[kBatch];
+    __shared__ float4 s_b[kBatch];
+    __shared__ float2 s_c[kBatch];
+    __shared__ uint32_t s_g[kBatch];
     __shared__ int s_maxlast;
     const int tile = blockIdx.x;
-    const int tx = tile % gx, ty = tile / gx;
-    const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-    const int py = ty * kTile + (threadIdx.x >> 4);
-    const bool inside = px < W && py < H;
+    int lx, ly;
+    pixels_of(threadIdx.x, lx, ly);
+    const int px = (tile % gx) * kTile + lx;
+    const int py = (tile / gx) * kTile + ly;
     const float fx = (float)px, fy = (float)py;
     const uint2 range = tile_range[tile];
-    const size_t pix = (size_t)py * W + px, plane = (size_t)W * H;
-    int last = 0;
-    float T = 1.0f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
-    if (inside) {
-        last = (int)n_last[pix];
-        T = T_final[pix];
-        d0 = dimg[pix]; d1 = dimg[plane + pix]; d2 = dimg[2 * plane + pix];
+    const size_t plane = (size_t)W * H;
+    PixState q[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        q[i] = PixState{1.f, bg0, bg1, bg2, 0.f, 0.f, 0.f, 0};
+        if (px < W && py + i < H) {
+            const size_t pix = (size_t)(py + i) * W + px;
+            q[i].last = (int)n_last[pix];
+            q[i].T = T_final[pix];
+            q[i].d0 = dimg[pix]; q[i].d1 = dimg[plane + pix]; q[i].d2 = dimg[2 * plane + pix];
+        }
     }
     if (threadIdx.x == 0) s_maxlast = 0;
     __syncthreads();
-    atomicMax(&s_maxlast, last);
+    atomicMax(&s_maxlast, max(q[0].last, q[1].last));
     __syncthreads();
     const int n = s_maxlast;           // entries beyond every pixel's last blend are unused
-    float S0 = bg0, S1 = bg1, S2 = bg2;
     const unsigned lane = lane_id();
-    for (int top = n; top > 0; top -= kBwdThreads) {
-        const int lo = max(top - kBwdThreads, 0);
-        const int e = lo + threadIdx.x;
+    for (int top = n; top > 0; top -= kBatch) {
+        const int lo = max(top - kBatch, 0);
         __syncthreads();
-        if (e < top) {
-            const uint32_t g = pair_gauss[range.x + e];
-            s_g[threadIdx.x] = g;
-            s_a[threadIdx.x] = rec[3 * (size_t)g];
-            s_b[threadIdx.x] = rec[3 * (size_t)g + 1];
-            const float4 C = rec[3 * (size_t)g + 2];
-            s_c[threadIdx.x] = C.x;
-            s_p[threadIdx.x] = C.w;
+        for (int e = threadIdx.x; lo + e < top; e += kThreads) {
+            const uint32_t g = pair_gauss[range.x + lo + e];
+            const Rec r = load_rec(rec, g);
+            s_g[e] = g;
+            s_a[e] = r.A;
+            s_b[e] = r.B;
+            s_c[e] = r.C;
         }
         __syncthreads();
         for (int j = top - lo - 1; j >= 0; --j) {
             const int idx = lo + j;        // list position of this entry
-            float gu = 0.f, gv = 0.f, ga = 0.f, gb = 0.f, gc = 0.f, go = 0.f;
-            float gr = 0.f, gg = 0.f, gbl = 0.f;
-            bool act = false;
-            if (idx < last) {
-                const float4 A = s_a[j];
-                const float4 B = s_b[j];
-                const float dx = A.x - fx, dy = A.y - fy;
-                const float power = -0.5f * (A.z * dx * dx + B.x * dy * dy) - A.w * dx * dy;
-                // the forward's skip test, bit for bit: power > 0 or alpha < 1/255
-                if (power <= 0.0f && power >= s_p[j]) {
-                    const float G = __expf(power);
-                    const float raw = B.y * G;
-                    const float alpha = fminf(0.99f, raw);
-                    {
-                        act = true;
-                        T = T / (1.0f - alpha);               // T_i, before this Gaussian
-                        const float cb = s_c[j];
-                        const float wgt = alpha * T;
-                        gr = wgt * d0; gg = wgt * d1; gbl = wgt * d2;
-                        const float dalpha = T * ((B.z - S0) * d0 + (B.w - S1) * d1 + (cb - S2) * d2);
-                        S0 = alpha * B.z + (1.0f - alpha) * S0;
-                        S1 = alpha * B.w + (1.0f - alpha) * S1;
-                        S2 = alpha * cb + (1.0f - alpha) * S2;
-                        if (raw < 0.99f) {
-                            go = dalpha * G;
-                            const float dp = dalpha * alpha;
-                            gu = -dp * (A.z * dx + A.w * dy);
-                            gv = -dp * (B.x * dy + A.w * dx);
-                            ga = -0.5f * dp * dx * dx;
-                            gb = -dp * dx * dy;
-                            gc = -0.5f * dp * dy * dy;
-                        }
-                    }
-                }
-            }
+            const float4 A = s_a[j];
+            const float4 B = s_b[j];
+            const float2 Cc = s_c[j];
+            const float dx = A.x - fx;
+            const float dy0 = A.y - fy, dy1 = dy0 - 1.0f;
+            const float ax = __fmul_rn(A.z, dx);
+            float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            bool act = pixel_step(q[0], idx, power2(ax, dx, dy0, A.w, B.x), A, B, Cc, dx, dy0, g);
+            act |= pixel_step(q[1], idx, power2(ax, dx, dy1, A.w, B.x), A, B, Cc, dx, dy1, g);
             if (__any_sync(0xffffffffu, act)) {
-                gu = warp_sum(gu); gv = warp_sum(gv); ga = warp_sum(ga); gb = warp_sum(gb);
-                gc = warp_sum(gc); go = warp_sum(go); gr = warp_sum(gr); gg = warp_sum(gg);
-                gbl = warp_sum(gbl);
+#pragma unroll
+                for (int c = 0; c < 9; ++c) g[c] = warp_sum(g[c]);
                 if (lane == 0) {
                     float* d = drec + 9 * (size_t)s_g[j];
-                    atomicAdd(d + 0, gu); atomicAdd(d + 1, gv); atomicAdd(d + 2, ga);
-                    atomicAdd(d + 3, gb); atomicAdd(d + 4, gc); atomicAdd(d + 5, go);
-                    atomicAdd(d + 6, gr); atomicAdd(d + 7, gg); atomicAdd(d + 8, gbl);
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) atomicAdd(d + c, g[c]);
                 }
             }
         }
@@ -132,7 +140,7 @@ extern "C" ogs_status ogs_blend_bwd(const ogs_rec2d* rec, const uint32_t* pair_g
         return OGS_ERR_ARG;
     if (width <= 0 || height <= 0 || !aligned(rec, 16) || !aligned(tile_range, 8)) return OGS_ERR_ARG;
     const int gx = (width + kTile - 1) / kTile, gy = (height + kTile - 1) / kTile;
-    blend_bwd_kernel<<<gx * gy, kBwdThreads, 0, (cudaStream_t)stream>>>(
+    blend_bwd_kernel<<<gx * gy, blend::kThreads, 0, (cudaStream_t)stream>>>(
         reinterpret_cast<const float4*>(rec), pair_gauss,
         reinterpret_cast<const uint2*>(tile_range), width, height, gx, bg[0], bg[1], bg[2],
         T_final, n_last, dimg, drec);

@@ -6,11 +6,14 @@
 //   layer 2:  D2[128 x 112] = H[128 x 96] . W2blk^T    (block-diagonal: each decoder's
 //                                                        outputs only see its own hidden)
 // Operands live in shared memory in the no-swizzle K-major core-matrix layout (8 rows x 16
-// bytes per core matrix); accumulators live in tensor memory (columns 0..95 and 128..239 of
-// a 256-column allocation).  One thread issues the MMAs and commits them to an mbarrier; the
-// four warps read their 32 accumulator rows each (one anchor per thread) for the bias/ReLU
-// epilogue of layer 1 and the activation epilogue of layer 2 (FP32).  Every mbarrier wait is
-// bounded; on expiry the kernel flags ogs_counts.timeout, releases its tensor memory and exits.
+// bytes per core matrix); accumulators live in tensor memory (128 columns: layer 2 reuses the
+// columns of layer 1 once its epilogue has read them), so three CTAs share an SM.  One thread
+// issues the MMAs and commits them to an mbarrier; the four warps read their 32 accumulator
+// rows each (one anchor per thread) for the bias/ReLU epilogue of layer 1 and the activation
+// epilogue of layer 2 (FP32).  Each output array of a tile is staged in the (then free)
+// layer-2 operand buffer and written with one TMA bulk copy, so global stores are
+// contiguous.  Every mbarrier wait is bounded; on expiry the kernel flags ogs_counts.timeout,
+// releases its tensor memory and exits.
 #include "internal.cuh"
 #include "tc.cuh"
 
@@ -26,8 +29,8 @@ constexpr int kK1 = 48;             // padded layer-1 K
 constexpr int kN1 = 3 * kH;         // 96 hidden (layer-1 N, layer-2 K)
 constexpr int kK = 10;              // Gaussians per anchor
 constexpr int kN2 = 112;            // 110 outputs padded to a multiple of 16
-constexpr uint32_t kTmemCols = 256;
-constexpr uint32_t kD2Col = 128;
+constexpr uint32_t kTmemCols = 128;
+constexpr uint32_t kD2Col = 0;          // layer 2 overwrites layer 1's (already read) columns
 constexpr uint32_t kWaitLimit = 1u << 24;
 
 // shared-memory carve (bytes)
@@ -37,8 +40,9 @@ constexpr int kOffA2 = kOffB1 + kN1 * kK1 * 2;          // 128 x 96 bf16
 constexpr int kOffB2 = kOffA2 + kTM * kN1 * 2;          // 112 x 96 bf16
 constexpr int kOffBias = kOffB2 + kN2 * kN1 * 2;        // 96 + 112 f32
 constexpr int kSmemUsed = kOffBias + (kN1 + kN2) * 4;
-// request enough shared memory that at most two CTAs share an SM: 2 x 256 TMEM columns fit
-constexpr int kSmemRequest = 100 * 1024;
+// three CTAs per SM: 3 x 72 KB of shared memory and 3 x 128 of the 512 TMEM columns
+constexpr int kSmemRequest = 72 * 1024;
+static_assert(kTM * kK * 4 * 4 <= kTM * kN1 * 2, "largest staged output (quats) fits in A2");
 static_assert(kSmemUsed <= kSmemRequest, "shared memory carve");
 
 struct TcArgs {
@@ -56,11 +60,17 @@ struct TcArgs {
 
 __device__ __forceinline__ float sigm(float x) { return 1.0f / (1.0f + __expf(-x)); }
 
-__device__ __forceinline__ void put_bf16(unsigned char* base, int row, int k, int Kpad, float v) {
-    *reinterpret_cast<__nv_bfloat16*>(base + tc::core_offset(row, k, Kpad)) = __float2bfloat16_rn(v);
+// 8 consecutive K values of one row = one 16-byte core-matrix row: a single vector store
+__device__ __forceinline__ void put8(unsigned char* base, int row, int kc, int Kpad,
+                                     const float (&v)[8]) {
+    __nv_bfloat162 h[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    *reinterpret_cast<uint4*>(base + tc::core_offset(row, 8 * kc, Kpad)) =
+        *reinterpret_cast<const uint4*>(h);
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1) decode_bf16_tc(TcArgs a) {
+__global__ void __launch_bounds__(kTcThreads, 3) decode_bf16_tc(TcArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
@@ -72,26 +82,39 @@ __global__ void __launch_bounds__(kTcThreads, 1) decode_bf16_tc(TcArgs a) {
     float* sb2 = sb1 + kN1;
     const int t = threadIdx.x, w = t >> 5;
 
-    // weights -> bf16 operand tiles (zero padding included), biases -> f32
-    for (int e = t; e < kN1 * kK1; e += kTcThreads) {
-        const int n = e / kK1, k = e % kK1;
-        put_bf16(sB1, n, k, kK1, k < kDin ? a.mlp.w1[n * kDin + k] : 0.f);
+    // weights -> bf16 operand tiles (zero padding included), one 8-value chunk per store
+    for (int e = t; e < kN1 * (kK1 / 8); e += kTcThreads) {
+        const int n = e / (kK1 / 8), kc = e % (kK1 / 8);
+        float v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int k = 8 * kc + i;
+            v[i] = k < kDin ? a.mlp.w1[n * kDin + k] : 0.f;
+        }
+        put8(sB1, n, kc, kK1, v);
     }
-    for (int e = t; e < kN2 * kN1; e += kTcThreads) {
-        const int n = e / kN1, k = e % kN1;
-        float v = 0.f;
-        if (n < kK) { if (k < kH) v = a.mlp.w2_op[n * kH + k]; }
-        else if (n < 4 * kK) { if (k >= kH && k < 2 * kH) v = a.mlp.w2_col[(n - kK) * kH + (k - kH)]; }
-        else if (n < 11 * kK) { if (k >= 2 * kH) v = a.mlp.w2_cov[(n - 4 * kK) * kH + (k - 2 * kH)]; }
-        put_bf16(sB2, n, k, kN1, v);
+    for (int e = t; e < kN2 * (kN1 / 8); e += kTcThreads) {
+        const int n = e / (kN1 / 8), kc = e % (kN1 / 8);
+        float v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int k = 8 * kc + i;
+            float x = 0.f;
+            if (n < kK) { if (k < kH) x = a.mlp.w2_op[n * kH + k]; }
+            else if (n < 4 * kK) { if (k >= kH && k < 2 * kH) x = a.mlp.w2_col[(n - kK) * kH + (k - kH)]; }
+            else if (n < 11 * kK) { if (k >= 2 * kH) x = a.mlp.w2_cov[(n - 4 * kK) * kH + (k - 2 * kH)]; }
+            v[i] = x;
+        }
+        put8(sB2, n, kc, kN1, v);
     }
     for (int e = t; e < kN1; e += kTcThreads) sb1[e] = a.mlp.b1[e];
     for (int e = t; e < kN2; e += kTcThreads)
         sb2[e] = e < kK ? a.mlp.b2_op[e] : (e < 4 * kK ? a.mlp.b2_col[e - kK]
                                                     : (e < 11 * kK ? a.mlp.b2_cov[e - 4 * kK] : 0.f));
-    // zero the K padding of the layer-1 A tile once (columns 36..47 never change)
-    for (int e = t; e < kTM * (kK1 - kDin); e += kTcThreads)
-        put_bf16(sA1, e / (kK1 - kDin), kDin + e % (kK1 - kDin), kK1, 0.f);
+    {   // the last K chunk (columns 40..47) of the input tile is always zero
+        const float z8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        put8(sA1, t, kK1 / 8 - 1, kK1, z8);
+    }
     if (t == 0) tc::mbar_init(&mbar, 1);
     if (w == 0) {
         tc::tmem_alloc(&tmem_base, kTmemCols);
@@ -115,6 +138,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) decode_bf16_tc(TcArgs a) {
         const bool valid = r < M;
         uint32_t j = 0;
         float wgt = 0.f, dv[3] = {0.f, 0.f, 0.f};
+        float zc[8];
         if (valid) {
             j = a.sel_idx[r];
             wgt = a.sel_w[r];
@@ -123,20 +147,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) decode_bf16_tc(TcArgs a) {
             const float d = sqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
             const float4* f4 = reinterpret_cast<const float4*>(a.feat + (size_t)j * kF);
 #pragma unroll
-            for (int i = 0; i < kF / 4; ++i) {
-                const float4 v = f4[i];
-                put_bf16(sA1, t, 4 * i, kK1, v.x);
-                put_bf16(sA1, t, 4 * i + 1, kK1, v.y);
-                put_bf16(sA1, t, 4 * i + 2, kK1, v.z);
-                put_bf16(sA1, t, 4 * i + 3, kK1, v.w);
+            for (int kc = 0; kc < kF / 8; ++kc) {
+                const float4 u0 = f4[2 * kc], u1 = f4[2 * kc + 1];
+                const float v[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+                put8(sA1, t, kc, kK1, v);
             }
-            put_bf16(sA1, t, kF, kK1, dv[0] / d);
-            put_bf16(sA1, t, kF + 1, kK1, dv[1] / d);
-            put_bf16(sA1, t, kF + 2, kK1, dv[2] / d);
-            put_bf16(sA1, t, kF + 3, kK1, d);
+            zc[0] = dv[0] / d; zc[1] = dv[1] / d; zc[2] = dv[2] / d; zc[3] = d;
         } else {
-            for (int k = 0; k < kDin; ++k) put_bf16(sA1, t, k, kK1, 0.f);
+            const float z8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int kc = 0; kc < kF / 8; ++kc) put8(sA1, t, kc, kK1, z8);
+            zc[0] = zc[1] = zc[2] = zc[3] = 0.f;
         }
+        zc[4] = zc[5] = zc[6] = zc[7] = 0.f;
+        put8(sA1, t, kF / 8, kK1, zc);
         tc::fence_smem_to_async();
         tc::fence_before_sync();
         __syncthreads();
@@ -158,7 +182,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) decode_bf16_tc(TcArgs a) {
             float v[32];
             tc::tmem_ld32(lane_addr + c0, v);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) put_bf16(sA2, t, c0 + i, kN1, fmaxf(v[i] + sb1[c0 + i], 0.f));
+            for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i] + sb1[c0 + i], 0.f);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float h8[8] = {v[8 * q], v[8 * q + 1], v[8 * q + 2], v[8 * q + 3],
+                                     v[8 * q + 4], v[8 * q + 5], v[8 * q + 6], v[8 * q + 7]};
+                put8(sA2, t, c0 / 8 + q, kN1, h8);
+            }
         }
         tc::fence_smem_to_async();
         tc::fence_before_sync();
@@ -175,7 +205,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) decode_bf16_tc(TcArgs a) {
         if (__syncthreads_or(!ok)) { aborted = true; break; }
         phase ^= 1;
         tc::fence_after_sync();
-        // layer-2 epilogue (FP32): activations, positions
+        // layer-2 epilogue (FP32): activations, positions.  The 112 accumulator columns of
+        // this anchor are read once; each output array is staged row-major for the tile in the
+        // layer-2 operand buffer (free now) and written with one bulk copy.
         float y[128];
 #pragma unroll
         for (int c0 = 0; c0 < 128; c0 += 32) {
@@ -184,29 +216,58 @@ __global__ void __launch_bounds__(kTcThreads, 1) decode_bf16_tc(TcArgs a) {
 #pragma unroll
             for (int i = 0; i < 32; ++i) y[c0 + i] = v[i];
         }
+        float lvv[3] = {0.f, 0.f, 0.f};
         if (valid) {
 #pragma unroll
             for (int i = 0; i < kN2; ++i) y[i] += sb2[i];
-            const size_t g0 = (size_t)r * kK;
-            float lvv[3];
 #pragma unroll
             for (int q = 0; q < 3; ++q) lvv[q] = a.lv[3 * (size_t)j + q];
+        }
+        const uint32_t nvalid = min((uint32_t)kTM, M - tile * kTM);
+        const size_t g0 = (size_t)tile * kTM * kK;        // first Gaussian of the tile
+        float* stage = reinterpret_cast<float*>(sA2);
+        // (array, floats per Gaussian): opacity 1, colours 3, scales 3, quats 4, means 3
+        for (int arr = 0; arr < 5; ++arr) {
+            const int per = arr == 0 ? 1 : (arr == 3 ? 4 : 3);
+            float* rowp = stage + (size_t)t * kK * per;
+            if (valid) {
 #pragma unroll
-            for (int i = 0; i < kK; ++i) {
-                const size_t g = g0 + i;
-                a.out.opac[g] = wgt * tanhf(y[i]);
+                for (int i = 0; i < kK; ++i) {
+                    if (arr == 0) {
+                        rowp[i] = wgt * tanhf(y[i]);
+                    } else if (arr == 1) {
 #pragma unroll
-                for (int q = 0; q < 3; ++q) a.out.colors[3 * g + q] = sigm(y[kK + 3 * i + q]);
-                const float* yc = y + 4 * kK + 7 * i;
+                        for (int q = 0; q < 3; ++q) rowp[3 * i + q] = sigm(y[kK + 3 * i + q]);
+                    } else if (arr == 2) {
 #pragma unroll
-                for (int q = 0; q < 3; ++q) a.out.scales[3 * g + q] = lvv[q] * sigm(yc[q]);
-                const float inv = 1.0f / sqrtf(yc[3] * yc[3] + yc[4] * yc[4] + yc[5] * yc[5] + yc[6] * yc[6]);
-                *reinterpret_cast<float4*>(a.out.quats + 4 * g) =
-                    make_float4(yc[3] * inv, yc[4] * inv, yc[5] * inv, yc[6] * inv);
-                const float* O = a.offs + ((size_t)j * kK + i) * 3;
+                        for (int q = 0; q < 3; ++q) rowp[3 * i + q] = lvv[q] * sigm(y[4 * kK + 7 * i + q]);
+                    } else if (arr == 3) {
+                        const float* yc = y + 4 * kK + 7 * i + 3;
+                        const float inv = 1.0f / sqrtf(yc[0] * yc[0] + yc[1] * yc[1] + yc[2] * yc[2] + yc[3] * yc[3]);
 #pragma unroll
-                for (int q = 0; q < 3; ++q) a.out.means[3 * g + q] = dv[q] + O[q] * lvv[q];
+                        for (int q = 0; q < 4; ++q) rowp[4 * i + q] = yc[q] * inv;
+                    } else {
+                        const float* O = a.offs + ((size_t)j * kK + i) * 3;
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) rowp[3 * i + q] = dv[q] + O[q] * lvv[q];
+                    }
+                }
             }
+            tc::fence_smem_to_async();
+            __syncthreads();
+            float* dst = arr == 0 ? a.out.opac : (arr == 1 ? a.out.colors :
+                         (arr == 2 ? a.out.scales : (arr == 3 ? a.out.quats : a.out.means)));
+            const uint32_t bytes = nvalid * kK * per * 4u;
+            if ((bytes & 15u) == 0 && (((uintptr_t)(dst + g0 * per)) & 15u) == 0) {
+                if (t == 0) {
+                    tc::bulk_store(dst + g0 * per, stage, bytes);
+                    tc::bulk_commit();
+                    tc::bulk_wait_read();
+                }
+            } else {
+                for (uint32_t e = t; e < nvalid * kK * per; e += kTcThreads) dst[g0 * per + e] = stage[e];
+            }
+            __syncthreads();
         }
         tc::fence_before_sync();
         __syncthreads();
@@ -217,6 +278,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) decode_bf16_tc(TcArgs a) {
         // wait (bounded) for the MMA group that may still be in flight before releasing TMEM
         tc::mbar_wait(&mbar, phase, kWaitLimit);
     }
+    if (t == 0) tc::bulk_wait_all();
     tc::fence_before_sync();
     __syncthreads();
     if (w == 0) tc::tmem_dealloc(tbase, kTmemCols);

@@ -221,6 +221,7 @@ struct TrainArgs {
     const ogs_counts* counts;
     const uint32_t* maxc;
     uint32_t tau_bits;
+    float pos_weight;
     float* partial;
     float* loss;
 };
@@ -287,10 +288,11 @@ __global__ void __launch_bounds__(kTrThreads) prop_train_kernel(TrainArgs a) {
         float dz = 0.f;
         if (valid) {
             const float y = a.maxc[j] >= a.tau_bits ? 1.f : 0.f;
-            dz = (p - y) * invM;
+            const float wy = y > 0.f ? a.pos_weight : 1.f;
+            dz = wy * (p - y) * invM;
             // BCE with the log-sigmoid written stably: -y z + log(1 + e^z)
             const float sp = z > 0.f ? z + log1pf(__expf(-z)) : log1pf(__expf(z));
-            lsum += (sp - y * z) * invM;
+            lsum += wy * (sp - y * z) * invM;
         }
         sDZ[t] = dz;
 #pragma unroll
@@ -419,12 +421,13 @@ extern "C" ogs_status ogs_proposal_train(const float* pos, const uint8_t* level,
                                          int64_t N, int32_t NL, const ogs_camera* cam,
                                          const ogs_proposal* net, const uint32_t* sel_idx,
                                          const ogs_counts* counts, const uint32_t* maxc,
-                                         float tau, const ogs_proposal* grads, float* loss,
+                                         float tau, float pos_weight, const ogs_proposal* grads,
+                                         float* loss,
                                          void* scratch, size_t scratch_bytes, void* stream) {
     if (!pos || !level || !feat || !cam || !net_ok(net) || !sel_idx || !counts || !maxc ||
         !net_ok(grads) || !scratch)
         return OGS_ERR_ARG;
-    if (N < 0 || NL < 1 || !(tau >= 0.f)) return OGS_ERR_ARG;
+    if (N < 0 || NL < 1 || !(tau >= 0.f) || !(pos_weight > 0.f)) return OGS_ERR_ARG;
     if (scratch_bytes < ogs_proposal_train_scratch_bytes() || !aligned(scratch, 16) ||
         !aligned(feat, 16))
         return OGS_ERR_ARG;
@@ -435,7 +438,7 @@ extern "C" ogs_status ogs_proposal_train(const float* pos, const uint8_t* level,
     uint32_t tau_bits;
     memcpy(&tau_bits, &tau, sizeof tau_bits);
     TrainArgs a{{pos, level, feat, NL, make_cam(*cam), *net}, sel_idx, counts, maxc, tau_bits,
-                (float*)scratch, loss};
+                pos_weight, (float*)scratch, loss};
     cudaStream_t st = (cudaStream_t)stream;
     prop_train_kernel<<<kTrBlocks, kTrThreads, smem, st>>>(a);
     prop_reduce<<<(kGrads + 255) / 256, 256, 0, st>>>((const float*)scratch, kTrBlocks, *grads);

@@ -1,20 +1,21 @@
 // Front-to-back per-tile lists (Sec. 3.1): a tile's list holds every Gaussian whose tile
 // rectangle covers it, in ascending depth, ties by Gaussian id.
 //
-// Instead of duplicating every Gaussian into 64-bit (tile, depth) keys and radix-sorting all
-// ~45 key bits over all pairs, the work is factored:
-//   1. stable radix sort of the G Gaussians by their 32-bit depth key (4 passes over G items);
-//   2. exclusive scan of tile counts in depth order, fused with a block-cooperative emission of
-//      (tile, Gaussian) pairs in depth order (load-balanced over pairs, not Gaussians);
-//   3. stable radix sort of the P pairs by tile id only (ceil(log2 tiles) bits, 2 passes);
-//   4. tile ranges from the boundaries of equal tile ids.
-// Because step 3 is stable and step 2 emits in (depth, id) order, every tile list comes out in
-// (depth, id) order, the same result as one stable sort of (tile << 32 | depth) keys, for
-// about a third of the memory traffic when P is a few times G.
+// Lists are short (hundreds of entries, a few thousand at most), so instead of sorting all
+// (tile, depth) pairs globally the work is split by tile:
+//   1. per-tile pair counts (atomics over each Gaussian's rectangle) and their exclusive scan,
+//      which gives every tile's range directly;
+//   2. block-cooperative fill: each pair is written into its tile's range at an atomic cursor
+//      slot as (depth key, Gaussian id), in arbitrary order;
+//   3. one CTA per tile sorts its range by the 64-bit key (depth bits << 32 | id) with a
+//      bitonic network in shared memory (lists longer than the shared-memory capacity use the
+//      same network on global memory).
+// The key is unique per Gaussian, so the order is fully determined: the same lists as one
+// stable sort of (tile, depth) keys in Gaussian-id order, without multi-pass global traffic.
 //
-// The radix sort is a classic three-kernel LSD pass (per-block digit histograms -> per-digit
-// scan over blocks -> stable block-local multisplit and coalesced scatter) with 8-bit digits;
-// every item count is read on the device, so no host synchronisation is needed.
+// ogs_radix_sort_pairs (a classic three-kernel LSD radix sort: per-block digit histograms ->
+// per-digit scan over blocks -> stable block-local multisplit and coalesced scatter, 8-bit
+// digits, item count read on the device) is kept as a general entry point.
 #include <mutex>
 
 #include "internal.cuh"
@@ -245,81 +246,110 @@ bool radix_sort(uint32_t* keys, uint32_t* vals, const uint32_t* n_dev, int64_t n
 }
 
 // ---------------------------------------------------------------------------------------
-// depth order -> pair emission
+// per-tile lists: count -> scan -> fill -> per-tile sort
 // ---------------------------------------------------------------------------------------
 
-constexpr int kEmThreads = 256;
-constexpr int kEmItems = 4;
-constexpr int kEmTile = kEmThreads * kEmItems;
+constexpr int kBinThreads = 256;
+constexpr int kBinItems = 4;
+constexpr int kBinTile = kBinThreads * kBinItems;
+constexpr int kSortThreads = 256;
+constexpr int kSortSmem = 8192;          // entries sorted in shared memory (64 KB of keys)
 
-__global__ void iota_keys(const uint32_t* __restrict__ dkey, uint32_t* __restrict__ k,
-                          uint32_t* __restrict__ v, const uint32_t* n_dev, int64_t n_cap) {
-    const uint32_t n = count_of(n_dev, n_cap);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        k[i] = dkey[i];
-        v[i] = (uint32_t)i;
+__device__ __forceinline__ void rect_of(uint2 r, uint32_t& x0, uint32_t& y0, uint32_t& x1,
+                                        uint32_t& y1) {
+    x0 = r.x & 0xFFFFu; y0 = r.x >> 16; x1 = r.y & 0xFFFFu; y1 = r.y >> 16;
+}
+
+// Block-cooperative walk over the pairs of kBinTile Gaussians (load balanced over pairs, not
+// Gaussians): calls f(gaussian, tile) for every pair.
+template <class F>
+__device__ __forceinline__ void for_each_pair(const uint32_t* __restrict__ tiles,
+                                              const uint2* __restrict__ rect, uint32_t n,
+                                              int gx, F f) {
+    __shared__ uint32_t s_off[kBinThreads + 1];
+    __shared__ uint32_t s_g[kBinThreads];
+    __shared__ uint2 s_rect[kBinThreads];
+    __shared__ uint32_t ws[kBinThreads / 32];
+    const int64_t base = (int64_t)blockIdx.x * kBinTile;
+    for (int it = 0; it < kBinItems; ++it) {
+        const int64_t i = base + it * kBinThreads + threadIdx.x;
+        uint32_t c = 0;
+        uint2 rc = make_uint2(0, 0);
+        if (i < n) {
+            c = tiles[i];
+            if (c) rc = rect[i];
+        }
+        uint32_t excl;
+        const uint32_t tot = block_excl_scan(c, excl, ws);
+        s_off[threadIdx.x] = excl;
+        s_g[threadIdx.x] = (uint32_t)i;
+        s_rect[threadIdx.x] = rc;
+        __syncthreads();
+        for (uint32_t p = threadIdx.x; p < tot; p += kBinThreads) {
+            int lo = 0, hi = kBinThreads - 1;          // owner: largest k with s_off[k] <= p
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_off[mid] <= p) lo = mid; else hi = mid - 1;
+            }
+            uint32_t x0, y0, x1, y1;
+            rect_of(s_rect[lo], x0, y0, x1, y1);
+            const uint32_t local = p - s_off[lo], w = x1 - x0;
+            f(s_g[lo], (y0 + local / w) * (uint32_t)gx + x0 + local % w);
+        }
+        __syncthreads();
     }
 }
 
-// per-block sums of tile counts, taken in depth order
-__global__ void __launch_bounds__(kEmThreads) emit_count(const uint32_t* __restrict__ order,
-                                                         const uint32_t* __restrict__ tiles,
+__global__ void __launch_bounds__(kBinThreads) bin_count(const uint32_t* __restrict__ tiles,
+                                                         const uint2* __restrict__ rect,
                                                          const uint32_t* n_dev, int64_t n_cap,
-                                                         uint32_t* block_sum) {
-    __shared__ uint32_t ws[kEmThreads / 32];
+                                                         int gx, uint32_t* __restrict__ tcount) {
     const uint32_t n = count_of(n_dev, n_cap);
-    const int64_t base = (int64_t)blockIdx.x * kEmTile;
-    uint64_t s = 0;
-    for (int it = 0; it < kEmItems; ++it) {
-        int64_t i = base + it * kEmThreads + threadIdx.x;
-        if (i < n) s += tiles[order[i]];
-    }
-    // pair counts stay below 2^32 (pair capacity is 32-bit); saturate defensively
-    uint32_t v = s > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)s;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane_id() == 0) ws[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint64_t t = 0;
-        for (int q = 0; q < kEmThreads / 32; ++q) t += ws[q];
-        block_sum[blockIdx.x] = t > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)t;
-    }
+    if ((int64_t)blockIdx.x * kBinTile >= n) return;
+    for_each_pair(tiles, rect, n, gx, [&](uint32_t, uint32_t t) { atomicAdd(&tcount[t], 1u); });
 }
 
-// exclusive scan of block sums (one block); publishes P or the overflow state
-__global__ void __launch_bounds__(1024) emit_scan(uint32_t* block_sum, int nb, int64_t pair_cap,
+// exclusive scan of the tile counts (one block): tile ranges, P, overflow state
+__global__ void __launch_bounds__(1024) tile_scan(const uint32_t* __restrict__ tcount, int ntiles,
+                                                  int64_t pair_cap, uint2* __restrict__ range,
+                                                  uint32_t* __restrict__ cursor,
                                                   ogs_counts* counts) {
     __shared__ uint32_t ws[32];
     __shared__ unsigned long long carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    for (int b0 = 0; b0 < nb; b0 += 1024) {
-        int b = b0 + threadIdx.x;
-        uint32_t v = b < nb ? block_sum[b] : 0;
+    for (int b0 = 0; b0 < ntiles; b0 += 1024) {
+        const int b = b0 + threadIdx.x;
+        const uint32_t v = b < ntiles ? tcount[b] : 0;
         uint32_t x = v;
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane_id() >= (unsigned)o) x += y;
         }
         if (lane_id() == 31) ws[threadIdx.x >> 5] = x;
         __syncthreads();
         uint32_t wpre = 0, tot = 0;
         for (int q = 0; q < 32; ++q) {
-            uint32_t s = ws[q];
-            wpre += (q < (int)(threadIdx.x >> 5)) ? s : 0;
-            tot += s;
+            wpre += (q < (int)(threadIdx.x >> 5)) ? ws[q] : 0;
+            tot += ws[q];
         }
-        unsigned long long excl = carry + wpre + x - v;
-        if (b < nb) block_sum[b] = (uint32_t)(excl > 0xFFFFFFFFull ? 0xFFFFFFFFull : excl);
+        const unsigned long long excl = carry + wpre + x - v;
+        if (b < ntiles) {
+            range[b] = make_uint2((uint32_t)excl, (uint32_t)(excl + v));
+            cursor[b] = 0;
+        }
         __syncthreads();
         if (threadIdx.x == 0) carry += tot;
         __syncthreads();
     }
+    __syncthreads();
+    const unsigned long long P = carry;
+    const bool over = P > (unsigned long long)pair_cap;
+    if (over)   // no pairs are emitted: every range empty
+        for (int b = threadIdx.x; b < ntiles; b += 1024) range[b] = make_uint2(0, 0);
     if (threadIdx.x == 0) {
-        unsigned long long P = carry;
         counts->need_pairs = (uint32_t)(P > 0xFFFFFFFFull ? 0xFFFFFFFFull : P);
-        if (P > (unsigned long long)pair_cap) {
+        if (over) {
             atomicOr(&counts->overflow, 2u);
             counts->n_pairs = 0;
         } else {
@@ -328,102 +358,95 @@ __global__ void __launch_bounds__(1024) emit_scan(uint32_t* block_sum, int nb, i
     }
 }
 
-// Block-cooperative emission: per step, the block scans 256 Gaussians' tile counts and then
-// all 256 threads walk the step's pairs together (binary search for the owning Gaussian).
-__global__ void __launch_bounds__(kEmThreads) emit_pairs(const uint32_t* __restrict__ order,
-                                                         const uint32_t* __restrict__ tiles,
-                                                         const uint2* __restrict__ rect,
-                                                         const uint32_t* n_dev, int64_t n_cap,
-                                                         const uint32_t* __restrict__ block_off,
-                                                         const ogs_counts* counts, int gx,
-                                                         uint32_t* __restrict__ pkey,
-                                                         uint32_t* __restrict__ pval) {
-    __shared__ uint32_t s_off[kEmThreads + 1];
-    __shared__ uint32_t s_g[kEmThreads];
-    __shared__ uint2 s_rect[kEmThreads];
-    __shared__ uint32_t ws[kEmThreads / 32];
+__global__ void __launch_bounds__(kBinThreads) bin_fill(const uint32_t* __restrict__ tiles,
+                                                        const uint2* __restrict__ rect,
+                                                        const uint32_t* __restrict__ dkey,
+                                                        const uint32_t* n_dev, int64_t n_cap,
+                                                        int gx, const uint2* __restrict__ range,
+                                                        uint32_t* __restrict__ cursor,
+                                                        const ogs_counts* counts,
+                                                        uint32_t* __restrict__ keys,
+                                                        uint32_t* __restrict__ ids) {
     if (counts->overflow & 2u) return;
     const uint32_t n = count_of(n_dev, n_cap);
-    const int64_t base = (int64_t)blockIdx.x * kEmTile;
-    if (base >= n) return;
-    uint32_t running = block_off[blockIdx.x];
-    for (int it = 0; it < kEmItems; ++it) {
-        int64_t i = base + it * kEmThreads + threadIdx.x;
-        uint32_t g = 0, c = 0;
-        uint2 rc = make_uint2(0, 0);
-        if (i < n) {
-            g = order[i];
-            c = tiles[g];
-            if (c) rc = rect[g];
+    if ((int64_t)blockIdx.x * kBinTile >= n) return;
+    for_each_pair(tiles, rect, n, gx, [&](uint32_t g, uint32_t t) {
+        const uint32_t o = range[t].x + atomicAdd(&cursor[t], 1u);
+        keys[o] = dkey[g];
+        ids[o] = g;
+    });
+}
+
+// Bitonic sorting network in its "flip" form over m = next power of two >= cnt slots: each
+// merge stage first compares mirrored pairs of a block, then runs half-cleaners, and every
+// comparator puts the smaller key at the lower index.  Slots >= cnt behave as +infinity, so a
+// comparator that touches one is a no-op: arbitrary counts sort without padding.
+template <class Get, class Swap>
+__device__ __forceinline__ void bitonic(uint32_t cnt, Get get, Swap swp) {
+    uint32_t m = 1;
+    while (m < cnt) m <<= 1;
+    for (uint32_t size = 2; size <= m; size <<= 1) {
+        const uint32_t half = size >> 1;
+        for (uint32_t i = threadIdx.x; i < m / 2; i += blockDim.x) {
+            const uint32_t blk = i / half, off = i - blk * half;
+            const uint32_t lo = blk * size + off, hi = blk * size + size - 1 - off;
+            if (hi < cnt && get(lo) > get(hi)) swp(lo, hi);
         }
-        uint32_t excl;
-        uint32_t tot = block_excl_scan(c, excl, ws);
-        s_off[threadIdx.x] = excl;
-        s_g[threadIdx.x] = g;
-        s_rect[threadIdx.x] = rc;
-        if (threadIdx.x == 0) s_off[kEmThreads] = tot;
         __syncthreads();
-        for (uint32_t p = threadIdx.x; p < tot; p += kEmThreads) {
-            // owner: largest k with s_off[k] <= p (entries with zero count share offsets)
-            int lo = 0, hi = kEmThreads - 1;
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (s_off[mid] <= p) lo = mid; else hi = mid - 1;
+        for (uint32_t stride = half >> 1; stride > 0; stride >>= 1) {
+            for (uint32_t i = threadIdx.x; i < m / 2; i += blockDim.x) {
+                const uint32_t lo = 2 * i - (i & (stride - 1)), hi = lo + stride;
+                if (hi < cnt && get(lo) > get(hi)) swp(lo, hi);
             }
-            const uint32_t local = p - s_off[lo];
-            const uint2 r = s_rect[lo];
-            const uint32_t x0 = r.x & 0xFFFFu, y0 = r.x >> 16, x1 = r.y & 0xFFFFu;
-            const uint32_t wdt = x1 - x0;
-            const uint32_t ty = y0 + local / wdt, tx = x0 + local % wdt;
-            const uint32_t o = running + p;
-            pkey[o] = ty * (uint32_t)gx + tx;
-            pval[o] = s_g[lo];
+            __syncthreads();
         }
-        running += tot;
-        __syncthreads();
     }
 }
 
-__global__ void tile_ranges(const uint32_t* __restrict__ pkey, const ogs_counts* counts,
-                            uint2* __restrict__ range) {
-    const uint32_t P = counts->n_pairs;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t t = pkey[i];
-        if (i == 0 || pkey[i - 1] != t) range[t].x = (uint32_t)i;
-        if (i == P - 1 || pkey[i + 1] != t) range[t].y = (uint32_t)(i + 1);
+__global__ void __launch_bounds__(kSortThreads) tile_sort(const uint2* __restrict__ range,
+                                                          const ogs_counts* counts,
+                                                          uint32_t* __restrict__ keys,
+                                                          uint32_t* __restrict__ ids) {
+    extern __shared__ unsigned long long s_k[];
+    if (counts->overflow & 2u) return;
+    const uint2 r = range[blockIdx.x];
+    const uint32_t cnt = r.y - r.x;
+    if (cnt <= 1) return;
+    if (cnt <= (uint32_t)kSortSmem) {
+        for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x)
+            s_k[i] = ((unsigned long long)keys[r.x + i] << 32) | ids[r.x + i];
+        __syncthreads();
+        bitonic(cnt, [&](uint32_t i) { return s_k[i]; },
+                [&](uint32_t i, uint32_t j) {
+                    const unsigned long long t = s_k[i]; s_k[i] = s_k[j]; s_k[j] = t;
+                });
+        for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) ids[r.x + i] = (uint32_t)s_k[i];
+    } else {
+        // long list: the same network on global memory
+        uint32_t* K = keys + r.x;
+        uint32_t* I = ids + r.x;
+        bitonic(cnt, [&](uint32_t i) { return ((unsigned long long)K[i] << 32) | I[i]; },
+                [&](uint32_t i, uint32_t j) {
+                    const uint32_t tk = K[i], ti = I[i];
+                    K[i] = K[j]; I[i] = I[j]; K[j] = tk; I[j] = ti;
+                });
     }
 }
 
 struct SortScratch {
-    uint32_t* dk;      // depth keys (sorted in place)
-    uint32_t* order;   // Gaussian ids in depth order
-    uint32_t* bsum;    // emission block offsets
-    uint32_t* pkey;    // pair tile keys
-    RsScratch rs;
+    uint32_t* tcount;   // per-tile pair counts
+    uint32_t* cursor;   // per-tile fill cursors
+    uint32_t* keys;     // depth key of every pair
 };
 
-size_t sort_layout(int64_t g_cap, int64_t pair_cap, void* base, SortScratch* s) {
-    int64_t nbe = (g_cap + kEmTile - 1) / kEmTile;
-    if (nbe < 1) nbe = 1;
+size_t sort_layout(int64_t pair_cap, int n_tiles, void* base, SortScratch* s) {
     Carver cv(base);
     SortScratch t;
-    t.dk = cv.take<uint32_t>(g_cap > 0 ? g_cap : 1);
-    t.order = cv.take<uint32_t>(g_cap > 0 ? g_cap : 1);
-    t.bsum = cv.take<uint32_t>(nbe);
-    t.pkey = cv.take<uint32_t>(pair_cap > 0 ? pair_cap : 1);
-    int64_t rs_cap = g_cap > pair_cap ? g_cap : pair_cap;
-    size_t rs_bytes = rs_layout(rs_cap, nullptr, nullptr);
-    char* rs_base = cv.take<char>(rs_bytes);
-    rs_layout(rs_cap, rs_base, &t.rs);
+    t.tcount = cv.take<uint32_t>(n_tiles > 0 ? n_tiles : 1);
+    t.cursor = cv.take<uint32_t>(n_tiles > 0 ? n_tiles : 1);
+    t.keys = cv.take<uint32_t>(pair_cap > 0 ? pair_cap : 1);
     if (s) *s = t;
     return cv.off + 256;
-}
-
-int bits_for(int64_t n) {
-    int b = 0;
-    while (((int64_t)1 << b) < n) ++b;
-    return b < 1 ? 1 : b;
 }
 
 }  // namespace
@@ -450,8 +473,8 @@ extern "C" ogs_status ogs_radix_sort_pairs(uint32_t* keys, uint32_t* vals, const
 }
 
 extern "C" size_t ogs_sort_scratch_bytes(int64_t g_cap, int64_t pair_cap, int32_t n_tiles) {
-    (void)n_tiles;
-    return sort_layout(g_cap < 0 ? 0 : g_cap, pair_cap < 0 ? 0 : pair_cap, nullptr, nullptr);
+    (void)g_cap;
+    return sort_layout(pair_cap < 0 ? 0 : pair_cap, n_tiles, nullptr, nullptr);
 }
 
 extern "C" ogs_status ogs_sort(const uint32_t* depth_key, const uint32_t* rect, const uint32_t* tiles,
@@ -466,35 +489,30 @@ extern "C" ogs_status ogs_sort(const uint32_t* depth_key, const uint32_t* rect, 
     if (grid_x <= 0 || grid_y <= 0 || (int64_t)grid_x * grid_y > 65536 || grid_x > 65535)
         return OGS_ERR_ARG;
     if (scratch_bytes < ogs_sort_scratch_bytes(g_cap, pair_cap, grid_x * grid_y) ||
-        !aligned(scratch, 16) || !aligned(rect, 8))
+        !aligned(scratch, 16) || !aligned(rect, 8) || !aligned(tile_range, 8))
         return OGS_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const int n_tiles = grid_x * grid_y;
-    if (cudaMemsetAsync(tile_range, 0, sizeof(uint32_t) * 2 * (size_t)n_tiles, st) != cudaSuccess)
-        return OGS_ERR_CUDA;
-    if (g_cap == 0) return OGS_OK;
     SortScratch s;
-    sort_layout(g_cap, pair_cap, scratch, &s);
+    sort_layout(pair_cap, n_tiles, scratch, &s);
+    uint2* range = reinterpret_cast<uint2*>(tile_range);
+    if (cudaMemsetAsync(s.tcount, 0, sizeof(uint32_t) * n_tiles, st) != cudaSuccess)
+        return OGS_ERR_CUDA;
     // the Gaussian count is the device count written by the decoder, or the caller's n_gauss
     const uint32_t* n_dev = n_gauss < 0 ? &counts->n_gaussians : nullptr;
     const int64_t n_cap = n_gauss < 0 ? g_cap : (n_gauss < g_cap ? n_gauss : g_cap);
-    // 1. depth order
-    iota_keys<<<stride_grid(n_cap, 256, 8), 256, 0, st>>>(depth_key, s.dk, s.order, n_dev, n_cap);
-    if (!radix_sort(s.dk, s.order, n_dev, n_cap, 0, 32, s.rs, st)) return OGS_ERR_CUDA;
-    // 2. pair emission in depth order
-    int nbe = (int)((n_cap + kEmTile - 1) / kEmTile);
-    if (nbe < 1) nbe = 1;
-    emit_count<<<nbe, kEmThreads, 0, st>>>(s.order, tiles, n_dev, n_cap, s.bsum);
-    emit_scan<<<1, 1024, 0, st>>>(s.bsum, nbe, pair_cap, counts);
-    emit_pairs<<<nbe, kEmThreads, 0, st>>>(s.order, tiles, reinterpret_cast<const uint2*>(rect),
-                                           n_dev, n_cap, s.bsum, counts, grid_x, s.pkey,
-                                           pair_gauss);
-    // 3. stable sort of pairs by tile id
-    if (!radix_sort(s.pkey, pair_gauss, &counts->n_pairs, pair_cap, 0, bits_for(n_tiles), s.rs, st))
+    int nb = (int)((n_cap + kBinTile - 1) / kBinTile);
+    if (nb < 1) nb = 1;
+    const uint2* rc = reinterpret_cast<const uint2*>(rect);
+    bin_count<<<nb, kBinThreads, 0, st>>>(tiles, rc, n_dev, n_cap, grid_x, s.tcount);
+    tile_scan<<<1, 1024, 0, st>>>(s.tcount, n_tiles, pair_cap, range, s.cursor, counts);
+    bin_fill<<<nb, kBinThreads, 0, st>>>(tiles, rc, depth_key, n_dev, n_cap, grid_x, range,
+                                         s.cursor, counts, s.keys, pair_gauss);
+    const size_t smem = sizeof(unsigned long long) * kSortSmem;
+    if (cudaFuncSetAttribute(tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
         return OGS_ERR_CUDA;
-    // 4. tile ranges
-    tile_ranges<<<stride_grid(pair_cap, 256, 8), 256, 0, st>>>(s.pkey, counts,
-                                                                reinterpret_cast<uint2*>(tile_range));
+    tile_sort<<<n_tiles, kSortThreads, smem, st>>>(range, counts, s.keys, pair_gauss);
     return launch_status();
 }
 

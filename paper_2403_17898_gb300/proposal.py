@@ -39,9 +39,9 @@ class ProposalNet:
         out["w3"] = out["w3"].reshape(1, -1)
         return out
 
-    def train_view(self, rd, cam, sel_idx, counts, maxc, tau):
+    def train_view(self, rd, cam, sel_idx, counts, maxc, tau, pos_weight=1.0):
         abi.proposal_train(rd.pos, rd.level, rd.feat, rd.N, rd.NL, cam, self.w, sel_idx, counts,
-                           maxc, tau, self.g, self.loss, self.scratch)
+                           maxc, tau, self.g, self.loss, self.scratch, pos_weight)
 
     def step(self):
         self.steps += 1
@@ -71,16 +71,16 @@ def collect_labels(rd, cams, infer=True):
     return out
 
 
-def train(net, rd, views, epochs=20, tau=1.0 / 255.0, seed=0):
-    """Adam on the mean BCE of each view's selected anchors, views shuffled per epoch;
-    returns the mean loss per epoch."""
+def train(net, rd, views, epochs=20, tau=1.0 / 255.0, seed=0, pos_weight=1.0):
+    """Adam on the mean (weighted) BCE of each view's selected anchors, views shuffled per
+    epoch; returns the mean loss per epoch."""
     rng = np.random.default_rng(seed)
     hist = []
     for _ in range(epochs):
         net.loss.zero_()
         for i in rng.permutation(len(views)):
             v = views[i]
-            net.train_view(rd, v.cam, v.sel_idx, v.counts, v.maxc, tau)
+            net.train_view(rd, v.cam, v.sel_idx, v.counts, v.maxc, tau, pos_weight)
             net.step()
         hist.append(float(net.loss.item()) / len(views))
     return hist

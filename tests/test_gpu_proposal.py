@@ -74,7 +74,7 @@ def test_train_loss_and_gradients_match_oracle(abi):
     tau = 0.01
     X = oracle.proposal_inputs(sc.pos, sc.level, sc.feat, sc.NL, sel, cam)
     y = (maxc[sel] >= tau).astype(np.float64)
-    loss_ref, g_ref = oracle.proposal_bce_grad(net, X, y)
+    loss_ref, g_ref = oracle.proposal_bce_grad(net, X, y, 3.0)
     counts = np.zeros(8, np.uint32)
     counts[0] = M
     nt = _net_tensors(net)
@@ -83,7 +83,7 @@ def test_train_loss_and_gradients_match_oracle(abi):
     scr = torch.empty(abi.proposal_train_scratch_bytes(), dtype=torch.uint8, device="cuda")
     abi.proposal_train(cuda(sc.pos), cuda(sc.level), cuda(sc.feat), sc.N, sc.NL, cam, nt,
                        cuda(sel.astype(np.int32)), cuda(counts.view(np.int32)),
-                       cuda(maxc.view(np.int32)), tau, grads, loss, scr)
+                       cuda(maxc.view(np.int32)), tau, grads, loss, scr, pos_weight=3.0)
     torch.cuda.synchronize()
     assert abs(loss.item() - loss_ref) <= 1e-5 * max(1.0, loss_ref)
     for n in ("w1", "b1", "w2", "b2", "w3", "b3"):

@@ -37,6 +37,10 @@ def test_bias_only_network():
     # -(3 ln .75 + 2 ln .25)/5 and dL/db3 = mean(p - y) = (5*.75 - 3)/5
     assert loss == pytest.approx(-(3 * math.log(0.75) + 2 * math.log(0.25)) / 5, rel=1e-12)
     assert g["b3"][0] == pytest.approx((5 * 0.75 - 3) / 5, rel=1e-12)
+    # positives weighted 3x: loss -(3*3 ln .75 + 2 ln .25)/5, dL/db3 = (3*3*(.75-1) + 2*.75)/5
+    loss, g = oracle.proposal_bce_grad(net, X, np.array([1, 1, 0, 0, 1]), 3.0)
+    assert loss == pytest.approx(-(9 * math.log(0.75) + 2 * math.log(0.25)) / 5, rel=1e-12)
+    assert g["b3"][0] == pytest.approx((9 * (0.75 - 1) + 2 * 0.75) / 5, rel=1e-12)
 
 
 def test_single_path_copies_input():
@@ -54,20 +58,20 @@ def test_single_path_copies_input():
     np.testing.assert_allclose(t["z"], X[:, 36], atol=1e-12)
 
 
-def test_backward_matches_finite_differences():
+@pytest.mark.parametrize("pw", [1.0, 4.0])
+def test_backward_matches_finite_differences(pw):
     rng = np.random.default_rng(1)
     net = _net(3)
-    net = synth.ProposalMLP(*[a.astype(np.float64) for a in net.arrays()])
     X = rng.normal(size=(40, 37))
     y = (rng.uniform(size=40) < 0.4).astype(np.float64)
-    loss, g = oracle.proposal_bce_grad(net, X, y)
+    loss, g = oracle.proposal_bce_grad(net, X, y, pw)
     for name, ix in [("w1", (3, 7)), ("w1", (60, 36)), ("b1", (5,)), ("w2", (10, 20)),
                      ("b2", (63,)), ("w3", (0, 11)), ("b3", (0,))]:
         arr = getattr(net, name)
         x0 = arr[ix]
         arr[ix] = x0 + 1e-6
-        lp = oracle.proposal_bce_grad(net, X, y)[0]
+        lp = oracle.proposal_bce_grad(net, X, y, pw)[0]
         arr[ix] = x0 - 1e-6
-        lm = oracle.proposal_bce_grad(net, X, y)[0]
+        lm = oracle.proposal_bce_grad(net, X, y, pw)[0]
         arr[ix] = x0
         assert g[name][ix] == pytest.approx((lp - lm) / 2e-6, rel=1e-5, abs=1e-9), (name, ix)
