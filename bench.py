@@ -220,7 +220,7 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------
 
 # kernels each ABI call launches per frame
-LAUNCHES = {"lod_select": 3, "proposal_gate": 3, "decode": 1, "project_bin": 1, "sort": 4,
+LAUNCHES = {"lod_select": 1, "proposal_gate": 1, "decode": 1, "project_bin": 1, "sort": 4,
             "blend_fwd": 1}
 DPSNR_GATE_DB = 0.05
 
@@ -263,6 +263,91 @@ def _per_pose(rd, cams, gate=None):
     return out
 
 
+# training-step workloads: (scene, views per step, SSIM weight, timed steps, warm-up steps)
+TRAIN_WORKLOADS = (
+    ("city8M_1080p", 16, 0.2, 8, 3,
+     "8M anchors / 10 levels / 4 km city grid, 16 views of 1920x1080 per step (every 4th pose "
+     "of a 64-pose zoom-out 8 m -> 4 km), 0.8 L1 + 0.2 D-SSIM vs seeded U[0,1] targets, "
+     "dense Adam over all anchors and decoder weights"),
+    ("street500k_1600x900", 1, 0.0, 60, 5,
+     "500k anchors / 6 levels / 600 m street grid, one 1600x900 view per step (30-pose "
+     "zoom-out 8 m -> 250 m, cycled), L1 vs seeded U[0,1] targets, dense Adam"),
+)
+
+
+def _train_bench(clk_index, steps_scale=1.0):
+    """Training steps per second of both training workloads, plain FP32 decode and BF16
+    decode: each step clears the gradients, runs forward + loss + backward for its views and
+    one Adam update (device time, CUDA events around every step)."""
+    import torch
+    import synth
+    from paper_2403_17898_gb300.render import Trainer
+    out = {}
+    for name, vps, lam, K, Wm, desc in TRAIN_WORKLOADS:
+        K = max(2, int(round(K * steps_scale)))
+        sc, mlp, cams = synth.CONFIGS[name]()
+        W, H = cams[0].W, cams[0].H
+        stride = max(1, len(cams) // 16) if vps > 1 else 1
+        views = cams[::stride][:vps] if vps > 1 else cams
+        tr = Trainer(sc, mlp, W, H, ssim_lambda=lam, sel_cap=400_000, pair_cap=8_000_000)
+        del sc
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(1)
+        n_t = vps if vps > 1 else len(views)
+        targets = [torch.rand(3, H, W, generator=gen, device="cuda") for _ in range(n_t)]
+        # size the buffers on every view (training mode), with headroom for the updates
+        sel_max = pair_max = 0
+        for cam in views:
+            c = tr.render(cam, infer=False)
+            sel_max, pair_max = max(sel_max, c.n_selected), max(pair_max, c.n_pairs)
+        tr.sel_cap, tr.pair_cap = int(sel_max * 1.2) + 1024, int(pair_max * 1.5) + 4096
+        tr._alloc()
+        res = {"workload": desc, "anchors": int(tr.N), "views_per_step": vps,
+               "resolution": f"{W}x{H}", "ssim_lambda": lam, "steps": K, "warmup": Wm,
+               "l2": "no flush: every step streams the dense Adam state (>= 1 GB) through L2",
+               "max_selected": sel_max, "max_pairs": pair_max}
+        # both forms start from the same parameters and optimiser state
+        init = {n: getattr(tr, n).clone() for n in tr.PARAMS}
+        init.update({"mlp." + n: t.clone() for n, t in tr.mlp.items()})
+        for precision in ("fp32", "bf16"):
+            for n in tr.PARAMS:
+                getattr(tr, n).copy_(init[n])
+            for n, t in tr.mlp.items():
+                t.copy_(init["mlp." + n])
+            for t in list(tr.adam_m.values()) + list(tr.adam_v.values()):
+                t.zero_()
+            tr.zero_grad()
+            tr.step_count = 0
+            tr.precision = precision
+            batch = lambda i: ([views[(i * vps + v) % len(views)] for v in range(vps)],
+                               [targets[(i * vps + v) % n_t] for v in range(vps)])
+            for i in range(Wm):
+                tr.train_step(*batch(i))
+            torch.cuda.synchronize()
+            timers, ev = {}, []
+            with ClockSampler(clk_index) as clk:
+                for i in range(K):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    tr.train_step(*batch(Wm + i), timers=timers)
+                    e1.record()
+                    ev.append((e0, e1))
+                torch.cuda.synchronize()
+            c = tr.counts()
+            assert c.overflow == 0 and c.timeout == 0, "overflow or expired wait in training"
+            ms = [a.elapsed_time(b) for a, b in ev]
+            stages = {k: round(float(np.sum([a.elapsed_time(b) for a, b in v])) / K, 4)
+                      for k, v in timers.items()}
+            res[precision] = {"train_steps_per_s": 1e3 * K / float(np.sum(ms)),
+                              "ms_per_step": float(np.mean(ms)), "stages_ms_per_step": stages,
+                              "loss_last_step": float(tr.loss.item()),
+                              "clocks": clk.summary()}
+        out[name] = res
+        del tr, targets
+        torch.cuda.empty_cache()
+    return out
+
+
 POS_WEIGHT = 4.0
 
 
@@ -272,6 +357,7 @@ def _train_proposal(rd, train_cams, test_cams, full_rd):
     calibrates p* as the largest threshold whose WORST calibration pose stays within the
     PSNR budget, and judges it on the held-out poses against full-detail renders.  If the
     held-out poses exceed the budget, the plain LOD path is used (the gate's fallback)."""
+    import torch
     import synth
     from paper_2403_17898_gb300 import proposal
     t0 = time.perf_counter()
@@ -281,37 +367,49 @@ def _train_proposal(rd, train_cams, test_cams, full_rd):
     t_train = time.perf_counter() - t0
 
     def judge(cams, p_star):
-        dps, kept, direct = [], [], []
+        """Set-level PSNR loss (pixel MSE pooled over the views) of the gated BF16 form
+        against the full-detail render, relative to the plain FP32 path, plus per-view
+        figures and the kept anchor fraction."""
+        se_plain = se_gate = 0.0
+        dps, kept = [], []
         for cam in cams:
             full_rd.render(proposal.full_detail(cam))
             ref = full_rd.img
+            rd.precision = "fp32"
             c0 = rd.render(cam)
             plain = rd.img.clone()
+            rd.precision = "bf16"
             c1 = rd.render(cam, gate=(net.w, p_star))
+            rd.precision = "fp32"
+            m0 = float(torch.mean((plain - ref) ** 2).item())
+            m1 = float(torch.mean((rd.img - ref) ** 2).item())
+            se_plain += m0
+            se_gate += m1
             dps.append(proposal.psnr(plain, ref) - proposal.psnr(rd.img, ref))
-            direct.append(proposal.psnr(rd.img, plain))
             kept.append(c1.n_selected / max(c0.n_selected, 1))
-        return (float(np.mean(dps)), float(np.max(dps)), float(np.mean(kept)),
-                float(np.median(direct)))
+        pooled = 10.0 * math.log10(se_gate / se_plain) if se_plain > 0 else 0.0
+        return pooled, float(np.median(dps)), float(np.max(dps)), float(np.mean(kept))
 
     calib = train_cams[::5]
     p_star, curve = 0.0, []
-    for cand in (0.001, 0.002, 0.005, 0.01, 0.02, 0.05, 0.1, 0.2):
+    for cand in (0.001, 0.002, 0.005, 0.01, 0.02, 0.05, 0.1, 0.2, 0.3, 0.5):
         r = judge(calib, cand)
-        curve.append([cand, round(r[0], 4), round(r[1], 4), round(r[2], 4)])
-        if r[1] <= DPSNR_GATE_DB:
+        curve.append([cand] + [round(x, 4) for x in r])
+        if r[0] <= DPSNR_GATE_DB:
             p_star = cand
-    mean_dp, max_dp, kept, direct = judge(test_cams, p_star) if p_star > 0 else (0.0, 0.0, 1.0, float("inf"))
-    use_gate = p_star > 0 and mean_dp <= DPSNR_GATE_DB
+    pooled, med, mx, kept = judge(test_cams, p_star) if p_star > 0 else (0.0, 0.0, 0.0, 1.0)
+    use_gate = p_star > 0 and pooled <= DPSNR_GATE_DB
     info = {"train_poses": len(train_cams), "heldout_poses": len(test_cams),
             "epochs": len(hist), "bce_first_epoch": hist[0], "bce_last_epoch": hist[-1],
             "pos_weight": POS_WEIGHT, "train_s": t_train, "p_star": p_star,
             "label": "max T*alpha >= 1/255",
-            "calibration_curve[p*, dPSNR mean, dPSNR max, kept]": curve,
-            "heldout_dpsnr_db_mean": mean_dp, "heldout_dpsnr_db_max": max_dp,
-            "heldout_psnr_vs_plain_db_median": direct, "heldout_kept_anchor_frac": kept,
+            "calibration_curve[p*, dPSNR set, dPSNR view median, dPSNR view max, kept]": curve,
+            "heldout_dpsnr_db_set": pooled, "heldout_dpsnr_db_view_median": med,
+            "heldout_dpsnr_db_view_max": mx, "heldout_kept_anchor_frac": kept,
             "gate_used": use_gate,
-            "dpsnr_definition": "PSNR(plain FP32 LOD vs full-detail) - PSNR(gated BF16 vs full-detail)"}
+            "dpsnr_definition": "10 log10(sum_v MSE(gated BF16_v, full_v) / sum_v MSE(plain FP32_v, "
+                                "full_v)) over the views: the PSNR of the view set, full = "
+                                "every level selected; per-view PSNR differences beside it"}
     return net, p_star, use_gate, info
 
 
@@ -447,6 +545,10 @@ def run_gpu(args):
                 "call": "Renderer.render_to_host (render + image to pinned host memory)"},
         "gpu_launches": args.steps * (sum(LAUNCHES.values()) - (0 if use_gate else LAUNCHES["proposal_gate"])),
     }
+    if ws == 1 and not args.no_train:
+        del rd
+        torch.cuda.empty_cache()
+        line["train"] = _train_bench(local)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(*_as_f64(sc, mlp), cams)
     print(json.dumps(line), flush=True)
@@ -472,6 +574,30 @@ def run_profile(args):
     return 0
 
 
+def run_profile_train(args):
+    """A few training steps of the 500k-anchor street workload (one 1600x900 view per step,
+    L1 + D-SSIM, BF16 decode): the small case the training-kernel ncu captures are taken on."""
+    import torch
+    import synth
+    from paper_2403_17898_gb300 import build as _b
+    _b.build()
+    from paper_2403_17898_gb300.render import Trainer
+    sc, mlp, cams = synth.CONFIGS["street500k_1600x900"]()
+    W, H = cams[0].W, cams[0].H
+    tr = Trainer(sc, mlp, W, H, ssim_lambda=0.2, sel_cap=100_000, pair_cap=2_000_000,
+                 precision=args.precision)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1)
+    tgt = torch.rand(3, H, W, generator=gen, device="cuda")
+    cam = cams[len(cams) // 2]
+    tr.render(cam, infer=False)
+    for _ in range(args.warmup + args.steps):
+        tr.train_step([cam], [tgt])
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_train_steps": args.warmup + args.steps, **tr.counts().__dict__}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -479,12 +605,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-train", action="store_true",
+                    help="skip the training-step measurements")
     ap.add_argument("--profile", action="store_true",
                     help="render a few frames only (the case profiled with ncu)")
+    ap.add_argument("--profile-train", action="store_true",
+                    help="run a few training steps only (the case training kernels are profiled on)")
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
     args = ap.parse_args()
     if args.profile:
         return run_profile(args)
+    if args.profile_train:
+        return run_profile_train(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

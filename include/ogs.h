@@ -178,19 +178,26 @@ ogs_status ogs_decode_bf16(const float* pos, const float* feat, const float* off
  *   means_relative: 1 if means are camera-relative (as written by ogs_decode), 0 if world
  *   rec ogs_rec2d[G], depth_key u32[G] (float bits of depth), rect u32[G][2]
  *   (x0 | y0 << 16, x1 | y1 << 16), tiles u32[G] (number of tiles covered)
+ *   tile_count u32[grid_x * grid_y] (optional, may be NULL): zeroed by the call, then the
+ *   number of (tile, Gaussian) pairs of every tile — pass it to ogs_sort, which then skips
+ *   its own counting pass
  * ------------------------------------------------------------------------------------- */
 ogs_status ogs_project_bin(const ogs_gaussians* g /* host struct */, int64_t n_gauss,
                            int32_t means_relative, const ogs_camera* cam /* host */,
                            ogs_rec2d* rec, uint32_t* depth_key, uint32_t* rect,
-                           uint32_t* tiles, ogs_counts* counts, void* stream);
+                           uint32_t* tiles, uint32_t* tile_count, ogs_counts* counts,
+                           void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * ogs_sort — Sec. 3.1: for every tile, the Gaussians whose rectangle covers it, in
  * front-to-back order (ascending depth, ties by Gaussian id).  Built per tile: pair counts per
  * tile and their exclusive scan (the tile ranges), an unordered fill of each tile's range, and
- * one CTA per tile sorting its range by the unique key (depth bits << 32 | Gaussian id) in
- * shared memory.  The result is fully determined by the inputs.
- *   depth_key/rect/tiles from ogs_project_bin; n_gauss < 0 takes the Gaussian count from
+ * a sort of every range by the unique key (depth bits << 32 | Gaussian id) in shared memory
+ * (one small CTA per list of up to 2048 pairs, larger CTAs for the few longer lists).  The
+ * result is fully determined by the inputs.
+ *   depth_key/rect/tiles from ogs_project_bin; tile_count (optional) the per-tile pair counts
+ *   written by ogs_project_bin for the same Gaussians, or NULL to count here; n_gauss < 0
+ *   takes the Gaussian count from
  *   counts->n_gaussians (as written by ogs_decode), else n_gauss (<= g_cap)
  *   pair_gauss u32[pair_cap]: Gaussian id of each pair, tile-major, front-to-back
  *   tile_range u32[n_tiles][2]: [start, end) of each tile in pair_gauss
@@ -200,14 +207,16 @@ ogs_status ogs_project_bin(const ogs_gaussians* g /* host struct */, int64_t n_g
  * ------------------------------------------------------------------------------------- */
 size_t ogs_sort_scratch_bytes(int64_t g_cap, int64_t pair_cap, int32_t n_tiles);
 ogs_status ogs_sort(const uint32_t* depth_key, const uint32_t* rect, const uint32_t* tiles,
-                    int64_t g_cap, int64_t n_gauss, int32_t grid_x, int32_t grid_y,
+                    const uint32_t* tile_count, int64_t g_cap, int64_t n_gauss,
+                    int32_t grid_x, int32_t grid_y,
                     uint32_t* pair_gauss, uint32_t* tile_range, int64_t pair_cap,
                     ogs_counts* counts, void* scratch, size_t scratch_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------------------
- * ogs_radix_sort_pairs — the stable LSD radix sort used by ogs_sort, exposed on its own:
- * sorts (key, value) pairs by bits [bit_lo, bit_hi) of the key, equal keys keeping their
- * input order.  n = *n_dev if n_dev != NULL (device count, <= n_cap) else n_cap.  Result
+ * ogs_radix_sort_pairs — a stable LSD radix sort of (key, value) pairs (the sort of the
+ * cited rasterizer's global (tile, depth) key design; ogs_sort builds the same lists per tile
+ * instead): sorts by bits [bit_lo, bit_hi) of the key, equal keys keeping their input
+ * order.  n = *n_dev if n_dev != NULL (device count, <= n_cap) else n_cap.  Result
  * replaces keys/vals in place.
  *   scratch: ogs_radix_sort_scratch_bytes(n_cap) bytes, 16-byte aligned.
  * ------------------------------------------------------------------------------------- */
@@ -270,15 +279,20 @@ ogs_status ogs_project_bwd(const ogs_gaussians* g /* host struct */, int64_t n_g
  * dscales, dquats from ogs_project_bwd; opacity and colour gradients from drec) into
  *   dfeat f32[N][F], doffs f32[N][k][3], dlv f32[N][3]   (ACCUMULATED: +=)
  *   dmlp: decoder weight gradients, same layout as ogs_mlp  (ACCUMULATED: +=)
- * Anchor positions, LOD bias and the selection are constants.  Weight gradients are summed
- * per block and then across blocks in a fixed order.
- *   scratch: ogs_decode_bwd_scratch_bytes() bytes, 16-byte aligned.
+ * Anchor positions, LOD bias and the selection are constants.  A row pass (thread per
+ * anchor) writes each anchor's output, hidden and input rows to scratch; weight gradients are
+ * summed per block over those rows and then across blocks in a fixed order (deterministic).
+ *   sel_idx/sel_w: the selection the forward decoded (counts->n_selected <= sel_cap entries)
+ *   feat and dfeat 16-byte aligned
+ *   scratch: ogs_decode_bwd_scratch_bytes(sel_cap) bytes, 16-byte aligned (about 1.4 KB per
+ *   selectable anchor plus 8.7 MB).
  * ------------------------------------------------------------------------------------- */
-size_t ogs_decode_bwd_scratch_bytes(void);
+size_t ogs_decode_bwd_scratch_bytes(int64_t sel_cap);
 ogs_status ogs_decode_bwd(const float* pos, const float* feat, const float* offs, const float* lv,
                           int64_t N, const ogs_mlp* mlp /* host struct */,
                           const ogs_camera* cam /* host */, const uint32_t* sel_idx,
-                          const float* sel_w, const ogs_counts* counts, const float* dmeans,
+                          const float* sel_w, int64_t sel_cap, const ogs_counts* counts,
+                          const float* dmeans,
                           const float* dscales, const float* dquats, const float* drec,
                           float* dfeat, float* doffs, float* dlv,
                           const ogs_mlp* dmlp /* host struct of device ptrs, written */,
@@ -363,6 +377,20 @@ ogs_status ogs_proposal_gate(const float* pos, const uint8_t* level, const float
                              const uint32_t* sel_in, const float* w_in, int64_t sel_cap,
                              ogs_counts* counts, uint32_t* sel_out, float* w_out, float* p_out,
                              void* scratch, size_t scratch_bytes, void* stream);
+
+/* ogs_proposal_gate_bf16 — ogs_proposal_gate with both hidden layers computed as BF16 x BF16
+ * -> FP32 tensor-core products (inputs and first hidden layer rounded to BF16; biases, ReLU,
+ * the output layer and the sigmoid in FP32).  Same arguments, scratch and results; p differs
+ * from the FP32 form by the BF16 rounding, so entries with p near p_star may be decided
+ * differently.  On a tensor-core wait that does not complete, counts->timeout is set. */
+ogs_status ogs_proposal_gate_bf16(const float* pos, const uint8_t* level, const float* feat,
+                                  int64_t N, int32_t NL, int32_t k,
+                                  const ogs_camera* cam /* host */,
+                                  const ogs_proposal* net /* host struct */, float p_star,
+                                  const uint32_t* sel_in, const float* w_in, int64_t sel_cap,
+                                  ogs_counts* counts, uint32_t* sel_out, float* w_out,
+                                  float* p_out, void* scratch, size_t scratch_bytes,
+                                  void* stream);
 
 /* ogs_proposal_train — mean weighted binary cross-entropy of the keep probability over the
  * selected anchors of one view against labels y = (maxc[anchor] >= tau) (maxc as written by

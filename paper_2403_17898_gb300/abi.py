@@ -66,9 +66,10 @@ _SIGS = {
     "ogs_decode_bf16": (C.c_int, [_P, _P, _P, _P, _I64, C.POINTER(MLP), C.POINTER(Camera), _P,
                                   _P, _I64, _P, C.POINTER(Gaussians), _P]),
     "ogs_project_bin": (C.c_int, [C.POINTER(Gaussians), _I64, _I32, C.POINTER(Camera), _P, _P,
-                                  _P, _P, _P, _P]),
+                                  _P, _P, _P, _P, _P]),
     "ogs_sort_scratch_bytes": (_SZ, [_I64, _I64, _I32]),
-    "ogs_sort": (C.c_int, [_P, _P, _P, _I64, _I64, _I32, _I32, _P, _P, _I64, _P, _P, _SZ, _P]),
+    "ogs_sort": (C.c_int, [_P, _P, _P, _P, _I64, _I64, _I32, _I32, _P, _P, _I64, _P, _P, _SZ,
+                           _P]),
     "ogs_radix_sort_scratch_bytes": (_SZ, [_I64]),
     "ogs_radix_sort_pairs": (C.c_int, [_P, _P, _P, _I64, _I32, _I32, _P, _SZ, _P]),
     "ogs_blend_fwd": (C.c_int, [_P, _P, _P, _I32, _I32, C.POINTER(C.c_float * 3), _P, _P, _P,
@@ -77,9 +78,10 @@ _SIGS = {
                                 _P, _P]),
     "ogs_project_bwd": (C.c_int, [C.POINTER(Gaussians), _I64, _I32, C.POINTER(Camera), _P, _P,
                                   _P, _P, _P, _P, _P]),
-    "ogs_decode_bwd_scratch_bytes": (_SZ, []),
+    "ogs_decode_bwd_scratch_bytes": (_SZ, [_I64]),
     "ogs_decode_bwd": (C.c_int, [_P, _P, _P, _P, _I64, C.POINTER(MLP), C.POINTER(Camera), _P, _P,
-                                 _P, _P, _P, _P, _P, _P, _P, _P, C.POINTER(MLP), _P, _SZ, _P]),
+                                 _I64, _P, _P, _P, _P, _P, _P, _P, _P, C.POINTER(MLP), _P, _SZ,
+                                 _P]),
     "ogs_loss_l1": (C.c_int, [_P, _P, _I64, _P, _P, _P]),
     "ogs_loss_l1_ssim_scratch_bytes": (_SZ, [_I32, _I32, _I32]),
     "ogs_loss_l1_ssim": (C.c_int, [_P, _P, _I32, _I32, _I32, C.c_float, _P, _P, _P, _SZ, _P]),
@@ -89,6 +91,9 @@ _SIGS = {
     "ogs_radix_sort_pairs_noalloc": (C.c_int, [_P, _P, _P, _I64, _I32, _I32, _P]),
     "ogs_proposal_gate_scratch_bytes": (_SZ, [_I64]),
     "ogs_proposal_gate": (C.c_int, [_P, _P, _P, _I64, _I32, _I32, C.POINTER(Camera),
+                                    C.POINTER(Proposal), C.c_float, _P, _P, _I64, _P, _P, _P,
+                                    _P, _P, _SZ, _P]),
+    "ogs_proposal_gate_bf16": (C.c_int, [_P, _P, _P, _I64, _I32, _I32, C.POINTER(Camera),
                                     C.POINTER(Proposal), C.c_float, _P, _P, _I64, _P, _P, _P,
                                     _P, _P, _SZ, _P]),
     "ogs_proposal_train_scratch_bytes": (_SZ, []),
@@ -210,12 +215,13 @@ def decode_bf16(pos, feat, offs, lv, N, mlp, cam, sel_idx, sel_w, sel_cap, count
 
 
 def project_bin(g, n_gauss, means_relative, cam, rec, depth_key, rect, tiles, counts=None,
-                stream=None):
+                stream=None, tile_count=None):
     c = cam if isinstance(cam, Camera) else camera(cam)
     gs = g if isinstance(g, Gaussians) else gaussians_struct(g)
     _check(lib().ogs_project_bin(C.byref(gs), int(n_gauss), int(means_relative), C.byref(c),
                                  _ptr(rec), _ptr(depth_key), _ptr(rect), _ptr(tiles),
-                                 _ptr(counts), _stream(stream)), "ogs_project_bin")
+                                 _ptr(tile_count), _ptr(counts), _stream(stream)),
+           "ogs_project_bin")
 
 
 def sort_scratch_bytes(g_cap, pair_cap, n_tiles):
@@ -223,8 +229,9 @@ def sort_scratch_bytes(g_cap, pair_cap, n_tiles):
 
 
 def sort(depth_key, rect, tiles, g_cap, n_gauss, grid_x, grid_y, pair_gauss, tile_range,
-         pair_cap, counts, scratch, stream=None):
-    _check(lib().ogs_sort(_ptr(depth_key), _ptr(rect), _ptr(tiles), int(g_cap), int(n_gauss),
+         pair_cap, counts, scratch, stream=None, tile_count=None):
+    _check(lib().ogs_sort(_ptr(depth_key), _ptr(rect), _ptr(tiles), _ptr(tile_count),
+                          int(g_cap), int(n_gauss),
                           int(grid_x), int(grid_y), _ptr(pair_gauss), _ptr(tile_range),
                           int(pair_cap), _ptr(counts), _ptr(scratch), scratch.numel(),
                           _stream(stream)), "ogs_sort")
@@ -266,17 +273,18 @@ def project_bwd(g, n_gauss, means_relative, cam, rect, drec, dmeans, dscales, dq
                                  _ptr(dquats), _ptr(counts), _stream(stream)), "ogs_project_bwd")
 
 
-def decode_bwd_scratch_bytes():
-    return int(lib().ogs_decode_bwd_scratch_bytes())
+def decode_bwd_scratch_bytes(sel_cap):
+    return int(lib().ogs_decode_bwd_scratch_bytes(int(sel_cap)))
 
 
-def decode_bwd(pos, feat, offs, lv, N, mlp, cam, sel_idx, sel_w, counts, dmeans, dscales,
-               dquats, drec, dfeat, doffs, dlv, dmlp, scratch, stream=None):
+def decode_bwd(pos, feat, offs, lv, N, mlp, cam, sel_idx, sel_w, sel_cap, counts, dmeans,
+               dscales, dquats, drec, dfeat, doffs, dlv, dmlp, scratch, stream=None):
     c = cam if isinstance(cam, Camera) else camera(cam)
     m = mlp if isinstance(mlp, MLP) else mlp_struct(mlp)
     dm = dmlp if isinstance(dmlp, MLP) else mlp_struct(dmlp)
     _check(lib().ogs_decode_bwd(_ptr(pos), _ptr(feat), _ptr(offs), _ptr(lv), int(N), C.byref(m),
-                                C.byref(c), _ptr(sel_idx), _ptr(sel_w), _ptr(counts),
+                                C.byref(c), _ptr(sel_idx), _ptr(sel_w), int(sel_cap),
+                                _ptr(counts),
                                 _ptr(dmeans), _ptr(dscales), _ptr(dquats), _ptr(drec),
                                 _ptr(dfeat), _ptr(doffs), _ptr(dlv), C.byref(dm), _ptr(scratch),
                                 scratch.numel(), _stream(stream)), "ogs_decode_bwd")
@@ -329,14 +337,16 @@ def proposal_gate_scratch_bytes(sel_cap):
 
 
 def proposal_gate(pos, level, feat, N, NL, k, cam, net, p_star, sel_in, w_in, sel_cap, counts,
-                  sel_out, w_out, p_out, scratch, stream=None):
+                  sel_out, w_out, p_out, scratch, stream=None, bf16=False):
+    """ogs_proposal_gate, or ogs_proposal_gate_bf16 (tensor-core scoring) when bf16."""
     c = cam if isinstance(cam, Camera) else camera(cam)
     n = net if isinstance(net, Proposal) else proposal_struct(net)
-    _check(lib().ogs_proposal_gate(_ptr(pos), _ptr(level), _ptr(feat), int(N), int(NL), int(k),
-                                   C.byref(c), C.byref(n), float(p_star), _ptr(sel_in),
-                                   _ptr(w_in), int(sel_cap), _ptr(counts), _ptr(sel_out),
-                                   _ptr(w_out), _ptr(p_out), _ptr(scratch), scratch.numel(),
-                                   _stream(stream)), "ogs_proposal_gate")
+    name = "ogs_proposal_gate_bf16" if bf16 else "ogs_proposal_gate"
+    _check(getattr(lib(), name)(_ptr(pos), _ptr(level), _ptr(feat), int(N), int(NL), int(k),
+                                C.byref(c), C.byref(n), float(p_star), _ptr(sel_in),
+                                _ptr(w_in), int(sel_cap), _ptr(counts), _ptr(sel_out),
+                                _ptr(w_out), _ptr(p_out), _ptr(scratch), scratch.numel(),
+                                _stream(stream)), name)
 
 
 def proposal_train_scratch_bytes():

@@ -3,10 +3,12 @@
 // One CTA of 4 warps per tile; each thread blends two vertically adjacent pixels (warps cover
 // compact 8x8 blocks, so pixels that saturate together share a warp).  The tile's list is
 // consumed in batches of 256 records gathered into shared memory, converted once per batch to
-// pre-scaled coefficients so that one (pixel, Gaussian) evaluation is: offset, a 5-operation
-// quadratic form, the exponent-bound skip test, and only for surviving pairs one ex2 and the
-// compositing update.  The CTA leaves as soon as every pixel has saturated (barrier vote).
-// The kernel is bound by instruction issue (FP32 + MUFU), not by memory.
+// pre-scaled coefficients and to a mask of the 8x8 blocks that the record's alpha >= 1/255
+// ellipse can reach; each warp then walks, in list order, only the records whose mask holds
+// its block.  One (pixel, Gaussian) evaluation is: offset, a 5-operation quadratic form, the
+// exponent-bound skip test, and only for surviving pairs one ex2 and the compositing update.
+// The CTA leaves as soon as every pixel has saturated (barrier vote).  The kernel is bound by
+// instruction issue (FP32 + MUFU), not by memory.
 #include "blend_common.cuh"
 
 namespace ogs {
@@ -24,16 +26,20 @@ __global__ void __launch_bounds__(kThreads) blend_fwd_kernel(
     __shared__ float4 s_a[kBatch];
     __shared__ float4 s_b[kBatch];
     __shared__ float2 s_c[kBatch];
+    __shared__ uint8_t s_m[kBatch];
+    __shared__ uint8_t s_list[kThreads / 32][kBatch];
     __shared__ uint32_t s_anchor[kMaxC ? kBatch : 1];
     const int tile = blockIdx.x;
     int lx, ly;
     pixels_of(threadIdx.x, lx, ly);
-    const int px = (tile % gx) * kTile + lx;
-    const int py = (tile / gx) * kTile + ly;
+    const int tx0 = (tile % gx) * kTile, ty0 = (tile / gx) * kTile;
+    const int px = tx0 + lx;
+    const int py = ty0 + ly;
     const bool in0 = px < W && py < H, in1 = px < W && py + 1 < H;
     const float fx = (float)px, fy = (float)py;
     const uint2 range = tile_range[tile];
     const int n = (int)(range.y - range.x);
+    uint8_t* list = s_list[threadIdx.x >> 5];
     float T0 = 1.f, T1 = 1.f, C00 = 0.f, C01 = 0.f, C02 = 0.f, C10 = 0.f, C11 = 0.f, C12 = 0.f;
     int last0 = 0, last1 = 0, stop0 = n, stop1 = n;
     bool done0 = !in0, done1 = !in1;
@@ -41,16 +47,19 @@ __global__ void __launch_bounds__(kThreads) blend_fwd_kernel(
         if (__syncthreads_count(done0 && done1) == kThreads) break;
         for (int e = threadIdx.x; e < kBatch && b0 + e < n; e += kThreads) {
             const uint32_t g = pair_gauss[range.x + b0 + e];
-            const Rec r = load_rec(rec, g);
+            const Rec r = load_rec(rec, g, (float)tx0, (float)ty0);
             s_a[e] = r.A;
             s_b[e] = r.B;
             s_c[e] = r.C;
+            s_m[e] = (uint8_t)r.blocks;
             if (kMaxC) s_anchor[e] = sel_idx[g / (uint32_t)k];
         }
         __syncthreads();
         const int cnt = min(kBatch, n - b0);
-        for (int j = 0; j < cnt; ++j) {
+        const int nw = warp_list(s_m, cnt, list);
+        for (int q = 0; q < nw; ++q) {
             if (!kMaxC && done0 && done1) break;
+            const int j = list[q];
             const float4 A = s_a[j];
             const float4 B = s_b[j];
             const float2 Cc = s_c[j];

@@ -6,8 +6,10 @@
 // recovering T_i = T_{i+1} / (1 - a_i) from the final transmittance instead of storing
 // per-pair values (1 - a_i >= 0.01 because a is clamped to 0.99).  a = min(0.99, o G) has
 // zero derivative where clamped.  Same tile/pixel mapping and skip test as the forward (two
-// pixels per thread); a thread's two contributions are summed, then a warp's with shuffles,
-// before one atomic add per warp and Gaussian.
+// pixels per thread, each warp walking only the records whose alpha >= 1/255 ellipse can
+// reach its 8x8 block); a thread's two contributions are summed, then a warp's nine sums
+// with a recursive-halving shuffle reduction, and nine lanes add them with one atomic
+// instruction per warp and Gaussian.
 #include "blend_common.cuh"
 
 namespace ogs {
@@ -15,13 +17,25 @@ namespace {
 
 using namespace blend;
 
-__device__ __forceinline__ float warp_sum(float v) {
+// Sums each of 16 per-lane values over the warp by recursive halving: at every step a lane
+// keeps half of its values and sends the other half to its partner, so 8 + 4 + 2 + 1 + 1
+// shuffles replace 16 x 5.  On return, lane 2k holds the warp total of value k.
+__device__ __forceinline__ float warp_sum16(float (&v)[16]) {
+    const unsigned lane = lane_id();
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int half = 8; half >= 1; half >>= 1) {
+        const bool upper = lane & (2u * half);          // partner at xor 2*half
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const float send = upper ? v[i] : v[half + i];
+            const float keep = upper ? v[half + i] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2 * half);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
-// one pixel's contribution of one Gaussian, accumulated into g[9]:
+// one pixel's contribution of one Gaussian, accumulated into g[0..8] (g[9..15] stay 0):
 // du dv da db dc do dr dg db (w.r.t. the unscaled record)
 struct PixState {
     float T, S0, S1, S2, d0, d1, d2;
@@ -30,7 +44,7 @@ struct PixState {
 
 __device__ __forceinline__ bool pixel_step(PixState& s, int idx, float p2, const float4& A,
                                            const float4& B, const float2& Cc, float dx, float dy,
-                                           float (&g)[9]) {
+                                           float (&g)[16]) {
     if (idx >= s.last || !(p2 <= 0.f && p2 >= Cc.y)) return false;
     const float raw = raw_alpha(B.y, p2);
     const float alpha = fminf(0.99f, raw);
@@ -65,12 +79,16 @@ __global__ void __launch_bounds__(kThreads) blend_bwd_kernel(
     __shared__ float4 s_b[kBatch];
     __shared__ float2 s_c[kBatch];
     __shared__ uint32_t s_g[kBatch];
+    __shared__ uint8_t s_m[kBatch];
+    __shared__ uint8_t s_list[kThreads / 32][kBatch];
     __shared__ int s_maxlast;
     const int tile = blockIdx.x;
     int lx, ly;
     pixels_of(threadIdx.x, lx, ly);
-    const int px = (tile % gx) * kTile + lx;
-    const int py = (tile / gx) * kTile + ly;
+    const int tx0 = (tile % gx) * kTile, ty0 = (tile / gx) * kTile;
+    const int px = tx0 + lx;
+    const int py = ty0 + ly;
+    uint8_t* list = s_list[threadIdx.x >> 5];
     const float fx = (float)px, fy = (float)py;
     const uint2 range = tile_range[tile];
     const size_t plane = (size_t)W * H;
@@ -96,14 +114,17 @@ __global__ void __launch_bounds__(kThreads) blend_bwd_kernel(
         __syncthreads();
         for (int e = threadIdx.x; lo + e < top; e += kThreads) {
             const uint32_t g = pair_gauss[range.x + lo + e];
-            const Rec r = load_rec(rec, g);
+            const Rec r = load_rec(rec, g, (float)tx0, (float)ty0);
             s_g[e] = g;
             s_a[e] = r.A;
             s_b[e] = r.B;
             s_c[e] = r.C;
+            s_m[e] = (uint8_t)r.blocks;
         }
         __syncthreads();
-        for (int j = top - lo - 1; j >= 0; --j) {
+        const int nw = warp_list(s_m, top - lo, list);
+        for (int it = nw - 1; it >= 0; --it) {
+            const int j = list[it];
             const int idx = lo + j;        // list position of this entry
             const float4 A = s_a[j];
             const float4 B = s_b[j];
@@ -111,17 +132,15 @@ __global__ void __launch_bounds__(kThreads) blend_bwd_kernel(
             const float dx = A.x - fx;
             const float dy0 = A.y - fy, dy1 = dy0 - 1.0f;
             const float ax = __fmul_rn(A.z, dx);
-            float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            float g[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f,
+                           0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             bool act = pixel_step(q[0], idx, power2(ax, dx, dy0, A.w, B.x), A, B, Cc, dx, dy0, g);
             act |= pixel_step(q[1], idx, power2(ax, dx, dy1, A.w, B.x), A, B, Cc, dx, dy1, g);
             if (__any_sync(0xffffffffu, act)) {
-#pragma unroll
-                for (int c = 0; c < 9; ++c) g[c] = warp_sum(g[c]);
-                if (lane == 0) {
-                    float* d = drec + 9 * (size_t)s_g[j];
-#pragma unroll
-                    for (int c = 0; c < 9; ++c) atomicAdd(d + c, g[c]);
-                }
+                const float tot = warp_sum16(g);
+                // lane 2c adds component c: one atomic instruction for the nine sums
+                if ((lane & 1u) == 0 && (lane >> 1) < 9)
+                    atomicAdd(drec + 9 * (size_t)s_g[j] + (lane >> 1), tot);
             }
         }
     }

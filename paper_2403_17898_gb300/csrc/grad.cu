@@ -173,6 +173,12 @@ constexpr int kOffB1 = kNW1;
 constexpr int kOffW2 = kOffB1 + kNB1;
 constexpr int kOffB2 = kOffW2 + kNW2;
 
+// per-anchor rows handed from the row pass to the weight pass (f32, 16-byte aligned rows)
+constexpr int kRowY = 112;    // dL/dy of the 110 stacked outputs (+2 zero)
+constexpr int kRowH = 96;     // hidden activations of the three decoders
+constexpr int kRowP = 96;     // dL/d(pre-activation) of the three decoders
+constexpr int kRowZ = 40;     // decoder input z (36, +4 zero)
+
 struct DbArgs {
     const float* pos;
     const float* feat;
@@ -190,207 +196,386 @@ struct DbArgs {
     float* dfeat;
     float* doffs;
     float* dlv;
-    float* partial;      // [gridDim.x][kNWeights]
+    float* rowY;         // [sel_cap][kRowY]
+    float* rowH;         // [sel_cap][kRowH]
+    float* rowP;         // [sel_cap][kRowP]
+    float* rowZ;         // [sel_cap][kRowZ]
+    float* partial;      // [kDbBlocks][kNWeights]
 };
 
 __device__ __forceinline__ float sigm(float x) { return 1.0f / (1.0f + __expf(-x)); }
 
 // out rows of decoder m (opacity 0, colour 1, covariance 2) inside the 110 stacked outputs
 __device__ __forceinline__ int out_base(int m) { return m == 0 ? 0 : (m == 1 ? kK : 4 * kK); }
-__device__ __forceinline__ int out_count(int m) { return m == 0 ? kK : (m == 1 ? 3 * kK : 7 * kK); }
+__device__ __forceinline__ int dec_of(int row) { return row < kK ? 0 : (row < 4 * kK ? 1 : 2); }
 
-__global__ void __launch_bounds__(kDbThreads) decode_bwd_kernel(DbArgs a) {
-    extern __shared__ __align__(16) float sm[];
-    float* acc = sm;                                   // [kNWeights] block accumulators
-    float* sZ = acc + kNWeights;                       // [threads][kDin]
-    float* sH = sZ + kDbThreads * kDin;                // [threads][kH]
-    float* sP = sH + kDbThreads * kH;                  // [threads][kH]  d pre-activation
-    float* sY = sP + kDbThreads * kH;                  // [threads][7k]  d outputs of one decoder
-    for (int i = threadIdx.x; i < kNWeights; i += blockDim.x) acc[i] = 0.f;
+// Row pass: one thread per selected anchor recomputes its three decoders (weights in shared
+// memory, broadcast reads) and chains the per-Gaussian gradients into dy (110), the hidden
+// pre-activation gradients dp (96) and the feature gradient (dfeat, doffs, dlv accumulate;
+// each anchor appears once per view, so no atomics).  dy, h, dp and z are written as rows
+// for the weight pass.  Layer 1 runs in outer-product form over a streamed input (only the 32
+// hidden accumulators live in registers), so the thread keeps h, dh and dz (96 values).
+__global__ void __launch_bounds__(kDbThreads, 3) decode_bwd_rows(DbArgs a) {
+    __shared__ __align__(16) float sW1t[3 * kDin * kH];   // [m][i][o]
+    __shared__ __align__(16) float sW1[3 * kH * kDin];    // [m][o][i]
+    __shared__ float sB1[kNB1];
+    __shared__ __align__(16) float sW2[kNOut * kH];
+    __shared__ float sB2[kNOut];
+    for (int e = threadIdx.x; e < 3 * kH * kDin; e += kDbThreads) {
+        const float v = a.mlp.w1[e];
+        sW1[e] = v;
+        const int m = e / (kH * kDin), o = (e / kDin) % kH, i = e % kDin;
+        sW1t[(m * kDin + i) * kH + o] = v;
+    }
+    for (int e = threadIdx.x; e < kNOut * kH; e += kDbThreads)
+        sW2[e] = e < kK * kH ? a.mlp.w2_op[e]
+                             : (e < 4 * kK * kH ? a.mlp.w2_col[e - kK * kH]
+                                                : a.mlp.w2_cov[e - 4 * kK * kH]);
+    for (int e = threadIdx.x; e < kNB1; e += kDbThreads) sB1[e] = a.mlp.b1[e];
+    for (int e = threadIdx.x; e < kNOut; e += kDbThreads)
+        sB2[e] = e < kK ? a.mlp.b2_op[e] : (e < 4 * kK ? a.mlp.b2_col[e - kK] : a.mlp.b2_cov[e - 4 * kK]);
+    __syncthreads();
     const uint32_t M = a.counts->n_selected;
     const Cam& c = a.cam;
-    const int t = threadIdx.x;
-    const float* W1 = a.mlp.w1;
-    for (uint32_t base = blockIdx.x * kDbThreads; base < M; base += gridDim.x * kDbThreads) {
-        const uint32_t r = base + t;
-        const bool valid = r < M;
-        uint32_t j = 0;
-        float w = 0.f, z[kDin], dz[kF], lvv[3] = {0.f, 0.f, 0.f}, dlv[3] = {0.f, 0.f, 0.f};
+    for (uint32_t r = blockIdx.x * kDbThreads + threadIdx.x; r < M; r += gridDim.x * kDbThreads) {
+        const uint32_t j = a.sel_idx[r];
+        const float w = a.sel_w[r];
+        const float4* f4 = reinterpret_cast<const float4*>(a.feat + (size_t)j * kF);
+        float dz[kF], lvv[3], dlv[3] = {0.f, 0.f, 0.f}, zc[4];
+        float dv[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            dv[q] = a.pos[3 * (size_t)j + q] - c.c[q];
+            lvv[q] = a.lv[3 * (size_t)j + q];
+        }
+        const float d = sqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+        zc[0] = dv[0] / d; zc[1] = dv[1] / d; zc[2] = dv[2] / d; zc[3] = d;
 #pragma unroll
         for (int i = 0; i < kF; ++i) dz[i] = 0.f;
-        if (valid) {
-            j = a.sel_idx[r];
-            w = a.sel_w[r];
+        {
+            float4* zr = reinterpret_cast<float4*>(a.rowZ + (size_t)r * kRowZ);
 #pragma unroll
-            for (int i = 0; i < kF; ++i) z[i] = a.feat[(size_t)j * kF + i];
-            float dv[3];
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                dv[q] = a.pos[3 * (size_t)j + q] - c.c[q];
-                lvv[q] = a.lv[3 * (size_t)j + q];
-            }
-            const float d = sqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
-            z[kF] = dv[0] / d; z[kF + 1] = dv[1] / d; z[kF + 2] = dv[2] / d; z[kF + 3] = d;
-        } else {
-#pragma unroll
-            for (int i = 0; i < kDin; ++i) z[i] = 0.f;
+            for (int i = 0; i < kF / 4; ++i) zr[i] = f4[i];
+            zr[kF / 4] = make_float4(zc[0], zc[1], zc[2], zc[3]);
+            zr[kF / 4 + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-#pragma unroll
-        for (int i = 0; i < kDin; ++i) sZ[t * kDin + i] = z[i];
+        float* yrow = a.rowY + (size_t)r * kRowY;
+        yrow[kNOut] = 0.f;
+        yrow[kNOut + 1] = 0.f;
         const size_t g0 = (size_t)r * kK;
+#pragma unroll 1
         for (int m = 0; m < 3; ++m) {
-            const float* w1 = W1 + m * kH * kDin;
-            const float* b1 = a.mlp.b1 + m * kH;
             float h[kH], dh[kH];
-            unsigned mask = 0;
+#pragma unroll
+            for (int o = 0; o < kH; ++o) h[o] = sB1[m * kH + o];
+            // layer 1, outer-product form: h += W1[:, i] z_i over the streamed input
+#pragma unroll 1
+            for (int i4 = 0; i4 < kDin / 4; ++i4) {
+                const float4 zv = i4 < kF / 4 ? f4[i4] : make_float4(zc[0], zc[1], zc[2], zc[3]);
+                const float zz[4] = {zv.x, zv.y, zv.z, zv.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float4* col = reinterpret_cast<const float4*>(sW1t + (m * kDin + 4 * i4 + u) * kH);
+#pragma unroll
+                    for (int q = 0; q < kH / 4; ++q) {
+                        const float4 wv = col[q];
+                        h[4 * q] = fmaf(wv.x, zz[u], h[4 * q]);
+                        h[4 * q + 1] = fmaf(wv.y, zz[u], h[4 * q + 1]);
+                        h[4 * q + 2] = fmaf(wv.z, zz[u], h[4 * q + 2]);
+                        h[4 * q + 3] = fmaf(wv.w, zz[u], h[4 * q + 3]);
+                    }
+                }
+            }
+            uint32_t mask = 0;
 #pragma unroll
             for (int o = 0; o < kH; ++o) {
-                float p = b1[o];
-#pragma unroll
-                for (int i = 0; i < kDin; ++i) p = fmaf(w1[o * kDin + i], z[i], p);
-                h[o] = fmaxf(p, 0.f);
-                mask |= (p > 0.f ? 1u : 0u) << o;
+                mask |= (h[o] > 0.f ? 1u : 0u) << o;
+                h[o] = fmaxf(h[o], 0.f);
                 dh[o] = 0.f;
             }
-            const int nout = out_count(m);
-            const float* w2 = m == 0 ? a.mlp.w2_op : (m == 1 ? a.mlp.w2_col : a.mlp.w2_cov);
-            const float* b2 = m == 0 ? a.mlp.b2_op : (m == 1 ? a.mlp.b2_col : a.mlp.b2_cov);
-            // per Gaussian: outputs, their gradients, and the chain into the hidden layer
+            {
+                float4* hr = reinterpret_cast<float4*>(a.rowH + (size_t)r * kRowH + m * kH);
+#pragma unroll
+                for (int i = 0; i < kH / 4; ++i)
+                    hr[i] = make_float4(h[4 * i], h[4 * i + 1], h[4 * i + 2], h[4 * i + 3]);
+            }
+            const int per = m == 0 ? 1 : (m == 1 ? 3 : 7);
+#pragma unroll 1
             for (int i = 0; i < kK; ++i) {
-                const int per = m == 0 ? 1 : (m == 1 ? 3 : 7);
                 float y[7], dy[7];
 #pragma unroll
                 for (int e = 0; e < 7; ++e) {
-                    if (e >= per) { y[e] = 0.f; continue; }
-                    const int row = per * i + e;
-                    float v = b2[row];
+                    y[e] = 0.f;
+                    dy[e] = 0.f;
+                    if (e < per) {
+                        const int row = out_base(m) + per * i + e;
+                        const float4* wr = reinterpret_cast<const float4*>(sW2 + row * kH);
+                        float v = sB2[row];
 #pragma unroll
-                    for (int o = 0; o < kH; ++o) v = fmaf(w2[row * kH + o], h[o], v);
-                    y[e] = v;
+                        for (int q = 0; q < kH / 4; ++q) {
+                            const float4 wv = wr[q];
+                            v = fmaf(wv.x, h[4 * q], v);
+                            v = fmaf(wv.y, h[4 * q + 1], v);
+                            v = fmaf(wv.z, h[4 * q + 2], v);
+                            v = fmaf(wv.w, h[4 * q + 3], v);
+                        }
+                        y[e] = v;
+                    }
                 }
+                const size_t g = g0 + i;
+                if (m == 0) {
+                    const float th = tanhf(y[0]);
+                    if (w * th > 0.f) dy[0] = a.drec[9 * g + 5] * w * (1.f - th * th);
+                } else if (m == 1) {
 #pragma unroll
-                for (int e = 0; e < 7; ++e) dy[e] = 0.f;
-                if (valid) {
-                    const size_t g = g0 + i;
-                    if (m == 0) {
-                        const float th = tanhf(y[0]);
-                        if (w * th > 0.f) dy[0] = a.drec[9 * g + 5] * w * (1.f - th * th);
-                    } else if (m == 1) {
+                    for (int e = 0; e < 3; ++e) {
+                        const float sg = sigm(y[e]);
+                        dy[e] = a.drec[9 * g + 6 + e] * sg * (1.f - sg);
+                    }
+                } else {
 #pragma unroll
-                        for (int e = 0; e < 3; ++e) {
-                            const float sg = sigm(y[e]);
-                            dy[e] = a.drec[9 * g + 6 + e] * sg * (1.f - sg);
-                        }
-                    } else {
+                    for (int e = 0; e < 3; ++e) {
+                        const float sg = sigm(y[e]);
+                        const float gsc = a.dscales[3 * g + e];
+                        dlv[e] += gsc * sg;
+                        dy[e] = gsc * lvv[e] * sg * (1.f - sg);
+                    }
+                    const float n2 = y[3] * y[3] + y[4] * y[4] + y[5] * y[5] + y[6] * y[6];
+                    const float inv = 1.0f / sqrtf(n2);
+                    const float4 gq = *reinterpret_cast<const float4*>(a.dquats + 4 * g);
+                    const float qn[4] = {y[3] * inv, y[4] * inv, y[5] * inv, y[6] * inv};
+                    const float gqa[4] = {gq.x, gq.y, gq.z, gq.w};
+                    const float dot = qn[0] * gqa[0] + qn[1] * gqa[1] + qn[2] * gqa[2] + qn[3] * gqa[3];
 #pragma unroll
-                        for (int e = 0; e < 3; ++e) {
-                            const float sg = sigm(y[e]);
-                            const float gsc = a.dscales[3 * g + e];
-                            dlv[e] += gsc * sg;
-                            dy[e] = gsc * lvv[e] * sg * (1.f - sg);
-                        }
-                        const float n2 = y[3] * y[3] + y[4] * y[4] + y[5] * y[5] + y[6] * y[6];
-                        const float inv = 1.0f / sqrtf(n2);
-                        const float4 gq = *reinterpret_cast<const float4*>(a.dquats + 4 * g);
-                        const float qn[4] = {y[3] * inv, y[4] * inv, y[5] * inv, y[6] * inv};
-                        const float gqa[4] = {gq.x, gq.y, gq.z, gq.w};
-                        const float dot = qn[0] * gqa[0] + qn[1] * gqa[1] + qn[2] * gqa[2] + qn[3] * gqa[3];
+                    for (int e = 0; e < 4; ++e) dy[3 + e] = (gqa[e] - qn[e] * dot) * inv;
+                    // positions: mu = x_v + O * l_v
+                    const float* O = a.offs + ((size_t)j * kK + i) * 3;
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) dy[3 + e] = (gqa[e] - qn[e] * dot) * inv;
-                        // positions: mu = x_v + O * l_v
-                        const float* O = a.offs + ((size_t)j * kK + i) * 3;
-#pragma unroll
-                        for (int e = 0; e < 3; ++e) {
-                            const float gmu = a.dmeans[3 * g + e];
-                            a.doffs[((size_t)j * kK + i) * 3 + e] += gmu * lvv[e];
-                            dlv[e] += gmu * O[e];
-                        }
+                    for (int e = 0; e < 3; ++e) {
+                        const float gmu = a.dmeans[3 * g + e];
+                        a.doffs[((size_t)j * kK + i) * 3 + e] += gmu * lvv[e];
+                        dlv[e] += gmu * O[e];
                     }
                 }
 #pragma unroll
                 for (int e = 0; e < 7; ++e) {
-                    if (e >= per) continue;
-                    const int row = per * i + e;
-                    sY[t * (7 * kK) + row] = dy[e];
+                    if (e < per) {
+                        const int row = out_base(m) + per * i + e;
+                        yrow[row] = dy[e];
+                        const float4* wr = reinterpret_cast<const float4*>(sW2 + row * kH);
 #pragma unroll
-                    for (int o = 0; o < kH; ++o) dh[o] = fmaf(w2[row * kH + o], dy[e], dh[o]);
+                        for (int q = 0; q < kH / 4; ++q) {
+                            const float4 wv = wr[q];
+                            dh[4 * q] = fmaf(wv.x, dy[e], dh[4 * q]);
+                            dh[4 * q + 1] = fmaf(wv.y, dy[e], dh[4 * q + 1]);
+                            dh[4 * q + 2] = fmaf(wv.z, dy[e], dh[4 * q + 2]);
+                            dh[4 * q + 3] = fmaf(wv.w, dy[e], dh[4 * q + 3]);
+                        }
+                    }
                 }
             }
-            // hidden: relu mask, then into the input features
+            // through the ReLU, then into the features: dz_i += sum_o W1[o][i] dp_o
+#pragma unroll
+            for (int o = 0; o < kH; ++o) dh[o] = (mask >> o) & 1u ? dh[o] : 0.f;
+            {
+                float4* pr = reinterpret_cast<float4*>(a.rowP + (size_t)r * kRowP + m * kH);
+#pragma unroll
+                for (int i = 0; i < kH / 4; ++i)
+                    pr[i] = make_float4(dh[4 * i], dh[4 * i + 1], dh[4 * i + 2], dh[4 * i + 3]);
+            }
 #pragma unroll
             for (int o = 0; o < kH; ++o) {
-                const float dp = (mask >> o) & 1u ? dh[o] : 0.f;
-                sH[t * kH + o] = h[o];
-                sP[t * kH + o] = dp;
+                const float4* wr = reinterpret_cast<const float4*>(sW1 + (m * kH + o) * kDin);
 #pragma unroll
-                for (int i = 0; i < kF; ++i) dz[i] = fmaf(w1[o * kDin + i], dp, dz[i]);
+                for (int i = 0; i < kF / 4; ++i) {
+                    const float4 wv = wr[i];
+                    dz[4 * i] = fmaf(wv.x, dh[o], dz[4 * i]);
+                    dz[4 * i + 1] = fmaf(wv.y, dh[o], dz[4 * i + 1]);
+                    dz[4 * i + 2] = fmaf(wv.z, dh[o], dz[4 * i + 2]);
+                    dz[4 * i + 3] = fmaf(wv.w, dh[o], dz[4 * i + 3]);
+                }
             }
-            __syncthreads();
-            // block products: dW2_m += dY^T H, db2_m += sum dY, dW1_m += dP^T Z, db1_m += sum dP
-            const int nv = min((uint32_t)kDbThreads, M - base);
-            float* aw2 = acc + kOffW2 + out_base(m) * kH;
-            float* ab2 = acc + kOffB2 + out_base(m);
-            for (int e = t; e < nout * kH; e += kDbThreads) {
-                const int row = e / kH, o = e % kH;
-                float s = 0.f;
-                for (int q = 0; q < nv; ++q) s = fmaf(sY[q * (7 * kK) + row], sH[q * kH + o], s);
-                aw2[e] += s;
-            }
-            for (int e = t; e < nout; e += kDbThreads) {
-                float s = 0.f;
-                for (int q = 0; q < nv; ++q) s += sY[q * (7 * kK) + e];
-                ab2[e] += s;
-            }
-            float* aw1 = acc + m * kH * kDin;
-            float* ab1 = acc + kOffB1 + m * kH;
-            for (int e = t; e < kH * kDin; e += kDbThreads) {
-                const int o = e / kDin, i = e % kDin;
-                float s = 0.f;
-                for (int q = 0; q < nv; ++q) s = fmaf(sP[q * kH + o], sZ[q * kDin + i], s);
-                aw1[e] += s;
-            }
-            for (int e = t; e < kH; e += kDbThreads) {
-                float s = 0.f;
-                for (int q = 0; q < nv; ++q) s += sP[q * kH + e];
-                ab1[e] += s;
-            }
-            __syncthreads();
         }
-        if (valid) {
+        float4* df = reinterpret_cast<float4*>(a.dfeat + (size_t)j * kF);
 #pragma unroll
-            for (int i = 0; i < kF; ++i) a.dfeat[(size_t)j * kF + i] += dz[i];
-#pragma unroll
-            for (int e = 0; e < 3; ++e) a.dlv[3 * (size_t)j + e] += dlv[e];
+        for (int i = 0; i < kF / 4; ++i) {
+            float4 v = df[i];
+            v.x += dz[4 * i]; v.y += dz[4 * i + 1]; v.z += dz[4 * i + 2]; v.w += dz[4 * i + 3];
+            df[i] = v;
         }
+#pragma unroll
+        for (int e = 0; e < 3; ++e) a.dlv[3 * (size_t)j + e] += dlv[e];
     }
-    __syncthreads();
-    float* out = a.partial + (size_t)blockIdx.x * kNWeights;
-    for (int i = threadIdx.x; i < kNWeights; i += blockDim.x) out[i] = acc[i];
 }
 
-// dmlp[e] += sum over blocks of partial[b][e] (fixed order: deterministic)
-__global__ void reduce_partials(const float* __restrict__ partial, int nblocks, ogs_mlp grads) {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kNWeights; e += gridDim.x * blockDim.x) {
-        float s = 0.f;
-        for (int b = 0; b < nblocks; ++b) s += partial[(size_t)b * kNWeights + e];
-        float* dst;
-        int i = e;
-        if (i < kNW1) dst = const_cast<float*>(grads.w1) + i;
-        else if ((i -= kNW1) < kNB1) dst = const_cast<float*>(grads.b1) + i;
-        else if ((i -= kNB1) < kK * kH) dst = const_cast<float*>(grads.w2_op) + i;
-        else if ((i -= kK * kH) < 3 * kK * kH) dst = const_cast<float*>(grads.w2_col) + i;
-        else if ((i -= 3 * kK * kH) < 7 * kK * kH) dst = const_cast<float*>(grads.w2_cov) + i;
-        else if ((i -= 7 * kK * kH) < kK) dst = const_cast<float*>(grads.b2_op) + i;
-        else if ((i -= kK) < 3 * kK) dst = const_cast<float*>(grads.b2_col) + i;
-        else dst = const_cast<float*>(grads.b2_cov) + (i - 3 * kK);
-        *dst += s;
+// Weight pass: dW2 = dY^T H (block-diagonal), dW1 = dP^T Z, db2 = sum dY, db1 = sum dP over
+// the selected anchors.  Split over anchors: each CTA stages chunks of kWChunk rows in shared
+// memory and accumulates fixed output items in registers (4 columns per item: 2 shared loads
+// per 4 FMAs); its totals go to its partial row, summed across CTAs in a fixed order.
+constexpr int kWThreads = 256;
+constexpr int kWChunk = 32;
+constexpr int kItemsW2 = kNOut * (kH / 4);                // 880
+constexpr int kItemsW1 = 3 * kH * (kDin / 4);             // 864
+constexpr int kItems4 = kItemsW2 + kItemsW1;              // 1744
+constexpr int kPerThread4 = (kItems4 + kWThreads - 1) / kWThreads;   // 7
+constexpr int kItems1 = kNOut + kNB1;                     // 206 bias sums
+
+__global__ void __launch_bounds__(kWThreads) decode_bwd_weights(DbArgs a) {
+    __shared__ __align__(16) float sY[kWChunk][kRowY];
+    __shared__ __align__(16) float sH[kWChunk][kRowH];
+    __shared__ __align__(16) float sP[kWChunk][kRowP];
+    __shared__ __align__(16) float sZ[kWChunk][kRowZ];
+    const uint32_t M = a.counts->n_selected;
+    const int t = threadIdx.x;
+    float4 acc[kPerThread4];
+#pragma unroll
+    for (int q = 0; q < kPerThread4; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    float acc1 = 0.f;
+    const uint32_t nchunks = (M + kWChunk - 1) / kWChunk;
+    for (uint32_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const uint32_t r0 = ch * kWChunk;
+        const int nv = (int)min((uint32_t)kWChunk, M - r0);
+        __syncthreads();
+        for (int e = t; e < kWChunk * (kRowY / 4); e += kWThreads) {
+            const int q = e / (kRowY / 4), c4 = e % (kRowY / 4);
+            reinterpret_cast<float4*>(sY[q])[c4] = q < nv
+                ? reinterpret_cast<const float4*>(a.rowY + (size_t)(r0 + q) * kRowY)[c4]
+                : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        for (int e = t; e < kWChunk * (kRowH / 4); e += kWThreads) {
+            const int q = e / (kRowH / 4), c4 = e % (kRowH / 4);
+            const bool in = q < nv;
+            reinterpret_cast<float4*>(sH[q])[c4] = in
+                ? reinterpret_cast<const float4*>(a.rowH + (size_t)(r0 + q) * kRowH)[c4]
+                : make_float4(0.f, 0.f, 0.f, 0.f);
+            reinterpret_cast<float4*>(sP[q])[c4] = in
+                ? reinterpret_cast<const float4*>(a.rowP + (size_t)(r0 + q) * kRowP)[c4]
+                : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        for (int e = t; e < kWChunk * (kRowZ / 4); e += kWThreads) {
+            const int q = e / (kRowZ / 4), c4 = e % (kRowZ / 4);
+            reinterpret_cast<float4*>(sZ[q])[c4] = q < nv
+                ? reinterpret_cast<const float4*>(a.rowZ + (size_t)(r0 + q) * kRowZ)[c4]
+                : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kPerThread4; ++q) {
+            const int item = t + q * kWThreads;
+            if (item < kItemsW2) {
+                const int row = item / (kH / 4), c4 = item % (kH / 4);
+                const int hc = dec_of(row) * kH + 4 * c4;
+                float4 s = acc[q];
+#pragma unroll 8
+                for (int k = 0; k < kWChunk; ++k) {
+                    const float yv = sY[k][row];
+                    const float4 hv = *reinterpret_cast<const float4*>(&sH[k][hc]);
+                    s.x = fmaf(yv, hv.x, s.x); s.y = fmaf(yv, hv.y, s.y);
+                    s.z = fmaf(yv, hv.z, s.z); s.w = fmaf(yv, hv.w, s.w);
+                }
+                acc[q] = s;
+            } else if (item < kItems4) {
+                const int it = item - kItemsW2;
+                const int row = it / (kDin / 4), c4 = it % (kDin / 4);
+                float4 s = acc[q];
+#pragma unroll 8
+                for (int k = 0; k < kWChunk; ++k) {
+                    const float pv = sP[k][row];
+                    const float4 zv = *reinterpret_cast<const float4*>(&sZ[k][4 * c4]);
+                    s.x = fmaf(pv, zv.x, s.x); s.y = fmaf(pv, zv.y, s.y);
+                    s.z = fmaf(pv, zv.z, s.z); s.w = fmaf(pv, zv.w, s.w);
+                }
+                acc[q] = s;
+            }
+        }
+        if (t < kItems1) {
+            float s = 0.f;
+            if (t < kNOut) {
+                for (int k = 0; k < kWChunk; ++k) s += sY[k][t];
+            } else {
+                for (int k = 0; k < kWChunk; ++k) s += sP[k][t - kNOut];
+            }
+            acc1 += s;
+        }
+    }
+    // this CTA's totals -> its partial row (flat layout of the decoder gradients)
+    float* out = a.partial + (size_t)blockIdx.x * kNWeights;
+#pragma unroll
+    for (int q = 0; q < kPerThread4; ++q) {
+        const int item = t + q * kWThreads;
+        const float v4[4] = {acc[q].x, acc[q].y, acc[q].z, acc[q].w};
+        if (item < kItemsW2) {
+            const int row = item / (kH / 4), c4 = item % (kH / 4);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) out[kOffW2 + row * kH + 4 * c4 + e] = v4[e];
+        } else if (item < kItems4) {
+            const int it = item - kItemsW2;
+            const int row = it / (kDin / 4), c4 = it % (kDin / 4);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) out[row * kDin + 4 * c4 + e] = v4[e];
+        }
+    }
+    if (t < kItems1) {
+        if (t < kNOut) out[kOffB2 + t] = acc1;
+        else out[kOffB1 + (t - kNOut)] = acc1;
+    }
+}
+
+// dmlp[e] += sum over blocks of partial[b][e].  A CTA owns 32 consecutive outputs (one per
+// lane, coalesced reads); its 8 warps sum interleaved blocks, then warp 0 adds the 8 warp
+// sums in a fixed order: deterministic.
+constexpr int kRedWarps = 8;
+
+__device__ __forceinline__ float* grad_slot(const ogs_mlp& grads, int e) {
+    int i = e;
+    if (i < kNW1) return const_cast<float*>(grads.w1) + i;
+    if ((i -= kNW1) < kNB1) return const_cast<float*>(grads.b1) + i;
+    if ((i -= kNB1) < kK * kH) return const_cast<float*>(grads.w2_op) + i;
+    if ((i -= kK * kH) < 3 * kK * kH) return const_cast<float*>(grads.w2_col) + i;
+    if ((i -= 3 * kK * kH) < 7 * kK * kH) return const_cast<float*>(grads.w2_cov) + i;
+    if ((i -= 7 * kK * kH) < kK) return const_cast<float*>(grads.b2_op) + i;
+    if ((i -= kK) < 3 * kK) return const_cast<float*>(grads.b2_col) + i;
+    return const_cast<float*>(grads.b2_cov) + (i - 3 * kK);
+}
+
+__global__ void __launch_bounds__(32 * kRedWarps) reduce_partials(const float* __restrict__ partial,
+                                                                  int nblocks, ogs_mlp grads) {
+    __shared__ float s[kRedWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + lane;
+    float acc = 0.f;
+    if (e < kNWeights) {
+#pragma unroll 4
+        for (int b = warp; b < nblocks; b += kRedWarps) acc += partial[(size_t)b * kNWeights + e];
+    }
+    s[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && e < kNWeights) {
+        float t = 0.f;
+#pragma unroll
+        for (int w = 0; w < kRedWarps; ++w) t += s[w][lane];
+        *grad_slot(grads, e) += t;
     }
 }
 
 constexpr int kDbBlocks = 2 * kSmCount;
 
-size_t decode_bwd_smem() {
-    return sizeof(float) * (kNWeights + kDbThreads * (kDin + kH + kH + 7 * kK));
+struct DbScratch {
+    float* partial;
+    float *rowY, *rowH, *rowP, *rowZ;
+};
+
+size_t db_layout(int64_t sel_cap, void* base, DbScratch* s) {
+    Carver cv(base);
+    DbScratch t;
+    const size_t n = (size_t)(sel_cap > 0 ? sel_cap : 1);
+    t.partial = cv.take<float>((size_t)kDbBlocks * kNWeights);
+    t.rowY = cv.take<float>(n * kRowY);
+    t.rowH = cv.take<float>(n * kRowH);
+    t.rowP = cv.take<float>(n * kRowP);
+    t.rowZ = cv.take<float>(n * kRowZ);
+    if (s) *s = t;
+    return cv.off + 256;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -413,18 +598,47 @@ __global__ void l1_kernel(const float* __restrict__ img, const float* __restrict
     if (lane_id() == 0 && loss) atomicAdd(loss, s * scale);
 }
 
-__global__ void adam_kernel(float* __restrict__ p, float* __restrict__ grad, float* __restrict__ m,
-                            float* __restrict__ v, int64_t n, float lr, float b1, float b2,
-                            float eps, float bc1, float bc2, int zero_grad) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const float g = grad[i];
-        const float mi = b1 * m[i] + (1.f - b1) * g;
-        const float vi = b2 * v[i] + (1.f - b2) * g * g;
-        m[i] = mi;
-        v[i] = vi;
-        p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
-        if (zero_grad) grad[i] = 0.f;
+__device__ __forceinline__ void adam_one(float& p, float& g, float& m, float& v, float lr,
+                                         float b1, float b2, float eps, float bc1, float bc2,
+                                         int zero_grad) {
+    m = b1 * m + (1.f - b1) * g;
+    v = b2 * v + (1.f - b2) * g * g;
+    p -= lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+    if (zero_grad) g = 0.f;
+}
+
+// Streaming update: 16-byte vectors when all four arrays are 16-byte aligned (n/4 vectors
+// plus a scalar tail), scalars otherwise.  HBM-bound: 16 B read + 12 B (16 B with zero_grad)
+// written per parameter.
+__global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ p, float* __restrict__ grad,
+                                                   float* __restrict__ m, float* __restrict__ v,
+                                                   int64_t n, float lr, float b1, float b2,
+                                                   float eps, float bc1, float bc2, int zero_grad,
+                                                   int vec) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t first = 0;
+    if (vec) {
+        const int64_t n4 = n / 4;
+        float4* p4 = reinterpret_cast<float4*>(p);
+        float4* g4 = reinterpret_cast<float4*>(grad);
+        float4* m4 = reinterpret_cast<float4*>(m);
+        float4* v4 = reinterpret_cast<float4*>(v);
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+            float4 P = p4[i], G = g4[i], M = m4[i], V = v4[i];
+            adam_one(P.x, G.x, M.x, V.x, lr, b1, b2, eps, bc1, bc2, zero_grad);
+            adam_one(P.y, G.y, M.y, V.y, lr, b1, b2, eps, bc1, bc2, zero_grad);
+            adam_one(P.z, G.z, M.z, V.z, lr, b1, b2, eps, bc1, bc2, zero_grad);
+            adam_one(P.w, G.w, M.w, V.w, lr, b1, b2, eps, bc1, bc2, zero_grad);
+            p4[i] = P; m4[i] = M; v4[i] = V;
+            if (zero_grad) g4[i] = G;
+        }
+        first = 4 * n4;
+    }
+    for (int64_t i = first + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        float P = p[i], G = grad[i], M = m[i], V = v[i];
+        adam_one(P, G, M, V, lr, b1, b2, eps, bc1, bc2, zero_grad);
+        p[i] = P; m[i] = M; v[i] = V;
+        if (zero_grad) grad[i] = G;
     }
 }
 
@@ -448,37 +662,37 @@ extern "C" ogs_status ogs_project_bwd(const ogs_gaussians* g, int64_t n_gauss, i
     return launch_status();
 }
 
-extern "C" size_t ogs_decode_bwd_scratch_bytes(void) {
-    return sizeof(float) * (size_t)kDbBlocks * kNWeights + 256;
+extern "C" size_t ogs_decode_bwd_scratch_bytes(int64_t sel_cap) {
+    return db_layout(sel_cap < 0 ? 0 : sel_cap, nullptr, nullptr);
 }
 
 extern "C" ogs_status ogs_decode_bwd(const float* pos, const float* feat, const float* offs,
                                      const float* lv, int64_t N, const ogs_mlp* mlp,
                                      const ogs_camera* cam, const uint32_t* sel_idx,
-                                     const float* sel_w, const ogs_counts* counts,
-                                     const float* dmeans, const float* dscales,
-                                     const float* dquats, const float* drec, float* dfeat,
-                                     float* doffs, float* dlv, const ogs_mlp* dmlp, void* scratch,
-                                     size_t scratch_bytes, void* stream) {
+                                     const float* sel_w, int64_t sel_cap,
+                                     const ogs_counts* counts, const float* dmeans,
+                                     const float* dscales, const float* dquats, const float* drec,
+                                     float* dfeat, float* doffs, float* dlv, const ogs_mlp* dmlp,
+                                     void* scratch, size_t scratch_bytes, void* stream) {
     if (!pos || !feat || !offs || !lv || !mlp || !cam || !sel_idx || !sel_w || !counts ||
         !dmeans || !dscales || !dquats || !drec || !dfeat || !doffs || !dlv || !dmlp || !scratch)
         return OGS_ERR_ARG;
-    if (mlp->F != kF || mlp->H != kH || mlp->k != kK || N < 0) return OGS_ERR_ARG;
+    if (mlp->F != kF || mlp->H != kH || mlp->k != kK || N < 0 || sel_cap < 0) return OGS_ERR_ARG;
     if (!dmlp->w1 || !dmlp->b1 || !dmlp->w2_op || !dmlp->b2_op || !dmlp->w2_col ||
         !dmlp->b2_col || !dmlp->w2_cov || !dmlp->b2_cov)
         return OGS_ERR_ARG;
-    if (scratch_bytes < ogs_decode_bwd_scratch_bytes() || !aligned(scratch, 16) ||
-        !aligned(dquats, 16))
+    if (scratch_bytes < ogs_decode_bwd_scratch_bytes(sel_cap) || !aligned(scratch, 16) ||
+        !aligned(dquats, 16) || !aligned(feat, 16) || !aligned(dfeat, 16))
         return OGS_ERR_ARG;
+    if (sel_cap == 0) return OGS_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    size_t smem = decode_bwd_smem();
-    if (cudaFuncSetAttribute(decode_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-        return OGS_ERR_CUDA;
+    DbScratch sc;
+    db_layout(sel_cap, scratch, &sc);
     DbArgs a{pos, feat, offs, lv, sel_idx, sel_w, counts, *mlp, make_cam(*cam), dmeans, dscales,
-             dquats, drec, dfeat, doffs, dlv, (float*)scratch};
-    decode_bwd_kernel<<<kDbBlocks, kDbThreads, smem, st>>>(a);
-    reduce_partials<<<(kNWeights + 255) / 256, 256, 0, st>>>((const float*)scratch, kDbBlocks, *dmlp);
+             dquats, drec, dfeat, doffs, dlv, sc.rowY, sc.rowH, sc.rowP, sc.rowZ, sc.partial};
+    decode_bwd_rows<<<stride_grid(sel_cap, kDbThreads, 3), kDbThreads, 0, st>>>(a);
+    decode_bwd_weights<<<kDbBlocks, kWThreads, 0, st>>>(a);
+    reduce_partials<<<(kNWeights + 31) / 32, 32 * kRedWarps, 0, st>>>(sc.partial, kDbBlocks, *dmlp);
     return launch_status();
 }
 
@@ -496,7 +710,8 @@ extern "C" ogs_status ogs_adam(float* param, float* grad, float* m, float* v, in
     if (!param || !grad || !m || !v || n < 0 || step < 1) return OGS_ERR_ARG;
     if (n == 0) return OGS_OK;
     const float bc1 = 1.f - powf(beta1, (float)step), bc2 = 1.f - powf(beta2, (float)step);
-    adam_kernel<<<stride_grid(n, 256, 8), 256, 0, (cudaStream_t)stream>>>(
-        param, grad, m, v, n, lr, beta1, beta2, eps, bc1, bc2, zero_grad);
+    const int vec = aligned(param, 16) && aligned(grad, 16) && aligned(m, 16) && aligned(v, 16);
+    adam_kernel<<<stride_grid(vec ? n / 4 + 1 : n, 256, 8), 256, 0, (cudaStream_t)stream>>>(
+        param, grad, m, v, n, lr, beta1, beta2, eps, bc1, bc2, zero_grad, vec);
     return launch_status();
 }

@@ -72,4 +72,84 @@ struct Carver {
     }
 };
 
+
+// ---------------------------------------------------------------------------------------
+// Single-pass order-preserving compaction: tiles taken in ticket order publish their count
+// in a status word (flag in the top two bits) and find their output offset by a decoupled
+// look-back over their predecessors.
+// ---------------------------------------------------------------------------------------
+constexpr uint32_t kSpinLimit = 1u << 20;                  // polls of one status word
+constexpr unsigned long long kFlagAgg = 1ull << 62;        // tile's own count published
+constexpr unsigned long long kFlagPrefix = 2ull << 62;     // inclusive prefix published
+constexpr unsigned long long kValMask = (1ull << 62) - 1;
+
+__device__ __forceinline__ unsigned long long load_status(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void store_status(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
+}
+
+// Exclusive output offset of tile `tile` (count `agg`) by a decoupled look-back, called by
+// every thread of the CTA: each round inspects the kThreads nearest unresolved predecessors
+// at once (one status word per thread), adds their counts up to the nearest one that has
+// published an inclusive prefix, and stops there.  All tiles of a launch run at about the
+// same time, so a wide window keeps the chain of rounds short.  Predecessors hold earlier
+// tickets, so they are running or done and publish without waiting on this tile; every wait
+// is still bounded: on expiry the prefix is published anyway (so successors finish) and
+// *timeout is set, which marks the whole result invalid.
+template <int kThreads>
+__device__ __forceinline__ unsigned long long block_tile_offset(unsigned long long* status,
+                                                                uint32_t tile,
+                                                                unsigned long long agg,
+                                                                uint32_t* timeout) {
+    __shared__ unsigned long long s_sum[kThreads / 32];
+    __shared__ int s_stop;
+    __shared__ int s_bad;
+    if (tile == 0) {
+        if (threadIdx.x == 0) store_status(status, kFlagPrefix | agg);
+        return 0;
+    }
+    if (threadIdx.x == 0) store_status(status + tile, kFlagAgg | agg);
+    unsigned long long excl = 0;
+    bool ok = true;
+    for (int64_t end = tile; end > 0; end -= kThreads) {
+        const int64_t idx = end - 1 - (int64_t)threadIdx.x;
+        unsigned long long v = kFlagPrefix;             // before tile 0: prefix 0
+        if (idx >= 0) {
+            uint32_t polls = 0;
+            while (((v = load_status(status + idx)) >> 62) == 0) {
+                if (++polls > kSpinLimit) break;
+                __nanosleep(32);
+            }
+        }
+        if (threadIdx.x == 0) { s_stop = kThreads; s_bad = 0; }
+        __syncthreads();
+        if ((v >> 62) == 0) s_bad = 1;
+        if ((v >> 62) == 2) atomicMin(&s_stop, (int)threadIdx.x);   // nearest prefix
+        __syncthreads();
+        if (s_bad) { ok = false; break; }
+        const int stop = s_stop;
+        unsigned long long add = (int)threadIdx.x <= stop ? (v & kValMask) : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) add += __shfl_xor_sync(0xffffffffu, add, o);
+        if (lane_id() == 0) s_sum[threadIdx.x >> 5] = add;
+        __syncthreads();
+        unsigned long long round = 0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) round += s_sum[w];
+        excl += round;
+        __syncthreads();                                 // s_sum, s_stop reused next round
+        if (stop < kThreads) break;
+    }
+    if (threadIdx.x == 0) {
+        store_status(status + tile, kFlagPrefix | ((excl + agg) & kValMask));
+        if (!ok) atomicExch(timeout, 1u);
+    }
+    return excl;
+}
+
 }  // namespace ogs

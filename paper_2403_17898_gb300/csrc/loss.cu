@@ -6,8 +6,9 @@
 // + C1, A2 = 2 (m3 - m1 my) + C2, B1 = m1^2 + my^2 + C1, B2 = m2 - m1^2 + sy^2 + C2):
 //   dS/dm1 = S (2my/A1 - 2my/A2 - 2m1/B1 + 2m1/B2),  dS/dm2 = -S/B2,  dS/dm3 = 2S/A2,
 // and for the mean SSIM:  d/dx = G*g1 + 2 x (G*g2) + y (G*g3), g_i = dS/dm_i / n.
-// Four streaming passes (horizontal blur of 5 maps, vertical blur + SSIM map, horizontal blur
-// of the 3 partial maps, vertical blur + gradient), all HBM-bound.
+// Two tiled passes (moments -> SSIM map and partial maps; blur of the partial maps ->
+// gradient), each staging its tile and halo in shared memory; HBM-bound (x, y and three
+// partial maps read or written once per pass).
 #include <cmath>
 
 #include "internal.cuh"
@@ -36,119 +37,147 @@ Win make_window() {
     return g;
 }
 
-// horizontal blur of x, y, x^2, y^2, x y  ->  h[5][C*H*W]
-__global__ void ssim_h5(const float* __restrict__ x, const float* __restrict__ y, int C, int H,
-                        int W, Win g, float* __restrict__ h) {
-    const int64_t n = (int64_t)C * H * W;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int xx = (int)(i % W);
-        const int64_t row = i - xx;
+// Tiled passes: a CTA owns a kTX x kTY output tile of one channel.  It stages the inputs of
+// the tile plus a kRad halo in shared memory (zero outside the image: the zero-padded window),
+// blurs horizontally into shared memory and vertically into registers.
+constexpr int kTX = 32, kTY = 32;
+constexpr int kHX = kTX + 2 * kRad, kHY = kTY + 2 * kRad;   // 42 x 42 staged inputs
+constexpr int kLossThreads = 256;
+
+__device__ __forceinline__ float block_sum(float v, float* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane_id() == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float s = 0.f;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < kLossThreads / 32; ++i) s += red[i];
+    return s;                                       // valid in thread 0
+}
+
+// pass 1: the five blurred moments -> SSIM map (summed) and the three partial maps
+// gp_i = dS/dm_i / n for the backward
+__global__ void __launch_bounds__(kLossThreads) ssim_fwd(const float* __restrict__ x,
+                                                         const float* __restrict__ y, int H, int W,
+                                                         Win g, float inv_n,
+                                                         float* __restrict__ gp, int64_t n,
+                                                         float* __restrict__ ssim_sum) {
+    __shared__ float sx[kHY][kHX + 1];
+    __shared__ float sy[kHY][kHX + 1];
+    __shared__ float hs[5][kHY][kTX + 1];
+    __shared__ float red[kLossThreads / 32];
+    const int c = blockIdx.z;
+    const int x0 = blockIdx.x * kTX - kRad, y0 = blockIdx.y * kTY - kRad;
+    const int64_t plane = (int64_t)c * H * W;
+    for (int e = threadIdx.x; e < kHX * kHY; e += kLossThreads) {
+        const int r = e / kHX, q = e % kHX;
+        const int gy = y0 + r, gx = x0 + q;
+        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+        const int64_t i = plane + (int64_t)gy * W + gx;
+        sx[r][q] = in ? x[i] : 0.f;
+        sy[r][q] = in ? y[i] : 0.f;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kHY * kTX; e += kLossThreads) {
+        const int r = e / kTX, q = e % kTX;
         float a = 0.f, b = 0.f, aa = 0.f, bb = 0.f, ab = 0.f;
 #pragma unroll
         for (int k = 0; k < kWin; ++k) {
-            const int q = xx + k - kRad;
-            if (q < 0 || q >= W) continue;
-            const float u = x[row + q], v = y[row + q], w = g.w[k];
+            const float u = sx[r][q + k], v = sy[r][q + k], w = g.w[k];
             a = fmaf(w, u, a); b = fmaf(w, v, b);
             aa = fmaf(w, u * u, aa); bb = fmaf(w, v * v, bb); ab = fmaf(w, u * v, ab);
         }
-        h[i] = a; h[n + i] = b; h[2 * n + i] = aa; h[3 * n + i] = bb; h[4 * n + i] = ab;
+        hs[0][r][q] = a; hs[1][r][q] = b; hs[2][r][q] = aa; hs[3][r][q] = bb; hs[4][r][q] = ab;
     }
-}
-
-// vertical blur -> SSIM map -> partial maps g[3][n]; sum of S into *ssim_sum
-__global__ void ssim_v5(const float* __restrict__ h, int C, int H, int W, Win g,
-                        float* __restrict__ gp, float* __restrict__ ssim_sum) {
-    const int64_t n = (int64_t)C * H * W;
-    const float inv_n = 1.0f / (float)n;
+    __syncthreads();
     float local = 0.f;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int xx = (int)(i % W);
-        const int yy = (int)((i / W) % H);
-        const int64_t plane = i - (int64_t)yy * W - xx;
+    for (int e = threadIdx.x; e < kTY * kTX; e += kLossThreads) {
+        const int r = e / kTX, q = e % kTX;
+        const int gy = y0 + kRad + r, gx = x0 + kRad + q;
+        if (gx >= W || gy >= H) continue;
         float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int k = 0; k < kWin; ++k) {
-            const int q = yy + k - kRad;
-            if (q < 0 || q >= H) continue;
-            const int64_t j = plane + (int64_t)q * W + xx;
             const float w = g.w[k];
 #pragma unroll
-            for (int c = 0; c < 5; ++c) m[c] = fmaf(w, h[c * n + j], m[c]);
+            for (int j = 0; j < 5; ++j) m[j] = fmaf(w, hs[j][r + k][q], m[j]);
         }
         const float mx = m[0], my = m[1];
-        const float sx = m[2] - mx * mx, sy = m[3] - my * my, sxy = m[4] - mx * my;
-        const float A1 = 2.f * mx * my + kC1, A2 = 2.f * sxy + kC2;
-        const float B1 = mx * mx + my * my + kC1, B2 = sx + sy + kC2;
+        const float vx = m[2] - mx * mx, vy = m[3] - my * my, vxy = m[4] - mx * my;
+        const float A1 = 2.f * mx * my + kC1, A2 = 2.f * vxy + kC2;
+        const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
         const float S = (A1 * A2) / (B1 * B2);
         local += S;
         const float sS = S * inv_n;
+        const int64_t i = plane + (int64_t)gy * W + gx;
         gp[i] = sS * (2.f * my / A1 - 2.f * my / A2 - 2.f * mx / B1 + 2.f * mx / B2);
         gp[n + i] = -sS / B2;
         gp[2 * n + i] = 2.f * sS / A2;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
-    if (lane_id() == 0) atomicAdd(ssim_sum, local);
+    const float s = block_sum(local, red);
+    if (threadIdx.x == 0) atomicAdd(ssim_sum, s);
 }
 
-__global__ void ssim_h3(const float* __restrict__ gp, int C, int H, int W, Win g,
-                        float* __restrict__ t) {
-    const int64_t n = (int64_t)C * H * W;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int xx = (int)(i % W);
-        const int64_t row = i - xx;
-        float a = 0.f, b = 0.f, c = 0.f;
-#pragma unroll
-        for (int k = 0; k < kWin; ++k) {
-            const int q = xx + k - kRad;
-            if (q < 0 || q >= W) continue;
-            const float w = g.w[k];
-            a = fmaf(w, gp[row + q], a);
-            b = fmaf(w, gp[n + row + q], b);
-            c = fmaf(w, gp[2 * n + row + q], c);
-        }
-        t[i] = a; t[n + i] = b; t[2 * n + i] = c;
+// pass 2: blur of the partial maps -> dSSIM/dx = G*gp0 + 2 x (G*gp1) + y (G*gp2);
+// dimg = (1 - lam) sign(x - y) / n - lam dSSIM/dx, and the L1 sum
+__global__ void __launch_bounds__(kLossThreads) ssim_bwd(const float* __restrict__ gp,
+                                                         const float* __restrict__ x,
+                                                         const float* __restrict__ y, int H, int W,
+                                                         Win g, float lam, float inv_n, int64_t n,
+                                                         float* __restrict__ dimg,
+                                                         float* __restrict__ l1_sum) {
+    __shared__ float sg[3][kHY][kHX + 1];
+    __shared__ float hs[3][kHY][kTX + 1];
+    __shared__ float red[kLossThreads / 32];
+    const int c = blockIdx.z;
+    const int x0 = blockIdx.x * kTX - kRad, y0 = blockIdx.y * kTY - kRad;
+    const int64_t plane = (int64_t)c * H * W;
+    for (int e = threadIdx.x; e < kHX * kHY; e += kLossThreads) {
+        const int r = e / kHX, q = e % kHX;
+        const int gy = y0 + r, gx = x0 + q;
+        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+        const int64_t i = plane + (int64_t)gy * W + gx;
+        sg[0][r][q] = in ? gp[i] : 0.f;
+        sg[1][r][q] = in ? gp[n + i] : 0.f;
+        sg[2][r][q] = in ? gp[2 * n + i] : 0.f;
     }
-}
-
-// vertical blur of the partial maps -> dSSIM/dx; dimg = (1-lam) sign(x-y)/n - lam dSSIM/dx;
-// also the L1 sum into *l1_sum
-__global__ void ssim_v3(const float* __restrict__ t, const float* __restrict__ x,
-                        const float* __restrict__ y, int C, int H, int W, Win g, float lam,
-                        float* __restrict__ dimg, float* __restrict__ l1_sum) {
-    const int64_t n = (int64_t)C * H * W;
-    const float inv_n = 1.0f / (float)n;
-    float local = 0.f;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int xx = (int)(i % W);
-        const int yy = (int)((i / W) % H);
-        const int64_t plane = i - (int64_t)yy * W - xx;
-        float a = 0.f, b = 0.f, c = 0.f;
+    __syncthreads();
+    for (int e = threadIdx.x; e < kHY * kTX; e += kLossThreads) {
+        const int r = e / kTX, q = e % kTX;
+        float a = 0.f, b = 0.f, d = 0.f;
 #pragma unroll
         for (int k = 0; k < kWin; ++k) {
-            const int q = yy + k - kRad;
-            if (q < 0 || q >= H) continue;
-            const int64_t j = plane + (int64_t)q * W + xx;
             const float w = g.w[k];
-            a = fmaf(w, t[j], a);
-            b = fmaf(w, t[n + j], b);
-            c = fmaf(w, t[2 * n + j], c);
+            a = fmaf(w, sg[0][r][q + k], a);
+            b = fmaf(w, sg[1][r][q + k], b);
+            d = fmaf(w, sg[2][r][q + k], d);
         }
+        hs[0][r][q] = a; hs[1][r][q] = b; hs[2][r][q] = d;
+    }
+    __syncthreads();
+    float local = 0.f;
+    for (int e = threadIdx.x; e < kTY * kTX; e += kLossThreads) {
+        const int r = e / kTX, q = e % kTX;
+        const int gy = y0 + kRad + r, gx = x0 + kRad + q;
+        if (gx >= W || gy >= H) continue;
+        float a = 0.f, b = 0.f, d = 0.f;
+#pragma unroll
+        for (int k = 0; k < kWin; ++k) {
+            const float w = g.w[k];
+            a = fmaf(w, hs[0][r + k][q], a);
+            b = fmaf(w, hs[1][r + k][q], b);
+            d = fmaf(w, hs[2][r + k][q], d);
+        }
+        const int64_t i = plane + (int64_t)gy * W + gx;
         const float xi = x[i], yi = y[i];
-        const float dssim = a + 2.f * xi * b + yi * c;
-        const float d = xi - yi;
-        local += fabsf(d);
-        const float sgn = d > 0.f ? inv_n : (d < 0.f ? -inv_n : 0.f);
+        const float dssim = a + 2.f * xi * b + yi * d;
+        const float df = xi - yi;
+        local += fabsf(df);
+        const float sgn = df > 0.f ? inv_n : (df < 0.f ? -inv_n : 0.f);
         dimg[i] = (1.f - lam) * sgn - lam * dssim;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
-    if (lane_id() == 0) atomicAdd(l1_sum, local);
+    const float s = block_sum(local, red);
+    if (threadIdx.x == 0) atomicAdd(l1_sum, s);
 }
 
 // loss = (1 - lam) * l1_sum / n + lam * (1 - ssim_sum / n), added to *loss
@@ -163,7 +192,7 @@ __global__ void combine_loss(const float* sums, int64_t n, float lam, float* los
 using namespace ogs;
 
 extern "C" size_t ogs_loss_l1_ssim_scratch_bytes(int32_t C, int32_t H, int32_t W) {
-    return sizeof(float) * ((size_t)8 * C * H * W + 4) + 512;
+    return sizeof(float) * ((size_t)3 * C * H * W + 4) + 512;
 }
 
 extern "C" ogs_status ogs_loss_l1_ssim(const float* img, const float* target, int32_t C,
@@ -177,17 +206,15 @@ extern "C" ogs_status ogs_loss_l1_ssim(const float* img, const float* target, in
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t n = (int64_t)C * H * W;
     Carver cv(scratch);
-    float* h = cv.take<float>(5 * n);
     float* gp = cv.take<float>(3 * n);
     float* sums = cv.take<float>(4);
-    float* t = h;   // the 5 blurred maps are dead once the partial maps exist
     const Win g = make_window();
     if (cudaMemsetAsync(sums, 0, 4 * sizeof(float), st) != cudaSuccess) return OGS_ERR_CUDA;
-    const int grid = stride_grid(n, 256, 8);
-    ssim_h5<<<grid, 256, 0, st>>>(img, target, C, H, W, g, h);
-    ssim_v5<<<grid, 256, 0, st>>>(h, C, H, W, g, gp, sums);
-    ssim_h3<<<grid, 256, 0, st>>>(gp, C, H, W, g, t);
-    ssim_v3<<<grid, 256, 0, st>>>(t, img, target, C, H, W, g, lambda, dimg, sums + 1);
+    const dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY, C);
+    const float inv_n = 1.0f / (float)n;
+    ssim_fwd<<<grid, kLossThreads, 0, st>>>(img, target, H, W, g, inv_n, gp, n, sums);
+    ssim_bwd<<<grid, kLossThreads, 0, st>>>(gp, img, target, H, W, g, lambda, inv_n, n, dimg,
+                                            sums + 1);
     if (loss) combine_loss<<<1, 32, 0, st>>>(sums, n, lambda, loss);
     return launch_status();
 }

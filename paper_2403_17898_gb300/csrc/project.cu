@@ -2,7 +2,8 @@
 // (Sec. 3.1, Eq. 1: Sigma = R S S^T R^T, projected with the local affine Jacobian).
 //
 // One thread per Gaussian, grid-stride over the device-side count.  HBM-bound: reads 56 B of
-// Gaussian SoA, writes a 48 B record, 4 B depth key, 8 B rect and 4 B tile count.
+// Gaussian SoA, writes a 48 B record, 4 B depth key, 8 B rect and 4 B tile count; optionally
+// also counts the pairs of every tile (the first step of building the per-tile lists).
 #include "internal.cuh"
 
 namespace ogs {
@@ -20,17 +21,48 @@ struct ProjArgs {
     uint32_t* depth_key;
     uint2* rect;
     uint32_t* tiles;
+    uint32_t* tile_count;    // optional per-tile pair counts (zeroed before the launch)
 };
+
+// Adds every lane's rectangle to the per-tile counts.  All 32 lanes call it.  The first tile
+// of each lane is added with one atomic per distinct tile of the warp (the k Gaussians of an
+// anchor sit in consecutive lanes and mostly share it); the rest of a small rectangle by its
+// lane, and rectangles of more than kOwnTiles tiles by the whole warp.
+constexpr uint32_t kOwnTiles = 8;
+
+__device__ __forceinline__ void count_tiles(uint32_t* tc, int gx, uint2 rc, uint32_t ntiles) {
+    const uint32_t x0 = rc.x & 0xFFFFu, y0 = rc.x >> 16, x1 = rc.y & 0xFFFFu;
+    const uint32_t w = x1 - x0;
+    const bool own = ntiles > 0 && ntiles <= kOwnTiles;
+    const uint32_t t0 = own ? y0 * (uint32_t)gx + x0 : 0xFFFFFFFFu;
+    const uint32_t peers = __match_any_sync(0xffffffffu, t0);
+    if (own && lane_id() == (uint32_t)(__ffs(peers) - 1)) atomicAdd(tc + t0, (uint32_t)__popc(peers));
+    if (own)
+        for (uint32_t i = 1; i < ntiles; ++i) atomicAdd(tc + (y0 + i / w) * (uint32_t)gx + x0 + i % w, 1u);
+    uint32_t big = __ballot_sync(0xffffffffu, ntiles > kOwnTiles);
+    while (big) {
+        const int src = __ffs(big) - 1;
+        big &= big - 1;
+        const uint2 r = make_uint2(__shfl_sync(0xffffffffu, rc.x, src),
+                                   __shfl_sync(0xffffffffu, rc.y, src));
+        const uint32_t bx0 = r.x & 0xFFFFu, by0 = r.x >> 16, bw = (r.y & 0xFFFFu) - bx0;
+        const uint32_t bn = bw * ((r.y >> 16) - by0);
+        for (uint32_t i = lane_id(); i < bn; i += 32)
+            atomicAdd(tc + (by0 + i / bw) * (uint32_t)gx + bx0 + i % bw, 1u);
+    }
+}
 
 __global__ void __launch_bounds__(kProjThreads) project_kernel(ProjArgs a) {
     const Cam& c = a.cam;
     const int64_t n = a.count ? (int64_t)*a.count : a.n_fixed;
-    for (int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < n;
-         gi += (int64_t)gridDim.x * blockDim.x) {
+    // uniform trip count per warp, so the tile counting can use full-warp intrinsics
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t gi = base + threadIdx.x;
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
         uint32_t dkey = 0xFFFFFFFFu, ntiles = 0;
         uint2 rc = make_uint2(0, 0);
-        const float o = a.g.opac[gi];
+        const float o = gi < n ? a.g.opac[gi] : 0.0f;
         if (o > 0.0f) {
             float m0 = a.g.means[3 * gi], m1 = a.g.means[3 * gi + 1], m2 = a.g.means[3 * gi + 2];
             if (!a.rel) { m0 -= c.c[0]; m1 -= c.c[1]; m2 -= c.c[2]; }
@@ -109,12 +141,15 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(ProjArgs a) {
                 }
             }
         }
-        a.rec[3 * gi] = r0;
-        a.rec[3 * gi + 1] = r1;
-        a.rec[3 * gi + 2] = r2;
-        a.depth_key[gi] = dkey;
-        a.rect[gi] = rc;
-        a.tiles[gi] = ntiles;
+        if (gi < n) {
+            a.rec[3 * gi] = r0;
+            a.rec[3 * gi + 1] = r1;
+            a.rec[3 * gi + 2] = r2;
+            a.depth_key[gi] = dkey;
+            a.rect[gi] = rc;
+            a.tiles[gi] = ntiles;
+        }
+        if (a.tile_count) count_tiles(a.tile_count, c.gx, rc, ntiles);
     }
 }
 
@@ -125,18 +160,23 @@ using namespace ogs;
 
 extern "C" ogs_status ogs_project_bin(const ogs_gaussians* g, int64_t n_gauss, int32_t means_relative,
                                       const ogs_camera* cam, ogs_rec2d* rec, uint32_t* depth_key,
-                                      uint32_t* rect, uint32_t* tiles, ogs_counts* counts,
-                                      void* stream) {
+                                      uint32_t* rect, uint32_t* tiles, uint32_t* tile_count,
+                                      ogs_counts* counts, void* stream) {
     if (!g || !cam || !rec || !depth_key || !rect || !tiles || n_gauss < 0) return OGS_ERR_ARG;
     if (!g->means || !g->scales || !g->quats || !g->opac || !g->colors) return OGS_ERR_ARG;
     if (!aligned(rec, 16) || !aligned(g->quats, 16) || !aligned(rect, 8)) return OGS_ERR_ARG;
     if (cam->width <= 0 || cam->height <= 0 || cam->width > 16 * 65535 || cam->height > 16 * 65535)
         return OGS_ERR_ARG;
+    const Cam cm = make_cam(*cam);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (tile_count &&
+        cudaMemsetAsync(tile_count, 0, sizeof(uint32_t) * (size_t)cm.gx * cm.gy, st) != cudaSuccess)
+        return OGS_ERR_CUDA;
     if (n_gauss == 0) return OGS_OK;
-    ProjArgs a{*g, counts ? &counts->n_gaussians : nullptr, n_gauss, means_relative,
-               make_cam(*cam), reinterpret_cast<float4*>(rec), depth_key,
-               reinterpret_cast<uint2*>(rect), tiles};
+    ProjArgs a{*g, counts ? &counts->n_gaussians : nullptr, n_gauss, means_relative, cm,
+               reinterpret_cast<float4*>(rec), depth_key, reinterpret_cast<uint2*>(rect), tiles,
+               tile_count};
     int grid = stride_grid(n_gauss, kProjThreads, 8);
-    project_kernel<<<grid, kProjThreads, 0, (cudaStream_t)stream>>>(a);
+    project_kernel<<<grid, kProjThreads, 0, st>>>(a);
     return launch_status();
 }

@@ -4,15 +4,17 @@
 // p*, before any Gaussian is decoded.  Training labels are the renderer's own per-anchor maximum
 // contribution (T * alpha) from ogs_blend_fwd.
 //
-// gate:  score pass (thread per selected anchor, weights in shared memory, outer-product
+// gate:  score pass (FP32: thread per selected anchor, weights in shared memory, outer-product
 //        form so only the 40-wide input and 64 second-layer accumulators live in registers;
-//        per-block keep counts) -> scan -> order-preserving scatter of the kept entries.
+//        BF16: both hidden layers as tcgen05 MMAs over 128-anchor tiles; per-tile keep
+//        counts) -> scan -> order-preserving scatter of the kept entries.
 // train: thread per selected anchor: forward, BCE gradient dL/dz = (p - y)/M, backward;
 //        weight gradients as per-block sums of outer products staged in shared memory,
 //        written as partials and summed in a fixed order.
 #include <cstring>
 
 #include "internal.cuh"
+#include "tc.cuh"
 
 namespace ogs {
 namespace {
@@ -148,11 +150,240 @@ __global__ void __launch_bounds__(kGateThreads) gate_score(PropArgs a, const uin
     }
 }
 
-__global__ void __launch_bounds__(1024) gate_scan(uint32_t* block_count, int nb, int k,
-                                                  ogs_counts* counts) {
+// ---------------------------------------------------------------------------------------
+// BF16 tensor-core scoring (tcgen05): 128 selected anchors per tile,
+//   layer 1: D[128 x 64] = X[128 x 48] . W1^T   (37 inputs padded to 48)
+//   layer 2: D[128 x 64] = H1[128 x 64] . W2^T  (reuses layer 1's TMEM columns)
+// operands in shared memory (no-swizzle K-major core matrices), FP32 accumulators in TMEM;
+// bias/ReLU epilogues and the final 64-wide dot product + sigmoid in FP32, one anchor per
+// thread.  Same outputs as gate_score: p per entry, keep count per 128-entry tile.
+// ---------------------------------------------------------------------------------------
+
+constexpr int kGK1 = 48;
+constexpr uint32_t kGTmemCols = 64;
+constexpr uint32_t kGWaitLimit = 1u << 24;
+constexpr int kGOffA1 = 0;                               // 128 x 48 bf16
+constexpr int kGOffB1 = kGOffA1 + 128 * kGK1 * 2;        // 64 x 48 bf16
+constexpr int kGOffA2 = kGOffB1 + kPH * kGK1 * 2;        // 128 x 64 bf16
+constexpr int kGOffB2 = kGOffA2 + 128 * kPH * 2;         // 64 x 64 bf16
+constexpr int kGOffVec = kGOffB2 + kPH * kPH * 2;        // b1, b2, w3 (f32), b3
+constexpr int kGSmem = kGOffVec + (3 * kPH + 4) * 4;
+static_assert(kGateThreads == 128, "one TMEM lane (anchor) per thread");
+
+__device__ __forceinline__ void gput8(unsigned char* base, int row, int kc, int Kpad,
+                                      const float (&v)[8]) {
+    __nv_bfloat162 h[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    *reinterpret_cast<uint4*>(base + tc::core_offset(row, 8 * kc, Kpad)) =
+        *reinterpret_cast<const uint4*>(h);
+}
+
+// Single pass: CTAs take 128-entry tiles by ticket, score them on the tensor cores, publish
+// the tile's keep count, find its output offset by look-back and write the kept entries in
+// order.  The last CTA to finish (when every CTA has read the input count) publishes the new
+// counts.
+__global__ void __launch_bounds__(kGateThreads, 4) gate_tc(PropArgs a, const uint32_t* sel_in,
+                                                           const float* w_in, int k,
+                                                           ogs_counts* counts, float p_star,
+                                                           float* p_out, uint32_t* sel_out,
+                                                           float* w_out,
+                                                           unsigned long long* status,
+                                                           uint32_t* sync_words) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    __shared__ uint32_t s_tile;
+    __shared__ uint32_t wc[kGateThreads / 32];
+    unsigned char* sA1 = sm + kGOffA1;
+    unsigned char* sB1 = sm + kGOffB1;
+    unsigned char* sA2 = sm + kGOffA2;
+    unsigned char* sB2 = sm + kGOffB2;
+    float* sb1 = reinterpret_cast<float*>(sm + kGOffVec);
+    float* sb2 = sb1 + kPH;
+    float* sw3 = sb2 + kPH;
+    const int t = threadIdx.x, w = t >> 5;
+    const uint32_t M = counts->n_selected;
+    const uint32_t ntiles = (M + 127) / 128;
+    uint32_t* ticket = sync_words;
+    uint32_t* done = sync_words + 1;
+
+    if (blockIdx.x < ntiles) {                   // uniform: CTAs with work own TMEM
+        for (int e = t; e < kPH * (kGK1 / 8); e += kGateThreads) {
+            const int n = e / (kGK1 / 8), kc = e % (kGK1 / 8);
+            float v[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int kk = 8 * kc + i;
+                v[i] = kk < kPIn ? a.net.w1[n * kPIn + kk] : 0.f;
+            }
+            gput8(sB1, n, kc, kGK1, v);
+        }
+        for (int e = t; e < kPH * (kPH / 8); e += kGateThreads) {
+            const int n = e / (kPH / 8), kc = e % (kPH / 8);
+            float v[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = a.net.w2[n * kPH + 8 * kc + i];
+            gput8(sB2, n, kc, kPH, v);
+        }
+        for (int e = t; e < kPH; e += kGateThreads) {
+            sb1[e] = a.net.b1[e];
+            sb2[e] = a.net.b2[e];
+            sw3[e] = a.net.w3[e];
+        }
+        const float b3 = a.net.b3[0];
+        {   // the last K chunk (inputs 40..47) is always zero
+            const float z8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            gput8(sA1, t, kGK1 / 8 - 1, kGK1, z8);
+        }
+        if (t == 0) tc::mbar_init(&mbar, 1);
+        if (w == 0) {
+            tc::tmem_alloc(&tmem_base, kGTmemCols);
+            tc::tmem_relinquish();
+        }
+        tc::fence_smem_to_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        const uint32_t tbase = tmem_base;
+        const uint32_t lane_addr = tbase + ((uint32_t)(32 * w) << 16);
+        const uint32_t id = tc::idesc_bf16(128, kPH);
+        uint32_t phase = 0;
+        bool aborted = false;
+
+        for (;;) {
+            if (t == 0) s_tile = atomicAdd(ticket, 1u);
+            __syncthreads();
+            const uint32_t tile = s_tile;
+            if (tile >= ntiles) break;
+            const uint32_t r = tile * 128 + t;
+            const bool valid = r < M;
+            {
+                float x[kPInPad];
+                if (valid) {
+                    prop_input(a, sel_in[r], x);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < kPInPad; ++i) x[i] = 0.f;
+                }
+#pragma unroll
+                for (int kc = 0; kc < kPInPad / 8; ++kc) {
+                    const float v[8] = {x[8 * kc], x[8 * kc + 1], x[8 * kc + 2], x[8 * kc + 3],
+                                        x[8 * kc + 4], x[8 * kc + 5], x[8 * kc + 6], x[8 * kc + 7]};
+                    gput8(sA1, t, kc, kGK1, v);
+                }
+            }
+            tc::fence_smem_to_async();
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+            if (t == 0) {
+#pragma unroll
+                for (int kk = 0; kk < kGK1 / 16; ++kk)
+                    tc::mma_bf16(tbase, tc::smem_desc(tc::smem_u32(sA1 + kk * 256), 128, 16 * kGK1),
+                                 tc::smem_desc(tc::smem_u32(sB1 + kk * 256), 128, 16 * kGK1), id,
+                                 kk > 0);
+                tc::commit(&mbar);
+            }
+            bool ok = tc::mbar_wait(&mbar, phase, kGWaitLimit);
+            if (__syncthreads_or(!ok)) {
+                aborted = true;
+                if (t == 0) store_status(status + tile, kFlagPrefix);   // let successors finish
+                break;
+            }
+            phase ^= 1;
+            tc::fence_after_sync();
+#pragma unroll
+            for (int c0 = 0; c0 < kPH; c0 += 32) {
+                float v[32];
+                tc::tmem_ld32(lane_addr + c0, v);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float h8[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) h8[i] = fmaxf(v[8 * q + i] + sb1[c0 + 8 * q + i], 0.f);
+                    gput8(sA2, t, c0 / 8 + q, kPH, h8);
+                }
+            }
+            tc::fence_smem_to_async();
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+            if (t == 0) {
+#pragma unroll
+                for (int kk = 0; kk < kPH / 16; ++kk)
+                    tc::mma_bf16(tbase, tc::smem_desc(tc::smem_u32(sA2 + kk * 256), 128, 16 * kPH),
+                                 tc::smem_desc(tc::smem_u32(sB2 + kk * 256), 128, 16 * kPH), id,
+                                 kk > 0);
+                tc::commit(&mbar);
+            }
+            ok = tc::mbar_wait(&mbar, phase, kGWaitLimit);
+            if (__syncthreads_or(!ok)) {
+                aborted = true;
+                if (t == 0) store_status(status + tile, kFlagPrefix);
+                break;
+            }
+            phase ^= 1;
+            tc::fence_after_sync();
+            float z = b3;
+#pragma unroll
+            for (int c0 = 0; c0 < kPH; c0 += 32) {
+                float v[32];
+                tc::tmem_ld32(lane_addr + c0, v);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) z = fmaf(sw3[c0 + i], fmaxf(v[i] + sb2[c0 + i], 0.f), z);
+            }
+            bool keep = false;
+            if (valid) {
+                const float p = 1.0f / (1.0f + __expf(-z));
+                if (p_out) p_out[r] = p;
+                keep = p >= p_star;
+            }
+            const unsigned b = __ballot_sync(0xffffffffu, keep);
+            if (lane_id() == 0) wc[w] = __popc(b);
+            // also orders this tile's TMEM reads before the next tile's MMAs
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+            const unsigned long long agg = wc[0] + wc[1] + wc[2] + wc[3];
+            const unsigned long long excl =
+                block_tile_offset<kGateThreads>(status, tile, agg, &counts->timeout);
+            if (keep) {
+                uint32_t wpre = 0;
+                for (int i = 0; i < w; ++i) wpre += wc[i];
+                const unsigned long long o = excl + wpre + __popc(b & lanemask_lt());
+                sel_out[o] = sel_in[r];
+                w_out[o] = w_in[r];
+            }
+        }
+        if (aborted) {
+            if (t == 0) atomicExch(&counts->timeout, 1u);
+            tc::mbar_wait(&mbar, phase, kGWaitLimit);
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        if (w == 0) tc::tmem_dealloc(tbase, kGTmemCols);
+    }
+    // the last CTA to finish publishes the kept count (every CTA has read M by then)
+    if (t == 0) {
+        __threadfence();
+        if (atomicAdd(done, 1u) == gridDim.x - 1) {
+            __threadfence();
+            const uint32_t kept =
+                ntiles ? (uint32_t)(load_status(status + ntiles - 1) & kValMask) : 0u;
+            counts->n_selected = kept;
+            counts->n_gaussians = kept * (uint32_t)k;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(1024) gate_scan(uint32_t* block_count, int nb_cap, int k,
+                                                  const uint32_t* m_saved, ogs_counts* counts) {
     __shared__ uint32_t ws[32];
     __shared__ uint32_t carry;
     if (threadIdx.x == 0) carry = 0;
+    // only the tiles that hold entries were scored
+    const int nb = min(nb_cap, (int)((*m_saved + kGateThreads - 1) / kGateThreads));
     __syncthreads();
     for (int b0 = 0; b0 < nb; b0 += 1024) {
         const int b = b0 + threadIdx.x;
@@ -377,18 +608,19 @@ extern "C" size_t ogs_proposal_gate_scratch_bytes(int64_t sel_cap) {
     if (nb < 1) nb = 1;
     Carver cv(nullptr);
     cv.take<float>(sel_cap > 0 ? sel_cap : 1);
-    cv.take<uint32_t>(nb);
+    cv.take<unsigned long long>(nb + 1);   // per-tile counts (FP32 form) or status words
     cv.take<uint32_t>(1);
     return cv.off + 256;
 }
 
-extern "C" ogs_status ogs_proposal_gate(const float* pos, const uint8_t* level, const float* feat,
-                                        int64_t N, int32_t NL, int32_t k, const ogs_camera* cam,
-                                        const ogs_proposal* net, float p_star,
-                                        const uint32_t* sel_in, const float* w_in, int64_t sel_cap,
-                                        ogs_counts* counts, uint32_t* sel_out, float* w_out,
-                                        float* p_out, void* scratch, size_t scratch_bytes,
-                                        void* stream) {
+namespace {
+
+ogs_status proposal_gate_impl(bool tensor_cores, const float* pos, const uint8_t* level,
+                              const float* feat, int64_t N, int32_t NL, int32_t k,
+                              const ogs_camera* cam, const ogs_proposal* net, float p_star,
+                              const uint32_t* sel_in, const float* w_in, int64_t sel_cap,
+                              ogs_counts* counts, uint32_t* sel_out, float* w_out, float* p_out,
+                              void* scratch, size_t scratch_bytes, void* stream) {
     if (!pos || !level || !feat || !cam || !net_ok(net) || !sel_in || !w_in || !counts ||
         !sel_out || !w_out || !scratch)
         return OGS_ERR_ARG;
@@ -400,17 +632,58 @@ extern "C" ogs_status ogs_proposal_gate(const float* pos, const uint8_t* level, 
     Carver cv(scratch);
     float* p = cv.take<float>(sel_cap);
     const int nb = (int)((sel_cap + kGateThreads - 1) / kGateThreads);
-    uint32_t* block = cv.take<uint32_t>(nb);
+    uint32_t* block = reinterpret_cast<uint32_t*>(cv.take<unsigned long long>(nb + 1));
     uint32_t* m_saved = cv.take<uint32_t>(1);
     PropArgs a{pos, level, feat, NL, make_cam(*cam), *net};
     cudaStream_t st = (cudaStream_t)stream;
+    if (tensor_cores) {
+        // single pass: tile status words + ticket and done counters, zeroed first
+        unsigned long long* status = reinterpret_cast<unsigned long long*>(block);
+        uint32_t* sync_words = reinterpret_cast<uint32_t*>(status + nb);
+        if (cudaMemsetAsync(status, 0, sizeof(unsigned long long) * (nb + 1), st) != cudaSuccess)
+            return OGS_ERR_CUDA;
+        if (cudaFuncSetAttribute(gate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kGSmem) != cudaSuccess)
+            return OGS_ERR_CUDA;
+        const int grid = nb < 4 * kSmCount ? nb : 4 * kSmCount;
+        gate_tc<<<grid, kGateThreads, kGSmem, st>>>(a, sel_in, w_in, k, counts, p_star, p_out,
+                                                    sel_out, w_out, status, sync_words);
+        return launch_status();
+    }
     const size_t smem = sizeof(float) * kNetFloats;
     gate_score<<<nb, kGateThreads, smem, st>>>(a, sel_in, counts, p_star, p, block, m_saved);
-    gate_scan<<<1, 1024, 0, st>>>(block, nb, k, counts);
+    gate_scan<<<1, 1024, 0, st>>>(block, nb, k, m_saved, counts);
     gate_scatter<<<nb, kGateThreads, 0, st>>>(sel_in, w_in, p, p_star, m_saved, block, sel_out, w_out);
     if (p_out)
         cudaMemcpyAsync(p_out, p, sizeof(float) * sel_cap, cudaMemcpyDeviceToDevice, st);
     return launch_status();
+}
+
+}  // namespace
+
+extern "C" ogs_status ogs_proposal_gate(const float* pos, const uint8_t* level, const float* feat,
+                                        int64_t N, int32_t NL, int32_t k, const ogs_camera* cam,
+                                        const ogs_proposal* net, float p_star,
+                                        const uint32_t* sel_in, const float* w_in, int64_t sel_cap,
+                                        ogs_counts* counts, uint32_t* sel_out, float* w_out,
+                                        float* p_out, void* scratch, size_t scratch_bytes,
+                                        void* stream) {
+    return proposal_gate_impl(false, pos, level, feat, N, NL, k, cam, net, p_star, sel_in, w_in,
+                              sel_cap, counts, sel_out, w_out, p_out, scratch, scratch_bytes,
+                              stream);
+}
+
+extern "C" ogs_status ogs_proposal_gate_bf16(const float* pos, const uint8_t* level,
+                                             const float* feat, int64_t N, int32_t NL, int32_t k,
+                                             const ogs_camera* cam, const ogs_proposal* net,
+                                             float p_star, const uint32_t* sel_in,
+                                             const float* w_in, int64_t sel_cap,
+                                             ogs_counts* counts, uint32_t* sel_out, float* w_out,
+                                             float* p_out, void* scratch, size_t scratch_bytes,
+                                             void* stream) {
+    return proposal_gate_impl(true, pos, level, feat, N, NL, k, cam, net, p_star, sel_in, w_in,
+                              sel_cap, counts, sel_out, w_out, p_out, scratch, scratch_bytes,
+                              stream);
 }
 
 extern "C" size_t ogs_proposal_train_scratch_bytes(void) {

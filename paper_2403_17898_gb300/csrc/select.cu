@@ -1,19 +1,23 @@
 // Anchor selection by octree level (Sec. 4.1.3, Eq. for L_hat) with the inference-time
 // opacity blending of the next level, followed by an order-preserving compaction.
 //
-// HBM-bound streaming pass over the anchor SoA (pos 12 B + level 1 B + dL 4 B per anchor).
-// Compaction is count -> scan of block counts -> scatter: the scatter pass re-evaluates the
-// predicate (cheaper than storing per-anchor flags) and ranks kept anchors with warp ballots,
-// so sel_idx stays in ascending anchor order without a global sort.
+// HBM-bound streaming pass over the anchor SoA (pos 12 B + level 1 B + dL 4 B per anchor),
+// read once: a single-pass order-preserving compaction.  Each CTA stages one tile of anchors
+// in shared memory with TMA bulk copies (so the whole tile's bytes are in flight at once),
+// evaluates the predicate from there, ranks its kept anchors with warp ballots, obtains the
+// tile's output offset by a decoupled look-back over the predecessor tiles' published counts
+// (tiles are taken in ticket order, so every predecessor is already running) and scatters,
+// so sel_idx stays in ascending anchor order without a second pass or a global sort.
 #include "internal.cuh"
+#include "tc.cuh"
 
 namespace ogs {
 namespace {
 
 constexpr int kSelThreads = 256;
-constexpr int kSelItems = 4;
-constexpr int kSelChunk = kSelThreads * kSelItems;   // anchors per block
-
+constexpr int kSelItems = 8;
+constexpr int kSelWarps = kSelThreads / 32;
+constexpr int kSelChunk = kSelThreads * kSelItems;   // anchors per tile (one CTA)
 struct SelArgs {
     const float* pos;
     const uint8_t* level;
@@ -25,12 +29,14 @@ struct SelArgs {
     Cam cam;
 };
 
-// Returns true if anchor j is kept; w receives its opacity weight.
-__device__ __forceinline__ bool keep_anchor(const SelArgs& a, int64_t j, float& w) {
+// Returns true if an anchor at (px, py, pz) with level `lvl` and LOD bias `dl` is kept; w
+// receives its opacity weight.
+__device__ __forceinline__ bool keep_anchor(const SelArgs& a, float px, float py, float pz,
+                                           uint32_t lvl, float dl, float& w) {
     const Cam& c = a.cam;
-    float dx = a.pos[3 * j] - c.c[0];
-    float dy = a.pos[3 * j + 1] - c.c[1];
-    float dz = a.pos[3 * j + 2] - c.c[2];
+    float dx = px - c.c[0];
+    float dy = py - c.c[1];
+    float dz = pz - c.c[2];
     // visibility of the anchor centre: in front of the near plane, within 1.3x half-fov
     float zc = c.R[6] * dx + c.R[7] * dy + c.R[8] * dz;
     float xc = c.R[0] * dx + c.R[1] * dy + c.R[2] * dz;
@@ -38,10 +44,10 @@ __device__ __forceinline__ bool keep_anchor(const SelArgs& a, int64_t j, float& 
     if (!(zc > c.znear) || fabsf(xc) > c.limx * zc || fabsf(yc) > c.limy * zc) return false;
     // fractional level from the viewing distance plus the anchor's LOD bias, clamped
     float d = sqrtf(dx * dx + dy * dy + dz * dz);
-    float Lraw = log2f(c.d_max / (d * c.s)) + a.dL[j];
+    float Lraw = log2f(c.d_max / (d * c.s)) + dl;
     float Ls = fminf(fmaxf(Lraw, 0.0f), (float)(a.NL - 1));
     float Lh = floorf(Ls);
-    float L = (float)a.level[j];
+    float L = (float)lvl;
     if (L <= Lh) {
         w = 1.0f;
         return true;
@@ -53,100 +59,101 @@ __device__ __forceinline__ bool keep_anchor(const SelArgs& a, int64_t j, float& 
     return false;
 }
 
-__global__ void __launch_bounds__(kSelThreads) select_count(SelArgs a, uint32_t* block_count) {
-    __shared__ uint32_t warp_tot[kSelThreads / 32];
-    const int64_t base = (int64_t)blockIdx.x * kSelChunk;
-    uint32_t mine = 0;
-#pragma unroll 4
+// Single pass: each CTA takes the next tile by ticket, evaluates the predicate for its
+// kSelChunk anchors (coalesced), counts them per (item, warp), publishes its count, looks
+// back for its exclusive offset and scatters its kept anchors in ascending order.
+__global__ void __launch_bounds__(kSelThreads) select_onepass(SelArgs a,
+                                                              unsigned long long* status,
+                                                              uint32_t* ticket, int nb,
+                                                              uint32_t* sel_idx, float* sel_w,
+                                                              int64_t cap, ogs_counts* counts,
+                                                              int bulk) {
+    __shared__ __align__(16) float s_pos[3 * kSelChunk];
+    __shared__ __align__(16) float s_dl[kSelChunk];
+    __shared__ __align__(16) uint8_t s_lvl[kSelChunk];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_cnt[kSelItems * kSelWarps];
+    __shared__ uint32_t s_agg;
+    if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const int64_t base = (int64_t)tile * kSelChunk;
+    const int n_here = (int)min((int64_t)kSelChunk, a.N - base);
+    const unsigned warp = threadIdx.x >> 5;
+    // stage the tile's anchor SoA in shared memory: three TMA bulk copies for a full tile of
+    // aligned arrays, cooperative loads otherwise
+    if (bulk && n_here == kSelChunk) {
+        if (threadIdx.x == 0) {
+            tc::mbar_init(&mbar, 1);
+            tc::mbar_expect_tx(&mbar, (3 * 4 + 4 + 1) * kSelChunk);
+            tc::bulk_load(s_pos, a.pos + 3 * base, 3 * 4 * kSelChunk, &mbar);
+            tc::bulk_load(s_dl, a.dL + base, 4 * kSelChunk, &mbar);
+            tc::bulk_load(s_lvl, a.level + base, kSelChunk, &mbar);
+        }
+        __syncthreads();                              // barrier initialised before anyone polls
+        if (!tc::mbar_wait(&mbar, 0, kSpinLimit)) {
+            atomicExch(&counts->timeout, 1u);
+            tc::mbar_wait(&mbar, 0, kSpinLimit);      // copies may still be landing
+        }
+    } else {
+        for (int e = threadIdx.x; e < 3 * n_here; e += kSelThreads) s_pos[e] = a.pos[3 * base + e];
+        for (int e = threadIdx.x; e < n_here; e += kSelThreads) {
+            s_dl[e] = a.dL[base + e];
+            s_lvl[e] = a.level[base + e];
+        }
+        __syncthreads();
+    }
+    uint32_t keepbits = 0;
+    float w[kSelItems];
+    unsigned bal[kSelItems];
+#pragma unroll
     for (int it = 0; it < kSelItems; ++it) {
-        int64_t j = base + it * kSelThreads + threadIdx.x;
-        float w;
-        bool keep = j < a.N && keep_anchor(a, j, w);
-        mine += __popc(__ballot_sync(0xffffffffu, keep));
+        const int l = it * kSelThreads + threadIdx.x;
+        w[it] = 0.0f;
+        const bool keep = l < n_here && keep_anchor(a, s_pos[3 * l], s_pos[3 * l + 1],
+                                                    s_pos[3 * l + 2], s_lvl[l], s_dl[l], w[it]);
+        keepbits |= (uint32_t)keep << it;
+        bal[it] = __ballot_sync(0xffffffffu, keep);
+        if (lane_id() == 0) s_cnt[it * kSelWarps + warp] = __popc(bal[it]);
     }
-    if (lane_id() == 0) warp_tot[threadIdx.x >> 5] = mine;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t s = 0;
-        for (int i = 0; i < kSelThreads / 32; ++i) s += warp_tot[i];
-        block_count[blockIdx.x] = s;
-    }
-}
-
-// Exclusive scan of per-block counts by one block; publishes M and the overflow state.
-__global__ void __launch_bounds__(1024) select_scan(uint32_t* block_count, int nb, int64_t cap,
-                                                     int k, ogs_counts* counts) {
-    __shared__ uint32_t warp_sum[32];
-    __shared__ uint32_t carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int b0 = 0; b0 < nb; b0 += 1024) {
-        int b = b0 + threadIdx.x;
-        uint32_t v = b < nb ? block_count[b] : 0;
-        // inclusive warp scan
-        uint32_t x = v;
+    if (warp == 0) {
+        // exclusive scan of the 64 (item, warp) counts in output order, two per lane
+        const uint32_t c0 = s_cnt[2 * lane_id()], c1 = s_cnt[2 * lane_id() + 1];
+        uint32_t x = c0 + c1;
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane_id() >= (unsigned)o) x += y;
         }
-        if (lane_id() == 31) warp_sum[threadIdx.x >> 5] = x;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            uint32_t s = warp_sum[threadIdx.x];
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
-                if (lane_id() >= (unsigned)o) s += y;
-            }
-            warp_sum[threadIdx.x] = s;   // inclusive over warps
-        }
-        __syncthreads();
-        uint32_t wpre = (threadIdx.x >> 5) ? warp_sum[(threadIdx.x >> 5) - 1] : 0;
-        uint32_t excl = carry + wpre + x - v;
-        if (b < nb) block_count[b] = excl;
-        __syncthreads();
-        if (threadIdx.x == 1023) carry = excl + v;
-        __syncthreads();
+        __syncwarp();
+        s_cnt[2 * lane_id()] = x - c0 - c1;
+        s_cnt[2 * lane_id() + 1] = x - c1;
+        if (lane_id() == 31) s_agg = x;
     }
-    if (threadIdx.x == 0) {
-        uint32_t total = carry;
-        uint32_t m = total > (uint64_t)cap ? (uint32_t)cap : total;
+    __syncthreads();
+    const unsigned long long agg = s_agg;
+    const unsigned long long excl0 =
+        block_tile_offset<kSelThreads>(status, tile, agg, &counts->timeout);
+    if (threadIdx.x == 0 && tile == (uint32_t)nb - 1) {      // the last tile knows the total
+        const unsigned long long total = excl0 + agg;
+        const uint32_t m = total > (unsigned long long)cap ? (uint32_t)cap : (uint32_t)total;
         counts->n_selected = m;
-        counts->n_gaussians = m * (uint32_t)k;
-        counts->need_selected = total;
-        if (total > (uint64_t)cap) atomicOr(&counts->overflow, 1u);
+        counts->n_gaussians = m * (uint32_t)a.k;
+        counts->need_selected = total > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)total;
+        if (total > (unsigned long long)cap) atomicOr(&counts->overflow, 1u);
     }
-}
-
-__global__ void __launch_bounds__(kSelThreads) select_scatter(SelArgs a, const uint32_t* block_off,
-                                                              uint32_t* sel_idx, float* sel_w,
-                                                              int64_t cap) {
-    __shared__ uint32_t warp_cnt[kSelThreads / 32];
-    const int64_t base = (int64_t)blockIdx.x * kSelChunk;
-    const unsigned warp = threadIdx.x >> 5;
-    uint32_t running = block_off[blockIdx.x];
-    for (int it = 0; it < kSelItems; ++it) {
-        int64_t j = base + it * kSelThreads + threadIdx.x;
-        float w = 0.0f;
-        bool keep = j < a.N && keep_anchor(a, j, w);
-        unsigned bal = __ballot_sync(0xffffffffu, keep);
-        if (lane_id() == 0) warp_cnt[warp] = __popc(bal);
-        __syncthreads();
-        uint32_t wpre = 0, tot = 0;
+    const unsigned long long excl = excl0;
 #pragma unroll
-        for (int i = 0; i < kSelThreads / 32; ++i) {
-            uint32_t c = warp_cnt[i];
-            wpre += (i < (int)warp) ? c : 0;
-            tot += c;
-        }
-        if (keep) {
-            uint64_t p = (uint64_t)running + wpre + __popc(bal & lanemask_lt());
-            if (p < (uint64_t)cap) {
-                sel_idx[p] = (uint32_t)j;
-                sel_w[p] = w;
+    for (int it = 0; it < kSelItems; ++it) {
+        if ((keepbits >> it) & 1u) {
+            const unsigned long long p = excl + s_cnt[it * kSelWarps + warp] +
+                                         __popc(bal[it] & lanemask_lt());
+            if (p < (unsigned long long)cap) {
+                sel_idx[p] = (uint32_t)(base + it * kSelThreads + threadIdx.x);
+                sel_w[p] = w[it];
             }
         }
-        running += tot;
-        __syncthreads();
     }
 }
 
@@ -157,7 +164,7 @@ using namespace ogs;
 
 extern "C" size_t ogs_lod_select_scratch_bytes(int64_t N) {
     int64_t nb = (N + kSelChunk - 1) / kSelChunk;
-    return (size_t)(nb < 1 ? 1 : nb) * sizeof(uint32_t) + 256;
+    return (size_t)((nb < 1 ? 1 : nb) + 1) * sizeof(unsigned long long) + 256;
 }
 
 extern "C" ogs_status ogs_lod_select(const float* pos, const uint8_t* level, const float* dL,
@@ -176,10 +183,14 @@ extern "C" ogs_status ogs_lod_select(const float* pos, const uint8_t* level, con
     SelArgs a{pos, level, dL, N, NL, k, infer, make_cam(*cam)};
     int nb = (int)((N + kSelChunk - 1) / kSelChunk);
     if (nb < 1) nb = 1;
-    uint32_t* block = (uint32_t*)scratch;
-    select_count<<<nb, kSelThreads, 0, st>>>(a, block);
-    select_scan<<<1, 1024, 0, st>>>(block, nb, sel_cap, k, counts);
-    select_scatter<<<nb, kSelThreads, 0, st>>>(a, block, sel_idx, sel_w, sel_cap);
+    // tile status words, then the ticket counter: all zero before the pass
+    unsigned long long* status = (unsigned long long*)scratch;
+    uint32_t* ticket = (uint32_t*)(status + nb);
+    if (cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * (nb + 1), st) != cudaSuccess)
+        return OGS_ERR_CUDA;
+    const int bulk = aligned(pos, 16) && aligned(dL, 16) && aligned(level, 16);
+    select_onepass<<<nb, kSelThreads, 0, st>>>(a, status, ticket, nb, sel_idx, sel_w, sel_cap,
+                                               counts, bulk);
     return launch_status();
 }
 

@@ -252,8 +252,12 @@ bool radix_sort(uint32_t* keys, uint32_t* vals, const uint32_t* n_dev, int64_t n
 constexpr int kBinThreads = 256;
 constexpr int kBinItems = 4;
 constexpr int kBinTile = kBinThreads * kBinItems;
-constexpr int kSortThreads = 256;
-constexpr int kSortSmem = 8192;          // entries sorted in shared memory (64 KB of keys)
+constexpr int kSmallThreads = 128;
+constexpr int kSmallSort = 2048;         // lists up to this length: one small CTA, 16 KB of keys
+constexpr int kLargeThreads = 512;
+constexpr int kLargeSort = 16384;        // longer lists: 128 KB of keys in dynamic shared memory
+constexpr int kLargeGrid = 152;          // CTAs looping over the long lists
+constexpr int kScanSmemTiles = 8192;     // tile counts staged in shared memory by the scan
 
 __device__ __forceinline__ void rect_of(uint2 r, uint32_t& x0, uint32_t& y0, uint32_t& x1,
                                         uint32_t& y1) {
@@ -261,7 +265,8 @@ __device__ __forceinline__ void rect_of(uint2 r, uint32_t& x0, uint32_t& y0, uin
 }
 
 // Block-cooperative walk over the pairs of kBinTile Gaussians (load balanced over pairs, not
-// Gaussians): calls f(gaussian, tile) for every pair.
+// Gaussians): calls f(gaussian, tile) for every pair.  Consecutive pairs of a warp mostly
+// belong to the k Gaussians of one anchor and so often share tiles, which f exploits.
 template <class F>
 __device__ __forceinline__ void for_each_pair(const uint32_t* __restrict__ tiles,
                                               const uint2* __restrict__ rect, uint32_t n,
@@ -285,19 +290,45 @@ __device__ __forceinline__ void for_each_pair(const uint32_t* __restrict__ tiles
         s_g[threadIdx.x] = (uint32_t)i;
         s_rect[threadIdx.x] = rc;
         __syncthreads();
-        for (uint32_t p = threadIdx.x; p < tot; p += kBinThreads) {
-            int lo = 0, hi = kBinThreads - 1;          // owner: largest k with s_off[k] <= p
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_off[mid] <= p) lo = mid; else hi = mid - 1;
+        // every lane runs the same number of rounds, so f may use full-warp intrinsics
+        const uint32_t rounds = (tot + kBinThreads - 1) / kBinThreads;
+        for (uint32_t q = 0; q < rounds; ++q) {
+            const uint32_t p = q * kBinThreads + threadIdx.x;
+            const bool valid = p < tot;
+            uint32_t g = 0, t = 0xFFFFFFFFu;
+            if (valid) {
+                int lo = 0, hi = kBinThreads - 1;      // owner: largest k with s_off[k] <= p
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_off[mid] <= p) lo = mid; else hi = mid - 1;
+                }
+                uint32_t x0, y0, x1, y1;
+                rect_of(s_rect[lo], x0, y0, x1, y1);
+                const uint32_t local = p - s_off[lo], w = x1 - x0;
+                g = s_g[lo];
+                t = (y0 + local / w) * (uint32_t)gx + x0 + local % w;
             }
-            uint32_t x0, y0, x1, y1;
-            rect_of(s_rect[lo], x0, y0, x1, y1);
-            const uint32_t local = p - s_off[lo], w = x1 - x0;
-            f(s_g[lo], (y0 + local / w) * (uint32_t)gx + x0 + local % w);
+            f(valid, g, t);
         }
         __syncthreads();
     }
+}
+
+// Warp-aggregated atomic add of 1 per lane on counter[t]: lanes with equal t are served by one
+// atomic; returns this lane's slot (old value + rank among the equal lanes).
+__device__ __forceinline__ uint32_t warp_agg_inc(uint32_t* counter, bool valid, uint32_t t,
+                                                 bool want_slot) {
+    const uint32_t peers = __match_any_sync(0xffffffffu, t);
+    const uint32_t leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (valid && lane_id() == leader) {
+        const uint32_t cnt = __popc(peers);
+        if (want_slot) base = atomicAdd(counter + t, cnt);
+        else atomicAdd(counter + t, cnt);
+    }
+    if (!want_slot) return 0;
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return base + __popc(peers & lanemask_lt());
 }
 
 __global__ void __launch_bounds__(kBinThreads) bin_count(const uint32_t* __restrict__ tiles,
@@ -306,48 +337,84 @@ __global__ void __launch_bounds__(kBinThreads) bin_count(const uint32_t* __restr
                                                          int gx, uint32_t* __restrict__ tcount) {
     const uint32_t n = count_of(n_dev, n_cap);
     if ((int64_t)blockIdx.x * kBinTile >= n) return;
-    for_each_pair(tiles, rect, n, gx, [&](uint32_t, uint32_t t) { atomicAdd(&tcount[t], 1u); });
+    for_each_pair(tiles, rect, n, gx, [&](bool valid, uint32_t, uint32_t t) {
+        warp_agg_inc(tcount, valid, t, false);
+    });
 }
 
-// exclusive scan of the tile counts (one block): tile ranges, P, overflow state
+// Exclusive scan of the tile counts (one block, each thread a run of consecutive tiles): tile
+// ranges, P, overflow state, and the list of tiles too long for the small sorter.
 __global__ void __launch_bounds__(1024) tile_scan(const uint32_t* __restrict__ tcount, int ntiles,
                                                   int64_t pair_cap, uint2* __restrict__ range,
                                                   uint32_t* __restrict__ cursor,
+                                                  uint32_t* __restrict__ big,
+                                                  uint32_t* __restrict__ nbig,
                                                   ogs_counts* counts) {
-    __shared__ uint32_t ws[32];
-    __shared__ unsigned long long carry;
-    if (threadIdx.x == 0) carry = 0;
+    __shared__ unsigned long long ws[32];
+    __shared__ uint32_t s_nbig;
+    __shared__ uint32_t s_cnt[kScanSmemTiles];
+    const bool staged = ntiles <= kScanSmemTiles;
+    if (staged)
+        for (int b = threadIdx.x; b < ntiles; b += 1024) s_cnt[b] = tcount[b];
+    if (threadIdx.x == 0) s_nbig = 0;
     __syncthreads();
-    for (int b0 = 0; b0 < ntiles; b0 += 1024) {
-        const int b = b0 + threadIdx.x;
-        const uint32_t v = b < ntiles ? tcount[b] : 0;
-        uint32_t x = v;
+    const uint32_t* cnt = staged ? s_cnt : tcount;
+    const int per = (ntiles + 1023) / 1024;
+    const int b0 = threadIdx.x * per, b1 = min(b0 + per, ntiles);
+    unsigned long long local = 0;
+    for (int b = b0; b < b1; ++b) local += cnt[b];
+    unsigned long long x = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane_id() >= (unsigned)o) x += y;
+    }
+    if (lane_id() == 31) ws[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        unsigned long long w = ws[threadIdx.x];
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane_id() >= (unsigned)o) x += y;
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane_id() >= (unsigned)o) w += y;
         }
-        if (lane_id() == 31) ws[threadIdx.x >> 5] = x;
-        __syncthreads();
-        uint32_t wpre = 0, tot = 0;
-        for (int q = 0; q < 32; ++q) {
-            wpre += (q < (int)(threadIdx.x >> 5)) ? ws[q] : 0;
-            tot += ws[q];
-        }
-        const unsigned long long excl = carry + wpre + x - v;
-        if (b < ntiles) {
-            range[b] = make_uint2((uint32_t)excl, (uint32_t)(excl + v));
-            cursor[b] = 0;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) carry += tot;
-        __syncthreads();
+        ws[threadIdx.x] = w;                         // inclusive warp totals
     }
     __syncthreads();
-    const unsigned long long P = carry;
+    const unsigned long long P = ws[31];
     const bool over = P > (unsigned long long)pair_cap;
-    if (over)   // no pairs are emitted: every range empty
-        for (int b = threadIdx.x; b < ntiles; b += 1024) range[b] = make_uint2(0, 0);
+    const unsigned long long run0 = (threadIdx.x >= 32 ? ws[(threadIdx.x >> 5) - 1] : 0) + x - local;
+    if (staged) {
+        // exclusive offsets back into shared memory, then coalesced writes
+        unsigned long long run = run0;
+        for (int b = b0; b < b1; ++b) {
+            const uint32_t v = s_cnt[b];
+            s_cnt[b] = (uint32_t)run;
+            if (!over && v > (uint32_t)kSmallSort) big[atomicAdd(&s_nbig, 1u)] = (uint32_t)b;
+            run += v;
+        }
+        __syncthreads();
+        for (int b = threadIdx.x; b < ntiles; b += 1024) {
+            const uint32_t st = s_cnt[b];
+            const uint32_t en = b + 1 < ntiles ? s_cnt[b + 1] : (uint32_t)P;
+            range[b] = over ? make_uint2(0, 0) : make_uint2(st, en);
+            cursor[b] = 0;
+        }
+    } else {
+        unsigned long long run = run0;
+        for (int b = b0; b < b1; ++b) {
+            const uint32_t v = tcount[b];
+            if (over) {                              // no pairs are emitted: every range empty
+                range[b] = make_uint2(0, 0);
+            } else {
+                range[b] = make_uint2((uint32_t)run, (uint32_t)(run + v));
+                if (v > (uint32_t)kSmallSort) big[atomicAdd(&s_nbig, 1u)] = (uint32_t)b;
+            }
+            cursor[b] = 0;
+            run += v;
+        }
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
+        *nbig = s_nbig;
         counts->need_pairs = (uint32_t)(P > 0xFFFFFFFFull ? 0xFFFFFFFFull : P);
         if (over) {
             atomicOr(&counts->overflow, 2u);
@@ -370,10 +437,13 @@ __global__ void __launch_bounds__(kBinThreads) bin_fill(const uint32_t* __restri
     if (counts->overflow & 2u) return;
     const uint32_t n = count_of(n_dev, n_cap);
     if ((int64_t)blockIdx.x * kBinTile >= n) return;
-    for_each_pair(tiles, rect, n, gx, [&](uint32_t g, uint32_t t) {
-        const uint32_t o = range[t].x + atomicAdd(&cursor[t], 1u);
-        keys[o] = dkey[g];
-        ids[o] = g;
+    for_each_pair(tiles, rect, n, gx, [&](bool valid, uint32_t g, uint32_t t) {
+        const uint32_t slot = warp_agg_inc(cursor, valid, t, true);
+        if (valid) {
+            const uint32_t o = range[t].x + slot;
+            keys[o] = dkey[g];
+            ids[o] = g;
+        }
     });
 }
 
@@ -403,39 +473,68 @@ __device__ __forceinline__ void bitonic(uint32_t cnt, Get get, Swap swp) {
     }
 }
 
-__global__ void __launch_bounds__(kSortThreads) tile_sort(const uint2* __restrict__ range,
-                                                          const ogs_counts* counts,
-                                                          uint32_t* __restrict__ keys,
-                                                          uint32_t* __restrict__ ids) {
-    extern __shared__ unsigned long long s_k[];
+// sorts one tile's list (cnt <= capacity of s_k) by the unique key (depth << 32 | id)
+__device__ __forceinline__ void sort_in_smem(unsigned long long* s_k, uint2 r,
+                                             uint32_t* __restrict__ keys,
+                                             uint32_t* __restrict__ ids) {
+    const uint32_t cnt = r.y - r.x;
+    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x)
+        s_k[i] = ((unsigned long long)keys[r.x + i] << 32) | ids[r.x + i];
+    __syncthreads();
+    bitonic(cnt, [&](uint32_t i) { return s_k[i]; },
+            [&](uint32_t i, uint32_t j) {
+                const unsigned long long t = s_k[i]; s_k[i] = s_k[j]; s_k[j] = t;
+            });
+    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) ids[r.x + i] = (uint32_t)s_k[i];
+}
+
+// one 128-thread CTA per tile; lists longer than kSmallSort are left to tile_sort_large
+__global__ void __launch_bounds__(kSmallThreads, 12) tile_sort_small(const uint2* __restrict__ range,
+                                                                 const ogs_counts* counts,
+                                                                 uint32_t* __restrict__ keys,
+                                                                 uint32_t* __restrict__ ids) {
+    __shared__ unsigned long long s_k[kSmallSort];
     if (counts->overflow & 2u) return;
     const uint2 r = range[blockIdx.x];
     const uint32_t cnt = r.y - r.x;
-    if (cnt <= 1) return;
-    if (cnt <= (uint32_t)kSortSmem) {
-        for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x)
-            s_k[i] = ((unsigned long long)keys[r.x + i] << 32) | ids[r.x + i];
+    if (cnt <= 1 || cnt > (uint32_t)kSmallSort) return;
+    sort_in_smem(s_k, r, keys, ids);
+}
+
+// kLargeGrid CTAs loop over the tiles listed as long by tile_scan
+__global__ void __launch_bounds__(kLargeThreads) tile_sort_large(const uint2* __restrict__ range,
+                                                                 const uint32_t* __restrict__ big,
+                                                                 const uint32_t* __restrict__ nbig,
+                                                                 const ogs_counts* counts,
+                                                                 uint32_t* __restrict__ keys,
+                                                                 uint32_t* __restrict__ ids) {
+    extern __shared__ unsigned long long s_k[];
+    if (counts->overflow & 2u) return;
+    const uint32_t n = *nbig;
+    for (uint32_t q = blockIdx.x; q < n; q += gridDim.x) {
+        const uint2 r = range[big[q]];
+        const uint32_t cnt = r.y - r.x;
+        if (cnt <= (uint32_t)kLargeSort) {
+            sort_in_smem(s_k, r, keys, ids);
+        } else {
+            // longer than shared memory holds: the same network on global memory
+            uint32_t* K = keys + r.x;
+            uint32_t* I = ids + r.x;
+            bitonic(cnt, [&](uint32_t i) { return ((unsigned long long)K[i] << 32) | I[i]; },
+                    [&](uint32_t i, uint32_t j) {
+                        const uint32_t tk = K[i], ti = I[i];
+                        K[i] = K[j]; I[i] = I[j]; K[j] = tk; I[j] = ti;
+                    });
+        }
         __syncthreads();
-        bitonic(cnt, [&](uint32_t i) { return s_k[i]; },
-                [&](uint32_t i, uint32_t j) {
-                    const unsigned long long t = s_k[i]; s_k[i] = s_k[j]; s_k[j] = t;
-                });
-        for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) ids[r.x + i] = (uint32_t)s_k[i];
-    } else {
-        // long list: the same network on global memory
-        uint32_t* K = keys + r.x;
-        uint32_t* I = ids + r.x;
-        bitonic(cnt, [&](uint32_t i) { return ((unsigned long long)K[i] << 32) | I[i]; },
-                [&](uint32_t i, uint32_t j) {
-                    const uint32_t tk = K[i], ti = I[i];
-                    K[i] = K[j]; I[i] = I[j]; K[j] = tk; I[j] = ti;
-                });
     }
 }
 
 struct SortScratch {
     uint32_t* tcount;   // per-tile pair counts
     uint32_t* cursor;   // per-tile fill cursors
+    uint32_t* big;      // tiles whose lists exceed kSmallSort
+    uint32_t* nbig;     // their number
     uint32_t* keys;     // depth key of every pair
 };
 
@@ -444,6 +543,8 @@ size_t sort_layout(int64_t pair_cap, int n_tiles, void* base, SortScratch* s) {
     SortScratch t;
     t.tcount = cv.take<uint32_t>(n_tiles > 0 ? n_tiles : 1);
     t.cursor = cv.take<uint32_t>(n_tiles > 0 ? n_tiles : 1);
+    t.big = cv.take<uint32_t>(n_tiles > 0 ? n_tiles : 1);
+    t.nbig = cv.take<uint32_t>(1);
     t.keys = cv.take<uint32_t>(pair_cap > 0 ? pair_cap : 1);
     if (s) *s = t;
     return cv.off + 256;
@@ -478,7 +579,8 @@ extern "C" size_t ogs_sort_scratch_bytes(int64_t g_cap, int64_t pair_cap, int32_
 }
 
 extern "C" ogs_status ogs_sort(const uint32_t* depth_key, const uint32_t* rect, const uint32_t* tiles,
-                               int64_t g_cap, int64_t n_gauss, int32_t grid_x, int32_t grid_y,
+                               const uint32_t* tile_count, int64_t g_cap, int64_t n_gauss,
+                               int32_t grid_x, int32_t grid_y,
                                uint32_t* pair_gauss, uint32_t* tile_range, int64_t pair_cap,
                                ogs_counts* counts, void* scratch, size_t scratch_bytes,
                                void* stream) {
@@ -496,7 +598,7 @@ extern "C" ogs_status ogs_sort(const uint32_t* depth_key, const uint32_t* rect, 
     SortScratch s;
     sort_layout(pair_cap, n_tiles, scratch, &s);
     uint2* range = reinterpret_cast<uint2*>(tile_range);
-    if (cudaMemsetAsync(s.tcount, 0, sizeof(uint32_t) * n_tiles, st) != cudaSuccess)
+    if (!tile_count && cudaMemsetAsync(s.tcount, 0, sizeof(uint32_t) * n_tiles, st) != cudaSuccess)
         return OGS_ERR_CUDA;
     // the Gaussian count is the device count written by the decoder, or the caller's n_gauss
     const uint32_t* n_dev = n_gauss < 0 ? &counts->n_gaussians : nullptr;
@@ -504,15 +606,18 @@ extern "C" ogs_status ogs_sort(const uint32_t* depth_key, const uint32_t* rect, 
     int nb = (int)((n_cap + kBinTile - 1) / kBinTile);
     if (nb < 1) nb = 1;
     const uint2* rc = reinterpret_cast<const uint2*>(rect);
-    bin_count<<<nb, kBinThreads, 0, st>>>(tiles, rc, n_dev, n_cap, grid_x, s.tcount);
-    tile_scan<<<1, 1024, 0, st>>>(s.tcount, n_tiles, pair_cap, range, s.cursor, counts);
+    if (!tile_count) bin_count<<<nb, kBinThreads, 0, st>>>(tiles, rc, n_dev, n_cap, grid_x, s.tcount);
+    tile_scan<<<1, 1024, 0, st>>>(tile_count ? tile_count : s.tcount, n_tiles, pair_cap, range,
+                                  s.cursor, s.big, s.nbig, counts);
     bin_fill<<<nb, kBinThreads, 0, st>>>(tiles, rc, depth_key, n_dev, n_cap, grid_x, range,
                                          s.cursor, counts, s.keys, pair_gauss);
-    const size_t smem = sizeof(unsigned long long) * kSortSmem;
-    if (cudaFuncSetAttribute(tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
+    tile_sort_small<<<n_tiles, kSmallThreads, 0, st>>>(range, counts, s.keys, pair_gauss);
+    const size_t smem = sizeof(unsigned long long) * kLargeSort;
+    if (cudaFuncSetAttribute(tile_sort_large, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
         return OGS_ERR_CUDA;
-    tile_sort<<<n_tiles, kSortThreads, smem, st>>>(range, counts, s.keys, pair_gauss);
+    tile_sort_large<<<kLargeGrid, kLargeThreads, smem, st>>>(range, s.big, s.nbig, counts, s.keys,
+                                                             pair_gauss);
     return launch_status();
 }
 

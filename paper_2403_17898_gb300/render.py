@@ -34,6 +34,18 @@ class FrameCounts:
     n_visible: int
 
 
+def _stage(timers, name, st, fn):
+    """Runs fn; if ``timers`` is a dict, brackets it with a CUDA event pair on stream st."""
+    if timers is None:
+        fn()
+        return
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    fn()
+    e1.record(st)
+    timers.setdefault(name, []).append((e0, e1))
+
+
 class Renderer:
     """Renders views of one anchor set with one decoder at a fixed image size.
 
@@ -67,6 +79,7 @@ class Renderer:
         self.T = torch.empty(self.H, self.W, device="cuda")
         self.n_last = torch.empty(self.H, self.W, dtype=torch.int32, device="cuda")
         self.tile_range = torch.empty(self.gx * self.gy, 2, dtype=torch.int32, device="cuda")
+        self.tile_count = torch.empty(self.gx * self.gy, dtype=torch.int32, device="cuda")
         self._alloc()
 
     # -- buffers ---------------------------------------------------------------------------
@@ -108,14 +121,7 @@ class Renderer:
         st = stream if stream is not None else torch.cuda.current_stream()
 
         def stage(name, fn):
-            if timers is None:
-                fn()
-                return
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            fn()
-            e1.record(st)
-            timers.setdefault(name, []).append((e0, e1))
+            _stage(timers, name, st, fn)
 
         self.counts_t.zero_()
         stage("lod_select", lambda: abi.lod_select(
@@ -127,7 +133,7 @@ class Renderer:
             stage("proposal_gate", lambda: abi.proposal_gate(
                 self.pos, self.level, self.feat, self.N, self.NL, self.k, c, net, p_star,
                 self.sel_idx, self.sel_w, self.sel_cap, self.counts_t, self.sel_idx_g,
-                self.sel_w_g, None, self.gate_scratch, st))
+                self.sel_w_g, None, self.gate_scratch, st, bf16=self.precision == "bf16"))
             sel, selw = self.sel_idx_g, self.sel_w_g
         self.active_sel = sel
         dec = abi.decode_bf16 if self.precision == "bf16" else abi.decode
@@ -136,11 +142,11 @@ class Renderer:
             self.sel_cap, self.counts_t, self._g_struct, st))
         stage("project_bin", lambda: abi.project_bin(
             self._g_struct, self.g_cap, 1, c, self.rec, self.depth_key, self.rect, self.tiles,
-            self.counts_t, st))
+            self.counts_t, st, tile_count=self.tile_count))
         stage("sort", lambda: abi.sort(
             self.depth_key, self.rect, self.tiles, self.g_cap, -1, self.gx, self.gy,
             self.pair_gauss, self.tile_range, self.pair_cap, self.counts_t, self.sort_scratch,
-            st))
+            st, tile_count=self.tile_count))
         stage("blend_fwd", lambda: abi.blend_fwd(
             self.rec, self.pair_gauss, self.tile_range, self.W, self.H, bg, self.img, self.T,
             self.n_last, sel, self.k, maxc, n_eval, st))
@@ -202,8 +208,6 @@ class Trainer(Renderer):
             self.adam_v["mlp." + n] = torch.zeros_like(t)
         self.dimg = torch.zeros(3, self.H, self.W, device=dev)
         self.loss = torch.zeros(1, device=dev)
-        self.db_scratch = torch.empty(abi.decode_bwd_scratch_bytes(), dtype=torch.uint8,
-                                      device=dev)
         self.loss_scratch = None
         if self.ssim_lambda > 0:
             self.loss_scratch = torch.empty(abi.loss_l1_ssim_scratch_bytes(3, self.H, self.W),
@@ -222,26 +226,35 @@ class Trainer(Renderer):
         self.dmeans = torch.empty(G, 3, device=dev)
         self.dscales = torch.empty(G, 3, device=dev)
         self.dquats = torch.empty(G, 4, device=dev)
+        self.db_scratch = torch.empty(abi.decode_bwd_scratch_bytes(self.sel_cap),
+                                      dtype=torch.uint8, device=dev)
 
-    def backward_view(self, cam, target, bg=(0.0, 0.0, 0.0), stream=None):
+    def backward_view(self, cam, target, bg=(0.0, 0.0, 0.0), stream=None, timers=None):
         """Loss and backward of the view last enqueued (its forward must have run in
         training mode with ``cam``); gradients accumulate."""
         c = abi.camera(cam)
         st = stream if stream is not None else torch.cuda.current_stream()
         if self.ssim_lambda > 0:
-            abi.loss_l1_ssim(self.img, target, self.ssim_lambda, self.dimg, self.loss,
-                             self.loss_scratch, st)
+            _stage(timers, "loss", st, lambda: abi.loss_l1_ssim(
+                self.img, target, self.ssim_lambda, self.dimg, self.loss, self.loss_scratch, st))
         else:
-            abi.loss_l1(self.img, target, self.img.numel(), self.dimg, self.loss, st)
-        self.drec.zero_()
-        abi.blend_bwd(self.rec, self.pair_gauss, self.tile_range, self.W, self.H, bg, self.T,
-                      self.n_last, self.dimg, self.drec, st)
-        abi.project_bwd(self._g_struct, self.g_cap, 1, c, self.rect, self.drec, self.dmeans,
-                        self.dscales, self.dquats, self.counts_t, st)
-        abi.decode_bwd(self.pos, self.feat, self.offs, self.lv, self.N, self._mlp_struct, c,
-                       self.sel_idx, self.sel_w, self.counts_t, self.dmeans, self.dscales,
-                       self.dquats, self.drec, self.grads["feat"], self.grads["offs"],
-                       self.grads["lv"], self._dmlp_struct, self.db_scratch, st)
+            _stage(timers, "loss", st, lambda: abi.loss_l1(
+                self.img, target, self.img.numel(), self.dimg, self.loss, st))
+
+        def bb():
+            self.drec.zero_()
+            abi.blend_bwd(self.rec, self.pair_gauss, self.tile_range, self.W, self.H, bg, self.T,
+                          self.n_last, self.dimg, self.drec, st)
+        _stage(timers, "blend_bwd", st, bb)
+        _stage(timers, "project_bwd", st, lambda: abi.project_bwd(
+            self._g_struct, self.g_cap, 1, c, self.rect, self.drec, self.dmeans, self.dscales,
+            self.dquats, self.counts_t, st))
+        _stage(timers, "decode_bwd", st, lambda: abi.decode_bwd(
+            self.pos, self.feat, self.offs, self.lv, self.N, self._mlp_struct, c, self.sel_idx,
+            self.sel_w, self.sel_cap, self.counts_t, self.dmeans, self.dscales, self.dquats,
+            self.drec,
+            self.grads["feat"], self.grads["offs"], self.grads["lv"], self._dmlp_struct,
+            self.db_scratch, st))
 
     def zero_grad(self):
         for t in self.grads.values():
@@ -249,21 +262,26 @@ class Trainer(Renderer):
         for t in self.dmlp.values():
             t.zero_()
 
-    def optimizer_step(self, stream=None):
+    def optimizer_step(self, stream=None, timers=None):
         self.step_count += 1
         b1, b2 = self.betas
+        st = stream if stream is not None else torch.cuda.current_stream()
         pairs = [(getattr(self, n), self.grads[n], n) for n in self.PARAMS]
         pairs += [(self.mlp[n], self.dmlp[n], "mlp." + n) for n in self.mlp]
-        for p, g, n in pairs:
-            abi.adam(p, g, self.adam_m[n], self.adam_v[n], p.numel(), self.lr, b1, b2, self.eps,
-                     self.step_count, True, stream)
+
+        def run():
+            for p, g, n in pairs:
+                abi.adam(p, g, self.adam_m[n], self.adam_v[n], p.numel(), self.lr, b1, b2,
+                         self.eps, self.step_count, True, st)
+        _stage(timers, "adam", st, run)
 
     def train_step(self, cams, targets, bg=(0.0, 0.0, 0.0), update=True, timers=None):
-        """Forward + backward over the views, then (optionally) the Adam update; returns
-        nothing (the summed per-view loss is left in ``self.loss``)."""
+        """One optimisation step: forward + backward over the views (gradients summed over
+        them), then (optionally) the Adam update, which also clears the gradients for the next
+        step; returns nothing (the summed per-view loss is left in ``self.loss``)."""
         self.loss.zero_()
         for cam, tgt in zip(cams, targets):
             self.enqueue(cam, infer=False, bg=bg, timers=timers)
-            self.backward_view(cam, tgt, bg)
+            self.backward_view(cam, tgt, bg, timers=timers)
         if update:
-            self.optimizer_step()
+            self.optimizer_step(timers=timers)

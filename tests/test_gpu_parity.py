@@ -46,6 +46,7 @@ def _gpu_select(abi, torch, sc, cam, infer, cap=None):
                    sel, w, cap, counts, scr)
     torch.cuda.synchronize()
     c = _counts(abi, counts)
+    assert c["timeout"] == 0                 # no look-back wait expired
     M = c["n_selected"]
     return to_np_u32(sel)[:M].astype(np.int64), w.cpu().numpy()[:M], c
 
@@ -82,6 +83,23 @@ def test_lod_select_random_views_and_ragged_sizes(abi, torch):
         eye = rng.uniform(-30, 30, 3)
         cam = synth.look_at_camera(eye, rng.uniform(-5, 5, 3), 160, 90, d_max=60.0)
         _check_select(abi, torch, sc, cam, infer=bool(N % 2))
+
+
+def test_lod_select_many_tiles(abi, torch):
+    # ~1500 tiles of 2048 anchors: offsets resolved across many look-back windows, with long
+    # runs of tiles that keep nothing (most of the box is outside the view)
+    rng = np.random.default_rng(5)
+    N = 3_000_001
+    pos = rng.uniform(-200, 200, size=(N, 3)).astype(np.float32)
+    sc = synth.Scene(pos=pos, level=rng.integers(0, 8, N).astype(np.uint8),
+                     dL=rng.uniform(0, 0.3, N).astype(np.float32),
+                     feat=np.zeros((1, 32), np.float32), offs=np.zeros((1, 10, 3), np.float32),
+                     lv=np.ones((1, 3), np.float32), NL=8)
+    cam = synth.look_at_camera(np.array([150.0, -160.0, 40.0]), np.array([60.0, -20.0, 0.0]),
+                               1920, 1080, d_max=500.0)
+    for infer in (False, True):
+        M, nk = _check_select(abi, torch, sc, cam, infer)
+        assert M > 10_000
 
 
 def test_lod_select_empty_and_overflow(abi, torch):
@@ -143,10 +161,17 @@ def _gpu_project(abi, torch, g, cam, rel=0):
     dk = torch.zeros(G, dtype=torch.int32, device="cuda")
     rect = torch.zeros(G, 2, dtype=torch.int32, device="cuda")
     tiles = torch.zeros(G, dtype=torch.int32, device="cuda")
-    abi.project_bin(gt, G, rel, cam, rec, dk, rect, tiles, None)
+    gx, gy = (cam.W + 15) // 16, (cam.H + 15) // 16
+    tcount = torch.full((gx * gy,), 7, dtype=torch.int32, device="cuda")   # zeroed by the call
+    abi.project_bin(gt, G, rel, cam, rec, dk, rect, tiles, None, tile_count=tcount)
     torch.cuda.synchronize()
     r = to_np_u32(rect)
     rect4 = np.stack([r[:, 0] & 0xFFFF, r[:, 0] >> 16, r[:, 1] & 0xFFFF, r[:, 1] >> 16], 1)
+    # the per-tile pair counts are exactly those of the rectangles the call wrote
+    want = np.zeros((gy, gx), np.int64)
+    for x0, y0, x1, y1 in rect4.astype(np.int64):
+        want[y0:y1, x0:x1] += 1
+    assert np.array_equal(to_np_u32(tcount).astype(np.int64), want.reshape(-1))
     return rec.cpu().numpy(), to_np_u32(dk), rect4.astype(np.int64), to_np_u32(tiles)
 
 
@@ -207,7 +232,7 @@ def test_radix_sort_device_count(abi, torch):
     assert np.array_equal(to_np_u32(vt)[12_345:], vals[12_345:])   # untouched beyond n
 
 
-def _gpu_sort(abi, torch, rect, depth, gx, gy, pair_cap=None):
+def _gpu_sort(abi, torch, rect, depth, gx, gy, pair_cap=None, ext_counts=False):
     G = len(depth)
     area = np.maximum(rect[:, 2] - rect[:, 0], 0) * np.maximum(rect[:, 3] - rect[:, 1], 0)
     P = int(area.sum())
@@ -221,17 +246,28 @@ def _gpu_sort(abi, torch, rect, depth, gx, gy, pair_cap=None):
     counts = torch.zeros(8, dtype=torch.int32, device="cuda")
     scr = torch.empty(abi.sort_scratch_bytes(G, pair_cap, gx * gy), dtype=torch.uint8,
                       device="cuda")
+    tc = None
+    if ext_counts:          # per-tile counts handed in (as ogs_project_bin writes them)
+        want = np.zeros((gy, gx), np.int64)
+        for x0, y0, x1, y1 in rect.astype(np.int64):
+            want[y0:y1, x0:x1] += 1
+        tc = cuda(want.reshape(-1).astype(np.int32))
     abi.sort(cuda(dk.view(np.int32)), cuda(packed.view(np.int32)),
-             cuda(area.astype(np.int32)), G, G, gx, gy, pg, tr, pair_cap, counts, scr)
+             cuda(area.astype(np.int32)), G, G, gx, gy, pg, tr, pair_cap, counts, scr,
+             tile_count=tc)
     torch.cuda.synchronize()
     return to_np_u32(pg), to_np_u32(tr), _counts(abi, counts), P
 
 
-@pytest.mark.parametrize("G,gx,gy", [(1, 3, 2), (3000, 9, 7), (60_000, 120, 68)])
-def test_sort_matches_oracle_lists(abi, torch, G, gx, gy):
+# lists of every length class: short (one small CTA per tile), beyond 2048 entries (the
+# long-list sorter in shared memory) and beyond 16384 entries (its global-memory network)
+@pytest.mark.parametrize("G,gx,gy", [(1, 3, 2), (3000, 9, 7), (60_000, 120, 68), (20_000, 4, 4),
+                                     (100_000, 2, 2)])
+@pytest.mark.parametrize("ext_counts", [False, True])
+def test_sort_matches_oracle_lists(abi, torch, G, gx, gy, ext_counts):
     rect, depth = synth.random_rects_depths(G, G, gx, gy, max_span=8, equal_depth_frac=0.05)
     start, lst, _ = oracle.tile_lists(rect, depth.astype(np.float64), gx, gy)
-    pg, tr, c, P = _gpu_sort(abi, torch, rect, depth, gx, gy)
+    pg, tr, c, P = _gpu_sort(abi, torch, rect, depth, gx, gy, ext_counts=ext_counts)
     assert c["n_pairs"] == P == len(lst) and c["overflow"] == 0
     assert np.array_equal(pg[:P], lst)
     nonempty = start[1:] > start[:-1]
