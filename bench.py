@@ -121,6 +121,23 @@ def _workload():
     return synth.CONFIGS[WORKLOAD]()
 
 
+def pose_of(rank, ws, n_poses):
+    """Pose of step i on this rank: ranks interleave over the path (weak scaling: every rank
+    renders its own frames, no data exchange)."""
+    return lambda i: (rank + i * ws) % n_poses
+
+
+def max_over_ranks(values, ws, device):
+    """Element-wise maximum of per-rank timings (the job takes as long as its slowest rank)."""
+    if ws <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
 # ---------------------------------------------------------------------------------------
 # algorithmic bytes per stage (inputs read once, outputs written once)
 # ---------------------------------------------------------------------------------------
@@ -430,7 +447,7 @@ def run_gpu(args):
     n = len(cams)
     W, H = cams[0].W, cams[0].H
     rd = Renderer(sc, mlp, W, H, sel_cap=200_000, pair_cap=4_000_000)
-    pose = lambda i: (rank + i * ws) % n
+    pose = pose_of(rank, ws, n)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 126 MB L2
 
     # the learned proposal (trained on its own poses of the same scene, judged on held-out)
@@ -449,8 +466,11 @@ def run_gpu(args):
         dist.barrier()
     t_plain, stages_plain, _ = _time_form(rd, cams, pose, args.steps, args.warmup, None, flush,
                                           local)
-    # BF16 decode + learned gate: the measured form
+    # BF16 decode alone (what the gate is compared with)
     rd.precision = "bf16"
+    t_bf16, stages_bf16, _ = _time_form(rd, cams, pose, args.steps, args.warmup, None, flush,
+                                        local)
+    # BF16 decode + learned gate: the measured form
     work = _per_pose(rd, cams, gate)
     if ws > 1:
         dist.barrier()
@@ -458,13 +478,10 @@ def run_gpu(args):
                                           local)
     if ws > 1:
         dist.barrier()
-    t_max, tp_max = total_s, t_plain
-    if ws > 1:
-        t = torch.tensor([total_s, t_plain], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max, tp_max = float(t[0].item()), float(t[1].item())
+    t_max, tp_max, tb_max = max_over_ranks([total_s, t_plain, t_bf16], ws, "cuda")
     fps = ws * args.steps / t_max
     fps_plain = ws * args.steps / tp_max
+    fps_bf16 = ws * args.steps / tb_max
 
     # end-to-end through the public call: render + image to pinned host memory, per step
     host = torch.empty(3, H, W, dtype=torch.float32, pin_memory=True)
@@ -475,11 +492,7 @@ def run_gpu(args):
     t0 = time.perf_counter()
     for i in range(n_e2e):
         rd.render_to_host(cams[pose(i)], host, gate=gate)
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks([time.perf_counter() - t0], ws, "cuda")[0]
     e2e_fps = ws * n_e2e / e2e_s
 
     if rank != 0:
@@ -534,7 +547,11 @@ def run_gpu(args):
                        "mean_selected_anchors": mean(work_plain, 0),
                        "mean_pairs": mean(work_plain, 2),
                        "mean_evaluations": mean(work_plain, 3)},
+        "bf16_no_gate": {"value": fps_bf16, "unit": "frames/s",
+                         "ms_per_step": 1e3 * t_bf16 / args.steps,
+                         "stages_ms": {k: round(v, 5) for k, v in stages_bf16.items()}},
         "speedup_vs_plain_fp32": fps / fps_plain,
+        "gate_speedup_vs_bf16_no_gate": fps / fps_bf16,
         "proposal": pinfo,
         "roofline": roof,
         "stages_ms": {k: round(v, 5) for k, v in mean_ms.items()},
@@ -575,24 +592,26 @@ def run_profile(args):
 
 
 def run_profile_train(args):
-    """A few training steps of the 500k-anchor street workload (one 1600x900 view per step,
-    L1 + D-SSIM, BF16 decode): the small case the training-kernel ncu captures are taken on."""
+    """A few training steps (L1 + D-SSIM): by default one 1600x900 view of the 500k-anchor
+    street workload per step (the small case the training-kernel ncu captures are taken on),
+    or the 16-view steps of the 8M-anchor city (for a launch list)."""
     import torch
     import synth
     from paper_2403_17898_gb300 import build as _b
     _b.build()
     from paper_2403_17898_gb300.render import Trainer
-    sc, mlp, cams = synth.CONFIGS["street500k_1600x900"]()
+    sc, mlp, cams = synth.CONFIGS[args.train_workload]()
     W, H = cams[0].W, cams[0].H
     tr = Trainer(sc, mlp, W, H, ssim_lambda=0.2, sel_cap=100_000, pair_cap=2_000_000,
                  precision=args.precision)
     gen = torch.Generator(device="cuda")
     gen.manual_seed(1)
-    tgt = torch.rand(3, H, W, generator=gen, device="cuda")
-    cam = cams[len(cams) // 2]
-    tr.render(cam, infer=False)
+    views = cams[::4][:16] if args.train_workload == "city8M_1080p" else [cams[len(cams) // 2]]
+    tgts = [torch.rand(3, H, W, generator=gen, device="cuda") for _ in views]
+    for cam in views:
+        tr.render(cam, infer=False)
     for _ in range(args.warmup + args.steps):
-        tr.train_step([cam], [tgt])
+        tr.train_step(views, tgts)
     torch.cuda.synchronize()
     print(json.dumps({"profile_train_steps": args.warmup + args.steps, **tr.counts().__dict__}))
     return 0
@@ -611,6 +630,8 @@ def main():
                     help="render a few frames only (the case profiled with ncu)")
     ap.add_argument("--profile-train", action="store_true",
                     help="run a few training steps only (the case training kernels are profiled on)")
+    ap.add_argument("--train-workload", default="street500k_1600x900",
+                    choices=["street500k_1600x900", "city8M_1080p"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
     args = ap.parse_args()
     if args.profile:

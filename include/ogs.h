@@ -299,6 +299,24 @@ ogs_status ogs_decode_bwd(const float* pos, const float* feat, const float* offs
                           void* scratch, size_t scratch_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------------------
+ * ogs_decode_bwd_bf16 — ogs_decode_bwd with the per-anchor products on the tensor cores
+ * (tcgen05, BF16 operands, FP32 accumulation in tensor memory): the recomputed decoder
+ * layers, dy . W2 and dp . W1 take BF16-rounded inputs, weights and gradients (relative
+ * 2^-9 each); the output gradients dy, the ReLU masks, the weight-gradient products over the
+ * anchors and every accumulation stay FP32.  The backward of ogs_decode_bf16.  Same
+ * arguments, scratch and results as ogs_decode_bwd, except that counts is written: on a
+ * tensor-core wait that does not complete, counts->timeout is set.
+ * ------------------------------------------------------------------------------------- */
+ogs_status ogs_decode_bwd_bf16(const float* pos, const float* feat, const float* offs,
+                               const float* lv, int64_t N, const ogs_mlp* mlp /* host struct */,
+                               const ogs_camera* cam /* host */, const uint32_t* sel_idx,
+                               const float* sel_w, int64_t sel_cap, ogs_counts* counts,
+                               const float* dmeans, const float* dscales, const float* dquats,
+                               const float* drec, float* dfeat, float* doffs, float* dlv,
+                               const ogs_mlp* dmlp /* host struct of device ptrs, written */,
+                               void* scratch, size_t scratch_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------
  * ogs_loss_l1 — photometric L1 term of Sec. 5.1.5: loss = mean |img - target| over n
  * values; dimg = sign(img - target) / n (written); *loss += the mean (device float, caller
  * zeroes; may be NULL).

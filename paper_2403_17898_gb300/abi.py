@@ -82,6 +82,9 @@ _SIGS = {
     "ogs_decode_bwd": (C.c_int, [_P, _P, _P, _P, _I64, C.POINTER(MLP), C.POINTER(Camera), _P, _P,
                                  _I64, _P, _P, _P, _P, _P, _P, _P, _P, C.POINTER(MLP), _P, _SZ,
                                  _P]),
+    "ogs_decode_bwd_bf16": (C.c_int, [_P, _P, _P, _P, _I64, C.POINTER(MLP), C.POINTER(Camera), _P, _P,
+                                 _I64, _P, _P, _P, _P, _P, _P, _P, _P, C.POINTER(MLP), _P, _SZ,
+                                 _P]),
     "ogs_loss_l1": (C.c_int, [_P, _P, _I64, _P, _P, _P]),
     "ogs_loss_l1_ssim_scratch_bytes": (_SZ, [_I32, _I32, _I32]),
     "ogs_loss_l1_ssim": (C.c_int, [_P, _P, _I32, _I32, _I32, C.c_float, _P, _P, _P, _SZ, _P]),
@@ -278,16 +281,19 @@ def decode_bwd_scratch_bytes(sel_cap):
 
 
 def decode_bwd(pos, feat, offs, lv, N, mlp, cam, sel_idx, sel_w, sel_cap, counts, dmeans,
-               dscales, dquats, drec, dfeat, doffs, dlv, dmlp, scratch, stream=None):
+               dscales, dquats, drec, dfeat, doffs, dlv, dmlp, scratch, stream=None, bf16=False):
+    """ogs_decode_bwd, or ogs_decode_bwd_bf16 (tensor-core products) when bf16."""
     c = cam if isinstance(cam, Camera) else camera(cam)
     m = mlp if isinstance(mlp, MLP) else mlp_struct(mlp)
     dm = dmlp if isinstance(dmlp, MLP) else mlp_struct(dmlp)
-    _check(lib().ogs_decode_bwd(_ptr(pos), _ptr(feat), _ptr(offs), _ptr(lv), int(N), C.byref(m),
+    fn = lib().ogs_decode_bwd_bf16 if bf16 else lib().ogs_decode_bwd
+    _check(fn(_ptr(pos), _ptr(feat), _ptr(offs), _ptr(lv), int(N), C.byref(m),
                                 C.byref(c), _ptr(sel_idx), _ptr(sel_w), int(sel_cap),
                                 _ptr(counts),
                                 _ptr(dmeans), _ptr(dscales), _ptr(dquats), _ptr(drec),
                                 _ptr(dfeat), _ptr(doffs), _ptr(dlv), C.byref(dm), _ptr(scratch),
-                                scratch.numel(), _stream(stream)), "ogs_decode_bwd")
+                                scratch.numel(), _stream(stream)),
+           "ogs_decode_bwd_bf16" if bf16 else "ogs_decode_bwd")
 
 
 def loss_l1(img, target, n, dimg, loss=None, stream=None):

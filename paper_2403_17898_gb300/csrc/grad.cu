@@ -8,9 +8,12 @@
 //   dY^T H and dPre^T Z of the block's anchors (staged in shared memory), each element owned
 //   by one thread, written as per-block partials and summed by a deterministic reduction.
 #include "internal.cuh"
+#include "decode_bwd.cuh"
 
 namespace ogs {
 namespace {
+
+using namespace db;
 
 constexpr int kPbThreads = 256;
 
@@ -155,72 +158,24 @@ __global__ void __launch_bounds__(kPbThreads) project_bwd_kernel(PbArgs a) {
 // decoder backward
 // ---------------------------------------------------------------------------------------
 
-constexpr int kDbThreads = 128;
-constexpr int kF = 32;
-constexpr int kH = 32;
-constexpr int kDin = kF + 4;
-constexpr int kK = 10;
-constexpr int kNW1 = 3 * kH * kDin;                       // 3456
-constexpr int kNB1 = 3 * kH;                              // 96
-constexpr int kNOut = 11 * kK;                            // 110 (10 + 30 + 70)
-constexpr int kNW2 = kNOut * kH;                          // 3520
-constexpr int kNWeights = kNW1 + kNB1 + kNW2 + kNOut;     // 7182
-
-// offsets of the decoder gradients inside one flat partial row:
-//   dw1 [3][H][Din] | db1 [3][H] | dw2_op [k][H] | dw2_col [3k][H] | dw2_cov [7k][H] |
-//   db2_op [k] | db2_col [3k] | db2_cov [7k]
-constexpr int kOffB1 = kNW1;
-constexpr int kOffW2 = kOffB1 + kNB1;
-constexpr int kOffB2 = kOffW2 + kNW2;
-
-// per-anchor rows handed from the row pass to the weight pass (f32, 16-byte aligned rows)
-constexpr int kRowY = 112;    // dL/dy of the 110 stacked outputs (+2 zero)
-constexpr int kRowH = 96;     // hidden activations of the three decoders
-constexpr int kRowP = 96;     // dL/d(pre-activation) of the three decoders
-constexpr int kRowZ = 40;     // decoder input z (36, +4 zero)
-
-struct DbArgs {
-    const float* pos;
-    const float* feat;
-    const float* offs;
-    const float* lv;
-    const uint32_t* sel_idx;
-    const float* sel_w;
-    const ogs_counts* counts;
-    ogs_mlp mlp;
-    Cam cam;
-    const float* dmeans;
-    const float* dscales;
-    const float* dquats;
-    const float* drec;
-    float* dfeat;
-    float* doffs;
-    float* dlv;
-    float* rowY;         // [sel_cap][kRowY]
-    float* rowH;         // [sel_cap][kRowH]
-    float* rowP;         // [sel_cap][kRowP]
-    float* rowZ;         // [sel_cap][kRowZ]
-    float* partial;      // [kDbBlocks][kNWeights]
-};
-
-__device__ __forceinline__ float sigm(float x) { return 1.0f / (1.0f + __expf(-x)); }
-
-// out rows of decoder m (opacity 0, colour 1, covariance 2) inside the 110 stacked outputs
-__device__ __forceinline__ int out_base(int m) { return m == 0 ? 0 : (m == 1 ? kK : 4 * kK); }
-__device__ __forceinline__ int dec_of(int row) { return row < kK ? 0 : (row < 4 * kK ? 1 : 2); }
-
-// Row pass: one thread per selected anchor recomputes its three decoders (weights in shared
-// memory, broadcast reads) and chains the per-Gaussian gradients into dy (110), the hidden
+// Row pass: two threads per selected anchor recompute its decoders (weights in shared memory,
+// broadcast reads) and chain the per-Gaussian gradients into dy (110), the hidden
 // pre-activation gradients dp (96) and the feature gradient (dfeat, doffs, dlv accumulate;
-// each anchor appears once per view, so no atomics).  dy, h, dp and z are written as rows
-// for the weight pass.  Layer 1 runs in outer-product form over a streamed input (only the 32
-// hidden accumulators live in registers), so the thread keeps h, dh and dz (96 values).
+// each anchor appears once per view, so no atomics).  The CTA's first two warps take the
+// opacity and colour decoders of 64 anchors, the last two the covariance decoder (and the
+// position terms) of the same anchors: equal work, no divergence inside a warp; the two
+// feature-gradient halves meet in shared memory.  dy, h, dp and z are written as rows for
+// the weight pass.  Layer 1 runs in outer-product form over a streamed input (only the 32
+// hidden accumulators live in registers), so a thread keeps h, dh and dz (96 values).
+constexpr int kRowAnchors = kDbThreads / 2;
+
 __global__ void __launch_bounds__(kDbThreads, 3) decode_bwd_rows(DbArgs a) {
     __shared__ __align__(16) float sW1t[3 * kDin * kH];   // [m][i][o]
     __shared__ __align__(16) float sW1[3 * kH * kDin];    // [m][o][i]
     __shared__ float sB1[kNB1];
     __shared__ __align__(16) float sW2[kNOut * kH];
     __shared__ float sB2[kNOut];
+    __shared__ float sDz[kRowAnchors][kF + 1];
     for (int e = threadIdx.x; e < 3 * kH * kDin; e += kDbThreads) {
         const float v = a.mlp.w1[e];
         sW1[e] = v;
@@ -237,11 +192,20 @@ __global__ void __launch_bounds__(kDbThreads, 3) decode_bwd_rows(DbArgs a) {
     __syncthreads();
     const uint32_t M = a.counts->n_selected;
     const Cam& c = a.cam;
-    for (uint32_t r = blockIdx.x * kDbThreads + threadIdx.x; r < M; r += gridDim.x * kDbThreads) {
+    const bool cov_half = threadIdx.x >= kRowAnchors;        // warp-uniform
+    const int slot = threadIdx.x - (cov_half ? kRowAnchors : 0);
+    const int m_lo = cov_half ? 2 : 0, m_hi = cov_half ? 3 : 2;
+    for (uint32_t base = blockIdx.x * kRowAnchors; base < M; base += gridDim.x * kRowAnchors) {
+        const uint32_t r = base + slot;
+        const bool valid = r < M;
+        float dz[kF];
+#pragma unroll
+        for (int i = 0; i < kF; ++i) dz[i] = 0.f;
+        if (valid) {
         const uint32_t j = a.sel_idx[r];
         const float w = a.sel_w[r];
         const float4* f4 = reinterpret_cast<const float4*>(a.feat + (size_t)j * kF);
-        float dz[kF], lvv[3], dlv[3] = {0.f, 0.f, 0.f}, zc[4];
+        float lvv[3], dlv[3] = {0.f, 0.f, 0.f}, zc[4];
         float dv[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
@@ -250,9 +214,7 @@ __global__ void __launch_bounds__(kDbThreads, 3) decode_bwd_rows(DbArgs a) {
         }
         const float d = sqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
         zc[0] = dv[0] / d; zc[1] = dv[1] / d; zc[2] = dv[2] / d; zc[3] = d;
-#pragma unroll
-        for (int i = 0; i < kF; ++i) dz[i] = 0.f;
-        {
+        if (!cov_half) {
             float4* zr = reinterpret_cast<float4*>(a.rowZ + (size_t)r * kRowZ);
 #pragma unroll
             for (int i = 0; i < kF / 4; ++i) zr[i] = f4[i];
@@ -260,11 +222,13 @@ __global__ void __launch_bounds__(kDbThreads, 3) decode_bwd_rows(DbArgs a) {
             zr[kF / 4 + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         float* yrow = a.rowY + (size_t)r * kRowY;
-        yrow[kNOut] = 0.f;
-        yrow[kNOut + 1] = 0.f;
+        if (cov_half) {
+            yrow[kNOut] = 0.f;
+            yrow[kNOut + 1] = 0.f;
+        }
         const size_t g0 = (size_t)r * kK;
 #pragma unroll 1
-        for (int m = 0; m < 3; ++m) {
+        for (int m = m_lo; m < m_hi; ++m) {
             float h[kH], dh[kH];
 #pragma unroll
             for (int o = 0; o < kH; ++o) h[o] = sB1[m * kH + o];
@@ -322,41 +286,7 @@ __global__ void __launch_bounds__(kDbThreads, 3) decode_bwd_rows(DbArgs a) {
                         y[e] = v;
                     }
                 }
-                const size_t g = g0 + i;
-                if (m == 0) {
-                    const float th = tanhf(y[0]);
-                    if (w * th > 0.f) dy[0] = a.drec[9 * g + 5] * w * (1.f - th * th);
-                } else if (m == 1) {
-#pragma unroll
-                    for (int e = 0; e < 3; ++e) {
-                        const float sg = sigm(y[e]);
-                        dy[e] = a.drec[9 * g + 6 + e] * sg * (1.f - sg);
-                    }
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 3; ++e) {
-                        const float sg = sigm(y[e]);
-                        const float gsc = a.dscales[3 * g + e];
-                        dlv[e] += gsc * sg;
-                        dy[e] = gsc * lvv[e] * sg * (1.f - sg);
-                    }
-                    const float n2 = y[3] * y[3] + y[4] * y[4] + y[5] * y[5] + y[6] * y[6];
-                    const float inv = 1.0f / sqrtf(n2);
-                    const float4 gq = *reinterpret_cast<const float4*>(a.dquats + 4 * g);
-                    const float qn[4] = {y[3] * inv, y[4] * inv, y[5] * inv, y[6] * inv};
-                    const float gqa[4] = {gq.x, gq.y, gq.z, gq.w};
-                    const float dot = qn[0] * gqa[0] + qn[1] * gqa[1] + qn[2] * gqa[2] + qn[3] * gqa[3];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) dy[3 + e] = (gqa[e] - qn[e] * dot) * inv;
-                    // positions: mu = x_v + O * l_v
-                    const float* O = a.offs + ((size_t)j * kK + i) * 3;
-#pragma unroll
-                    for (int e = 0; e < 3; ++e) {
-                        const float gmu = a.dmeans[3 * g + e];
-                        a.doffs[((size_t)j * kK + i) * 3 + e] += gmu * lvv[e];
-                        dlv[e] += gmu * O[e];
-                    }
-                }
+                gaussian_dy(a, m, g0 + i, j, i, w, lvv, y, dy, dlv);
 #pragma unroll
                 for (int e = 0; e < 7; ++e) {
                     if (e < per) {
@@ -396,15 +326,28 @@ __global__ void __launch_bounds__(kDbThreads, 3) decode_bwd_rows(DbArgs a) {
                 }
             }
         }
-        float4* df = reinterpret_cast<float4*>(a.dfeat + (size_t)j * kF);
+        if (cov_half) {
 #pragma unroll
-        for (int i = 0; i < kF / 4; ++i) {
-            float4 v = df[i];
-            v.x += dz[4 * i]; v.y += dz[4 * i + 1]; v.z += dz[4 * i + 2]; v.w += dz[4 * i + 3];
-            df[i] = v;
+            for (int i = 0; i < kF; ++i) sDz[slot][i] = dz[i];
+#pragma unroll
+            for (int e = 0; e < 3; ++e) a.dlv[3 * (size_t)j + e] += dlv[e];
         }
+        }
+        __syncthreads();
+        if (valid && !cov_half) {
+            const uint32_t j = a.sel_idx[r];
+            float4* df = reinterpret_cast<float4*>(a.dfeat + (size_t)j * kF);
 #pragma unroll
-        for (int e = 0; e < 3; ++e) a.dlv[3 * (size_t)j + e] += dlv[e];
+            for (int i = 0; i < kF / 4; ++i) {
+                float4 v = df[i];
+                v.x += dz[4 * i] + sDz[slot][4 * i];
+                v.y += dz[4 * i + 1] + sDz[slot][4 * i + 1];
+                v.z += dz[4 * i + 2] + sDz[slot][4 * i + 2];
+                v.w += dz[4 * i + 3] + sDz[slot][4 * i + 3];
+                df[i] = v;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -558,26 +501,6 @@ __global__ void __launch_bounds__(32 * kRedWarps) reduce_partials(const float* _
     }
 }
 
-constexpr int kDbBlocks = 2 * kSmCount;
-
-struct DbScratch {
-    float* partial;
-    float *rowY, *rowH, *rowP, *rowZ;
-};
-
-size_t db_layout(int64_t sel_cap, void* base, DbScratch* s) {
-    Carver cv(base);
-    DbScratch t;
-    const size_t n = (size_t)(sel_cap > 0 ? sel_cap : 1);
-    t.partial = cv.take<float>((size_t)kDbBlocks * kNWeights);
-    t.rowY = cv.take<float>(n * kRowY);
-    t.rowH = cv.take<float>(n * kRowH);
-    t.rowP = cv.take<float>(n * kRowP);
-    t.rowZ = cv.take<float>(n * kRowZ);
-    if (s) *s = t;
-    return cv.off + 256;
-}
-
 // ---------------------------------------------------------------------------------------
 // loss and optimiser
 // ---------------------------------------------------------------------------------------
@@ -598,23 +521,27 @@ __global__ void l1_kernel(const float* __restrict__ img, const float* __restrict
     if (lane_id() == 0 && loss) atomicAdd(loss, s * scale);
 }
 
+// One parameter: m, v moments; step lr * m_hat / (sqrt(v_hat) + eps) with the bias
+// corrections folded into reciprocals (ibc1 = 1/(1 - b1^t), ibc2 = 1/(1 - b2^t)) and one
+// fast division, so the update costs a handful of instructions and the kernel stays
+// memory-bound.
 __device__ __forceinline__ void adam_one(float& p, float& g, float& m, float& v, float lr,
-                                         float b1, float b2, float eps, float bc1, float bc2,
+                                         float b1, float b2, float eps, float ibc1, float ibc2,
                                          int zero_grad) {
-    m = b1 * m + (1.f - b1) * g;
-    v = b2 * v + (1.f - b2) * g * g;
-    p -= lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+    m = fmaf(b1, m, (1.f - b1) * g);
+    v = fmaf(b2, v, (1.f - b2) * g * g);
+    p -= __fdividef(lr * ibc1 * m, __fsqrt_rn(v * ibc2) + eps);
     if (zero_grad) g = 0.f;
 }
 
 // Streaming update: 16-byte vectors when all four arrays are 16-byte aligned (n/4 vectors
-// plus a scalar tail), scalars otherwise.  HBM-bound: 16 B read + 12 B (16 B with zero_grad)
-// written per parameter.
+// plus a scalar tail), scalars otherwise.  HBM-bound: 16 B read + 12 B written per parameter
+// (+4 B for the gradients that were nonzero, cleared with zero_grad).
 __global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ p, float* __restrict__ grad,
                                                    float* __restrict__ m, float* __restrict__ v,
                                                    int64_t n, float lr, float b1, float b2,
-                                                   float eps, float bc1, float bc2, int zero_grad,
-                                                   int vec) {
+                                                   float eps, float ibc1, float ibc2,
+                                                   int zero_grad, int vec) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int64_t first = 0;
     if (vec) {
@@ -625,27 +552,38 @@ __global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ p, float*
         float4* v4 = reinterpret_cast<float4*>(v);
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
             float4 P = p4[i], G = g4[i], M = m4[i], V = v4[i];
-            adam_one(P.x, G.x, M.x, V.x, lr, b1, b2, eps, bc1, bc2, zero_grad);
-            adam_one(P.y, G.y, M.y, V.y, lr, b1, b2, eps, bc1, bc2, zero_grad);
-            adam_one(P.z, G.z, M.z, V.z, lr, b1, b2, eps, bc1, bc2, zero_grad);
-            adam_one(P.w, G.w, M.w, V.w, lr, b1, b2, eps, bc1, bc2, zero_grad);
+            // most anchors get no gradient in a step: clear only vectors that hold one
+            const bool touched = G.x != 0.f || G.y != 0.f || G.z != 0.f || G.w != 0.f;
+            adam_one(P.x, G.x, M.x, V.x, lr, b1, b2, eps, ibc1, ibc2, zero_grad);
+            adam_one(P.y, G.y, M.y, V.y, lr, b1, b2, eps, ibc1, ibc2, zero_grad);
+            adam_one(P.z, G.z, M.z, V.z, lr, b1, b2, eps, ibc1, ibc2, zero_grad);
+            adam_one(P.w, G.w, M.w, V.w, lr, b1, b2, eps, ibc1, ibc2, zero_grad);
             p4[i] = P; m4[i] = M; v4[i] = V;
-            if (zero_grad) g4[i] = G;
+            if (zero_grad && touched) g4[i] = G;
         }
         first = 4 * n4;
     }
     for (int64_t i = first + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         float P = p[i], G = grad[i], M = m[i], V = v[i];
-        adam_one(P, G, M, V, lr, b1, b2, eps, bc1, bc2, zero_grad);
+        adam_one(P, G, M, V, lr, b1, b2, eps, ibc1, ibc2, zero_grad);
         p[i] = P; m[i] = M; v[i] = V;
         if (zero_grad) grad[i] = G;
     }
 }
 
 }  // namespace
+
+cudaError_t db::launch_weight_pass(const DbArgs& a, const DbScratch& s, const ogs_mlp& dmlp,
+                                   cudaStream_t st) {
+    decode_bwd_weights<<<kDbBlocks, kWThreads, 0, st>>>(a);
+    reduce_partials<<<(kNWeights + 31) / 32, 32 * kRedWarps, 0, st>>>(s.partial, kDbBlocks, dmlp);
+    return cudaGetLastError();
+}
+
 }  // namespace ogs
 
 using namespace ogs;
+using namespace ogs::db;
 
 extern "C" ogs_status ogs_project_bwd(const ogs_gaussians* g, int64_t n_gauss, int32_t means_relative,
                                       const ogs_camera* cam, const uint32_t* rect, const float* drec,
@@ -690,9 +628,8 @@ extern "C" ogs_status ogs_decode_bwd(const float* pos, const float* feat, const 
     db_layout(sel_cap, scratch, &sc);
     DbArgs a{pos, feat, offs, lv, sel_idx, sel_w, counts, *mlp, make_cam(*cam), dmeans, dscales,
              dquats, drec, dfeat, doffs, dlv, sc.rowY, sc.rowH, sc.rowP, sc.rowZ, sc.partial};
-    decode_bwd_rows<<<stride_grid(sel_cap, kDbThreads, 3), kDbThreads, 0, st>>>(a);
-    decode_bwd_weights<<<kDbBlocks, kWThreads, 0, st>>>(a);
-    reduce_partials<<<(kNWeights + 31) / 32, 32 * kRedWarps, 0, st>>>(sc.partial, kDbBlocks, *dmlp);
+    decode_bwd_rows<<<stride_grid(sel_cap, kRowAnchors, 3), kDbThreads, 0, st>>>(a);
+    if (launch_weight_pass(a, sc, *dmlp, st) != cudaSuccess) return OGS_ERR_CUDA;
     return launch_status();
 }
 
@@ -709,9 +646,11 @@ extern "C" ogs_status ogs_adam(float* param, float* grad, float* m, float* v, in
                                int32_t zero_grad, void* stream) {
     if (!param || !grad || !m || !v || n < 0 || step < 1) return OGS_ERR_ARG;
     if (n == 0) return OGS_OK;
-    const float bc1 = 1.f - powf(beta1, (float)step), bc2 = 1.f - powf(beta2, (float)step);
+    const double bc1 = 1.0 - pow((double)beta1, (double)step);
+    const double bc2 = 1.0 - pow((double)beta2, (double)step);
     const int vec = aligned(param, 16) && aligned(grad, 16) && aligned(m, 16) && aligned(v, 16);
     adam_kernel<<<stride_grid(vec ? n / 4 + 1 : n, 256, 8), 256, 0, (cudaStream_t)stream>>>(
-        param, grad, m, v, n, lr, beta1, beta2, eps, bc1, bc2, zero_grad, vec);
+        param, grad, m, v, n, lr, beta1, beta2, eps, (float)(1.0 / bc1), (float)(1.0 / bc2),
+        zero_grad, vec);
     return launch_status();
 }

@@ -96,7 +96,8 @@ __device__ __forceinline__ void store_status(unsigned long long* p, unsigned lon
 // Exclusive output offset of tile `tile` (count `agg`) by a decoupled look-back, called by
 // every thread of the CTA: each round inspects the kThreads nearest unresolved predecessors
 // at once (one status word per thread), adds their counts up to the nearest one that has
-// published an inclusive prefix, and stops there.  All tiles of a launch run at about the
+// published an inclusive prefix, and stops there; a thread stops waiting for its own
+// predecessor as soon as a nearer one is known to hold a prefix.  All tiles of a launch run at about the
 // same time, so a wide window keeps the chain of rounds short.  Predecessors hold earlier
 // tickets, so they are running or done and publish without waiting on this tile; every wait
 // is still bounded: on expiry the prefix is published anyway (so successors finish) and
@@ -118,26 +119,34 @@ __device__ __forceinline__ unsigned long long block_tile_offset(unsigned long lo
     bool ok = true;
     for (int64_t end = tile; end > 0; end -= kThreads) {
         const int64_t idx = end - 1 - (int64_t)threadIdx.x;
+        if (threadIdx.x == 0) { s_stop = kThreads; s_bad = 0; }
+        __syncthreads();
         unsigned long long v = kFlagPrefix;             // before tile 0: prefix 0
         if (idx >= 0) {
             uint32_t polls = 0;
-            while (((v = load_status(status + idx)) >> 62) == 0) {
+            for (;;) {
+                v = load_status(status + idx);
+                const uint32_t f = (uint32_t)(v >> 62);
+                if (f == 2) { atomicMin(&s_stop, (int)threadIdx.x); break; }
+                if (f == 1) break;
+                // a nearer predecessor already holds a prefix: this one is not needed
+                if (*(volatile int*)&s_stop < (int)threadIdx.x) break;
                 if (++polls > kSpinLimit) break;
                 __nanosleep(32);
             }
+        } else {
+            atomicMin(&s_stop, (int)threadIdx.x);
         }
-        if (threadIdx.x == 0) { s_stop = kThreads; s_bad = 0; }
         __syncthreads();
-        if ((v >> 62) == 0) s_bad = 1;
-        if ((v >> 62) == 2) atomicMin(&s_stop, (int)threadIdx.x);   // nearest prefix
-        __syncthreads();
-        if (s_bad) { ok = false; break; }
-        const int stop = s_stop;
-        unsigned long long add = (int)threadIdx.x <= stop ? (v & kValMask) : 0;
+        const int stop = s_stop;                         // nearest prefix in this window
+        const bool mine = (int)threadIdx.x <= stop;
+        if (mine && (v >> 62) == 0) s_bad = 1;
+        unsigned long long add = mine ? (v & kValMask) : 0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) add += __shfl_xor_sync(0xffffffffu, add, o);
         if (lane_id() == 0) s_sum[threadIdx.x >> 5] = add;
         __syncthreads();
+        if (s_bad) { ok = false; break; }
         unsigned long long round = 0;
 #pragma unroll
         for (int w = 0; w < kThreads / 32; ++w) round += s_sum[w];

@@ -55,6 +55,13 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
     return s;                                       // valid in thread 0
 }
 
+// Register-blocked 11-tap blurs: a thread produces kRun consecutive outputs along the blur
+// direction from kRun + 10 loaded inputs (each input loaded once instead of once per tap).
+constexpr int kRun = 4;
+constexpr int kSpan = kRun + kWin - 1;                     // 14 inputs per run
+constexpr int kHRuns = kHY * (kTX / kRun);                 // 42 rows x 8 runs = 336
+constexpr int kVRuns = kTX * (kTY / kRun);                 // 32 columns x 8 runs = 256
+
 // pass 1: the five blurred moments -> SSIM map (summed) and the three partial maps
 // gp_i = dS/dm_i / n for the backward
 __global__ void __launch_bounds__(kLossThreads) ssim_fwd(const float* __restrict__ x,
@@ -69,50 +76,100 @@ __global__ void __launch_bounds__(kLossThreads) ssim_fwd(const float* __restrict
     const int c = blockIdx.z;
     const int x0 = blockIdx.x * kTX - kRad, y0 = blockIdx.y * kTY - kRad;
     const int64_t plane = (int64_t)c * H * W;
-    for (int e = threadIdx.x; e < kHX * kHY; e += kLossThreads) {
-        const int r = e / kHX, q = e % kHX;
-        const int gy = y0 + r, gx = x0 + q;
-        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-        const int64_t i = plane + (int64_t)gy * W + gx;
-        sx[r][q] = in ? x[i] : 0.f;
-        sy[r][q] = in ? y[i] : 0.f;
+    {
+        // 6 rows of 42 per pass, 7 passes; all loads issued before any store (threads 252..255
+        // idle)
+        constexpr int kRowsPer = kLossThreads / kHX, kPasses = (kHY + kRowsPer - 1) / kRowsPer;
+        const int q = threadIdx.x % kHX, r0 = threadIdx.x / kHX;
+        const bool act = threadIdx.x < kRowsPer * kHX;
+        float vx[kPasses], vy[kPasses];
+#pragma unroll
+        for (int k = 0; k < kPasses; ++k) {
+            const int gy = y0 + r0 + kRowsPer * k, gx = x0 + q;
+            const bool in = act && r0 + kRowsPer * k < kHY && gx >= 0 && gx < W && gy >= 0 && gy < H;
+            const int64_t i = plane + (int64_t)gy * W + gx;
+            vx[k] = in ? x[i] : 0.f;
+            vy[k] = in ? y[i] : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < kPasses; ++k) {
+            if (act && r0 + kRowsPer * k < kHY) {
+                sx[r0 + kRowsPer * k][q] = vx[k];
+                sy[r0 + kRowsPer * k][q] = vy[k];
+            }
+        }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < kHY * kTX; e += kLossThreads) {
-        const int r = e / kTX, q = e % kTX;
-        float a = 0.f, b = 0.f, aa = 0.f, bb = 0.f, ab = 0.f;
+    for (int e = threadIdx.x; e < kHRuns; e += kLossThreads) {
+        const int r = e >> 3, q0 = (e & 7) * kRun;
+        float u[kSpan], v[kSpan];
 #pragma unroll
-        for (int k = 0; k < kWin; ++k) {
-            const float u = sx[r][q + k], v = sy[r][q + k], w = g.w[k];
-            a = fmaf(w, u, a); b = fmaf(w, v, b);
-            aa = fmaf(w, u * u, aa); bb = fmaf(w, v * v, bb); ab = fmaf(w, u * v, ab);
+        for (int k = 0; k < kSpan; ++k) { u[k] = sx[r][q0 + k]; v[k] = sy[r][q0 + k]; }
+        float acc[5][kRun];
+#pragma unroll
+        for (int t = 0; t < kRun; ++t)
+#pragma unroll
+            for (int j = 0; j < 5; ++j) acc[j][t] = 0.f;
+#pragma unroll
+        for (int k = 0; k < kSpan; ++k) {
+            const float uu = u[k] * u[k], vv = v[k] * v[k], uv = u[k] * v[k];
+#pragma unroll
+            for (int t = 0; t < kRun; ++t) {
+                const int tap = k - t;
+                if (tap < 0 || tap >= kWin) continue;
+                const float w = g.w[tap];
+                acc[0][t] = fmaf(w, u[k], acc[0][t]);
+                acc[1][t] = fmaf(w, v[k], acc[1][t]);
+                acc[2][t] = fmaf(w, uu, acc[2][t]);
+                acc[3][t] = fmaf(w, vv, acc[3][t]);
+                acc[4][t] = fmaf(w, uv, acc[4][t]);
+            }
         }
-        hs[0][r][q] = a; hs[1][r][q] = b; hs[2][r][q] = aa; hs[3][r][q] = bb; hs[4][r][q] = ab;
+#pragma unroll
+        for (int t = 0; t < kRun; ++t)
+#pragma unroll
+            for (int j = 0; j < 5; ++j) hs[j][r][q0 + t] = acc[j][t];
     }
     __syncthreads();
     float local = 0.f;
-    for (int e = threadIdx.x; e < kTY * kTX; e += kLossThreads) {
-        const int r = e / kTX, q = e % kTX;
-        const int gy = y0 + kRad + r, gx = x0 + kRad + q;
-        if (gx >= W || gy >= H) continue;
-        float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    {
+        const int qc = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * kRun;   // one run per thread
+        float m[5][kRun];
 #pragma unroll
-        for (int k = 0; k < kWin; ++k) {
-            const float w = g.w[k];
+        for (int t = 0; t < kRun; ++t)
 #pragma unroll
-            for (int j = 0; j < 5; ++j) m[j] = fmaf(w, hs[j][r + k][q], m[j]);
+            for (int j = 0; j < 5; ++j) m[j][t] = 0.f;
+#pragma unroll
+        for (int k = 0; k < kSpan; ++k) {
+            float hv[5];
+#pragma unroll
+            for (int j = 0; j < 5; ++j) hv[j] = hs[j][r0 + k][qc];
+#pragma unroll
+            for (int t = 0; t < kRun; ++t) {
+                const int tap = k - t;
+                if (tap < 0 || tap >= kWin) continue;
+                const float w = g.w[tap];
+#pragma unroll
+                for (int j = 0; j < 5; ++j) m[j][t] = fmaf(w, hv[j], m[j][t]);
+            }
         }
-        const float mx = m[0], my = m[1];
-        const float vx = m[2] - mx * mx, vy = m[3] - my * my, vxy = m[4] - mx * my;
-        const float A1 = 2.f * mx * my + kC1, A2 = 2.f * vxy + kC2;
-        const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
-        const float S = (A1 * A2) / (B1 * B2);
-        local += S;
-        const float sS = S * inv_n;
-        const int64_t i = plane + (int64_t)gy * W + gx;
-        gp[i] = sS * (2.f * my / A1 - 2.f * my / A2 - 2.f * mx / B1 + 2.f * mx / B2);
-        gp[n + i] = -sS / B2;
-        gp[2 * n + i] = 2.f * sS / A2;
+        const int gx = x0 + kRad + qc;
+#pragma unroll
+        for (int t = 0; t < kRun; ++t) {
+            const int gy = y0 + kRad + r0 + t;
+            if (gx >= W || gy >= H) continue;
+            const float mx = m[0][t], my = m[1][t];
+            const float vx = m[2][t] - mx * mx, vy = m[3][t] - my * my, vxy = m[4][t] - mx * my;
+            const float A1 = 2.f * mx * my + kC1, A2 = 2.f * vxy + kC2;
+            const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
+            const float S = (A1 * A2) / (B1 * B2);
+            local += S;
+            const float sS = S * inv_n;
+            const int64_t i = plane + (int64_t)gy * W + gx;
+            gp[i] = sS * (2.f * my / A1 - 2.f * my / A2 - 2.f * mx / B1 + 2.f * mx / B2);
+            gp[n + i] = -sS / B2;
+            gp[2 * n + i] = 2.f * sS / A2;
+        }
     }
     const float s = block_sum(local, red);
     if (threadIdx.x == 0) atomicAdd(ssim_sum, s);
@@ -132,49 +189,101 @@ __global__ void __launch_bounds__(kLossThreads) ssim_bwd(const float* __restrict
     const int c = blockIdx.z;
     const int x0 = blockIdx.x * kTX - kRad, y0 = blockIdx.y * kTY - kRad;
     const int64_t plane = (int64_t)c * H * W;
-    for (int e = threadIdx.x; e < kHX * kHY; e += kLossThreads) {
-        const int r = e / kHX, q = e % kHX;
-        const int gy = y0 + r, gx = x0 + q;
-        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-        const int64_t i = plane + (int64_t)gy * W + gx;
-        sg[0][r][q] = in ? gp[i] : 0.f;
-        sg[1][r][q] = in ? gp[n + i] : 0.f;
-        sg[2][r][q] = in ? gp[2 * n + i] : 0.f;
+    {
+        constexpr int kRowsPer = kLossThreads / kHX, kPasses = (kHY + kRowsPer - 1) / kRowsPer;
+        const int q = threadIdx.x % kHX, r0 = threadIdx.x / kHX;
+        const bool act = threadIdx.x < kRowsPer * kHX;
+        float v0[kPasses], v1[kPasses], v2[kPasses];
+#pragma unroll
+        for (int k = 0; k < kPasses; ++k) {
+            const int gy = y0 + r0 + kRowsPer * k, gx = x0 + q;
+            const bool in = act && r0 + kRowsPer * k < kHY && gx >= 0 && gx < W && gy >= 0 && gy < H;
+            const int64_t i = plane + (int64_t)gy * W + gx;
+            v0[k] = in ? gp[i] : 0.f;
+            v1[k] = in ? gp[n + i] : 0.f;
+            v2[k] = in ? gp[2 * n + i] : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < kPasses; ++k) {
+            if (act && r0 + kRowsPer * k < kHY) {
+                sg[0][r0 + kRowsPer * k][q] = v0[k];
+                sg[1][r0 + kRowsPer * k][q] = v1[k];
+                sg[2][r0 + kRowsPer * k][q] = v2[k];
+            }
+        }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < kHY * kTX; e += kLossThreads) {
-        const int r = e / kTX, q = e % kTX;
-        float a = 0.f, b = 0.f, d = 0.f;
+    for (int e = threadIdx.x; e < kHRuns; e += kLossThreads) {
+        const int r = e >> 3, q0 = (e & 7) * kRun;
+        float acc[3][kRun];
 #pragma unroll
-        for (int k = 0; k < kWin; ++k) {
-            const float w = g.w[k];
-            a = fmaf(w, sg[0][r][q + k], a);
-            b = fmaf(w, sg[1][r][q + k], b);
-            d = fmaf(w, sg[2][r][q + k], d);
+        for (int t = 0; t < kRun; ++t)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) acc[j][t] = 0.f;
+#pragma unroll
+        for (int k = 0; k < kSpan; ++k) {
+            float gv[3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) gv[j] = sg[j][r][q0 + k];
+#pragma unroll
+            for (int t = 0; t < kRun; ++t) {
+                const int tap = k - t;
+                if (tap < 0 || tap >= kWin) continue;
+                const float w = g.w[tap];
+#pragma unroll
+                for (int j = 0; j < 3; ++j) acc[j][t] = fmaf(w, gv[j], acc[j][t]);
+            }
         }
-        hs[0][r][q] = a; hs[1][r][q] = b; hs[2][r][q] = d;
+#pragma unroll
+        for (int t = 0; t < kRun; ++t)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) hs[j][r][q0 + t] = acc[j][t];
     }
     __syncthreads();
     float local = 0.f;
-    for (int e = threadIdx.x; e < kTY * kTX; e += kLossThreads) {
-        const int r = e / kTX, q = e % kTX;
-        const int gy = y0 + kRad + r, gx = x0 + kRad + q;
-        if (gx >= W || gy >= H) continue;
-        float a = 0.f, b = 0.f, d = 0.f;
+    {
+        const int qc = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * kRun;
+        const int gx = x0 + kRad + qc;
+        float xs[kRun], ys[kRun];                 // loaded before the blur, used after it
 #pragma unroll
-        for (int k = 0; k < kWin; ++k) {
-            const float w = g.w[k];
-            a = fmaf(w, hs[0][r + k][q], a);
-            b = fmaf(w, hs[1][r + k][q], b);
-            d = fmaf(w, hs[2][r + k][q], d);
+        for (int t = 0; t < kRun; ++t) {
+            const int gy = y0 + kRad + r0 + t;
+            const bool in = gx < W && gy < H;
+            const int64_t i = plane + (int64_t)gy * W + gx;
+            xs[t] = in ? x[i] : 0.f;
+            ys[t] = in ? y[i] : 0.f;
         }
-        const int64_t i = plane + (int64_t)gy * W + gx;
-        const float xi = x[i], yi = y[i];
-        const float dssim = a + 2.f * xi * b + yi * d;
-        const float df = xi - yi;
-        local += fabsf(df);
-        const float sgn = df > 0.f ? inv_n : (df < 0.f ? -inv_n : 0.f);
-        dimg[i] = (1.f - lam) * sgn - lam * dssim;
+        float m[3][kRun];
+#pragma unroll
+        for (int t = 0; t < kRun; ++t)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) m[j][t] = 0.f;
+#pragma unroll
+        for (int k = 0; k < kSpan; ++k) {
+            float hv[3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) hv[j] = hs[j][r0 + k][qc];
+#pragma unroll
+            for (int t = 0; t < kRun; ++t) {
+                const int tap = k - t;
+                if (tap < 0 || tap >= kWin) continue;
+                const float w = g.w[tap];
+#pragma unroll
+                for (int j = 0; j < 3; ++j) m[j][t] = fmaf(w, hv[j], m[j][t]);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < kRun; ++t) {
+            const int gy = y0 + kRad + r0 + t;
+            if (gx >= W || gy >= H) continue;
+            const int64_t i = plane + (int64_t)gy * W + gx;
+            const float xi = xs[t], yi = ys[t];
+            const float dssim = m[0][t] + 2.f * xi * m[1][t] + yi * m[2][t];
+            const float df = xi - yi;
+            local += fabsf(df);
+            const float sgn = df > 0.f ? inv_n : (df < 0.f ? -inv_n : 0.f);
+            dimg[i] = (1.f - lam) * sgn - lam * dssim;
+        }
     }
     const float s = block_sum(local, red);
     if (threadIdx.x == 0) atomicAdd(l1_sum, s);

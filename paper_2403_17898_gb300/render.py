@@ -254,7 +254,7 @@ class Trainer(Renderer):
             self.sel_w, self.sel_cap, self.counts_t, self.dmeans, self.dscales, self.dquats,
             self.drec,
             self.grads["feat"], self.grads["offs"], self.grads["lv"], self._dmlp_struct,
-            self.db_scratch, st))
+            self.db_scratch, st, bf16=self.precision == "bf16"))
 
     def zero_grad(self):
         for t in self.grads.values():
