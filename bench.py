@@ -584,8 +584,14 @@ def run_profile(args):
     sc, mlp, cams = _workload()
     rd = Renderer(sc, mlp, cams[0].W, cams[0].H, sel_cap=200_000, pair_cap=4_000_000,
                   precision=args.precision)
+    gate = None
+    if args.gate:
+        # an untrained proposal network at p* = 0.5: the gate kernel's cost, not its quality
+        import synth
+        from paper_2403_17898_gb300 import proposal
+        gate = (proposal.ProposalNet(synth.proposal_mlp(seed=0)).w, 0.5)
     for i in range(args.warmup + args.steps):
-        rd.render(cams[(37 * i + 60) % len(cams)])
+        rd.render(cams[(37 * i + 60) % len(cams)], gate=gate)
     torch.cuda.synchronize()
     print(json.dumps({"profile_frames": args.warmup + args.steps, **rd.counts().__dict__}))
     return 0
@@ -628,6 +634,8 @@ def main():
                     help="skip the training-step measurements")
     ap.add_argument("--profile", action="store_true",
                     help="render a few frames only (the case profiled with ncu)")
+    ap.add_argument("--gate", action="store_true",
+                    help="with --profile: also run the proposal gate (untrained network)")
     ap.add_argument("--profile-train", action="store_true",
                     help="run a few training steps only (the case training kernels are profiled on)")
     ap.add_argument("--train-workload", default="street500k_1600x900",

@@ -46,9 +46,10 @@ __device__ __forceinline__ bool pixel_step(PixState& s, int idx, float p2, const
                                            const float4& B, const float2& Cc, float dx, float dy,
                                            float (&g)[16]) {
     if (idx >= s.last || !(p2 <= 0.f && p2 >= Cc.y)) return false;
-    const float raw = raw_alpha(B.y, p2);
+    const float G = ex2(p2);
+    const float raw = __fmul_rn(B.y, G);            // the forward's raw_alpha(o, p2)
     const float alpha = fminf(0.99f, raw);
-    s.T = s.T / (1.0f - alpha);                     // T_i, before this Gaussian
+    s.T = __fdividef(s.T, 1.0f - alpha);            // T_i, before this Gaussian
     const float wgt = alpha * s.T;
     g[6] += wgt * s.d0; g[7] += wgt * s.d1; g[8] += wgt * s.d2;
     const float dalpha = s.T * ((B.z - s.S0) * s.d0 + (B.w - s.S1) * s.d1 + (Cc.x - s.S2) * s.d2);
@@ -56,11 +57,14 @@ __device__ __forceinline__ bool pixel_step(PixState& s, int idx, float p2, const
     s.S1 = alpha * B.w + (1.0f - alpha) * s.S1;
     s.S2 = alpha * Cc.x + (1.0f - alpha) * s.S2;
     if (raw < 0.99f) {
-        // d alpha / d power = alpha, d alpha / d o = G = alpha / o; the record's conic is
-        // (a, b, c) with power = -0.5 (a dx^2 + c dy^2) - b dx dy, and a2 = -0.5 a log2e etc.
-        g[5] += dalpha * (alpha / B.y);
+        // d alpha / d power = alpha, d alpha / d o = G; the record's conic is (a, b, c) with
+        // power = -0.5 (a dx^2 + c dy^2) - b dx dy, recovered from a2 = -0.5 a log2e,
+        // b2 = -b log2e, c2 = -0.5 c log2e
+        g[5] += dalpha * G;
         const float dp = dalpha * alpha;
-        const float a = -2.0f * A.z / kLog2e, b = -A.w / kLog2e, c = -2.0f * B.x / kLog2e;
+        constexpr float kA = -1.3862943611198906f;     // -2 / log2(e) = -2 ln 2
+        constexpr float kB = -0.6931471805599453f;     // -1 / log2(e) = -ln 2
+        const float a = A.z * kA, b = A.w * kB, c = B.x * kA;
         g[0] += -dp * (a * dx + b * dy);
         g[1] += -dp * (c * dy + b * dx);
         g[2] += -0.5f * dp * dx * dx;

@@ -2,12 +2,11 @@
 // opacity blending of the next level, followed by an order-preserving compaction.
 //
 // HBM-bound streaming pass over the anchor SoA (pos 12 B + level 1 B + dL 4 B per anchor),
-// read once: a single-pass order-preserving compaction.  Each CTA stages one tile of anchors
-// in shared memory with TMA bulk copies (so the whole tile's bytes are in flight at once),
-// evaluates the predicate from there, ranks its kept anchors with warp ballots, obtains the
-// tile's output offset by a decoupled look-back over the predecessor tiles' published counts
-// (tiles are taken in ticket order, so every predecessor is already running) and scatters,
-// so sel_idx stays in ascending anchor order without a second pass or a global sort.
+// read once, then an order-preserving compaction: each CTA stages one tile of anchors in
+// shared memory with TMA bulk copies (so the whole tile's bytes are in flight at once) and
+// writes every anchor's weight (4 B) and the tile's kept count; one CTA scans the counts; the
+// scatter re-reads only the weights, ranks kept anchors with warp scans and writes them in
+// ascending anchor order.  No CTA waits on another, so every tile streams at full rate.
 #include "internal.cuh"
 #include "tc.cuh"
 
@@ -59,30 +58,20 @@ __device__ __forceinline__ bool keep_anchor(const SelArgs& a, float px, float py
     return false;
 }
 
-// Single pass: each CTA takes the next tile by ticket, evaluates the predicate for its
-// kSelChunk anchors (coalesced), counts them per (item, warp), publishes its count, looks
-// back for its exclusive offset and scatters its kept anchors in ascending order.
-__global__ void __launch_bounds__(kSelThreads) select_onepass(SelArgs a,
-                                                              unsigned long long* status,
-                                                              uint32_t* ticket, int nb,
-                                                              uint32_t* sel_idx, float* sel_w,
-                                                              int64_t cap, ogs_counts* counts,
-                                                              int bulk) {
+// Pass 1 (tile of kSelChunk anchors per CTA): the tile's anchor SoA lands in shared memory by
+// three TMA bulk copies (plain loads for a partial tile or unaligned arrays); the predicate
+// writes each anchor's opacity weight (0 = not kept, kept weights are > 0) and the tile's
+// kept count.
+__global__ void __launch_bounds__(kSelThreads) select_eval(SelArgs a, float* __restrict__ wsel,
+                                                           uint32_t* __restrict__ tile_count,
+                                                           ogs_counts* counts, int bulk) {
     __shared__ __align__(16) float s_pos[3 * kSelChunk];
     __shared__ __align__(16) float s_dl[kSelChunk];
     __shared__ __align__(16) uint8_t s_lvl[kSelChunk];
     __shared__ __align__(8) uint64_t mbar;
-    __shared__ uint32_t s_tile;
-    __shared__ uint32_t s_cnt[kSelItems * kSelWarps];
-    __shared__ uint32_t s_agg;
-    if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
-    __syncthreads();
-    const uint32_t tile = s_tile;
-    const int64_t base = (int64_t)tile * kSelChunk;
+    __shared__ uint32_t s_wc[kSelWarps];
+    const int64_t base = (int64_t)blockIdx.x * kSelChunk;
     const int n_here = (int)min((int64_t)kSelChunk, a.N - base);
-    const unsigned warp = threadIdx.x >> 5;
-    // stage the tile's anchor SoA in shared memory: three TMA bulk copies for a full tile of
-    // aligned arrays, cooperative loads otherwise
     if (bulk && n_here == kSelChunk) {
         if (threadIdx.x == 0) {
             tc::mbar_init(&mbar, 1);
@@ -93,7 +82,7 @@ __global__ void __launch_bounds__(kSelThreads) select_onepass(SelArgs a,
         }
         __syncthreads();                              // barrier initialised before anyone polls
         if (!tc::mbar_wait(&mbar, 0, kSpinLimit)) {
-            atomicExch(&counts->timeout, 1u);
+            if (threadIdx.x == 0) atomicExch(&counts->timeout, 1u);
             tc::mbar_wait(&mbar, 0, kSpinLimit);      // copies may still be landing
         }
     } else {
@@ -104,56 +93,127 @@ __global__ void __launch_bounds__(kSelThreads) select_onepass(SelArgs a,
         }
         __syncthreads();
     }
-    uint32_t keepbits = 0;
-    float w[kSelItems];
-    unsigned bal[kSelItems];
+    uint32_t mine = 0;
 #pragma unroll
     for (int it = 0; it < kSelItems; ++it) {
         const int l = it * kSelThreads + threadIdx.x;
-        w[it] = 0.0f;
+        float w = 0.0f;
         const bool keep = l < n_here && keep_anchor(a, s_pos[3 * l], s_pos[3 * l + 1],
-                                                    s_pos[3 * l + 2], s_lvl[l], s_dl[l], w[it]);
-        keepbits |= (uint32_t)keep << it;
-        bal[it] = __ballot_sync(0xffffffffu, keep);
-        if (lane_id() == 0) s_cnt[it * kSelWarps + warp] = __popc(bal[it]);
+                                                    s_pos[3 * l + 2], s_lvl[l], s_dl[l], w);
+        if (l < n_here) wsel[base + l] = keep ? w : 0.0f;
+        mine += __popc(__ballot_sync(0xffffffffu, keep));
+    }
+    if (lane_id() == 0) s_wc[threadIdx.x >> 5] = mine;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+#pragma unroll
+        for (int i = 0; i < kSelWarps; ++i) t += s_wc[i];
+        tile_count[blockIdx.x] = t;
+    }
+}
+
+// Pass 2 (one CTA): exclusive scan of the tile counts in place; M and the overflow state.
+__global__ void __launch_bounds__(1024) select_scan(uint32_t* __restrict__ tile_count, int nb,
+                                                    int64_t cap, int k, ogs_counts* counts) {
+    __shared__ unsigned long long ws[32];
+    const int per = (nb + 1023) / 1024;
+    const int b0 = threadIdx.x * per, b1 = min(b0 + per, nb);
+    unsigned long long local = 0;
+    for (int b = b0; b < b1; ++b) local += tile_count[b];
+    unsigned long long x = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane_id() >= (unsigned)o) x += y;
+    }
+    if (lane_id() == 31) ws[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        unsigned long long v = ws[threadIdx.x];
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane_id() >= (unsigned)o) v += y;
+        }
+        ws[threadIdx.x] = v;                          // inclusive warp totals
     }
     __syncthreads();
-    if (warp == 0) {
-        // exclusive scan of the 64 (item, warp) counts in output order, two per lane
-        const uint32_t c0 = s_cnt[2 * lane_id()], c1 = s_cnt[2 * lane_id() + 1];
-        uint32_t x = c0 + c1;
+    unsigned long long run = (threadIdx.x >= 32 ? ws[(threadIdx.x >> 5) - 1] : 0) + x - local;
+    for (int b = b0; b < b1; ++b) {
+        const uint32_t v = tile_count[b];
+        tile_count[b] = (uint32_t)min(run, 0xFFFFFFFFull);
+        run += v;
+    }
+    if (threadIdx.x == 0) {
+        const unsigned long long total = ws[31];
+        const uint32_t m = total > (unsigned long long)cap ? (uint32_t)cap : (uint32_t)total;
+        counts->n_selected = m;
+        counts->n_gaussians = m * (uint32_t)k;
+        counts->need_selected = total > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)total;
+        if (total > (unsigned long long)cap) atomicOr(&counts->overflow, 1u);
+    }
+}
+
+// Pass 3 (same tiles as pass 1): kept anchors ranked by warp ballots and written in
+// ascending order at the tile's offset (16-byte weight loads, four anchors per thread and
+// round).
+__global__ void __launch_bounds__(kSelThreads) select_scatter(const float* __restrict__ wsel,
+                                                              const uint32_t* __restrict__ tile_off,
+                                                              int64_t N, uint32_t* sel_idx,
+                                                              float* sel_w, int64_t cap) {
+    __shared__ uint32_t s_cnt[kSelItems / 4][kSelWarps];
+    const int64_t base = (int64_t)blockIdx.x * kSelChunk;
+    const int n_here = (int)min((int64_t)kSelChunk, N - base);
+    const unsigned warp = threadIdx.x >> 5;
+    constexpr int kRounds = kSelItems / 4;
+    float4 wv[kRounds];
+    uint32_t cnt[kRounds];
+#pragma unroll
+    for (int q = 0; q < kRounds; ++q) {
+        const int l = 4 * (q * kSelThreads + threadIdx.x);   // four consecutive anchors
+        float v[4];
+        if (l + 4 <= n_here && ((base & 3) == 0)) {
+            const float4 u = *reinterpret_cast<const float4*>(wsel + base + l);
+            v[0] = u.x; v[1] = u.y; v[2] = u.z; v[3] = u.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[e] = l + e < n_here ? wsel[base + l + e] : 0.f;
+        }
+        wv[q] = make_float4(v[0], v[1], v[2], v[3]);
+        cnt[q] = (v[0] > 0.f) + (v[1] > 0.f) + (v[2] > 0.f) + (v[3] > 0.f);
+        // warp-inclusive scan of the per-thread counts
+        uint32_t x = cnt[q];
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane_id() >= (unsigned)o) x += y;
         }
-        __syncwarp();
-        s_cnt[2 * lane_id()] = x - c0 - c1;
-        s_cnt[2 * lane_id() + 1] = x - c1;
-        if (lane_id() == 31) s_agg = x;
+        if (lane_id() == 31) s_cnt[q][warp] = x;
+        cnt[q] = x - cnt[q];                           // exclusive within the warp
     }
     __syncthreads();
-    const unsigned long long agg = s_agg;
-    const unsigned long long excl0 =
-        block_tile_offset<kSelThreads>(status, tile, agg, &counts->timeout);
-    if (threadIdx.x == 0 && tile == (uint32_t)nb - 1) {      // the last tile knows the total
-        const unsigned long long total = excl0 + agg;
-        const uint32_t m = total > (unsigned long long)cap ? (uint32_t)cap : (uint32_t)total;
-        counts->n_selected = m;
-        counts->n_gaussians = m * (uint32_t)a.k;
-        counts->need_selected = total > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)total;
-        if (total > (unsigned long long)cap) atomicOr(&counts->overflow, 1u);
-    }
-    const unsigned long long excl = excl0;
+    unsigned long long off = tile_off[blockIdx.x];
 #pragma unroll
-    for (int it = 0; it < kSelItems; ++it) {
-        if ((keepbits >> it) & 1u) {
-            const unsigned long long p = excl + s_cnt[it * kSelWarps + warp] +
-                                         __popc(bal[it] & lanemask_lt());
-            if (p < (unsigned long long)cap) {
-                sel_idx[p] = (uint32_t)(base + it * kSelThreads + threadIdx.x);
-                sel_w[p] = w[it];
+    for (int q = 0; q < kRounds; ++q) {
+        uint32_t before = 0, tot = 0;
+#pragma unroll
+        for (int i = 0; i < kSelWarps; ++i) {
+            const uint32_t c = s_cnt[q][i];
+            before += (i < (int)warp) ? c : 0;
+            tot += c;
+        }
+        unsigned long long p = off + before + cnt[q];
+        const int l = 4 * (q * kSelThreads + threadIdx.x);
+        const float v[4] = {wv[q].x, wv[q].y, wv[q].z, wv[q].w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (v[e] > 0.f) {
+                if (p < (unsigned long long)cap) {
+                    sel_idx[p] = (uint32_t)(base + l + e);
+                    sel_w[p] = v[e];
+                }
+                ++p;
             }
         }
+        off += tot;
     }
 }
 
@@ -164,7 +224,10 @@ using namespace ogs;
 
 extern "C" size_t ogs_lod_select_scratch_bytes(int64_t N) {
     int64_t nb = (N + kSelChunk - 1) / kSelChunk;
-    return (size_t)((nb < 1 ? 1 : nb) + 1) * sizeof(unsigned long long) + 256;
+    Carver cv(nullptr);
+    cv.take<uint32_t>((size_t)(nb < 1 ? 1 : nb));
+    cv.take<float>((size_t)(N > 0 ? N : 1));
+    return cv.off + 256;
 }
 
 extern "C" ogs_status ogs_lod_select(const float* pos, const uint8_t* level, const float* dL,
@@ -183,14 +246,13 @@ extern "C" ogs_status ogs_lod_select(const float* pos, const uint8_t* level, con
     SelArgs a{pos, level, dL, N, NL, k, infer, make_cam(*cam)};
     int nb = (int)((N + kSelChunk - 1) / kSelChunk);
     if (nb < 1) nb = 1;
-    // tile status words, then the ticket counter: all zero before the pass
-    unsigned long long* status = (unsigned long long*)scratch;
-    uint32_t* ticket = (uint32_t*)(status + nb);
-    if (cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * (nb + 1), st) != cudaSuccess)
-        return OGS_ERR_CUDA;
+    Carver cv(scratch);
+    uint32_t* tile_count = cv.take<uint32_t>((size_t)nb);
+    float* wsel = cv.take<float>((size_t)(N > 0 ? N : 1));
     const int bulk = aligned(pos, 16) && aligned(dL, 16) && aligned(level, 16);
-    select_onepass<<<nb, kSelThreads, 0, st>>>(a, status, ticket, nb, sel_idx, sel_w, sel_cap,
-                                               counts, bulk);
+    select_eval<<<nb, kSelThreads, 0, st>>>(a, wsel, tile_count, counts, bulk);
+    select_scan<<<1, 1024, 0, st>>>(tile_count, nb, sel_cap, k, counts);
+    select_scatter<<<nb, kSelThreads, 0, st>>>(wsel, tile_count, N, sel_idx, sel_w, sel_cap);
     return launch_status();
 }
 
