@@ -422,3 +422,116 @@ def photometric_loss(img, target, lam=0.2):
     l1, g1 = l1_loss(img, target)
     s, gs = ssim(img, target)
     return (1 - lam) * l1 + lam * (1 - s), (1 - lam) * g1 - lam * gs
+
+
+# ----------------------------------------------------------------------------------------
+# view-frequency pruning (Sec. 4.2.2 "Anchor Pruning")
+# ----------------------------------------------------------------------------------------
+
+def view_frequency_counts(N, selections):
+    """Number of training views in which each of the N anchors was selected: the numerator
+    of the view frequency (the probability that an anchor is selected in the training
+    views).  ``selections`` holds one array of selected anchor indices per view.  Pinned by
+    hand-built selections and by recounting oracle selections anchor by anchor."""
+    count = np.zeros(N, np.int64)
+    for sel in selections:
+        for j in np.asarray(sel, np.int64):
+            count[j] += 1
+    return count
+
+
+def prune_by_view_frequency(count, n_views, tau_v):
+    """Anchors kept by view-frequency pruning: those whose frequency count / n_views is not
+    below the visibility threshold tau_v, in ascending index order.  Pinned by hand cases at
+    the threshold (a frequency equal to tau_v is kept), tau_v = 0 (all kept) and tau_v > 1
+    (none kept), and monotonicity in tau_v."""
+    count = np.asarray(count, np.int64)
+    freq = count.astype(np.float64) / float(n_views)
+    return np.nonzero(~(freq < float(tau_v)))[0].astype(np.int64)
+
+
+def min_count_for(n_views, tau_v):
+    """Smallest selection count whose frequency count / n_views is not below tau_v (the
+    integer form of the pruning test, evaluated with the same float64 division)."""
+    c = int(np.ceil(float(tau_v) * n_views))
+    while c > 0 and not ((c - 1) / float(n_views) < float(tau_v)):
+        c -= 1
+    while c / float(n_views) < float(tau_v):
+        c += 1
+    return c
+
+
+# ----------------------------------------------------------------------------------------
+# explicit Gaussians per anchor ("Our-3D-GS", Sec. 5 and Sec. 3.2 Eq. offsets)
+# ----------------------------------------------------------------------------------------
+
+SH_C0 = 0.28209479177387814          # degree-0 spherical harmonic, 1 / (2 sqrt(pi))
+
+
+def explicit_gaussians(sel_idx, sel_w, scene, attr):
+    """The k explicit 3D Gaussians of every selected anchor, in place of the decoders:
+    position x_v + O_i * l_v (Eq. offsets), scale exp(s_i), unit quaternion q_i / |q_i|
+    (w, x, y, z), opacity sigmoid(a_i) times the anchor's LOD weight, colour from the
+    degree-0 spherical harmonic max(0, SH_C0 f_i + 1/2) (the cited 3D-GS activations).
+    ``attr`` holds log_scale [N][k][3], quat [N][k][4], opacity [N][k] (logits) and
+    color_dc [N][k][3].  World-space means.  Pinned by activation closed forms and the
+    offset composition."""
+    sel = np.asarray(sel_idx, np.int64)
+    w = _d(sel_w)
+    k = scene.k
+    pos, offs, lv = _d(scene.pos)[sel], _d(scene.offs)[sel], _d(scene.lv)[sel]
+    means = pos[:, None, :] + offs * lv[:, None, :]
+    scales = np.exp(_d(attr["log_scale"])[sel])
+    q = _d(attr["quat"])[sel]
+    quats = q / np.linalg.norm(q, axis=-1, keepdims=True)
+    opac = w[:, None] / (1.0 + np.exp(-_d(attr["opacity"])[sel]))
+    colors = np.maximum(SH_C0 * _d(attr["color_dc"])[sel] + 0.5, 0.0)
+    M = len(sel)
+    return dict(means=means.reshape(M * k, 3), scales=scales.reshape(M * k, 3),
+                quats=quats.reshape(M * k, 4), opac=opac.reshape(M * k),
+                colors=colors.reshape(M * k, 3))
+
+
+def explicit_gaussians_bwd(sel_idx, sel_w, scene, attr, g):
+    """Gradients of explicit_gaussians for per-Gaussian upstream gradients g (dmeans,
+    dscales, dquats, dopac, dcolors): d log_scale, d quat, d opacity logit, d color_dc and
+    the offsets / scalings terms (doffs, dlv), accumulated per anchor.  Pinned by central
+    finite differences of explicit_gaussians."""
+    sel = np.asarray(sel_idx, np.int64)
+    w = _d(sel_w)
+    k = scene.k
+    N = scene.N
+    M = len(sel)
+    sh = lambda a, c: _d(a).reshape(M, k, c)
+    offs, lv = _d(scene.offs)[sel], _d(scene.lv)[sel]
+    s = _d(attr["log_scale"])[sel]
+    q = _d(attr["quat"])[sel]
+    a = _d(attr["opacity"])[sel]
+    f = _d(attr["color_dc"])[sel]
+    dmeans, dscales, dquats = sh(g["dmeans"], 3), sh(g["dscales"], 3), sh(g["dquats"], 4)
+    dopac, dcolors = _d(g["dopac"]).reshape(M, k), sh(g["dcolors"], 3)
+    out = dict(dlog_scale=np.zeros((N, k, 3)), dquat=np.zeros((N, k, 4)),
+               dopacity=np.zeros((N, k)), dcolor_dc=np.zeros((N, k, 3)),
+               doffs=np.zeros((N, k, 3)), dlv=np.zeros((N, 3)))
+    n = np.linalg.norm(q, axis=-1, keepdims=True)
+    qn = q / n
+    sg = 1.0 / (1.0 + np.exp(-a))
+    np.add.at(out["dlog_scale"], sel, dscales * np.exp(s))
+    np.add.at(out["dquat"], sel, (dquats - qn * (qn * dquats).sum(-1, keepdims=True)) / n)
+    np.add.at(out["dopacity"], sel, dopac * w[:, None] * sg * (1.0 - sg))
+    np.add.at(out["dcolor_dc"], sel, np.where(SH_C0 * f + 0.5 > 0.0, dcolors * SH_C0, 0.0))
+    np.add.at(out["doffs"], sel, dmeans * lv[:, None, :])
+    np.add.at(out["dlv"], sel, (dmeans * offs).sum(1))
+    return out
+
+
+def render_explicit(scene, attr, cam, infer=True, bg=(0.0, 0.0, 0.0)):
+    """The forward pass of one view with explicit Gaussians in place of the decoders."""
+    sel_idx, sel_w, margin = lod_select(scene.pos, scene.level, scene.dL, scene.NL, cam, infer)
+    g = explicit_gaussians(sel_idx, sel_w, scene, attr)
+    pr = project(g["means"], g["scales"], g["quats"], g["opac"], cam)
+    gx, gy = grid(cam.W, cam.H)
+    start, lst, tie = tile_lists(pr["rect"], pr["depth"], gx, gy)
+    out = blend(cam.W, cam.H, start, lst, pr["uv"], pr["conic"], g["opac"], g["colors"], bg,
+                depth=pr["depth"])
+    return Frame(sel_idx, sel_w, margin, g, pr, start, lst, tie, out, gx, gy)

@@ -26,7 +26,7 @@ __all__ = [
     "cube_scene", "city_scene", "decoder_mlp", "proposal_mlp",
     "look_at_camera", "zoom_out_path", "trajectory_d_max", "proposal_poses",
     "random_gaussians", "random_records", "random_rects_depths", "random_sort_keys",
-    "CONFIGS",
+    "explicit_attributes", "CONFIGS",
 ]
 
 F_DIM = 32      # anchor feature width (all configs)
@@ -528,3 +528,18 @@ CONFIGS = {
     "city2M_1080p_heldout60": _cfg3_heldout_poses,
     "city8M_1080p": _cfg5,
 }
+
+
+def explicit_attributes(scene, seed=0):
+    """Seeded per-Gaussian attributes for the explicit-Gaussian variant: log-scales around
+    20-80 % of the anchor's cell (l_v), random quaternions, opacity logits N(0.5, 1) and
+    degree-0 colour coefficients N(0, 1.5)."""
+    rng = np.random.default_rng(seed)
+    N, k = scene.N, scene.k
+    frac = rng.uniform(0.2, 0.8, size=(N, k, 3))
+    return dict(
+        log_scale=np.log(scene.lv[:, None, :].astype(np.float64) * frac).astype(np.float32),
+        quat=rng.normal(size=(N, k, 4)).astype(np.float32),
+        opacity=rng.normal(0.5, 1.0, size=(N, k)).astype(np.float32),
+        color_dc=rng.normal(0.0, 1.5, size=(N, k, 3)).astype(np.float32),
+    )
