@@ -292,6 +292,31 @@ TRAIN_WORKLOADS = (
 )
 
 
+PRUNE_TAU_V = 0.01          # the paper's visibility threshold for large-scale scenes
+
+
+def _explicit_bench(cams, pose, steps, warmup, flush, clk_index):
+    """1080p frames/s of the explicit-Gaussian variant (each anchor's k Gaussians carry their
+    own attributes, no decoders) on the same scene and path; the rest of the path is shared."""
+    import torch
+    import synth
+    from paper_2403_17898_gb300.render import Renderer
+    sc, mlp, _ = _workload()
+    attr = synth.explicit_attributes(sc, seed=0)
+    W, H = cams[0].W, cams[0].H
+    rd = Renderer(sc, None, W, H, sel_cap=200_000, pair_cap=6_000_000, explicit=attr)
+    for cam in cams:                      # size the buffers on every pose
+        rd.render(cam)
+    t, stages, clk = _time_form(rd, cams, pose, steps, warmup, None, flush, clk_index)
+    out = {"value": steps / t, "unit": "frames/s", "ms_per_step": 1e3 * t / steps,
+           "stages_ms": {k: round(v, 5) for k, v in stages.items()},
+           "workload": "same 2M anchors and 120-pose path; 10 explicit 3D Gaussians per anchor "
+                       "(seeded attributes) in place of the decoders"}
+    del rd
+    torch.cuda.empty_cache()
+    return out
+
+
 def _train_bench(clk_index, steps_scale=1.0):
     """Training steps per second of both training workloads, plain FP32 decode and BF16
     decode: each step clears the gradients, runs forward + loss + backward for its views and
@@ -306,7 +331,8 @@ def _train_bench(clk_index, steps_scale=1.0):
         W, H = cams[0].W, cams[0].H
         stride = max(1, len(cams) // 16) if vps > 1 else 1
         views = cams[::stride][:vps] if vps > 1 else cams
-        tr = Trainer(sc, mlp, W, H, ssim_lambda=lam, sel_cap=400_000, pair_cap=8_000_000)
+        tr = Trainer(sc, mlp, W, H, ssim_lambda=lam, sel_cap=400_000, pair_cap=8_000_000,
+                     track_view_frequency=True)
         del sc
         gen = torch.Generator(device="cuda")
         gen.manual_seed(1)
@@ -324,17 +350,19 @@ def _train_bench(clk_index, steps_scale=1.0):
                "l2": "no flush: every step streams the dense Adam state (>= 1 GB) through L2",
                "max_selected": sel_max, "max_pairs": pair_max}
         # both forms start from the same parameters and optimiser state
-        init = {n: getattr(tr, n).clone() for n in tr.PARAMS}
+        init = {n: t.clone() for n, t in tr._anchor_params().items()}
         init.update({"mlp." + n: t.clone() for n, t in tr.mlp.items()})
         for precision in ("fp32", "bf16"):
-            for n in tr.PARAMS:
-                getattr(tr, n).copy_(init[n])
+            for n, t in tr._anchor_params().items():
+                t.copy_(init[n])
             for n, t in tr.mlp.items():
                 t.copy_(init["mlp." + n])
             for t in list(tr.adam_m.values()) + list(tr.adam_v.values()):
                 t.zero_()
             tr.zero_grad()
             tr.step_count = 0
+            tr.sel_count.zero_()
+            tr.n_views_seen = 0
             tr.precision = precision
             batch = lambda i: ([views[(i * vps + v) % len(views)] for v in range(vps)],
                                [targets[(i * vps + v) % n_t] for v in range(vps)])
@@ -355,6 +383,18 @@ def _train_bench(clk_index, steps_scale=1.0):
             ms = [a.elapsed_time(b) for a, b in ev]
             stages = {k: round(float(np.sum([a.elapsed_time(b) for a, b in v])) / K, 4)
                       for k, v in timers.items()}
+            if precision == "bf16":
+                # view-frequency pruning (Sec. 4.2.2) after the counted training views
+                n_before, n_views = tr.N, tr.n_views_seen
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                n_after = tr.prune(PRUNE_TAU_V)
+                torch.cuda.synchronize()
+                res["view_frequency_prune"] = {
+                    "tau_v": PRUNE_TAU_V, "views_counted": n_views, "anchors_before": n_before,
+                    "anchors_after": n_after, "seconds": time.perf_counter() - t0,
+                    "note": "count, order-preserving compaction and gather of every per-anchor "
+                            "array and its Adam state, all on the GPU"}
             res[precision] = {"train_steps_per_s": 1e3 * K / float(np.sum(ms)),
                               "ms_per_step": float(np.mean(ms)), "stages_ms_per_step": stages,
                               "loss_last_step": float(tr.loss.item()),
@@ -565,6 +605,8 @@ def run_gpu(args):
     if ws == 1 and not args.no_train:
         del rd
         torch.cuda.empty_cache()
+        line["explicit_3dgs"] = _explicit_bench(cams, pose, min(args.steps, 600), args.warmup,
+                                                flush, local)
         line["train"] = _train_bench(local)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(*_as_f64(sc, mlp), cams)

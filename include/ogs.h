@@ -9,6 +9,8 @@
  *   ogs_sort         per-tile Gaussian lists in front-to-back order         (Sec. 3.1)
  *   ogs_blend_fwd    per-pixel front-to-back alpha blending                 (Sec. 3.1, Eq. 2)
  *   ogs_blend_bwd, ogs_project_bwd, ogs_decode_bwd   analytic backward (training)
+ *   ogs_explicit_gaussians(_bwd)   explicit per-anchor Gaussians in place of decoding
+ *   ogs_count_selected, ogs_prune_anchors, ogs_gather_rows   view-frequency pruning
  *
  * Conventions shared by every entry point
  *   - Every pointer argument is a DEVICE pointer unless its comment says "host".  All device
@@ -366,6 +368,64 @@ int64_t ogs_radix_sort_pairs_noalloc_max_items(void);
 ogs_status ogs_radix_sort_pairs_noalloc(uint32_t* keys, uint32_t* vals, const uint32_t* n_dev,
                                         int64_t n_cap, int32_t bit_lo, int32_t bit_hi,
                                         void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Explicit Gaussians per anchor ("Our-3D-GS", Sec. 5): each anchor carries k explicit 3D
+ * Gaussians (per-Gaussian SoA, anchor-major: element [j][i] of anchor j, slot i):
+ *   log_scale f32[N][k][3], quat f32[N][k][4] (w, x, y, z; 16-byte aligned), opacity
+ *   f32[N][k] (logits), color_dc f32[N][k][3] (degree-0 spherical-harmonic coefficients)
+ * ------------------------------------------------------------------------------------- */
+typedef struct ogs_explicit {
+    const float* log_scale;
+    const float* quat;
+    const float* opacity;
+    const float* color_dc;
+} ogs_explicit;
+
+/* ogs_explicit_gaussians — in place of ogs_decode: for every selected anchor j (weight w) and
+ * slot i, mean x_j - campos + O_ji * l_j (Eq. offsets, camera-relative like ogs_decode),
+ * scale exp(log_scale), unit quaternion, opacity w sigmoid(opacity), colour
+ * max(0, 0.28209479 color_dc + 1/2) (the cited 3D-GS activations).  Reads M from
+ * counts->n_selected; writes Gaussians 0 .. M*k-1 of out (same layout as ogs_decode). */
+ogs_status ogs_explicit_gaussians(const float* pos, const float* offs, const float* lv,
+                                  int64_t N, int32_t k, const ogs_explicit* attr /* host */,
+                                  const ogs_camera* cam /* host */, const uint32_t* sel_idx,
+                                  const float* sel_w, int64_t sel_cap, const ogs_counts* counts,
+                                  const ogs_gaussians* out /* host struct */, void* stream);
+
+/* ogs_explicit_gaussians_bwd — backward of ogs_explicit_gaussians: per-Gaussian dmeans,
+ * dscales, dquats (ogs_project_bwd) and the opacity / colour gradients of drec
+ * (ogs_blend_bwd) into grad (same layout as attr, ACCUMULATED), doffs f32[N][k][3] and
+ * dlv f32[N][3] (ACCUMULATED). */
+ogs_status ogs_explicit_gaussians_bwd(const float* pos, const float* offs, const float* lv,
+                                      int64_t N, int32_t k, const ogs_explicit* attr /* host */,
+                                      const ogs_camera* cam /* host */, const uint32_t* sel_idx,
+                                      const float* sel_w, int64_t sel_cap,
+                                      const ogs_counts* counts, const float* dmeans,
+                                      const float* dscales, const float* dquats,
+                                      const float* drec, const ogs_explicit* grad /* host */,
+                                      float* doffs, float* dlv, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * View-frequency anchor pruning (Sec. 4.2.2): anchors whose view frequency (fraction of the
+ * training views that select them) is below tau_v are removed.
+ *   ogs_count_selected: sel_count[j] += 1 for the counts->n_selected entries of sel_idx
+ *   (one view's selection; an anchor appears at most once per view).
+ *   ogs_prune_anchors: keep_idx u32[N] receives, in ascending order, the anchors with
+ *   sel_count >= min_count, and *n_kept (device) their number.  min_count is the smallest
+ *   count whose frequency count / n_views is not below tau_v (computed by the caller).
+ *   scratch: ogs_prune_scratch_bytes(N) bytes, 16-byte aligned.
+ *   ogs_gather_rows: dst row r = src row keep_idx[r] for r < min(*n_dev, n_cap) (n_dev may
+ *   be NULL: n_cap rows); rows of row_bytes bytes (any per-anchor array); src != dst.
+ * ------------------------------------------------------------------------------------- */
+ogs_status ogs_count_selected(const uint32_t* sel_idx, const ogs_counts* counts,
+                              uint32_t* sel_count, void* stream);
+size_t ogs_prune_scratch_bytes(int64_t N);
+ogs_status ogs_prune_anchors(const uint32_t* sel_count, int64_t N, uint32_t min_count,
+                             uint32_t* keep_idx, uint32_t* n_kept, void* scratch,
+                             size_t scratch_bytes, void* stream);
+ogs_status ogs_gather_rows(const void* src, void* dst, int64_t row_bytes, const uint32_t* idx,
+                           const uint32_t* n_dev, int64_t n_cap, void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * Learned anchor-visibility proposal (not in the paper: a gate in front of decoding).  A

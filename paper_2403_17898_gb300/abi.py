@@ -57,6 +57,10 @@ _I64 = C.c_int64
 _I32 = C.c_int32
 _SZ = C.c_size_t
 
+class Explicit(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("log_scale", "quat", "opacity", "color_dc")]
+
+
 _SIGS = {
     "ogs_lod_select_scratch_bytes": (_SZ, [_I64]),
     "ogs_lod_select": (C.c_int, [_P, _P, _P, _I64, _I32, _I32, C.POINTER(Camera), _I32, _P, _P,
@@ -103,6 +107,16 @@ _SIGS = {
     "ogs_proposal_train": (C.c_int, [_P, _P, _P, _I64, _I32, C.POINTER(Camera),
                                      C.POINTER(Proposal), _P, _P, _P, C.c_float, C.c_float,
                                      C.POINTER(Proposal), _P, _P, _SZ, _P]),
+    "ogs_explicit_gaussians": (C.c_int, [_P, _P, _P, _I64, _I32, C.POINTER(Explicit),
+                                         C.POINTER(Camera), _P, _P, _I64, _P,
+                                         C.POINTER(Gaussians), _P]),
+    "ogs_explicit_gaussians_bwd": (C.c_int, [_P, _P, _P, _I64, _I32, C.POINTER(Explicit),
+                                             C.POINTER(Camera), _P, _P, _I64, _P, _P, _P, _P,
+                                             _P, C.POINTER(Explicit), _P, _P, _P]),
+    "ogs_count_selected": (C.c_int, [_P, _P, _P, _P]),
+    "ogs_prune_scratch_bytes": (_SZ, [_I64]),
+    "ogs_prune_anchors": (C.c_int, [_P, _I64, C.c_uint32, _P, _P, _P, _SZ, _P]),
+    "ogs_gather_rows": (C.c_int, [_P, _P, _I64, _P, _P, _I64, _P]),
     "ogs_version": (C.c_char_p, []),
 }
 
@@ -374,3 +388,62 @@ def proposal_train(pos, level, feat, N, NL, cam, net, sel_idx, counts, maxc, tau
 
 def version():
     return lib().ogs_version().decode()
+
+
+# ---------------------------------------------------------------------------------------
+# explicit Gaussians per anchor and view-frequency pruning
+# ---------------------------------------------------------------------------------------
+
+EXPLICIT_NAMES = ("log_scale", "quat", "opacity", "color_dc")
+
+
+def explicit_struct(t) -> Explicit:
+    """Explicit per-Gaussian attributes (dict of CUDA float32 tensors)."""
+    e = Explicit()
+    for n in EXPLICIT_NAMES:
+        setattr(e, n, t[n].data_ptr())
+    return e
+
+
+def explicit_gaussians(pos, offs, lv, N, k, attr, cam, sel_idx, sel_w, sel_cap, counts, out,
+                       stream=None):
+    c = cam if isinstance(cam, Camera) else camera(cam)
+    e = attr if isinstance(attr, Explicit) else explicit_struct(attr)
+    g = out if isinstance(out, Gaussians) else gaussians_struct(out)
+    _check(lib().ogs_explicit_gaussians(_ptr(pos), _ptr(offs), _ptr(lv), int(N), int(k),
+                                        C.byref(e), C.byref(c), _ptr(sel_idx), _ptr(sel_w),
+                                        int(sel_cap), _ptr(counts), C.byref(g), _stream(stream)),
+           "ogs_explicit_gaussians")
+
+
+def explicit_gaussians_bwd(pos, offs, lv, N, k, attr, cam, sel_idx, sel_w, sel_cap, counts,
+                           dmeans, dscales, dquats, drec, grad, doffs, dlv, stream=None):
+    c = cam if isinstance(cam, Camera) else camera(cam)
+    e = attr if isinstance(attr, Explicit) else explicit_struct(attr)
+    ge = grad if isinstance(grad, Explicit) else explicit_struct(grad)
+    _check(lib().ogs_explicit_gaussians_bwd(_ptr(pos), _ptr(offs), _ptr(lv), int(N), int(k),
+                                            C.byref(e), C.byref(c), _ptr(sel_idx), _ptr(sel_w),
+                                            int(sel_cap), _ptr(counts), _ptr(dmeans),
+                                            _ptr(dscales), _ptr(dquats), _ptr(drec),
+                                            C.byref(ge), _ptr(doffs), _ptr(dlv), _stream(stream)),
+           "ogs_explicit_gaussians_bwd")
+
+
+def count_selected(sel_idx, counts, sel_count, stream=None):
+    _check(lib().ogs_count_selected(_ptr(sel_idx), _ptr(counts), _ptr(sel_count),
+                                    _stream(stream)), "ogs_count_selected")
+
+
+def prune_scratch_bytes(N):
+    return int(lib().ogs_prune_scratch_bytes(int(N)))
+
+
+def prune_anchors(sel_count, N, min_count, keep_idx, n_kept, scratch, stream=None):
+    _check(lib().ogs_prune_anchors(_ptr(sel_count), int(N), int(min_count), _ptr(keep_idx),
+                                   _ptr(n_kept), _ptr(scratch), scratch.numel(), _stream(stream)),
+           "ogs_prune_anchors")
+
+
+def gather_rows(src, dst, row_bytes, idx, n_dev, n_cap, stream=None):
+    _check(lib().ogs_gather_rows(_ptr(src), _ptr(dst), int(row_bytes), _ptr(idx), _ptr(n_dev),
+                                 int(n_cap), _stream(stream)), "ogs_gather_rows")

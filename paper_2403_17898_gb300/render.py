@@ -7,6 +7,8 @@ from __future__ import annotations
 
 from dataclasses import dataclass
 
+import math
+
 import numpy as np
 import torch
 
@@ -53,7 +55,11 @@ class Renderer:
     pairs; ``render(..., check=True)`` grows them and re-renders when a view overflows.
     """
 
-    def __init__(self, scene, mlp, W, H, sel_cap=None, pair_cap=None, k=10, precision="fp32"):
+    def __init__(self, scene, mlp, W, H, sel_cap=None, pair_cap=None, k=10, precision="fp32",
+                 explicit=None):
+        """``explicit``: per-Gaussian attributes (dict log_scale, quat, opacity, color_dc of
+        [N][k][...] arrays) for the explicit-Gaussian variant; then ``mlp`` is unused and each
+        anchor's k Gaussians come from ogs_explicit_gaussians instead of the decoders."""
         assert precision in ("fp32", "bf16")
         self.precision = precision
         self.k = k
@@ -68,8 +74,14 @@ class Renderer:
         self.offs = _cuda(scene.offs, torch.float32)
         self.lv = _cuda(scene.lv, torch.float32)
         names = ("w1", "b1", "w2_op", "b2_op", "w2_col", "b2_col", "w2_cov", "b2_cov")
-        self.mlp = {n: _cuda(a, torch.float32) for n, a in zip(names, mlp.arrays())}
-        self._mlp_struct = abi.mlp_struct(self.mlp, k=k)
+        self.explicit = None
+        if explicit is not None:
+            self.explicit = {n: _cuda(explicit[n], torch.float32) for n in abi.EXPLICIT_NAMES}
+            self.mlp = {}
+            self._mlp_struct = None
+        else:
+            self.mlp = {n: _cuda(a, torch.float32) for n, a in zip(names, mlp.arrays())}
+            self._mlp_struct = abi.mlp_struct(self.mlp, k=k)
         self.sel_cap = int(sel_cap if sel_cap is not None else max(1024, self.N))
         self.pair_cap = int(pair_cap if pair_cap is not None else 1 << 20)
         self.sel_scratch = torch.empty(abi.lod_select_scratch_bytes(self.N), dtype=torch.uint8,
@@ -136,10 +148,15 @@ class Renderer:
                 self.sel_w_g, None, self.gate_scratch, st, bf16=self.precision == "bf16"))
             sel, selw = self.sel_idx_g, self.sel_w_g
         self.active_sel = sel
-        dec = abi.decode_bf16 if self.precision == "bf16" else abi.decode
-        stage("decode", lambda: dec(
-            self.pos, self.feat, self.offs, self.lv, self.N, self._mlp_struct, c, sel, selw,
-            self.sel_cap, self.counts_t, self._g_struct, st))
+        if self.explicit is not None:
+            stage("decode", lambda: abi.explicit_gaussians(
+                self.pos, self.offs, self.lv, self.N, self.k, self.explicit, c, sel, selw,
+                self.sel_cap, self.counts_t, self._g_struct, st))
+        else:
+            dec = abi.decode_bf16 if self.precision == "bf16" else abi.decode
+            stage("decode", lambda: dec(
+                self.pos, self.feat, self.offs, self.lv, self.N, self._mlp_struct, c, sel, selw,
+                self.sel_cap, self.counts_t, self._g_struct, st))
         stage("project_bin", lambda: abi.project_bin(
             self._g_struct, self.g_cap, 1, c, self.rec, self.depth_key, self.rect, self.tiles,
             self.counts_t, st, tile_count=self.tile_count))
@@ -183,26 +200,37 @@ class Renderer:
         raise abi.OgsError("buffers kept overflowing")
 
 
+def min_count_for(n_views, tau_v):
+    """Smallest selection count whose view frequency count / n_views is not below tau_v
+    (Sec. 4.2.2: anchors below the threshold are pruned), with the division in float64."""
+    c = int(math.ceil(float(tau_v) * n_views))
+    while c > 0 and not ((c - 1) / float(n_views) < float(tau_v)):
+        c -= 1
+    while c / float(n_views) < float(tau_v):
+        c += 1
+    return c
+
+
 class Trainer(Renderer):
     """One optimisation step over a batch of views: for each view the training-mode forward
-    (no next-level anchors), the L1 loss against its target, and the backward chain
-    blend_bwd -> project_bwd -> decode_bwd accumulating anchor and decoder gradients; then one
-    fused Adam update of features, offsets, scalings and decoder weights."""
-
-    PARAMS = ("feat", "offs", "lv")
+    (no next-level anchors), the loss against its target, and the backward chain
+    blend_bwd -> project_bwd -> decode_bwd (or the explicit-Gaussian backward) accumulating
+    the anchor and decoder gradients; then one Adam update of every trainable array.  With
+    ``track_view_frequency`` every training view's selection is counted per anchor, and
+    ``prune(tau_v)`` removes the anchors whose view frequency is below tau_v."""
 
     def __init__(self, scene, mlp, W, H, lr=1e-3, betas=(0.9, 0.999), eps=1e-15, ssim_lambda=0.0,
-                 **kw):
+                 track_view_frequency=False, **kw):
         super().__init__(scene, mlp, W, H, **kw)
         self.ssim_lambda = float(ssim_lambda)   # 0.2 gives the 0.8 L1 + 0.2 D-SSIM loss
         self.lr, self.betas, self.eps = lr, betas, eps
         self.step_count = 0
         dev = "cuda"
-        self.grads = {n: torch.zeros_like(getattr(self, n)) for n in self.PARAMS}
+        self.grads = {n: torch.zeros_like(t) for n, t in self._anchor_params().items()}
         self.dmlp = {n: torch.zeros_like(t) for n, t in self.mlp.items()}
-        self._dmlp_struct = abi.mlp_struct(self.dmlp, k=self.k)
-        self.adam_m = {n: torch.zeros_like(getattr(self, n)) for n in self.PARAMS}
-        self.adam_v = {n: torch.zeros_like(getattr(self, n)) for n in self.PARAMS}
+        self._dmlp_struct = abi.mlp_struct(self.dmlp, k=self.k) if self.mlp else None
+        self.adam_m = {n: torch.zeros_like(t) for n, t in self._anchor_params().items()}
+        self.adam_v = {n: torch.zeros_like(t) for n, t in self._anchor_params().items()}
         for n, t in self.mlp.items():
             self.adam_m["mlp." + n] = torch.zeros_like(t)
             self.adam_v["mlp." + n] = torch.zeros_like(t)
@@ -212,7 +240,19 @@ class Trainer(Renderer):
         if self.ssim_lambda > 0:
             self.loss_scratch = torch.empty(abi.loss_l1_ssim_scratch_bytes(3, self.H, self.W),
                                             dtype=torch.uint8, device=dev)
+        self.track_view_frequency = bool(track_view_frequency)
+        self.sel_count = torch.zeros(self.N, dtype=torch.int32, device=dev)
+        self.n_views_seen = 0
         self._alloc_grad()
+
+    def _anchor_params(self):
+        """Trainable per-anchor arrays: features, offsets and l_v of the neural form; offsets,
+        l_v and the explicit attributes of the explicit form."""
+        if self.explicit is not None:
+            out = {"offs": self.offs, "lv": self.lv}
+            out.update({"ex." + n: t for n, t in self.explicit.items()})
+            return out
+        return {"feat": self.feat, "offs": self.offs, "lv": self.lv}
 
     def _alloc(self):
         super()._alloc()
@@ -249,12 +289,19 @@ class Trainer(Renderer):
         _stage(timers, "project_bwd", st, lambda: abi.project_bwd(
             self._g_struct, self.g_cap, 1, c, self.rect, self.drec, self.dmeans, self.dscales,
             self.dquats, self.counts_t, st))
-        _stage(timers, "decode_bwd", st, lambda: abi.decode_bwd(
-            self.pos, self.feat, self.offs, self.lv, self.N, self._mlp_struct, c, self.sel_idx,
-            self.sel_w, self.sel_cap, self.counts_t, self.dmeans, self.dscales, self.dquats,
-            self.drec,
-            self.grads["feat"], self.grads["offs"], self.grads["lv"], self._dmlp_struct,
-            self.db_scratch, st, bf16=self.precision == "bf16"))
+        if self.explicit is not None:
+            gex = {n: self.grads["ex." + n] for n in abi.EXPLICIT_NAMES}
+            _stage(timers, "decode_bwd", st, lambda: abi.explicit_gaussians_bwd(
+                self.pos, self.offs, self.lv, self.N, self.k, self.explicit, c, self.sel_idx,
+                self.sel_w, self.sel_cap, self.counts_t, self.dmeans, self.dscales,
+                self.dquats, self.drec, gex, self.grads["offs"], self.grads["lv"], st))
+        else:
+            _stage(timers, "decode_bwd", st, lambda: abi.decode_bwd(
+                self.pos, self.feat, self.offs, self.lv, self.N, self._mlp_struct, c,
+                self.sel_idx, self.sel_w, self.sel_cap, self.counts_t, self.dmeans,
+                self.dscales, self.dquats, self.drec, self.grads["feat"], self.grads["offs"],
+                self.grads["lv"], self._dmlp_struct, self.db_scratch, st,
+                bf16=self.precision == "bf16"))
 
     def zero_grad(self):
         for t in self.grads.values():
@@ -266,7 +313,7 @@ class Trainer(Renderer):
         self.step_count += 1
         b1, b2 = self.betas
         st = stream if stream is not None else torch.cuda.current_stream()
-        pairs = [(getattr(self, n), self.grads[n], n) for n in self.PARAMS]
+        pairs = [(t, self.grads[n], n) for n, t in self._anchor_params().items()]
         pairs += [(self.mlp[n], self.dmlp[n], "mlp." + n) for n in self.mlp]
 
         def run():
@@ -282,6 +329,45 @@ class Trainer(Renderer):
         self.loss.zero_()
         for cam, tgt in zip(cams, targets):
             self.enqueue(cam, infer=False, bg=bg, timers=timers)
+            if self.track_view_frequency:
+                abi.count_selected(self.sel_idx, self.counts_t, self.sel_count)
+                self.n_views_seen += 1
             self.backward_view(cam, tgt, bg, timers=timers)
         if update:
             self.optimizer_step(timers=timers)
+
+    def prune(self, tau_v):
+        """View-frequency pruning (Sec. 4.2.2): keeps the anchors selected in at least a tau_v
+        fraction of the training views counted since the last prune (order preserved), and
+        compacts every per-anchor array and its optimiser state.  Returns the kept count."""
+        assert self.n_views_seen > 0, "no training views counted"
+        dev = "cuda"
+        min_count = min_count_for(self.n_views_seen, tau_v)
+        keep = torch.empty(self.N, dtype=torch.int32, device=dev)
+        n_kept = torch.zeros(1, dtype=torch.int32, device=dev)
+        scratch = torch.empty(abi.prune_scratch_bytes(self.N), dtype=torch.uint8, device=dev)
+        abi.prune_anchors(self.sel_count, self.N, min_count, keep, n_kept, scratch)
+        n = int(n_kept.item())
+
+        def gather(t):
+            out = torch.empty((n,) + tuple(t.shape[1:]), dtype=t.dtype, device=dev)
+            if n:
+                row = t[0].numel() * t.element_size()
+                abi.gather_rows(t, out, row, keep, n_kept, n)
+            return out
+
+        for name in ("pos", "level", "dL", "feat", "offs", "lv"):
+            setattr(self, name, gather(getattr(self, name)))
+        if self.explicit is not None:
+            self.explicit = {k: gather(v) for k, v in self.explicit.items()}
+        for store in (self.adam_m, self.adam_v):
+            for k in list(store):
+                if not k.startswith("mlp."):
+                    store[k] = gather(store[k])
+        self.grads = {k: torch.zeros_like(t) for k, t in self._anchor_params().items()}
+        self.N = n
+        self.sel_count = torch.zeros(self.N, dtype=torch.int32, device=dev)
+        self.n_views_seen = 0
+        self.sel_scratch = torch.empty(abi.lod_select_scratch_bytes(self.N), dtype=torch.uint8,
+                                       device=dev)
+        return n
