@@ -240,6 +240,9 @@ def run_reference(args):
 LAUNCHES = {"lod_select": 1, "proposal_gate": 1, "decode": 1, "project_bin": 1, "sort": 4,
             "blend_fwd": 1}
 DPSNR_GATE_DB = 0.05
+# DRAM bytes (read + write) of one blend_fwd launch from an ncu capture of the same kernel
+# (pose 14 of the path, profiles/blend_fwd_city2M_1080p.md): 31.71 MB + 2.09 MB
+BLEND_FWD_DRAM_BYTES = 33.80e6
 
 
 def _time_form(rd, cams, pose, steps, warmup, gate, flush, clk_index):
@@ -557,7 +560,9 @@ def run_gpu(args):
     if dominant == "blend_fwd":
         ach = evals * OPS_PER_EVAL / (mean_ms["blend_fwd"] * 1e-3) / 1e12
         roof = {"kernel": "blend_fwd", "bound": "alu", "achieved": ach, "peak": alu_peak,
-                "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": BLEND_FWD_DRAM_BYTES,
+                "traffic_note": "bytes per launch from one ncu capture (pose 14); records "
+                                "written by the projection mostly stay in L2",
                 "work": f"{evals:.4g} (pixel, Gaussian) evaluations x {OPS_PER_EVAL} FP32 ops",
                 "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                f"{sm_max:.0f} MHz ({src} sm_max_mhz)"}
