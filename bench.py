@@ -237,7 +237,7 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------
 
 # kernels each ABI call launches per frame
-LAUNCHES = {"lod_select": 1, "proposal_gate": 1, "decode": 1, "project_bin": 1, "sort": 4,
+LAUNCHES = {"lod_select": 3, "proposal_gate": 2, "decode": 1, "project_bin": 1, "sort": 4,
             "blend_fwd": 1}
 DPSNR_GATE_DB = 0.05
 # DRAM bytes (read + write) of one blend_fwd launch from an ncu capture of the same kernel

@@ -6,9 +6,12 @@
 // pre-scaled coefficients and to a mask of the 8x8 blocks that the record's alpha >= 1/255
 // ellipse can reach; each warp then walks, in list order, only the records whose mask holds
 // its block.  One (pixel, Gaussian) evaluation is: offset, a 5-operation quadratic form, the
-// exponent-bound skip test, and only for surviving pairs one ex2 and the compositing update.
-// The CTA leaves as soon as every pixel has saturated (barrier vote).  The kernel is bound by
-// instruction issue (FP32 + MUFU), not by memory.
+// exponent-bound skip test, one ex2 and the compositing update, done branch-free: a pixel that
+// skips the Gaussian (or saturates on it) adds a zero weight and keeps its transmittance, which
+// leaves its sums bit-for-bit as a skipped update would.  Lanes of a warp therefore never
+// diverge inside the walk.  A warp stops walking once all its pixels have saturated (checked
+// every few records) and the CTA stops loading batches once all of its pixels have.  The
+// kernel is bound by instruction issue (FP32 + MUFU), not by memory.
 #include "blend_common.cuh"
 
 namespace ogs {
@@ -16,7 +19,34 @@ namespace {
 
 using namespace blend;
 
-template <bool kMaxC>
+constexpr int kExitEvery = 8;    // records walked between two warp-wide saturation checks
+
+// One pixel's compositing step with Gaussian `idx - 1` of the list, branch-free.  Returns the
+// weight alpha T added to the pixel (0 when it skipped the Gaussian or saturated on it).
+template <bool kEval>
+__device__ __forceinline__ float composite(float p2, float o, float cr, float cg, float cb,
+                                           float pskip2, int idx, bool& done, float& T,
+                                           float& C0, float& C1, float& C2, int& last,
+                                           int& stop) {
+    // skip if power > 0 or alpha < 1/255 (power2 < pskip2)
+    const bool pass = !done && p2 <= 0.f && p2 >= pskip2;
+    const float alpha = fminf(0.99f, raw_alpha(o, p2));
+    const float w = alpha * T;
+    const float Tn = T - w;                         // T (1 - alpha)
+    const bool sat = pass && Tn < 1e-4f;            // this Gaussian would saturate the pixel
+    const bool apply = pass && !sat;
+    const float wgt = apply ? w : 0.0f;
+    C0 = fmaf(cr, wgt, C0);
+    C1 = fmaf(cg, wgt, C1);
+    C2 = fmaf(cb, wgt, C2);
+    T = apply ? Tn : T;
+    last = apply ? idx : last;
+    if (kEval) stop = sat ? idx : stop;
+    done = done || sat;
+    return wgt;
+}
+
+template <bool kMaxC, bool kEval>
 __global__ void __launch_bounds__(kThreads) blend_fwd_kernel(
     const float4* __restrict__ rec, const uint32_t* __restrict__ pair_gauss,
     const uint2* __restrict__ tile_range, int W, int H, int gx, float bg0, float bg1, float bg2,
@@ -57,57 +87,30 @@ __global__ void __launch_bounds__(kThreads) blend_fwd_kernel(
         __syncthreads();
         const int cnt = min(kBatch, n - b0);
         const int nw = warp_list(s_m, cnt, list);
-        for (int q = 0; q < nw; ++q) {
-            if (!kMaxC && done0 && done1) break;
-            const int j = list[q];
-            const float4 A = s_a[j];
-            const float4 B = s_b[j];
-            const float2 Cc = s_c[j];
-            const float dx = A.x - fx;
-            const float dy0 = A.y - fy, dy1 = dy0 - 1.0f;
-            const float ax = __fmul_rn(A.z, dx);
-            const float p0 = power2(ax, dx, dy0, A.w, B.x);
-            const float p1 = power2(ax, dx, dy1, A.w, B.x);
-            float c0 = 0.f, c1 = 0.f;
-            // pixel 0: skip if power > 0 or alpha < 1/255 (power2 < pskip2)
-            if (!done0 && p0 <= 0.f && p0 >= Cc.y) {
-                const float alpha = fminf(0.99f, raw_alpha(B.y, p0));
-                const float Tn = T0 * (1.0f - alpha);
-                if (Tn < 1e-4f) {
-                    done0 = true;
-                    stop0 = b0 + j + 1;
-                } else {
-                    const float wgt = alpha * T0;
-                    C00 = fmaf(B.z, wgt, C00);
-                    C01 = fmaf(B.w, wgt, C01);
-                    C02 = fmaf(Cc.x, wgt, C02);
-                    T0 = Tn;
-                    last0 = b0 + j + 1;
-                    c0 = wgt;
+        for (int q0 = 0; q0 < nw; q0 += kExitEvery) {
+            if (__all_sync(0xffffffffu, done0 && done1)) break;
+            const int q1 = min(q0 + kExitEvery, nw);
+            for (int q = q0; q < q1; ++q) {
+                const int j = list[q];
+                const float4 A = s_a[j];
+                const float4 B = s_b[j];
+                const float2 Cc = s_c[j];
+                const float dx = A.x - fx;
+                const float dy0 = A.y - fy, dy1 = dy0 - 1.0f;
+                const float ax = __fmul_rn(A.z, dx);
+                const float p0 = power2(ax, dx, dy0, A.w, B.x);
+                const float p1 = power2(ax, dx, dy1, A.w, B.x);
+                const int idx = b0 + j + 1;
+                const float c0 = composite<kEval>(p0, B.y, B.z, B.w, Cc.x, Cc.y, idx, done0, T0,
+                                                  C00, C01, C02, last0, stop0);
+                const float c1 = composite<kEval>(p1, B.y, B.z, B.w, Cc.x, Cc.y, idx, done1, T1,
+                                                  C10, C11, C12, last1, stop1);
+                if (kMaxC) {
+                    // contributions are >= 0, so their float bits order like unsigned ints
+                    const uint32_t m = __reduce_max_sync(0xffffffffu,
+                                                         __float_as_uint(fmaxf(c0, c1)));
+                    if (lane_id() == 0 && m) atomicMax(&maxc[s_anchor[j]], m);
                 }
-            }
-            if (!done1 && p1 <= 0.f && p1 >= Cc.y) {
-                const float alpha = fminf(0.99f, raw_alpha(B.y, p1));
-                const float Tn = T1 * (1.0f - alpha);
-                if (Tn < 1e-4f) {
-                    done1 = true;
-                    stop1 = b0 + j + 1;
-                } else {
-                    const float wgt = alpha * T1;
-                    C10 = fmaf(B.z, wgt, C10);
-                    C11 = fmaf(B.w, wgt, C11);
-                    C12 = fmaf(Cc.x, wgt, C12);
-                    T1 = Tn;
-                    last1 = b0 + j + 1;
-                    c1 = wgt;
-                }
-            }
-            if (kMaxC) {
-                // contributions are >= 0, so their float bits order like unsigned ints
-                const uint32_t m = __reduce_max_sync(0xffffffffu,
-                                                     __float_as_uint(fmaxf(c0, c1)));
-                if (lane_id() == 0 && m) atomicMax(&maxc[s_anchor[j]], m);
-                if (__all_sync(0xffffffffu, done0 && done1)) break;
             }
         }
     }
@@ -119,7 +122,7 @@ __global__ void __launch_bounds__(kThreads) blend_fwd_kernel(
         img[2 * plane + pix] = C02 + T0 * bg2;
         T_final[pix] = T0;
         n_last[pix] = (uint32_t)last0;
-        if (n_eval) n_eval[pix] = (uint32_t)stop0;
+        if (kEval) n_eval[pix] = (uint32_t)stop0;
     }
     if (in1) {
         const size_t pix = (size_t)(py + 1) * W + px;
@@ -128,7 +131,7 @@ __global__ void __launch_bounds__(kThreads) blend_fwd_kernel(
         img[2 * plane + pix] = C12 + T1 * bg2;
         T_final[pix] = T1;
         n_last[pix] = (uint32_t)last1;
-        if (n_eval) n_eval[pix] = (uint32_t)stop1;
+        if (kEval) n_eval[pix] = (uint32_t)stop1;
     }
 }
 
@@ -149,13 +152,22 @@ extern "C" ogs_status ogs_blend_fwd(const ogs_rec2d* rec, const uint32_t* pair_g
     cudaStream_t st = (cudaStream_t)stream;
     const float4* r = reinterpret_cast<const float4*>(rec);
     const uint2* tr = reinterpret_cast<const uint2*>(tile_range);
-    if (maxc)
-        blend_fwd_kernel<true><<<gx * gy, blend::kThreads, 0, st>>>(
+    const dim3 grid(gx * gy);
+    if (maxc && n_eval)
+        blend_fwd_kernel<true, true><<<grid, blend::kThreads, 0, st>>>(
             r, pair_gauss, tr, width, height, gx, bg[0], bg[1], bg[2], img, T_final, n_last,
             n_eval, sel_idx, k, maxc);
-    else
-        blend_fwd_kernel<false><<<gx * gy, blend::kThreads, 0, st>>>(
+    else if (maxc)
+        blend_fwd_kernel<true, false><<<grid, blend::kThreads, 0, st>>>(
+            r, pair_gauss, tr, width, height, gx, bg[0], bg[1], bg[2], img, T_final, n_last,
+            nullptr, sel_idx, k, maxc);
+    else if (n_eval)
+        blend_fwd_kernel<false, true><<<grid, blend::kThreads, 0, st>>>(
             r, pair_gauss, tr, width, height, gx, bg[0], bg[1], bg[2], img, T_final, n_last,
             n_eval, nullptr, 1, nullptr);
+    else
+        blend_fwd_kernel<false, false><<<grid, blend::kThreads, 0, st>>>(
+            r, pair_gauss, tr, width, height, gx, bg[0], bg[1], bg[2], img, T_final, n_last,
+            nullptr, nullptr, 1, nullptr);
     return launch_status();
 }

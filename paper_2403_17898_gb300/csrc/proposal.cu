@@ -162,12 +162,17 @@ __global__ void __launch_bounds__(kGateThreads) gate_score(PropArgs a, const uin
 constexpr int kGK1 = 48;
 constexpr uint32_t kGTmemCols = 64;
 constexpr uint32_t kGWaitLimit = 1u << 24;
-constexpr int kGOffA1 = 0;                               // 128 x 48 bf16
-constexpr int kGOffB1 = kGOffA1 + 128 * kGK1 * 2;        // 64 x 48 bf16
-constexpr int kGOffA2 = kGOffB1 + kPH * kGK1 * 2;        // 128 x 64 bf16
-constexpr int kGOffB2 = kGOffA2 + 128 * kPH * 2;         // 64 x 64 bf16
-constexpr int kGOffVec = kGOffB2 + kPH * kPH * 2;        // b1, b2, w3 (f32), b3
-constexpr int kGSmem = kGOffVec + (3 * kPH + 4) * 4;
+// Shared memory: the network image (B1, B2, vectors; packed once per call by gate_pack and
+// fetched by one bulk copy) followed by the A operand.  Layer 1's A (128 x 48) and layer 2's A
+// (128 x 64) share one buffer: the first-layer epilogue writes H1 only after the layer-1
+// product has completed, and the next tile's inputs land only after layer 2 has.
+constexpr int kGOffB1 = 0;                               // 64 x 48 bf16
+constexpr int kGOffB2 = kGOffB1 + kPH * kGK1 * 2;        // 64 x 64 bf16
+constexpr int kGOffVec = kGOffB2 + kPH * kPH * 2;        // b1, b2, w3 (f32), b3 (+ pad)
+constexpr int kGImgBytes = kGOffVec + (3 * kPH + 4) * 4;
+constexpr int kGOffA = kGImgBytes;                       // 128 x 64 bf16 (A1 uses 128 x 48)
+constexpr int kGSmem = kGOffA + 128 * kPH * 2;
+static_assert(kGImgBytes % 16 == 0 && kGOffA % 16 == 0, "bulk copy granularity");
 static_assert(kGateThreads == 128, "one TMEM lane (anchor) per thread");
 
 __device__ __forceinline__ void gput8(unsigned char* base, int row, int kc, int Kpad,
@@ -179,29 +184,74 @@ __device__ __forceinline__ void gput8(unsigned char* base, int row, int kc, int 
         *reinterpret_cast<const uint4*>(h);
 }
 
+// Per call: the first kGPackCtas CTAs write the network image (BF16 operand tiles of W1 (K
+// padded to 48) and W2 in the no-swizzle K-major core-matrix layout, then b1, b2, w3, b3 in
+// FP32) to global scratch, one 8-element group or vector entry per thread; the other CTAs zero
+// the tile status words and the ticket/done counters.
+constexpr int kGPackThreads = 256;
+constexpr int kGGroups1 = kPH * (kGK1 / 8), kGGroups2 = kPH * (kPH / 8);
+constexpr int kGPackItems = kGGroups1 + kGGroups2 + 3 * kPH + 4;
+constexpr int kGPackCtas = (kGPackItems + kGPackThreads - 1) / kGPackThreads;
+
+__global__ void __launch_bounds__(kGPackThreads) gate_pack(ogs_proposal net, unsigned char* img,
+                                                           unsigned long long* status,
+                                                           int n_words) {
+    if (blockIdx.x < kGPackCtas) {
+        const int e = blockIdx.x * kGPackThreads + threadIdx.x;
+        float v[8];
+        if (e < kGGroups1) {
+            const int n = e / (kGK1 / 8), kc = e % (kGK1 / 8);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int kk = 8 * kc + i;
+                v[i] = kk < kPIn ? net.w1[n * kPIn + kk] : 0.f;
+            }
+            gput8(img + kGOffB1, n, kc, kGK1, v);
+        } else if (e < kGGroups1 + kGGroups2) {
+            const int f = e - kGGroups1;
+            const int n = f / (kPH / 8), kc = f % (kPH / 8);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = net.w2[n * kPH + 8 * kc + i];
+            gput8(img + kGOffB2, n, kc, kPH, v);
+        } else if (e < kGPackItems) {
+            const int f = e - kGGroups1 - kGGroups2;
+            reinterpret_cast<float*>(img + kGOffVec)[f] =
+                f < kPH ? net.b1[f] : f < 2 * kPH ? net.b2[f - kPH]
+                : f < 3 * kPH ? net.w3[f - 2 * kPH] : f == 3 * kPH ? net.b3[0] : 0.f;
+        }
+        return;
+    }
+    const int nz = gridDim.x - kGPackCtas;
+    for (int e = (blockIdx.x - kGPackCtas) * kGPackThreads + threadIdx.x; e < n_words;
+         e += nz * kGPackThreads)
+        status[e] = 0ull;
+}
+
 // Single pass: CTAs take 128-entry tiles by ticket, score them on the tensor cores, publish
 // the tile's keep count, find its output offset by look-back and write the kept entries in
 // order.  The last CTA to finish (when every CTA has read the input count) publishes the new
 // counts.
-__global__ void __launch_bounds__(kGateThreads, 4) gate_tc(PropArgs a, const uint32_t* sel_in,
+__global__ void __launch_bounds__(kGateThreads, 5) gate_tc(PropArgs a, const uint32_t* sel_in,
                                                            const float* w_in, int k,
                                                            ogs_counts* counts, float p_star,
                                                            float* p_out, uint32_t* sel_out,
                                                            float* w_out,
+                                                           const unsigned char* img,
                                                            unsigned long long* status,
                                                            uint32_t* sync_words) {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t wbar;
     __shared__ uint32_t tmem_base;
     __shared__ uint32_t s_tile;
     __shared__ uint32_t wc[kGateThreads / 32];
-    unsigned char* sA1 = sm + kGOffA1;
+    unsigned char* sA1 = sm + kGOffA;
     unsigned char* sB1 = sm + kGOffB1;
-    unsigned char* sA2 = sm + kGOffA2;
+    unsigned char* sA2 = sm + kGOffA;
     unsigned char* sB2 = sm + kGOffB2;
-    float* sb1 = reinterpret_cast<float*>(sm + kGOffVec);
-    float* sb2 = sb1 + kPH;
-    float* sw3 = sb2 + kPH;
+    const float* sb1 = reinterpret_cast<const float*>(sm + kGOffVec);
+    const float* sb2 = sb1 + kPH;
+    const float* sw3 = sb2 + kPH;
     const int t = threadIdx.x, w = t >> 5;
     const uint32_t M = counts->n_selected;
     const uint32_t ntiles = (M + 127) / 128;
@@ -209,39 +259,16 @@ __global__ void __launch_bounds__(kGateThreads, 4) gate_tc(PropArgs a, const uin
     uint32_t* done = sync_words + 1;
 
     if (blockIdx.x < ntiles) {                   // uniform: CTAs with work own TMEM
-        for (int e = t; e < kPH * (kGK1 / 8); e += kGateThreads) {
-            const int n = e / (kGK1 / 8), kc = e % (kGK1 / 8);
-            float v[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int kk = 8 * kc + i;
-                v[i] = kk < kPIn ? a.net.w1[n * kPIn + kk] : 0.f;
-            }
-            gput8(sB1, n, kc, kGK1, v);
+        if (t == 0) {
+            tc::mbar_init(&mbar, 1);
+            tc::mbar_init(&wbar, 1);
+            tc::mbar_expect_tx(&wbar, kGImgBytes);
+            tc::bulk_load(sm, img, kGImgBytes, &wbar);   // lands while the inputs are gathered
         }
-        for (int e = t; e < kPH * (kPH / 8); e += kGateThreads) {
-            const int n = e / (kPH / 8), kc = e % (kPH / 8);
-            float v[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) v[i] = a.net.w2[n * kPH + 8 * kc + i];
-            gput8(sB2, n, kc, kPH, v);
-        }
-        for (int e = t; e < kPH; e += kGateThreads) {
-            sb1[e] = a.net.b1[e];
-            sb2[e] = a.net.b2[e];
-            sw3[e] = a.net.w3[e];
-        }
-        const float b3 = a.net.b3[0];
-        {   // the last K chunk (inputs 40..47) is always zero
-            const float z8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            gput8(sA1, t, kGK1 / 8 - 1, kGK1, z8);
-        }
-        if (t == 0) tc::mbar_init(&mbar, 1);
         if (w == 0) {
             tc::tmem_alloc(&tmem_base, kGTmemCols);
             tc::tmem_relinquish();
         }
-        tc::fence_smem_to_async();
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
@@ -250,6 +277,7 @@ __global__ void __launch_bounds__(kGateThreads, 4) gate_tc(PropArgs a, const uin
         const uint32_t id = tc::idesc_bf16(128, kPH);
         uint32_t phase = 0;
         bool aborted = false;
+        bool have_net = false;
 
         for (;;) {
             if (t == 0) s_tile = atomicAdd(ticket, 1u);
@@ -271,6 +299,16 @@ __global__ void __launch_bounds__(kGateThreads, 4) gate_tc(PropArgs a, const uin
                     const float v[8] = {x[8 * kc], x[8 * kc + 1], x[8 * kc + 2], x[8 * kc + 3],
                                         x[8 * kc + 4], x[8 * kc + 5], x[8 * kc + 6], x[8 * kc + 7]};
                     gput8(sA1, t, kc, kGK1, v);
+                }
+                const float z8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                gput8(sA1, t, kGK1 / 8 - 1, kGK1, z8);    // inputs 40..47 (H1 overwrote them)
+            }
+            if (!have_net) {                          // the network image, once per CTA
+                have_net = true;
+                if (!tc::mbar_wait(&wbar, 0, kGWaitLimit)) {
+                    // copy still in flight: wait once more (bounded) before anyone leaves
+                    if (t == 0) atomicExch(&counts->timeout, 1u);
+                    tc::mbar_wait(&wbar, 0, kGWaitLimit);
                 }
             }
             tc::fence_smem_to_async();
@@ -325,7 +363,7 @@ __global__ void __launch_bounds__(kGateThreads, 4) gate_tc(PropArgs a, const uin
             }
             phase ^= 1;
             tc::fence_after_sync();
-            float z = b3;
+            float z = sb1[3 * kPH];                  // b3
 #pragma unroll
             for (int c0 = 0; c0 < kPH; c0 += 32) {
                 float v[32];
@@ -360,6 +398,7 @@ __global__ void __launch_bounds__(kGateThreads, 4) gate_tc(PropArgs a, const uin
             if (t == 0) atomicExch(&counts->timeout, 1u);
             tc::mbar_wait(&mbar, phase, kGWaitLimit);
         }
+        if (!have_net) tc::mbar_wait(&wbar, 0, kGWaitLimit);   // no tile taken: let the copy land
         tc::fence_before_sync();
         __syncthreads();
         if (w == 0) tc::tmem_dealloc(tbase, kGTmemCols);
@@ -610,6 +649,7 @@ extern "C" size_t ogs_proposal_gate_scratch_bytes(int64_t sel_cap) {
     cv.take<float>(sel_cap > 0 ? sel_cap : 1);
     cv.take<unsigned long long>(nb + 1);   // per-tile counts (FP32 form) or status words
     cv.take<uint32_t>(1);
+    cv.take<unsigned char>(kGImgBytes);    // BF16 network image (tensor-core form)
     return cv.off + 256;
 }
 
@@ -634,20 +674,19 @@ ogs_status proposal_gate_impl(bool tensor_cores, const float* pos, const uint8_t
     const int nb = (int)((sel_cap + kGateThreads - 1) / kGateThreads);
     uint32_t* block = reinterpret_cast<uint32_t*>(cv.take<unsigned long long>(nb + 1));
     uint32_t* m_saved = cv.take<uint32_t>(1);
+    unsigned char* img = cv.take<unsigned char>(kGImgBytes);
     PropArgs a{pos, level, feat, NL, make_cam(*cam), *net};
     cudaStream_t st = (cudaStream_t)stream;
     if (tensor_cores) {
-        // single pass: tile status words + ticket and done counters, zeroed first
+        // single pass: tile status words + ticket and done counters, zeroed by gate_pack
+        // together with the network image
         unsigned long long* status = reinterpret_cast<unsigned long long*>(block);
         uint32_t* sync_words = reinterpret_cast<uint32_t*>(status + nb);
-        if (cudaMemsetAsync(status, 0, sizeof(unsigned long long) * (nb + 1), st) != cudaSuccess)
-            return OGS_ERR_CUDA;
-        if (cudaFuncSetAttribute(gate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kGSmem) != cudaSuccess)
-            return OGS_ERR_CUDA;
-        const int grid = nb < 4 * kSmCount ? nb : 4 * kSmCount;
+        gate_pack<<<kGPackCtas + (nb + 1 + 1023) / 1024, kGPackThreads, 0, st>>>(*net, img, status,
+                                                                              nb + 1);
+        const int grid = nb < 5 * kSmCount ? nb : 5 * kSmCount;
         gate_tc<<<grid, kGateThreads, kGSmem, st>>>(a, sel_in, w_in, k, counts, p_star, p_out,
-                                                    sel_out, w_out, status, sync_words);
+                                                    sel_out, w_out, img, status, sync_words);
         return launch_status();
     }
     const size_t smem = sizeof(float) * kNetFloats;
