@@ -147,6 +147,7 @@ def stage_bytes(N, M, G, P, n_tiles, pixels, k=10):
         "lod_select": N * (12 + 1 + 4) + M * 8,
         "decode": M * (8 + 12 + 128 + 12 * k + 12) + G * 56,
         "project_bin": G * 56 + G * (48 + 4 + 8 + 4),
+        "decode_project": M * (8 + 12 + 128 + 12 * k + 12) + G * (48 + 4 + 8 + 4),
         "sort": G * (4 + 8 + 4) + P * 4 + n_tiles * 8,
         "blend_fwd": P * (36 + 4) + n_tiles * 8 + pixels * (12 + 4 + 4),
     }
@@ -237,7 +238,7 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------
 
 # kernels each ABI call launches per frame
-LAUNCHES = {"lod_select": 3, "proposal_gate": 2, "decode": 1, "project_bin": 1, "sort": 4,
+LAUNCHES = {"lod_select": 3, "proposal_gate": 2, "decode_project": 2, "sort": 4,
             "blend_fwd": 1}
 DPSNR_GATE_DB = 0.05
 # DRAM bytes (read + write) of one blend_fwd launch from an ncu capture of the same kernel

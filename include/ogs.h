@@ -191,6 +191,32 @@ ogs_status ogs_project_bin(const ogs_gaussians* g /* host struct */, int64_t n_g
                            void* stream);
 
 /* ---------------------------------------------------------------------------------------
+ * ogs_decode_project_bf16 — Sec. 3.2 (Eq. offsets, Eq. mlp) fused with Sec. 3.1 (Eq. 1 and
+ * the EWA projection): the Gaussians decoded on the tensor cores are projected in the same
+ * kernel, without passing through global memory.  The outputs are bit-for-bit those of
+ * ogs_decode_bf16 (into `out`) followed by ogs_project_bin(out, sel_cap * k,
+ * means_relative = 1, cam, rec, depth_key, rect, tiles, tile_count, counts).
+ *   pos, feat, offs, lv, N, mlp, cam, sel_idx, sel_w, sel_cap, counts: as ogs_decode_bf16
+ *   out (optional, may be NULL): the Gaussian SoA is also written (training needs it for the
+ *   backward); NULL writes records only
+ *   rec, depth_key, rect, tiles, tile_count (optional): as ogs_project_bin, counted over
+ *   counts->n_gaussians Gaussians; tile_count is zeroed by the call
+ *   scratch: ogs_decode_project_scratch_bytes() bytes, 16-byte aligned (the BF16 operand
+ *   image of the decoder, packed by the call)
+ * counts->timeout is set if a bounded internal wait expires (records of the remaining
+ * anchors not written).
+ * ------------------------------------------------------------------------------------- */
+size_t ogs_decode_project_scratch_bytes(void);
+ogs_status ogs_decode_project_bf16(const float* pos, const float* feat, const float* offs,
+                                   const float* lv, int64_t N, const ogs_mlp* mlp /* host */,
+                                   const ogs_camera* cam /* host */, const uint32_t* sel_idx,
+                                   const float* sel_w, int64_t sel_cap, ogs_counts* counts,
+                                   const ogs_gaussians* out /* host struct or NULL */,
+                                   ogs_rec2d* rec, uint32_t* depth_key, uint32_t* rect,
+                                   uint32_t* tiles, uint32_t* tile_count, void* scratch,
+                                   size_t scratch_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------
  * ogs_sort — Sec. 3.1: for every tile, the Gaussians whose rectangle covers it, in
  * front-to-back order (ascending depth, ties by Gaussian id).  Built per tile: pair counts per
  * tile and their exclusive scan (the tile ranges), an unordered fill of each tile's range, and

@@ -71,6 +71,11 @@ _SIGS = {
                                   _P, _I64, _P, C.POINTER(Gaussians), _P]),
     "ogs_project_bin": (C.c_int, [C.POINTER(Gaussians), _I64, _I32, C.POINTER(Camera), _P, _P,
                                   _P, _P, _P, _P, _P]),
+    "ogs_decode_project_scratch_bytes": (_SZ, []),
+    "ogs_decode_project_bf16": (C.c_int, [_P, _P, _P, _P, _I64, C.POINTER(MLP),
+                                          C.POINTER(Camera), _P, _P, _I64, _P,
+                                          C.POINTER(Gaussians), _P, _P, _P, _P, _P, _P, _SZ,
+                                          _P]),
     "ogs_sort_scratch_bytes": (_SZ, [_I64, _I64, _I32]),
     "ogs_sort": (C.c_int, [_P, _P, _P, _P, _I64, _I64, _I32, _I32, _P, _P, _I64, _P, _P, _SZ,
                            _P]),
@@ -239,6 +244,26 @@ def project_bin(g, n_gauss, means_relative, cam, rec, depth_key, rect, tiles, co
                                  _ptr(rec), _ptr(depth_key), _ptr(rect), _ptr(tiles),
                                  _ptr(tile_count), _ptr(counts), _stream(stream)),
            "ogs_project_bin")
+
+
+def decode_project_scratch_bytes():
+    return int(lib().ogs_decode_project_scratch_bytes())
+
+
+def decode_project_bf16(pos, feat, offs, lv, N, mlp, cam, sel_idx, sel_w, sel_cap, counts,
+                        rec, depth_key, rect, tiles, scratch, out=None, tile_count=None,
+                        stream=None):
+    """Fused BF16 decode + projection; ``out`` (Gaussian SoA) is written only if given."""
+    c = cam if isinstance(cam, Camera) else camera(cam)
+    m = mlp if isinstance(mlp, MLP) else mlp_struct(mlp)
+    g = None
+    if out is not None:
+        g = C.byref(out if isinstance(out, Gaussians) else gaussians_struct(out))
+    _check(lib().ogs_decode_project_bf16(
+        _ptr(pos), _ptr(feat), _ptr(offs), _ptr(lv), int(N), C.byref(m), C.byref(c),
+        _ptr(sel_idx), _ptr(sel_w), int(sel_cap), _ptr(counts), g, _ptr(rec), _ptr(depth_key),
+        _ptr(rect), _ptr(tiles), _ptr(tile_count), _ptr(scratch), scratch.numel(),
+        _stream(stream)), "ogs_decode_project_bf16")
 
 
 def sort_scratch_bytes(g_cap, pair_cap, n_tiles):

@@ -14,24 +14,16 @@
 // layer-2 operand buffer and written with one TMA bulk copy, so global stores are
 // contiguous.  Every mbarrier wait is bounded; on expiry the kernel flags ogs_counts.timeout,
 // releases its tensor memory and exits.
-#include "internal.cuh"
-#include "tc.cuh"
+#include "decode_common.cuh"
 
 namespace ogs {
 namespace {
 
+using namespace dec;
+
 constexpr int kTcThreads = 128;     // 4 warps, one anchor (TMEM lane) per thread
-constexpr int kTM = 128;            // anchors per tile (MMA M)
-constexpr int kF = 32;
-constexpr int kH = 32;
-constexpr int kDin = kF + 4;        // 36
-constexpr int kK1 = 48;             // padded layer-1 K
-constexpr int kN1 = 3 * kH;         // 96 hidden (layer-1 N, layer-2 K)
-constexpr int kK = 10;              // Gaussians per anchor
-constexpr int kN2 = 112;            // 110 outputs padded to a multiple of 16
 constexpr uint32_t kTmemCols = 128;
 constexpr uint32_t kD2Col = 0;          // layer 2 overwrites layer 1's (already read) columns
-constexpr uint32_t kWaitLimit = 1u << 24;
 
 // shared-memory carve (bytes)
 constexpr int kOffA1 = 0;                               // 128 x 48 bf16
@@ -58,18 +50,6 @@ struct TcArgs {
     Cam cam;
 };
 
-__device__ __forceinline__ float sigm(float x) { return 1.0f / (1.0f + __expf(-x)); }
-
-// 8 consecutive K values of one row = one 16-byte core-matrix row: a single vector store
-__device__ __forceinline__ void put8(unsigned char* base, int row, int kc, int Kpad,
-                                     const float (&v)[8]) {
-    __nv_bfloat162 h[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-    *reinterpret_cast<uint4*>(base + tc::core_offset(row, 8 * kc, Kpad)) =
-        *reinterpret_cast<const uint4*>(h);
-}
-
 __global__ void __launch_bounds__(kTcThreads, 3) decode_bf16_tc(TcArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t mbar;
@@ -87,30 +67,18 @@ __global__ void __launch_bounds__(kTcThreads, 3) decode_bf16_tc(TcArgs a) {
         const int n = e / (kK1 / 8), kc = e % (kK1 / 8);
         float v[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int k = 8 * kc + i;
-            v[i] = k < kDin ? a.mlp.w1[n * kDin + k] : 0.f;
-        }
+        for (int i = 0; i < 8; ++i) v[i] = w1_elem(a.mlp, n, 8 * kc + i);
         put8(sB1, n, kc, kK1, v);
     }
     for (int e = t; e < kN2 * (kN1 / 8); e += kTcThreads) {
         const int n = e / (kN1 / 8), kc = e % (kN1 / 8);
         float v[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int k = 8 * kc + i;
-            float x = 0.f;
-            if (n < kK) { if (k < kH) x = a.mlp.w2_op[n * kH + k]; }
-            else if (n < 4 * kK) { if (k >= kH && k < 2 * kH) x = a.mlp.w2_col[(n - kK) * kH + (k - kH)]; }
-            else if (n < 11 * kK) { if (k >= 2 * kH) x = a.mlp.w2_cov[(n - 4 * kK) * kH + (k - 2 * kH)]; }
-            v[i] = x;
-        }
+        for (int i = 0; i < 8; ++i) v[i] = w2_elem(a.mlp, n, 8 * kc + i);
         put8(sB2, n, kc, kN1, v);
     }
     for (int e = t; e < kN1; e += kTcThreads) sb1[e] = a.mlp.b1[e];
-    for (int e = t; e < kN2; e += kTcThreads)
-        sb2[e] = e < kK ? a.mlp.b2_op[e] : (e < 4 * kK ? a.mlp.b2_col[e - kK]
-                                                    : (e < 11 * kK ? a.mlp.b2_cov[e - 4 * kK] : 0.f));
+    for (int e = t; e < kN2; e += kTcThreads) sb2[e] = b2_elem(a.mlp, e);
     {   // the last K chunk (columns 40..47) of the input tile is always zero
         const float z8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         put8(sA1, t, kK1 / 8 - 1, kK1, z8);
@@ -142,9 +110,7 @@ __global__ void __launch_bounds__(kTcThreads, 3) decode_bf16_tc(TcArgs a) {
         if (valid) {
             j = a.sel_idx[r];
             wgt = a.sel_w[r];
-#pragma unroll
-            for (int q = 0; q < 3; ++q) dv[q] = a.pos[3 * (size_t)j + q] - c.c[q];
-            const float d = sqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+            const float d = anchor_offset(a.pos + 3 * (size_t)j, c.c, dv);
             const float4* f4 = reinterpret_cast<const float4*>(a.feat + (size_t)j * kF);
 #pragma unroll
             for (int kc = 0; kc < kF / 8; ++kc) {
@@ -234,22 +200,23 @@ __global__ void __launch_bounds__(kTcThreads, 3) decode_bf16_tc(TcArgs a) {
 #pragma unroll
                 for (int i = 0; i < kK; ++i) {
                     if (arr == 0) {
-                        rowp[i] = wgt * tanhf(y[i]);
+                        rowp[i] = act_opacity(wgt, y[i]);
                     } else if (arr == 1) {
 #pragma unroll
-                        for (int q = 0; q < 3; ++q) rowp[3 * i + q] = sigm(y[kK + 3 * i + q]);
+                        for (int q = 0; q < 3; ++q) rowp[3 * i + q] = act_color(y[kK + 3 * i + q]);
                     } else if (arr == 2) {
 #pragma unroll
-                        for (int q = 0; q < 3; ++q) rowp[3 * i + q] = lvv[q] * sigm(y[4 * kK + 7 * i + q]);
+                        for (int q = 0; q < 3; ++q)
+                            rowp[3 * i + q] = act_scale(lvv[q], y[4 * kK + 7 * i + q]);
                     } else if (arr == 3) {
                         const float* yc = y + 4 * kK + 7 * i + 3;
-                        const float inv = 1.0f / sqrtf(yc[0] * yc[0] + yc[1] * yc[1] + yc[2] * yc[2] + yc[3] * yc[3]);
+                        const float inv = act_qinv(yc);
 #pragma unroll
                         for (int q = 0; q < 4; ++q) rowp[4 * i + q] = yc[q] * inv;
                     } else {
                         const float* O = a.offs + ((size_t)j * kK + i) * 3;
 #pragma unroll
-                        for (int q = 0; q < 3; ++q) rowp[3 * i + q] = dv[q] + O[q] * lvv[q];
+                        for (int q = 0; q < 3; ++q) rowp[3 * i + q] = act_mean(dv[q], O[q], lvv[q]);
                     }
                 }
             }

@@ -62,6 +62,9 @@ class Renderer:
         anchor's k Gaussians come from ogs_explicit_gaussians instead of the decoders."""
         assert precision in ("fp32", "bf16")
         self.precision = precision
+        # BF16 neural form: decode and projection in one kernel (ogs_decode_project_bf16);
+        # False runs ogs_decode_bf16 and ogs_project_bin as two calls
+        self.fuse_decode_project = True
         self.k = k
         self.W, self.H = int(W), int(H)
         self.gx, self.gy = (self.W + TILE - 1) // TILE, (self.H + TILE - 1) // TILE
@@ -105,6 +108,8 @@ class Renderer:
         self.sel_w_g = torch.empty(S, device=dev)
         self.gate_scratch = torch.empty(abi.proposal_gate_scratch_bytes(S), dtype=torch.uint8,
                                         device=dev)
+        self.dp_scratch = torch.empty(abi.decode_project_scratch_bytes(), dtype=torch.uint8,
+                                      device=dev)
         self.g = {"means": torch.empty(G, 3, device=dev), "scales": torch.empty(G, 3, device=dev),
                   "quats": torch.empty(G, 4, device=dev), "opac": torch.empty(G, device=dev),
                   "colors": torch.empty(G, 3, device=dev)}
@@ -148,18 +153,27 @@ class Renderer:
                 self.sel_w_g, None, self.gate_scratch, st, bf16=self.precision == "bf16"))
             sel, selw = self.sel_idx_g, self.sel_w_g
         self.active_sel = sel
-        if self.explicit is not None:
-            stage("decode", lambda: abi.explicit_gaussians(
-                self.pos, self.offs, self.lv, self.N, self.k, self.explicit, c, sel, selw,
-                self.sel_cap, self.counts_t, self._g_struct, st))
-        else:
-            dec = abi.decode_bf16 if self.precision == "bf16" else abi.decode
-            stage("decode", lambda: dec(
+        if self.explicit is None and self.precision == "bf16" and self.fuse_decode_project:
+            # decoded Gaussians go straight to screen records; the Gaussian SoA is written only
+            # when a backward pass will need it
+            stage("decode_project", lambda: abi.decode_project_bf16(
                 self.pos, self.feat, self.offs, self.lv, self.N, self._mlp_struct, c, sel, selw,
-                self.sel_cap, self.counts_t, self._g_struct, st))
-        stage("project_bin", lambda: abi.project_bin(
-            self._g_struct, self.g_cap, 1, c, self.rec, self.depth_key, self.rect, self.tiles,
-            self.counts_t, st, tile_count=self.tile_count))
+                self.sel_cap, self.counts_t, self.rec, self.depth_key, self.rect, self.tiles,
+                self.dp_scratch, out=None if infer else self._g_struct,
+                tile_count=self.tile_count, stream=st))
+        else:
+            if self.explicit is not None:
+                stage("decode", lambda: abi.explicit_gaussians(
+                    self.pos, self.offs, self.lv, self.N, self.k, self.explicit, c, sel, selw,
+                    self.sel_cap, self.counts_t, self._g_struct, st))
+            else:
+                dec = abi.decode_bf16 if self.precision == "bf16" else abi.decode
+                stage("decode", lambda: dec(
+                    self.pos, self.feat, self.offs, self.lv, self.N, self._mlp_struct, c, sel,
+                    selw, self.sel_cap, self.counts_t, self._g_struct, st))
+            stage("project_bin", lambda: abi.project_bin(
+                self._g_struct, self.g_cap, 1, c, self.rec, self.depth_key, self.rect,
+                self.tiles, self.counts_t, st, tile_count=self.tile_count))
         stage("sort", lambda: abi.sort(
             self.depth_key, self.rect, self.tiles, self.g_cap, -1, self.gx, self.gy,
             self.pair_gauss, self.tile_range, self.pair_cap, self.counts_t, self.sort_scratch,
