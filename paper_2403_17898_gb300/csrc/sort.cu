@@ -450,16 +450,18 @@ __global__ void __launch_bounds__(kBinThreads) bin_fill(const uint32_t* __restri
 // Bitonic sorting network in its "flip" form over m = next power of two >= cnt slots: each
 // merge stage first compares mirrored pairs of a block, then runs half-cleaners, and every
 // comparator puts the smaller key at the lower index.  Slots >= cnt behave as +infinity, so a
-// comparator that touches one is a no-op: arbitrary counts sort without padding.
+// comparator that touches one is a no-op: arbitrary counts sort without padding.  (Generic
+// form, used for lists kept in global memory.)
 template <class Get, class Swap>
 __device__ __forceinline__ void bitonic(uint32_t cnt, Get get, Swap swp) {
     uint32_t m = 1;
     while (m < cnt) m <<= 1;
-    for (uint32_t size = 2; size <= m; size <<= 1) {
+    for (uint32_t lg = 1, size = 2; size <= m; ++lg, size <<= 1) {
         const uint32_t half = size >> 1;
         for (uint32_t i = threadIdx.x; i < m / 2; i += blockDim.x) {
-            const uint32_t blk = i / half, off = i - blk * half;
-            const uint32_t lo = blk * size + off, hi = blk * size + size - 1 - off;
+            const uint32_t off = i & (half - 1);
+            const uint32_t base = (i >> (lg - 1)) << lg;       // (i / half) * size
+            const uint32_t lo = base + off, hi = base + size - 1 - off;
             if (hi < cnt && get(lo) > get(hi)) swp(lo, hi);
         }
         __syncthreads();
@@ -473,6 +475,90 @@ __device__ __forceinline__ void bitonic(uint32_t cnt, Get get, Swap swp) {
     }
 }
 
+// One compare-exchange step of the same network inside a 64-slot window held by a warp in
+// registers, lane l holding slots 2l (v[0]) and 2l + 1 (v[1]): every slot e meets slot e ^ mask
+// and the lower of the two keeps the smaller key.  mask is 1 (within a lane), an odd block-flip
+// mask size - 1, or an even half-cleaner stride.
+__device__ __forceinline__ void window_step(unsigned long long (&v)[2], uint32_t mask,
+                                            uint32_t lane) {
+    if (mask == 1) {
+        const unsigned long long a = v[0], b = v[1];
+        v[0] = a < b ? a : b;
+        v[1] = a < b ? b : a;
+        return;
+    }
+    const uint32_t pl = lane ^ (mask >> 1);
+    // an odd mask pairs my even slot with the partner's odd slot and vice versa
+    const unsigned long long send0 = (mask & 1) ? v[1] : v[0];
+    const unsigned long long send1 = (mask & 1) ? v[0] : v[1];
+    const unsigned long long p0 = __shfl_sync(0xffffffffu, send0, pl);
+    const unsigned long long p1 = __shfl_sync(0xffffffffu, send1, pl);
+    const uint32_t e0 = 2 * lane, e1 = 2 * lane + 1;
+    const bool low0 = e0 < (e0 ^ mask), low1 = e1 < (e1 ^ mask);
+    v[0] = (low0 == (v[0] < p0)) ? v[0] : p0;
+    v[1] = (low1 == (v[1] < p1)) ? v[1] : p1;
+}
+
+// Loads window `win` of s (slots >= cnt read as +infinity), runs the steps of `masks`, stores
+// the slots < cnt back.  Called by whole warps.
+template <int kN>
+__device__ __forceinline__ void window_pass(unsigned long long* s, uint32_t cnt, uint32_t win,
+                                            const uint32_t (&masks)[kN]) {
+    const uint32_t lane = lane_id();
+    const uint32_t e = win * 64 + 2 * lane;
+    unsigned long long v[2];
+    v[0] = e < cnt ? s[e] : ~0ull;
+    v[1] = e + 1 < cnt ? s[e + 1] : ~0ull;
+#pragma unroll
+    for (int q = 0; q < kN; ++q) window_step(v, masks[q], lane);
+    if (e < cnt) s[e] = v[0];
+    if (e + 1 < cnt) s[e + 1] = v[1];
+}
+
+// Sorts the cnt unique 64-bit keys of s (no real key is ~0; cnt <= capacity of s) with the flip
+// bitonic network: every step whose span fits a 64-slot window runs in registers with warp
+// shuffles (the first six merge sizes entirely, and the last six steps of every larger merge);
+// only the wider steps go through shared memory, between barriers of the CTA.  Slots >= cnt are
+// never written.  Starts and ends with a barrier.
+__device__ __forceinline__ void sort_u64_smem(unsigned long long* s, uint32_t cnt) {
+    uint32_t m = 64;
+    while (m < cnt) m <<= 1;
+    const uint32_t nwin = m / 64, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    __syncthreads();
+    {   // merge sizes 2 .. 64 inside each window
+        const uint32_t masks[21] = {1, 3, 1, 7, 2, 1, 15, 4, 2, 1, 31, 8, 4, 2, 1,
+                                    63, 16, 8, 4, 2, 1};
+        for (uint32_t w = warp; w < nwin; w += nwarps) window_pass(s, cnt, w, masks);
+    }
+    const uint32_t tail[6] = {32, 16, 8, 4, 2, 1};
+    for (uint32_t lg = 7, size = 128; size <= m; ++lg, size <<= 1) {
+        __syncthreads();
+        const uint32_t half = size >> 1;
+        for (uint32_t i = threadIdx.x; i < m / 2; i += blockDim.x) {      // flip
+            const uint32_t off = i & (half - 1);
+            const uint32_t base = (i >> (lg - 1)) << lg;
+            const uint32_t lo = base + off, hi = base + size - 1 - off;
+            if (hi < cnt) {
+                const unsigned long long a = s[lo], b = s[hi];
+                if (a > b) { s[lo] = b; s[hi] = a; }
+            }
+        }
+        for (uint32_t stride = half >> 1; stride >= 64; stride >>= 1) {   // wide half-cleaners
+            __syncthreads();
+            for (uint32_t i = threadIdx.x; i < m / 2; i += blockDim.x) {
+                const uint32_t lo = 2 * i - (i & (stride - 1)), hi = lo + stride;
+                if (hi < cnt) {
+                    const unsigned long long a = s[lo], b = s[hi];
+                    if (a > b) { s[lo] = b; s[hi] = a; }
+                }
+            }
+        }
+        __syncthreads();
+        for (uint32_t w = warp; w < nwin; w += nwarps) window_pass(s, cnt, w, tail);
+    }
+    __syncthreads();
+}
+
 // sorts one tile's list (cnt <= capacity of s_k) by the unique key (depth << 32 | id)
 __device__ __forceinline__ void sort_in_smem(unsigned long long* s_k, uint2 r,
                                              uint32_t* __restrict__ keys,
@@ -480,16 +566,12 @@ __device__ __forceinline__ void sort_in_smem(unsigned long long* s_k, uint2 r,
     const uint32_t cnt = r.y - r.x;
     for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x)
         s_k[i] = ((unsigned long long)keys[r.x + i] << 32) | ids[r.x + i];
-    __syncthreads();
-    bitonic(cnt, [&](uint32_t i) { return s_k[i]; },
-            [&](uint32_t i, uint32_t j) {
-                const unsigned long long t = s_k[i]; s_k[i] = s_k[j]; s_k[j] = t;
-            });
+    sort_u64_smem(s_k, cnt);
     for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) ids[r.x + i] = (uint32_t)s_k[i];
 }
 
 // one 128-thread CTA per tile; lists longer than kSmallSort are left to tile_sort_large
-__global__ void __launch_bounds__(kSmallThreads, 12) tile_sort_small(const uint2* __restrict__ range,
+__global__ void __launch_bounds__(kSmallThreads, 10) tile_sort_small(const uint2* __restrict__ range,
                                                                  const ogs_counts* counts,
                                                                  uint32_t* __restrict__ keys,
                                                                  uint32_t* __restrict__ ids) {
