@@ -9,7 +9,9 @@
 //   layer 1    D[128 x 96]  = A1 . W1^T     (tcgen05, FP32 in TMEM)
 //   epilogue   bias, ReLU -> BF16 A2 (the two warps of a lane quarter split the columns)
 //   layer 2    D[128 x 112] = A2 . W2blk^T  (block-diagonal decoders; reuses the columns)
-//   stage      the 112 FP32 outputs of every anchor -> shared memory (over the free operands)
+//   in two rounds of 64 anchors (so that three CTAs share an SM):
+//   stage      the 112 FP32 outputs of each anchor of the round -> shared memory (over the
+//              consumed operands)
 //   project    one thread per Gaussian, consecutive Gaussians on consecutive threads: bias,
 //              activations, mean, projection, tile extent; coalesced record writes and the
 //              per-tile pair counts
@@ -40,12 +42,13 @@ constexpr int kOffWork = kImgBytes;
 constexpr int kOffA1 = kOffWork;                          // 128 x 48 bf16
 constexpr int kOffA2 = kOffA1 + kTM * kK1 * 2;            // 128 x 96 bf16
 constexpr int kOperandBytes = kTM * kK1 * 2 + kTM * kN1 * 2;
-constexpr int kStageBytes = kTM * kYStride * 4;
+constexpr int kRoundRows = kTM / 2;                      // anchors staged per round
+constexpr int kStageBytes = kRoundRows * kYStride * 4;
 constexpr int kWorkBytes = kOperandBytes > kStageBytes ? kOperandBytes : kStageBytes;
 constexpr int kOffRows = kOffWork + kWorkBytes;
 constexpr int kDpSmem = kOffRows + kTM * kRowWords * 4;
 static_assert(kImgBytes % 16 == 0 && kOffWork % 16 == 0 && kOffA2 % 16 == 0, "alignment");
-static_assert((kTM * kK) % kDpThreads == 0, "Gaussians of a tile per thread");
+constexpr int kRoundGauss = kRoundRows * kK;               // 640 Gaussians per round
 
 constexpr int kPackThreads = 256;
 constexpr int kPackG1 = kN1 * (kK1 / 8), kPackG2 = kN2 * (kN1 / 8);
@@ -104,7 +107,7 @@ __global__ void __launch_bounds__(kPackThreads) dp_pack(ogs_mlp m, unsigned char
         tile_count[e] = 0u;
 }
 
-__global__ void __launch_bounds__(kDpThreads, 2) decode_project_tc(DpArgs a) {
+__global__ void __launch_bounds__(kDpThreads, 3) decode_project_tc(DpArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ __align__(8) uint64_t wbar;
@@ -228,73 +231,82 @@ __global__ void __launch_bounds__(kDpThreads, 2) decode_project_tc(DpArgs a) {
         if (__syncthreads_or(!ok)) { aborted = true; break; }
         phase ^= 1;
         tc::fence_after_sync();
-        // ---- stage the layer-2 outputs over the (consumed) operands: half 0 columns 0..63,
-        //      half 1 columns 64..111 ----
-        for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 32) {
-            float v[32];
-            tc::tmem_ld32(lane_addr + c0, v);
-            float* y = stage + row * kYStride + c0;
-#pragma unroll
-            for (int i = 0; i < 32; ++i)
-                if (c0 + i < kN2) y[i] = v[i];
-        }
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        // ---- project: Gaussian g of the tile on thread g % 256 ----
         const size_t g_base = (size_t)tile * kTM * kK;
-#pragma unroll 1
-        for (int it = 0; it < kTM * kK / kDpThreads; ++it) {
-            const int gl = it * kDpThreads + t;
-            const int rl = gl / kK, i = gl - rl * kK;
-            const bool gv = tile * kTM + rl < M;
-            ProjOut p;
-            if (gv) {
-                const float* y = stage + rl * kYStride;
-                const float* rw = rows + rl * kRowWords;
-                const uint32_t j = __float_as_uint(rw[0]);
-                const float wgt = rw[1];
-                const float dv[3] = {rw[2], rw[3], rw[4]};
-                const float lvv[3] = {rw[5], rw[6], rw[7]};
-                const float o = act_opacity(wgt, y[i] + sb2[i]);
-                float col[3], scl[3], yc[4], mu[3];
+        for (int round = 0; round < 2; ++round) {
+            // ---- stage the layer-2 outputs of anchors 64 round .. + 63 over the consumed
+            //      operands (lane quarters 2 round, 2 round + 1): half 0 columns 0..63, half 1
+            //      columns 64..111 ----
+            if (((w & 3) >> 1) == round) {
+                for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 32) {
+                    float v[32];
+                    tc::tmem_ld32(lane_addr + c0, v);
+                    float* y = stage + (row - kRoundRows * round) * kYStride + c0;
 #pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    col[q] = act_color(y[kK + 3 * i + q] + sb2[kK + 3 * i + q]);
-                    scl[q] = act_scale(lvv[q], y[4 * kK + 7 * i + q] + sb2[4 * kK + 7 * i + q]);
+                    for (int i = 0; i < 32; ++i)
+                        if (c0 + i < kN2) y[i] = v[i];
                 }
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    yc[q] = y[4 * kK + 7 * i + 3 + q] + sb2[4 * kK + 7 * i + 3 + q];
-                const float inv = act_qinv(yc);
-                const float4 qu = make_float4(yc[0] * inv, yc[1] * inv, yc[2] * inv, yc[3] * inv);
-                const float* O = a.offs + ((size_t)j * kK + i) * 3;
-#pragma unroll
-                for (int q = 0; q < 3; ++q) mu[q] = act_mean(dv[q], O[q], lvv[q]);
-                const size_t gi = g_base + gl;
-                if (a.write_gauss) {
-                    a.out.opac[gi] = o;
+            }
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+            // ---- project: Gaussian g of the round on thread g % 256 (the same trip count for
+            //      every lane of a warp, for the tile counting) ----
+#pragma unroll 1
+            for (int it = 0; it < (kRoundGauss + kDpThreads - 1) / kDpThreads; ++it) {
+                const int gr = it * kDpThreads + t;                 // Gaussian of the round
+                const int gl = kRoundGauss * round + gr;            // Gaussian of the tile
+                const int rl = gl / kK, i = gl - rl * kK;
+                const bool gv = gr < kRoundGauss && tile * kTM + rl < M;
+                ProjOut p;
+                if (gv) {
+                    const float* y = stage + (rl - kRoundRows * round) * kYStride;
+                    const float* rw = rows + rl * kRowWords;
+                    const uint32_t j = __float_as_uint(rw[0]);
+                    const float wgt = rw[1];
+                    const float dv[3] = {rw[2], rw[3], rw[4]};
+                    const float lvv[3] = {rw[5], rw[6], rw[7]};
+                    const float o = act_opacity(wgt, y[i] + sb2[i]);
+                    float col[3], scl[3], yc[4], mu[3];
 #pragma unroll
                     for (int q = 0; q < 3; ++q) {
-                        a.out.colors[3 * gi + q] = col[q];
-                        a.out.scales[3 * gi + q] = scl[q];
-                        a.out.means[3 * gi + q] = mu[q];
+                        col[q] = act_color(y[kK + 3 * i + q] + sb2[kK + 3 * i + q]);
+                        scl[q] = act_scale(lvv[q], y[4 * kK + 7 * i + q] + sb2[4 * kK + 7 * i + q]);
                     }
-                    *reinterpret_cast<float4*>(a.out.quats + 4 * gi) = qu;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        yc[q] = y[4 * kK + 7 * i + 3 + q] + sb2[4 * kK + 7 * i + 3 + q];
+                    const float inv = act_qinv(yc);
+                    const float4 qu = make_float4(yc[0] * inv, yc[1] * inv, yc[2] * inv, yc[3] * inv);
+                    const float* O = a.offs + ((size_t)j * kK + i) * 3;
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) mu[q] = act_mean(dv[q], O[q], lvv[q]);
+                    const size_t gi = g_base + gl;
+                    if (a.write_gauss) {
+                        a.out.opac[gi] = o;
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            a.out.colors[3 * gi + q] = col[q];
+                            a.out.scales[3 * gi + q] = scl[q];
+                            a.out.means[3 * gi + q] = mu[q];
+                        }
+                        *reinterpret_cast<float4*>(a.out.quats + 4 * gi) = qu;
+                    }
+                    p = project_one(c, mu[0], mu[1], mu[2], qu, scl[0], scl[1], scl[2], o,
+                                    col[0], col[1], col[2]);
+                    a.rec[3 * gi] = p.r0;
+                    a.rec[3 * gi + 1] = p.r1;
+                    a.rec[3 * gi + 2] = p.r2;
+                    a.depth_key[gi] = p.dkey;
+                    a.rect[gi] = p.rc;
+                    a.tiles[gi] = p.ntiles;
+                } else {
+                    p.rc = make_uint2(0, 0);
+                    p.ntiles = 0;
                 }
-                p = project_one(c, mu[0], mu[1], mu[2], qu, scl[0], scl[1], scl[2], o, col[0],
-                                col[1], col[2]);
-                a.rec[3 * gi] = p.r0;
-                a.rec[3 * gi + 1] = p.r1;
-                a.rec[3 * gi + 2] = p.r2;
-                a.depth_key[gi] = p.dkey;
-                a.rect[gi] = p.rc;
-                a.tiles[gi] = p.ntiles;
-            } else {
-                p.rc = make_uint2(0, 0);
-                p.ntiles = 0;
+                if (a.tile_count) count_tiles(a.tile_count, c.gx, p.rc, p.ntiles);
             }
-            if (a.tile_count) count_tiles(a.tile_count, c.gx, p.rc, p.ntiles);
+            // the staged round is overwritten by the next round or tile
+            __syncthreads();
         }
         // staged outputs and rows are rewritten by the next tile
         tc::fence_before_sync();
@@ -356,7 +368,7 @@ extern "C" ogs_status ogs_decode_project_bf16(
              write_gauss ? 1 : 0, reinterpret_cast<float4*>(rec), depth_key,
              reinterpret_cast<uint2*>(rect), tiles, tile_count, img, cm};
     const int64_t tiles_cap = (sel_cap + kTM - 1) / kTM;
-    const int grid = (int)(tiles_cap < 2 * kSmCount ? tiles_cap : 2 * kSmCount);
+    const int grid = (int)(tiles_cap < 3 * kSmCount ? tiles_cap : 3 * kSmCount);
     decode_project_tc<<<grid, kDpThreads, kDpSmem, st>>>(a);
     return launch_status();
 }
