@@ -238,7 +238,7 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------
 
 # kernels each ABI call launches per frame
-LAUNCHES = {"lod_select": 3, "proposal_gate": 2, "decode_project": 2, "sort": 4,
+LAUNCHES = {"lod_select": 3, "lod_select_gated": 4, "decode_project": 2, "sort": 4,
             "blend_fwd": 1}
 DPSNR_GATE_DB = 0.05
 # DRAM bytes (read + write) of one blend_fwd launch from an ncu capture of the same kernel
@@ -606,7 +606,9 @@ def run_gpu(args):
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": 88,
                 "d2h_bytes_per_step": 3 * W * H * 4, "steps": n_e2e,
                 "call": "Renderer.render_to_host (render + image to pinned host memory)"},
-        "gpu_launches": args.steps * (sum(LAUNCHES.values()) - (0 if use_gate else LAUNCHES["proposal_gate"])),
+        "gpu_launches": args.steps * (LAUNCHES["lod_select_gated" if use_gate else "lod_select"]
+                                      + LAUNCHES["decode_project"] + LAUNCHES["sort"]
+                                      + LAUNCHES["blend_fwd"]),
     }
     if ws == 1 and not args.no_train:
         del rd

@@ -496,6 +496,27 @@ ogs_status ogs_proposal_gate_bf16(const float* pos, const uint8_t* level, const 
                                   float* p_out, void* scratch, size_t scratch_bytes,
                                   void* stream);
 
+/* ogs_lod_select_gated — ogs_lod_select followed by ogs_proposal_gate_bf16, in one pass over
+ * the anchors: inside the selection's tile pass, the anchors kept by the LOD rule are scored by
+ * the same tensor-core network arithmetic as ogs_proposal_gate_bf16 (so every keep decision is
+ * the same), and only the anchors that pass both are listed, in ascending order, with their
+ * LOD weights.  sel_idx, sel_w, counts->n_selected and n_gaussians are those of the two calls
+ * whenever neither overflows; here the capacity check (sel_cap, overflow bit 0, need_selected)
+ * applies to the gated list.  No keep probabilities are returned.
+ *   pos, level, dL, N, NL, k, cam, infer: as ogs_lod_select; feat f32[N][32] (16-byte
+ *   aligned), net, p_star: as ogs_proposal_gate_bf16
+ *   scratch: ogs_lod_select_gated_scratch_bytes(N) bytes, 16-byte aligned.
+ * On a tensor-core wait that does not complete, counts->timeout is set (that tile's anchors
+ * keep their LOD selection). */
+size_t ogs_lod_select_gated_scratch_bytes(int64_t N);
+ogs_status ogs_lod_select_gated(const float* pos, const uint8_t* level, const float* dL,
+                                const float* feat, int64_t N, int32_t NL, int32_t k,
+                                const ogs_camera* cam /* host */, int32_t infer,
+                                const ogs_proposal* net /* host struct */, float p_star,
+                                uint32_t* sel_idx, float* sel_w, int64_t sel_cap,
+                                ogs_counts* counts, void* scratch, size_t scratch_bytes,
+                                void* stream);
+
 /* ogs_proposal_train — mean weighted binary cross-entropy of the keep probability over the
  * selected anchors of one view against labels y = (maxc[anchor] >= tau) (maxc as written by
  * ogs_blend_fwd: float bits of the largest T*alpha), positives weighted by pos_weight (> 0),

@@ -65,6 +65,10 @@ _SIGS = {
     "ogs_lod_select_scratch_bytes": (_SZ, [_I64]),
     "ogs_lod_select": (C.c_int, [_P, _P, _P, _I64, _I32, _I32, C.POINTER(Camera), _I32, _P, _P,
                                  _I64, _P, _P, _SZ, _P]),
+    "ogs_lod_select_gated_scratch_bytes": (_SZ, [_I64]),
+    "ogs_lod_select_gated": (C.c_int, [_P, _P, _P, _P, _I64, _I32, _I32, C.POINTER(Camera),
+                                       _I32, C.POINTER(Proposal), C.c_float, _P, _P, _I64, _P,
+                                       _P, _SZ, _P]),
     "ogs_decode": (C.c_int, [_P, _P, _P, _P, _I64, C.POINTER(MLP), C.POINTER(Camera), _P, _P,
                              _I64, _P, C.POINTER(Gaussians), _P]),
     "ogs_decode_bf16": (C.c_int, [_P, _P, _P, _P, _I64, C.POINTER(MLP), C.POINTER(Camera), _P,
@@ -213,6 +217,23 @@ def lod_select(pos, level, dL, N, NL, k, cam, infer, sel_idx, sel_w, sel_cap, co
                                 C.byref(c), int(bool(infer)), _ptr(sel_idx), _ptr(sel_w),
                                 int(sel_cap), _ptr(counts), _ptr(scratch), scratch.numel(),
                                 _stream(stream)), "ogs_lod_select")
+
+
+def lod_select_gated_scratch_bytes(N):
+    return int(lib().ogs_lod_select_gated_scratch_bytes(int(N)))
+
+
+def lod_select_gated(pos, level, dL, feat, N, NL, k, cam, infer, net, p_star, sel_idx, sel_w,
+                     sel_cap, counts, scratch, stream=None):
+    """LOD selection and the BF16 proposal gate in one pass (ogs_lod_select_gated)."""
+    c = cam if isinstance(cam, Camera) else camera(cam)
+    n = net if isinstance(net, Proposal) else proposal_struct(net)
+    _check(lib().ogs_lod_select_gated(_ptr(pos), _ptr(level), _ptr(dL), _ptr(feat), int(N),
+                                      int(NL), int(k), C.byref(c), int(bool(infer)),
+                                      C.byref(n), float(p_star), _ptr(sel_idx), _ptr(sel_w),
+                                      int(sel_cap), _ptr(counts), _ptr(scratch),
+                                      scratch.numel(), _stream(stream)),
+           "ogs_lod_select_gated")
 
 
 def decode(pos, feat, offs, lv, N, mlp, cam, sel_idx, sel_w, sel_cap, counts, out,

@@ -13,15 +13,13 @@
 //        written as partials and summed in a fixed order.
 #include <cstring>
 
-#include "internal.cuh"
-#include "tc.cuh"
+#include "gate_common.cuh"
 
 namespace ogs {
 namespace {
 
-constexpr int kPIn = 37;
-constexpr int kPInPad = 40;
-constexpr int kPH = 64;
+using namespace gate;
+
 constexpr int kGateThreads = 128;
 constexpr int kNetFloats = kPH * kPInPad + kPH + kPH * kPH + kPH + kPH + 4;   // smem image
 
@@ -60,23 +58,8 @@ __device__ void load_net(const ogs_proposal& n, float* s) {
 }
 
 __device__ __forceinline__ void prop_input(const PropArgs& a, uint32_t j, float (&x)[kPInPad]) {
-    const Cam& c = a.cam;
-    const float4* f4 = reinterpret_cast<const float4*>(a.feat + (size_t)j * 32);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const float4 v = f4[i];
-        x[4 * i] = v.x; x[4 * i + 1] = v.y; x[4 * i + 2] = v.z; x[4 * i + 3] = v.w;
-    }
-    const float dx = a.pos[3 * (size_t)j] - c.c[0], dy = a.pos[3 * (size_t)j + 1] - c.c[1],
-                dz = a.pos[3 * (size_t)j + 2] - c.c[2];
-    const float d = sqrtf(dx * dx + dy * dy + dz * dz);
-    x[32] = (float)a.level[j] / (float)max(a.NL - 1, 1);
-    // viewing direction in the camera frame
-    x[33] = (c.R[0] * dx + c.R[1] * dy + c.R[2] * dz) / d;
-    x[34] = (c.R[3] * dx + c.R[4] * dy + c.R[5] * dz) / d;
-    x[35] = (c.R[6] * dx + c.R[7] * dy + c.R[8] * dz) / d;
-    x[36] = logf(d / c.d_max);
-    x[37] = x[38] = x[39] = 0.f;
+    prop_input_vals(a.feat + (size_t)j * 32, a.pos[3 * (size_t)j], a.pos[3 * (size_t)j + 1],
+                    a.pos[3 * (size_t)j + 2], a.level[j], a.NL, a.cam, x);
 }
 
 __device__ __forceinline__ float prop_logit(const float* s, const float (&x)[kPInPad]) {
@@ -159,30 +142,10 @@ __global__ void __launch_bounds__(kGateThreads) gate_score(PropArgs a, const uin
 // thread.  Same outputs as gate_score: p per entry, keep count per 128-entry tile.
 // ---------------------------------------------------------------------------------------
 
-constexpr int kGK1 = 48;
-constexpr uint32_t kGTmemCols = 64;
-constexpr uint32_t kGWaitLimit = 1u << 24;
-// Shared memory: the network image (B1, B2, vectors; packed once per call by gate_pack and
-// fetched by one bulk copy) followed by the A operand.  Layer 1's A (128 x 48) and layer 2's A
-// (128 x 64) share one buffer: the first-layer epilogue writes H1 only after the layer-1
-// product has completed, and the next tile's inputs land only after layer 2 has.
-constexpr int kGOffB1 = 0;                               // 64 x 48 bf16
-constexpr int kGOffB2 = kGOffB1 + kPH * kGK1 * 2;        // 64 x 64 bf16
-constexpr int kGOffVec = kGOffB2 + kPH * kPH * 2;        // b1, b2, w3 (f32), b3 (+ pad)
-constexpr int kGImgBytes = kGOffVec + (3 * kPH + 4) * 4;
-constexpr int kGOffA = kGImgBytes;                       // 128 x 64 bf16 (A1 uses 128 x 48)
-constexpr int kGSmem = kGOffA + 128 * kPH * 2;
-static_assert(kGImgBytes % 16 == 0 && kGOffA % 16 == 0, "bulk copy granularity");
+constexpr int kGOffA = kGImgBytes;                       // A operand after the image
+constexpr int kGSmem = kGOffA + kGABytes;
+static_assert(kGOffA % 16 == 0, "bulk copy granularity");
 static_assert(kGateThreads == 128, "one TMEM lane (anchor) per thread");
-
-__device__ __forceinline__ void gput8(unsigned char* base, int row, int kc, int Kpad,
-                                      const float (&v)[8]) {
-    __nv_bfloat162 h[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-    *reinterpret_cast<uint4*>(base + tc::core_offset(row, 8 * kc, Kpad)) =
-        *reinterpret_cast<const uint4*>(h);
-}
 
 // Per call: the first kGPackCtas CTAs write the network image (BF16 operand tiles of W1 (K
 // padded to 48) and W2 in the no-swizzle K-major core-matrix layout, then b1, b2, w3, b3 in
@@ -246,12 +209,6 @@ __global__ void __launch_bounds__(kGateThreads, 5) gate_tc(PropArgs a, const uin
     __shared__ uint32_t s_tile;
     __shared__ uint32_t wc[kGateThreads / 32];
     unsigned char* sA1 = sm + kGOffA;
-    unsigned char* sB1 = sm + kGOffB1;
-    unsigned char* sA2 = sm + kGOffA;
-    unsigned char* sB2 = sm + kGOffB2;
-    const float* sb1 = reinterpret_cast<const float*>(sm + kGOffVec);
-    const float* sb2 = sb1 + kPH;
-    const float* sw3 = sb2 + kPH;
     const int t = threadIdx.x, w = t >> 5;
     const uint32_t M = counts->n_selected;
     const uint32_t ntiles = (M + 127) / 128;
@@ -273,8 +230,6 @@ __global__ void __launch_bounds__(kGateThreads, 5) gate_tc(PropArgs a, const uin
         __syncthreads();
         tc::fence_after_sync();
         const uint32_t tbase = tmem_base;
-        const uint32_t lane_addr = tbase + ((uint32_t)(32 * w) << 16);
-        const uint32_t id = tc::idesc_bf16(128, kPH);
         uint32_t phase = 0;
         bool aborted = false;
         bool have_net = false;
@@ -294,14 +249,7 @@ __global__ void __launch_bounds__(kGateThreads, 5) gate_tc(PropArgs a, const uin
 #pragma unroll
                     for (int i = 0; i < kPInPad; ++i) x[i] = 0.f;
                 }
-#pragma unroll
-                for (int kc = 0; kc < kPInPad / 8; ++kc) {
-                    const float v[8] = {x[8 * kc], x[8 * kc + 1], x[8 * kc + 2], x[8 * kc + 3],
-                                        x[8 * kc + 4], x[8 * kc + 5], x[8 * kc + 6], x[8 * kc + 7]};
-                    gput8(sA1, t, kc, kGK1, v);
-                }
-                const float z8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                gput8(sA1, t, kGK1 / 8 - 1, kGK1, z8);    // inputs 40..47 (H1 overwrote them)
+                put_input_row(sA1, t, x);
             }
             if (!have_net) {                          // the network image, once per CTA
                 have_net = true;
@@ -311,69 +259,15 @@ __global__ void __launch_bounds__(kGateThreads, 5) gate_tc(PropArgs a, const uin
                     tc::mbar_wait(&wbar, 0, kGWaitLimit);
                 }
             }
-            tc::fence_smem_to_async();
-            tc::fence_before_sync();
-            __syncthreads();
-            tc::fence_after_sync();
-            if (t == 0) {
-#pragma unroll
-                for (int kk = 0; kk < kGK1 / 16; ++kk)
-                    tc::mma_bf16(tbase, tc::smem_desc(tc::smem_u32(sA1 + kk * 256), 128, 16 * kGK1),
-                                 tc::smem_desc(tc::smem_u32(sB1 + kk * 256), 128, 16 * kGK1), id,
-                                 kk > 0);
-                tc::commit(&mbar);
-            }
-            bool ok = tc::mbar_wait(&mbar, phase, kGWaitLimit);
-            if (__syncthreads_or(!ok)) {
+            float z;
+            if (!gate_hidden(sA1, sm, tbase, &mbar, phase, z)) {
                 aborted = true;
                 if (t == 0) store_status(status + tile, kFlagPrefix);   // let successors finish
                 break;
             }
-            phase ^= 1;
-            tc::fence_after_sync();
-#pragma unroll
-            for (int c0 = 0; c0 < kPH; c0 += 32) {
-                float v[32];
-                tc::tmem_ld32(lane_addr + c0, v);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    float h8[8];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) h8[i] = fmaxf(v[8 * q + i] + sb1[c0 + 8 * q + i], 0.f);
-                    gput8(sA2, t, c0 / 8 + q, kPH, h8);
-                }
-            }
-            tc::fence_smem_to_async();
-            tc::fence_before_sync();
-            __syncthreads();
-            tc::fence_after_sync();
-            if (t == 0) {
-#pragma unroll
-                for (int kk = 0; kk < kPH / 16; ++kk)
-                    tc::mma_bf16(tbase, tc::smem_desc(tc::smem_u32(sA2 + kk * 256), 128, 16 * kPH),
-                                 tc::smem_desc(tc::smem_u32(sB2 + kk * 256), 128, 16 * kPH), id,
-                                 kk > 0);
-                tc::commit(&mbar);
-            }
-            ok = tc::mbar_wait(&mbar, phase, kGWaitLimit);
-            if (__syncthreads_or(!ok)) {
-                aborted = true;
-                if (t == 0) store_status(status + tile, kFlagPrefix);
-                break;
-            }
-            phase ^= 1;
-            tc::fence_after_sync();
-            float z = sb1[3 * kPH];                  // b3
-#pragma unroll
-            for (int c0 = 0; c0 < kPH; c0 += 32) {
-                float v[32];
-                tc::tmem_ld32(lane_addr + c0, v);
-#pragma unroll
-                for (int i = 0; i < 32; ++i) z = fmaf(sw3[c0 + i], fmaxf(v[i] + sb2[c0 + i], 0.f), z);
-            }
             bool keep = false;
             if (valid) {
-                const float p = 1.0f / (1.0f + __expf(-z));
+                const float p = keep_prob(z);
                 if (p_out) p_out[r] = p;
                 keep = p >= p_star;
             }
@@ -642,6 +536,13 @@ bool net_ok(const ogs_proposal* n) {
 
 using namespace ogs;
 
+ogs_status ogs::gate::pack_image(const ogs_proposal& net, unsigned char* img,
+                                 unsigned long long* status, int n_words, cudaStream_t st) {
+    const int nz = n_words > 0 ? (n_words + 1023) / 1024 : 0;
+    gate_pack<<<kGPackCtas + nz, kGPackThreads, 0, st>>>(net, img, status, n_words);
+    return launch_status();
+}
+
 extern "C" size_t ogs_proposal_gate_scratch_bytes(int64_t sel_cap) {
     int64_t nb = (sel_cap + kGateThreads - 1) / kGateThreads;
     if (nb < 1) nb = 1;
@@ -682,8 +583,7 @@ ogs_status proposal_gate_impl(bool tensor_cores, const float* pos, const uint8_t
         // together with the network image
         unsigned long long* status = reinterpret_cast<unsigned long long*>(block);
         uint32_t* sync_words = reinterpret_cast<uint32_t*>(status + nb);
-        gate_pack<<<kGPackCtas + (nb + 1 + 1023) / 1024, kGPackThreads, 0, st>>>(*net, img, status,
-                                                                              nb + 1);
+        if (gate::pack_image(*net, img, status, nb + 1, st) != OGS_OK) return OGS_ERR_CUDA;
         const int grid = nb < 5 * kSmCount ? nb : 5 * kSmCount;
         gate_tc<<<grid, kGateThreads, kGSmem, st>>>(a, sel_in, w_in, k, counts, p_star, p_out,
                                                     sel_out, w_out, img, status, sync_words);

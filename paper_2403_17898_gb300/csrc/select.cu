@@ -7,8 +7,7 @@
 // writes every anchor's weight (4 B) and the tile's kept count; one CTA scans the counts; the
 // scatter re-reads only the weights, ranks kept anchors with warp scans and writes them in
 // ascending anchor order.  No CTA waits on another, so every tile streams at full rate.
-#include "internal.cuh"
-#include "tc.cuh"
+#include "gate_common.cuh"
 
 namespace ogs {
 namespace {
@@ -110,6 +109,143 @@ __global__ void __launch_bounds__(kSelThreads) select_eval(SelArgs a, float* __r
 #pragma unroll
         for (int i = 0; i < kSelWarps; ++i) t += s_wc[i];
         tile_count[blockIdx.x] = t;
+    }
+}
+
+// Pass 1 of the gated selection (same tiles): the LOD predicate as in select_eval, then the
+// learned gate on the tile's kept anchors in chunks of 128 rows (tensor-core network shared
+// with ogs_proposal_gate_bf16, so the keep decisions are the same bits); an anchor the gate
+// drops gets weight 0, so passes 2 and 3 build the gated list directly.
+constexpr int kSgOffImg = 0;                              // network image
+constexpr int kSgOffA = gate::kGImgBytes;                 // gate A operand
+constexpr int kSgSmem = kSgOffA + gate::kGABytes;
+
+__global__ void __launch_bounds__(kSelThreads, 3) select_eval_gated(
+    SelArgs a, const float* __restrict__ feat, const unsigned char* __restrict__ img,
+    float p_star, float* __restrict__ wsel, uint32_t* __restrict__ tile_count,
+    ogs_counts* counts, int bulk) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ __align__(16) float s_pos[3 * kSelChunk];
+    __shared__ __align__(16) float s_dl[kSelChunk];
+    __shared__ __align__(16) uint8_t s_lvl[kSelChunk];
+    __shared__ uint16_t s_list[kSelChunk];
+    __shared__ uint8_t s_drop[kSelChunk];
+    __shared__ __align__(8) uint64_t mbar, wbar, gbar;
+    __shared__ uint32_t s_wc[kSelWarps];
+    __shared__ uint32_t s_n;
+    __shared__ uint32_t tmem_base;
+    const int t = threadIdx.x;
+    const int64_t base = (int64_t)blockIdx.x * kSelChunk;
+    const int n_here = (int)min((int64_t)kSelChunk, a.N - base);
+    const bool tma = bulk && n_here == kSelChunk;
+    if (t == 0) {
+        s_n = 0;
+        tc::mbar_init(&wbar, 1);
+        tc::mbar_init(&gbar, 1);
+        tc::mbar_expect_tx(&wbar, gate::kGImgBytes);
+        tc::bulk_load(sm + kSgOffImg, img, gate::kGImgBytes, &wbar);
+        if (tma) {
+            tc::mbar_init(&mbar, 1);
+            tc::mbar_expect_tx(&mbar, (3 * 4 + 4 + 1) * kSelChunk);
+            tc::bulk_load(s_pos, a.pos + 3 * base, 3 * 4 * kSelChunk, &mbar);
+            tc::bulk_load(s_dl, a.dL + base, 4 * kSelChunk, &mbar);
+            tc::bulk_load(s_lvl, a.level + base, kSelChunk, &mbar);
+        }
+    }
+    if (tma) {
+        __syncthreads();                              // barriers initialised before anyone polls
+        if (!tc::mbar_wait(&mbar, 0, kSpinLimit)) {
+            if (t == 0) atomicExch(&counts->timeout, 1u);
+            tc::mbar_wait(&mbar, 0, kSpinLimit);      // copies may still be landing
+        }
+    } else {
+        for (int e = t; e < 3 * n_here; e += kSelThreads) s_pos[e] = a.pos[3 * base + e];
+        for (int e = t; e < n_here; e += kSelThreads) {
+            s_dl[e] = a.dL[base + e];
+            s_lvl[e] = a.level[base + e];
+        }
+        __syncthreads();
+    }
+    // LOD predicate; kept anchors listed (in any order) for the gate
+    float wv[kSelItems];
+#pragma unroll
+    for (int it = 0; it < kSelItems; ++it) {
+        const int l = it * kSelThreads + t;
+        float w = 0.0f;
+        const bool keep = l < n_here && keep_anchor(a, s_pos[3 * l], s_pos[3 * l + 1],
+                                                    s_pos[3 * l + 2], s_lvl[l], s_dl[l], w);
+        wv[it] = keep ? w : 0.0f;
+        if (keep) {
+            s_drop[l] = 0;
+            s_list[atomicAdd(&s_n, 1u)] = (uint16_t)l;
+        }
+    }
+    __syncthreads();
+    const uint32_t K = s_n;
+    bool gated = true;
+    if (K > 0) {                                      // uniform
+        if ((t >> 5) == 0) {
+            tc::tmem_alloc(&tmem_base, gate::kGTmemCols);
+            tc::tmem_relinquish();
+        }
+        if (!tc::mbar_wait(&wbar, 0, gate::kGWaitLimit)) {
+            if (t == 0) atomicExch(&counts->timeout, 1u);
+            tc::mbar_wait(&wbar, 0, gate::kGWaitLimit);
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        const uint32_t tbase = tmem_base;
+        uint32_t phase = 0;
+        unsigned char* sA = sm + kSgOffA;
+        for (uint32_t c0 = 0; c0 < K; c0 += 128) {
+            const uint32_t r = c0 + (uint32_t)t;
+            if (t < 128) {
+                float x[gate::kPInPad];
+                if (r < K) {
+                    const int l = s_list[r];
+                    gate::prop_input_vals(feat + (size_t)(base + l) * 32, s_pos[3 * l],
+                                          s_pos[3 * l + 1], s_pos[3 * l + 2], s_lvl[l], a.NL,
+                                          a.cam, x);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < gate::kPInPad; ++i) x[i] = 0.f;
+                }
+                gate::put_input_row(sA, t, x);
+            }
+            float z;
+            if (!gate::gate_hidden(sA, sm + kSgOffImg, tbase, &gbar, phase, z)) {
+                gated = false;                        // keep the LOD selection of this tile
+                break;
+            }
+            if (t < 128 && r < K) s_drop[s_list[r]] = gate::keep_prob(z) >= p_star ? 0 : 1;
+        }
+        if (!gated) {
+            if (t == 0) atomicExch(&counts->timeout, 1u);
+            tc::mbar_wait(&gbar, phase, gate::kGWaitLimit);   // the product still in flight
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        if ((t >> 5) == 0) tc::tmem_dealloc(tbase, gate::kGTmemCols);
+    } else if (!tc::mbar_wait(&wbar, 0, gate::kGWaitLimit)) {   // let the image copy land
+        if (t == 0) atomicExch(&counts->timeout, 1u);
+        tc::mbar_wait(&wbar, 0, gate::kGWaitLimit);
+    }
+    uint32_t mine = 0;
+#pragma unroll
+    for (int it = 0; it < kSelItems; ++it) {
+        const int l = it * kSelThreads + t;
+        const bool keep = wv[it] > 0.0f && !(gated && s_drop[l]);
+        if (l < n_here) wsel[base + l] = keep ? wv[it] : 0.0f;
+        mine += __popc(__ballot_sync(0xffffffffu, keep));
+    }
+    if (lane_id() == 0) s_wc[t >> 5] = mine;
+    __syncthreads();
+    if (t == 0) {
+        uint32_t tot = 0;
+#pragma unroll
+        for (int i = 0; i < kSelWarps; ++i) tot += s_wc[i];
+        tile_count[blockIdx.x] = tot;
     }
 }
 
@@ -251,6 +387,48 @@ extern "C" ogs_status ogs_lod_select(const float* pos, const uint8_t* level, con
     float* wsel = cv.take<float>((size_t)(N > 0 ? N : 1));
     const int bulk = aligned(pos, 16) && aligned(dL, 16) && aligned(level, 16);
     select_eval<<<nb, kSelThreads, 0, st>>>(a, wsel, tile_count, counts, bulk);
+    select_scan<<<1, 1024, 0, st>>>(tile_count, nb, sel_cap, k, counts);
+    select_scatter<<<nb, kSelThreads, 0, st>>>(wsel, tile_count, N, sel_idx, sel_w, sel_cap);
+    return launch_status();
+}
+
+extern "C" size_t ogs_lod_select_gated_scratch_bytes(int64_t N) {
+    return ogs_lod_select_scratch_bytes(N) + gate::kGImgBytes + 256;
+}
+
+extern "C" ogs_status ogs_lod_select_gated(const float* pos, const uint8_t* level,
+                                           const float* dL, const float* feat, int64_t N,
+                                           int32_t NL, int32_t k, const ogs_camera* cam,
+                                           int32_t infer, const ogs_proposal* net,
+                                           float p_star, uint32_t* sel_idx, float* sel_w,
+                                           int64_t sel_cap, ogs_counts* counts, void* scratch,
+                                           size_t scratch_bytes, void* stream) {
+    if (!pos || !level || !dL || !feat || !cam || !net || !sel_idx || !sel_w || !counts ||
+        !scratch)
+        return OGS_ERR_ARG;
+    if (!net->w1 || !net->b1 || !net->w2 || !net->b2 || !net->w3 || !net->b3) return OGS_ERR_ARG;
+    if (N < 0 || N > 0xFFFFFFFFll || NL < 1 || NL > 255 || k < 1 || sel_cap < 0)
+        return OGS_ERR_ARG;
+    if (cam->width <= 0 || cam->height <= 0 || !(cam->d_max > 0) || !(cam->s > 0))
+        return OGS_ERR_ARG;
+    if (scratch_bytes < ogs_lod_select_gated_scratch_bytes(N) || !aligned(scratch, 16) ||
+        !aligned(feat, 16))
+        return OGS_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    SelArgs a{pos, level, dL, N, NL, k, infer, make_cam(*cam)};
+    int nb = (int)((N + kSelChunk - 1) / kSelChunk);
+    if (nb < 1) nb = 1;
+    Carver cv(scratch);
+    uint32_t* tile_count = cv.take<uint32_t>((size_t)nb);
+    float* wsel = cv.take<float>((size_t)(N > 0 ? N : 1));
+    unsigned char* img = cv.take<unsigned char>(gate::kGImgBytes);
+    if (gate::pack_image(*net, img, nullptr, 0, st) != OGS_OK) return OGS_ERR_CUDA;
+    if (cudaFuncSetAttribute(select_eval_gated, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kSgSmem) != cudaSuccess)
+        return OGS_ERR_CUDA;
+    const int bulk = aligned(pos, 16) && aligned(dL, 16) && aligned(level, 16);
+    select_eval_gated<<<nb, kSelThreads, kSgSmem, st>>>(a, feat, img, p_star, wsel, tile_count,
+                                                        counts, bulk);
     select_scan<<<1, 1024, 0, st>>>(tile_count, nb, sel_cap, k, counts);
     select_scatter<<<nb, kSelThreads, 0, st>>>(wsel, tile_count, N, sel_idx, sel_w, sel_cap);
     return launch_status();

@@ -65,6 +65,9 @@ class Renderer:
         # BF16 neural form: decode and projection in one kernel (ogs_decode_project_bf16);
         # False runs ogs_decode_bf16 and ogs_project_bin as two calls
         self.fuse_decode_project = True
+        # BF16 gate: scored inside the selection pass (ogs_lod_select_gated); False runs
+        # ogs_lod_select and ogs_proposal_gate_bf16 as two calls
+        self.fuse_gate = True
         self.k = k
         self.W, self.H = int(W), int(H)
         self.gx, self.gy = (self.W + TILE - 1) // TILE, (self.H + TILE - 1) // TILE
@@ -87,8 +90,8 @@ class Renderer:
             self._mlp_struct = abi.mlp_struct(self.mlp, k=k)
         self.sel_cap = int(sel_cap if sel_cap is not None else max(1024, self.N))
         self.pair_cap = int(pair_cap if pair_cap is not None else 1 << 20)
-        self.sel_scratch = torch.empty(abi.lod_select_scratch_bytes(self.N), dtype=torch.uint8,
-                                       device="cuda")
+        self.sel_scratch = torch.empty(abi.lod_select_gated_scratch_bytes(self.N),
+                                       dtype=torch.uint8, device="cuda")
         self.counts_t = torch.zeros(8, dtype=torch.int32, device="cuda")
         self.img = torch.empty(3, self.H, self.W, device="cuda")
         self.T = torch.empty(self.H, self.W, device="cuda")
@@ -141,17 +144,24 @@ class Renderer:
             _stage(timers, name, st, fn)
 
         self.counts_t.zero_()
-        stage("lod_select", lambda: abi.lod_select(
-            self.pos, self.level, self.dL, self.N, self.NL, self.k, c, infer, self.sel_idx,
-            self.sel_w, self.sel_cap, self.counts_t, self.sel_scratch, st))
         sel, selw = self.sel_idx, self.sel_w
-        if gate is not None:
+        if gate is not None and self.precision == "bf16" and self.fuse_gate:
             net, p_star = gate
-            stage("proposal_gate", lambda: abi.proposal_gate(
-                self.pos, self.level, self.feat, self.N, self.NL, self.k, c, net, p_star,
-                self.sel_idx, self.sel_w, self.sel_cap, self.counts_t, self.sel_idx_g,
-                self.sel_w_g, None, self.gate_scratch, st, bf16=self.precision == "bf16"))
-            sel, selw = self.sel_idx_g, self.sel_w_g
+            stage("lod_select", lambda: abi.lod_select_gated(
+                self.pos, self.level, self.dL, self.feat, self.N, self.NL, self.k, c, infer,
+                net, p_star, self.sel_idx, self.sel_w, self.sel_cap, self.counts_t,
+                self.sel_scratch, st))
+        else:
+            stage("lod_select", lambda: abi.lod_select(
+                self.pos, self.level, self.dL, self.N, self.NL, self.k, c, infer, self.sel_idx,
+                self.sel_w, self.sel_cap, self.counts_t, self.sel_scratch, st))
+            if gate is not None:
+                net, p_star = gate
+                stage("proposal_gate", lambda: abi.proposal_gate(
+                    self.pos, self.level, self.feat, self.N, self.NL, self.k, c, net, p_star,
+                    self.sel_idx, self.sel_w, self.sel_cap, self.counts_t, self.sel_idx_g,
+                    self.sel_w_g, None, self.gate_scratch, st, bf16=self.precision == "bf16"))
+                sel, selw = self.sel_idx_g, self.sel_w_g
         self.active_sel = sel
         if self.explicit is None and self.precision == "bf16" and self.fuse_decode_project:
             # decoded Gaussians go straight to screen records; the Gaussian SoA is written only
@@ -382,6 +392,6 @@ class Trainer(Renderer):
         self.N = n
         self.sel_count = torch.zeros(self.N, dtype=torch.int32, device=dev)
         self.n_views_seen = 0
-        self.sel_scratch = torch.empty(abi.lod_select_scratch_bytes(self.N), dtype=torch.uint8,
-                                       device=dev)
+        self.sel_scratch = torch.empty(abi.lod_select_gated_scratch_bytes(self.N),
+                                       dtype=torch.uint8, device=dev)
         return n
