@@ -115,10 +115,23 @@ __global__ void __launch_bounds__(kSelThreads) select_eval(SelArgs a, float* __r
 // Pass 1 of the gated selection (same tiles): the LOD predicate as in select_eval, then the
 // learned gate on the tile's kept anchors in chunks of 128 rows (tensor-core network shared
 // with ogs_proposal_gate_bf16, so the keep decisions are the same bits); an anchor the gate
-// drops gets weight 0, so passes 2 and 3 build the gated list directly.
+// drops gets weight 0, so passes 2 and 3 build the gated list directly.  Persistent CTAs
+// (three per SM) take tiles round-robin: the network image and the tensor memory are set up
+// once per CTA, and the next tile's bulk copy is issued as soon as the current tile's staged
+// arrays are no longer read (once the last chunk's gate inputs are built), so it lands while
+// the gate runs.
 constexpr int kSgOffImg = 0;                              // network image
 constexpr int kSgOffA = gate::kGImgBytes;                 // gate A operand
 constexpr int kSgSmem = kSgOffA + gate::kGABytes;
+
+__device__ __forceinline__ void sg_issue_tile(const SelArgs& a, int64_t tile, float* s_pos,
+                                              float* s_dl, uint8_t* s_lvl, uint64_t* mbar) {
+    const int64_t base = tile * kSelChunk;
+    tc::mbar_expect_tx(mbar, (3 * 4 + 4 + 1) * kSelChunk);
+    tc::bulk_load(s_pos, a.pos + 3 * base, 3 * 4 * kSelChunk, mbar);
+    tc::bulk_load(s_dl, a.dL + base, 4 * kSelChunk, mbar);
+    tc::bulk_load(s_lvl, a.level + base, kSelChunk, mbar);
+}
 
 __global__ void __launch_bounds__(kSelThreads, 3) select_eval_gated(
     SelArgs a, const float* __restrict__ feat, const unsigned char* __restrict__ img,
@@ -135,70 +148,76 @@ __global__ void __launch_bounds__(kSelThreads, 3) select_eval_gated(
     __shared__ uint32_t s_n;
     __shared__ uint32_t tmem_base;
     const int t = threadIdx.x;
-    const int64_t base = (int64_t)blockIdx.x * kSelChunk;
-    const int n_here = (int)min((int64_t)kSelChunk, a.N - base);
-    const bool tma = bulk && n_here == kSelChunk;
+    const int64_t nb = (a.N + kSelChunk - 1) / kSelChunk;
+    // a tile is copied in bulk when it is full and the arrays are aligned
+    auto full = [&](int64_t tile) { return bulk && (tile + 1) * kSelChunk <= a.N; };
     if (t == 0) {
-        s_n = 0;
+        tc::mbar_init(&mbar, 1);
         tc::mbar_init(&wbar, 1);
         tc::mbar_init(&gbar, 1);
         tc::mbar_expect_tx(&wbar, gate::kGImgBytes);
         tc::bulk_load(sm + kSgOffImg, img, gate::kGImgBytes, &wbar);
-        if (tma) {
-            tc::mbar_init(&mbar, 1);
-            tc::mbar_expect_tx(&mbar, (3 * 4 + 4 + 1) * kSelChunk);
-            tc::bulk_load(s_pos, a.pos + 3 * base, 3 * 4 * kSelChunk, &mbar);
-            tc::bulk_load(s_dl, a.dL + base, 4 * kSelChunk, &mbar);
-            tc::bulk_load(s_lvl, a.level + base, kSelChunk, &mbar);
-        }
+        if (full(blockIdx.x)) sg_issue_tile(a, blockIdx.x, s_pos, s_dl, s_lvl, &mbar);
     }
-    if (tma) {
-        __syncthreads();                              // barriers initialised before anyone polls
-        if (!tc::mbar_wait(&mbar, 0, kSpinLimit)) {
-            if (t == 0) atomicExch(&counts->timeout, 1u);
-            tc::mbar_wait(&mbar, 0, kSpinLimit);      // copies may still be landing
-        }
-    } else {
-        for (int e = t; e < 3 * n_here; e += kSelThreads) s_pos[e] = a.pos[3 * base + e];
-        for (int e = t; e < n_here; e += kSelThreads) {
-            s_dl[e] = a.dL[base + e];
-            s_lvl[e] = a.level[base + e];
-        }
-        __syncthreads();
+    if ((t >> 5) == 0) {
+        tc::tmem_alloc(&tmem_base, gate::kGTmemCols);
+        tc::tmem_relinquish();
     }
-    // LOD predicate; kept anchors listed (in any order) for the gate
-    float wv[kSelItems];
-#pragma unroll
-    for (int it = 0; it < kSelItems; ++it) {
-        const int l = it * kSelThreads + t;
-        float w = 0.0f;
-        const bool keep = l < n_here && keep_anchor(a, s_pos[3 * l], s_pos[3 * l + 1],
-                                                    s_pos[3 * l + 2], s_lvl[l], s_dl[l], w);
-        wv[it] = keep ? w : 0.0f;
-        if (keep) {
-            s_drop[l] = 0;
-            s_list[atomicAdd(&s_n, 1u)] = (uint16_t)l;
-        }
-    }
+    tc::fence_before_sync();
     __syncthreads();
-    const uint32_t K = s_n;
-    bool gated = true;
-    if (K > 0) {                                      // uniform
-        if ((t >> 5) == 0) {
-            tc::tmem_alloc(&tmem_base, gate::kGTmemCols);
-            tc::tmem_relinquish();
+    tc::fence_after_sync();
+    const uint32_t tbase = tmem_base;
+    bool net_ok = tc::mbar_wait(&wbar, 0, gate::kGWaitLimit);
+    if (!net_ok) {
+        if (t == 0) atomicExch(&counts->timeout, 1u);
+        tc::mbar_wait(&wbar, 0, gate::kGWaitLimit);   // the copy may still be landing
+    }
+    uint32_t tma_phase = 0, phase = 0;
+    bool mma_ok = true;
+    unsigned char* sA = sm + kSgOffA;
+    for (int64_t tile = blockIdx.x; tile < nb; tile += gridDim.x) {
+        const int64_t base = tile * kSelChunk;
+        const int n_here = (int)min((int64_t)kSelChunk, a.N - base);
+        if (full(tile)) {
+            if (!tc::mbar_wait(&mbar, tma_phase, kSpinLimit)) {
+                if (t == 0) atomicExch(&counts->timeout, 1u);
+                tc::mbar_wait(&mbar, tma_phase, kSpinLimit);   // copies may still be landing
+            }
+            tma_phase ^= 1;
+        } else {
+            for (int e = t; e < 3 * n_here; e += kSelThreads) s_pos[e] = a.pos[3 * base + e];
+            for (int e = t; e < n_here; e += kSelThreads) {
+                s_dl[e] = a.dL[base + e];
+                s_lvl[e] = a.level[base + e];
+            }
         }
-        if (!tc::mbar_wait(&wbar, 0, gate::kGWaitLimit)) {
-            if (t == 0) atomicExch(&counts->timeout, 1u);
-            tc::mbar_wait(&wbar, 0, gate::kGWaitLimit);
-        }
-        tc::fence_before_sync();
+        if (t == 0) s_n = 0;
         __syncthreads();
-        tc::fence_after_sync();
-        const uint32_t tbase = tmem_base;
-        uint32_t phase = 0;
-        unsigned char* sA = sm + kSgOffA;
-        for (uint32_t c0 = 0; c0 < K; c0 += 128) {
+        // LOD predicate; kept anchors listed (in any order) for the gate
+        float wv[kSelItems];
+#pragma unroll
+        for (int it = 0; it < kSelItems; ++it) {
+            const int l = it * kSelThreads + t;
+            float w = 0.0f;
+            const bool keep = l < n_here && keep_anchor(a, s_pos[3 * l], s_pos[3 * l + 1],
+                                                        s_pos[3 * l + 2], s_lvl[l], s_dl[l], w);
+            wv[it] = keep ? w : 0.0f;
+            if (keep) {
+                s_drop[l] = 0;
+                s_list[atomicAdd(&s_n, 1u)] = (uint16_t)l;
+            }
+        }
+        __syncthreads();
+        const uint32_t K = s_n;
+        const int64_t next = tile + gridDim.x;
+        const bool prefetch = next < nb && full(next);
+        bool issued = false;
+        if (K == 0) {                                 // staged arrays no longer read
+            if (t == 0 && prefetch) sg_issue_tile(a, next, s_pos, s_dl, s_lvl, &mbar);
+            issued = true;
+        }
+        bool gated = mma_ok;
+        for (uint32_t c0 = 0; gated && c0 < K; c0 += 128) {
             const uint32_t r = c0 + (uint32_t)t;
             if (t < 128) {
                 float x[gate::kPInPad];
@@ -213,40 +232,45 @@ __global__ void __launch_bounds__(kSelThreads, 3) select_eval_gated(
                 }
                 gate::put_input_row(sA, t, x);
             }
+            if (c0 + 128 >= K) {                      // last chunk: staged arrays now free
+                __syncthreads();
+                if (t == 0 && prefetch) sg_issue_tile(a, next, s_pos, s_dl, s_lvl, &mbar);
+                issued = true;
+            }
             float z;
             if (!gate::gate_hidden(sA, sm + kSgOffImg, tbase, &gbar, phase, z)) {
-                gated = false;                        // keep the LOD selection of this tile
+                gated = mma_ok = false;               // this and later tiles keep the LOD list
+                if (t == 0) atomicExch(&counts->timeout, 1u);
+                tc::mbar_wait(&gbar, phase, gate::kGWaitLimit);   // product still in flight
                 break;
             }
             if (t < 128 && r < K) s_drop[s_list[r]] = gate::keep_prob(z) >= p_star ? 0 : 1;
         }
-        if (!gated) {
-            if (t == 0) atomicExch(&counts->timeout, 1u);
-            tc::mbar_wait(&gbar, phase, gate::kGWaitLimit);   // the product still in flight
-        }
         tc::fence_before_sync();
+        __syncthreads();                              // s_drop complete; TMEM reads done
+        tc::fence_after_sync();
+        uint32_t mine = 0;
+#pragma unroll
+        for (int it = 0; it < kSelItems; ++it) {
+            const int l = it * kSelThreads + t;
+            const bool keep = wv[it] > 0.0f && !(gated && s_drop[l]);
+            if (l < n_here) wsel[base + l] = keep ? wv[it] : 0.0f;
+            mine += __popc(__ballot_sync(0xffffffffu, keep));
+        }
+        if (lane_id() == 0) s_wc[t >> 5] = mine;
+        // a gate that stopped early: the staged arrays are free only now
+        if (!issued && t == 0 && prefetch) sg_issue_tile(a, next, s_pos, s_dl, s_lvl, &mbar);
         __syncthreads();
-        if ((t >> 5) == 0) tc::tmem_dealloc(tbase, gate::kGTmemCols);
-    } else if (!tc::mbar_wait(&wbar, 0, gate::kGWaitLimit)) {   // let the image copy land
-        if (t == 0) atomicExch(&counts->timeout, 1u);
-        tc::mbar_wait(&wbar, 0, gate::kGWaitLimit);
-    }
-    uint32_t mine = 0;
+        if (t == 0) {
+            uint32_t tot = 0;
 #pragma unroll
-    for (int it = 0; it < kSelItems; ++it) {
-        const int l = it * kSelThreads + t;
-        const bool keep = wv[it] > 0.0f && !(gated && s_drop[l]);
-        if (l < n_here) wsel[base + l] = keep ? wv[it] : 0.0f;
-        mine += __popc(__ballot_sync(0xffffffffu, keep));
+            for (int i = 0; i < kSelWarps; ++i) tot += s_wc[i];
+            tile_count[tile] = tot;
+        }
     }
-    if (lane_id() == 0) s_wc[t >> 5] = mine;
+    tc::fence_before_sync();
     __syncthreads();
-    if (t == 0) {
-        uint32_t tot = 0;
-#pragma unroll
-        for (int i = 0; i < kSelWarps; ++i) tot += s_wc[i];
-        tile_count[blockIdx.x] = tot;
-    }
+    if ((t >> 5) == 0) tc::tmem_dealloc(tbase, gate::kGTmemCols);
 }
 
 // Pass 2 (one CTA): exclusive scan of the tile counts in place; M and the overflow state.
@@ -427,8 +451,9 @@ extern "C" ogs_status ogs_lod_select_gated(const float* pos, const uint8_t* leve
                              kSgSmem) != cudaSuccess)
         return OGS_ERR_CUDA;
     const int bulk = aligned(pos, 16) && aligned(dL, 16) && aligned(level, 16);
-    select_eval_gated<<<nb, kSelThreads, kSgSmem, st>>>(a, feat, img, p_star, wsel, tile_count,
-                                                        counts, bulk);
+    const int grid = nb < 3 * kSmCount ? nb : 3 * kSmCount;
+    select_eval_gated<<<grid, kSelThreads, kSgSmem, st>>>(a, feat, img, p_star, wsel, tile_count,
+                                                          counts, bulk);
     select_scan<<<1, 1024, 0, st>>>(tile_count, nb, sel_cap, k, counts);
     select_scatter<<<nb, kSelThreads, 0, st>>>(wsel, tile_count, N, sel_idx, sel_w, sel_cap);
     return launch_status();
