@@ -34,10 +34,26 @@ __device__ __forceinline__ void gput8(unsigned char* base, int row, int kc, int 
         *reinterpret_cast<const uint4*>(h);
 }
 
+// Inputs 32..39 of an anchor's vector: L / (NL - 1), the unit viewing direction in the camera
+// frame, ln(d / d_max), zeros.  Every operation is an explicit round-to-nearest intrinsic, so
+// each kernel that inlines this computes the same bits.
+__device__ __forceinline__ void prop_extras(float p0, float p1, float p2, uint32_t level, int NL,
+                                            const Cam& c, float (&e)[8]) {
+    const float dx = __fsub_rn(p0, c.c[0]), dy = __fsub_rn(p1, c.c[1]), dz = __fsub_rn(p2, c.c[2]);
+    const float d = __fsqrt_rn(__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))));
+    e[0] = __fdiv_rn((float)level, (float)max(NL - 1, 1));
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+        e[1 + r] = __fdiv_rn(__fmaf_rn(c.R[3 * r + 2], dz,
+                                       __fmaf_rn(c.R[3 * r + 1], dy, __fmul_rn(c.R[3 * r], dx))),
+                             d);
+    e[4] = logf(__fdiv_rn(d, c.d_max));
+    e[5] = e[6] = e[7] = 0.f;
+}
+
 // Input vector of an anchor: [f_v, L / (NL - 1), unit viewing direction in the camera frame,
 // ln(d / d_max)], padded with zeros to 40.  feat: the anchor's 32 features (16-byte aligned);
-// p: its position.  Every operation is an explicit round-to-nearest intrinsic, so each kernel
-// that inlines this computes the same bits.
+// p: its position.
 __device__ __forceinline__ void prop_input_vals(const float* __restrict__ feat, float p0,
                                                 float p1, float p2, uint32_t level, int NL,
                                                 const Cam& c, float (&x)[kPInPad]) {
@@ -47,17 +63,10 @@ __device__ __forceinline__ void prop_input_vals(const float* __restrict__ feat, 
         const float4 v = f4[i];
         x[4 * i] = v.x; x[4 * i + 1] = v.y; x[4 * i + 2] = v.z; x[4 * i + 3] = v.w;
     }
-    const float dx = __fsub_rn(p0, c.c[0]), dy = __fsub_rn(p1, c.c[1]), dz = __fsub_rn(p2, c.c[2]);
-    const float d = __fsqrt_rn(__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))));
-    x[32] = __fdiv_rn((float)level, (float)max(NL - 1, 1));
-    // viewing direction in the camera frame
+    float e[8];
+    prop_extras(p0, p1, p2, level, NL, c, e);
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
-        x[33 + r] = __fdiv_rn(__fmaf_rn(c.R[3 * r + 2], dz,
-                                        __fmaf_rn(c.R[3 * r + 1], dy, __fmul_rn(c.R[3 * r], dx))),
-                              d);
-    x[36] = logf(__fdiv_rn(d, c.d_max));
-    x[37] = x[38] = x[39] = 0.f;
+    for (int i = 0; i < 8; ++i) x[32 + i] = e[i];
 }
 
 // Writes row `row` of the layer-1 A operand (K = 48) from an input vector (inputs 40..47 zero).
@@ -70,6 +79,37 @@ __device__ __forceinline__ void put_input_row(unsigned char* sA, int row, const 
     }
     const float z8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     gput8(sA, row, kGK1 / 8 - 1, kGK1, z8);
+}
+
+// Half `half` (0 or 1) of row `row` of the layer-1 A operand, written by one of two threads:
+// half 0 writes features 0..15 and inputs 32..39 (extras), half 1 features 16..31 and the zero
+// inputs 40..47.  feat: the anchor's features, or null for an empty row.  The same bits as
+// put_input_row of the full vector.
+__device__ __forceinline__ void put_input_half(unsigned char* sA, int row, int half,
+                                               const float* __restrict__ feat, float p0,
+                                               float p1, float p2, uint32_t level, int NL,
+                                               const Cam& c) {
+    float v0[8], v1[8], e[8];
+    if (feat) {
+        const float4* f4 = reinterpret_cast<const float4*>(feat) + 4 * half;
+        const float4 u0 = f4[0], u1 = f4[1], u2 = f4[2], u3 = f4[3];
+        v0[0] = u0.x; v0[1] = u0.y; v0[2] = u0.z; v0[3] = u0.w;
+        v0[4] = u1.x; v0[5] = u1.y; v0[6] = u1.z; v0[7] = u1.w;
+        v1[0] = u2.x; v1[1] = u2.y; v1[2] = u2.z; v1[3] = u2.w;
+        v1[4] = u3.x; v1[5] = u3.y; v1[6] = u3.z; v1[7] = u3.w;
+        if (half == 0) {
+            prop_extras(p0, p1, p2, level, NL, c, e);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) e[i] = 0.f;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v0[i] = v1[i] = e[i] = 0.f;
+    }
+    gput8(sA, row, 2 * half, kGK1, v0);
+    gput8(sA, row, 2 * half + 1, kGK1, v1);
+    gput8(sA, row, half == 0 ? kPInPad / 8 - 1 : kGK1 / 8 - 1, kGK1, e);
 }
 
 // Both hidden layers of the network for the 128 rows of the layer-1 operand in sA (written by

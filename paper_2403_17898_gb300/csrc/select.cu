@@ -218,19 +218,16 @@ __global__ void __launch_bounds__(kSelThreads, 3) select_eval_gated(
         }
         bool gated = mma_ok;
         for (uint32_t c0 = 0; gated && c0 < K; c0 += 128) {
-            const uint32_t r = c0 + (uint32_t)t;
-            if (t < 128) {
-                float x[gate::kPInPad];
-                if (r < K) {
-                    const int l = s_list[r];
-                    gate::prop_input_vals(feat + (size_t)(base + l) * 32, s_pos[3 * l],
-                                          s_pos[3 * l + 1], s_pos[3 * l + 2], s_lvl[l], a.NL,
-                                          a.cam, x);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < gate::kPInPad; ++i) x[i] = 0.f;
-                }
-                gate::put_input_row(sA, t, x);
+            // gate inputs: two threads per row (t and t + 128)
+            const uint32_t r = c0 + (uint32_t)(t & 127);
+            if (r < K) {
+                const int l = s_list[r];
+                gate::put_input_half(sA, t & 127, t >> 7, feat + (size_t)(base + l) * 32,
+                                     s_pos[3 * l], s_pos[3 * l + 1], s_pos[3 * l + 2], s_lvl[l],
+                                     a.NL, a.cam);
+            } else {
+                gate::put_input_half(sA, t & 127, t >> 7, nullptr, 0.f, 0.f, 0.f, 0u, a.NL,
+                                     a.cam);
             }
             if (c0 + 128 >= K) {                      // last chunk: staged arrays now free
                 __syncthreads();
