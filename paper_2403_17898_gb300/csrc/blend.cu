@@ -53,6 +53,8 @@ __global__ void __launch_bounds__(kThreads) blend_fwd_kernel(
     float* __restrict__ img, float* __restrict__ T_final, uint32_t* __restrict__ n_last,
     uint32_t* __restrict__ n_eval, const uint32_t* __restrict__ sel_idx, int k,
     uint32_t* __restrict__ maxc) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ float4 s_a[kBatch];
     __shared__ float4 s_b[kBatch];
     __shared__ float2 s_c[kBatch];
@@ -154,19 +156,19 @@ extern "C" ogs_status ogs_blend_fwd(const ogs_rec2d* rec, const uint32_t* pair_g
     const uint2* tr = reinterpret_cast<const uint2*>(tile_range);
     const dim3 grid(gx * gy);
     if (maxc && n_eval)
-        blend_fwd_kernel<true, true><<<grid, blend::kThreads, 0, st>>>(
+        launch_pdl(blend_fwd_kernel<true, true>, dim3(grid), dim3(blend::kThreads), 0, st,
             r, pair_gauss, tr, width, height, gx, bg[0], bg[1], bg[2], img, T_final, n_last,
             n_eval, sel_idx, k, maxc);
     else if (maxc)
-        blend_fwd_kernel<true, false><<<grid, blend::kThreads, 0, st>>>(
+        launch_pdl(blend_fwd_kernel<true, false>, dim3(grid), dim3(blend::kThreads), 0, st,
             r, pair_gauss, tr, width, height, gx, bg[0], bg[1], bg[2], img, T_final, n_last,
             nullptr, sel_idx, k, maxc);
     else if (n_eval)
-        blend_fwd_kernel<false, true><<<grid, blend::kThreads, 0, st>>>(
+        launch_pdl(blend_fwd_kernel<false, true>, dim3(grid), dim3(blend::kThreads), 0, st,
             r, pair_gauss, tr, width, height, gx, bg[0], bg[1], bg[2], img, T_final, n_last,
             n_eval, nullptr, 1, nullptr);
     else
-        blend_fwd_kernel<false, false><<<grid, blend::kThreads, 0, st>>>(
+        launch_pdl(blend_fwd_kernel<false, false>, dim3(grid), dim3(blend::kThreads), 0, st,
             r, pair_gauss, tr, width, height, gx, bg[0], bg[1], bg[2], img, T_final, n_last,
             nullptr, nullptr, 1, nullptr);
     return launch_status();

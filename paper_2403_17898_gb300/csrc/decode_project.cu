@@ -78,6 +78,8 @@ struct DpArgs {
 // per thread; the others zero the n_tc per-tile counts.
 __global__ void __launch_bounds__(kPackThreads) dp_pack(ogs_mlp m, unsigned char* img,
                                                         uint32_t* tile_count, int n_tc) {
+    pdl_wait();
+    pdl_trigger();
     if (blockIdx.x < kPackCtas) {
         const int e = blockIdx.x * kPackThreads + threadIdx.x;
         float v[8];
@@ -108,6 +110,8 @@ __global__ void __launch_bounds__(kPackThreads) dp_pack(ogs_mlp m, unsigned char
 }
 
 __global__ void __launch_bounds__(kDpThreads, 3) decode_project_tc(DpArgs a) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ __align__(8) uint64_t wbar;
@@ -357,8 +361,8 @@ extern "C" ogs_status ogs_decode_project_bf16(
     cudaStream_t st = (cudaStream_t)stream;
     const int n_tc = tile_count ? cm.gx * cm.gy : 0;
     unsigned char* img = (unsigned char*)scratch;
-    dp_pack<<<kPackCtas + (n_tc + 4 * kPackThreads - 1) / (4 * kPackThreads), kPackThreads, 0,
-              st>>>(*mlp, img, tile_count, n_tc);
+    const int pack_grid = kPackCtas + (n_tc + 4 * kPackThreads - 1) / (4 * kPackThreads);
+    launch_pdl(dp_pack, dim3(pack_grid), dim3(kPackThreads), 0, st, *mlp, img, tile_count, n_tc);
     if (sel_cap == 0) return launch_status();
     if (cudaFuncSetAttribute(decode_project_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kDpSmem) != cudaSuccess)
@@ -369,6 +373,6 @@ extern "C" ogs_status ogs_decode_project_bf16(
              reinterpret_cast<uint2*>(rect), tiles, tile_count, img, cm};
     const int64_t tiles_cap = (sel_cap + kTM - 1) / kTM;
     const int grid = (int)(tiles_cap < 3 * kSmCount ? tiles_cap : 3 * kSmCount);
-    decode_project_tc<<<grid, kDpThreads, kDpSmem, st>>>(a);
+    launch_pdl(decode_project_tc, dim3(grid), dim3(kDpThreads), kDpSmem, st, a);
     return launch_status();
 }

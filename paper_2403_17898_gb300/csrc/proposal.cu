@@ -159,6 +159,8 @@ constexpr int kGPackCtas = (kGPackItems + kGPackThreads - 1) / kGPackThreads;
 __global__ void __launch_bounds__(kGPackThreads) gate_pack(ogs_proposal net, unsigned char* img,
                                                            unsigned long long* status,
                                                            int n_words) {
+    pdl_wait();
+    pdl_trigger();
     if (blockIdx.x < kGPackCtas) {
         const int e = blockIdx.x * kGPackThreads + threadIdx.x;
         float v[8];
@@ -539,7 +541,8 @@ using namespace ogs;
 ogs_status ogs::gate::pack_image(const ogs_proposal& net, unsigned char* img,
                                  unsigned long long* status, int n_words, cudaStream_t st) {
     const int nz = n_words > 0 ? (n_words + 1023) / 1024 : 0;
-    gate_pack<<<kGPackCtas + nz, kGPackThreads, 0, st>>>(net, img, status, n_words);
+    launch_pdl(gate_pack, dim3(kGPackCtas + nz), dim3(kGPackThreads), 0, st,
+               net, img, status, n_words);
     return launch_status();
 }
 

@@ -64,6 +64,8 @@ __device__ __forceinline__ bool keep_anchor(const SelArgs& a, float px, float py
 __global__ void __launch_bounds__(kSelThreads) select_eval(SelArgs a, float* __restrict__ wsel,
                                                            uint32_t* __restrict__ tile_count,
                                                            ogs_counts* counts, int bulk) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ __align__(16) float s_pos[3 * kSelChunk];
     __shared__ __align__(16) float s_dl[kSelChunk];
     __shared__ __align__(16) uint8_t s_lvl[kSelChunk];
@@ -137,6 +139,8 @@ __global__ void __launch_bounds__(kSelThreads, 3) select_eval_gated(
     SelArgs a, const float* __restrict__ feat, const unsigned char* __restrict__ img,
     float p_star, float* __restrict__ wsel, uint32_t* __restrict__ tile_count,
     ogs_counts* counts, int bulk) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(16) float s_pos[3 * kSelChunk];
     __shared__ __align__(16) float s_dl[kSelChunk];
@@ -273,6 +277,8 @@ __global__ void __launch_bounds__(kSelThreads, 3) select_eval_gated(
 // Pass 2 (one CTA): exclusive scan of the tile counts in place; M and the overflow state.
 __global__ void __launch_bounds__(1024) select_scan(uint32_t* __restrict__ tile_count, int nb,
                                                     int64_t cap, int k, ogs_counts* counts) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ unsigned long long ws[32];
     const int per = (nb + 1023) / 1024;
     const int b0 = threadIdx.x * per, b1 = min(b0 + per, nb);
@@ -317,6 +323,8 @@ __global__ void __launch_bounds__(kSelThreads) select_scatter(const float* __res
                                                               const uint32_t* __restrict__ tile_off,
                                                               int64_t N, uint32_t* sel_idx,
                                                               float* sel_w, int64_t cap) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t s_cnt[kSelItems / 4][kSelWarps];
     const int64_t base = (int64_t)blockIdx.x * kSelChunk;
     const int n_here = (int)min((int64_t)kSelChunk, N - base);
@@ -407,9 +415,10 @@ extern "C" ogs_status ogs_lod_select(const float* pos, const uint8_t* level, con
     uint32_t* tile_count = cv.take<uint32_t>((size_t)nb);
     float* wsel = cv.take<float>((size_t)(N > 0 ? N : 1));
     const int bulk = aligned(pos, 16) && aligned(dL, 16) && aligned(level, 16);
-    select_eval<<<nb, kSelThreads, 0, st>>>(a, wsel, tile_count, counts, bulk);
-    select_scan<<<1, 1024, 0, st>>>(tile_count, nb, sel_cap, k, counts);
-    select_scatter<<<nb, kSelThreads, 0, st>>>(wsel, tile_count, N, sel_idx, sel_w, sel_cap);
+    launch_pdl(select_eval, dim3(nb), dim3(kSelThreads), 0, st, a, wsel, tile_count, counts, bulk);
+    launch_pdl(select_scan, dim3(1), dim3(1024), 0, st, tile_count, nb, sel_cap, k, counts);
+    launch_pdl(select_scatter, dim3(nb), dim3(kSelThreads), 0, st,
+               wsel, tile_count, N, sel_idx, sel_w, sel_cap);
     return launch_status();
 }
 
@@ -449,10 +458,11 @@ extern "C" ogs_status ogs_lod_select_gated(const float* pos, const uint8_t* leve
         return OGS_ERR_CUDA;
     const int bulk = aligned(pos, 16) && aligned(dL, 16) && aligned(level, 16);
     const int grid = nb < 3 * kSmCount ? nb : 3 * kSmCount;
-    select_eval_gated<<<grid, kSelThreads, kSgSmem, st>>>(a, feat, img, p_star, wsel, tile_count,
-                                                          counts, bulk);
-    select_scan<<<1, 1024, 0, st>>>(tile_count, nb, sel_cap, k, counts);
-    select_scatter<<<nb, kSelThreads, 0, st>>>(wsel, tile_count, N, sel_idx, sel_w, sel_cap);
+    launch_pdl(select_eval_gated, dim3(grid), dim3(kSelThreads), kSgSmem, st,
+               a, feat, img, p_star, wsel, tile_count, counts, bulk);
+    launch_pdl(select_scan, dim3(1), dim3(1024), 0, st, tile_count, nb, sel_cap, k, counts);
+    launch_pdl(select_scatter, dim3(nb), dim3(kSelThreads), 0, st,
+               wsel, tile_count, N, sel_idx, sel_w, sel_cap);
     return launch_status();
 }
 

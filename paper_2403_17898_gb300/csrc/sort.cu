@@ -350,6 +350,8 @@ __global__ void __launch_bounds__(1024) tile_scan(const uint32_t* __restrict__ t
                                                   uint32_t* __restrict__ big,
                                                   uint32_t* __restrict__ nbig,
                                                   ogs_counts* counts) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ unsigned long long ws[32];
     __shared__ uint32_t s_nbig;
     __shared__ uint32_t s_cnt[kScanSmemTiles];
@@ -434,6 +436,8 @@ __global__ void __launch_bounds__(kBinThreads) bin_fill(const uint32_t* __restri
                                                         const ogs_counts* counts,
                                                         uint32_t* __restrict__ keys,
                                                         uint32_t* __restrict__ ids) {
+    pdl_wait();
+    pdl_trigger();
     if (counts->overflow & 2u) return;
     const uint32_t n = count_of(n_dev, n_cap);
     if ((int64_t)blockIdx.x * kBinTile >= n) return;
@@ -575,6 +579,8 @@ __global__ void __launch_bounds__(kSmallThreads, 10) tile_sort_small(const uint2
                                                                  const ogs_counts* counts,
                                                                  uint32_t* __restrict__ keys,
                                                                  uint32_t* __restrict__ ids) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ unsigned long long s_k[kSmallSort];
     if (counts->overflow & 2u) return;
     const uint2 r = range[blockIdx.x];
@@ -590,6 +596,8 @@ __global__ void __launch_bounds__(kLargeThreads) tile_sort_large(const uint2* __
                                                                  const ogs_counts* counts,
                                                                  uint32_t* __restrict__ keys,
                                                                  uint32_t* __restrict__ ids) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ unsigned long long s_k[];
     if (counts->overflow & 2u) return;
     const uint32_t n = *nbig;
@@ -689,17 +697,18 @@ extern "C" ogs_status ogs_sort(const uint32_t* depth_key, const uint32_t* rect, 
     if (nb < 1) nb = 1;
     const uint2* rc = reinterpret_cast<const uint2*>(rect);
     if (!tile_count) bin_count<<<nb, kBinThreads, 0, st>>>(tiles, rc, n_dev, n_cap, grid_x, s.tcount);
-    tile_scan<<<1, 1024, 0, st>>>(tile_count ? tile_count : s.tcount, n_tiles, pair_cap, range,
-                                  s.cursor, s.big, s.nbig, counts);
-    bin_fill<<<nb, kBinThreads, 0, st>>>(tiles, rc, depth_key, n_dev, n_cap, grid_x, range,
-                                         s.cursor, counts, s.keys, pair_gauss);
-    tile_sort_small<<<n_tiles, kSmallThreads, 0, st>>>(range, counts, s.keys, pair_gauss);
+    launch_pdl(tile_scan, dim3(1), dim3(1024), 0, st, tile_count ? tile_count : s.tcount,
+               n_tiles, pair_cap, range, s.cursor, s.big, s.nbig, counts);
+    launch_pdl(bin_fill, dim3(nb), dim3(kBinThreads), 0, st, tiles, rc, depth_key, n_dev, n_cap,
+               grid_x, range, s.cursor, counts, s.keys, pair_gauss);
+    launch_pdl(tile_sort_small, dim3(n_tiles), dim3(kSmallThreads), 0, st,
+               range, counts, s.keys, pair_gauss);
     const size_t smem = sizeof(unsigned long long) * kLargeSort;
     if (cudaFuncSetAttribute(tile_sort_large, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return OGS_ERR_CUDA;
-    tile_sort_large<<<kLargeGrid, kLargeThreads, smem, st>>>(range, s.big, s.nbig, counts, s.keys,
-                                                             pair_gauss);
+    launch_pdl(tile_sort_large, dim3(kLargeGrid), dim3(kLargeThreads), smem, st, range, s.big,
+               s.nbig, counts, s.keys, pair_gauss);
     return launch_status();
 }
 
