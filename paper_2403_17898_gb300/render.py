@@ -131,7 +131,7 @@ class Renderer:
 
     # -- one view --------------------------------------------------------------------------
     def enqueue(self, cam, infer=True, bg=(0.0, 0.0, 0.0), maxc=None, stream=None, timers=None,
-                n_eval=None, gate=None):
+                n_eval=None, gate=None, img=None):
         """Enqueues the whole forward pass of one view (no host synchronisation).  If
         ``timers`` is a dict, a CUDA event pair is recorded around every stage under its name
         (on the launching stream).  ``gate = (proposal_weights, p_star)`` inserts the learned
@@ -189,7 +189,8 @@ class Renderer:
             self.pair_gauss, self.tile_range, self.pair_cap, self.counts_t, self.sort_scratch,
             st, tile_count=self.tile_count))
         stage("blend_fwd", lambda: abi.blend_fwd(
-            self.rec, self.pair_gauss, self.tile_range, self.W, self.H, bg, self.img, self.T,
+            self.rec, self.pair_gauss, self.tile_range, self.W, self.H, bg,
+            self.img if img is None else img, self.T,
             self.n_last, sel, self.k, maxc, n_eval, st))
 
     def counts(self) -> FrameCounts:
@@ -203,6 +204,45 @@ class Renderer:
         host_img.copy_(self.img, non_blocking=True)
         torch.cuda.current_stream().synchronize()
         return host_img
+
+    def render_sequence_to_host(self, cams, host_imgs, bg=(0.0, 0.0, 0.0), gate=None,
+                                on_frame=None):
+        """End-to-end rendering of a sequence of views into pinned host memory, pipelined: the
+        image of view i is copied to the host on a copy stream while view i + 1 renders.
+        ``host_imgs``: two pinned float32 [3, H, W] CPU tensors used in turn; view i lands in
+        ``host_imgs[i % 2]``, and ``on_frame(i, host_img)`` (if given) is called once it is
+        there (before that buffer is reused two views later).  Returns when every image is on
+        the host."""
+        if not hasattr(self, "_seq_img"):
+            self._seq_img = torch.empty_like(self.img)
+            self._copy_stream = torch.cuda.Stream()
+        dev_imgs = (self.img, self._seq_img)
+        comp = torch.cuda.current_stream()
+        ready = [torch.cuda.Event(), torch.cuda.Event()]
+        copied = [None, None]
+        for i, cam in enumerate(cams):
+            b = i % 2
+            if copied[b] is not None:
+                # the buffer pair's previous image: its copy must be done before the blend
+                # overwrites the device image and before the host buffer is handed out again
+                comp.wait_event(copied[b])
+                copied[b].synchronize()
+                if on_frame is not None:
+                    on_frame(i - 2, host_imgs[b])
+            self.enqueue(cam, True, bg, gate=gate, img=dev_imgs[b])
+            ready[b].record(comp)
+            self._copy_stream.wait_event(ready[b])
+            with torch.cuda.stream(self._copy_stream):
+                host_imgs[b].copy_(dev_imgs[b], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(self._copy_stream)
+            copied[b] = ev
+        for j in range(max(len(cams) - 2, 0), len(cams)):
+            b = j % 2
+            copied[b].synchronize()
+            if on_frame is not None:
+                on_frame(j, host_imgs[b])
+        return host_imgs
 
     def render(self, cam, infer=True, bg=(0.0, 0.0, 0.0), maxc=None, check=True, gate=None):
         """Renders one view; with ``check`` it synchronises, grows overflowing buffers and
