@@ -55,7 +55,7 @@ def _declare(L):
     L.orc_decode.restype = None
     L.orc_decode.argtypes = [C.c_long, _P, _P, _P, _P, C.c_int, _P, _P, C.c_int,
                              _P, _P, C.c_int, _P, _P, _P, _P, _P, _P, _P,
-                             _P, _P, _P, _P, _P, _P]
+                             _P, _P, _P, _P, _P, _P, _P, C.c_int, _P]
     L.orc_project.restype = None
     L.orc_project.argtypes = [C.c_long] + [_P] * 12
     L.orc_tile_lists.restype = C.c_long
@@ -69,7 +69,7 @@ def _declare(L):
     L.orc_decode_bwd.restype = None
     L.orc_decode_bwd.argtypes = ([C.c_long, _P, _P, _P, _P, C.c_int, _P, _P, C.c_int,
                                   _P, _P, C.c_int, _P, _P, _P, _P, _P, _P, _P]
-                                 + [_P] * 16)
+                                 + [_P] * 16 + [_P, C.c_int, _P, _P, _P])
 
 
 def _d(a):
@@ -111,10 +111,22 @@ def lod_select(pos, level, dL, NL, cam, infer):
     return idx[:M].copy(), w[:M].copy(), margin
 
 
+def _appearance(scene, mlp):
+    """Per-anchor appearance codes and the colour decoder's weights for them (Sec. 4.4), as
+    (codes f64[N][A] or None, A, weights f64[H][A] or None)."""
+    app = getattr(scene, "app", None)
+    if app is None:
+        return None, 0, None
+    return _d(app), int(app.shape[1]), _d(mlp.w1_app)
+
+
 def decode(sel_idx, sel_w, scene, mlp, cam):
     """Sec. 3.2 (Eq. offsets, Eq. mlp).  Gaussian g = rank*k + i.  Pinned by closed forms with
     zeroed second layers, the affine collapse when every hidden unit is active, and position
-    offsets (tests/test_oracle_decode)."""
+    offsets (tests/test_oracle_decode).  With appearance codes (Sec. 4.4: a learnable code per
+    anchor fed to the colour MLP as an additional input), the colour decoder's first layer also
+    sees the anchor's code; pinned by its equality with a decoder whose features are extended
+    by the code (tests/test_oracle_appearance)."""
     sel_idx = np.ascontiguousarray(sel_idx, np.int64)
     sel_w = _d(sel_w)
     M = sel_idx.shape[0]
@@ -130,8 +142,13 @@ def decode(sel_idx, sel_w, scene, mlp, cam):
                      _p(ws[2]), _p(ws[3]), _p(ws[4]), _p(ws[5]), _p(ws[6]), _p(ws[7]),
                      _p(cam_array(cam)), _p(out["means"]), _p(out["scales"]),
                      _p(out["quats"]), _p(out["opac"]), _p(out["colors"]),
-                     _p(out["op_margin"]))
+                     _p(out["op_margin"]), *_app_args(scene, mlp))
     return out
+
+
+def _app_args(scene, mlp):
+    app, A, w = _appearance(scene, mlp)
+    return (_p(app) if app is not None else None, A, _p(w) if w is not None else None)
 
 
 def project(means, scales, quats, opac, cam):
@@ -229,13 +246,19 @@ def decode_bwd(sel_idx, sel_w, scene, mlp, cam, g):
     names = ["dw1", "db1", "dw2_op", "db2_op", "dw2_col", "db2_col", "dw2_cov", "db2_cov"]
     for n, a in zip(names, mlp.arrays()):
         o[n] = np.zeros(a.shape)
+    app, A, w1app = _appearance(scene, mlp)
+    if A:
+        o["dapp"] = np.zeros((N, A))
+        o["dw1_app"] = np.zeros(w1app.shape)
     lib().orc_decode_bwd(M, _p(sel_idx), _p(sel_w), _p(_d(scene.pos)), _p(_d(scene.feat)), F,
                          _p(_d(scene.offs)), _p(_d(scene.lv)), k, _p(ws[0]), _p(ws[1]), Hd,
                          _p(ws[2]), _p(ws[3]), _p(ws[4]), _p(ws[5]), _p(ws[6]), _p(ws[7]),
                          _p(cam_array(cam)), _p(_d(g["dmeans"])), _p(_d(g["dscales"])),
                          _p(_d(g["dquats"])), _p(_d(g["dopac"])), _p(_d(g["dcolors"])),
                          _p(o["dfeat"]), _p(o["doffs"]), _p(o["dlv"]),
-                         *[_p(o[n]) for n in names])
+                         *[_p(o[n]) for n in names],
+                         _p(app) if A else None, A, _p(w1app) if A else None,
+                         _p(o["dapp"]) if A else None, _p(o["dw1_app"]) if A else None)
     return o
 
 

@@ -130,16 +130,23 @@ long orc_lod_select(long N, const double* pos, const int32_t* level, const doubl
 typedef struct {
     const double *w1, *b1, *w2op, *b2op, *w2col, *b2col, *w2cov, *b2cov;
     int F, Hd, k;
+    const double* w1app;   /* colour decoder's weights of the appearance code [Hd][A], or NULL */
+    int A;                 /* appearance code width (0: none) */
 } mlp_t;
 
-/* z = [f_v, dir, dist]; hidden[m][h] = relu(W1[m] z + b1[m]); pre-activation kept too. */
-static void mlp_hidden(const mlp_t* W, const double* z, double* hid, double* pre) {
+/* z = [f_v, dir, dist]; hidden[m][h] = relu(W1[m] z + b1[m]); pre-activation kept too.  The
+ * colour decoder (m = 1) also sees the anchor's appearance code a (Sec. 4.4):
+ * + W1app[h] . a. */
+static void mlp_hidden(const mlp_t* W, const double* z, const double* app, double* hid,
+                       double* pre) {
     int Din = W->F + 4;
     for (int m = 0; m < 3; ++m)
         for (int h = 0; h < W->Hd; ++h) {
             const double* row = W->w1 + ((long)m * W->Hd + h) * Din;
             double a = W->b1[m * W->Hd + h];
             for (int i = 0; i < Din; ++i) a += row[i] * z[i];
+            if (m == 1 && W->A > 0)
+                for (int c = 0; c < W->A; ++c) a += W->w1app[(long)h * W->A + c] * app[c];
             pre[m * W->Hd + h] = a;
             hid[m * W->Hd + h] = a > 0 ? a : 0;
         }
@@ -171,16 +178,16 @@ void orc_decode(long M, const int64_t* sel_idx, const double* sel_w, const doubl
                 const double* b2op, const double* w2col, const double* b2col,
                 const double* w2cov, const double* b2cov, const double* camp, double* means,
                 double* scales, double* quats, double* opac, double* colors,
-                double* op_margin) {
+                double* op_margin, const double* app, int A, const double* w1app) {
     cam_t cam = read_cam(camp);
-    mlp_t W = {w1, b1, w2op, b2op, w2col, b2col, w2cov, b2cov, F, Hd, k};
+    mlp_t W = {w1, b1, w2op, b2op, w2col, b2col, w2cov, b2cov, F, Hd, k, w1app, A};
     double* z = malloc(sizeof(double) * (F + 4));
     double* hid = malloc(sizeof(double) * 3 * Hd);
     double* pre = malloc(sizeof(double) * 3 * Hd);
     for (long r = 0; r < M; ++r) {
         long j = sel_idx[r];
         anchor_input(&cam, pos + 3 * j, feat + (long)j * F, F, z);
-        mlp_hidden(&W, z, hid, pre);
+        mlp_hidden(&W, z, A > 0 ? app + (long)j * A : NULL, hid, pre);
         const double* hop = hid;
         const double* hcol = hid + Hd;
         const double* hcov = hid + 2 * Hd;
@@ -662,9 +669,11 @@ void orc_decode_bwd(long M, const int64_t* sel_idx, const double* sel_w, const d
                     const double* dmeans, const double* dscales, const double* dquats,
                     const double* dopac, const double* dcolors, double* dfeat, double* doffs,
                     double* dlv, double* dw1, double* db1, double* dw2op, double* db2op,
-                    double* dw2col, double* db2col, double* dw2cov, double* db2cov) {
+                    double* dw2col, double* db2col, double* dw2cov, double* db2cov,
+                    const double* app, int A, const double* w1app, double* dapp,
+                    double* dw1app) {
     cam_t cam = read_cam(camp);
-    mlp_t W = {w1, b1, w2op, b2op, w2col, b2col, w2cov, b2cov, F, Hd, k};
+    mlp_t W = {w1, b1, w2op, b2op, w2col, b2col, w2cov, b2cov, F, Hd, k, w1app, A};
     int Din = F + 4;
     double* z = malloc(sizeof(double) * Din);
     double* hid = malloc(sizeof(double) * 3 * Hd);
@@ -672,8 +681,9 @@ void orc_decode_bwd(long M, const int64_t* sel_idx, const double* sel_w, const d
     double* dhid = malloc(sizeof(double) * 3 * Hd);
     for (long r = 0; r < M; ++r) {
         long j = sel_idx[r];
+        const double* aj = A > 0 ? app + (long)j * A : NULL;
         anchor_input(&cam, pos + 3 * j, feat + (long)j * F, F, z);
-        mlp_hidden(&W, z, hid, pre);
+        mlp_hidden(&W, z, aj, hid, pre);
         for (int h = 0; h < 3 * Hd; ++h) dhid[h] = 0;
         const double* l = lv + 3 * j;
         for (int i = 0; i < k; ++i) {
@@ -750,6 +760,11 @@ void orc_decode_bwd(long M, const int64_t* sel_idx, const double* sel_w, const d
                 db1[idx] += dp;
                 for (int i = 0; i < Din; ++i) dw1[(long)idx * Din + i] += dp * z[i];
                 for (int i = 0; i < F; ++i) dfeat[(long)j * F + i] += dp * w1[(long)idx * Din + i];
+                if (m == 1 && A > 0)                  /* appearance code of the colour MLP */
+                    for (int c = 0; c < A; ++c) {
+                        dw1app[(long)h * A + c] += dp * aj[c];
+                        dapp[(long)j * A + c] += dp * w1app[(long)h * A + c];
+                    }
             }
     }
     free(z); free(hid); free(pre); free(dhid);

@@ -26,7 +26,7 @@ __all__ = [
     "cube_scene", "city_scene", "decoder_mlp", "proposal_mlp",
     "look_at_camera", "zoom_out_path", "trajectory_d_max", "proposal_poses",
     "random_gaussians", "random_records", "random_rects_depths", "random_sort_keys",
-    "explicit_attributes", "CONFIGS",
+    "explicit_attributes", "with_appearance", "APP_DIM", "CONFIGS",
 ]
 
 F_DIM = 32      # anchor feature width (all configs)
@@ -46,6 +46,7 @@ class Scene:
     NL: int                # number of levels
     k: int = K_GAUSS
     meta: dict = field(default_factory=dict)
+    app: np.ndarray = None  # f32[N,A] per-anchor appearance codes (Sec. 4.4), or None
 
     @property
     def N(self) -> int:
@@ -69,6 +70,7 @@ class DecoderMLP:
     b2_col: np.ndarray  # f32[3k]
     w2_cov: np.ndarray  # f32[7k, H]
     b2_cov: np.ndarray  # f32[7k]
+    w1_app: np.ndarray = None  # f32[H, A] colour decoder's weights of the appearance code
 
     def arrays(self):
         return [self.w1, self.b1, self.w2_op, self.b2_op, self.w2_col, self.b2_col,
@@ -528,6 +530,23 @@ CONFIGS = {
     "city2M_1080p_heldout60": _cfg3_heldout_poses,
     "city8M_1080p": _cfg5,
 }
+
+
+APP_DIM = 8   # appearance code width (Sec. 4.4 gives none; 8 fills the decoders' K padding)
+
+
+def with_appearance(scene, mlp, seed=0, A=APP_DIM, scale=0.5):
+    """Copies of (scene, mlp) with a seeded appearance code per anchor, N(0, scale), and the
+    colour decoder's first-layer weights for it, U(+-1/sqrt(F + 4 + A))."""
+    import copy
+    rng = np.random.default_rng(seed + 777)
+    sc = copy.copy(scene)
+    sc.app = rng.normal(0.0, scale, size=(scene.N, A)).astype(np.float32)
+    m = copy.copy(mlp)
+    H = mlp.w1.shape[1]
+    b = 1.0 / math.sqrt(mlp.w1.shape[2] + A)
+    m.w1_app = rng.uniform(-b, b, size=(H, A)).astype(np.float32)
+    return sc, m
 
 
 def explicit_attributes(scene, seed=0):
