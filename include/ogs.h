@@ -83,7 +83,12 @@ typedef struct ogs_counts {
  *   w2_op  f32[k][H],   b2_op  f32[k]    opacity_i  = w * tanh(.)   (dropped if <= 0)
  *   w2_col f32[3k][H],  b2_col f32[3k]   colour_i   = sigmoid(rows 3i..3i+2)
  *   w2_cov f32[7k][H],  b2_cov f32[7k]   scale_i    = l_v * sigmoid(rows 7i..7i+2),
- *                                        quat_i (w,x,y,z) = normalise(rows 7i+3..7i+6) */
+ *                                        quat_i (w,x,y,z) = normalise(rows 7i+3..7i+6)
+ * Appearance codes (Sec. 4.4, optional, A = 0 disables them): anchor j carries a learnable
+ * code a_j of A <= 8 values that only the colour decoder sees; its first layer adds
+ * w1_app a_j to the hidden pre-activations (w1_app f32[H][A], app f32[N][A]; no alignment
+ * requirement; A > 0 needs both).  When an ogs_mlp passes gradients (dmlp of ogs_decode_bwd),
+ * w1_app and app are the gradient arrays of the same shapes (ACCUMULATED: +=). */
 typedef struct ogs_mlp {
     const float* w1;
     const float* b1;
@@ -96,7 +101,9 @@ typedef struct ogs_mlp {
     int32_t F;          /* feature width (32) */
     int32_t H;          /* hidden width, must be 32 */
     int32_t k;          /* Gaussians per anchor (1..16) */
-    int32_t pad;
+    int32_t A;          /* appearance code width (0..8); 0: no codes, w1_app/app unused */
+    const float* w1_app;  /* f32[H][A] colour decoder's first-layer weights of the code */
+    const float* app;     /* f32[N][A] per-anchor appearance codes */
 } ogs_mlp;
 
 /* Neural-Gaussian structure of arrays (device, f32); Gaussian g = r*k + i belongs to the r-th
@@ -148,6 +155,7 @@ ogs_status ogs_lod_select(const float* pos, const uint8_t* level, const float* d
  *   pos f32[N][3], feat f32[N][F], offs f32[N][k][3], lv f32[N][3]   anchor SoA
  *   sel_idx/sel_w from ogs_lod_select; sel_cap = their capacity
  *   out: Gaussian SoA with room for sel_cap * k Gaussians (means camera-relative)
+ *   mlp->A > 0: the colour decoder also sees the anchor's appearance code (Sec. 4.4)
  * ------------------------------------------------------------------------------------- */
 ogs_status ogs_decode(const float* pos, const float* feat, const float* offs, const float* lv,
                       int64_t N, const ogs_mlp* mlp /* host struct of device ptrs */,
@@ -159,7 +167,8 @@ ogs_status ogs_decode(const float* pos, const float* feat, const float* offs, co
  * ogs_decode_bf16 — ogs_decode on the tensor cores: both decoder layers as BF16 x BF16 MMAs
  * with FP32 accumulation (tcgen05, accumulators in tensor memory); inputs and hidden
  * activations are rounded to BF16, everything after the GEMMs (biases, activations,
- * normalisation, positions) is FP32.  Same arguments, layout and outputs as ogs_decode.
+ * normalisation, positions) is FP32.  Same arguments, layout and outputs as ogs_decode;
+ * an appearance code enters layer 1 as BF16 K columns 40..47 (the input's zero padding).
  * counts is written only if a bounded internal wait expires (counts->timeout = 1, outputs
  * of the remaining anchors not written).
  * ------------------------------------------------------------------------------------- */
@@ -306,7 +315,9 @@ ogs_status ogs_project_bwd(const ogs_gaussians* g /* host struct */, int64_t n_g
  * anchor, recomputes the three decoders and chains the per-Gaussian gradients (dmeans,
  * dscales, dquats from ogs_project_bwd; opacity and colour gradients from drec) into
  *   dfeat f32[N][F], doffs f32[N][k][3], dlv f32[N][3]   (ACCUMULATED: +=)
- *   dmlp: decoder weight gradients, same layout as ogs_mlp  (ACCUMULATED: +=)
+ *   dmlp: decoder weight gradients, same layout as ogs_mlp  (ACCUMULATED: +=); with
+ *   appearance codes (mlp->A > 0) also dmlp->w1_app f32[H][A] and the code gradients
+ *   dmlp->app f32[N][A] (both +=, both required; dmlp->A is ignored)
  * Anchor positions, LOD bias and the selection are constants.  A row pass (thread per
  * anchor) writes each anchor's output, hidden and input rows to scratch; weight gradients are
  * summed per block over those rows and then across blocks in a fixed order (deterministic).
@@ -333,7 +344,8 @@ ogs_status ogs_decode_bwd(const float* pos, const float* feat, const float* offs
  * 2^-9 each); the output gradients dy, the ReLU masks, the weight-gradient products over the
  * anchors and every accumulation stay FP32.  The backward of ogs_decode_bf16.  Same
  * arguments, scratch and results as ogs_decode_bwd, except that counts is written: on a
- * tensor-core wait that does not complete, counts->timeout is set.
+ * tensor-core wait that does not complete, counts->timeout is set.  Decoders with appearance
+ * codes (mlp->A > 0) are rejected with OGS_ERR_ARG: their backward is ogs_decode_bwd.
  * ------------------------------------------------------------------------------------- */
 ogs_status ogs_decode_bwd_bf16(const float* pos, const float* feat, const float* offs,
                                const float* lv, int64_t N, const ogs_mlp* mlp /* host struct */,

@@ -41,7 +41,8 @@ COUNT_FIELDS = [f[0] for f in Counts._fields_]
 class MLP(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("w1", "b1", "w2_op", "b2_op", "w2_col", "b2_col",
                                           "w2_cov", "b2_cov")] + \
-               [("F", C.c_int32), ("H", C.c_int32), ("k", C.c_int32), ("pad", C.c_int32)]
+               [("F", C.c_int32), ("H", C.c_int32), ("k", C.c_int32), ("A", C.c_int32),
+                ("w1_app", C.c_void_p), ("app", C.c_void_p)]
 
 
 class Proposal(C.Structure):
@@ -186,12 +187,18 @@ def camera(cam) -> Camera:
     return c
 
 
-def mlp_struct(t, k=10, F=32, H=32) -> MLP:
-    """Decoder weights (dict of CUDA float32 tensors named like synth.DecoderMLP)."""
+def mlp_struct(t, k=10, F=32, H=32, app=None) -> MLP:
+    """Decoder weights (dict of CUDA float32 tensors named like synth.DecoderMLP).  With
+    appearance codes, ``t["w1_app"]`` is [H][A] and ``app`` the per-anchor codes [N][A] (for
+    a gradient struct: their gradient arrays)."""
     m = MLP()
     for n in ("w1", "b1", "w2_op", "b2_op", "w2_col", "b2_col", "w2_cov", "b2_cov"):
         setattr(m, n, t[n].data_ptr())
     m.F, m.H, m.k = F, H, k
+    if t.get("w1_app") is not None:
+        assert app is not None, "appearance weights without codes"
+        m.A = int(t["w1_app"].shape[1])
+        m.w1_app, m.app = t["w1_app"].data_ptr(), app.data_ptr()
     return m
 
 

@@ -5,7 +5,8 @@
 // shared memory and every weight read is a warp-wide broadcast.  Each decoder runs in
 // outer-product form (loop over hidden units, all outputs accumulated in registers), so only
 // the 36-wide input and one decoder's outputs are live.  Means are written camera-relative
-// (x_v - campos + O_i * l_v) so FP32 keeps them accurate far from the world origin.
+// (x_v - campos + O_i * l_v) so FP32 keeps them accurate far from the world origin.  With
+// appearance codes (Sec. 4.4) the colour decoder's hidden units also see the anchor's code.
 #include "internal.cuh"
 
 namespace ogs {
@@ -40,11 +41,14 @@ template <int K> struct Widths {
     static constexpr int cov = (7 * K + 3) / 4 * 4;
 };
 
-// One decoder: y = W2 relu(W1 z + b1) + b2.  w2t is the transposed second layer [H][NP].
-template <int NOUT, int NP>
+// One decoder: y = W2 relu(W1 z + b1 [+ Wa code]) + b2.  w2t is the transposed second layer
+// [H][NP]; with APP the hidden unit o also adds wa[o][0..8) . code (Sec. 4.4, zero-padded).
+template <int NOUT, int NP, bool APP = false>
 __device__ __forceinline__ void decoder(const float* __restrict__ w1, const float* __restrict__ b1,
                                         const float* __restrict__ w2t, const float* __restrict__ b2,
-                                        const float (&z)[kDin], float (&y)[NOUT]) {
+                                        const float (&z)[kDin], float (&y)[NOUT],
+                                        const float* __restrict__ wa = nullptr,
+                                        const float* code = nullptr) {
 #pragma unroll
     for (int i = 0; i < NOUT; ++i) y[i] = b2[i];
 #pragma unroll 1
@@ -58,6 +62,10 @@ __device__ __forceinline__ void decoder(const float* __restrict__ w1, const floa
             a = fmaf(w.y, z[4 * i + 1], a);
             a = fmaf(w.z, z[4 * i + 2], a);
             a = fmaf(w.w, z[4 * i + 3], a);
+        }
+        if (APP) {
+#pragma unroll
+            for (int c = 0; c < kMaxApp; ++c) a = fmaf(wa[o * kMaxApp + c], code[c], a);
         }
         a = fmaxf(a, 0.0f);
         const float4* col = reinterpret_cast<const float4*>(w2t + o * NP);
@@ -74,7 +82,7 @@ __device__ __forceinline__ void decoder(const float* __restrict__ w1, const floa
     }
 }
 
-template <int K>
+template <int K, bool APP>
 __global__ void __launch_bounds__(kDecThreads) decode_fp32(DecArgs a) {
     using Wd = Widths<K>;
     extern __shared__ __align__(16) float sm[];
@@ -86,6 +94,7 @@ __global__ void __launch_bounds__(kDecThreads) decode_fp32(DecArgs a) {
     float* b_op = t_cov + kH * Wd::cov;              // [op]
     float* b_col = b_op + Wd::op;                    // [col]
     float* b_cov = b_col + Wd::col;                  // [cov]
+    float* w_app = b_cov + Wd::cov;                  // [H][8] appearance weights (APP only)
     for (int i = threadIdx.x; i < 3 * kH * kDin; i += blockDim.x) w1[i] = a.mlp.w1[i];
     for (int i = threadIdx.x; i < 3 * kH; i += blockDim.x) b1[i] = a.mlp.b1[i];
     for (int i = threadIdx.x; i < kH * Wd::op; i += blockDim.x) {
@@ -103,6 +112,12 @@ __global__ void __launch_bounds__(kDecThreads) decode_fp32(DecArgs a) {
     for (int i = threadIdx.x; i < Wd::op; i += blockDim.x) b_op[i] = i < K ? a.mlp.b2_op[i] : 0.f;
     for (int i = threadIdx.x; i < Wd::col; i += blockDim.x) b_col[i] = i < 3 * K ? a.mlp.b2_col[i] : 0.f;
     for (int i = threadIdx.x; i < Wd::cov; i += blockDim.x) b_cov[i] = i < 7 * K ? a.mlp.b2_cov[i] : 0.f;
+    if (APP) {
+        for (int i = threadIdx.x; i < kH * kMaxApp; i += blockDim.x) {
+            const int o = i / kMaxApp, q = i % kMaxApp;
+            w_app[i] = q < a.mlp.A ? a.mlp.w1_app[o * a.mlp.A + q] : 0.f;
+        }
+    }
     __syncthreads();
     const uint32_t M = a.counts->n_selected;
     const Cam& c = a.cam;
@@ -130,7 +145,16 @@ __global__ void __launch_bounds__(kDecThreads) decode_fp32(DecArgs a) {
         }
         {   // colour: sigmoid
             float y[3 * K];
-            decoder<3 * K, Wd::col>(w1 + kH * kDin, b1 + kH, t_col, b_col, z, y);
+            if (APP) {
+                float code[kMaxApp];
+#pragma unroll
+                for (int q = 0; q < kMaxApp; ++q)
+                    code[q] = q < a.mlp.A ? a.mlp.app[(size_t)j * a.mlp.A + q] : 0.f;
+                decoder<3 * K, Wd::col, true>(w1 + kH * kDin, b1 + kH, t_col, b_col, z, y, w_app,
+                                              code);
+            } else {
+                decoder<3 * K, Wd::col>(w1 + kH * kDin, b1 + kH, t_col, b_col, z, y);
+            }
 #pragma unroll
             for (int i = 0; i < 3 * K; ++i) a.out.colors[3 * g0 + i] = sigmoidf_(y[i]);
         }
@@ -157,15 +181,16 @@ __global__ void __launch_bounds__(kDecThreads) decode_fp32(DecArgs a) {
     }
 }
 
-template <int K>
+template <int K, bool APP>
 ogs_status launch_decode(const DecArgs& a, cudaStream_t st) {
     using Wd = Widths<K>;
-    size_t smem = sizeof(float) * (3 * kH * kDin + 3 * kH + (kH + 1) * (Wd::op + Wd::col + Wd::cov));
-    if (cudaFuncSetAttribute(decode_fp32<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    size_t smem = sizeof(float) * (3 * kH * kDin + 3 * kH + (kH + 1) * (Wd::op + Wd::col + Wd::cov) +
+                                   (APP ? kH * kMaxApp : 0));
+    if (cudaFuncSetAttribute(decode_fp32<K, APP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return OGS_ERR_CUDA;
     int grid = stride_grid(a.sel_cap, kDecThreads, 4);
-    decode_fp32<K><<<grid, kDecThreads, smem, st>>>(a);
+    decode_fp32<K, APP><<<grid, kDecThreads, smem, st>>>(a);
     return launch_status();
 }
 
@@ -181,7 +206,8 @@ extern "C" ogs_status ogs_decode(const float* pos, const float* feat, const floa
                                  const ogs_gaussians* out, void* stream) {
     if (!pos || !feat || !offs || !lv || !mlp || !cam || !sel_idx || !sel_w || !counts || !out)
         return OGS_ERR_ARG;
-    if (mlp->F != kF || mlp->H != kH || mlp->k != 10 || N < 0 || sel_cap < 0) return OGS_ERR_ARG;
+    if (mlp->F != kF || mlp->H != kH || mlp->k != 10 || N < 0 || sel_cap < 0 || !app_ok(*mlp))
+        return OGS_ERR_ARG;
     if (!mlp->w1 || !mlp->b1 || !mlp->w2_op || !mlp->b2_op || !mlp->w2_col || !mlp->b2_col ||
         !mlp->w2_cov || !mlp->b2_cov)
         return OGS_ERR_ARG;
@@ -190,5 +216,6 @@ extern "C" ogs_status ogs_decode(const float* pos, const float* feat, const floa
     if (!aligned(feat, 16) || !aligned(out->quats, 16) || !aligned(mlp->w1, 16)) return OGS_ERR_ARG;
     if (sel_cap == 0) return OGS_OK;
     DecArgs a{pos, feat, offs, lv, sel_idx, sel_w, counts, sel_cap, *mlp, *out, make_cam(*cam)};
-    return launch_decode<10>(a, (cudaStream_t)stream);
+    return mlp->A > 0 ? launch_decode<10, true>(a, (cudaStream_t)stream)
+                      : launch_decode<10, false>(a, (cudaStream_t)stream);
 }

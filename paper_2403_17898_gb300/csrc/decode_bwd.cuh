@@ -54,6 +54,7 @@ struct DbArgs {
     float* rowP;         // [sel_cap][kRowP]
     float* rowZ;         // [sel_cap][kRowZ]
     float* partial;      // [kDbBlocks][kNWeights]
+    float* dapp;         // f32[N][A] appearance code gradients (+=), with codes only
 };
 
 __device__ __forceinline__ float sigm(float x) { return 1.0f / (1.0f + __expf(-x)); }
@@ -107,9 +108,13 @@ __device__ __forceinline__ void gaussian_dy(const DbArgs& a, int m, size_t g, ui
 
 constexpr int kDbBlocks = 2 * kSmCount;
 
+// partial sums of the appearance weight gradients: one kH x kMaxApp row per block
+constexpr int kAppItems = kH * kMaxApp;
+
 struct DbScratch {
     float* partial;
     float *rowY, *rowH, *rowP, *rowZ;
+    float* partial_app;  // [kDbBlocks][kAppItems]
 };
 
 inline size_t db_layout(int64_t sel_cap, void* base, DbScratch* s) {
@@ -121,6 +126,7 @@ inline size_t db_layout(int64_t sel_cap, void* base, DbScratch* s) {
     t.rowH = cv.take<float>(n * kRowH);
     t.rowP = cv.take<float>(n * kRowP);
     t.rowZ = cv.take<float>(n * kRowZ);
+    t.partial_app = cv.take<float>((size_t)kDbBlocks * kAppItems);
     if (s) *s = t;
     return cv.off + 256;
 }

@@ -397,7 +397,9 @@ extern "C" ogs_status ogs_decode_bwd_bf16(const float* pos, const float* feat, c
     if (!pos || !feat || !offs || !lv || !mlp || !cam || !sel_idx || !sel_w || !counts ||
         !dmeans || !dscales || !dquats || !drec || !dfeat || !doffs || !dlv || !dmlp || !scratch)
         return OGS_ERR_ARG;
-    if (mlp->F != kF || mlp->H != kH || mlp->k != kK || N < 0 || sel_cap < 0) return OGS_ERR_ARG;
+    // appearance codes: their backward is the FP32 ogs_decode_bwd
+    if (mlp->F != kF || mlp->H != kH || mlp->k != kK || N < 0 || sel_cap < 0 || mlp->A != 0)
+        return OGS_ERR_ARG;
     if (!dmlp->w1 || !dmlp->b1 || !dmlp->w2_op || !dmlp->b2_op || !dmlp->w2_col ||
         !dmlp->b2_col || !dmlp->w2_cov || !dmlp->b2_cov)
         return OGS_ERR_ARG;
@@ -410,7 +412,7 @@ extern "C" ogs_status ogs_decode_bwd_bf16(const float* pos, const float* feat, c
     db_layout(sel_cap, scratch, &sc);
     TcBwdArgs args{{pos, feat, offs, lv, sel_idx, sel_w, counts, *mlp, make_cam(*cam), dmeans,
                     dscales, dquats, drec, dfeat, doffs, dlv, sc.rowY, sc.rowH, sc.rowP, sc.rowZ,
-                    sc.partial},
+                    sc.partial, nullptr},
                    &counts->timeout};
     if (cudaFuncSetAttribute(decode_bwd_rows_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kSmem) != cudaSuccess)

@@ -32,9 +32,24 @@ __device__ __forceinline__ void put8(unsigned char* base, int row, int kc, int K
         *reinterpret_cast<const uint4*>(h);
 }
 
-// Element (n, k) of the layer-1 B operand: W1 [96][36] with K zero-padded to 48.
+constexpr int kAppCol = 40;         // layer-1 K column of an appearance code's first value
+static_assert(kAppCol + kMaxApp == kK1, "the code fills the last K chunk");
+
+// Element (n, k) of the layer-1 B operand: W1 [96][36] with K zero-padded to 48; with
+// appearance codes (Sec. 4.4) the colour rows 32..63 hold w1_app in columns 40..40+A.
 __device__ __forceinline__ float w1_elem(const ogs_mlp& m, int n, int k) {
-    return k < kDin ? m.w1[n * kDin + k] : 0.f;
+    if (k < kDin) return m.w1[n * kDin + k];
+    const int c = k - kAppCol;
+    if (c >= 0 && c < m.A && n >= kH && n < 2 * kH) return m.w1_app[(n - kH) * m.A + c];
+    return 0.f;
+}
+
+// Layer-1 K columns 40..47 of anchor j's input row: its appearance code, zero-padded (all
+// zero without codes).  app: f32[N][A] codes, A: their width (0..8).
+__device__ __forceinline__ void app_chunk(const float* __restrict__ app, int A, uint32_t j,
+                                          float (&v)[8]) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = i < A ? app[(size_t)j * A + i] : 0.f;
 }
 
 // Element (n, k) of the block-diagonal layer-2 B operand [112][96]: output rows 0..9 (opacity)

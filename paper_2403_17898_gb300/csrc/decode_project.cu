@@ -71,6 +71,8 @@ struct DpArgs {
     uint32_t* tiles;
     uint32_t* tile_count;       // may be null
     const unsigned char* img;
+    const float* app;           // appearance codes f32[N][n_app] (n_app = 0: none)
+    int n_app;
     Cam cam;
 };
 
@@ -178,7 +180,9 @@ __global__ void __launch_bounds__(kDpThreads, 3) decode_project_tc(DpArgs a) {
                         rw[5 + q] = a.lv[3 * (size_t)j + q];
                     }
                 } else {
-                    put8(sA1, row, kK1 / 8 - 1, kK1, z8);
+                    float code[8];
+                    app_chunk(a.app, a.n_app, j, code);
+                    put8(sA1, row, kK1 / 8 - 1, kK1, code);
                 }
             } else {
                 put8(sA1, row, 2 * half, kK1, z8);
@@ -344,7 +348,8 @@ extern "C" ogs_status ogs_decode_project_bf16(
     if (!pos || !feat || !offs || !lv || !mlp || !cam || !sel_idx || !sel_w || !counts || !rec ||
         !depth_key || !rect || !tiles || !scratch)
         return OGS_ERR_ARG;
-    if (mlp->F != kF || mlp->H != kH || mlp->k != kK || N < 0 || sel_cap < 0) return OGS_ERR_ARG;
+    if (mlp->F != kF || mlp->H != kH || mlp->k != kK || N < 0 || sel_cap < 0 || !app_ok(*mlp))
+        return OGS_ERR_ARG;
     if (!mlp->w1 || !mlp->b1 || !mlp->w2_op || !mlp->b2_op || !mlp->w2_col || !mlp->b2_col ||
         !mlp->w2_cov || !mlp->b2_cov)
         return OGS_ERR_ARG;
@@ -370,7 +375,7 @@ extern "C" ogs_status ogs_decode_project_bf16(
     DpArgs a{pos, feat, offs, lv, sel_idx, sel_w, counts,
              write_gauss ? *out : ogs_gaussians{nullptr, nullptr, nullptr, nullptr, nullptr},
              write_gauss ? 1 : 0, reinterpret_cast<float4*>(rec), depth_key,
-             reinterpret_cast<uint2*>(rect), tiles, tile_count, img, cm};
+             reinterpret_cast<uint2*>(rect), tiles, tile_count, img, mlp->app, mlp->A, cm};
     const int64_t tiles_cap = (sel_cap + kTM - 1) / kTM;
     const int grid = (int)(tiles_cap < 3 * kSmCount ? tiles_cap : 3 * kSmCount);
     launch_pdl(decode_project_tc, dim3(grid), dim3(kDpThreads), kDpSmem, st, a);

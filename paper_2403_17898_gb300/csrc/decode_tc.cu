@@ -79,10 +79,11 @@ __global__ void __launch_bounds__(kTcThreads, 3) decode_bf16_tc(TcArgs a) {
     }
     for (int e = t; e < kN1; e += kTcThreads) sb1[e] = a.mlp.b1[e];
     for (int e = t; e < kN2; e += kTcThreads) sb2[e] = b2_elem(a.mlp, e);
-    {   // the last K chunk (columns 40..47) of the input tile is always zero
+    {   // the last K chunk (columns 40..47) of the input tile: zero unless codes are used
         const float z8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         put8(sA1, t, kK1 / 8 - 1, kK1, z8);
     }
+    const bool app = a.mlp.A > 0;
     if (t == 0) tc::mbar_init(&mbar, 1);
     if (w == 0) {
         tc::tmem_alloc(&tmem_base, kTmemCols);
@@ -119,10 +120,16 @@ __global__ void __launch_bounds__(kTcThreads, 3) decode_bf16_tc(TcArgs a) {
                 put8(sA1, t, kc, kK1, v);
             }
             zc[0] = dv[0] / d; zc[1] = dv[1] / d; zc[2] = dv[2] / d; zc[3] = d;
+            if (app) {
+                float code[8];
+                app_chunk(a.mlp.app, a.mlp.A, j, code);
+                put8(sA1, t, kK1 / 8 - 1, kK1, code);
+            }
         } else {
             const float z8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int kc = 0; kc < kF / 8; ++kc) put8(sA1, t, kc, kK1, z8);
+            if (app) put8(sA1, t, kK1 / 8 - 1, kK1, z8);
             zc[0] = zc[1] = zc[2] = zc[3] = 0.f;
         }
         zc[4] = zc[5] = zc[6] = zc[7] = 0.f;
@@ -263,7 +270,8 @@ extern "C" ogs_status ogs_decode_bf16(const float* pos, const float* feat, const
                                       const ogs_gaussians* out, void* stream) {
     if (!pos || !feat || !offs || !lv || !mlp || !cam || !sel_idx || !sel_w || !counts || !out)
         return OGS_ERR_ARG;
-    if (mlp->F != kF || mlp->H != kH || mlp->k != kK || N < 0 || sel_cap < 0) return OGS_ERR_ARG;
+    if (mlp->F != kF || mlp->H != kH || mlp->k != kK || N < 0 || sel_cap < 0 || !app_ok(*mlp))
+        return OGS_ERR_ARG;
     if (!mlp->w1 || !mlp->b1 || !mlp->w2_op || !mlp->b2_op || !mlp->w2_col || !mlp->b2_col ||
         !mlp->w2_cov || !mlp->b2_cov)
         return OGS_ERR_ARG;

@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(kPbThreads) project_bwd_kernel(PbArgs a) {
 // hidden accumulators live in registers), so a thread keeps h, dh and dz (96 values).
 constexpr int kRowAnchors = kDbThreads / 2;
 
+template <bool APP>
 __global__ void __launch_bounds__(kDbThreads, 3) decode_bwd_rows(DbArgs a) {
     __shared__ __align__(16) float sW1t[3 * kDin * kH];   // [m][i][o]
     __shared__ __align__(16) float sW1[3 * kH * kDin];    // [m][o][i]
@@ -176,6 +177,12 @@ __global__ void __launch_bounds__(kDbThreads, 3) decode_bwd_rows(DbArgs a) {
     __shared__ __align__(16) float sW2[kNOut * kH];
     __shared__ float sB2[kNOut];
     __shared__ float sDz[kRowAnchors][kF + 1];
+    __shared__ __align__(16) float sWa[kH * kMaxApp];     // appearance weights [o][c], padded
+    const int napp = a.mlp.A;
+    for (int e = threadIdx.x; e < kH * kMaxApp; e += kDbThreads) {
+        const int o = e / kMaxApp, q = e % kMaxApp;
+        sWa[e] = q < napp ? a.mlp.w1_app[o * napp + q] : 0.f;
+    }
     for (int e = threadIdx.x; e < 3 * kH * kDin; e += kDbThreads) {
         const float v = a.mlp.w1[e];
         sW1[e] = v;
@@ -250,6 +257,19 @@ __global__ void __launch_bounds__(kDbThreads, 3) decode_bwd_rows(DbArgs a) {
                     }
                 }
             }
+            if (APP && m == 1) {           // the colour decoder also sees the code (Sec. 4.4)
+                float code[kMaxApp];
+#pragma unroll
+                for (int q = 0; q < kMaxApp; ++q)
+                    code[q] = q < napp ? a.mlp.app[(size_t)j * napp + q] : 0.f;
+#pragma unroll
+                for (int o = 0; o < kH; ++o) {
+                    float v = h[o];
+#pragma unroll
+                    for (int q = 0; q < kMaxApp; ++q) v = fmaf(sWa[o * kMaxApp + q], code[q], v);
+                    h[o] = v;
+                }
+            }
             uint32_t mask = 0;
 #pragma unroll
             for (int o = 0; o < kH; ++o) {
@@ -312,6 +332,17 @@ __global__ void __launch_bounds__(kDbThreads, 3) decode_bwd_rows(DbArgs a) {
 #pragma unroll
                 for (int i = 0; i < kH / 4; ++i)
                     pr[i] = make_float4(dh[4 * i], dh[4 * i + 1], dh[4 * i + 2], dh[4 * i + 3]);
+            }
+            if (APP && m == 1) {           // code gradient: dapp_c += sum_o Wa[o][c] dp_o
+#pragma unroll
+                for (int q = 0; q < kMaxApp; ++q) {
+                    if (q < napp) {
+                        float v = 0.f;
+#pragma unroll
+                        for (int o = 0; o < kH; ++o) v = fmaf(sWa[o * kMaxApp + q], dh[o], v);
+                        a.dapp[(size_t)j * napp + q] += v;
+                    }
+                }
             }
 #pragma unroll
             for (int o = 0; o < kH; ++o) {
@@ -462,6 +493,51 @@ __global__ void __launch_bounds__(kWThreads) decode_bwd_weights(DbArgs a) {
         if (t < kNOut) out[kOffB2 + t] = acc1;
         else out[kOffB1 + (t - kNOut)] = acc1;
     }
+}
+
+// Appearance weight gradients (Sec. 4.4): dWa[o][c] = sum over the selected anchors of the
+// colour decoder's pre-activation gradient dp_o (rowP columns 32..63) times the anchor's code
+// value c.  Thread (o, c) of each CTA accumulates over chunks of kWChunk rows staged in shared
+// memory; its total goes to the CTA's partial row, summed across CTAs by reduce_app in a
+// fixed order.
+static_assert(kWChunk * kMaxApp == kAppItems, "one code value staged per thread");
+
+__global__ void __launch_bounds__(kAppItems) decode_bwd_app_weights(DbArgs a,
+                                                                    float* __restrict__ part) {
+    __shared__ float sP[kWChunk][kH + 1];
+    __shared__ float sC[kWChunk][kMaxApp];
+    const uint32_t M = a.counts->n_selected;
+    const int t = threadIdx.x, o = t / kMaxApp, q = t % kMaxApp;
+    const int napp = a.mlp.A;
+    float acc = 0.f;
+    const uint32_t nchunks = (M + kWChunk - 1) / kWChunk;
+    for (uint32_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const uint32_t r0 = ch * kWChunk;
+        const int nv = (int)min((uint32_t)kWChunk, M - r0);
+        __syncthreads();
+        for (int e = t; e < kWChunk * kH; e += kAppItems) {
+            const int k = e / kH, h = e % kH;
+            sP[k][h] = k < nv ? a.rowP[(size_t)(r0 + k) * kRowP + kH + h] : 0.f;
+        }
+        {
+            const int k = t / kMaxApp, c = t % kMaxApp;
+            sC[k][c] = (k < nv && c < napp) ? a.mlp.app[(size_t)a.sel_idx[r0 + k] * napp + c] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < kWChunk; ++k) acc = fmaf(sP[k][o], sC[k][q], acc);
+    }
+    part[(size_t)blockIdx.x * kAppItems + t] = acc;
+}
+
+// dw1_app[o][c] += sum over blocks of part[b][o * kMaxApp + c] (fixed order, c < A).
+__global__ void __launch_bounds__(kAppItems) reduce_app(const float* __restrict__ part,
+                                                        int nblocks, float* dw1_app, int napp) {
+    const int t = threadIdx.x, o = t / kMaxApp, q = t % kMaxApp;
+    float s = 0.f;
+#pragma unroll 8
+    for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * kAppItems + t];
+    if (q < napp) dw1_app[o * napp + q] += s;
 }
 
 // dmlp[e] += sum over blocks of partial[b][e].  A CTA owns 32 consecutive outputs (one per
@@ -615,10 +691,12 @@ extern "C" ogs_status ogs_decode_bwd(const float* pos, const float* feat, const 
     if (!pos || !feat || !offs || !lv || !mlp || !cam || !sel_idx || !sel_w || !counts ||
         !dmeans || !dscales || !dquats || !drec || !dfeat || !doffs || !dlv || !dmlp || !scratch)
         return OGS_ERR_ARG;
-    if (mlp->F != kF || mlp->H != kH || mlp->k != kK || N < 0 || sel_cap < 0) return OGS_ERR_ARG;
+    if (mlp->F != kF || mlp->H != kH || mlp->k != kK || N < 0 || sel_cap < 0 || !app_ok(*mlp))
+        return OGS_ERR_ARG;
     if (!dmlp->w1 || !dmlp->b1 || !dmlp->w2_op || !dmlp->b2_op || !dmlp->w2_col ||
         !dmlp->b2_col || !dmlp->w2_cov || !dmlp->b2_cov)
         return OGS_ERR_ARG;
+    if (mlp->A > 0 && (!dmlp->w1_app || !dmlp->app)) return OGS_ERR_ARG;
     if (scratch_bytes < ogs_decode_bwd_scratch_bytes(sel_cap) || !aligned(scratch, 16) ||
         !aligned(dquats, 16) || !aligned(feat, 16) || !aligned(dfeat, 16))
         return OGS_ERR_ARG;
@@ -627,9 +705,18 @@ extern "C" ogs_status ogs_decode_bwd(const float* pos, const float* feat, const 
     DbScratch sc;
     db_layout(sel_cap, scratch, &sc);
     DbArgs a{pos, feat, offs, lv, sel_idx, sel_w, counts, *mlp, make_cam(*cam), dmeans, dscales,
-             dquats, drec, dfeat, doffs, dlv, sc.rowY, sc.rowH, sc.rowP, sc.rowZ, sc.partial};
-    decode_bwd_rows<<<stride_grid(sel_cap, kRowAnchors, 3), kDbThreads, 0, st>>>(a);
+             dquats, drec, dfeat, doffs, dlv, sc.rowY, sc.rowH, sc.rowP, sc.rowZ, sc.partial,
+             const_cast<float*>(dmlp->app)};
+    if (mlp->A > 0)
+        decode_bwd_rows<true><<<stride_grid(sel_cap, kRowAnchors, 3), kDbThreads, 0, st>>>(a);
+    else
+        decode_bwd_rows<false><<<stride_grid(sel_cap, kRowAnchors, 3), kDbThreads, 0, st>>>(a);
     if (launch_weight_pass(a, sc, *dmlp, st) != cudaSuccess) return OGS_ERR_CUDA;
+    if (mlp->A > 0) {
+        decode_bwd_app_weights<<<kDbBlocks, kAppItems, 0, st>>>(a, sc.partial_app);
+        reduce_app<<<1, kAppItems, 0, st>>>(sc.partial_app, kDbBlocks,
+                                            const_cast<float*>(dmlp->w1_app), mlp->A);
+    }
     return launch_status();
 }
 

@@ -38,6 +38,15 @@ inline Cam make_cam(const ogs_camera& k) {
 
 inline bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
+// Appearance codes (Sec. 4.4): at most this many values per anchor, so that a code fits the
+// zero-padded K columns 40..47 of the tensor-core decoders' first layer.
+constexpr int kMaxApp = 8;
+
+// The appearance fields of a decoder are usable: A in [0, kMaxApp], both arrays given if A > 0.
+inline bool app_ok(const ogs_mlp& m) {
+    return m.A >= 0 && m.A <= kMaxApp && (m.A == 0 || (m.w1_app && m.app));
+}
+
 inline ogs_status launch_status() {
     return cudaGetLastError() == cudaSuccess ? OGS_OK : OGS_ERR_CUDA;
 }

@@ -87,7 +87,12 @@ class Renderer:
             self._mlp_struct = None
         else:
             self.mlp = {n: _cuda(a, torch.float32) for n, a in zip(names, mlp.arrays())}
-            self._mlp_struct = abi.mlp_struct(self.mlp, k=k)
+        # appearance codes (Sec. 4.4): a code per anchor, seen by the colour decoder
+        self.app = None
+        if explicit is None and getattr(scene, "app", None) is not None:
+            self.app = _cuda(scene.app, torch.float32)
+            self.mlp["w1_app"] = _cuda(mlp.w1_app, torch.float32)
+        self._structs()
         self.sel_cap = int(sel_cap if sel_cap is not None else max(1024, self.N))
         self.pair_cap = int(pair_cap if pair_cap is not None else 1 << 20)
         self.sel_scratch = torch.empty(abi.lod_select_gated_scratch_bytes(self.N),
@@ -99,6 +104,11 @@ class Renderer:
         self.tile_range = torch.empty(self.gx * self.gy, 2, dtype=torch.int32, device="cuda")
         self.tile_count = torch.empty(self.gx * self.gy, dtype=torch.int32, device="cuda")
         self._alloc()
+
+    def _structs(self):
+        """(Re)builds the decoder struct after the per-anchor arrays were replaced."""
+        if self.explicit is None:
+            self._mlp_struct = abi.mlp_struct(self.mlp, k=self.k, app=self.app)
 
     # -- buffers ---------------------------------------------------------------------------
     def _alloc(self):
@@ -292,7 +302,7 @@ class Trainer(Renderer):
         dev = "cuda"
         self.grads = {n: torch.zeros_like(t) for n, t in self._anchor_params().items()}
         self.dmlp = {n: torch.zeros_like(t) for n, t in self.mlp.items()}
-        self._dmlp_struct = abi.mlp_struct(self.dmlp, k=self.k) if self.mlp else None
+        self._structs()
         self.adam_m = {n: torch.zeros_like(t) for n, t in self._anchor_params().items()}
         self.adam_v = {n: torch.zeros_like(t) for n, t in self._anchor_params().items()}
         for n, t in self.mlp.items():
@@ -316,7 +326,16 @@ class Trainer(Renderer):
             out = {"offs": self.offs, "lv": self.lv}
             out.update({"ex." + n: t for n, t in self.explicit.items()})
             return out
-        return {"feat": self.feat, "offs": self.offs, "lv": self.lv}
+        out = {"feat": self.feat, "offs": self.offs, "lv": self.lv}
+        if self.app is not None:
+            out["app"] = self.app
+        return out
+
+    def _structs(self):
+        super()._structs()
+        self._dmlp_struct = None
+        if self.explicit is None and hasattr(self, "dmlp"):
+            self._dmlp_struct = abi.mlp_struct(self.dmlp, k=self.k, app=self.grads.get("app"))
 
     def _alloc(self):
         super()._alloc()
@@ -365,7 +384,8 @@ class Trainer(Renderer):
                 self.sel_idx, self.sel_w, self.sel_cap, self.counts_t, self.dmeans,
                 self.dscales, self.dquats, self.drec, self.grads["feat"], self.grads["offs"],
                 self.grads["lv"], self._dmlp_struct, self.db_scratch, st,
-                bf16=self.precision == "bf16"))
+                # the tensor-core backward has no appearance term: codes take the FP32 one
+                bf16=self.precision == "bf16" and self.app is None))
 
     def zero_grad(self):
         for t in self.grads.values():
@@ -422,6 +442,8 @@ class Trainer(Renderer):
 
         for name in ("pos", "level", "dL", "feat", "offs", "lv"):
             setattr(self, name, gather(getattr(self, name)))
+        if self.app is not None:
+            self.app = gather(self.app)
         if self.explicit is not None:
             self.explicit = {k: gather(v) for k, v in self.explicit.items()}
         for store in (self.adam_m, self.adam_v):
@@ -429,6 +451,7 @@ class Trainer(Renderer):
                 if not k.startswith("mlp."):
                     store[k] = gather(store[k])
         self.grads = {k: torch.zeros_like(t) for k, t in self._anchor_params().items()}
+        self._structs()
         self.N = n
         self.sel_count = torch.zeros(self.N, dtype=torch.int32, device=dev)
         self.n_views_seen = 0

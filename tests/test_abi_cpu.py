@@ -67,3 +67,35 @@ def test_product_path_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(abi, "_lib", None)
     with pytest.raises(abi.OgsError):
         abi.lib()
+
+
+def test_appearance_fields_checked_on_host(lib):
+    """Appearance codes (Sec. 4.4): a code wider than 8 values, or codes without their arrays,
+    are rejected; so are codes in the tensor-core backward (its backward is the FP32 one).
+    The fake device pointers are never dereferenced: every check runs on the host first."""
+    from paper_2403_17898_gb300 import abi
+    L = abi.lib()
+    assert ctypes.sizeof(abi.MLP) == 96 and abi.MLP.app.offset == 88
+    cam = abi.Camera()
+    cam.width, cam.height, cam.d_max, cam.s = 64, 64, 10.0, 1.0
+    fake = 4096
+    m = abi.MLP()
+    for n in ("w1", "b1", "w2_op", "b2_op", "w2_col", "b2_col", "w2_cov", "b2_cov"):
+        setattr(m, n, fake)
+    m.F, m.H, m.k = 32, 32, 10
+    g = abi.Gaussians(*([fake] * 5))
+
+    def decode(mm):
+        return L.ogs_decode(fake, fake, fake, fake, 100, ctypes.byref(mm), ctypes.byref(cam),
+                            fake, fake, 0, fake, ctypes.byref(g), None)
+    assert decode(m) == 0                  # valid, sel_cap = 0: nothing enqueued
+    m.A = 9
+    assert decode(m) == 1
+    m.A = 4
+    assert decode(m) == 1                  # no code arrays
+    m.w1_app, m.app = fake, fake
+    assert decode(m) == 0
+    st = L.ogs_decode_bwd_bf16(fake, fake, fake, fake, 100, ctypes.byref(m), ctypes.byref(cam),
+                               fake, fake, 0, fake, fake, fake, fake, fake, fake, fake, fake,
+                               ctypes.byref(m), fake, 1 << 30, None)
+    assert st == 1
