@@ -328,6 +328,31 @@ def _explicit_bench(cams, pose, steps, warmup, flush, clk_index):
     return out
 
 
+def _appearance_bench(cams, pose, steps, warmup, flush, clk_index):
+    """1080p frames/s of the BF16 neural form with per-anchor appearance codes (Sec. 4.4:
+    an 8-value code per anchor in the colour decoder's first layer) on the same scene and path,
+    without the gate: compare with the no-gate BF16 line."""
+    import torch
+    import synth
+    from paper_2403_17898_gb300.render import Renderer
+    sc, mlp, _ = _workload()
+    sa, ma = synth.with_appearance(sc, mlp, seed=0)
+    del sc
+    W, H = cams[0].W, cams[0].H
+    rd = Renderer(sa, ma, W, H, sel_cap=200_000, pair_cap=6_000_000, precision="bf16")
+    for cam in cams:                      # size the buffers on every pose
+        rd.render(cam)
+    t, stages, clk = _time_form(rd, cams, pose, steps, warmup, None, flush, clk_index)
+    out = {"value": steps / t, "unit": "frames/s", "ms_per_step": 1e3 * t / steps,
+           "stages_ms": {k: round(v, 5) for k, v in stages.items()},
+           "workload": f"same 2M anchors and 120-pose path; {sa.app.shape[1]}-value appearance "
+                       "code per anchor (seeded N(0, 0.5)) fed to the colour decoder, BF16, "
+                       "no gate"}
+    del rd
+    torch.cuda.empty_cache()
+    return out
+
+
 def _train_bench(clk_index, steps_scale=1.0):
     """Training steps per second of both training workloads, plain FP32 decode and BF16
     decode: each step clears the gradients, runs forward + loss + backward for its views and
@@ -634,6 +659,8 @@ def run_gpu(args):
         torch.cuda.empty_cache()
         line["explicit_3dgs"] = _explicit_bench(cams, pose, min(args.steps, 600), args.warmup,
                                                 flush, local)
+        line["appearance_codes"] = _appearance_bench(cams, pose, min(args.steps, 600),
+                                                     args.warmup, flush, local)
         line["train"] = _train_bench(local)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(*_as_f64(sc, mlp), cams)
