@@ -485,6 +485,186 @@ def min_count_for(n_views, tau_v):
 
 
 # ----------------------------------------------------------------------------------------
+# anchor growing and the LOD-bias update (Sec. 4.2.1)
+# ----------------------------------------------------------------------------------------
+#
+# Decisions that floating point takes (threshold tests, the voxel a position falls in) are
+# taken in FP32, the precision of the CUDA path, with one IEEE operation per step (product,
+# sum, quotient, each correctly rounded), so that both sides decide identically.  The
+# accumulated gradient norms themselves are FP64.
+
+VOX_BITS = 20                       # bits per voxel coordinate in a key
+VOX_LIM = 1 << (VOX_BITS - 1)       # coordinates lie in [-VOX_LIM, VOX_LIM)
+
+
+def grow_thresholds(tau_g, beta, NL):
+    """Per-level growing thresholds tau_g * 2^(beta L) (Sec. 4.2.1) and the LOD-bias
+    thresholds 0.25 tau_g * 2^(beta L), both rounded to FP32.  Pinned by tau[0] = tau_g,
+    the ratio 2^beta between levels and the factor 0.25."""
+    L = np.arange(NL, dtype=np.float64)
+    tau = float(tau_g) * np.power(2.0, float(beta) * L)
+    return tau.astype(np.float32), (0.25 * tau).astype(np.float32)
+
+
+def grow_accumulate(N, k, sel_idx, drec, tiles, W, H, acc=None, cnt=None):
+    """One view's contribution to the growing statistics: for every Gaussian g (g = r k + i
+    of the r-th selected anchor) whose projection touches a tile, the norm of its view-space
+    mean gradient (dL/du, dL/dv scaled by W/2 and H/2 to normalised device coordinates, the
+    units of the cited 3D-GS thresholds) is added to acc[anchor][i] and cnt[anchor][i] += 1.
+    Pinned by hand values (a 3-4-5 gradient) and invisible Gaussians adding nothing."""
+    acc = np.zeros((N, k)) if acc is None else acc
+    cnt = np.zeros((N, k), np.int64) if cnt is None else cnt
+    drec = np.asarray(drec, np.float64)
+    tiles = np.asarray(tiles)
+    G = len(sel_idx) * k
+    for g in range(G):
+        if tiles[g] <= 0:
+            continue
+        j, i = int(sel_idx[g // k]), g % k
+        acc[j, i] += np.hypot(drec[g, 0] * (W / 2.0), drec[g, 1] * (H / 2.0))
+        cnt[j, i] += 1
+    return acc, cnt
+
+
+def _avg_f32(acc, cnt):
+    """FP32 average of FP32 sums: acc / cnt, one correctly rounded division."""
+    return np.float32(acc) / np.float32(cnt)
+
+
+def lod_bias_update(level, acc, cnt, thr_bias, eps, dL):
+    """LOD-bias update (Sec. 4.2.1): an anchor's gradient grad_v is the average over all its
+    Gaussians' counted views (sum of its k accumulated norms, summed in slot order in FP32,
+    over the sum of their counts); anchors of level L with grad_v > thr_bias[L] get
+    dL += eps (FP32).  Pinned by hand cases on both sides of the threshold and anchors that
+    no view saw."""
+    acc = np.asarray(acc, np.float32)
+    cnt = np.asarray(cnt, np.int64)
+    out = np.array(dL, np.float32, copy=True)
+    for j in range(acc.shape[0]):
+        s = np.float32(0.0)
+        for i in range(acc.shape[1]):
+            s = np.float32(s + acc[j, i])
+        c = int(cnt[j].sum())
+        if c > 0 and _avg_f32(s, c) > np.float32(thr_bias[int(level[j])]):
+            out[j] = np.float32(out[j] + np.float32(eps))
+    return out
+
+
+def voxel_of(p, vs):
+    """Voxel index of a point on a grid of spacing vs: the nearest grid point rint(p / vs)
+    per axis (Eq. for V_L: voxels are centred on the grid points; ties to even), the quotient
+    rounded to FP32 first; None if a coordinate falls outside [-VOX_LIM, VOX_LIM)."""
+    v = np.rint(np.asarray(p, np.float32) / np.float32(vs)).astype(np.int64)
+    if np.any(v < -VOX_LIM) or np.any(v >= VOX_LIM):
+        return None
+    return tuple(int(x) for x in v)
+
+
+def grow_anchors(pos, level, offs, lv, acc, cnt, NL, tau, voxel):
+    """Anchor growing (Sec. 4.2.1, next-level growth).  Every Gaussian (j, i) seen in at least
+    one view, with FP32 average gradient g = acc / cnt and anchor level L, proposes a voxel:
+    at level L + 1 if L + 1 < NL and g > tau[L + 1], else at level L if g > tau[L], holding
+    its position mu = pos_j + offs_ji * lv_j (FP32 product, then sum).  A proposal becomes an
+    anchor if no anchor of that level occupies that voxel and no proposal with a smaller index
+    j k + i took it first.  Returns (new_pos at the voxel centres = grid points, new_level,
+    new_lv = voxel size per axis, parent = proposing anchor), in increasing proposal index.  Pinned by hand
+    cases (each branch of the level rule, the finest level, occupied voxels, duplicate
+    proposals, unseen Gaussians, the centre formula) and a brute-force loop on small scenes."""
+    pos = np.asarray(pos, np.float32)
+    offs = np.asarray(offs, np.float32)
+    lv = np.asarray(lv, np.float32)
+    acc = np.asarray(acc, np.float32)
+    cnt = np.asarray(cnt, np.int64)
+    N, k = acc.shape
+    occupied = set()
+    for j in range(N):
+        L = int(level[j])
+        v = voxel_of(pos[j], voxel[L])
+        if v is not None:
+            occupied.add((L,) + v)
+    taken = set()
+    new_pos, new_level, new_lv, parent = [], [], [], []
+    for j in range(N):
+        L = int(level[j])
+        for i in range(k):
+            if cnt[j, i] <= 0:
+                continue
+            g = _avg_f32(acc[j, i], cnt[j, i])
+            if L + 1 < NL and g > np.float32(tau[L + 1]):
+                T = L + 1
+            elif g > np.float32(tau[L]):
+                T = L
+            else:
+                continue
+            mu = (pos[j] + offs[j, i] * lv[j]).astype(np.float32)
+            v = voxel_of(mu, voxel[T])
+            if v is None:
+                continue
+            key = (T,) + v
+            if key in occupied or key in taken:
+                continue
+            taken.add(key)
+            vs = np.float32(voxel[T])
+            new_pos.append(np.asarray(v, np.float32) * vs)
+            new_level.append(T)
+            new_lv.append([vs, vs, vs])
+            parent.append(j)
+    return (np.asarray(new_pos, np.float32).reshape(-1, 3), np.asarray(new_level, np.uint8),
+            np.asarray(new_lv, np.float32).reshape(-1, 3), np.asarray(parent, np.int64))
+
+
+def _pack_keys(T, v):
+    """Voxel keys (level, x, y, z) as unsigned 64-bit integers (one per row)."""
+    u = (np.asarray(v, np.int64) + VOX_LIM).astype(np.uint64)
+    return ((np.asarray(T, np.uint64) << np.uint64(60)) | (u[..., 0] << np.uint64(40)) |
+            (u[..., 1] << np.uint64(20)) | u[..., 2])
+
+
+def grow_anchors_vectorized(pos, level, offs, lv, acc, cnt, NL, tau, voxel):
+    """grow_anchors with array operations (the same FP32 steps; set membership by np.isin,
+    first proposal per voxel by np.unique over proposals in index order), for scenes of
+    millions of anchors.  Pinned against the loop form grow_anchors on seeded scenes."""
+    pos = np.asarray(pos, np.float32)
+    offs = np.asarray(offs, np.float32)
+    lv = np.asarray(lv, np.float32)
+    acc = np.asarray(acc, np.float32)
+    cnt = np.asarray(cnt, np.int64)
+    lev = np.asarray(level, np.int64)
+    N, k = acc.shape
+    vox = np.asarray(voxel, np.float32)
+    t32 = np.asarray(tau, np.float32)
+
+    def in_range(v):
+        return np.all((v >= -VOX_LIM) & (v < VOX_LIM), axis=-1)
+
+    ev = np.rint(pos / vox[lev][:, None]).astype(np.int64)
+    eok = in_range(ev)
+    ekeys = _pack_keys(lev[eok], ev[eok])
+    seen = cnt > 0
+    g = np.zeros((N, k), np.float32)
+    np.divide(acc, cnt.astype(np.float32), out=g, where=seen)
+    Lj = np.broadcast_to(lev[:, None], (N, k))
+    up = (Lj + 1 < NL) & (g > t32[np.minimum(Lj + 1, NL - 1)])
+    same = ~up & (g > t32[Lj])
+    T = np.where(up, Lj + 1, Lj)
+    prop = seen & (up | same)
+    mu = pos[:, None, :] + offs * lv[:, None, :]
+    pv = np.rint(mu / vox[T][..., None]).astype(np.int64)
+    prop &= in_range(pv)
+    cid = np.nonzero(prop.ravel())[0]
+    keys = _pack_keys(T.ravel()[cid], pv.reshape(-1, 3)[cid])
+    fresh = ~np.isin(keys, ekeys)
+    cid, keys = cid[fresh], keys[fresh]
+    _, first = np.unique(keys, return_index=True)
+    win = cid[np.sort(first)]
+    Tw = T.ravel()[win]
+    vs = vox[Tw]
+    new_pos = pv.reshape(-1, 3)[win].astype(np.float32) * vs[:, None]
+    return (new_pos.astype(np.float32), Tw.astype(np.uint8),
+            np.repeat(vs[:, None], 3, axis=1).astype(np.float32), (win // k).astype(np.int64))
+
+
+# ----------------------------------------------------------------------------------------
 # explicit Gaussians per anchor ("Our-3D-GS", Sec. 5 and Sec. 3.2 Eq. offsets)
 # ----------------------------------------------------------------------------------------
 
