@@ -304,6 +304,7 @@ TRAIN_WORKLOADS = (
 
 
 PRUNE_TAU_V = 0.01          # the paper's visibility threshold for large-scale scenes
+GROW_TAU_G, GROW_BETA, GROW_EPS = 2e-4, 0.2, 0.01   # the paper's growing defaults
 
 
 def _explicit_bench(cams, pose, steps, warmup, flush, clk_index):
@@ -368,7 +369,8 @@ def _train_bench(clk_index, steps_scale=1.0):
         stride = max(1, len(cams) // 16) if vps > 1 else 1
         views = cams[::stride][:vps] if vps > 1 else cams
         tr = Trainer(sc, mlp, W, H, ssim_lambda=lam, sel_cap=400_000, pair_cap=8_000_000,
-                     track_view_frequency=True)
+                     track_view_frequency=True, track_growth=True)
+        voxel = synth.voxel_sizes(sc)
         del sc
         gen = torch.Generator(device="cuda")
         gen.manual_seed(1)
@@ -431,6 +433,25 @@ def _train_bench(clk_index, steps_scale=1.0):
                     "anchors_after": n_after, "seconds": time.perf_counter() - t0,
                     "note": "count, order-preserving compaction and gather of every per-anchor "
                             "array and its Adam state, all on the GPU"}
+                # next-level growing + LOD-bias update (Sec. 4.2.1) from the statistics of the
+                # same training views (accumulated inside every timed step)
+                seen = int((tr.grad_cnt > 0).sum().item())
+                n_before = tr.N
+                dL0 = tr.dL.clone()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                added = tr.grow(voxel, tau_g=GROW_TAU_G, beta=GROW_BETA, eps=GROW_EPS)
+                torch.cuda.synchronize()
+                res["anchor_growth"] = {
+                    "tau_g": GROW_TAU_G, "beta": GROW_BETA, "eps": GROW_EPS,
+                    "gaussians_with_statistics": seen, "anchors_before": n_before,
+                    "anchors_added": added,
+                    "lod_bias_raised": int((tr.dL[:n_before] != dL0).sum().item()),
+                    "seconds": time.perf_counter() - t0,
+                    "note": "LOD-bias update, voxel-hash proposals, first-proposal-wins "
+                            "compaction, appended rows with the parents' features and fresh "
+                            "Adam state, all on the GPU (random targets: the statistics are "
+                            "not those of a converging scene)"}
             res[precision] = {"train_steps_per_s": 1e3 * K / float(np.sum(ms)),
                               "ms_per_step": float(np.mean(ms)), "stages_ms_per_step": stages,
                               "loss_last_step": float(tr.loss.item()),

@@ -11,6 +11,7 @@
  *   ogs_blend_bwd, ogs_project_bwd, ogs_decode_bwd   analytic backward (training)
  *   ogs_explicit_gaussians(_bwd)   explicit per-anchor Gaussians in place of decoding
  *   ogs_count_selected, ogs_prune_anchors, ogs_gather_rows   view-frequency pruning
+ *   ogs_grow_accumulate, ogs_update_lod_bias, ogs_grow_anchors   anchor growing (Sec. 4.2.1)
  *
  * Conventions shared by every entry point
  *   - Every pointer argument is a DEVICE pointer unless its comment says "host".  All device
@@ -543,6 +544,63 @@ ogs_status ogs_proposal_train(const float* pos, const uint8_t* level, const floa
                               float pos_weight,
                               const ogs_proposal* grads /* host struct, written */, float* loss,
                               void* scratch, size_t scratch_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Anchor growing and the LOD-bias update (Sec. 4.2.1).  Over the training views between two
+ * densification steps, every neural Gaussian (anchor j, slot i) accumulates the norm of its
+ * view-space position gradient; the average over the views that saw it, grad_g, decides:
+ *   - growing: with tau[L] = tau_g * 2^(beta L) (per level, FP32, given by the caller), a
+ *     Gaussian of an anchor of level L with grad_g > tau[L + 1] (and L + 1 < NL) proposes a
+ *     new anchor at level L + 1 ("next level"), else with grad_g > tau[L] one at level L.
+ *     The proposal is the voxel of the target level L' holding the Gaussian's position
+ *     mu = pos_j + offs_ji * l_v (FP32: product, then sum); voxels are centred on the grid
+ *     points of spacing voxel[L'] = delta / 2^L' (given), as in the Eq. for V_L, so the
+ *     voxel index is rint(mu / voxel[L']) per axis (FP32 quotient, ties to even).  It
+ *     becomes an anchor only if no anchor of that level lies in that voxel (an anchor's own
+ *     voxel: rint(pos / voxel) at its level), and among proposals of the same new voxel the
+ *     one with the smallest index j k + i wins.  New anchors sit at the voxel centre, the
+ *     grid point index * voxel[L'].
+ *   - LOD bias: grad_v = (sum_i acc_ji) / (sum_i cnt_ji) (FP32, slots summed in order); an
+ *     anchor of level L with grad_v > thr_bias[L] (the caller passes 0.25 tau[L]) gets
+ *     dL += eps.
+ * Voxel coordinates must lie in [-2^19, 2^19) per axis and NL <= 15; an anchor or proposal
+ * outside that range takes no part in growing.
+ *
+ *   ogs_grow_accumulate: for each Gaussian g < counts->n_gaussians of one view with
+ *   tiles[g] > 0 (its projection touches a tile): grad_acc[j][i] += |(du W/2, dv H/2)|
+ *   (drec columns 0 and 1, the pixel-space mean gradient, scaled to normalised device
+ *   coordinates) and grad_cnt[j][i] += 1, where j = sel_idx[g / k], i = g % k.  An anchor
+ *   appears once per view, so the call needs no atomics; drec, tiles: as from ogs_blend_bwd
+ *   and ogs_project_bin / ogs_decode_project_bf16.  grad_acc f32[N][k], grad_cnt u32[N][k]
+ *   (the caller zeroes them after each densification step).
+ *   ogs_update_lod_bias: dL[j] += eps where grad_v > thr_bias[level_j] (host float[NL]).
+ *   ogs_grow_anchors: the proposals above, written as new anchor rows r < n_new[0]:
+ *   new_pos f32[max_new][3] (voxel centre), new_level u8[max_new], new_lv f32[max_new][3]
+ *   (the voxel size on every axis), parent u32[max_new] (the proposing anchor, whose other
+ *   attributes the caller copies, e.g. with ogs_gather_rows), in increasing j k + i.
+ *   n_new u32[2] (device): [0] rows written = min(needed, max_new), [1] rows needed; the
+ *   call is deterministic, so a caller that finds [1] > max_new grows the buffers and calls
+ *   again.  tau, voxel: host float[NL].  N k < 2^32 - 1; with N = 0 the anchor arrays may be NULL.
+ *   scratch: ogs_grow_scratch_bytes(N, k) bytes, 16-byte aligned (a hash table of 2^ceil(
+ *   log2(2 N (k + 1))) voxel keys at 12 bytes each, plus 12 bytes per proposal slot).
+ * ------------------------------------------------------------------------------------- */
+ogs_status ogs_grow_accumulate(const float* drec, const uint32_t* tiles, const uint32_t* sel_idx,
+                               const ogs_counts* counts, int32_t k, int32_t width,
+                               int32_t height, float* grad_acc, uint32_t* grad_cnt,
+                               void* stream);
+ogs_status ogs_update_lod_bias(const uint8_t* level, const float* grad_acc,
+                               const uint32_t* grad_cnt, int64_t N, int32_t k, int32_t NL,
+                               const float* thr_bias /* host float[NL] */, float eps, float* dL,
+                               void* stream);
+size_t ogs_grow_scratch_bytes(int64_t N, int32_t k);
+ogs_status ogs_grow_anchors(const float* pos, const uint8_t* level, const float* offs,
+                            const float* lv, const float* grad_acc, const uint32_t* grad_cnt,
+                            int64_t N, int32_t k, int32_t NL,
+                            const float* tau /* host float[NL] */,
+                            const float* voxel /* host float[NL] */, float* new_pos,
+                            uint8_t* new_level, float* new_lv, uint32_t* parent,
+                            int64_t max_new, uint32_t* n_new, void* scratch,
+                            size_t scratch_bytes, void* stream);
 
 /* Library version string (host). */
 const char* ogs_version(void);

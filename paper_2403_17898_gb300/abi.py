@@ -127,6 +127,11 @@ _SIGS = {
     "ogs_prune_scratch_bytes": (_SZ, [_I64]),
     "ogs_prune_anchors": (C.c_int, [_P, _I64, C.c_uint32, _P, _P, _P, _SZ, _P]),
     "ogs_gather_rows": (C.c_int, [_P, _P, _I64, _P, _P, _I64, _P]),
+    "ogs_grow_accumulate": (C.c_int, [_P, _P, _P, _P, _I32, _I32, _I32, _P, _P, _P]),
+    "ogs_update_lod_bias": (C.c_int, [_P, _P, _P, _I64, _I32, _I32, _P, C.c_float, _P, _P]),
+    "ogs_grow_scratch_bytes": (_SZ, [_I64, _I32]),
+    "ogs_grow_anchors": (C.c_int, [_P, _P, _P, _P, _P, _P, _I64, _I32, _I32, _P, _P, _P, _P,
+                                   _P, _P, _I64, _P, _P, _SZ, _P]),
     "ogs_version": (C.c_char_p, []),
 }
 
@@ -495,6 +500,50 @@ def prune_anchors(sel_count, N, min_count, keep_idx, n_kept, scratch, stream=Non
     _check(lib().ogs_prune_anchors(_ptr(sel_count), int(N), int(min_count), _ptr(keep_idx),
                                    _ptr(n_kept), _ptr(scratch), scratch.numel(), _stream(stream)),
            "ogs_prune_anchors")
+
+
+def _host_f32(vals):
+    """Host float array (kept alive by the caller) and its pointer."""
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(vals, dtype=np.float32))
+    return a, a.ctypes.data_as(C.c_void_p)
+
+
+def grow_thresholds(tau_g, beta, NL):
+    """Per-level growing thresholds tau_g * 2^(beta L) and the LOD-bias thresholds 0.25 times
+    those (Sec. 4.2.1), as FP32 host arrays."""
+    import numpy as np
+    tau = [float(tau_g) * 2.0 ** (float(beta) * L) for L in range(int(NL))]
+    return np.asarray(tau, np.float32), np.asarray([0.25 * t for t in tau], np.float32)
+
+
+def grow_accumulate(drec, tiles, sel_idx, counts, k, width, height, grad_acc, grad_cnt,
+                    stream=None):
+    _check(lib().ogs_grow_accumulate(_ptr(drec), _ptr(tiles), _ptr(sel_idx), _ptr(counts),
+                                     int(k), int(width), int(height), _ptr(grad_acc),
+                                     _ptr(grad_cnt), _stream(stream)), "ogs_grow_accumulate")
+
+
+def update_lod_bias(level, grad_acc, grad_cnt, N, k, NL, thr_bias, eps, dL, stream=None):
+    thr, tp = _host_f32(thr_bias)
+    _check(lib().ogs_update_lod_bias(_ptr(level), _ptr(grad_acc), _ptr(grad_cnt), int(N),
+                                     int(k), int(NL), tp, float(eps), _ptr(dL),
+                                     _stream(stream)), "ogs_update_lod_bias")
+
+
+def grow_scratch_bytes(N, k):
+    return int(lib().ogs_grow_scratch_bytes(int(N), int(k)))
+
+
+def grow_anchors(pos, level, offs, lv, grad_acc, grad_cnt, N, k, NL, tau, voxel, new_pos,
+                 new_level, new_lv, parent, max_new, n_new, scratch, stream=None):
+    t, tp = _host_f32(tau)
+    v, vp = _host_f32(voxel)
+    _check(lib().ogs_grow_anchors(_ptr(pos), _ptr(level), _ptr(offs), _ptr(lv), _ptr(grad_acc),
+                                  _ptr(grad_cnt), int(N), int(k), int(NL), tp, vp,
+                                  _ptr(new_pos), _ptr(new_level), _ptr(new_lv), _ptr(parent),
+                                  int(max_new), _ptr(n_new), _ptr(scratch), scratch.numel(),
+                                  _stream(stream)), "ogs_grow_anchors")
 
 
 def gather_rows(src, dst, row_bytes, idx, n_dev, n_cap, stream=None):

@@ -294,7 +294,7 @@ class Trainer(Renderer):
     ``prune(tau_v)`` removes the anchors whose view frequency is below tau_v."""
 
     def __init__(self, scene, mlp, W, H, lr=1e-3, betas=(0.9, 0.999), eps=1e-15, ssim_lambda=0.0,
-                 track_view_frequency=False, **kw):
+                 track_view_frequency=False, track_growth=False, **kw):
         super().__init__(scene, mlp, W, H, **kw)
         self.ssim_lambda = float(ssim_lambda)   # 0.2 gives the 0.8 L1 + 0.2 D-SSIM loss
         self.lr, self.betas, self.eps = lr, betas, eps
@@ -317,6 +317,10 @@ class Trainer(Renderer):
         self.track_view_frequency = bool(track_view_frequency)
         self.sel_count = torch.zeros(self.N, dtype=torch.int32, device=dev)
         self.n_views_seen = 0
+        # growing statistics (Sec. 4.2.1): per (anchor, slot) sum of the view-space mean
+        # gradient norms and the number of views that saw the Gaussian
+        self.track_growth = bool(track_growth)
+        self._reset_growth_stats()
         self._alloc_grad()
 
     def _anchor_params(self):
@@ -369,6 +373,10 @@ class Trainer(Renderer):
             abi.blend_bwd(self.rec, self.pair_gauss, self.tile_range, self.W, self.H, bg, self.T,
                           self.n_last, self.dimg, self.drec, st)
         _stage(timers, "blend_bwd", st, bb)
+        if self.track_growth and self.explicit is None:
+            _stage(timers, "grow_stats", st, lambda: abi.grow_accumulate(
+                self.drec, self.tiles, self.sel_idx, self.counts_t, self.k, self.W, self.H,
+                self.grad_acc, self.grad_cnt, st))
         _stage(timers, "project_bwd", st, lambda: abi.project_bwd(
             self._g_struct, self.g_cap, 1, c, self.rect, self.drec, self.dmeans, self.dscales,
             self.dquats, self.counts_t, st))
@@ -420,6 +428,70 @@ class Trainer(Renderer):
         if update:
             self.optimizer_step(timers=timers)
 
+    def _reset_growth_stats(self):
+        dev = "cuda"
+        n = self.N if self.track_growth else 0
+        self.grad_acc = torch.zeros(n, self.k, device=dev)
+        self.grad_cnt = torch.zeros(n, self.k, dtype=torch.int32, device=dev)
+
+    def grow(self, voxel, tau_g=2e-4, beta=0.2, eps=0.01):
+        """Densification step of Sec. 4.2.1 from the statistics accumulated since the last one:
+        the LOD-bias update (dL += eps where an anchor's average gradient exceeds 0.25 tau[L]),
+        then next-level growing (new anchors in free voxels of level L or L + 1, at the voxel
+        centre, l_v = voxel size, zero offsets and LOD bias, features and appearance code of
+        the proposing anchor, fresh optimiser state).  ``voxel``: voxel size per level.
+        Clears the statistics; returns the number of anchors added."""
+        assert self.track_growth and self.explicit is None, "growing needs track_growth"
+        dev = "cuda"
+        tau, thr_bias = abi.grow_thresholds(tau_g, beta, self.NL)
+        abi.update_lod_bias(self.level, self.grad_acc, self.grad_cnt, self.N, self.k, self.NL,
+                            thr_bias, eps, self.dL)
+        scratch = torch.empty(abi.grow_scratch_bytes(self.N, self.k), dtype=torch.uint8,
+                              device=dev)
+        n_new = torch.zeros(2, dtype=torch.int32, device=dev)
+        max_new = max(1024, self.N // 8)
+        while True:
+            new_pos = torch.empty(max_new, 3, device=dev)
+            new_level = torch.empty(max_new, dtype=torch.uint8, device=dev)
+            new_lv = torch.empty(max_new, 3, device=dev)
+            parent = torch.empty(max_new, dtype=torch.int32, device=dev)
+            abi.grow_anchors(self.pos, self.level, self.offs, self.lv, self.grad_acc,
+                             self.grad_cnt, self.N, self.k, self.NL, tau, voxel, new_pos,
+                             new_level, new_lv, parent, max_new, n_new, scratch)
+            got, need = (int(x) for x in n_new.cpu().numpy().view(np.uint32))
+            if need <= max_new:
+                break
+            max_new = need              # the call is deterministic: rerun with room for all
+        n = got
+        if n:
+            def rows(t):
+                out = torch.empty((n,) + tuple(t.shape[1:]), dtype=t.dtype, device=dev)
+                abi.gather_rows(t, out, t[0].numel() * t.element_size(), parent, None, n)
+                return out
+
+            def zeros(t):
+                return torch.zeros((n,) + tuple(t.shape[1:]), dtype=t.dtype, device=dev)
+            self.pos = torch.cat([self.pos, new_pos[:n]])
+            self.level = torch.cat([self.level, new_level[:n]])
+            self.dL = torch.cat([self.dL, zeros(self.dL)])
+            self.offs = torch.cat([self.offs, zeros(self.offs)])
+            self.lv = torch.cat([self.lv, new_lv[:n]])
+            self.feat = torch.cat([self.feat, rows(self.feat)])
+            if self.app is not None:
+                self.app = torch.cat([self.app, rows(self.app)])
+            for store in (self.adam_m, self.adam_v):
+                for key in list(store):
+                    if not key.startswith("mlp."):
+                        store[key] = torch.cat([store[key], zeros(store[key])])
+            self.sel_count = torch.cat([self.sel_count, zeros(self.sel_count)])
+            self.N += n
+            self.grads = {key: torch.zeros_like(t) for key, t in self._anchor_params().items()}
+            self.sel_scratch = torch.empty(abi.lod_select_gated_scratch_bytes(self.N),
+                                           dtype=torch.uint8, device=dev)
+            self._structs()
+        self._reset_growth_stats()
+        return n
+
     def prune(self, tau_v):
         """View-frequency pruning (Sec. 4.2.2): keeps the anchors selected in at least a tau_v
         fraction of the training views counted since the last prune (order preserved), and
@@ -457,4 +529,7 @@ class Trainer(Renderer):
         self.n_views_seen = 0
         self.sel_scratch = torch.empty(abi.lod_select_gated_scratch_bytes(self.N),
                                        dtype=torch.uint8, device=dev)
+        if self.track_growth:              # growing statistics follow their anchors
+            self.grad_acc = gather(self.grad_acc)
+            self.grad_cnt = gather(self.grad_cnt)
         return n

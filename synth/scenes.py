@@ -26,7 +26,7 @@ __all__ = [
     "cube_scene", "city_scene", "decoder_mlp", "proposal_mlp",
     "look_at_camera", "zoom_out_path", "trajectory_d_max", "proposal_poses",
     "random_gaussians", "random_records", "random_rects_depths", "random_sort_keys",
-    "explicit_attributes", "with_appearance", "APP_DIM", "CONFIGS",
+    "explicit_attributes", "with_appearance", "APP_DIM", "CONFIGS", "voxel_sizes",
 ]
 
 F_DIM = 32      # anchor feature width (all configs)
@@ -533,6 +533,14 @@ CONFIGS = {
 
 
 APP_DIM = 8   # appearance code width (Sec. 4.4 gives none; 8 fills the decoders' K padding)
+
+
+def voxel_sizes(scene):
+    """Voxel size of every level of a generated scene (float32[NL]): the cube's cells, or the
+    city's base cell c0 halved per level."""
+    if "cell" in scene.meta:
+        return np.asarray(scene.meta["cell"], np.float32)
+    return np.asarray([scene.meta["c0"] / 2 ** L for L in range(scene.NL)], np.float32)
 
 
 def with_appearance(scene, mlp, seed=0, A=APP_DIM, scale=0.5):
