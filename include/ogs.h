@@ -345,8 +345,9 @@ ogs_status ogs_decode_bwd(const float* pos, const float* feat, const float* offs
  * 2^-9 each); the output gradients dy, the ReLU masks, the weight-gradient products over the
  * anchors and every accumulation stay FP32.  The backward of ogs_decode_bf16.  Same
  * arguments, scratch and results as ogs_decode_bwd, except that counts is written: on a
- * tensor-core wait that does not complete, counts->timeout is set.  Decoders with appearance
- * codes (mlp->A > 0) are rejected with OGS_ERR_ARG: their backward is ogs_decode_bwd.
+ * tensor-core wait that does not complete, counts->timeout is set.  Appearance codes enter
+ * the recomputed first layer as BF16 K columns 40..47; their gradients (dmlp->app, w1_app)
+ * are formed in FP32 from the FP32 pre-activation gradients.
  * ------------------------------------------------------------------------------------- */
 ogs_status ogs_decode_bwd_bf16(const float* pos, const float* feat, const float* offs,
                                const float* lv, int64_t N, const ogs_mlp* mlp /* host struct */,

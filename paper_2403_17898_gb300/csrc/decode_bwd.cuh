@@ -131,7 +131,8 @@ inline size_t db_layout(int64_t sel_cap, void* base, DbScratch* s) {
     return cv.off + 256;
 }
 
-// Weight pass + fixed-order reduction over the rows written by a row pass (grad.cu).
+// Weight pass + fixed-order reduction over the rows written by a row pass (grad.cu); with
+// appearance codes (a.mlp.A > 0) also the code weights' gradient dmlp.w1_app.
 cudaError_t launch_weight_pass(const DbArgs& a, const DbScratch& s, const ogs_mlp& dmlp,
                                cudaStream_t st);
 

@@ -10,8 +10,10 @@
 //
 // Between them the FP32 epilogues apply bias/ReLU, compute the output gradients dy of every
 // Gaussian (shared with the FP32 row pass), mask dh by the ReLU and accumulate dfeat, doffs
-// and dlv.  The f32 rows z, h, dy, dp go to scratch for the weight pass, which is the FP32
-// split-over-anchors product of grad.cu.  Operands live in shared memory in the no-swizzle
+// and dlv.  With appearance codes (Sec. 4.4) the code fills Z's zero-padded columns 40..47
+// and the colour rows of W1 carry its weights there; the code gradient W_app^T dp is formed
+// on the CUDA cores in epilogue 3.  The f32 rows z, h, dy, dp go to scratch for the weight
+// pass, which is the FP32 split-over-anchors product of grad.cu.  Operands live in shared memory in the no-swizzle
 // K-major core-matrix layout; every mbarrier wait is bounded and on expiry the kernel sets
 // ogs_counts.timeout, waits (bounded) for the MMAs in flight, releases TMEM and exits.
 #include "decode_bwd.cuh"
@@ -32,6 +34,7 @@ constexpr uint32_t kColD1 = 0;           // MMA 1 and MMA 3 (96 columns)
 constexpr uint32_t kColD4 = 96;          // MMA 4 (32 columns)
 constexpr uint32_t kColD2 = 128;         // MMA 2 (112 columns)
 constexpr uint32_t kWaitLimit = 1u << 24;
+constexpr int kAppK = 40;                // layer-1 K column of an appearance code's first value
 
 constexpr int kOffA1 = 0;                               // Z   128 x 48
 constexpr int kOffB1 = kOffA1 + kTM * kK1 * 2;          // W1   96 x 48
@@ -116,6 +119,7 @@ __global__ void __launch_bounds__(kThreads, 1) decode_bwd_rows_tc(TcBwdArgs args
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
+    __shared__ float sWa[kH * kMaxApp];            // appearance weights [o][c], zero-padded
     const DbArgs& a = args.a;
     unsigned char* sA1 = sm + kOffA1;
     unsigned char* sB1 = sm + kOffB1;
@@ -134,6 +138,7 @@ __global__ void __launch_bounds__(kThreads, 1) decode_bwd_rows_tc(TcBwdArgs args
     const uint32_t M = a.counts->n_selected;
     const uint32_t ntiles = (M + kTM - 1) / kTM;
     if (blockIdx.x >= ntiles) return;                      // uniform, before any TMEM use
+    const int napp = a.mlp.A;                              // appearance code width (0: none)
 
     // weights -> bf16 operand tiles, one 8-value chunk per store
     for (int e = t; e < kN1 * (kK1 / 8); e += kThreads) {  // W1 [o][k]
@@ -141,10 +146,17 @@ __global__ void __launch_bounds__(kThreads, 1) decode_bwd_rows_tc(TcBwdArgs args
         float v[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const int k = 8 * kc + i;
-            v[i] = k < kDin ? a.mlp.w1[n * kDin + k] : 0.f;
+            const int k = 8 * kc + i, ca = k - kAppK;
+            // columns 40..47: the colour decoder's appearance weights (Sec. 4.4), else zero
+            v[i] = k < kDin ? a.mlp.w1[n * kDin + k]
+                            : (ca >= 0 && ca < napp && n >= kH && n < 2 * kH
+                                   ? a.mlp.w1_app[(n - kH) * napp + ca] : 0.f);
         }
         put8(sB1, n, kc, kK1, v);
+    }
+    for (int e = t; e < kH * kMaxApp; e += kThreads) {
+        const int o = e / kMaxApp, ca = e % kMaxApp;
+        sWa[e] = ca < napp ? a.mlp.w1_app[o * napp + ca] : 0.f;
     }
     for (int e = t; e < kN2 * (kN1 / 8); e += kThreads) {  // W2 block-diagonal [n][o]
         const int n = e / (kN1 / 8), kc = e % (kN1 / 8);
@@ -172,7 +184,7 @@ __global__ void __launch_bounds__(kThreads, 1) decode_bwd_rows_tc(TcBwdArgs args
         sb2[e] = e < kK ? a.mlp.b2_op[e]
                         : (e < 4 * kK ? a.mlp.b2_col[e - kK]
                                       : (e < kNOut ? a.mlp.b2_cov[e - 4 * kK] : 0.f));
-    if (half == 0) {   // the last K chunk of the input tile (inputs 40..47) is always zero
+    if (half == 0) {   // the last K chunk of the input tile (inputs 40..47): zero or the code
         const float z8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         put8(sA1, al, kK1 / 8 - 1, kK1, z8);
     }
@@ -249,6 +261,13 @@ __global__ void __launch_bounds__(kThreads, 1) decode_bwd_rows_tc(TcBwdArgs args
                 for (int kc = 0; kc < kF / 8; ++kc) put8(sA1, al, kc, kK1, z8);
             }
             put8(sA1, al, kF / 8, kK1, zc);
+            if (napp > 0) {
+                float code[8];
+#pragma unroll
+                for (int ca = 0; ca < 8; ++ca)
+                    code[ca] = valid && ca < napp ? a.mlp.app[(size_t)j * napp + ca] : 0.f;
+                put8(sA1, al, kK1 / 8 - 1, kK1, code);
+            }
         }
         if (!run([&] { mma_chain(tbase + kColD1, sA1, sB1, kK1, id96); })) { aborted = true; break; }
 
@@ -348,6 +367,14 @@ __global__ void __launch_bounds__(kThreads, 1) decode_bwd_rows_tc(TcBwdArgs args
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
                     pr[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                if (q == 1 && napp > 0) {   // code gradient: dapp_c += sum_o Wa[o][c] dp_o
+                    for (int ca = 0; ca < napp; ++ca) {
+                        float g = 0.f;
+#pragma unroll
+                        for (int o = 0; o < kH; ++o) g = fmaf(sWa[o * kMaxApp + ca], v[o], g);
+                        a.dapp[(size_t)j * napp + ca] += g;
+                    }
+                }
             }
         }
         if (!run([&] { mma_chain(tbase + kColD4, sA2, sB4, kN1, id32); })) { aborted = true; break; }
@@ -397,9 +424,9 @@ extern "C" ogs_status ogs_decode_bwd_bf16(const float* pos, const float* feat, c
     if (!pos || !feat || !offs || !lv || !mlp || !cam || !sel_idx || !sel_w || !counts ||
         !dmeans || !dscales || !dquats || !drec || !dfeat || !doffs || !dlv || !dmlp || !scratch)
         return OGS_ERR_ARG;
-    // appearance codes: their backward is the FP32 ogs_decode_bwd
-    if (mlp->F != kF || mlp->H != kH || mlp->k != kK || N < 0 || sel_cap < 0 || mlp->A != 0)
+    if (mlp->F != kF || mlp->H != kH || mlp->k != kK || N < 0 || sel_cap < 0 || !app_ok(*mlp))
         return OGS_ERR_ARG;
+    if (mlp->A > 0 && (!dmlp->w1_app || !dmlp->app)) return OGS_ERR_ARG;
     if (!dmlp->w1 || !dmlp->b1 || !dmlp->w2_op || !dmlp->b2_op || !dmlp->w2_col ||
         !dmlp->b2_col || !dmlp->w2_cov || !dmlp->b2_cov)
         return OGS_ERR_ARG;
@@ -412,7 +439,7 @@ extern "C" ogs_status ogs_decode_bwd_bf16(const float* pos, const float* feat, c
     db_layout(sel_cap, scratch, &sc);
     TcBwdArgs args{{pos, feat, offs, lv, sel_idx, sel_w, counts, *mlp, make_cam(*cam), dmeans,
                     dscales, dquats, drec, dfeat, doffs, dlv, sc.rowY, sc.rowH, sc.rowP, sc.rowZ,
-                    sc.partial, nullptr},
+                    sc.partial, const_cast<float*>(dmlp->app)},
                    &counts->timeout};
     if (cudaFuncSetAttribute(decode_bwd_rows_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kSmem) != cudaSuccess)

@@ -653,6 +653,11 @@ cudaError_t db::launch_weight_pass(const DbArgs& a, const DbScratch& s, const og
                                    cudaStream_t st) {
     decode_bwd_weights<<<kDbBlocks, kWThreads, 0, st>>>(a);
     reduce_partials<<<(kNWeights + 31) / 32, 32 * kRedWarps, 0, st>>>(s.partial, kDbBlocks, dmlp);
+    if (a.mlp.A > 0) {
+        decode_bwd_app_weights<<<kDbBlocks, kAppItems, 0, st>>>(a, s.partial_app);
+        reduce_app<<<1, kAppItems, 0, st>>>(s.partial_app, kDbBlocks,
+                                            const_cast<float*>(dmlp.w1_app), a.mlp.A);
+    }
     return cudaGetLastError();
 }
 
@@ -712,11 +717,6 @@ extern "C" ogs_status ogs_decode_bwd(const float* pos, const float* feat, const 
     else
         decode_bwd_rows<false><<<stride_grid(sel_cap, kRowAnchors, 3), kDbThreads, 0, st>>>(a);
     if (launch_weight_pass(a, sc, *dmlp, st) != cudaSuccess) return OGS_ERR_CUDA;
-    if (mlp->A > 0) {
-        decode_bwd_app_weights<<<kDbBlocks, kAppItems, 0, st>>>(a, sc.partial_app);
-        reduce_app<<<1, kAppItems, 0, st>>>(sc.partial_app, kDbBlocks,
-                                            const_cast<float*>(dmlp->w1_app), mlp->A);
-    }
     return launch_status();
 }
 

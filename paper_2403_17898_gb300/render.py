@@ -392,8 +392,7 @@ class Trainer(Renderer):
                 self.sel_idx, self.sel_w, self.sel_cap, self.counts_t, self.dmeans,
                 self.dscales, self.dquats, self.drec, self.grads["feat"], self.grads["offs"],
                 self.grads["lv"], self._dmlp_struct, self.db_scratch, st,
-                # the tensor-core backward has no appearance term: codes take the FP32 one
-                bf16=self.precision == "bf16" and self.app is None))
+                bf16=self.precision == "bf16"))
 
     def zero_grad(self):
         for t in self.grads.values():

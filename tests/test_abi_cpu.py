@@ -70,9 +70,9 @@ def test_product_path_fails_loudly_without_library(tmp_path, monkeypatch):
 
 
 def test_appearance_fields_checked_on_host(lib):
-    """Appearance codes (Sec. 4.4): a code wider than 8 values, or codes without their arrays,
-    are rejected; so are codes in the tensor-core backward (its backward is the FP32 one).
-    The fake device pointers are never dereferenced: every check runs on the host first."""
+    """Appearance codes (Sec. 4.4): a code wider than 8 values, or codes without their arrays
+    (in the decoder or, for the backward, in the gradient struct), are rejected.  The fake
+    device pointers are never dereferenced: every check fails on the host first."""
     from paper_2403_17898_gb300 import abi
     L = abi.lib()
     assert ctypes.sizeof(abi.MLP) == 96 and abi.MLP.app.offset == 88
@@ -95,7 +95,11 @@ def test_appearance_fields_checked_on_host(lib):
     assert decode(m) == 1                  # no code arrays
     m.w1_app, m.app = fake, fake
     assert decode(m) == 0
-    st = L.ogs_decode_bwd_bf16(fake, fake, fake, fake, 100, ctypes.byref(m), ctypes.byref(cam),
-                               fake, fake, 0, fake, fake, fake, fake, fake, fake, fake, fake,
-                               ctypes.byref(m), fake, 1 << 30, None)
-    assert st == 1
+    dm = abi.MLP()
+    ctypes.memmove(ctypes.byref(dm), ctypes.byref(m), ctypes.sizeof(abi.MLP))
+    dm.w1_app, dm.app = None, None          # codes in the decoder, no code gradients given
+    for fn in (L.ogs_decode_bwd, L.ogs_decode_bwd_bf16):
+        st = fn(fake, fake, fake, fake, 100, ctypes.byref(m), ctypes.byref(cam), fake, fake, 0,
+                fake, fake, fake, fake, fake, fake, fake, fake, ctypes.byref(dm), fake, 1 << 30,
+                None)
+        assert st == 1
