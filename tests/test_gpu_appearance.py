@@ -300,3 +300,54 @@ def test_prune_keeps_codes_aligned(abi, torch):
         tr.render(v)
         fresh.render(v)
         assert torch.equal(tr.img, fresh.img)
+
+
+@pytest.mark.parametrize("kind", ["fp32", "bf16", "fused"])
+def test_narrow_codes_match_oracle(abi, torch, kind):
+    """A 3-value code: the zero padding of the code columns 3..7 must not leak in."""
+    sc, mlp, cams = synth.CONFIGS["cube4k_128"]()
+    sa, ma = synth.with_appearance(sc, mlp, seed=9, A=3)
+    sel, w = _pick(sc, 777, 9)
+    ref = oracle.decode(sel, w, sa, ma, cams[0])
+    got = _decode(abi, torch, sa, ma, cams[0], sel, w, kind, sa.app)
+    col = np.abs(got["colors"].astype(np.float64) - ref["colors"]).max()
+    assert col <= (2e-5 if kind == "fp32" else 1e-2), col
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_narrow_codes_backward(abi, torch, bf16):
+    sc, mlp, cams = synth.CONFIGS["cube4k_128"]()
+    sa, ma = synth.with_appearance(sc, mlp, seed=10, A=3)
+    cam = cams[0]
+    rng = np.random.default_rng(6)
+    M = 500
+    sel = np.sort(rng.choice(sc.N, size=M, replace=False)).astype(np.int64)
+    w = rng.uniform(0.05, 1.0, size=M).astype(np.float32)
+    G = M * 10
+    grads = {k: rng.normal(size=s).astype(np.float32) for k, s in
+             (("dmeans", (G, 3)), ("dscales", (G, 3)), ("dquats", (G, 4)), ("dopac", (G,)),
+              ("dcolors", (G, 3)))}
+    ref = oracle.decode_bwd(sel, w, sa, ma, cam, grads)
+    from paper_2403_17898_gb300 import abi as A
+    counts = np.zeros(8, np.uint32)
+    counts[0], counts[1] = M, G
+    drec = np.zeros((G, 9), np.float32)
+    drec[:, 5] = grads["dopac"]
+    drec[:, 6:9] = grads["dcolors"]
+    m, keep = _mlp(ma, sa.app)
+    dt = {n: torch.zeros_like(t) for n, t in keep[0].items()}
+    dapp = torch.zeros(sc.N, 3, device="cuda")
+    scr = torch.empty(abi.decode_bwd_scratch_bytes(M), dtype=torch.uint8, device="cuda")
+    abi.decode_bwd(cuda(sa.pos), cuda(sa.feat), cuda(sa.offs), cuda(sa.lv), sc.N, m, cam,
+                   cuda(sel.astype(np.int32)), cuda(w), M, cuda(counts.view(np.int32)),
+                   cuda(grads["dmeans"]), cuda(grads["dscales"]), cuda(grads["dquats"]),
+                   cuda(drec), torch.zeros(sc.N, 32, device="cuda"),
+                   torch.zeros(sc.N, 10, 3, device="cuda"), torch.zeros(sc.N, 3, device="cuda"),
+                   A.mlp_struct(dt, app=dapp), scr, bf16=bf16)
+    torch.cuda.synchronize()
+    tol = 6e-2 if bf16 else 1e-4
+    for name, got in (("dapp", dapp), ("dw1_app", dt["w1_app"])):
+        a, b = got.cpu().numpy(), ref[name]
+        assert a.shape == b.shape
+        err = np.linalg.norm(a - b) / np.linalg.norm(b)
+        assert err <= tol, (name, err)
