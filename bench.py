@@ -6,7 +6,7 @@ neural Gaussians per anchor, 1920x1080, a 120-pose zoom-out from 10 m to 2 km al
 step is one view through the whole forward hot path (LOD selection, learned visibility gate,
 BF16 tensor-core decoding, projection and binning, sorting, blending); step i renders pose
 (rank + i * world) mod 120.  The same steps are also timed on the plain FP32 path (no gate,
-FP32 decode), and the gate's image cost is judged on 60 held-out poses.
+FP32 decode), and the gate's image cost is assessed on 60 held-out poses.
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on the host
 cores instead (rank 0 only), each step a 1/16 sub-view of a frame.
@@ -469,7 +469,7 @@ def _train_proposal(rd, train_cams, test_cams, full_rd):
     """Trains the anchor-visibility proposal on the training poses (BCE with positives
     weighted, so dropping a visible anchor costs more than keeping an invisible one),
     calibrates p* as the largest threshold whose WORST calibration pose stays within the
-    PSNR budget, and judges it on the held-out poses against full-detail renders.  If the
+    PSNR budget, and assesses it on the held-out poses against full-detail renders.  If the
     held-out poses exceed the budget, the plain LOD path is used (the gate's fallback)."""
     import torch
     import synth
@@ -480,7 +480,7 @@ def _train_proposal(rd, train_cams, test_cams, full_rd):
     hist = proposal.train(net, rd, views, epochs=30, pos_weight=POS_WEIGHT)
     t_train = time.perf_counter() - t0
 
-    def judge(cams, p_star):
+    def assess(cams, p_star):
         """Set-level PSNR loss (pixel MSE pooled over the views) of the gated BF16 form
         against the full-detail render, relative to the plain FP32 path, plus per-view
         figures and the kept anchor fraction."""
@@ -507,11 +507,11 @@ def _train_proposal(rd, train_cams, test_cams, full_rd):
     calib = train_cams[::5]
     p_star, curve = 0.0, []
     for cand in (0.001, 0.002, 0.005, 0.01, 0.02, 0.05, 0.1, 0.2, 0.3, 0.5):
-        r = judge(calib, cand)
+        r = assess(calib, cand)
         curve.append([cand] + [round(x, 4) for x in r])
         if r[0] <= DPSNR_GATE_DB:
             p_star = cand
-    pooled, med, mx, kept = judge(test_cams, p_star) if p_star > 0 else (0.0, 0.0, 0.0, 1.0)
+    pooled, med, mx, kept = assess(test_cams, p_star) if p_star > 0 else (0.0, 0.0, 0.0, 1.0)
     use_gate = p_star > 0 and pooled <= DPSNR_GATE_DB
     info = {"train_poses": len(train_cams), "heldout_poses": len(test_cams),
             "epochs": len(hist), "bce_first_epoch": hist[0], "bce_last_epoch": hist[-1],
@@ -547,7 +547,7 @@ def run_gpu(args):
     pose = pose_of(rank, ws, n)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 126 MB L2
 
-    # the learned proposal (trained on its own poses of the same scene, judged on held-out)
+    # the learned proposal (trained on its own poses of the same scene, assessed on held-out)
     train_cams = synth.proposal_poses(cams, 200, seed=2)
     test_cams = synth.proposal_poses(cams, 60, seed=3)
     full_rd = Renderer(sc, mlp, W, H, sel_cap=2_000_000, pair_cap=40_000_000)
