@@ -270,7 +270,9 @@ ogs_status ogs_radix_sort_pairs(uint32_t* keys, uint32_t* vals, const uint32_t* 
  *   rec, pair_gauss, tile_range from the calls above
  *   bg: host float[3]
  *   img f32[3][H][W], T_final f32[H][W], n_last u32[H][W] (list entries up to and
- *   including the last blended one)
+ *   including the last blended one); img may be pinned host memory (page-locked, so its
+ *   address is valid on the device under unified addressing): the image then goes to the
+ *   host while the kernel runs, with no separate copy
  *   n_eval (optional, may be NULL): u32[H][W], list entries the pixel evaluated before it
  *   saturated or ran out (the blend's unit of work)
  *   maxc (optional, may be NULL): u32[N_anchors], float bits of the largest T*alpha of any

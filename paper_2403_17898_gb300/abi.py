@@ -171,6 +171,17 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _ptr_out(t):
+    """Pointer of an output that may live in pinned host memory: with unified addressing a
+    pinned (page-locked) host tensor's address is valid on the device, and kernels write it
+    over the host link directly."""
+    if t is not None and not t.is_cuda:
+        if not t.is_pinned():
+            raise OgsError("expected a CUDA tensor or a pinned host tensor")
+        return C.c_void_p(t.data_ptr())
+    return _ptr(t)
+
+
 def _stream(stream):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -326,7 +337,8 @@ def blend_fwd(rec, pair_gauss, tile_range, width, height, bg, img, T_final, n_la
               sel_idx=None, k=10, maxc=None, n_eval=None, stream=None):
     b = (C.c_float * 3)(*[float(x) for x in bg])
     _check(lib().ogs_blend_fwd(_ptr(rec), _ptr(pair_gauss), _ptr(tile_range), int(width),
-                               int(height), C.byref(b), _ptr(img), _ptr(T_final), _ptr(n_last),
+                               int(height), C.byref(b), _ptr_out(img), _ptr(T_final),
+                               _ptr(n_last),
                                _ptr(n_eval), _ptr(sel_idx), int(k), _ptr(maxc),
                                _stream(stream)), "ogs_blend_fwd")
 

@@ -207,22 +207,49 @@ class Renderer:
         v = self.counts_t.cpu().numpy().view(np.uint32)
         return FrameCounts(*[int(x) for x in v])
 
-    def render_to_host(self, cam, host_img, infer=True, bg=(0.0, 0.0, 0.0), gate=None):
-        """The end-to-end call: render one view and copy the image into ``host_img`` (a pinned
-        float32 [3, H, W] CPU tensor); returns when the image is on the host."""
-        self.enqueue(cam, infer, bg, gate=gate)
-        host_img.copy_(self.img, non_blocking=True)
+    def render_to_host(self, cam, host_img, infer=True, bg=(0.0, 0.0, 0.0), gate=None,
+                       zero_copy=True):
+        """The end-to-end call: render one view into ``host_img`` (a pinned float32 [3, H, W]
+        CPU tensor); returns when the image is on the host.  With ``zero_copy`` the blend
+        writes the image straight into the pinned buffer (the device-side image is then not
+        updated); otherwise it renders on the device and copies."""
+        if zero_copy:
+            self.enqueue(cam, infer, bg, gate=gate, img=host_img)
+        else:
+            self.enqueue(cam, infer, bg, gate=gate)
+            host_img.copy_(self.img, non_blocking=True)
         torch.cuda.current_stream().synchronize()
         return host_img
 
     def render_sequence_to_host(self, cams, host_imgs, bg=(0.0, 0.0, 0.0), gate=None,
-                                on_frame=None):
-        """End-to-end rendering of a sequence of views into pinned host memory, pipelined: the
-        image of view i is copied to the host on a copy stream while view i + 1 renders.
+                                on_frame=None, zero_copy=False):
+        """End-to-end rendering of a sequence of views into pinned host memory, pipelined.
         ``host_imgs``: two pinned float32 [3, H, W] CPU tensors used in turn; view i lands in
         ``host_imgs[i % 2]``, and ``on_frame(i, host_img)`` (if given) is called once it is
-        there (before that buffer is reused two views later).  Returns when every image is on
-        the host."""
+        there (before that buffer is reused two views later).  By default view i is rendered
+        on the device and copied to the host on a copy stream while view i + 1 renders; with
+        ``zero_copy`` the blend of view i writes straight into its host buffer instead (no
+        copy, but the blend's stores then cross the host link and lengthen it: slower when
+        views are pipelined, faster for one view at a time, see render_to_host).  Returns
+        when every image is on the host."""
+        if zero_copy:
+            done = [None, None]
+            for i, cam in enumerate(cams):
+                b = i % 2
+                if done[b] is not None:
+                    done[b].synchronize()            # view i - 2 is on the host
+                    if on_frame is not None:
+                        on_frame(i - 2, host_imgs[b])
+                self.enqueue(cam, True, bg, gate=gate, img=host_imgs[b])
+                ev = torch.cuda.Event()
+                ev.record()
+                done[b] = ev
+            for j in range(max(len(cams) - 2, 0), len(cams)):
+                b = j % 2
+                done[b].synchronize()
+                if on_frame is not None:
+                    on_frame(j, host_imgs[b])
+            return host_imgs
         if not hasattr(self, "_seq_img"):
             self._seq_img = torch.empty_like(self.img)
             self._copy_stream = torch.cuda.Stream()
