@@ -354,6 +354,55 @@ def _appearance_bench(cams, pose, steps, warmup, flush, clk_index):
     return out
 
 
+def _train_appearance_bench(clk_index, steps=60, warmup=5):
+    """Training steps per second of the street workload (one 1600x900 view per step, L1,
+    dense Adam) with an 8-value appearance code per anchor (Sec. 4.4), BF16: the codes and
+    their weights are trained with everything else."""
+    import torch
+    import synth
+    from paper_2403_17898_gb300.render import Trainer
+    sc, mlp, cams = synth.CONFIGS["street500k_1600x900"]()
+    sa, ma = synth.with_appearance(sc, mlp, seed=0)
+    W, H = cams[0].W, cams[0].H
+    tr = Trainer(sa, ma, W, H, sel_cap=400_000, pair_cap=8_000_000, precision="bf16")
+    del sc, sa
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1)
+    targets = [torch.rand(3, H, W, generator=gen, device="cuda") for _ in range(len(cams))]
+    sel_max = pair_max = 0
+    for cam in cams:
+        c = tr.render(cam, infer=False)
+        sel_max, pair_max = max(sel_max, c.n_selected), max(pair_max, c.n_pairs)
+    tr.sel_cap, tr.pair_cap = int(sel_max * 1.2) + 1024, int(pair_max * 1.5) + 4096
+    tr._alloc()
+    batch = lambda i: ([cams[i % len(cams)]], [targets[i % len(cams)]])
+    for i in range(warmup):
+        tr.train_step(*batch(i))
+    torch.cuda.synchronize()
+    timers, ev = {}, []
+    with ClockSampler(clk_index) as clk:
+        for i in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            tr.train_step(*batch(warmup + i), timers=timers)
+            e1.record()
+            ev.append((e0, e1))
+        torch.cuda.synchronize()
+    c = tr.counts()
+    assert c.overflow == 0 and c.timeout == 0, "overflow or expired wait in training"
+    ms = [a.elapsed_time(b) for a, b in ev]
+    out = {"workload": "street500k_1600x900 with an 8-value appearance code per anchor "
+                       "(codes and code weights trained), BF16, L1, dense Adam",
+           "train_steps_per_s": 1e3 * steps / float(np.sum(ms)),
+           "ms_per_step": float(np.mean(ms)), "steps": steps, "warmup": warmup,
+           "stages_ms_per_step": {k: round(float(np.sum([a.elapsed_time(b) for a, b in v]))
+                                            / steps, 4) for k, v in timers.items()},
+           "clocks": clk.summary()}
+    del tr, targets
+    torch.cuda.empty_cache()
+    return out
+
+
 def _train_bench(clk_index, steps_scale=1.0):
     """Training steps per second of both training workloads, plain FP32 decode and BF16
     decode: each step clears the gradients, runs forward + loss + backward for its views and
@@ -694,6 +743,7 @@ def run_gpu(args):
         line["appearance_codes"] = _appearance_bench(cams, pose, min(args.steps, 600),
                                                      args.warmup, flush, local)
         line["train"] = _train_bench(local)
+        line["train"]["street500k_1600x900_appearance"] = _train_appearance_bench(local)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(*_as_f64(sc, mlp), cams)
     print(json.dumps(line), flush=True)
