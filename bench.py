@@ -787,7 +787,7 @@ def run_profile_train(args):
     sc, mlp, cams = synth.CONFIGS[args.train_workload]()
     W, H = cams[0].W, cams[0].H
     tr = Trainer(sc, mlp, W, H, ssim_lambda=0.2, sel_cap=100_000, pair_cap=2_000_000,
-                 precision=args.precision)
+                 precision=args.precision, track_view_frequency=True, track_growth=True)
     gen = torch.Generator(device="cuda")
     gen.manual_seed(1)
     views = cams[::4][:16] if args.train_workload == "city8M_1080p" else [cams[len(cams) // 2]]
