@@ -354,17 +354,29 @@ __global__ void __launch_bounds__(1024) tile_scan(const uint32_t* __restrict__ t
     pdl_trigger();
     __shared__ unsigned long long ws[32];
     __shared__ uint32_t s_nbig;
-    __shared__ uint32_t s_cnt[kScanSmemTiles];
+    __shared__ __align__(16) uint32_t s_cnt[kScanSmemTiles];
+    static_assert(kScanSmemTiles == 1024 * 8, "staged scan: eight counts per thread");
     const bool staged = ntiles <= kScanSmemTiles;
-    if (staged)
-        for (int b = threadIdx.x; b < ntiles; b += 1024) s_cnt[b] = tcount[b];
+    if (staged)   // zero-padded to 8192 slots: thread t owns slots [8t, 8t + 8)
+        for (int b = threadIdx.x; b < kScanSmemTiles; b += 1024)
+            s_cnt[b] = b < ntiles ? tcount[b] : 0u;
     if (threadIdx.x == 0) s_nbig = 0;
     __syncthreads();
-    const uint32_t* cnt = staged ? s_cnt : tcount;
-    const int per = (ntiles + 1023) / 1024;
+    const int per = staged ? 8 : (ntiles + 1023) / 1024;
     const int b0 = threadIdx.x * per, b1 = min(b0 + per, ntiles);
+    uint32_t v8[8];
     unsigned long long local = 0;
-    for (int b = b0; b < b1; ++b) local += cnt[b];
+    if (staged) {
+        // two 16-byte shared loads per thread instead of eight strided words
+        const uint4 u0 = reinterpret_cast<const uint4*>(s_cnt)[2 * threadIdx.x];
+        const uint4 u1 = reinterpret_cast<const uint4*>(s_cnt)[2 * threadIdx.x + 1];
+        v8[0] = u0.x; v8[1] = u0.y; v8[2] = u0.z; v8[3] = u0.w;
+        v8[4] = u1.x; v8[5] = u1.y; v8[6] = u1.z; v8[7] = u1.w;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) local += v8[i];
+    } else {
+        for (int b = b0; b < b1; ++b) local += tcount[b];
+    }
     unsigned long long x = local;
     for (int o = 1; o < 32; o <<= 1) {
         const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
@@ -387,12 +399,17 @@ __global__ void __launch_bounds__(1024) tile_scan(const uint32_t* __restrict__ t
     if (staged) {
         // exclusive offsets back into shared memory, then coalesced writes
         unsigned long long run = run0;
-        for (int b = b0; b < b1; ++b) {
-            const uint32_t v = s_cnt[b];
-            s_cnt[b] = (uint32_t)run;
-            if (!over && v > (uint32_t)kSmallSort) big[atomicAdd(&s_nbig, 1u)] = (uint32_t)b;
-            run += v;
+        uint32_t o8[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            o8[i] = (uint32_t)run;
+            if (!over && v8[i] > (uint32_t)kSmallSort)   // padding slots hold 0: never long
+                big[atomicAdd(&s_nbig, 1u)] = (uint32_t)(b0 + i);
+            run += v8[i];
         }
+        reinterpret_cast<uint4*>(s_cnt)[2 * threadIdx.x] = make_uint4(o8[0], o8[1], o8[2], o8[3]);
+        reinterpret_cast<uint4*>(s_cnt)[2 * threadIdx.x + 1] =
+            make_uint4(o8[4], o8[5], o8[6], o8[7]);
         __syncthreads();
         for (int b = threadIdx.x; b < ntiles; b += 1024) {
             const uint32_t st = s_cnt[b];
