@@ -484,6 +484,34 @@ def min_count_for(n_views, tau_v):
     return c
 
 
+def opacity_accumulate(N, k, sel_idx, opac, acc=None, views=None):
+    """One training view's contribution to the average-opacity statistic of anchor pruning
+    (Sec. 4.2.2): every selected anchor adds the opacities of its k generated Gaussians, a
+    dropped Gaussian (opacity <= 0) counting as 0, and one view.  Pinned by hand values."""
+    acc = np.zeros(N) if acc is None else acc
+    views = np.zeros(N, np.int64) if views is None else views
+    opac = np.asarray(opac, np.float64).reshape(-1, k)
+    for r, j in enumerate(np.asarray(sel_idx, np.int64)):
+        acc[j] += np.maximum(opac[r], 0.0).sum()
+        views[j] += 1
+    return acc, views
+
+
+def prune_by_opacity(acc, views, k, tau_o):
+    """Anchors kept by opacity pruning (Sec. 4.2.2): an anchor seen in at least one counted
+    view is removed when the average opacity of the Gaussians it generated, acc / (views k)
+    (FP32 sum and quotient), is below tau_o; anchors no view selected are kept (view frequency
+    handles them).  Ascending index order.  Pinned by hand cases at the threshold."""
+    acc = np.asarray(acc, np.float32)
+    views = np.asarray(views, np.int64)
+    keep = []
+    for j in range(len(acc)):
+        if views[j] > 0 and np.float32(acc[j]) / np.float32(views[j] * k) < np.float32(tau_o):
+            continue
+        keep.append(j)
+    return np.asarray(keep, np.int64)
+
+
 # ----------------------------------------------------------------------------------------
 # anchor growing and the LOD-bias update (Sec. 4.2.1)
 # ----------------------------------------------------------------------------------------

@@ -45,3 +45,26 @@ def test_monotone_in_threshold_and_recount_of_real_selections():
         if prev is not None:
             assert kept <= prev
         prev = kept
+
+
+def test_opacity_statistic_hand_values():
+    """Sec. 4.2.2 average opacity: per view, an anchor adds its Gaussians' opacities (dropped
+    ones, opacity <= 0, as 0) and one view."""
+    opac = np.array([0.5, -0.2, 0.1,    # selected row 0 -> anchor 2: 0.6
+                     0.0, 0.3, 0.3])    # selected row 1 -> anchor 0: 0.6
+    acc, views = oracle.opacity_accumulate(3, 3, np.array([2, 0]), opac)
+    np.testing.assert_allclose(acc, [0.6, 0.0, 0.6], rtol=1e-15)
+    np.testing.assert_array_equal(views, [1, 0, 1])
+    acc, views = oracle.opacity_accumulate(3, 3, np.array([2]), opac[:3], acc, views)
+    np.testing.assert_allclose(acc, [0.6, 0.0, 1.2], rtol=1e-15)
+    np.testing.assert_array_equal(views, [1, 0, 2])
+
+
+def test_prune_by_opacity_threshold():
+    k = 10
+    acc = np.array([0.05, 0.049, 0.0, 7.0, 0.0], np.float32)
+    views = np.array([1, 1, 0, 2, 3])
+    # averages 0.005, 0.0049, unseen, 0.35, 0: tau 0.005 keeps the equal one and the unseen
+    assert list(oracle.prune_by_opacity(acc, views, k, 0.005)) == [0, 2, 3]
+    assert list(oracle.prune_by_opacity(acc, views, k, 0.0)) == [0, 1, 2, 3, 4]
+    assert list(oracle.prune_by_opacity(acc, views, k, 1.0)) == [2]
