@@ -304,6 +304,7 @@ TRAIN_WORKLOADS = (
 
 
 PRUNE_TAU_V = 0.01          # the paper's visibility threshold for large-scale scenes
+PRUNE_TAU_O = 0.005         # average-opacity threshold (the paper gives none: Scaffold-GS's)
 GROW_TAU_G, GROW_BETA, GROW_EPS = 2e-4, 0.2, 0.01   # the paper's growing defaults
 
 
@@ -418,7 +419,7 @@ def _train_bench(clk_index, steps_scale=1.0):
         stride = max(1, len(cams) // 16) if vps > 1 else 1
         views = cams[::stride][:vps] if vps > 1 else cams
         tr = Trainer(sc, mlp, W, H, ssim_lambda=lam, sel_cap=400_000, pair_cap=8_000_000,
-                     track_view_frequency=True, track_growth=True)
+                     track_view_frequency=True, track_growth=True, track_opacity=True)
         voxel = synth.voxel_sizes(sc)
         del sc
         gen = torch.Generator(device="cuda")
@@ -482,6 +483,17 @@ def _train_bench(clk_index, steps_scale=1.0):
                     "anchors_after": n_after, "seconds": time.perf_counter() - t0,
                     "note": "count, order-preserving compaction and gather of every per-anchor "
                             "array and its Adam state, all on the GPU"}
+                # average-opacity pruning (Sec. 4.2.2) from the same views' statistic
+                n_before = tr.N
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                n_after = tr.prune_opacity(PRUNE_TAU_O)
+                torch.cuda.synchronize()
+                res["opacity_prune"] = {
+                    "tau_o": PRUNE_TAU_O, "anchors_before": n_before, "anchors_after": n_after,
+                    "seconds": time.perf_counter() - t0,
+                    "note": "average opacity of each anchor's Gaussians over the counted views; "
+                            "anchors below tau_o removed with the same compaction"}
                 # next-level growing + LOD-bias update (Sec. 4.2.1) from the statistics of the
                 # same training views (accumulated inside every timed step)
                 seen = int((tr.grad_cnt > 0).sum().item())
@@ -787,7 +799,8 @@ def run_profile_train(args):
     sc, mlp, cams = synth.CONFIGS[args.train_workload]()
     W, H = cams[0].W, cams[0].H
     tr = Trainer(sc, mlp, W, H, ssim_lambda=0.2, sel_cap=100_000, pair_cap=2_000_000,
-                 precision=args.precision, track_view_frequency=True, track_growth=True)
+                 precision=args.precision, track_view_frequency=True, track_growth=True,
+                 track_opacity=True)
     gen = torch.Generator(device="cuda")
     gen.manual_seed(1)
     views = cams[::4][:16] if args.train_workload == "city8M_1080p" else [cams[len(cams) // 2]]

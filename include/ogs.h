@@ -11,6 +11,7 @@
  *   ogs_blend_bwd, ogs_project_bwd, ogs_decode_bwd   analytic backward (training)
  *   ogs_explicit_gaussians(_bwd)   explicit per-anchor Gaussians in place of decoding
  *   ogs_count_selected, ogs_prune_anchors, ogs_gather_rows   view-frequency pruning
+ *   ogs_opacity_accumulate, ogs_prune_by_opacity   average-opacity pruning (Sec. 4.2.2)
  *   ogs_grow_accumulate, ogs_update_lod_bias, ogs_grow_anchors   anchor growing (Sec. 4.2.1)
  *
  * Conventions shared by every entry point
@@ -468,6 +469,26 @@ ogs_status ogs_prune_anchors(const uint32_t* sel_count, int64_t N, uint32_t min_
                              size_t scratch_bytes, void* stream);
 ogs_status ogs_gather_rows(const void* src, void* dst, int64_t row_bytes, const uint32_t* idx,
                            const uint32_t* n_dev, int64_t n_cap, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Average-opacity anchor pruning (Sec. 4.2.2): anchors whose Gaussians' average opacity over
+ * the counted training views is below tau_o are removed.
+ *   ogs_opacity_accumulate: for the counts->n_selected anchors of one view's selection,
+ *   opac_sum[sel_idx[r]] += sum_i max(opac[r k + i], 0) (FP32, slots in order; opac as
+ *   written by the decoder, f32[G]) and opac_views[sel_idx[r]] += 1.  opac_sum f32[N],
+ *   opac_views u32[N] (caller zeroes).
+ *   ogs_prune_by_opacity: keep_idx u32[N] receives, in ascending order, every anchor except
+ *   those with opac_views > 0 and opac_sum / (opac_views k) < tau_o (FP32 quotient);
+ *   *n_kept (device) their number.  scratch: ogs_prune_opacity_scratch_bytes(N) bytes,
+ *   16-byte aligned.  Compact the per-anchor arrays with ogs_gather_rows.
+ * ------------------------------------------------------------------------------------- */
+ogs_status ogs_opacity_accumulate(const float* opac, const uint32_t* sel_idx,
+                                  const ogs_counts* counts, int32_t k, float* opac_sum,
+                                  uint32_t* opac_views, void* stream);
+size_t ogs_prune_opacity_scratch_bytes(int64_t N);
+ogs_status ogs_prune_by_opacity(const float* opac_sum, const uint32_t* opac_views, int64_t N,
+                                int32_t k, float tau_o, uint32_t* keep_idx, uint32_t* n_kept,
+                                void* scratch, size_t scratch_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * Learned anchor-visibility proposal (not in the paper: a gate in front of decoding).  A

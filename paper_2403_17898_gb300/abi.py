@@ -127,6 +127,9 @@ _SIGS = {
     "ogs_prune_scratch_bytes": (_SZ, [_I64]),
     "ogs_prune_anchors": (C.c_int, [_P, _I64, C.c_uint32, _P, _P, _P, _SZ, _P]),
     "ogs_gather_rows": (C.c_int, [_P, _P, _I64, _P, _P, _I64, _P]),
+    "ogs_opacity_accumulate": (C.c_int, [_P, _P, _P, _I32, _P, _P, _P]),
+    "ogs_prune_opacity_scratch_bytes": (_SZ, [_I64]),
+    "ogs_prune_by_opacity": (C.c_int, [_P, _P, _I64, _I32, C.c_float, _P, _P, _P, _SZ, _P]),
     "ogs_grow_accumulate": (C.c_int, [_P, _P, _P, _P, _I32, _I32, _I32, _P, _P, _P]),
     "ogs_update_lod_bias": (C.c_int, [_P, _P, _P, _I64, _I32, _I32, _P, C.c_float, _P, _P]),
     "ogs_grow_scratch_bytes": (_SZ, [_I64, _I32]),
@@ -512,6 +515,23 @@ def prune_anchors(sel_count, N, min_count, keep_idx, n_kept, scratch, stream=Non
     _check(lib().ogs_prune_anchors(_ptr(sel_count), int(N), int(min_count), _ptr(keep_idx),
                                    _ptr(n_kept), _ptr(scratch), scratch.numel(), _stream(stream)),
            "ogs_prune_anchors")
+
+
+def opacity_accumulate(opac, sel_idx, counts, k, opac_sum, opac_views, stream=None):
+    _check(lib().ogs_opacity_accumulate(_ptr(opac), _ptr(sel_idx), _ptr(counts), int(k),
+                                        _ptr(opac_sum), _ptr(opac_views), _stream(stream)),
+           "ogs_opacity_accumulate")
+
+
+def prune_opacity_scratch_bytes(N):
+    return int(lib().ogs_prune_opacity_scratch_bytes(int(N)))
+
+
+def prune_by_opacity(opac_sum, opac_views, N, k, tau_o, keep_idx, n_kept, scratch,
+                     stream=None):
+    _check(lib().ogs_prune_by_opacity(_ptr(opac_sum), _ptr(opac_views), int(N), int(k),
+                                      float(tau_o), _ptr(keep_idx), _ptr(n_kept), _ptr(scratch),
+                                      scratch.numel(), _stream(stream)), "ogs_prune_by_opacity")
 
 
 def _host_f32(vals):

@@ -6,6 +6,9 @@
 //   ogs_prune_anchors   order-preserving list of the anchors with count >= min_count
 //                       (count per 2048-anchor tile -> one-CTA scan -> ordered scatter)
 //   ogs_gather_rows     compacts any per-anchor array (rows of bytes) by that list
+//   ogs_opacity_accumulate, ogs_prune_by_opacity   the average-opacity rule of the same
+//                       section: anchors whose Gaussians' average opacity over the counted
+//                       views is below tau_o are removed (same compaction)
 #include "internal.cuh"
 
 namespace ogs {
@@ -100,6 +103,32 @@ __global__ void __launch_bounds__(kPrThreads) prune_scatter(const uint32_t* __re
     }
 }
 
+// Average-opacity statistic (Sec. 4.2.2): thread per selected anchor of one view adds the
+// opacities of its k Gaussians (dropped ones, opacity <= 0, as 0; summed in slot order) and
+// one view.  An anchor appears once per view: no atomics.
+__global__ void opacity_accumulate(const float* __restrict__ opac,
+                                   const uint32_t* __restrict__ sel_idx, const ogs_counts* counts,
+                                   int k, float* __restrict__ acc, uint32_t* __restrict__ views) {
+    const uint32_t M = counts->n_selected;
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < M; r += gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int i = 0; i < k; ++i) s = __fadd_rn(s, fmaxf(opac[(size_t)r * k + i], 0.f));
+        const uint32_t j = sel_idx[r];
+        acc[j] = __fadd_rn(acc[j], s);
+        views[j] += 1u;
+    }
+}
+
+// keep[j] = 0 where an anchor seen in some view has average opacity acc / (views k) < tau
+__global__ void opacity_keep(const float* __restrict__ acc, const uint32_t* __restrict__ views,
+                             int64_t N, int k, float tau, uint32_t* __restrict__ keep) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = views[j];
+        keep[j] = (v > 0 && __fdiv_rn(acc[j], (float)(v * (uint32_t)k)) < tau) ? 0u : 1u;
+    }
+}
+
 // dst row r = src row idx[r] for r < n; rows of `row` bytes, copied in 4-byte words when
 // the row size and both bases allow it
 __global__ void gather_rows(const unsigned char* __restrict__ src, unsigned char* __restrict__ dst,
@@ -165,4 +194,40 @@ extern "C" ogs_status ogs_gather_rows(const void* src, void* dst, int64_t row_by
     gather_rows<<<stride_grid(units, 256, 8), 256, 0, (cudaStream_t)stream>>>(
         (const unsigned char*)src, (unsigned char*)dst, row_bytes, idx, n_dev, n_cap, words);
     return launch_status();
+}
+
+extern "C" ogs_status ogs_opacity_accumulate(const float* opac, const uint32_t* sel_idx,
+                                             const ogs_counts* counts, int32_t k,
+                                             float* opac_sum, uint32_t* opac_views,
+                                             void* stream) {
+    if (!opac || !sel_idx || !counts || !opac_sum || !opac_views || k < 1 || k > 16)
+        return OGS_ERR_ARG;
+    opacity_accumulate<<<2 * kSmCount, 256, 0, (cudaStream_t)stream>>>(opac, sel_idx, counts, k,
+                                                                       opac_sum, opac_views);
+    return launch_status();
+}
+
+extern "C" size_t ogs_prune_opacity_scratch_bytes(int64_t N) {
+    if (N < 0) return 0;
+    const size_t flags = (sizeof(uint32_t) * (size_t)(N > 0 ? N : 1) + 255) / 256 * 256;
+    return flags + ogs_prune_scratch_bytes(N);
+}
+
+extern "C" ogs_status ogs_prune_by_opacity(const float* opac_sum, const uint32_t* opac_views,
+                                           int64_t N, int32_t k, float tau_o,
+                                           uint32_t* keep_idx, uint32_t* n_kept, void* scratch,
+                                           size_t scratch_bytes, void* stream) {
+    if (!opac_sum || !opac_views || !keep_idx || !n_kept || !scratch || N < 0 ||
+        N > 0xFFFFFFFFll || k < 1 || k > 16)
+        return OGS_ERR_ARG;
+    if (scratch_bytes < ogs_prune_opacity_scratch_bytes(N) || !aligned(scratch, 16))
+        return OGS_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t* keep = (uint32_t*)scratch;
+    const size_t flags = (sizeof(uint32_t) * (size_t)(N > 0 ? N : 1) + 255) / 256 * 256;
+    if (N > 0)
+        opacity_keep<<<stride_grid(N, 256, 8), 256, 0, st>>>(opac_sum, opac_views, N, k, tau_o,
+                                                             keep);
+    return ogs_prune_anchors(keep, N, 1u, keep_idx, n_kept, (unsigned char*)scratch + flags,
+                             scratch_bytes - flags, stream);
 }

@@ -321,7 +321,7 @@ class Trainer(Renderer):
     ``prune(tau_v)`` removes the anchors whose view frequency is below tau_v."""
 
     def __init__(self, scene, mlp, W, H, lr=1e-3, betas=(0.9, 0.999), eps=1e-15, ssim_lambda=0.0,
-                 track_view_frequency=False, track_growth=False, **kw):
+                 track_view_frequency=False, track_growth=False, track_opacity=False, **kw):
         super().__init__(scene, mlp, W, H, **kw)
         self.ssim_lambda = float(ssim_lambda)   # 0.2 gives the 0.8 L1 + 0.2 D-SSIM loss
         self.lr, self.betas, self.eps = lr, betas, eps
@@ -348,6 +348,10 @@ class Trainer(Renderer):
         # gradient norms and the number of views that saw the Gaussian
         self.track_growth = bool(track_growth)
         self._reset_growth_stats()
+        # average-opacity statistic (Sec. 4.2.2): per anchor, the summed opacity of its
+        # Gaussians and the number of training views that selected it
+        self.track_opacity = bool(track_opacity)
+        self._reset_opacity_stats()
         self._alloc_grad()
 
     def _anchor_params(self):
@@ -450,9 +454,34 @@ class Trainer(Renderer):
             if self.track_view_frequency:
                 abi.count_selected(self.sel_idx, self.counts_t, self.sel_count)
                 self.n_views_seen += 1
+            if self.track_opacity:
+                abi.opacity_accumulate(self.g["opac"], self.sel_idx, self.counts_t, self.k,
+                                       self.opac_sum, self.opac_views)
             self.backward_view(cam, tgt, bg, timers=timers)
         if update:
             self.optimizer_step(timers=timers)
+
+    def _reset_opacity_stats(self):
+        n = self.N if self.track_opacity else 0
+        self.opac_sum = torch.zeros(n, device="cuda")
+        self.opac_views = torch.zeros(n, dtype=torch.int32, device="cuda")
+
+    def prune_opacity(self, tau_o=0.005):
+        """Average-opacity pruning (Sec. 4.2.2): removes the anchors whose Gaussians' average
+        opacity over the training views counted since the last prune is below tau_o (anchors
+        no counted view selected are kept), compacting every per-anchor array and its
+        optimiser state like prune(); clears the opacity statistic.  Returns the kept count."""
+        assert self.track_opacity, "opacity pruning needs track_opacity"
+        dev = "cuda"
+        keep = torch.empty(self.N, dtype=torch.int32, device=dev)
+        n_kept = torch.zeros(1, dtype=torch.int32, device=dev)
+        scratch = torch.empty(abi.prune_opacity_scratch_bytes(self.N), dtype=torch.uint8,
+                              device=dev)
+        abi.prune_by_opacity(self.opac_sum, self.opac_views, self.N, self.k, tau_o, keep, n_kept,
+                             scratch)
+        n = self._compact(keep, n_kept)
+        self._reset_opacity_stats()
+        return n
 
     def _reset_growth_stats(self):
         dev = "cuda"
@@ -510,6 +539,9 @@ class Trainer(Renderer):
                     if not key.startswith("mlp."):
                         store[key] = torch.cat([store[key], zeros(store[key])])
             self.sel_count = torch.cat([self.sel_count, zeros(self.sel_count)])
+            if self.track_opacity:
+                self.opac_sum = torch.cat([self.opac_sum, zeros(self.opac_sum)])
+                self.opac_views = torch.cat([self.opac_views, zeros(self.opac_views)])
             self.N += n
             self.grads = {key: torch.zeros_like(t) for key, t in self._anchor_params().items()}
             self.sel_scratch = torch.empty(abi.lod_select_gated_scratch_bytes(self.N),
@@ -529,6 +561,15 @@ class Trainer(Renderer):
         n_kept = torch.zeros(1, dtype=torch.int32, device=dev)
         scratch = torch.empty(abi.prune_scratch_bytes(self.N), dtype=torch.uint8, device=dev)
         abi.prune_anchors(self.sel_count, self.N, min_count, keep, n_kept, scratch)
+        n = self._compact(keep, n_kept)
+        self.sel_count = torch.zeros(self.N, dtype=torch.int32, device=dev)
+        self.n_views_seen = 0
+        return n
+
+    def _compact(self, keep, n_kept):
+        """Keeps the anchors listed in keep[:n_kept] (ascending): every per-anchor array, its
+        optimiser state and the per-anchor statistics are gathered on the GPU."""
+        dev = "cuda"
         n = int(n_kept.item())
 
         def gather(t):
@@ -551,11 +592,13 @@ class Trainer(Renderer):
         self.grads = {k: torch.zeros_like(t) for k, t in self._anchor_params().items()}
         self._structs()
         self.N = n
-        self.sel_count = torch.zeros(self.N, dtype=torch.int32, device=dev)
-        self.n_views_seen = 0
+        self.sel_count = gather(self.sel_count)
         self.sel_scratch = torch.empty(abi.lod_select_gated_scratch_bytes(self.N),
                                        dtype=torch.uint8, device=dev)
-        if self.track_growth:              # growing statistics follow their anchors
+        if self.track_growth:              # the statistics follow their anchors
             self.grad_acc = gather(self.grad_acc)
             self.grad_cnt = gather(self.grad_cnt)
+        if self.track_opacity:
+            self.opac_sum = gather(self.opac_sum)
+            self.opac_views = gather(self.opac_views)
         return n
