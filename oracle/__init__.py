@@ -588,7 +588,33 @@ def voxel_of(p, vs):
     return tuple(int(x) for x in v)
 
 
-def grow_anchors(pos, level, offs, lv, acc, cnt, NL, tau, voxel):
+def progressive_schedule(NL, total, omega):
+    """Progressive training (Sec. 4.3): training starts with levels 0 .. floor(NL / 2) active
+    and activates one more level at a time; level i is the finest active level for N_i
+    iterations with N_{i-1} = omega N_i and the N_i summing to `total`.  Returns the list of
+    (first iteration, finest active level) stages, the last level staying active after
+    `total`.  Pinned by the sum, the ratios and the start level."""
+    s0 = NL // 2
+    levels = list(range(s0, NL))
+    n_last = float(total) / sum(float(omega) ** m for m in range(len(levels)))
+    lengths = [n_last * float(omega) ** (NL - 1 - i) for i in levels]
+    stages, start = [], 0.0
+    for i, n in zip(levels, lengths):
+        stages.append((int(round(start)), i))
+        start += n
+    return stages
+
+
+def active_level(stages, it):
+    """Finest active level at iteration `it` of a progressive schedule."""
+    lvl = stages[0][1]
+    for first, L in stages:
+        if it >= first:
+            lvl = L
+    return lvl
+
+
+def grow_anchors(pos, level, offs, lv, acc, cnt, NL, tau, voxel, next_level=True):
     """Anchor growing (Sec. 4.2.1, next-level growth).  Every Gaussian (j, i) seen in at least
     one view, with FP32 average gradient g = acc / cnt and anchor level L, proposes a voxel:
     at level L + 1 if L + 1 < NL and g > tau[L + 1], else at level L if g > tau[L], holding
@@ -597,7 +623,9 @@ def grow_anchors(pos, level, offs, lv, acc, cnt, NL, tau, voxel):
     j k + i took it first.  Returns (new_pos at the voxel centres = grid points, new_level,
     new_lv = voxel size per axis, parent = proposing anchor), in increasing proposal index.  Pinned by hand
     cases (each branch of the level rule, the finest level, occupied voxels, duplicate
-    proposals, unseen Gaussians, the centre formula) and a brute-force loop on small scenes."""
+    proposals, unseen Gaussians, the centre formula) and a brute-force loop on small scenes.
+    next_level=False grows at the Gaussian's own level only (the progressive stage of
+    Sec. 4.3 disables the next-level operator)."""
     pos = np.asarray(pos, np.float32)
     offs = np.asarray(offs, np.float32)
     lv = np.asarray(lv, np.float32)
@@ -618,7 +646,7 @@ def grow_anchors(pos, level, offs, lv, acc, cnt, NL, tau, voxel):
             if cnt[j, i] <= 0:
                 continue
             g = _avg_f32(acc[j, i], cnt[j, i])
-            if L + 1 < NL and g > np.float32(tau[L + 1]):
+            if next_level and L + 1 < NL and g > np.float32(tau[L + 1]):
                 T = L + 1
             elif g > np.float32(tau[L]):
                 T = L
@@ -648,7 +676,7 @@ def _pack_keys(T, v):
             (u[..., 1] << np.uint64(20)) | u[..., 2])
 
 
-def grow_anchors_vectorized(pos, level, offs, lv, acc, cnt, NL, tau, voxel):
+def grow_anchors_vectorized(pos, level, offs, lv, acc, cnt, NL, tau, voxel, next_level=True):
     """grow_anchors with array operations (the same FP32 steps; set membership by np.isin,
     first proposal per voxel by np.unique over proposals in index order), for scenes of
     millions of anchors.  Pinned against the loop form grow_anchors on seeded scenes."""
@@ -672,7 +700,7 @@ def grow_anchors_vectorized(pos, level, offs, lv, acc, cnt, NL, tau, voxel):
     g = np.zeros((N, k), np.float32)
     np.divide(acc, cnt.astype(np.float32), out=g, where=seen)
     Lj = np.broadcast_to(lev[:, None], (N, k))
-    up = (Lj + 1 < NL) & (g > t32[np.minimum(Lj + 1, NL - 1)])
+    up = (Lj + 1 < NL) & (g > t32[np.minimum(Lj + 1, NL - 1)]) & bool(next_level)
     same = ~up & (g > t32[Lj])
     T = np.where(up, Lj + 1, Lj)
     prop = seen & (up | same)

@@ -145,3 +145,40 @@ def test_vectorized_equals_loop_on_seeded_scenes():
         assert len(a[0]) > 100
         for x, y in zip(a, b):
             assert np.array_equal(x, y)
+
+
+def test_same_level_only_when_next_level_disabled():
+    pos, lev, o, lv, acc, cnt = _one(level=1, g=1.0, offs=(2.0, 0.0, 0.0))
+    p, L, s, par = oracle.grow_anchors(pos, lev, o, lv, acc, cnt, 4, TAU, VOX, next_level=False)
+    assert list(L) == [1]                               # above tau[2], yet stays at level 1
+    np.testing.assert_array_equal(p[0], [4.0, 2.0, 0.0])
+    sc, _, _ = synth.CONFIGS["cube4k_128"]()
+    rng = np.random.default_rng(5)
+    cnt = rng.integers(0, 3, size=(sc.N, sc.k))
+    acc = (rng.lognormal(np.log(3e-4), 0.6, size=(sc.N, sc.k)) * cnt).astype(np.float32)
+    tau, _ = oracle.grow_thresholds(2e-4, 0.2, sc.NL)
+    vox = np.asarray(sc.meta["cell"], np.float32)
+    a = oracle.grow_anchors(sc.pos, sc.level, sc.offs, sc.lv, acc, cnt, sc.NL, tau, vox, False)
+    b = oracle.grow_anchors_vectorized(sc.pos, sc.level, sc.offs, sc.lv, acc, cnt, sc.NL, tau,
+                                       vox, False)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    # every new anchor sits at its parent's level
+    assert np.array_equal(a[1], sc.level[a[3]])
+
+
+def test_progressive_schedule():
+    """Sec. 4.3: start at floor(K/2), one more level per stage, N_{i-1} = omega N_i, the
+    stage lengths summing to the progressive iterations."""
+    st = oracle.progressive_schedule(8, 10_000, 1.5)
+    assert [L for _, L in st] == [4, 5, 6, 7]
+    starts = [f for f, _ in st] + [10_000]
+    n = np.diff(starts).astype(np.float64)
+    np.testing.assert_allclose(n[:-1] / n[1:], 1.5, rtol=2e-3)
+    assert st[0][0] == 0
+    assert oracle.active_level(st, 0) == 4 and oracle.active_level(st, 9_999) == 7
+    assert oracle.active_level(st, starts[1] - 1) == 4 and oracle.active_level(st, starts[1]) == 5
+    # omega = 1: equal stages; a single level: one stage
+    n1 = np.diff([f for f, _ in oracle.progressive_schedule(6, 900, 1.0)] + [900])
+    assert list(n1) == [300, 300, 300]
+    assert oracle.progressive_schedule(1, 100, 1.5) == [(0, 0)]
