@@ -604,7 +604,8 @@ ogs_status ogs_proposal_train(const float* pos, const uint8_t* level, const floa
  *   attributes the caller copies, e.g. with ogs_gather_rows), in increasing j k + i.
  *   n_new u32[2] (device): [0] rows written = min(needed, max_new), [1] rows needed; the
  *   call is deterministic, so a caller that finds [1] > max_new grows the buffers and calls
- *   again.  tau, voxel: host float[NL].  N k < 2^32 - 1; with N = 0 the anchor arrays may be NULL.
+ *   again.  tau, voxel: host float[NL].  next_level = 0 disables the promotion to L + 1
+ *   (proposals at the Gaussian's own level only: the progressive stage of Sec. 4.3).  N k < 2^32 - 1; with N = 0 the anchor arrays may be NULL.
  *   scratch: ogs_grow_scratch_bytes(N, k) bytes, 16-byte aligned (a hash table of 2^ceil(
  *   log2(2 N (k + 1))) voxel keys at 12 bytes each, plus 12 bytes per proposal slot).
  * ------------------------------------------------------------------------------------- */
@@ -621,7 +622,8 @@ ogs_status ogs_grow_anchors(const float* pos, const uint8_t* level, const float*
                             const float* lv, const float* grad_acc, const uint32_t* grad_cnt,
                             int64_t N, int32_t k, int32_t NL,
                             const float* tau /* host float[NL] */,
-                            const float* voxel /* host float[NL] */, float* new_pos,
+                            const float* voxel /* host float[NL] */, int32_t next_level,
+                            float* new_pos,
                             uint8_t* new_level, float* new_lv, uint32_t* parent,
                             int64_t max_new, uint32_t* n_new, void* scratch,
                             size_t scratch_bytes, void* stream);

@@ -133,8 +133,8 @@ _SIGS = {
     "ogs_grow_accumulate": (C.c_int, [_P, _P, _P, _P, _I32, _I32, _I32, _P, _P, _P]),
     "ogs_update_lod_bias": (C.c_int, [_P, _P, _P, _I64, _I32, _I32, _P, C.c_float, _P, _P]),
     "ogs_grow_scratch_bytes": (_SZ, [_I64, _I32]),
-    "ogs_grow_anchors": (C.c_int, [_P, _P, _P, _P, _P, _P, _I64, _I32, _I32, _P, _P, _P, _P,
-                                   _P, _P, _I64, _P, _P, _SZ, _P]),
+    "ogs_grow_anchors": (C.c_int, [_P, _P, _P, _P, _P, _P, _I64, _I32, _I32, _P, _P, _I32, _P,
+                                   _P, _P, _P, _I64, _P, _P, _SZ, _P]),
     "ogs_version": (C.c_char_p, []),
 }
 
@@ -568,13 +568,14 @@ def grow_scratch_bytes(N, k):
 
 
 def grow_anchors(pos, level, offs, lv, grad_acc, grad_cnt, N, k, NL, tau, voxel, new_pos,
-                 new_level, new_lv, parent, max_new, n_new, scratch, stream=None):
+                 new_level, new_lv, parent, max_new, n_new, scratch, stream=None,
+                 next_level=True):
     t, tp = _host_f32(tau)
     v, vp = _host_f32(voxel)
     _check(lib().ogs_grow_anchors(_ptr(pos), _ptr(level), _ptr(offs), _ptr(lv), _ptr(grad_acc),
                                   _ptr(grad_cnt), int(N), int(k), int(NL), tp, vp,
-                                  _ptr(new_pos), _ptr(new_level), _ptr(new_lv), _ptr(parent),
-                                  int(max_new), _ptr(n_new), _ptr(scratch), scratch.numel(),
+                                  1 if next_level else 0, _ptr(new_pos), _ptr(new_level),
+                                  _ptr(new_lv), _ptr(parent), int(max_new), _ptr(n_new), _ptr(scratch), scratch.numel(),
                                   _stream(stream)), "ogs_grow_anchors")
 
 

@@ -35,6 +35,7 @@ struct GrowParams {
     float voxel[16];      // voxel size per level
     int NL;
     int k;
+    int next_level;       // 0: proposals stay at the Gaussian's own level
 };
 
 // Voxel key of point (x, y, z) on the grid of level L with spacing vs: the nearest grid point
@@ -159,7 +160,7 @@ __global__ void grow_propose(const float* __restrict__ pos, const uint8_t* __res
         if (L >= p.NL) continue;
         const float g = __fdiv_rn(acc[c], (float)n);
         int T;
-        if (L + 1 < p.NL && g > p.tau[L + 1]) T = L + 1;
+        if (p.next_level && L + 1 < p.NL && g > p.tau[L + 1]) T = L + 1;
         else if (g > p.tau[L]) T = L;
         else continue;
         float mu[3];
@@ -254,6 +255,7 @@ bool fill_params(GrowParams& p, const float* tau, const float* voxel, int32_t NL
     if (NL < 1 || NL > kMaxLevels || k < 1 || k > 16) return false;
     p.NL = NL;
     p.k = k;
+    p.next_level = 1;
     for (int L = 0; L < 16; ++L) {
         p.tau[L] = L < NL && tau ? tau[L] : 0.f;
         p.voxel[L] = L < NL && voxel ? voxel[L] : 1.f;
@@ -302,15 +304,16 @@ extern "C" size_t ogs_grow_scratch_bytes(int64_t N, int32_t k) {
 extern "C" ogs_status ogs_grow_anchors(const float* pos, const uint8_t* level, const float* offs,
                                        const float* lv, const float* grad_acc,
                                        const uint32_t* grad_cnt, int64_t N, int32_t k, int32_t NL,
-                                       const float* tau, const float* voxel, float* new_pos,
-                                       uint8_t* new_level, float* new_lv, uint32_t* parent,
-                                       int64_t max_new, uint32_t* n_new, void* scratch,
-                                       size_t scratch_bytes, void* stream) {
+                                       const float* tau, const float* voxel, int32_t next_level,
+                                       float* new_pos, uint8_t* new_level, float* new_lv,
+                                       uint32_t* parent, int64_t max_new, uint32_t* n_new,
+                                       void* scratch, size_t scratch_bytes, void* stream) {
     if (!tau || !voxel || !n_new || !scratch || N < 0 || max_new < 0) return OGS_ERR_ARG;
     if (N > 0 && (!pos || !level || !offs || !lv || !grad_acc || !grad_cnt)) return OGS_ERR_ARG;
     if (max_new > 0 && (!new_pos || !new_level || !new_lv || !parent)) return OGS_ERR_ARG;
     GrowParams p;
     if (!fill_params(p, tau, voxel, NL, k)) return OGS_ERR_ARG;
+    p.next_level = next_level != 0;
     if ((uint64_t)N * (uint64_t)k >= 0xFFFFFFFFull || table_slots(N, k) > (1ull << 31))
         return OGS_ERR_ARG;
     if (scratch_bytes < ogs_grow_scratch_bytes(N, k) || !aligned(scratch, 16)) return OGS_ERR_ARG;

@@ -141,11 +141,13 @@ class Renderer:
 
     # -- one view --------------------------------------------------------------------------
     def enqueue(self, cam, infer=True, bg=(0.0, 0.0, 0.0), maxc=None, stream=None, timers=None,
-                n_eval=None, gate=None, img=None):
+                n_eval=None, gate=None, img=None, max_level=None):
         """Enqueues the whole forward pass of one view (no host synchronisation).  If
         ``timers`` is a dict, a CUDA event pair is recorded around every stage under its name
         (on the launching stream).  ``gate = (proposal_weights, p_star)`` inserts the learned
-        anchor-visibility gate between selection and decoding."""
+        anchor-visibility gate between selection and decoding.  ``max_level`` caps the octree
+        levels the selection may use (levels above it stay inactive: the progressive training
+        of Sec. 4.3); the selection then runs as on a tree of max_level + 1 levels."""
         assert int(cam.W) == self.W and int(cam.H) == self.H
         c = abi.camera(cam)
         st = stream if stream is not None else torch.cuda.current_stream()
@@ -155,15 +157,17 @@ class Renderer:
 
         self.counts_t.zero_()
         sel, selw = self.sel_idx, self.sel_w
+        assert max_level is None or gate is None, "a level cap is a training-time setting"
+        NL = self.NL if max_level is None else max(1, min(self.NL, int(max_level) + 1))
         if gate is not None and self.precision == "bf16" and self.fuse_gate:
             net, p_star = gate
             stage("lod_select", lambda: abi.lod_select_gated(
-                self.pos, self.level, self.dL, self.feat, self.N, self.NL, self.k, c, infer,
+                self.pos, self.level, self.dL, self.feat, self.N, NL, self.k, c, infer,
                 net, p_star, self.sel_idx, self.sel_w, self.sel_cap, self.counts_t,
                 self.sel_scratch, st))
         else:
             stage("lod_select", lambda: abi.lod_select(
-                self.pos, self.level, self.dL, self.N, self.NL, self.k, c, infer, self.sel_idx,
+                self.pos, self.level, self.dL, self.N, NL, self.k, c, infer, self.sel_idx,
                 self.sel_w, self.sel_cap, self.counts_t, self.sel_scratch, st))
             if gate is not None:
                 net, p_star = gate
@@ -312,6 +316,20 @@ def min_count_for(n_views, tau_v):
     return c
 
 
+def progressive_schedule(NL, total, omega):
+    """Progressive training (Sec. 4.3): levels 0 .. NL // 2 start active and one more level
+    is activated per stage; stage i (finest active level i) lasts N_i iterations with
+    N_{i-1} = omega N_i and the N_i summing to `total`.  Returns [(first iteration, level)]."""
+    first = NL // 2
+    weights = [float(omega) ** (NL - 1 - i) for i in range(first, NL)]
+    unit = float(total) / sum(weights)
+    out, at = [], 0.0
+    for i, w in zip(range(first, NL), weights):
+        out.append((int(round(at)), i))
+        at += unit * w
+    return out
+
+
 class Trainer(Renderer):
     """One optimisation step over a batch of views: for each view the training-mode forward
     (no next-level anchors), the loss against its target, and the backward chain
@@ -321,7 +339,8 @@ class Trainer(Renderer):
     ``prune(tau_v)`` removes the anchors whose view frequency is below tau_v."""
 
     def __init__(self, scene, mlp, W, H, lr=1e-3, betas=(0.9, 0.999), eps=1e-15, ssim_lambda=0.0,
-                 track_view_frequency=False, track_growth=False, track_opacity=False, **kw):
+                 track_view_frequency=False, track_growth=False, track_opacity=False,
+                 progressive=None, **kw):
         super().__init__(scene, mlp, W, H, **kw)
         self.ssim_lambda = float(ssim_lambda)   # 0.2 gives the 0.8 L1 + 0.2 D-SSIM loss
         self.lr, self.betas, self.eps = lr, betas, eps
@@ -352,6 +371,11 @@ class Trainer(Renderer):
         # Gaussians and the number of training views that selected it
         self.track_opacity = bool(track_opacity)
         self._reset_opacity_stats()
+        # progressive training (Sec. 4.3): (iterations of the progressive stage, omega)
+        self.progressive = None
+        if progressive is not None:
+            total, omega = progressive
+            self.progressive = (int(total), progressive_schedule(self.NL, total, omega))
         self._alloc_grad()
 
     def _anchor_params(self):
@@ -425,6 +449,23 @@ class Trainer(Renderer):
                 self.grads["lv"], self._dmlp_struct, self.db_scratch, st,
                 bf16=self.precision == "bf16"))
 
+    def active_level(self):
+        """Finest octree level trained at the current iteration (all levels without a
+        progressive schedule, or once its stage is over)."""
+        if self.progressive is None:
+            return self.NL - 1
+        lvl = self.NL - 1
+        total, stages = self.progressive
+        if self.step_count < total:
+            lvl = stages[0][1]
+            for first, L in stages:
+                if self.step_count >= first:
+                    lvl = L
+        return lvl
+
+    def in_progressive_stage(self):
+        return self.progressive is not None and self.step_count < self.progressive[0]
+
     def zero_grad(self):
         for t in self.grads.values():
             t.zero_()
@@ -449,8 +490,9 @@ class Trainer(Renderer):
         them), then (optionally) the Adam update, which also clears the gradients for the next
         step; returns nothing (the summed per-view loss is left in ``self.loss``)."""
         self.loss.zero_()
+        cap = self.active_level() if self.progressive is not None else None
         for cam, tgt in zip(cams, targets):
-            self.enqueue(cam, infer=False, bg=bg, timers=timers)
+            self.enqueue(cam, infer=False, bg=bg, timers=timers, max_level=cap)
             if self.track_view_frequency:
                 abi.count_selected(self.sel_idx, self.counts_t, self.sel_count)
                 self.n_views_seen += 1
@@ -489,13 +531,17 @@ class Trainer(Renderer):
         self.grad_acc = torch.zeros(n, self.k, device=dev)
         self.grad_cnt = torch.zeros(n, self.k, dtype=torch.int32, device=dev)
 
-    def grow(self, voxel, tau_g=2e-4, beta=0.2, eps=0.01):
+    def grow(self, voxel, tau_g=2e-4, beta=0.2, eps=0.01, next_level=None):
         """Densification step of Sec. 4.2.1 from the statistics accumulated since the last one:
         the LOD-bias update (dL += eps where an anchor's average gradient exceeds 0.25 tau[L]),
         then next-level growing (new anchors in free voxels of level L or L + 1, at the voxel
         centre, l_v = voxel size, zero offsets and LOD bias, features and appearance code of
-        the proposing anchor, fresh optimiser state).  ``voxel``: voxel size per level.
-        Clears the statistics; returns the number of anchors added."""
+        the proposing anchor, fresh optimiser state).  ``voxel``: voxel size per level;
+        ``next_level`` (default: off during a progressive stage, Sec. 4.3, on otherwise)
+        allows the promotion to L + 1.  Clears the statistics; returns the number of anchors
+        added."""
+        if next_level is None:
+            next_level = not self.in_progressive_stage()
         assert self.track_growth and self.explicit is None, "growing needs track_growth"
         dev = "cuda"
         tau, thr_bias = abi.grow_thresholds(tau_g, beta, self.NL)
@@ -512,7 +558,8 @@ class Trainer(Renderer):
             parent = torch.empty(max_new, dtype=torch.int32, device=dev)
             abi.grow_anchors(self.pos, self.level, self.offs, self.lv, self.grad_acc,
                              self.grad_cnt, self.N, self.k, self.NL, tau, voxel, new_pos,
-                             new_level, new_lv, parent, max_new, n_new, scratch)
+                             new_level, new_lv, parent, max_new, n_new, scratch,
+                             next_level=next_level)
             got, need = (int(x) for x in n_new.cpu().numpy().view(np.uint32))
             if need <= max_new:
                 break

@@ -43,7 +43,7 @@ def _voxels(sc):
     return synth.voxel_sizes(sc)
 
 
-def _gpu_grow(abi, torch, sc, acc, cnt, tau, vox, max_new):
+def _gpu_grow(abi, torch, sc, acc, cnt, tau, vox, max_new, next_level=True):
     N, k = acc.shape
     scr = torch.empty(abi.grow_scratch_bytes(N, k), dtype=torch.uint8, device="cuda")
     cap = max(max_new, 1)
@@ -53,7 +53,8 @@ def _gpu_grow(abi, torch, sc, acc, cnt, tau, vox, max_new):
            torch.full((cap,), -1, dtype=torch.int32, device="cuda"))
     n_new = torch.full((2,), 7, dtype=torch.int32, device="cuda")
     abi.grow_anchors(cuda(sc.pos), cuda(sc.level), cuda(sc.offs), cuda(sc.lv), cuda(acc),
-                     cuda(cnt.astype(np.int32)), N, k, sc.NL, tau, vox, *out, max_new, n_new, scr)
+                     cuda(cnt.astype(np.int32)), N, k, sc.NL, tau, vox, *out, max_new, n_new, scr,
+                     next_level=next_level)
     torch.cuda.synchronize()
     n, need = (int(x) for x in n_new.cpu().numpy().view(np.uint32))
     p, L, s, par = (t.cpu().numpy() for t in out)
@@ -209,3 +210,50 @@ def test_trainer_grows_and_keeps_training(abi, torch):
     c = tr.counts()
     assert c.overflow == 0 and c.timeout == 0
     assert tr.grad_cnt.sum().item() > 0
+
+
+def test_grow_without_next_level_matches_oracle(abi, torch):
+    """The progressive stage (Sec. 4.3) grows at the Gaussian's own level only."""
+    sc, _, _ = synth.CONFIGS["cube4k_128"]()
+    tau, _ = oracle.grow_thresholds(2e-4, 0.2, sc.NL)
+    vox = _voxels(sc)
+    acc, cnt = _stats(sc.N, sc.k, 8, tau[1])
+    ref = oracle.grow_anchors(sc.pos, sc.level, sc.offs, sc.lv, acc, cnt, sc.NL, tau, vox,
+                              next_level=False)
+    n, need, *got = _gpu_grow(abi, torch, sc, acc, cnt, tau, vox, sc.N * sc.k, next_level=False)
+    assert n == need == len(ref[0]) > 100
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
+
+
+def test_progressive_training_caps_the_levels(abi, torch):
+    """Progressive training (Sec. 4.3): the Trainer's schedule matches the oracle's, each
+    step selects only anchors up to the active level (the selection of a capped tree equals
+    the oracle's selection on that tree), and growing has no next-level promotion while the
+    stage lasts."""
+    from paper_2403_17898_gb300.render import Trainer, progressive_schedule
+    sc, mlp, cams = synth.CONFIGS["cube4k_128"]()
+    assert progressive_schedule(8, 10_000, 1.5) == oracle.progressive_schedule(8, 10_000, 1.5)
+    cam = cams[0]
+    tr = Trainer(sc, mlp, 128, 128, progressive=(4, 1.5), track_growth=True)
+    st = oracle.progressive_schedule(sc.NL, 4, 1.5)
+    tgt = [torch.rand(3, 128, 128, device="cuda")]
+    seen = []
+    for it in range(6):
+        L = tr.active_level()
+        assert L == (oracle.active_level(st, it) if it < 4 else sc.NL - 1)
+        assert tr.in_progressive_stage() == (it < 4)
+        tr.train_step([cam], tgt)
+        sel = tr.sel_idx[:tr.counts().n_selected].cpu().numpy()
+        assert sc.level[sel].max() <= L
+        # the same kept set as the oracle's selection on a tree of L + 1 levels, away from
+        # knife-edge decisions
+        idx, _, margin = oracle.lod_select(sc.pos, sc.level, sc.dL, L + 1, cam, False)
+        sure = margin >= 1e-4
+        ref = np.zeros(sc.N, bool)
+        ref[idx] = True
+        mine = np.zeros(sc.N, bool)
+        mine[sel] = True
+        assert np.array_equal(ref[sure], mine[sure])
+        seen.append(L)
+    assert seen[0] == sc.NL // 2 and seen[-1] == sc.NL - 1
