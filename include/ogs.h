@@ -543,6 +543,8 @@ ogs_status ogs_proposal_gate_bf16(const float* pos, const uint8_t* level, const 
  *   pos, level, dL, N, NL, k, cam, infer: as ogs_lod_select; feat f32[N][32] (16-byte
  *   aligned), net, p_star: as ogs_proposal_gate_bf16
  *   scratch: ogs_lod_select_gated_scratch_bytes(N) bytes, 16-byte aligned.
+ *   counts: every field is reset to zero by the call before anything else writes it (the
+ *   start of a frame's counters; the caller need not clear them).
  * On a tensor-core wait that does not complete, counts->timeout is set (that tile's anchors
  * keep their LOD selection). */
 size_t ogs_lod_select_gated_scratch_bytes(int64_t N);

@@ -452,7 +452,16 @@ extern "C" ogs_status ogs_lod_select_gated(const float* pos, const uint8_t* leve
     uint32_t* tile_count = cv.take<uint32_t>((size_t)nb);
     float* wsel = cv.take<float>((size_t)(N > 0 ? N : 1));
     unsigned char* img = cv.take<unsigned char>(gate::kGImgBytes);
-    if (gate::pack_image(*net, img, nullptr, 0, st) != OGS_OK) return OGS_ERR_CUDA;
+    // the packing launch also resets the frame's counters, so no separate clear runs first
+    static_assert(sizeof(ogs_counts) % 8 == 0, "counters cleared as 64-bit words");
+    if (aligned(counts, 8)) {
+        if (gate::pack_image(*net, img, reinterpret_cast<unsigned long long*>(counts),
+                             (int)(sizeof(ogs_counts) / 8), st) != OGS_OK)
+            return OGS_ERR_CUDA;
+    } else {
+        if (cudaMemsetAsync(counts, 0, sizeof(ogs_counts), st) != cudaSuccess) return OGS_ERR_CUDA;
+        if (gate::pack_image(*net, img, nullptr, 0, st) != OGS_OK) return OGS_ERR_CUDA;
+    }
     if (cudaFuncSetAttribute(select_eval_gated, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kSgSmem) != cudaSuccess)
         return OGS_ERR_CUDA;

@@ -155,11 +155,13 @@ class Renderer:
         def stage(name, fn):
             _stage(timers, name, st, fn)
 
-        self.counts_t.zero_()
+        fused_gate = gate is not None and self.precision == "bf16" and self.fuse_gate
+        if not fused_gate:               # the gated selection resets the counters itself
+            self.counts_t.zero_()
         sel, selw = self.sel_idx, self.sel_w
         assert max_level is None or gate is None, "a level cap is a training-time setting"
         NL = self.NL if max_level is None else max(1, min(self.NL, int(max_level) + 1))
-        if gate is not None and self.precision == "bf16" and self.fuse_gate:
+        if fused_gate:
             net, p_star = gate
             stage("lod_select", lambda: abi.lod_select_gated(
                 self.pos, self.level, self.dL, self.feat, self.N, NL, self.k, c, infer,

@@ -4,7 +4,8 @@ same weights, and the same counts.  Both compute the gate with the same tensor-c
 code, so the keep decisions must agree exactly, including at p*.  The two calls are pinned to
 the FP64 oracle by test_gpu_parity and test_gpu_proposal.  Cases: full 2048-anchor tiles read
 by bulk copies (4096-anchor cube, 2M-anchor city), a ragged last tile, arrays that are not
-16-byte aligned (plain loads), several networks and thresholds, and an empty view."""
+16-byte aligned (plain loads), several networks and thresholds, and an empty view; the fused
+call starts from stale counters, which it must reset."""
 import numpy as np
 import pytest
 
@@ -48,7 +49,8 @@ def _fused(abi, arrs, N, NL, cam, net, p_star, cap):
     pos, level, dL, feat = arrs
     sel = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
     w = torch.zeros(cap, device="cuda")
-    ct = torch.zeros(8, dtype=torch.int32, device="cuda")
+    # stale counters from an earlier frame: the call resets every field itself
+    ct = torch.full((8,), 0x5A5A, dtype=torch.int32, device="cuda")
     scr = torch.empty(abi.lod_select_gated_scratch_bytes(N), dtype=torch.uint8, device="cuda")
     abi.lod_select_gated(pos, level, dL, feat, N, NL, 10, cam, True, net, p_star, sel, w, cap,
                          ct, scr)
