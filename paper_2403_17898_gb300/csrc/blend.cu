@@ -19,7 +19,7 @@ namespace {
 
 using namespace blend;
 
-constexpr int kExitEvery = 8;    // records walked between two warp-wide saturation checks
+constexpr int kExitEvery = 32;   // records walked between two warp-wide saturation checks
 
 // One pixel's compositing step with Gaussian `idx - 1` of the list, branch-free.  Returns the
 // weight alpha T added to the pixel (0 when it skipped the Gaussian or saturated on it).
