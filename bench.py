@@ -242,8 +242,8 @@ LAUNCHES = {"lod_select": 3, "lod_select_gated": 4, "decode_project": 2, "sort":
             "blend_fwd": 1}
 DPSNR_GATE_DB = 0.05
 # DRAM bytes (read + write) of one blend_fwd launch from an ncu capture of the same kernel
-# (pose 14 of the path, profiles/blend_fwd_city2M_1080p.md): 31.72 MB + 2.42 MB
-BLEND_FWD_DRAM_BYTES = 34.14e6
+# (pose 14 of the path, profiles/blend_fwd_city2M_1080p.md): 31.72 MB + 2.33 MB
+BLEND_FWD_DRAM_BYTES = 34.05e6
 
 
 def _time_form(rd, cams, pose, steps, warmup, gate, flush, clk_index):

@@ -10,7 +10,7 @@
 // skips the Gaussian (or saturates on it) adds a zero weight and keeps its transmittance, which
 // leaves its sums bit-for-bit as a skipped update would.  Lanes of a warp therefore never
 // diverge inside the walk.  A warp stops walking once all its pixels have saturated (checked
-// every few records) and the CTA stops loading batches once all of its pixels have.  The
+// every 128 records) and the CTA stops loading batches once all of its pixels have.  The
 // kernel is bound by instruction issue (FP32 + MUFU), not by memory.
 #include "blend_common.cuh"
 
@@ -19,7 +19,7 @@ namespace {
 
 using namespace blend;
 
-constexpr int kExitEvery = 32;   // records walked between two warp-wide saturation checks
+constexpr int kExitEvery = 128;  // records walked between two warp-wide saturation checks
 
 // One pixel's compositing step with Gaussian `idx - 1` of the list, branch-free.  Returns the
 // weight alpha T added to the pixel (0 when it skipped the Gaussian or saturated on it).
