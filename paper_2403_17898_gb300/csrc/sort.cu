@@ -257,7 +257,6 @@ constexpr int kSmallSort = 2048;         // lists up to this length: one small C
 constexpr int kLargeThreads = 512;
 constexpr int kLargeSort = 16384;        // longer lists: 128 KB of keys in dynamic shared memory
 constexpr int kLargeGrid = 152;          // CTAs looping over the long lists
-constexpr int kScanSmemTiles = 8192;     // tile counts staged in shared memory by the scan
 
 __device__ __forceinline__ void rect_of(uint2 r, uint32_t& x0, uint32_t& y0, uint32_t& x1,
                                         uint32_t& y1) {
@@ -342,104 +341,84 @@ __global__ void __launch_bounds__(kBinThreads) bin_count(const uint32_t* __restr
     });
 }
 
-// Exclusive scan of the tile counts (one block, each thread a run of consecutive tiles): tile
-// ranges, P, overflow state, and the list of tiles too long for the small sorter.
-__global__ void __launch_bounds__(1024) tile_scan(const uint32_t* __restrict__ tcount, int ntiles,
-                                                  int64_t pair_cap, uint2* __restrict__ range,
-                                                  uint32_t* __restrict__ cursor,
-                                                  uint32_t* __restrict__ big,
-                                                  uint32_t* __restrict__ nbig,
-                                                  ogs_counts* counts) {
+// Exclusive scan of the tile counts: one CTA per kScanChunk consecutive tiles (one tile per
+// thread).  Each CTA sums every count itself (the total decides the overflow state; the part
+// before its chunk is its offset: a few thousand words from L2), then scans its chunk: tile
+// ranges, fill cursors cleared, and the chunk's tiles too long for the small sorter listed in
+// the chunk's slot of `big` (count in nbig[chunk]), so no counter needs clearing first.  CTA 0
+// writes P and the overflow state.
+constexpr int kScanChunk = 1024;
+
+__global__ void __launch_bounds__(kScanChunk) tile_scan(const uint32_t* __restrict__ tcount,
+                                                        int ntiles, int64_t pair_cap,
+                                                        uint2* __restrict__ range,
+                                                        uint32_t* __restrict__ cursor,
+                                                        uint32_t* __restrict__ big,
+                                                        uint32_t* __restrict__ nbig,
+                                                        ogs_counts* counts) {
     pdl_wait();
     pdl_trigger();
-    __shared__ unsigned long long ws[32];
+    __shared__ unsigned long long s_red[2][kScanChunk / 32];
     __shared__ uint32_t s_nbig;
-    __shared__ __align__(16) uint32_t s_cnt[kScanSmemTiles];
-    static_assert(kScanSmemTiles == 1024 * 8, "staged scan: eight counts per thread");
-    const bool staged = ntiles <= kScanSmemTiles;
-    if (staged)   // zero-padded to 8192 slots: thread t owns slots [8t, 8t + 8)
-        for (int b = threadIdx.x; b < kScanSmemTiles; b += 1024)
-            s_cnt[b] = b < ntiles ? tcount[b] : 0u;
-    if (threadIdx.x == 0) s_nbig = 0;
-    __syncthreads();
-    const int per = staged ? 8 : (ntiles + 1023) / 1024;
-    const int b0 = threadIdx.x * per, b1 = min(b0 + per, ntiles);
-    uint32_t v8[8];
-    unsigned long long local = 0;
-    if (staged) {
-        // two 16-byte shared loads per thread instead of eight strided words
-        const uint4 u0 = reinterpret_cast<const uint4*>(s_cnt)[2 * threadIdx.x];
-        const uint4 u1 = reinterpret_cast<const uint4*>(s_cnt)[2 * threadIdx.x + 1];
-        v8[0] = u0.x; v8[1] = u0.y; v8[2] = u0.z; v8[3] = u0.w;
-        v8[4] = u1.x; v8[5] = u1.y; v8[6] = u1.z; v8[7] = u1.w;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) local += v8[i];
-    } else {
-        for (int b = b0; b < b1; ++b) local += tcount[b];
+    const int t = threadIdx.x, lane = (int)lane_id(), warp = t >> 5;
+    const int c0 = blockIdx.x * kScanChunk;
+    if (t == 0) s_nbig = 0;
+    // totals: before the chunk, and over all tiles
+    unsigned long long before = 0, all = 0;
+    for (int b = t; b < ntiles; b += kScanChunk) {
+        const uint32_t v = tcount[b];
+        all += v;
+        before += b < c0 ? v : 0;
     }
-    unsigned long long x = local;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        before += __shfl_xor_sync(0xffffffffu, before, o);
+        all += __shfl_xor_sync(0xffffffffu, all, o);
+    }
+    if (lane == 0) {
+        s_red[0][warp] = before;
+        s_red[1][warp] = all;
+    }
+    // the chunk's own counts, inclusive scan within each warp
+    const int b = c0 + t;
+    const uint32_t v = b < ntiles ? tcount[b] : 0u;
+    unsigned long long x = v;
+#pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane_id() >= (unsigned)o) x += y;
-    }
-    if (lane_id() == 31) ws[threadIdx.x >> 5] = x;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        unsigned long long w = ws[threadIdx.x];
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane_id() >= (unsigned)o) w += y;
-        }
-        ws[threadIdx.x] = w;                         // inclusive warp totals
+        if (lane >= o) x += y;
     }
     __syncthreads();
-    const unsigned long long P = ws[31];
+    unsigned long long off = 0, P = 0;
+#pragma unroll 8
+    for (int w = 0; w < kScanChunk / 32; ++w) {
+        off += s_red[0][w];
+        P += s_red[1][w];
+    }
+    __syncthreads();                                  // s_red reused for the warp totals
+    if (lane == 31) s_red[0][warp] = x;
+    __syncthreads();
+    unsigned long long wbefore = 0;
+    for (int w = 0; w < warp; ++w) wbefore += s_red[0][w];
     const bool over = P > (unsigned long long)pair_cap;
-    const unsigned long long run0 = (threadIdx.x >= 32 ? ws[(threadIdx.x >> 5) - 1] : 0) + x - local;
-    if (staged) {
-        // exclusive offsets back into shared memory, then coalesced writes
-        unsigned long long run = run0;
-        uint32_t o8[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            o8[i] = (uint32_t)run;
-            if (!over && v8[i] > (uint32_t)kSmallSort)   // padding slots hold 0: never long
-                big[atomicAdd(&s_nbig, 1u)] = (uint32_t)(b0 + i);
-            run += v8[i];
-        }
-        reinterpret_cast<uint4*>(s_cnt)[2 * threadIdx.x] = make_uint4(o8[0], o8[1], o8[2], o8[3]);
-        reinterpret_cast<uint4*>(s_cnt)[2 * threadIdx.x + 1] =
-            make_uint4(o8[4], o8[5], o8[6], o8[7]);
-        __syncthreads();
-        for (int b = threadIdx.x; b < ntiles; b += 1024) {
-            const uint32_t st = s_cnt[b];
-            const uint32_t en = b + 1 < ntiles ? s_cnt[b + 1] : (uint32_t)P;
-            range[b] = over ? make_uint2(0, 0) : make_uint2(st, en);
-            cursor[b] = 0;
-        }
-    } else {
-        unsigned long long run = run0;
-        for (int b = b0; b < b1; ++b) {
-            const uint32_t v = tcount[b];
-            if (over) {                              // no pairs are emitted: every range empty
-                range[b] = make_uint2(0, 0);
-            } else {
-                range[b] = make_uint2((uint32_t)run, (uint32_t)(run + v));
-                if (v > (uint32_t)kSmallSort) big[atomicAdd(&s_nbig, 1u)] = (uint32_t)b;
-            }
-            cursor[b] = 0;
-            run += v;
-        }
+    if (b < ntiles) {
+        const unsigned long long st = off + wbefore + x - v;
+        range[b] = over ? make_uint2(0, 0) : make_uint2((uint32_t)st, (uint32_t)(st + v));
+        cursor[b] = 0;
+        if (!over && v > (uint32_t)kSmallSort)
+            big[c0 + atomicAdd(&s_nbig, 1u)] = (uint32_t)b;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        *nbig = s_nbig;
-        counts->need_pairs = (uint32_t)(P > 0xFFFFFFFFull ? 0xFFFFFFFFull : P);
-        if (over) {
-            atomicOr(&counts->overflow, 2u);
-            counts->n_pairs = 0;
-        } else {
-            counts->n_pairs = (uint32_t)P;
+    if (t == 0) {
+        nbig[blockIdx.x] = s_nbig;
+        if (blockIdx.x == 0) {
+            counts->need_pairs = (uint32_t)(P > 0xFFFFFFFFull ? 0xFFFFFFFFull : P);
+            if (over) {
+                atomicOr(&counts->overflow, 2u);
+                counts->n_pairs = 0;
+            } else {
+                counts->n_pairs = (uint32_t)P;
+            }
         }
     }
 }
@@ -606,10 +585,12 @@ __global__ void __launch_bounds__(kSmallThreads, 10) tile_sort_small(const uint2
     sort_in_smem(s_k, r, keys, ids);
 }
 
-// kLargeGrid CTAs loop over the tiles listed as long by tile_scan
+// kLargeGrid CTAs loop over the long tiles listed per scan chunk (chunk c: big[c * kScanChunk
+// .. + nbig[c]]), in chunk order
 __global__ void __launch_bounds__(kLargeThreads) tile_sort_large(const uint2* __restrict__ range,
                                                                  const uint32_t* __restrict__ big,
                                                                  const uint32_t* __restrict__ nbig,
+                                                                 int nchunks,
                                                                  const ogs_counts* counts,
                                                                  uint32_t* __restrict__ keys,
                                                                  uint32_t* __restrict__ ids) {
@@ -617,9 +598,12 @@ __global__ void __launch_bounds__(kLargeThreads) tile_sort_large(const uint2* __
     pdl_trigger();
     extern __shared__ unsigned long long s_k[];
     if (counts->overflow & 2u) return;
-    const uint32_t n = *nbig;
+    uint32_t n = 0;
+    for (int c = 0; c < nchunks; ++c) n += nbig[c];
     for (uint32_t q = blockIdx.x; q < n; q += gridDim.x) {
-        const uint2 r = range[big[q]];
+        uint32_t c = 0, i = q;
+        while (i >= nbig[c]) i -= nbig[c++];
+        const uint2 r = range[big[c * kScanChunk + i]];
         const uint32_t cnt = r.y - r.x;
         if (cnt <= (uint32_t)kLargeSort) {
             sort_in_smem(s_k, r, keys, ids);
@@ -650,8 +634,9 @@ size_t sort_layout(int64_t pair_cap, int n_tiles, void* base, SortScratch* s) {
     SortScratch t;
     t.tcount = cv.take<uint32_t>(n_tiles > 0 ? n_tiles : 1);
     t.cursor = cv.take<uint32_t>(n_tiles > 0 ? n_tiles : 1);
-    t.big = cv.take<uint32_t>(n_tiles > 0 ? n_tiles : 1);
-    t.nbig = cv.take<uint32_t>(1);
+    const int nchunks = n_tiles > 0 ? (n_tiles + kScanChunk - 1) / kScanChunk : 1;
+    t.big = cv.take<uint32_t>((size_t)nchunks * kScanChunk);
+    t.nbig = cv.take<uint32_t>(nchunks);
     t.keys = cv.take<uint32_t>(pair_cap > 0 ? pair_cap : 1);
     if (s) *s = t;
     return cv.off + 256;
@@ -714,8 +699,10 @@ extern "C" ogs_status ogs_sort(const uint32_t* depth_key, const uint32_t* rect, 
     if (nb < 1) nb = 1;
     const uint2* rc = reinterpret_cast<const uint2*>(rect);
     if (!tile_count) bin_count<<<nb, kBinThreads, 0, st>>>(tiles, rc, n_dev, n_cap, grid_x, s.tcount);
-    launch_pdl(tile_scan, dim3(1), dim3(1024), 0, st, tile_count ? tile_count : s.tcount,
-               n_tiles, pair_cap, range, s.cursor, s.big, s.nbig, counts);
+    const int nchunks = (n_tiles + kScanChunk - 1) / kScanChunk;
+    launch_pdl(tile_scan, dim3(nchunks), dim3(kScanChunk), 0, st,
+               tile_count ? tile_count : s.tcount, n_tiles, pair_cap, range, s.cursor, s.big,
+               s.nbig, counts);
     launch_pdl(bin_fill, dim3(nb), dim3(kBinThreads), 0, st, tiles, rc, depth_key, n_dev, n_cap,
                grid_x, range, s.cursor, counts, s.keys, pair_gauss);
     launch_pdl(tile_sort_small, dim3(n_tiles), dim3(kSmallThreads), 0, st,
@@ -725,7 +712,7 @@ extern "C" ogs_status ogs_sort(const uint32_t* depth_key, const uint32_t* rect, 
                              (int)smem) != cudaSuccess)
         return OGS_ERR_CUDA;
     launch_pdl(tile_sort_large, dim3(kLargeGrid), dim3(kLargeThreads), smem, st, range, s.big,
-               s.nbig, counts, s.keys, pair_gauss);
+               s.nbig, nchunks, counts, s.keys, pair_gauss);
     return launch_status();
 }
 
@@ -783,6 +770,10 @@ extern "C" ogs_status ogs_radix_sort_pairs_noalloc(uint32_t* keys, uint32_t* val
     if (bit_lo < 0 || bit_hi > 32 || bit_lo >= bit_hi) return OGS_ERR_ARG;
     if (n_cap > kNoAllocMaxItems) return OGS_ERR_CAPACITY;
     if (n_cap == 0) return OGS_OK;
+    // rs_layout's size includes 256 bytes of slack for an unaligned base; the array is
+    // 256-byte aligned, so the carve needs the rest.  This ties the fixed array to the carve:
+    // a layout that grows beyond it is refused instead of writing past the array.
+    if (rs_layout(n_cap, nullptr, nullptr) - 256 > kNoAllocBytes) return OGS_ERR_CAPACITY;
     void* base = nullptr;
     ogs_status st = noalloc_scratch(&base);
     if (st != OGS_OK) return st;

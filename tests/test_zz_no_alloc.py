@@ -40,6 +40,33 @@ def test_noalloc_sort_matches_regular_sort_twice():
         assert np.array_equal(to_np_u32(vt), to_np_u32(v_ref))
 
 
+def test_noalloc_sort_device_count_matches_regular_sort():
+    """A device-side item count below n_cap (how the renderer passes its counts): both entry
+    points sort the first 123457 of 300001 entries the same way and leave the rest as it was."""
+    import torch
+    abi = lib_ready()
+    L = abi.lib()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    n_cap, n = 300_001, 123_457
+    keys, vals = synth.random_sort_keys(13, n_cap, bits=32, dup_frac=0.3)
+    n_dev = cuda(np.array([n], np.int32))
+    kr, vr = cuda(keys.view(np.int32)), cuda(vals.view(np.int32))
+    scr = torch.empty(abi.radix_sort_scratch_bytes(n_cap), dtype=torch.uint8, device="cuda")
+    abi.radix_sort_pairs(kr, vr, n_dev, n_cap, 0, 32, scr)
+    for _ in range(2):
+        kt, vt = cuda(keys.view(np.int32)), cuda(vals.view(np.int32))
+        st = L.ogs_radix_sort_pairs_noalloc(ctypes.c_void_p(kt.data_ptr()),
+                                            ctypes.c_void_p(vt.data_ptr()),
+                                            ctypes.c_void_p(n_dev.data_ptr()), n_cap, 0, 32,
+                                            stream)
+        assert st == 0
+        torch.cuda.synchronize()
+        assert np.array_equal(to_np_u32(kt), to_np_u32(kr))
+        assert np.array_equal(to_np_u32(vt), to_np_u32(vr))
+        assert np.array_equal(to_np_u32(vt)[n:], vals[n:])
+        assert np.array_equal(to_np_u32(kt)[n:], keys[n:])
+
+
 def test_noalloc_sort_rejects_oversized_requests():
     import torch
     abi = lib_ready()
