@@ -2,11 +2,16 @@
 // opacity blending of the next level, followed by an order-preserving compaction.
 //
 // HBM-bound streaming pass over the anchor SoA (pos 12 B + level 1 B + dL 4 B per anchor),
-// read once, then an order-preserving compaction: each CTA stages one tile of anchors in
-// shared memory with TMA bulk copies (so the whole tile's bytes are in flight at once) and
-// writes every anchor's weight (4 B) and the tile's kept count; one CTA scans the counts; the
-// scatter re-reads only the weights, ranks kept anchors with warp scans and writes them in
-// ascending anchor order.  No CTA waits on another, so every tile streams at full rate.
+// read once, in two kernels:
+//   select_tiles  persistent CTAs (three per SM) walk 2048-anchor tiles; each tile's arrays
+//                 land in shared memory by TMA bulk copies, double-buffered so that the next
+//                 tile's copy is in flight while the current one is evaluated; the tile's kept
+//                 anchors (index and weight) are written compacted, in ascending order, to the
+//                 tile's slot of a staging area, with the tile's count;
+//   select_emit   one CTA per tile sums the counts of the tiles before it (its output offset)
+//                 and copies its staged entries into place; tile 0 also writes the totals.
+// No CTA waits on another, so every tile streams at full rate, and only kept anchors (a few
+// percent) are written twice.
 #include "gate_common.cuh"
 
 namespace ogs {
@@ -57,60 +62,135 @@ __device__ __forceinline__ bool keep_anchor(const SelArgs& a, float px, float py
     return false;
 }
 
-// Pass 1 (tile of kSelChunk anchors per CTA): the tile's anchor SoA lands in shared memory by
-// three TMA bulk copies (plain loads for a partial tile or unaligned arrays); the predicate
-// writes each anchor's opacity weight (0 = not kept, kept weights are > 0) and the tile's
-// kept count.
-__global__ void __launch_bounds__(kSelThreads) select_eval(SelArgs a, float* __restrict__ wsel,
-                                                           uint32_t* __restrict__ tile_count,
-                                                           ogs_counts* counts, int bulk) {
-    pdl_wait();
-    pdl_trigger();
-    __shared__ __align__(16) float s_pos[3 * kSelChunk];
-    __shared__ __align__(16) float s_dl[kSelChunk];
-    __shared__ __align__(16) uint8_t s_lvl[kSelChunk];
-    __shared__ __align__(8) uint64_t mbar;
-    __shared__ uint32_t s_wc[kSelWarps];
-    const int64_t base = (int64_t)blockIdx.x * kSelChunk;
-    const int n_here = (int)min((int64_t)kSelChunk, a.N - base);
-    if (bulk && n_here == kSelChunk) {
-        if (threadIdx.x == 0) {
-            tc::mbar_init(&mbar, 1);
-            tc::mbar_expect_tx(&mbar, (3 * 4 + 4 + 1) * kSelChunk);
-            tc::bulk_load(s_pos, a.pos + 3 * base, 3 * 4 * kSelChunk, &mbar);
-            tc::bulk_load(s_dl, a.dL + base, 4 * kSelChunk, &mbar);
-            tc::bulk_load(s_lvl, a.level + base, kSelChunk, &mbar);
+// Writes a tile's kept anchors compacted in ascending order: item `it` of thread t is anchor
+// it * kSelThreads + t of the tile, so the order is (item, warp, lane); keep/w of each item
+// come from registers.  s_wc[kSelItems][kSelWarps] is scratch; ends with a barrier.
+__device__ __forceinline__ uint32_t stage_tile(const bool (&keep)[kSelItems],
+                                               const float (&wv)[kSelItems], int64_t base,
+                                               uint32_t* __restrict__ st_idx,
+                                               float* __restrict__ st_w,
+                                               uint32_t (*s_wc)[kSelWarps]) {
+    const int t = threadIdx.x;
+    const unsigned warp = t >> 5, lane = lane_id();
+    uint32_t bal[kSelItems];
+#pragma unroll
+    for (int it = 0; it < kSelItems; ++it) {
+        bal[it] = __ballot_sync(0xffffffffu, keep[it]);
+        if (lane == 0) s_wc[it][warp] = __popc(bal[it]);
+    }
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+#pragma unroll
+    for (int it = 0; it < kSelItems; ++it) {
+        uint32_t in_item = 0, warps_before = 0;
+#pragma unroll
+        for (int w = 0; w < kSelWarps; ++w) {
+            const uint32_t c = s_wc[it][w];
+            warps_before += w < (int)warp ? c : 0;
+            in_item += c;
         }
-        __syncthreads();                              // barrier initialised before anyone polls
-        if (!tc::mbar_wait(&mbar, 0, kSpinLimit)) {
+        if (keep[it]) {
+            const uint32_t r = before + warps_before + __popc(bal[it] & lanemask_lt());
+            st_idx[r] = (uint32_t)(base + it * kSelThreads + t);
+            st_w[r] = wv[it];
+        }
+        before += in_item;
+    }
+    total = before;
+    __syncthreads();                                  // s_wc free for the next tile
+    return total;
+}
+
+// Pass 1: persistent CTAs walk the tiles tile = blockIdx.x + i * gridDim.x.  Full tiles of
+// aligned arrays arrive by three bulk copies into one of two shared-memory stages: the copy of
+// tile i + 1 is issued before tile i is evaluated (its stage was released by the barrier that
+// ended tile i - 1).  Partial tiles and unaligned arrays use plain loads.
+constexpr int kStStageBytes = (3 * 4 + 4 + 1) * kSelChunk;      // pos, dL, level
+constexpr int kStSmem = 2 * kStStageBytes;
+
+struct Stage {
+    float* pos;
+    float* dl;
+    uint8_t* lvl;
+};
+
+__device__ __forceinline__ Stage stage_of(unsigned char* sm, int s) {
+    unsigned char* b = sm + s * kStStageBytes;
+    return Stage{reinterpret_cast<float*>(b), reinterpret_cast<float*>(b + 12 * kSelChunk),
+                 b + 16 * kSelChunk};
+}
+
+__device__ __forceinline__ void issue_tile(const SelArgs& a, int64_t tile, const Stage& st,
+                                           uint64_t* mbar) {
+    const int64_t base = tile * kSelChunk;
+    tc::mbar_expect_tx(mbar, kStStageBytes);
+    tc::bulk_load(st.pos, a.pos + 3 * base, 3 * 4 * kSelChunk, mbar);
+    tc::bulk_load(st.dl, a.dL + base, 4 * kSelChunk, mbar);
+    tc::bulk_load(st.lvl, a.level + base, kSelChunk, mbar);
+}
+
+// Waits for a tile's copies (bounded; on expiry flags the timeout and waits once more, as the
+// copies may still be landing) or loads a partial / unaligned tile with plain loads.
+// `phases` holds the parity to wait for of stage s in bit s.
+__device__ __forceinline__ void land_tile(const SelArgs& a, int64_t base, int n_here, bool full,
+                                          const Stage& st, uint64_t* mbar, int s,
+                                          uint32_t& phases, ogs_counts* counts) {
+    if (full) {
+        const uint32_t parity = (phases >> s) & 1u;
+        if (!tc::mbar_wait(mbar, parity, kSpinLimit)) {
             if (threadIdx.x == 0) atomicExch(&counts->timeout, 1u);
-            tc::mbar_wait(&mbar, 0, kSpinLimit);      // copies may still be landing
+            tc::mbar_wait(mbar, parity, kSpinLimit);
         }
+        phases ^= 1u << s;
     } else {
-        for (int e = threadIdx.x; e < 3 * n_here; e += kSelThreads) s_pos[e] = a.pos[3 * base + e];
+        for (int e = threadIdx.x; e < 3 * n_here; e += kSelThreads) st.pos[e] = a.pos[3 * base + e];
         for (int e = threadIdx.x; e < n_here; e += kSelThreads) {
-            s_dl[e] = a.dL[base + e];
-            s_lvl[e] = a.level[base + e];
+            st.dl[e] = a.dL[base + e];
+            st.lvl[e] = a.level[base + e];
         }
         __syncthreads();
     }
-    uint32_t mine = 0;
-#pragma unroll
-    for (int it = 0; it < kSelItems; ++it) {
-        const int l = it * kSelThreads + threadIdx.x;
-        float w = 0.0f;
-        const bool keep = l < n_here && keep_anchor(a, s_pos[3 * l], s_pos[3 * l + 1],
-                                                    s_pos[3 * l + 2], s_lvl[l], s_dl[l], w);
-        if (l < n_here) wsel[base + l] = keep ? w : 0.0f;
-        mine += __popc(__ballot_sync(0xffffffffu, keep));
+}
+
+__global__ void __launch_bounds__(kSelThreads, 3) select_tiles(SelArgs a,
+                                                               uint32_t* __restrict__ st_idx,
+                                                               float* __restrict__ st_w,
+                                                               uint32_t* __restrict__ tile_count,
+                                                               ogs_counts* counts, int bulk) {
+    pdl_wait();
+    pdl_trigger();
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t s_wc[kSelItems][kSelWarps];
+    const int t = threadIdx.x;
+    const int64_t nb = (a.N + kSelChunk - 1) / kSelChunk;
+    auto full = [&](int64_t tile) { return bulk && (tile + 1) * kSelChunk <= a.N; };
+    if (t == 0) {
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
+        if (blockIdx.x < nb && full(blockIdx.x)) issue_tile(a, blockIdx.x, stage_of(sm, 0), &mbar[0]);
     }
-    if (lane_id() == 0) s_wc[threadIdx.x >> 5] = mine;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t t = 0;
+    uint32_t phases = 0u;
+    int s = 0;
+    for (int64_t tile = blockIdx.x; tile < nb; tile += gridDim.x, s ^= 1) {
+        const int64_t next = tile + gridDim.x;
+        if (t == 0 && next < nb && full(next)) issue_tile(a, next, stage_of(sm, s ^ 1), &mbar[s ^ 1]);
+        const int64_t base = tile * kSelChunk;
+        const int n_here = (int)min((int64_t)kSelChunk, a.N - base);
+        const Stage st = stage_of(sm, s);
+        land_tile(a, base, n_here, full(tile), st, &mbar[s], s, phases, counts);
+        bool keep[kSelItems];
+        float wv[kSelItems];
 #pragma unroll
-        for (int i = 0; i < kSelWarps; ++i) t += s_wc[i];
-        tile_count[blockIdx.x] = t;
+        for (int it = 0; it < kSelItems; ++it) {
+            const int l = it * kSelThreads + t;
+            wv[it] = 0.0f;
+            keep[it] = l < n_here && keep_anchor(a, st.pos[3 * l], st.pos[3 * l + 1],
+                                                 st.pos[3 * l + 2], st.lvl[l], st.dl[l], wv[it]);
+        }
+        const uint32_t n = stage_tile(keep, wv, base, st_idx + base, st_w + base, s_wc);
+        if (t == 0) tile_count[tile] = n;
     }
 }
 
@@ -137,8 +217,8 @@ __device__ __forceinline__ void sg_issue_tile(const SelArgs& a, int64_t tile, fl
 
 __global__ void __launch_bounds__(kSelThreads, 3) select_eval_gated(
     SelArgs a, const float* __restrict__ feat, const unsigned char* __restrict__ img,
-    float p_star, float* __restrict__ wsel, uint32_t* __restrict__ tile_count,
-    ogs_counts* counts, int bulk) {
+    float p_star, uint32_t* __restrict__ st_idx, float* __restrict__ st_w,
+    uint32_t* __restrict__ tile_count, ogs_counts* counts, int bulk) {
     pdl_wait();
     pdl_trigger();
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -148,7 +228,7 @@ __global__ void __launch_bounds__(kSelThreads, 3) select_eval_gated(
     __shared__ uint16_t s_list[kSelChunk];
     __shared__ uint8_t s_drop[kSelChunk];
     __shared__ __align__(8) uint64_t mbar, wbar, gbar;
-    __shared__ uint32_t s_wc[kSelWarps];
+    __shared__ uint32_t s_wc[kSelItems][kSelWarps];
     __shared__ uint32_t s_n;
     __shared__ uint32_t tmem_base;
     const int t = threadIdx.x;
@@ -250,135 +330,65 @@ __global__ void __launch_bounds__(kSelThreads, 3) select_eval_gated(
         tc::fence_before_sync();
         __syncthreads();                              // s_drop complete; TMEM reads done
         tc::fence_after_sync();
-        uint32_t mine = 0;
+        bool kp[kSelItems];
 #pragma unroll
-        for (int it = 0; it < kSelItems; ++it) {
-            const int l = it * kSelThreads + t;
-            const bool keep = wv[it] > 0.0f && !(gated && s_drop[l]);
-            if (l < n_here) wsel[base + l] = keep ? wv[it] : 0.0f;
-            mine += __popc(__ballot_sync(0xffffffffu, keep));
-        }
-        if (lane_id() == 0) s_wc[t >> 5] = mine;
+        for (int it = 0; it < kSelItems; ++it)
+            kp[it] = wv[it] > 0.0f && !(gated && s_drop[it * kSelThreads + t]);
         // a gate that stopped early: the staged arrays are free only now
         if (!issued && t == 0 && prefetch) sg_issue_tile(a, next, s_pos, s_dl, s_lvl, &mbar);
-        __syncthreads();
-        if (t == 0) {
-            uint32_t tot = 0;
-#pragma unroll
-            for (int i = 0; i < kSelWarps; ++i) tot += s_wc[i];
-            tile_count[tile] = tot;
-        }
+        const uint32_t n = stage_tile(kp, wv, base, st_idx + base, st_w + base, s_wc);
+        if (t == 0) tile_count[tile] = n;
     }
     tc::fence_before_sync();
     __syncthreads();
     if ((t >> 5) == 0) tc::tmem_dealloc(tbase, gate::kGTmemCols);
 }
 
-// Pass 2 (one CTA): exclusive scan of the tile counts in place; M and the overflow state.
-__global__ void __launch_bounds__(1024) select_scan(uint32_t* __restrict__ tile_count, int nb,
-                                                    int64_t cap, int k, ogs_counts* counts) {
+// Pass 2: one CTA per tile.  Its output offset is the sum of the counts of the tiles before
+// it (each CTA reads them itself: at most a few thousand words, from L2); its staged entries
+// are copied to sel_idx / sel_w at that offset, up to the capacity.  Tile 0 also sums every
+// count and writes M, the Gaussian count and the overflow state.
+constexpr int kEmitThreads = 256;
+
+__global__ void __launch_bounds__(kEmitThreads) select_emit(const uint32_t* __restrict__ tile_count,
+                                                            int nb,
+                                                            const uint32_t* __restrict__ st_idx,
+                                                            const float* __restrict__ st_w,
+                                                            uint32_t* __restrict__ sel_idx,
+                                                            float* __restrict__ sel_w, int64_t cap,
+                                                            int k, ogs_counts* counts) {
     pdl_wait();
     pdl_trigger();
-    __shared__ unsigned long long ws[32];
-    const int per = (nb + 1023) / 1024;
-    const int b0 = threadIdx.x * per, b1 = min(b0 + per, nb);
-    unsigned long long local = 0;
-    for (int b = b0; b < b1; ++b) local += tile_count[b];
-    unsigned long long x = local;
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane_id() >= (unsigned)o) x += y;
-    }
-    if (lane_id() == 31) ws[threadIdx.x >> 5] = x;
+    __shared__ unsigned long long s_part[kEmitThreads / 32];
+    const int tile = blockIdx.x;
+    const uint32_t n = tile_count[tile];
+    if (n == 0 && tile != 0) return;
+    const int upto = tile == 0 ? nb : tile;       // tile 0 sums everything (the total)
+    unsigned long long part = 0;
+    for (int i = threadIdx.x; i < upto; i += kEmitThreads) part += tile_count[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane_id() == 0) s_part[threadIdx.x >> 5] = part;
     __syncthreads();
-    if (threadIdx.x < 32) {
-        unsigned long long v = ws[threadIdx.x];
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane_id() >= (unsigned)o) v += y;
-        }
-        ws[threadIdx.x] = v;                          // inclusive warp totals
-    }
-    __syncthreads();
-    unsigned long long run = (threadIdx.x >= 32 ? ws[(threadIdx.x >> 5) - 1] : 0) + x - local;
-    for (int b = b0; b < b1; ++b) {
-        const uint32_t v = tile_count[b];
-        tile_count[b] = (uint32_t)min(run, 0xFFFFFFFFull);
-        run += v;
-    }
-    if (threadIdx.x == 0) {
-        const unsigned long long total = ws[31];
+    unsigned long long sum = 0;
+#pragma unroll
+    for (int w = 0; w < kEmitThreads / 32; ++w) sum += s_part[w];
+    const unsigned long long off = tile == 0 ? 0 : sum;
+    if (tile == 0 && threadIdx.x == 0) {
+        const unsigned long long total = sum;
         const uint32_t m = total > (unsigned long long)cap ? (uint32_t)cap : (uint32_t)total;
         counts->n_selected = m;
         counts->n_gaussians = m * (uint32_t)k;
         counts->need_selected = total > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)total;
         if (total > (unsigned long long)cap) atomicOr(&counts->overflow, 1u);
     }
-}
-
-// Pass 3 (same tiles as pass 1): kept anchors ranked by warp ballots and written in
-// ascending order at the tile's offset (16-byte weight loads, four anchors per thread and
-// round).
-__global__ void __launch_bounds__(kSelThreads) select_scatter(const float* __restrict__ wsel,
-                                                              const uint32_t* __restrict__ tile_off,
-                                                              int64_t N, uint32_t* sel_idx,
-                                                              float* sel_w, int64_t cap) {
-    pdl_wait();
-    pdl_trigger();
-    __shared__ uint32_t s_cnt[kSelItems / 4][kSelWarps];
-    const int64_t base = (int64_t)blockIdx.x * kSelChunk;
-    const int n_here = (int)min((int64_t)kSelChunk, N - base);
-    const unsigned warp = threadIdx.x >> 5;
-    constexpr int kRounds = kSelItems / 4;
-    float4 wv[kRounds];
-    uint32_t cnt[kRounds];
-#pragma unroll
-    for (int q = 0; q < kRounds; ++q) {
-        const int l = 4 * (q * kSelThreads + threadIdx.x);   // four consecutive anchors
-        float v[4];
-        if (l + 4 <= n_here && ((base & 3) == 0)) {
-            const float4 u = *reinterpret_cast<const float4*>(wsel + base + l);
-            v[0] = u.x; v[1] = u.y; v[2] = u.z; v[3] = u.w;
-        } else {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) v[e] = l + e < n_here ? wsel[base + l + e] : 0.f;
+    const size_t src = (size_t)tile * kSelChunk;
+    for (uint32_t r = threadIdx.x; r < n; r += kEmitThreads) {
+        const unsigned long long p = off + r;
+        if (p < (unsigned long long)cap) {
+            sel_idx[p] = st_idx[src + r];
+            sel_w[p] = st_w[src + r];
         }
-        wv[q] = make_float4(v[0], v[1], v[2], v[3]);
-        cnt[q] = (v[0] > 0.f) + (v[1] > 0.f) + (v[2] > 0.f) + (v[3] > 0.f);
-        // warp-inclusive scan of the per-thread counts
-        uint32_t x = cnt[q];
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane_id() >= (unsigned)o) x += y;
-        }
-        if (lane_id() == 31) s_cnt[q][warp] = x;
-        cnt[q] = x - cnt[q];                           // exclusive within the warp
-    }
-    __syncthreads();
-    unsigned long long off = tile_off[blockIdx.x];
-#pragma unroll
-    for (int q = 0; q < kRounds; ++q) {
-        uint32_t before = 0, tot = 0;
-#pragma unroll
-        for (int i = 0; i < kSelWarps; ++i) {
-            const uint32_t c = s_cnt[q][i];
-            before += (i < (int)warp) ? c : 0;
-            tot += c;
-        }
-        unsigned long long p = off + before + cnt[q];
-        const int l = 4 * (q * kSelThreads + threadIdx.x);
-        const float v[4] = {wv[q].x, wv[q].y, wv[q].z, wv[q].w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            if (v[e] > 0.f) {
-                if (p < (unsigned long long)cap) {
-                    sel_idx[p] = (uint32_t)(base + l + e);
-                    sel_w[p] = v[e];
-                }
-                ++p;
-            }
-        }
-        off += tot;
     }
 }
 
@@ -387,12 +397,37 @@ __global__ void __launch_bounds__(kSelThreads) select_scatter(const float* __res
 
 using namespace ogs;
 
-extern "C" size_t ogs_lod_select_scratch_bytes(int64_t N) {
-    int64_t nb = (N + kSelChunk - 1) / kSelChunk;
-    Carver cv(nullptr);
-    cv.take<uint32_t>((size_t)(nb < 1 ? 1 : nb));
-    cv.take<float>((size_t)(N > 0 ? N : 1));
+namespace ogs {
+namespace {
+
+// scratch: per-tile counts, then the staging area (one 2048-entry slot per tile) of indices
+// and weights
+struct SelScratch {
+    uint32_t* tile_count;
+    uint32_t* st_idx;
+    float* st_w;
+};
+
+size_t sel_layout(int64_t N, void* base, SelScratch* s) {
+    const int64_t nb = (N + kSelChunk - 1) / kSelChunk;
+    const size_t slots = (size_t)(nb < 1 ? 1 : nb) * kSelChunk;
+    Carver cv(base);
+    SelScratch t;
+    t.tile_count = cv.take<uint32_t>((size_t)(nb < 1 ? 1 : nb));
+    t.st_idx = cv.take<uint32_t>(slots);
+    t.st_w = cv.take<float>(slots);
+    if (s) *s = t;
     return cv.off + 256;
+}
+
+// persistent grid of the tile passes: three CTAs per SM, never more than the tiles
+int tile_grid(int nb) { return nb < 3 * kSmCount ? nb : 3 * kSmCount; }
+
+}  // namespace
+}  // namespace ogs
+
+extern "C" size_t ogs_lod_select_scratch_bytes(int64_t N) {
+    return sel_layout(N < 0 ? 0 : N, nullptr, nullptr);
 }
 
 extern "C" ogs_status ogs_lod_select(const float* pos, const uint8_t* level, const float* dL,
@@ -411,19 +446,25 @@ extern "C" ogs_status ogs_lod_select(const float* pos, const uint8_t* level, con
     SelArgs a{pos, level, dL, N, NL, k, infer, make_cam(*cam)};
     int nb = (int)((N + kSelChunk - 1) / kSelChunk);
     if (nb < 1) nb = 1;
-    Carver cv(scratch);
-    uint32_t* tile_count = cv.take<uint32_t>((size_t)nb);
-    float* wsel = cv.take<float>((size_t)(N > 0 ? N : 1));
+    SelScratch sc;
+    sel_layout(N, scratch, &sc);
     const int bulk = aligned(pos, 16) && aligned(dL, 16) && aligned(level, 16);
-    launch_pdl(select_eval, dim3(nb), dim3(kSelThreads), 0, st, a, wsel, tile_count, counts, bulk);
-    launch_pdl(select_scan, dim3(1), dim3(1024), 0, st, tile_count, nb, sel_cap, k, counts);
-    launch_pdl(select_scatter, dim3(nb), dim3(kSelThreads), 0, st,
-               wsel, tile_count, N, sel_idx, sel_w, sel_cap);
+    if (cudaFuncSetAttribute(select_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kStSmem) != cudaSuccess)
+        return OGS_ERR_CUDA;
+    if (N == 0 &&
+        cudaMemsetAsync(sc.tile_count, 0, sizeof(uint32_t), st) != cudaSuccess)
+        return OGS_ERR_CUDA;
+    launch_pdl(select_tiles, dim3(tile_grid(nb)), dim3(kSelThreads), kStSmem, st, a, sc.st_idx,
+               sc.st_w, sc.tile_count, counts, bulk);
+    launch_pdl(select_emit, dim3(nb), dim3(kEmitThreads), 0, st, (const uint32_t*)sc.tile_count,
+               nb, (const uint32_t*)sc.st_idx, (const float*)sc.st_w, sel_idx, sel_w, sel_cap, k,
+               counts);
     return launch_status();
 }
 
 extern "C" size_t ogs_lod_select_gated_scratch_bytes(int64_t N) {
-    return ogs_lod_select_scratch_bytes(N) + gate::kGImgBytes + 256;
+    return ((ogs_lod_select_scratch_bytes(N) + 255) & ~(size_t)255) + gate::kGImgBytes + 256;
 }
 
 extern "C" ogs_status ogs_lod_select_gated(const float* pos, const uint8_t* level,
@@ -448,10 +489,9 @@ extern "C" ogs_status ogs_lod_select_gated(const float* pos, const uint8_t* leve
     SelArgs a{pos, level, dL, N, NL, k, infer, make_cam(*cam)};
     int nb = (int)((N + kSelChunk - 1) / kSelChunk);
     if (nb < 1) nb = 1;
-    Carver cv(scratch);
-    uint32_t* tile_count = cv.take<uint32_t>((size_t)nb);
-    float* wsel = cv.take<float>((size_t)(N > 0 ? N : 1));
-    unsigned char* img = cv.take<unsigned char>(gate::kGImgBytes);
+    SelScratch sc;
+    const size_t sel_bytes = sel_layout(N, scratch, &sc);
+    unsigned char* img = static_cast<unsigned char*>(scratch) + ((sel_bytes + 255) & ~(size_t)255);
     // the packing launch also resets the frame's counters, so no separate clear runs first
     static_assert(sizeof(ogs_counts) % 8 == 0, "counters cleared as 64-bit words");
     if (aligned(counts, 8)) {
@@ -466,12 +506,14 @@ extern "C" ogs_status ogs_lod_select_gated(const float* pos, const uint8_t* leve
                              kSgSmem) != cudaSuccess)
         return OGS_ERR_CUDA;
     const int bulk = aligned(pos, 16) && aligned(dL, 16) && aligned(level, 16);
-    const int grid = nb < 3 * kSmCount ? nb : 3 * kSmCount;
-    launch_pdl(select_eval_gated, dim3(grid), dim3(kSelThreads), kSgSmem, st,
-               a, feat, img, p_star, wsel, tile_count, counts, bulk);
-    launch_pdl(select_scan, dim3(1), dim3(1024), 0, st, tile_count, nb, sel_cap, k, counts);
-    launch_pdl(select_scatter, dim3(nb), dim3(kSelThreads), 0, st,
-               wsel, tile_count, N, sel_idx, sel_w, sel_cap);
+    if (N == 0 &&
+        cudaMemsetAsync(sc.tile_count, 0, sizeof(uint32_t), st) != cudaSuccess)
+        return OGS_ERR_CUDA;
+    launch_pdl(select_eval_gated, dim3(tile_grid(nb)), dim3(kSelThreads), kSgSmem, st,
+               a, feat, img, p_star, sc.st_idx, sc.st_w, sc.tile_count, counts, bulk);
+    launch_pdl(select_emit, dim3(nb), dim3(kEmitThreads), 0, st, (const uint32_t*)sc.tile_count,
+               nb, (const uint32_t*)sc.st_idx, (const float*)sc.st_w, sel_idx, sel_w, sel_cap, k,
+               counts);
     return launch_status();
 }
 
