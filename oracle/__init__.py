@@ -288,9 +288,17 @@ class Frame:
     gy: int
 
 
-def render(scene, mlp, cam, infer=True, bg=(0.0, 0.0, 0.0), want_maxc=False):
-    """The whole forward pass of one view, stage by stage."""
+def render(scene, mlp, cam, infer=True, bg=(0.0, 0.0, 0.0), want_maxc=False, gate=None):
+    """The whole forward pass of one view, stage by stage.  ``gate = (net, p_star)`` applies
+    the learned anchor-visibility proposal after the LOD rule: of the selected anchors only
+    those whose keep probability is at least p_star go on to decoding (order kept)."""
     sel_idx, sel_w, margin = lod_select(scene.pos, scene.level, scene.dL, scene.NL, cam, infer)
+    if gate is not None:
+        net, p_star = gate
+        p, _ = proposal_forward(net, proposal_inputs(scene.pos, scene.level, scene.feat,
+                                                     scene.NL, sel_idx, cam))
+        keep = p >= p_star
+        sel_idx, sel_w = sel_idx[keep], sel_w[keep]
     g = decode(sel_idx, sel_w, scene, mlp, cam)
     pr = project(g["means"], g["scales"], g["quats"], g["opac"], cam)
     gx, gy = grid(cam.W, cam.H)
@@ -330,6 +338,20 @@ def adam(param, grad, m, v, lr, beta1, beta2, eps, step):
     mh = m / (1 - beta1 ** step)
     vh = v / (1 - beta2 ** step)
     return param - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def adam_rows(param, grad, m, v, rows, lr, beta1, beta2, eps, step):
+    """Adam over touched rows only (the optimiser step over the anchors a training step's
+    views selected): the rows listed in ``rows`` get one ``adam`` update with the bias
+    correction of the global step count; every other row keeps its parameters and moments
+    (lazy Adam).  Returns new (param, m, v).  Pinned by: all rows = dense Adam, no rows = no
+    change, and a row skipped on one step against the recursion written out by hand
+    (tests/test_oracle_train)."""
+    P, M, V = _d(param).copy(), _d(m).copy(), _d(v).copy()
+    r = np.asarray(rows, np.int64)
+    if len(r):
+        P[r], M[r], V[r] = adam(P[r], _d(grad)[r], M[r], V[r], lr, beta1, beta2, eps, step)
+    return P, M, V
 
 
 # ----------------------------------------------------------------------------------------

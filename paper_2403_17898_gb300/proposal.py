@@ -98,3 +98,62 @@ def full_detail(cam):
     c = copy.copy(cam)
     c.s = 1e-6
     return c
+
+
+@dataclass
+class GateAssessment:
+    """Image cost of the gated form on a set of views against full-detail renders."""
+    pooled_db: float              # 10 log10(sum MSE gated / sum MSE plain) over the views
+    psnr_plain: list              # per view: PSNR of the plain path vs full detail (dB)
+    psnr_gated: list              # per view: PSNR of the gated path vs full detail (dB)
+    kept: list                    # per view: gated / plain selected anchors
+
+    @property
+    def dpsnr(self):
+        return [a - b for a, b in zip(self.psnr_plain, self.psnr_gated)]
+
+
+def assess(rd, full_rd, cams, gate, plain_precision="fp32", gate_precision="bf16"):
+    """Renders every view three ways: full detail (every level, ``full_rd``), the plain LOD
+    path (``plain_precision``, no gate) and the gated path (``gate_precision`` with
+    ``gate = (weights, p_star)``); returns the pooled and per-view PSNR figures."""
+    se_plain = se_gate = 0.0
+    pp, pg, kept = [], [], []
+    prec = rd.precision
+    try:
+        for cam in cams:
+            full_rd.render(full_detail(cam))
+            ref = full_rd.img
+            rd.precision = plain_precision
+            c0 = rd.render(cam)
+            plain = rd.img.clone()
+            rd.precision = gate_precision
+            c1 = rd.render(cam, gate=gate)
+            se_plain += float(torch.mean((plain - ref) ** 2).item())
+            se_gate += float(torch.mean((rd.img - ref) ** 2).item())
+            pp.append(psnr(plain, ref))
+            pg.append(psnr(rd.img, ref))
+            kept.append(c1.n_selected / max(c0.n_selected, 1))
+    finally:
+        rd.precision = prec
+    pooled = 10.0 * math.log10(se_gate / se_plain) if se_plain > 0 else 0.0
+    return GateAssessment(pooled, pp, pg, kept)
+
+
+CANDIDATES = (0.001, 0.002, 0.005, 0.01, 0.02, 0.05, 0.1, 0.2, 0.3, 0.5, 0.6, 0.7, 0.8, 0.9,
+              0.95)
+
+
+def calibrate(rd, full_rd, cams, weights, budget_db, candidates=CANDIDATES, **kw):
+    """Largest threshold p* among ``candidates`` whose pooled PSNR loss on ``cams`` (views
+    the network was trained on, never the views it is judged on) is within ``budget_db``;
+    0 if none is.  Returns (p_star, [(p*, pooled dB, median dB, max dB, kept fraction)]);
+    ``kw`` (precisions) goes to ``assess``."""
+    p_star, curve = 0.0, []
+    for cand in candidates:
+        a = assess(rd, full_rd, cams, (weights, cand), **kw)
+        curve.append((cand, a.pooled_db, float(np.median(a.dpsnr)), float(np.max(a.dpsnr)),
+                      float(np.mean(a.kept))))
+        if a.pooled_db <= budget_db:
+            p_star = cand
+    return p_star, curve
