@@ -28,7 +28,9 @@
  *     stage writes only what fits (the caller grows the buffer and reruns the frame).
  *   - Return value: OGS_OK, or OGS_ERR_ARG for a null pointer / bad size / misaligned pointer
  *     detected on the host before anything is enqueued, or OGS_ERR_CUDA when a launch fails.
- *     No call throws, traps or exits.
+ *     Errors found on the device (capacity, expired waits, non-finite values) stay in device
+ *     words; ogs_counts_status turns a read-back copy into a status.  No call throws, traps
+ *     or exits.
  *   - Arrays are C-contiguous; "f32[N][3]" means N rows of 3 floats.
  *
  * Camera model: world point p has camera coordinates R (p - campos) (x right, y down, z
@@ -48,9 +50,10 @@ extern "C" {
 typedef enum ogs_status {
     OGS_OK = 0,
     OGS_ERR_ARG = 1,       /* invalid argument, nothing enqueued */
-    OGS_ERR_CAPACITY = 2,  /* reserved for host-side capacity checks */
+    OGS_ERR_CAPACITY = 2,  /* a capacity was too small (host check, or ogs_counts.overflow) */
     OGS_ERR_TIMEOUT = 3,   /* a bounded device-side wait expired (see ogs_counts.timeout) */
-    OGS_ERR_CUDA = 4       /* a CUDA launch or API call failed */
+    OGS_ERR_CUDA = 4,      /* a CUDA launch or API call failed */
+    OGS_ERR_NONFINITE = 5  /* ogs_scan_nonfinite found a NaN or infinity */
 } ogs_status;
 
 /* Host-side camera, passed by pointer and copied at call time. */
@@ -274,8 +277,10 @@ ogs_status ogs_radix_sort_pairs(uint32_t* keys, uint32_t* vals, const uint32_t* 
  *   including the last blended one); img may be pinned host memory (page-locked, so its
  *   address is valid on the device under unified addressing): the image then goes to the
  *   host while the kernel runs, with no separate copy
- *   n_eval (optional, may be NULL): u32[H][W], list entries the pixel evaluated before it
- *   saturated or ran out (the blend's unit of work)
+ *   n_eval (optional, may be NULL): u32[H][W], (pixel, Gaussian) tests the kernel made for
+ *   the pixel while it still needed them: the list entries whose alpha >= 1/255 ellipse box
+ *   reaches the pixel's 8x8 block, up to and including the one the pixel saturated on (the
+ *   blend's unit of work as executed; entries whose box misses the block are never tested)
  *   maxc (optional, may be NULL): u32[N_anchors], float bits of the largest T*alpha of any
  *   blended Gaussian of each anchor (atomic max; caller zeroes); anchor of Gaussian g is
  *   sel_idx[g / k].
@@ -374,12 +379,65 @@ ogs_status ogs_loss_l1(const float* img, const float* target, int64_t n, float* 
  * (lambda = 0.2 in the paper), SSIM with an 11x11 Gaussian window (sigma 1.5, zero padded),
  * C1 = 0.01^2, C2 = 0.03^2, averaged over the C x H x W values.  dimg (written) is the
  * gradient w.r.t. img; *loss += the loss (device float, may be NULL).
+ *   target_stats (optional, may be NULL): f32[2][C][H][W], the target's window moments G*y
+ *   and G*y^2 as written by ogs_ssim_target_stats for this target; with them the forward pass
+ *   blurs three moments instead of five (same loss and gradient up to FP32 rounding).
  *   scratch: ogs_loss_l1_ssim_scratch_bytes(C, H, W) bytes, 16-byte aligned.
+ * ogs_ssim_target_stats — the two window moments of a target image (zero padded), for reuse
+ * by every loss evaluation against that target.
  * ------------------------------------------------------------------------------------- */
 size_t ogs_loss_l1_ssim_scratch_bytes(int32_t C, int32_t H, int32_t W);
 ogs_status ogs_loss_l1_ssim(const float* img, const float* target, int32_t C, int32_t H,
-                            int32_t W, float lambda, float* dimg, float* loss, void* scratch,
-                            size_t scratch_bytes, void* stream);
+                            int32_t W, float lambda, float* dimg, float* loss,
+                            const float* target_stats, void* scratch, size_t scratch_bytes,
+                            void* stream);
+ogs_status ogs_ssim_target_stats(const float* target, int32_t C, int32_t H, int32_t W,
+                                 float* target_stats, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Adam over touched anchor rows (the optimiser step of the training loop, Sec. 5.1.5, over
+ * the anchors a step's views selected).  Anchors outside every view of a step receive no
+ * gradient; their parameters and moments are left as they are (lazy Adam: a row's moments
+ * decay only on the steps that touch it, bias correction uses the global step count), so a
+ * step streams only the touched rows instead of every anchor's state.
+ *
+ * ogs_stamp_selected — stamp[sel_idx[r]] = value for r < counts->n_selected (call once per
+ *   view of the step with value = the step number; stamp u32[N], caller-owned, zeroed once).
+ * ogs_adam_rows — for every row j < rows with stamp[j] == value, one Adam update of its
+ *   row_len values (param/grad/m/v f32[rows][row_len]) as ogs_adam (same bias correction with
+ *   the 1-based global `step`); zero_grad != 0 clears the updated rows' gradients.  Rows with
+ *   another stamp are not read or written beyond their stamp.
+ * ------------------------------------------------------------------------------------- */
+ogs_status ogs_stamp_selected(const uint32_t* sel_idx, const ogs_counts* counts,
+                              int64_t sel_cap, uint32_t* stamp, uint32_t value, void* stream);
+ogs_status ogs_adam_rows(float* param, float* grad, float* m, float* v, int64_t rows,
+                         int32_t row_len, const uint32_t* stamp, uint32_t value, float lr,
+                         float beta1, float beta2, float eps, int32_t step, int32_t zero_grad,
+                         void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Error surface.  The library keeps no context: a frame's device-side error state is its
+ * ogs_counts record (overflow bits, timeout) plus, on request, a non-finite flag word.
+ *
+ * ogs_scan_nonfinite — opt-in check of any f32 buffer (inputs, images, gradients): *flag |= bit
+ *   (device u32, caller zeroes) if any of x[0..n) is NaN or infinite.  Enqueued like every
+ *   call; nothing is synchronised.
+ * ogs_counts_status — host function: maps a copy of ogs_counts (read back by the caller) and a
+ *   non-finite flag word to a status: OGS_ERR_NONFINITE if the flag is set, else
+ *   OGS_ERR_TIMEOUT if a bounded wait expired, else OGS_ERR_CAPACITY if a capacity
+ *   overflowed (the needed sizes are in the record), else OGS_OK.
+ * ------------------------------------------------------------------------------------- */
+ogs_status ogs_scan_nonfinite(const float* x, int64_t n, uint32_t* flag, uint32_t bit,
+                              void* stream);
+ogs_status ogs_counts_status(const ogs_counts* counts /* host */, uint32_t nonfinite);
+
+/* ---------------------------------------------------------------------------------------
+ * ogs_scale — x[i] *= *s for i < n (s a device float).  The backward of a loss that enters a
+ * larger objective multiplies the loss's own gradient (dimg of ogs_loss_l1 /
+ * ogs_loss_l1_ssim) by the gradient arriving from that objective (the chain rule of the
+ * autograd wrappers); reading s on the device needs no host synchronisation.
+ * ------------------------------------------------------------------------------------- */
+ogs_status ogs_scale(float* x, int64_t n, const float* s, void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * ogs_adam — one Adam step over n parameters (step >= 1 is the 1-based step count used for
@@ -561,6 +619,9 @@ ogs_status ogs_lod_select_gated(const float* pos, const uint8_t* level, const fl
  * ogs_blend_fwd: float bits of the largest T*alpha), positives weighted by pos_weight (> 0),
  * and its gradients.
  *   grads: same layout as the network, ACCUMULATED (+=); *loss += mean BCE (may be NULL).
+ *   dloss: device float (may be NULL, meaning 1), the gradient of the caller's objective with
+ *   respect to this BCE; every gradient added to grads is multiplied by it (the backward of a
+ *   loss that enters a larger objective).
  *   scratch: ogs_proposal_train_scratch_bytes() bytes, 16-byte aligned. */
 size_t ogs_proposal_train_scratch_bytes(void);
 ogs_status ogs_proposal_train(const float* pos, const uint8_t* level, const float* feat,
@@ -569,7 +630,8 @@ ogs_status ogs_proposal_train(const float* pos, const uint8_t* level, const floa
                               const ogs_counts* counts, const uint32_t* maxc, float tau,
                               float pos_weight,
                               const ogs_proposal* grads /* host struct, written */, float* loss,
-                              void* scratch, size_t scratch_bytes, void* stream);
+                              const float* dloss, void* scratch, size_t scratch_bytes,
+                              void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * Anchor growing and the LOD-bias update (Sec. 4.2.1).  Over the training views between two

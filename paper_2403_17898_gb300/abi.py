@@ -101,9 +101,17 @@ _SIGS = {
                                  _P]),
     "ogs_loss_l1": (C.c_int, [_P, _P, _I64, _P, _P, _P]),
     "ogs_loss_l1_ssim_scratch_bytes": (_SZ, [_I32, _I32, _I32]),
-    "ogs_loss_l1_ssim": (C.c_int, [_P, _P, _I32, _I32, _I32, C.c_float, _P, _P, _P, _SZ, _P]),
+    "ogs_loss_l1_ssim": (C.c_int, [_P, _P, _I32, _I32, _I32, C.c_float, _P, _P, _P, _P, _SZ,
+                                   _P]),
+    "ogs_ssim_target_stats": (C.c_int, [_P, _I32, _I32, _I32, _P, _P]),
     "ogs_adam": (C.c_int, [_P, _P, _P, _P, _I64, C.c_float, C.c_float, C.c_float, C.c_float,
                            _I32, _I32, _P]),
+    "ogs_scale": (C.c_int, [_P, _I64, _P, _P]),
+    "ogs_scan_nonfinite": (C.c_int, [_P, _I64, _P, C.c_uint32, _P]),
+    "ogs_counts_status": (C.c_int, [_P, C.c_uint32]),
+    "ogs_stamp_selected": (C.c_int, [_P, _P, _I64, _P, C.c_uint32, _P]),
+    "ogs_adam_rows": (C.c_int, [_P, _P, _P, _P, _I64, _I32, _P, C.c_uint32, C.c_float,
+                                C.c_float, C.c_float, C.c_float, _I32, _I32, _P]),
     "ogs_radix_sort_pairs_noalloc_max_items": (_I64, []),
     "ogs_radix_sort_pairs_noalloc": (C.c_int, [_P, _P, _P, _I64, _I32, _I32, _P]),
     "ogs_proposal_gate_scratch_bytes": (_SZ, [_I64]),
@@ -116,7 +124,7 @@ _SIGS = {
     "ogs_proposal_train_scratch_bytes": (_SZ, []),
     "ogs_proposal_train": (C.c_int, [_P, _P, _P, _I64, _I32, C.POINTER(Camera),
                                      C.POINTER(Proposal), _P, _P, _P, C.c_float, C.c_float,
-                                     C.POINTER(Proposal), _P, _P, _SZ, _P]),
+                                     C.POINTER(Proposal), _P, _P, _P, _SZ, _P]),
     "ogs_explicit_gaussians": (C.c_int, [_P, _P, _P, _I64, _I32, C.POINTER(Explicit),
                                          C.POINTER(Camera), _P, _P, _I64, _P,
                                          C.POINTER(Gaussians), _P]),
@@ -392,11 +400,52 @@ def loss_l1_ssim_scratch_bytes(C, H, W):
     return int(lib().ogs_loss_l1_ssim_scratch_bytes(int(C), int(H), int(W)))
 
 
-def loss_l1_ssim(img, target, lam, dimg, loss, scratch, stream=None):
+def loss_l1_ssim(img, target, lam, dimg, loss, scratch, stream=None, target_stats=None):
     C, H, W = img.shape
     _check(lib().ogs_loss_l1_ssim(_ptr(img), _ptr(target), int(C), int(H), int(W), float(lam),
-                                  _ptr(dimg), _ptr(loss), _ptr(scratch), scratch.numel(),
-                                  _stream(stream)), "ogs_loss_l1_ssim")
+                                  _ptr(dimg), _ptr(loss), _ptr(target_stats), _ptr(scratch),
+                                  scratch.numel(), _stream(stream)), "ogs_loss_l1_ssim")
+
+
+def ssim_target_stats(target, stats, stream=None):
+    """The target's window moments G*y, G*y^2 into stats f32[2][C][H][W]."""
+    C, H, W = target.shape
+    _check(lib().ogs_ssim_target_stats(_ptr(target), int(C), int(H), int(W), _ptr(stats),
+                                       _stream(stream)), "ogs_ssim_target_stats")
+
+
+def stamp_selected(sel_idx, counts, stamp, value, stream=None):
+    _check(lib().ogs_stamp_selected(_ptr(sel_idx), _ptr(counts), sel_idx.numel(), _ptr(stamp),
+                                    int(value), _stream(stream)), "ogs_stamp_selected")
+
+
+def adam_rows(param, grad, m, v, stamp, value, lr, beta1, beta2, eps, step, zero_grad=True,
+              stream=None):
+    """Adam over the rows of param (rows = its first dimension) whose stamp equals value."""
+    rows = param.shape[0]
+    row_len = param[0].numel() if rows else 1
+    _check(lib().ogs_adam_rows(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), int(rows),
+                               int(row_len), _ptr(stamp), int(value), float(lr), float(beta1),
+                               float(beta2), float(eps), int(step), int(bool(zero_grad)),
+                               _stream(stream)), "ogs_adam_rows")
+
+
+def scan_nonfinite(x, flag, bit=1, stream=None):
+    """flag (one-element int32 device tensor) |= bit if x holds a NaN or an infinity."""
+    _check(lib().ogs_scan_nonfinite(_ptr(x), x.numel(), _ptr(flag), int(bit), _stream(stream)),
+           "ogs_scan_nonfinite")
+
+
+def counts_status(counts_host, nonfinite=0):
+    """ogs_status of a frame from its counters read back to the host (uint32 array of 8) and a
+    non-finite flag word: 0 OK, 2 capacity, 3 timeout, 5 non-finite."""
+    a = np.ascontiguousarray(counts_host, np.uint32)
+    return int(lib().ogs_counts_status(a.ctypes.data_as(C.c_void_p), int(nonfinite)))
+
+
+def scale(x, s, stream=None):
+    """x *= s in place, s a one-element device tensor (no host synchronisation)."""
+    _check(lib().ogs_scale(_ptr(x), x.numel(), _ptr(s), _stream(stream)), "ogs_scale")
 
 
 def adam(param, grad, m, v, n, lr, beta1, beta2, eps, step, zero_grad=True, stream=None):
@@ -447,14 +496,14 @@ def proposal_train_scratch_bytes():
 
 
 def proposal_train(pos, level, feat, N, NL, cam, net, sel_idx, counts, maxc, tau, grads, loss,
-                   scratch, pos_weight=1.0, stream=None):
+                   scratch, pos_weight=1.0, stream=None, dloss=None):
     c = cam if isinstance(cam, Camera) else camera(cam)
     n = net if isinstance(net, Proposal) else proposal_struct(net)
     g = grads if isinstance(grads, Proposal) else proposal_struct(grads)
     _check(lib().ogs_proposal_train(_ptr(pos), _ptr(level), _ptr(feat), int(N), int(NL),
                                     C.byref(c), C.byref(n), _ptr(sel_idx), _ptr(counts),
                                     _ptr(maxc), float(tau), float(pos_weight), C.byref(g),
-                                    _ptr(loss),
+                                    _ptr(loss), _ptr(dloss),
                                     _ptr(scratch), scratch.numel(), _stream(stream)),
            "ogs_proposal_train")
 

@@ -11,7 +11,9 @@
 // leaves its sums bit-for-bit as a skipped update would.  Lanes of a warp therefore never
 // diverge inside the walk.  A warp stops walking once all its pixels have saturated (checked
 // every 128 records) and the CTA stops loading batches once all of its pixels have.  The
-// kernel is bound by instruction issue (FP32 + MUFU), not by memory.
+// kernel is bound by instruction issue (FP32 + MUFU), not by memory.  The optional n_eval
+// output counts, per pixel, the (pixel, Gaussian) tests the kernel made while the pixel still
+// needed them: the entries of its warp block's list up to the one it saturated on.
 #include "blend_common.cuh"
 
 namespace ogs {
@@ -27,7 +29,8 @@ template <bool kEval>
 __device__ __forceinline__ float composite(float p2, float o, float cr, float cg, float cb,
                                            float pskip2, int idx, bool& done, float& T,
                                            float& C0, float& C1, float& C2, int& last,
-                                           int& stop) {
+                                           int& tests) {
+    if (kEval) tests += done ? 0 : 1;               // a test this pixel still needed
     // skip if power > 0 or alpha < 1/255 (power2 < pskip2)
     const bool pass = !done && p2 <= 0.f && p2 >= pskip2;
     const float alpha = fminf(0.99f, raw_alpha(o, p2));
@@ -41,7 +44,6 @@ __device__ __forceinline__ float composite(float p2, float o, float cr, float cg
     C2 = fmaf(cb, wgt, C2);
     T = apply ? Tn : T;
     last = apply ? idx : last;
-    if (kEval) stop = sat ? idx : stop;
     done = done || sat;
     return wgt;
 }
@@ -73,7 +75,7 @@ __global__ void __launch_bounds__(kThreads) blend_fwd_kernel(
     const int n = (int)(range.y - range.x);
     uint8_t* list = s_list[threadIdx.x >> 5];
     float T0 = 1.f, T1 = 1.f, C00 = 0.f, C01 = 0.f, C02 = 0.f, C10 = 0.f, C11 = 0.f, C12 = 0.f;
-    int last0 = 0, last1 = 0, stop0 = n, stop1 = n;
+    int last0 = 0, last1 = 0, tests0 = 0, tests1 = 0;
     bool done0 = !in0, done1 = !in1;
     for (int b0 = 0; b0 < n; b0 += kBatch) {
         if (__syncthreads_count(done0 && done1) == kThreads) break;
@@ -104,9 +106,9 @@ __global__ void __launch_bounds__(kThreads) blend_fwd_kernel(
                 const float p1 = power2(ax, dx, dy1, A.w, B.x);
                 const int idx = b0 + j + 1;
                 const float c0 = composite<kEval>(p0, B.y, B.z, B.w, Cc.x, Cc.y, idx, done0, T0,
-                                                  C00, C01, C02, last0, stop0);
+                                                  C00, C01, C02, last0, tests0);
                 const float c1 = composite<kEval>(p1, B.y, B.z, B.w, Cc.x, Cc.y, idx, done1, T1,
-                                                  C10, C11, C12, last1, stop1);
+                                                  C10, C11, C12, last1, tests1);
                 if (kMaxC) {
                     // contributions are >= 0, so their float bits order like unsigned ints
                     const uint32_t m = __reduce_max_sync(0xffffffffu,
@@ -124,7 +126,7 @@ __global__ void __launch_bounds__(kThreads) blend_fwd_kernel(
         img[2 * plane + pix] = C02 + T0 * bg2;
         T_final[pix] = T0;
         n_last[pix] = (uint32_t)last0;
-        if (kEval) n_eval[pix] = (uint32_t)stop0;
+        if (kEval) n_eval[pix] = (uint32_t)tests0;
     }
     if (in1) {
         const size_t pix = (size_t)(py + 1) * W + px;
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(kThreads) blend_fwd_kernel(
         img[2 * plane + pix] = C12 + T1 * bg2;
         T_final[pix] = T1;
         n_last[pix] = (uint32_t)last1;
-        if (kEval) n_eval[pix] = (uint32_t)stop1;
+        if (kEval) n_eval[pix] = (uint32_t)tests1;
     }
 }
 

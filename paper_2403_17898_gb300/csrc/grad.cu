@@ -597,6 +597,14 @@ __global__ void l1_kernel(const float* __restrict__ img, const float* __restrict
     if (lane_id() == 0 && loss) atomicAdd(loss, s * scale);
 }
 
+// x *= *s (the chain-rule factor that a loss's backward receives)
+__global__ void scale_kernel(float* __restrict__ x, int64_t n, const float* __restrict__ s) {
+    const float f = *s;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] *= f;
+}
+
 // One parameter: m, v moments; step lr * m_hat / (sqrt(v_hat) + eps) with the bias
 // corrections folded into reciprocals (ibc1 = 1/(1 - b1^t), ibc2 = 1/(1 - b2^t)) and one
 // fast division, so the update costs a handful of instructions and the kernel stays
@@ -725,6 +733,110 @@ extern "C" ogs_status ogs_loss_l1(const float* img, const float* target, int64_t
     if (!img || !target || !dimg || n <= 0) return OGS_ERR_ARG;
     l1_kernel<<<stride_grid(n, 256, 8), 256, 0, (cudaStream_t)stream>>>(img, target, n,
                                                                          1.0f / (float)n, dimg, loss);
+    return launch_status();
+}
+
+// Adam over the rows whose stamp equals `value` (the anchors a training step selected).  A
+// warp takes 32 rows at a time: their stamps are read in one coalesced load, and the warp then
+// walks the touched ones, its lanes covering a row's elements (rows of up to 64 values in two
+// rounds, longer rows in more); gradients of updated rows are cleared.
+__global__ void __launch_bounds__(256) adam_rows_kernel(float* __restrict__ p,
+                                                        float* __restrict__ grad,
+                                                        float* __restrict__ m,
+                                                        float* __restrict__ v, int64_t rows,
+                                                        int row_len,
+                                                        const uint32_t* __restrict__ stamp,
+                                                        uint32_t value, float lr, float b1,
+                                                        float b2, float eps, float ibc1,
+                                                        float ibc2, int zero_grad) {
+    const int lane = (int)lane_id();
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r0 = warp * 32; r0 < rows; r0 += nwarps * 32) {
+        const int64_t r = r0 + lane;
+        const bool hit = r < rows && stamp[r] == value;
+        uint32_t todo = __ballot_sync(0xffffffffu, hit);
+        while (todo) {
+            const int b = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t base = (r0 + b) * (int64_t)row_len;
+            for (int e = lane; e < row_len; e += 32) {
+                float P = p[base + e], G = grad[base + e], M = m[base + e], V = v[base + e];
+                adam_one(P, G, M, V, lr, b1, b2, eps, ibc1, ibc2, zero_grad);
+                p[base + e] = P;
+                m[base + e] = M;
+                v[base + e] = V;
+                if (zero_grad) grad[base + e] = G;
+            }
+        }
+    }
+}
+
+// stamp[sel_idx[r]] = value for the r < counts->n_selected selected anchors
+__global__ void stamp_rows_kernel(const uint32_t* __restrict__ sel_idx,
+                                  const ogs_counts* __restrict__ counts,
+                                  uint32_t* __restrict__ stamp, uint32_t value) {
+    const uint32_t M = counts->n_selected;
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < M; r += gridDim.x * blockDim.x)
+        stamp[sel_idx[r]] = value;
+}
+
+extern "C" ogs_status ogs_stamp_selected(const uint32_t* sel_idx, const ogs_counts* counts,
+                                         int64_t sel_cap, uint32_t* stamp, uint32_t value,
+                                         void* stream) {
+    if (!sel_idx || !counts || !stamp || sel_cap < 0) return OGS_ERR_ARG;
+    if (sel_cap == 0) return OGS_OK;
+    stamp_rows_kernel<<<stride_grid(sel_cap, 256, 8), 256, 0, (cudaStream_t)stream>>>(
+        sel_idx, counts, stamp, value);
+    return launch_status();
+}
+
+extern "C" ogs_status ogs_adam_rows(float* param, float* grad, float* m, float* v, int64_t rows,
+                                    int32_t row_len, const uint32_t* stamp, uint32_t value,
+                                    float lr, float beta1, float beta2, float eps, int32_t step,
+                                    int32_t zero_grad, void* stream) {
+    if (!param || !grad || !m || !v || !stamp || rows < 0 || row_len < 1 || step < 1)
+        return OGS_ERR_ARG;
+    if (rows == 0) return OGS_OK;
+    const double bc1 = 1.0 - pow((double)beta1, (double)step);
+    const double bc2 = 1.0 - pow((double)beta2, (double)step);
+    adam_rows_kernel<<<stride_grid((rows + 31) / 32 * 32, 256, 8), 256, 0,
+                       (cudaStream_t)stream>>>(param, grad, m, v, rows, row_len, stamp, value,
+                                               lr, beta1, beta2, eps, (float)(1.0 / bc1),
+                                               (float)(1.0 / bc2), zero_grad);
+    return launch_status();
+}
+
+// flag |= bit if any of x[0..n) is NaN or infinite (one atomic per warp that finds one)
+__global__ void nonfinite_kernel(const float* __restrict__ x, int64_t n, uint32_t* flag,
+                                 uint32_t bit) {
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        bad |= !isfinite(x[i]);
+    if (__any_sync(0xffffffffu, bad) && lane_id() == 0) atomicOr(flag, bit);
+}
+
+extern "C" ogs_status ogs_scan_nonfinite(const float* x, int64_t n, uint32_t* flag, uint32_t bit,
+                                         void* stream) {
+    if (!x || !flag || n < 0 || bit == 0) return OGS_ERR_ARG;
+    if (n == 0) return OGS_OK;
+    nonfinite_kernel<<<stride_grid(n, 256, 8), 256, 0, (cudaStream_t)stream>>>(x, n, flag, bit);
+    return launch_status();
+}
+
+extern "C" ogs_status ogs_counts_status(const ogs_counts* counts, uint32_t nonfinite) {
+    if (!counts) return OGS_ERR_ARG;
+    if (nonfinite) return OGS_ERR_NONFINITE;
+    if (counts->timeout) return OGS_ERR_TIMEOUT;
+    if (counts->overflow) return OGS_ERR_CAPACITY;
+    return OGS_OK;
+}
+
+extern "C" ogs_status ogs_scale(float* x, int64_t n, const float* s, void* stream) {
+    if (!x || !s || n < 0) return OGS_ERR_ARG;
+    if (n == 0) return OGS_OK;
+    scale_kernel<<<stride_grid(n, 256, 8), 256, 0, (cudaStream_t)stream>>>(x, n, s);
     return launch_status();
 }
 

@@ -7,8 +7,10 @@
 //   dS/dm1 = S (2my/A1 - 2my/A2 - 2m1/B1 + 2m1/B2),  dS/dm2 = -S/B2,  dS/dm3 = 2S/A2,
 // and for the mean SSIM:  d/dx = G*g1 + 2 x (G*g2) + y (G*g3), g_i = dS/dm_i / n.
 // Two tiled passes (moments -> SSIM map and partial maps; blur of the partial maps ->
-// gradient), each staging its tile and halo in shared memory; HBM-bound (x, y and three
-// partial maps read or written once per pass).
+// gradient), each staging its tile and halo in shared memory; bound by FP32 instruction issue
+// (11-tap blurs of every moment in both directions).  A training loop that renders against
+// fixed targets can compute the target's two moments once (ogs_ssim_target_stats) and pass
+// them in, so that the forward pass blurs three moments instead of five.
 #include <cmath>
 
 #include "internal.cuh"
@@ -62,16 +64,21 @@ constexpr int kSpan = kRun + kWin - 1;                     // 14 inputs per run
 constexpr int kHRuns = kHY * (kTX / kRun);                 // 42 rows x 8 runs = 336
 constexpr int kVRuns = kTX * (kTY / kRun);                 // 32 columns x 8 runs = 256
 
-// pass 1: the five blurred moments -> SSIM map (summed) and the three partial maps
-// gp_i = dS/dm_i / n for the backward
+// pass 1: the blurred moments -> SSIM map (summed) and the three partial maps
+// gp_i = dS/dm_i / n for the backward.  The five moments are G*x, G*y, G*x^2, G*y^2, G*xy;
+// with kCached the target's two (G*y, G*y^2) come precomputed in ystat[2][C][H][W] (they do
+// not change between training steps) and only three are blurred here.
+template <bool kCached>
 __global__ void __launch_bounds__(kLossThreads) ssim_fwd(const float* __restrict__ x,
                                                          const float* __restrict__ y, int H, int W,
                                                          Win g, float inv_n,
                                                          float* __restrict__ gp, int64_t n,
-                                                         float* __restrict__ ssim_sum) {
+                                                         float* __restrict__ ssim_sum,
+                                                         const float* __restrict__ ystat) {
+    constexpr int kM = kCached ? 3 : 5;           // moments blurred here: x, [y], x^2, [y^2], xy
     __shared__ float sx[kHY][kHX + 1];
     __shared__ float sy[kHY][kHX + 1];
-    __shared__ float hs[5][kHY][kTX + 1];
+    __shared__ float hs[kM][kHY][kTX + 1];
     __shared__ float red[kLossThreads / 32];
     const int c = blockIdx.z;
     const int x0 = blockIdx.x * kTX - kRad, y0 = blockIdx.y * kTY - kRad;
@@ -105,52 +112,61 @@ __global__ void __launch_bounds__(kLossThreads) ssim_fwd(const float* __restrict
         float u[kSpan], v[kSpan];
 #pragma unroll
         for (int k = 0; k < kSpan; ++k) { u[k] = sx[r][q0 + k]; v[k] = sy[r][q0 + k]; }
-        float acc[5][kRun];
+        float acc[kM][kRun];
 #pragma unroll
         for (int t = 0; t < kRun; ++t)
 #pragma unroll
-            for (int j = 0; j < 5; ++j) acc[j][t] = 0.f;
+            for (int j = 0; j < kM; ++j) acc[j][t] = 0.f;
 #pragma unroll
         for (int k = 0; k < kSpan; ++k) {
-            const float uu = u[k] * u[k], vv = v[k] * v[k], uv = u[k] * v[k];
+            // channel order: x, x^2, xy (cached) or x, y, x^2, y^2, xy
+            float ch[kM];
+            if (kCached) {
+                ch[0] = u[k];
+                ch[1] = u[k] * u[k];
+                ch[kM - 1] = u[k] * v[k];
+            } else {
+                ch[0] = u[k];
+                ch[1] = v[k];
+                ch[2] = u[k] * u[k];
+                ch[3] = v[k] * v[k];
+                ch[kM - 1] = u[k] * v[k];
+            }
 #pragma unroll
             for (int t = 0; t < kRun; ++t) {
                 const int tap = k - t;
                 if (tap < 0 || tap >= kWin) continue;
                 const float w = g.w[tap];
-                acc[0][t] = fmaf(w, u[k], acc[0][t]);
-                acc[1][t] = fmaf(w, v[k], acc[1][t]);
-                acc[2][t] = fmaf(w, uu, acc[2][t]);
-                acc[3][t] = fmaf(w, vv, acc[3][t]);
-                acc[4][t] = fmaf(w, uv, acc[4][t]);
+#pragma unroll
+                for (int j = 0; j < kM; ++j) acc[j][t] = fmaf(w, ch[j], acc[j][t]);
             }
         }
 #pragma unroll
         for (int t = 0; t < kRun; ++t)
 #pragma unroll
-            for (int j = 0; j < 5; ++j) hs[j][r][q0 + t] = acc[j][t];
+            for (int j = 0; j < kM; ++j) hs[j][r][q0 + t] = acc[j][t];
     }
     __syncthreads();
     float local = 0.f;
     {
         const int qc = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * kRun;   // one run per thread
-        float m[5][kRun];
+        float m[kM][kRun];
 #pragma unroll
         for (int t = 0; t < kRun; ++t)
 #pragma unroll
-            for (int j = 0; j < 5; ++j) m[j][t] = 0.f;
+            for (int j = 0; j < kM; ++j) m[j][t] = 0.f;
 #pragma unroll
         for (int k = 0; k < kSpan; ++k) {
-            float hv[5];
+            float hv[kM];
 #pragma unroll
-            for (int j = 0; j < 5; ++j) hv[j] = hs[j][r0 + k][qc];
+            for (int j = 0; j < kM; ++j) hv[j] = hs[j][r0 + k][qc];
 #pragma unroll
             for (int t = 0; t < kRun; ++t) {
                 const int tap = k - t;
                 if (tap < 0 || tap >= kWin) continue;
                 const float w = g.w[tap];
 #pragma unroll
-                for (int j = 0; j < 5; ++j) m[j][t] = fmaf(w, hv[j], m[j][t]);
+                for (int j = 0; j < kM; ++j) m[j][t] = fmaf(w, hv[j], m[j][t]);
             }
         }
         const int gx = x0 + kRad + qc;
@@ -158,14 +174,20 @@ __global__ void __launch_bounds__(kLossThreads) ssim_fwd(const float* __restrict
         for (int t = 0; t < kRun; ++t) {
             const int gy = y0 + kRad + r0 + t;
             if (gx >= W || gy >= H) continue;
-            const float mx = m[0][t], my = m[1][t];
-            const float vx = m[2][t] - mx * mx, vy = m[3][t] - my * my, vxy = m[4][t] - mx * my;
+            const int64_t i = plane + (int64_t)gy * W + gx;
+            float mx, my, exx, eyy, exy;
+            if (kCached) {
+                mx = m[0][t]; exx = m[1][t]; exy = m[2][t];
+                my = ystat[i]; eyy = ystat[n + i];
+            } else {
+                mx = m[0][t]; my = m[1][t]; exx = m[2][t]; eyy = m[3][t]; exy = m[4][t];
+            }
+            const float vx = exx - mx * mx, vy = eyy - my * my, vxy = exy - mx * my;
             const float A1 = 2.f * mx * my + kC1, A2 = 2.f * vxy + kC2;
             const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
             const float S = (A1 * A2) / (B1 * B2);
             local += S;
             const float sS = S * inv_n;
-            const int64_t i = plane + (int64_t)gy * W + gx;
             gp[i] = sS * (2.f * my / A1 - 2.f * my / A2 - 2.f * mx / B1 + 2.f * mx / B2);
             gp[n + i] = -sS / B2;
             gp[2 * n + i] = 2.f * sS / A2;
@@ -289,6 +311,72 @@ __global__ void __launch_bounds__(kLossThreads) ssim_bwd(const float* __restrict
     if (threadIdx.x == 0) atomicAdd(l1_sum, s);
 }
 
+// The target's two window moments G*y and G*y^2 (zero padded), written to ystat[2][C][H][W]:
+// the same tiling and blur order as ssim_fwd, so the cached form uses the same values.
+__global__ void __launch_bounds__(kLossThreads) ssim_target_stats(const float* __restrict__ y,
+                                                                  int H, int W, Win g, int64_t n,
+                                                                  float* __restrict__ ystat) {
+    __shared__ float sy[kHY][kHX + 1];
+    __shared__ float hs[2][kHY][kTX + 1];
+    const int c = blockIdx.z;
+    const int x0 = blockIdx.x * kTX - kRad, y0 = blockIdx.y * kTY - kRad;
+    const int64_t plane = (int64_t)c * H * W;
+    for (int e = threadIdx.x; e < kHY * kHX; e += kLossThreads) {
+        const int r = e / kHX, q = e % kHX;
+        const int gy = y0 + r, gx = x0 + q;
+        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+        sy[r][q] = in ? y[plane + (int64_t)gy * W + gx] : 0.f;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kHRuns; e += kLossThreads) {
+        const int r = e >> 3, q0 = (e & 7) * kRun;
+        float acc[2][kRun];
+#pragma unroll
+        for (int t = 0; t < kRun; ++t) acc[0][t] = acc[1][t] = 0.f;
+#pragma unroll
+        for (int k = 0; k < kSpan; ++k) {
+            const float v = sy[r][q0 + k], vv = v * v;
+#pragma unroll
+            for (int t = 0; t < kRun; ++t) {
+                const int tap = k - t;
+                if (tap < 0 || tap >= kWin) continue;
+                acc[0][t] = fmaf(g.w[tap], v, acc[0][t]);
+                acc[1][t] = fmaf(g.w[tap], vv, acc[1][t]);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < kRun; ++t) {
+            hs[0][r][q0 + t] = acc[0][t];
+            hs[1][r][q0 + t] = acc[1][t];
+        }
+    }
+    __syncthreads();
+    const int qc = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * kRun;
+    float m[2][kRun];
+#pragma unroll
+    for (int t = 0; t < kRun; ++t) m[0][t] = m[1][t] = 0.f;
+#pragma unroll
+    for (int k = 0; k < kSpan; ++k) {
+        const float h0 = hs[0][r0 + k][qc], h1 = hs[1][r0 + k][qc];
+#pragma unroll
+        for (int t = 0; t < kRun; ++t) {
+            const int tap = k - t;
+            if (tap < 0 || tap >= kWin) continue;
+            m[0][t] = fmaf(g.w[tap], h0, m[0][t]);
+            m[1][t] = fmaf(g.w[tap], h1, m[1][t]);
+        }
+    }
+    const int gx = x0 + kRad + qc;
+#pragma unroll
+    for (int t = 0; t < kRun; ++t) {
+        const int gy = y0 + kRad + r0 + t;
+        if (gx >= W || gy >= H) continue;
+        const int64_t i = plane + (int64_t)gy * W + gx;
+        ystat[i] = m[0][t];
+        ystat[n + i] = m[1][t];
+    }
+}
+
 // loss = (1 - lam) * l1_sum / n + lam * (1 - ssim_sum / n), added to *loss
 __global__ void combine_loss(const float* sums, int64_t n, float lam, float* loss) {
     if (threadIdx.x == 0 && blockIdx.x == 0)
@@ -304,10 +392,19 @@ extern "C" size_t ogs_loss_l1_ssim_scratch_bytes(int32_t C, int32_t H, int32_t W
     return sizeof(float) * ((size_t)3 * C * H * W + 4) + 512;
 }
 
+extern "C" ogs_status ogs_ssim_target_stats(const float* target, int32_t C, int32_t H,
+                                            int32_t W, float* ystat, void* stream) {
+    if (!target || !ystat || C <= 0 || H <= 0 || W <= 0) return OGS_ERR_ARG;
+    const dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY, C);
+    ssim_target_stats<<<grid, kLossThreads, 0, (cudaStream_t)stream>>>(
+        target, H, W, make_window(), (int64_t)C * H * W, ystat);
+    return launch_status();
+}
+
 extern "C" ogs_status ogs_loss_l1_ssim(const float* img, const float* target, int32_t C,
                                        int32_t H, int32_t W, float lambda, float* dimg,
-                                       float* loss, void* scratch, size_t scratch_bytes,
-                                       void* stream) {
+                                       float* loss, const float* target_stats, void* scratch,
+                                       size_t scratch_bytes, void* stream) {
     if (!img || !target || !dimg || !scratch || C <= 0 || H <= 0 || W <= 0) return OGS_ERR_ARG;
     if (!(lambda >= 0.f && lambda <= 1.f)) return OGS_ERR_ARG;
     if (scratch_bytes < ogs_loss_l1_ssim_scratch_bytes(C, H, W) || !aligned(scratch, 16))
@@ -321,7 +418,12 @@ extern "C" ogs_status ogs_loss_l1_ssim(const float* img, const float* target, in
     if (cudaMemsetAsync(sums, 0, 4 * sizeof(float), st) != cudaSuccess) return OGS_ERR_CUDA;
     const dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY, C);
     const float inv_n = 1.0f / (float)n;
-    ssim_fwd<<<grid, kLossThreads, 0, st>>>(img, target, H, W, g, inv_n, gp, n, sums);
+    if (target_stats)
+        ssim_fwd<true><<<grid, kLossThreads, 0, st>>>(img, target, H, W, g, inv_n, gp, n, sums,
+                                                      target_stats);
+    else
+        ssim_fwd<false><<<grid, kLossThreads, 0, st>>>(img, target, H, W, g, inv_n, gp, n, sums,
+                                                       nullptr);
     ssim_bwd<<<grid, kLossThreads, 0, st>>>(gp, img, target, H, W, g, lambda, inv_n, n, dimg,
                                             sums + 1);
     if (loss) combine_loss<<<1, 32, 0, st>>>(sums, n, lambda, loss);

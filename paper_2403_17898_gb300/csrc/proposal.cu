@@ -509,10 +509,15 @@ __global__ void __launch_bounds__(kTrThreads) prop_train_kernel(TrainArgs a) {
     for (int e = t; e < kGrads; e += kTrThreads) out[e] = acc[e];
 }
 
-__global__ void prop_reduce(const float* __restrict__ partial, int nblocks, ogs_proposal g) {
+// dloss (device, may be null = 1): gradient of the caller's objective with respect to the BCE
+// loss, the chain-rule factor of every weight gradient
+__global__ void prop_reduce(const float* __restrict__ partial, int nblocks, ogs_proposal g,
+                            const float* __restrict__ dloss) {
+    const float scale = dloss ? *dloss : 1.0f;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kGrads; e += gridDim.x * blockDim.x) {
         float sum = 0.f;
         for (int b = 0; b < nblocks; ++b) sum += partial[(size_t)b * kGrads + e];
+        sum *= scale;
         float* dst;
         if (e < kGB1) dst = const_cast<float*>(g.w1) + (e - kGW1);
         else if (e < kGW2) dst = const_cast<float*>(g.b1) + (e - kGB1);
@@ -637,7 +642,7 @@ extern "C" ogs_status ogs_proposal_train(const float* pos, const uint8_t* level,
                                          const ogs_proposal* net, const uint32_t* sel_idx,
                                          const ogs_counts* counts, const uint32_t* maxc,
                                          float tau, float pos_weight, const ogs_proposal* grads,
-                                         float* loss,
+                                         float* loss, const float* dloss,
                                          void* scratch, size_t scratch_bytes, void* stream) {
     if (!pos || !level || !feat || !cam || !net_ok(net) || !sel_idx || !counts || !maxc ||
         !net_ok(grads) || !scratch)
@@ -656,6 +661,7 @@ extern "C" ogs_status ogs_proposal_train(const float* pos, const uint8_t* level,
                 pos_weight, (float*)scratch, loss};
     cudaStream_t st = (cudaStream_t)stream;
     prop_train_kernel<<<kTrBlocks, kTrThreads, smem, st>>>(a);
-    prop_reduce<<<(kGrads + 255) / 256, 256, 0, st>>>((const float*)scratch, kTrBlocks, *grads);
+    prop_reduce<<<(kGrads + 255) / 256, 256, 0, st>>>((const float*)scratch, kTrBlocks, *grads,
+                                                       dloss);
     return launch_status();
 }

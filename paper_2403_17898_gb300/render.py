@@ -134,6 +134,21 @@ class Renderer:
         self.pair_gauss = torch.empty(max(P, 1), dtype=torch.int32, device=dev)
         self.sort_scratch = torch.empty(abi.sort_scratch_bytes(G, P, self.gx * self.gy),
                                         dtype=torch.uint8, device=dev)
+        self._grad_bufs_cap = None          # backward buffers follow the capacities
+
+    def _grad_buffers(self):
+        """Per-Gaussian backward buffers (record, mean, scale and quaternion gradients) and the
+        decoder backward's scratch, sized by the current capacities; allocated on first use."""
+        if self._grad_bufs_cap != (self.sel_cap, self.pair_cap):
+            G = self.g_cap
+            dev = "cuda"
+            self.drec = torch.zeros(G, 9, device=dev)
+            self.dmeans = torch.empty(G, 3, device=dev)
+            self.dscales = torch.empty(G, 3, device=dev)
+            self.dquats = torch.empty(G, 4, device=dev)
+            self.db_scratch = torch.empty(abi.decode_bwd_scratch_bytes(self.sel_cap),
+                                          dtype=torch.uint8, device=dev)
+            self._grad_bufs_cap = (self.sel_cap, self.pair_cap)
 
     @property
     def g_cap(self):
@@ -151,6 +166,8 @@ class Renderer:
         assert int(cam.W) == self.W and int(cam.H) == self.H
         c = abi.camera(cam)
         st = stream if stream is not None else torch.cuda.current_stream()
+        # every forward overwrites the per-view buffers a backward reads
+        self.generation = getattr(self, "generation", 0) + 1
 
         def stage(name, fn):
             _stage(timers, name, st, fn)
@@ -178,7 +195,7 @@ class Renderer:
                     self.sel_idx, self.sel_w, self.sel_cap, self.counts_t, self.sel_idx_g,
                     self.sel_w_g, None, self.gate_scratch, st, bf16=self.precision == "bf16"))
                 sel, selw = self.sel_idx_g, self.sel_w_g
-        self.active_sel = sel
+        self.active_sel, self.active_selw = sel, selw
         if self.explicit is None and self.precision == "bf16" and self.fuse_decode_project:
             # decoded Gaussians go straight to screen records; the Gaussian SoA is written only
             # when a backward pass will need it
@@ -208,6 +225,43 @@ class Renderer:
             self.rec, self.pair_gauss, self.tile_range, self.W, self.H, bg,
             self.img if img is None else img, self.T,
             self.n_last, sel, self.k, maxc, n_eval, st))
+
+    def backward(self, cam, dimg, grads, dmlp_struct, bg=(0.0, 0.0, 0.0), stream=None,
+                 timers=None, on_drec=None):
+        """Backward of the view last enqueued (training mode, with ``cam``): dL/dimage ``dimg``
+        (f32[3][H][W] on the device) -> ogs_blend_bwd (transmittance recomputed from T_final,
+        no per-pair storage) -> ogs_project_bwd -> ogs_decode_bwd (FP32 or tensor-core BF16,
+        as the forward) or ogs_explicit_gaussians_bwd.  Anchor gradients accumulate into
+        ``grads`` (feat, offs, lv[, app] or offs, lv, ex.*), decoder gradients into the arrays
+        of ``dmlp_struct`` (an abi.mlp_struct).  ``on_drec(st)`` runs after the blend backward
+        (per-Gaussian statistics read self.drec there)."""
+        self._grad_buffers()
+        c = abi.camera(cam)
+        st = stream if stream is not None else torch.cuda.current_stream()
+
+        def bb():
+            self.drec.zero_()
+            abi.blend_bwd(self.rec, self.pair_gauss, self.tile_range, self.W, self.H, bg, self.T,
+                          self.n_last, dimg, self.drec, st)
+        _stage(timers, "blend_bwd", st, bb)
+        if on_drec is not None:
+            on_drec(st)
+        _stage(timers, "project_bwd", st, lambda: abi.project_bwd(
+            self._g_struct, self.g_cap, 1, c, self.rect, self.drec, self.dmeans, self.dscales,
+            self.dquats, self.counts_t, st))
+        sel, selw = self.active_sel, self.active_selw
+        if self.explicit is not None:
+            gex = {n: grads["ex." + n] for n in abi.EXPLICIT_NAMES}
+            _stage(timers, "decode_bwd", st, lambda: abi.explicit_gaussians_bwd(
+                self.pos, self.offs, self.lv, self.N, self.k, self.explicit, c, sel, selw,
+                self.sel_cap, self.counts_t, self.dmeans, self.dscales, self.dquats, self.drec,
+                gex, grads["offs"], grads["lv"], st))
+        else:
+            _stage(timers, "decode_bwd", st, lambda: abi.decode_bwd(
+                self.pos, self.feat, self.offs, self.lv, self.N, self._mlp_struct, c, sel, selw,
+                self.sel_cap, self.counts_t, self.dmeans, self.dscales, self.dquats, self.drec,
+                grads["feat"], grads["offs"], grads["lv"], dmlp_struct, self.db_scratch, st,
+                bf16=self.precision == "bf16"))
 
     def counts(self) -> FrameCounts:
         v = self.counts_t.cpu().numpy().view(np.uint32)
@@ -342,12 +396,18 @@ class Trainer(Renderer):
 
     def __init__(self, scene, mlp, W, H, lr=1e-3, betas=(0.9, 0.999), eps=1e-15, ssim_lambda=0.0,
                  track_view_frequency=False, track_growth=False, track_opacity=False,
-                 progressive=None, **kw):
+                 progressive=None, sparse_adam=True, **kw):
+        """``sparse_adam``: the anchor arrays take Adam only on the rows the step's views
+        selected (ogs_stamp_selected + ogs_adam_rows: untouched rows keep parameters and
+        moments); False updates every row every step.  Decoder weights always update."""
         super().__init__(scene, mlp, W, H, **kw)
         self.ssim_lambda = float(ssim_lambda)   # 0.2 gives the 0.8 L1 + 0.2 D-SSIM loss
         self.lr, self.betas, self.eps = lr, betas, eps
         self.step_count = 0
+        self.sparse_adam = bool(sparse_adam)
         dev = "cuda"
+        # step number of the last step whose views selected each anchor
+        self.stamp = torch.zeros(self.N, dtype=torch.int32, device=dev)
         self.grads = {n: torch.zeros_like(t) for n, t in self._anchor_params().items()}
         self.dmlp = {n: torch.zeros_like(t) for n, t in self.mlp.items()}
         self._structs()
@@ -359,6 +419,7 @@ class Trainer(Renderer):
         self.dimg = torch.zeros(3, self.H, self.W, device=dev)
         self.loss = torch.zeros(1, device=dev)
         self.loss_scratch = None
+        self._ssim_stats = {}            # target data_ptr -> (version, window moments)
         if self.ssim_lambda > 0:
             self.loss_scratch = torch.empty(abi.loss_l1_ssim_scratch_bytes(3, self.H, self.W),
                                             dtype=torch.uint8, device=dev)
@@ -378,7 +439,7 @@ class Trainer(Renderer):
         if progressive is not None:
             total, omega = progressive
             self.progressive = (int(total), progressive_schedule(self.NL, total, omega))
-        self._alloc_grad()
+        self._grad_buffers()
 
     def _anchor_params(self):
         """Trainable per-anchor arrays: features, offsets and l_v of the neural form; offsets,
@@ -398,58 +459,43 @@ class Trainer(Renderer):
         if self.explicit is None and hasattr(self, "dmlp"):
             self._dmlp_struct = abi.mlp_struct(self.dmlp, k=self.k, app=self.grads.get("app"))
 
-    def _alloc(self):
-        super()._alloc()
-        if hasattr(self, "grads"):
-            self._alloc_grad()
+    def _target_stats(self, target, st):
+        """The SSIM window moments of a target, computed once per target tensor (recomputed if
+        the tensor was modified in place since)."""
+        key = target.data_ptr()
+        hit = self._ssim_stats.get(key)
+        if hit is None or hit[0] != target._version or hit[1].shape[1:] != target.shape:
+            stats = torch.empty((2,) + tuple(target.shape), device="cuda")
+            abi.ssim_target_stats(target, stats, st)
+            hit = (target._version, stats)
+            self._ssim_stats[key] = hit
+        return hit[1]
 
-    def _alloc_grad(self):
-        G = self.g_cap
-        dev = "cuda"
-        self.drec = torch.zeros(G, 9, device=dev)
-        self.dmeans = torch.empty(G, 3, device=dev)
-        self.dscales = torch.empty(G, 3, device=dev)
-        self.dquats = torch.empty(G, 4, device=dev)
-        self.db_scratch = torch.empty(abi.decode_bwd_scratch_bytes(self.sel_cap),
-                                      dtype=torch.uint8, device=dev)
+    def enqueue(self, cam, infer=True, *args, **kw):
+        super().enqueue(cam, infer, *args, **kw)
+        if not infer:           # a training view: its anchors take the coming optimiser step
+            abi.stamp_selected(self.active_sel, self.counts_t, self.stamp, self.step_count + 1,
+                               kw.get("stream"))
 
     def backward_view(self, cam, target, bg=(0.0, 0.0, 0.0), stream=None, timers=None):
         """Loss and backward of the view last enqueued (its forward must have run in
         training mode with ``cam``); gradients accumulate."""
-        c = abi.camera(cam)
         st = stream if stream is not None else torch.cuda.current_stream()
         if self.ssim_lambda > 0:
+            stats = self._target_stats(target, st)
             _stage(timers, "loss", st, lambda: abi.loss_l1_ssim(
-                self.img, target, self.ssim_lambda, self.dimg, self.loss, self.loss_scratch, st))
+                self.img, target, self.ssim_lambda, self.dimg, self.loss, self.loss_scratch, st,
+                target_stats=stats))
         else:
             _stage(timers, "loss", st, lambda: abi.loss_l1(
                 self.img, target, self.img.numel(), self.dimg, self.loss, st))
-
-        def bb():
-            self.drec.zero_()
-            abi.blend_bwd(self.rec, self.pair_gauss, self.tile_range, self.W, self.H, bg, self.T,
-                          self.n_last, self.dimg, self.drec, st)
-        _stage(timers, "blend_bwd", st, bb)
+        on_drec = None
         if self.track_growth and self.explicit is None:
-            _stage(timers, "grow_stats", st, lambda: abi.grow_accumulate(
-                self.drec, self.tiles, self.sel_idx, self.counts_t, self.k, self.W, self.H,
-                self.grad_acc, self.grad_cnt, st))
-        _stage(timers, "project_bwd", st, lambda: abi.project_bwd(
-            self._g_struct, self.g_cap, 1, c, self.rect, self.drec, self.dmeans, self.dscales,
-            self.dquats, self.counts_t, st))
-        if self.explicit is not None:
-            gex = {n: self.grads["ex." + n] for n in abi.EXPLICIT_NAMES}
-            _stage(timers, "decode_bwd", st, lambda: abi.explicit_gaussians_bwd(
-                self.pos, self.offs, self.lv, self.N, self.k, self.explicit, c, self.sel_idx,
-                self.sel_w, self.sel_cap, self.counts_t, self.dmeans, self.dscales,
-                self.dquats, self.drec, gex, self.grads["offs"], self.grads["lv"], st))
-        else:
-            _stage(timers, "decode_bwd", st, lambda: abi.decode_bwd(
-                self.pos, self.feat, self.offs, self.lv, self.N, self._mlp_struct, c,
-                self.sel_idx, self.sel_w, self.sel_cap, self.counts_t, self.dmeans,
-                self.dscales, self.dquats, self.drec, self.grads["feat"], self.grads["offs"],
-                self.grads["lv"], self._dmlp_struct, self.db_scratch, st,
-                bf16=self.precision == "bf16"))
+            def on_drec(s):
+                _stage(timers, "grow_stats", s, lambda: abi.grow_accumulate(
+                    self.drec, self.tiles, self.sel_idx, self.counts_t, self.k, self.W, self.H,
+                    self.grad_acc, self.grad_cnt, s))
+        self.backward(cam, self.dimg, self.grads, self._dmlp_struct, bg, st, timers, on_drec)
 
     def active_level(self):
         """Finest octree level trained at the current iteration (all levels without a
@@ -481,10 +527,17 @@ class Trainer(Renderer):
         pairs = [(t, self.grads[n], n) for n, t in self._anchor_params().items()]
         pairs += [(self.mlp[n], self.dmlp[n], "mlp." + n) for n in self.mlp]
 
+        n_anchor = len(self._anchor_params())
+
         def run():
-            for p, g, n in pairs:
-                abi.adam(p, g, self.adam_m[n], self.adam_v[n], p.numel(), self.lr, b1, b2,
-                         self.eps, self.step_count, True, st)
+            for i, (p, g, n) in enumerate(pairs):
+                if self.sparse_adam and i < n_anchor:
+                    abi.adam_rows(p, g, self.adam_m[n], self.adam_v[n], self.stamp,
+                                  self.step_count, self.lr, b1, b2, self.eps, self.step_count,
+                                  True, st)
+                else:
+                    abi.adam(p, g, self.adam_m[n], self.adam_v[n], p.numel(), self.lr, b1, b2,
+                             self.eps, self.step_count, True, st)
         _stage(timers, "adam", st, run)
 
     def train_step(self, cams, targets, bg=(0.0, 0.0, 0.0), update=True, timers=None):
@@ -588,6 +641,7 @@ class Trainer(Renderer):
                     if not key.startswith("mlp."):
                         store[key] = torch.cat([store[key], zeros(store[key])])
             self.sel_count = torch.cat([self.sel_count, zeros(self.sel_count)])
+            self.stamp = torch.cat([self.stamp, zeros(self.stamp)])
             if self.track_opacity:
                 self.opac_sum = torch.cat([self.opac_sum, zeros(self.opac_sum)])
                 self.opac_views = torch.cat([self.opac_views, zeros(self.opac_views)])
@@ -642,6 +696,7 @@ class Trainer(Renderer):
         self._structs()
         self.N = n
         self.sel_count = gather(self.sel_count)
+        self.stamp = gather(self.stamp)
         self.sel_scratch = torch.empty(abi.lod_select_gated_scratch_bytes(self.N),
                                        dtype=torch.uint8, device=dev)
         if self.track_growth:              # the statistics follow their anchors

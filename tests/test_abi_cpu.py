@@ -103,3 +103,18 @@ def test_appearance_fields_checked_on_host(lib):
                 fake, fake, fake, fake, fake, fake, fake, fake, ctypes.byref(dm), fake, 1 << 30,
                 None)
         assert st == 1
+
+
+def test_counts_status_mapping(lib):
+    """ogs_counts_status is host code: a read-back counter record -> a status, non-finite
+    first, then expired waits, then capacity."""
+    import numpy as np
+    from paper_2403_17898_gb300 import abi
+    c = np.zeros(8, np.uint32)
+    assert abi.counts_status(c) == 0
+    c[3] = 2                                    # pair capacity overflowed
+    assert abi.counts_status(c) == 2
+    c[6] = 1                                    # and a bounded wait expired
+    assert abi.counts_status(c) == 3
+    assert abi.counts_status(c, nonfinite=1) == 5
+    assert abi.counts_status(np.zeros(8, np.uint32), nonfinite=4) == 5

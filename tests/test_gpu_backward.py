@@ -350,3 +350,119 @@ def test_finite_difference_through_gpu_street_scale(abi, torch):
         p[ix] = x0
         fd = (lp - lm) / (2 * h)
         assert abs(fd - g) <= 0.03 * abs(g) + 1e-6, (name, ix, g, fd)
+
+
+def test_adam_rows_match_oracle(abi, torch):
+    """Adam over stamped rows against the oracle's row Adam over four steps with different
+    touched sets (rows of 30 values, like the offsets): touched rows within FP32 rounding,
+    untouched rows bit for bit unchanged, gradients of touched rows cleared."""
+    rng = np.random.default_rng(11)
+    N, L = 5000, 30
+    p = rng.normal(size=(N, L)).astype(np.float32)
+    pt, mt_, vt = cuda(p), torch.zeros(N, L, device="cuda"), torch.zeros(N, L, device="cuda")
+    stamp = torch.zeros(N, dtype=torch.int32, device="cuda")
+    po, mo, vo = p.astype(np.float64), np.zeros((N, L)), np.zeros((N, L))
+    for step in range(1, 5):
+        rows = np.sort(rng.choice(N, size=rng.integers(1, N // 3), replace=False))
+        sel = cuda(rows.astype(np.int32))
+        counts = np.zeros(8, np.uint32)
+        counts[0] = len(rows)
+        abi.stamp_selected(sel, cuda(counts.view(np.int32)), stamp, step)
+        gr = np.zeros((N, L), np.float32)
+        gr[rows] = rng.normal(size=(len(rows), L)).astype(np.float32)
+        gt = cuda(gr)
+        before = pt.cpu().numpy()
+        abi.adam_rows(pt, gt, mt_, vt, stamp, step, 1e-2, 0.9, 0.999, 1e-8, step)
+        po, mo, vo = oracle.adam_rows(po, gr, mo, vo, rows, 1e-2, 0.9, 0.999, 1e-8, step)
+        torch.cuda.synchronize()
+        got = pt.cpu().numpy()
+        untouched = np.setdiff1d(np.arange(N), rows)
+        assert np.array_equal(got[untouched], before[untouched])
+        assert np.all(gt.cpu().numpy()[rows] == 0)
+        np.testing.assert_allclose(got, po, rtol=1e-5, atol=1e-6)
+        np.testing.assert_allclose(mt_.cpu().numpy(), mo, rtol=1e-5, atol=1e-7)
+
+
+def test_trainer_sparse_adam_touches_selected_rows_only(abi, torch):
+    """One training step of the cube: anchors no view selected keep their features, offsets,
+    l_v and Adam moments bit for bit; the selected ones move (a dense step would move every
+    row with a nonzero first moment, here none yet)."""
+    from paper_2403_17898_gb300.render import Trainer
+    sc, mlp, cams = synth.CONFIGS["cube4k_128"]()
+    cam = cams[0]
+    target = cuda(np.random.default_rng(1).uniform(size=(3, 128, 128)).astype(np.float32))
+    tr = Trainer(sc, mlp, 128, 128)
+    assert tr.sparse_adam
+    f0 = tr.feat.clone()
+    tr.train_step([cam], [target])
+    c = tr.counts()
+    torch.cuda.synchronize()
+    sel = to_np_u32(tr.sel_idx)[:c.n_selected].astype(np.int64)
+    touched = np.zeros(sc.N, bool)
+    touched[sel] = True
+    moved = (tr.feat != f0).any(dim=1).cpu().numpy()
+    assert moved.any() and not moved[~touched].any()
+    assert np.array_equal(to_np_u32(tr.stamp)[touched], np.ones(touched.sum(), np.uint32))
+    assert not tr.adam_m["feat"].cpu().numpy()[~touched].any()
+
+
+def test_scan_nonfinite(abi, torch):
+    """The opt-in non-finite scan: a clean buffer leaves the flag alone; a NaN or an infinity
+    anywhere (ragged length, last element included) sets the requested bit."""
+    rng = np.random.default_rng(2)
+    x = rng.normal(size=1_000_003).astype(np.float32)
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    abi.scan_nonfinite(cuda(x), flag, 4)
+    torch.cuda.synchronize()
+    assert flag.item() == 0
+    for pos, val in ((0, np.nan), (517_311, np.inf), (1_000_002, -np.inf)):
+        y = x.copy()
+        y[pos] = val
+        flag.zero_()
+        abi.scan_nonfinite(cuda(y), flag, 4)
+        torch.cuda.synchronize()
+        assert flag.item() == 4
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 5e-3), ("bf16", 6e-2)])
+def test_training_view_gradient_street_scale(abi, torch, precision, tol):
+    """One training view of the 500k-anchor street workload (1600x900, pose 10 of the
+    zoom-out), L1 against a seeded target, through the forward and backward the benchmark
+    times: features, offsets and l_v on a seeded sample of kept anchors and every decoder
+    weight against the FP64 oracle's analytic gradient, relative L2 within the chain
+    tolerance (FP32) or the BF16 bound (the decoder backward's BF16 products: ~3% on the
+    feature and first-layer gradients, see the tensor-core decoder tests)."""
+    from paper_2403_17898_gb300.render import Trainer
+    sc, mlp, cams = synth.CONFIGS["street500k_1600x900"]()
+    cam = cams[10]
+    target = np.random.default_rng(1).uniform(size=(3, cam.H, cam.W)).astype(np.float32)
+    tr = Trainer(sc, mlp, cam.W, cam.H, sel_cap=200_000, pair_cap=4_000_000,
+                 precision=precision)
+    c = tr.render(cam, infer=False)
+    assert c.overflow == 0 and c.timeout == 0
+    tr.zero_grad()
+    tr.loss.zero_()
+    tr.backward_view(cam, cuda(target))
+    torch.cuda.synchronize()
+    fr = oracle.render(sc, mlp, cam, infer=False)
+    L, dimg = oracle.l1_loss(fr.out["img"], target)
+    ref = oracle.render_grad(sc, mlp, cam, fr, dimg)
+    kept = fr.sel_idx
+    rng = np.random.default_rng(3)
+    sample = np.sort(rng.choice(kept, size=min(4000, len(kept)), replace=False))
+    assert len(kept) > 2000 and len(sample) >= 2000
+    errs = {}
+    for name, got in (("dfeat", tr.grads["feat"]), ("doffs", tr.grads["offs"]),
+                      ("dlv", tr.grads["lv"])):
+        a = got.cpu().numpy()[sample].astype(np.float64)
+        b = ref[name][sample]
+        errs[name] = np.linalg.norm(a - b) / np.linalg.norm(b)
+    for n in tr.mlp:
+        a, b = tr.dmlp[n].cpu().numpy().astype(np.float64), ref["d" + n]
+        errs["d" + n] = np.linalg.norm(a - b) / np.linalg.norm(b)
+    print(f"street500k view ({precision}): {c.n_selected} anchors, {c.n_pairs} pairs, loss "
+          f"{tr.loss.item():.6f} vs {L:.6f}; gradient relative L2:",
+          {k: f"{v:.2e}" for k, v in errs.items()})
+    assert abs(tr.loss.item() - L) <= 1e-4 * L
+    for k, v in errs.items():
+        assert v <= tol, (k, v)

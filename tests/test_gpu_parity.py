@@ -9,8 +9,8 @@ import pytest
 
 import oracle
 import synth
-from gpu_helpers import (NEAR_MARGIN, PIXEL_TOL, SEL_MARGIN, cuda, knife_pixel_mask, lib_ready,
-                         rect_margin, to_np_u32)
+from gpu_helpers import (NEAR_MARGIN, PIXEL_TOL, PX_MARGIN, SEL_MARGIN, cuda, knife_pixel_mask,
+                         lib_ready, rect_margin, to_np_u32)
 
 pytestmark = pytest.mark.gpu
 
@@ -318,6 +318,63 @@ def test_blend_matches_oracle(abi, torch):
     assert err[:, ok].max() <= PIXEL_TOL
     assert np.abs(Tf.cpu().numpy() - ref["T"])[ok].max() <= 1e-5
     assert np.array_equal(to_np_u32(nl)[ok], ref["last"][ok])
+
+
+def test_blend_eval_counts(abi, torch):
+    """n_eval: the tests the kernel made for each pixel while it still needed them.  Every
+    Gaussian the pixel blended must have been tested, and nothing after the Gaussian the pixel
+    saturated on: blended <= n_eval <= entries up to the stop (FP64 replay of the list,
+    pixels off the alpha / transmittance knife edges)."""
+    W, H = 72, 40
+    gx, gy = 5, 3
+    r = synth.random_records(3, 300, W, H, sigma=(0.8, 10.0))
+    G = 300
+    order = np.argsort(r["depth"], kind="stable")
+    T_ = gx * gy
+    lst = np.tile(order, T_).astype(np.int64)
+    start = np.arange(T_ + 1, dtype=np.int64) * G
+    uv = np.stack([r["u"], r["v"]], 1)
+    ref = oracle.blend(W, H, start, lst, uv, r["conic"], r["opac"], r["colors"])
+    rec = np.zeros((G, 12), np.float32)
+    rec[:, 0], rec[:, 1] = r["u"], r["v"]
+    rec[:, 2:4] = r["conic"][:, 0:2]
+    rec[:, 4], rec[:, 5] = r["conic"][:, 2], r["opac"]
+    rec[:, 6:9] = r["colors"]
+    rec[:, 9] = r["depth"]
+    rec[:, 11] = -np.log(255.0 * r["opac"].astype(np.float64))
+    tr = np.stack([start[:-1], start[1:]], 1).astype(np.int32)
+    img = torch.zeros(3, H, W, device="cuda")
+    Tf = torch.zeros(H, W, device="cuda")
+    nl = torch.zeros(H, W, dtype=torch.int32, device="cuda")
+    ne = torch.zeros(H, W, dtype=torch.int32, device="cuda")
+    abi.blend_fwd(cuda(rec), cuda(lst.astype(np.int32)), cuda(tr), W, H, (0.0, 0.0, 0.0), img,
+                  Tf, nl, n_eval=ne)
+    torch.cuda.synchronize()
+    # FP64 replay of Eq. 2 with the conventions, every pixel at once
+    ys, xs = np.mgrid[0:H, 0:W].astype(np.float64)
+    T = np.ones((H, W))
+    done = np.zeros((H, W), bool)
+    blended = np.zeros((H, W), np.int64)
+    stop = np.full((H, W), G, np.int64)
+    con = r["conic"].astype(np.float64)
+    for i, g in enumerate(order):
+        dx, dy = r["u"][g] - xs, r["v"][g] - ys
+        power = -0.5 * (con[g, 0] * dx * dx + con[g, 2] * dy * dy) - con[g, 1] * dx * dy
+        a = np.minimum(0.99, r["opac"][g] * np.exp(power))
+        pas = ~done & (power <= 0) & (a >= 1.0 / 255.0)
+        sat = pas & (T * (1 - a) < 1e-4)
+        stop[sat] = i + 1
+        app = pas & ~sat
+        blended += app
+        T = np.where(app, T * (1 - a), T)
+        done |= sat
+    ok = ref["px_margin"] >= PX_MARGIN
+    n = to_np_u32(ne).astype(np.int64)
+    assert ok.mean() > 0.9
+    assert np.all(n[ok] >= blended[ok]) and np.all(n[ok] <= stop[ok])
+    assert n.sum() < stop.sum()          # the warp-block culling skipped tests
+    print(f"blend tests: {n.sum()} made, {blended.sum()} blended, {stop.sum()} list entries up "
+          f"to the stops")
 
 
 # ---------------------------------------------------------------------------------------
