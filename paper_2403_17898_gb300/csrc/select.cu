@@ -12,6 +12,8 @@
 //                 and copies its staged entries into place; tile 0 also writes the totals.
 // No CTA waits on another, so every tile streams at full rate, and only kept anchors (a few
 // percent) are written twice.
+#include <cmath>
+
 #include "gate_common.cuh"
 
 namespace ogs {
@@ -30,73 +32,99 @@ struct SelArgs {
     int k;
     int infer;
     Cam cam;
+    float lod0;     // log2(d_max / s), formed on the host in double precision
 };
 
-// Returns true if an anchor at (px, py, pz) with level `lvl` and LOD bias `dl` is kept; w
-// receives its opacity weight.
-__device__ __forceinline__ bool keep_anchor(const SelArgs& a, float px, float py, float pz,
-                                           uint32_t lvl, float dl, float& w) {
+// Opacity weight of an anchor at (px, py, pz) with level `lvl` and LOD bias `dl`: 0 if it is
+// not kept.  Branch-free (every lane of a warp takes the same path).  The distance enters as
+// L* = log2(d_max / (d s)) + dL = log2(d_max / s) - log2(d^2) / 2 + dL: no square root and no
+// division, and the fast log2 is within ~1e-7 (absolute) of log2, far inside the decision
+// margins the oracle reports.
+__device__ __forceinline__ float anchor_weight(const SelArgs& a, float px, float py, float pz,
+                                               uint32_t lvl, float dl) {
     const Cam& c = a.cam;
-    float dx = px - c.c[0];
-    float dy = py - c.c[1];
-    float dz = pz - c.c[2];
+    const float dx = px - c.c[0];
+    const float dy = py - c.c[1];
+    const float dz = pz - c.c[2];
     // visibility of the anchor centre: in front of the near plane, within 1.3x half-fov
-    float zc = c.R[6] * dx + c.R[7] * dy + c.R[8] * dz;
-    float xc = c.R[0] * dx + c.R[1] * dy + c.R[2] * dz;
-    float yc = c.R[3] * dx + c.R[4] * dy + c.R[5] * dz;
-    if (!(zc > c.znear) || fabsf(xc) > c.limx * zc || fabsf(yc) > c.limy * zc) return false;
+    const float zc = c.R[6] * dx + c.R[7] * dy + c.R[8] * dz;
+    const float xc = c.R[0] * dx + c.R[1] * dy + c.R[2] * dz;
+    const float yc = c.R[3] * dx + c.R[4] * dy + c.R[5] * dz;
+    const bool vis = zc > c.znear && !(fabsf(xc) > c.limx * zc) && !(fabsf(yc) > c.limy * zc);
     // fractional level from the viewing distance plus the anchor's LOD bias, clamped
-    float d = sqrtf(dx * dx + dy * dy + dz * dz);
-    float Lraw = log2f(c.d_max / (d * c.s)) + dl;
-    float Ls = fminf(fmaxf(Lraw, 0.0f), (float)(a.NL - 1));
-    float Lh = floorf(Ls);
-    float L = (float)lvl;
-    if (L <= Lh) {
-        w = 1.0f;
-        return true;
-    }
-    if (a.infer && L == Lh + 1.0f && Ls > Lh) {
-        w = Ls - Lh;
-        return true;
-    }
-    return false;
+    const float d2 = dx * dx + dy * dy + dz * dz;
+    const float Lraw = fmaf(-0.5f, __log2f(d2), a.lod0) + dl;
+    const float Ls = fminf(fmaxf(Lraw, 0.0f), (float)(a.NL - 1));
+    const float Lh = floorf(Ls);
+    const float L = (float)lvl;
+    const float wnext = (a.infer && L == Lh + 1.0f && Ls > Lh) ? Ls - Lh : 0.0f;
+    const float w = L <= Lh ? 1.0f : wnext;
+    return vis ? w : 0.0f;
 }
 
-// Writes a tile's kept anchors compacted in ascending order: item `it` of thread t is anchor
-// it * kSelThreads + t of the tile, so the order is (item, warp, lane); keep/w of each item
-// come from registers.  s_wc[kSelItems][kSelWarps] is scratch; ends with a barrier.
-__device__ __forceinline__ uint32_t stage_tile(const bool (&keep)[kSelItems],
-                                               const float (&wv)[kSelItems], int64_t base,
+// Thread t of a tile owns its kSelItems consecutive anchors kSelItems * t + it.
+// Their opacity weights (0 = not kept) from the staged SoA: positions as six 16-byte shared
+// loads, LOD biases as two and levels as one 8-byte load.
+__device__ __forceinline__ void tile_weights(const SelArgs& a, const float* s_pos,
+                                             const float* s_dl, const uint8_t* s_lvl, int n_here,
+                                             float (&wv)[kSelItems]) {
+    static_assert(kSelItems == 8, "eight consecutive anchors per thread");
+    const int l0 = kSelItems * threadIdx.x;
+    float p[3 * kSelItems], dl[kSelItems];
+    const float4* p4 = reinterpret_cast<const float4*>(s_pos + 3 * l0);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const float4 v = p4[q];
+        p[4 * q] = v.x; p[4 * q + 1] = v.y; p[4 * q + 2] = v.z; p[4 * q + 3] = v.w;
+    }
+    const float4 d0 = reinterpret_cast<const float4*>(s_dl + l0)[0];
+    const float4 d1 = reinterpret_cast<const float4*>(s_dl + l0)[1];
+    dl[0] = d0.x; dl[1] = d0.y; dl[2] = d0.z; dl[3] = d0.w;
+    dl[4] = d1.x; dl[5] = d1.y; dl[6] = d1.z; dl[7] = d1.w;
+    const uint2 lv = *reinterpret_cast<const uint2*>(s_lvl + l0);
+#pragma unroll
+    for (int it = 0; it < kSelItems; ++it) {
+        const uint32_t lvl = ((it < 4 ? lv.x : lv.y) >> (8 * (it & 3))) & 0xFFu;
+        const float w = anchor_weight(a, p[3 * it], p[3 * it + 1], p[3 * it + 2], lvl, dl[it]);
+        wv[it] = l0 + it < n_here ? w : 0.0f;
+    }
+}
+
+// Writes a tile's kept anchors (weight > 0) compacted in ascending order: thread t owns the
+// consecutive anchors kSelItems * t + it, so its rank is the block's exclusive scan of the
+// per-thread counts.  s_wc (kSelWarps + 1 words) is scratch; ends with a barrier.
+__device__ __forceinline__ uint32_t stage_tile(const float (&wv)[kSelItems], int64_t base,
                                                uint32_t* __restrict__ st_idx,
-                                               float* __restrict__ st_w,
-                                               uint32_t (*s_wc)[kSelWarps]) {
+                                               float* __restrict__ st_w, uint32_t* s_wc) {
     const int t = threadIdx.x;
     const unsigned warp = t >> 5, lane = lane_id();
-    uint32_t bal[kSelItems];
+    uint32_t cnt = 0;
 #pragma unroll
-    for (int it = 0; it < kSelItems; ++it) {
-        bal[it] = __ballot_sync(0xffffffffu, keep[it]);
-        if (lane == 0) s_wc[it][warp] = __popc(bal[it]);
+    for (int it = 0; it < kSelItems; ++it) cnt += wv[it] > 0.0f ? 1u : 0u;
+    uint32_t x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= (unsigned)o) x += y;
     }
+    if (lane == 31) s_wc[warp] = x;
     __syncthreads();
-    uint32_t before = 0, total = 0;
+    uint32_t r = x - cnt, total = 0;
+#pragma unroll
+    for (int w = 0; w < kSelWarps; ++w) {
+        const uint32_t c = s_wc[w];
+        r += w < (int)warp ? c : 0u;
+        total += c;
+    }
+    const int64_t a0 = base + kSelItems * t;
 #pragma unroll
     for (int it = 0; it < kSelItems; ++it) {
-        uint32_t in_item = 0, warps_before = 0;
-#pragma unroll
-        for (int w = 0; w < kSelWarps; ++w) {
-            const uint32_t c = s_wc[it][w];
-            warps_before += w < (int)warp ? c : 0;
-            in_item += c;
-        }
-        if (keep[it]) {
-            const uint32_t r = before + warps_before + __popc(bal[it] & lanemask_lt());
-            st_idx[r] = (uint32_t)(base + it * kSelThreads + t);
+        if (wv[it] > 0.0f) {
+            st_idx[r] = (uint32_t)(a0 + it);
             st_w[r] = wv[it];
+            ++r;
         }
-        before += in_item;
     }
-    total = before;
     __syncthreads();                                  // s_wc free for the next tile
     return total;
 }
@@ -161,7 +189,7 @@ __global__ void __launch_bounds__(kSelThreads, 3) select_tiles(SelArgs a,
     pdl_trigger();
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t mbar[2];
-    __shared__ uint32_t s_wc[kSelItems][kSelWarps];
+    __shared__ uint32_t s_wc[kSelWarps];
     const int t = threadIdx.x;
     const int64_t nb = (a.N + kSelChunk - 1) / kSelChunk;
     auto full = [&](int64_t tile) { return bulk && (tile + 1) * kSelChunk <= a.N; };
@@ -180,16 +208,9 @@ __global__ void __launch_bounds__(kSelThreads, 3) select_tiles(SelArgs a,
         const int n_here = (int)min((int64_t)kSelChunk, a.N - base);
         const Stage st = stage_of(sm, s);
         land_tile(a, base, n_here, full(tile), st, &mbar[s], s, phases, counts);
-        bool keep[kSelItems];
         float wv[kSelItems];
-#pragma unroll
-        for (int it = 0; it < kSelItems; ++it) {
-            const int l = it * kSelThreads + t;
-            wv[it] = 0.0f;
-            keep[it] = l < n_here && keep_anchor(a, st.pos[3 * l], st.pos[3 * l + 1],
-                                                 st.pos[3 * l + 2], st.lvl[l], st.dl[l], wv[it]);
-        }
-        const uint32_t n = stage_tile(keep, wv, base, st_idx + base, st_w + base, s_wc);
+        tile_weights(a, st.pos, st.dl, st.lvl, n_here, wv);
+        const uint32_t n = stage_tile(wv, base, st_idx + base, st_w + base, s_wc);
         if (t == 0) tile_count[tile] = n;
     }
 }
@@ -228,7 +249,7 @@ __global__ void __launch_bounds__(kSelThreads, 3) select_eval_gated(
     __shared__ uint16_t s_list[kSelChunk];
     __shared__ uint8_t s_drop[kSelChunk];
     __shared__ __align__(8) uint64_t mbar, wbar, gbar;
-    __shared__ uint32_t s_wc[kSelItems][kSelWarps];
+    __shared__ uint32_t s_wc[kSelWarps];
     __shared__ uint32_t s_n;
     __shared__ uint32_t tmem_base;
     const int t = threadIdx.x;
@@ -279,14 +300,11 @@ __global__ void __launch_bounds__(kSelThreads, 3) select_eval_gated(
         __syncthreads();
         // LOD predicate; kept anchors listed (in any order) for the gate
         float wv[kSelItems];
+        tile_weights(a, s_pos, s_dl, s_lvl, n_here, wv);
 #pragma unroll
         for (int it = 0; it < kSelItems; ++it) {
-            const int l = it * kSelThreads + t;
-            float w = 0.0f;
-            const bool keep = l < n_here && keep_anchor(a, s_pos[3 * l], s_pos[3 * l + 1],
-                                                        s_pos[3 * l + 2], s_lvl[l], s_dl[l], w);
-            wv[it] = keep ? w : 0.0f;
-            if (keep) {
+            if (wv[it] > 0.0f) {
+                const int l = kSelItems * t + it;
                 s_drop[l] = 0;
                 s_list[atomicAdd(&s_n, 1u)] = (uint16_t)l;
             }
@@ -330,13 +348,12 @@ __global__ void __launch_bounds__(kSelThreads, 3) select_eval_gated(
         tc::fence_before_sync();
         __syncthreads();                              // s_drop complete; TMEM reads done
         tc::fence_after_sync();
-        bool kp[kSelItems];
 #pragma unroll
         for (int it = 0; it < kSelItems; ++it)
-            kp[it] = wv[it] > 0.0f && !(gated && s_drop[it * kSelThreads + t]);
+            if (gated && wv[it] > 0.0f && s_drop[kSelItems * t + it]) wv[it] = 0.0f;
         // a gate that stopped early: the staged arrays are free only now
         if (!issued && t == 0 && prefetch) sg_issue_tile(a, next, s_pos, s_dl, s_lvl, &mbar);
-        const uint32_t n = stage_tile(kp, wv, base, st_idx + base, st_w + base, s_wc);
+        const uint32_t n = stage_tile(wv, base, st_idx + base, st_w + base, s_wc);
         if (t == 0) tile_count[tile] = n;
     }
     tc::fence_before_sync();
@@ -443,7 +460,8 @@ extern "C" ogs_status ogs_lod_select(const float* pos, const uint8_t* level, con
         return OGS_ERR_ARG;
     if (scratch_bytes < ogs_lod_select_scratch_bytes(N) || !aligned(scratch, 16)) return OGS_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    SelArgs a{pos, level, dL, N, NL, k, infer, make_cam(*cam)};
+    SelArgs a{pos, level, dL, N, NL, k, infer, make_cam(*cam),
+              (float)std::log2((double)cam->d_max / (double)cam->s)};
     int nb = (int)((N + kSelChunk - 1) / kSelChunk);
     if (nb < 1) nb = 1;
     SelScratch sc;
@@ -486,7 +504,8 @@ extern "C" ogs_status ogs_lod_select_gated(const float* pos, const uint8_t* leve
         !aligned(feat, 16))
         return OGS_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    SelArgs a{pos, level, dL, N, NL, k, infer, make_cam(*cam)};
+    SelArgs a{pos, level, dL, N, NL, k, infer, make_cam(*cam),
+              (float)std::log2((double)cam->d_max / (double)cam->s)};
     int nb = (int)((N + kSelChunk - 1) / kSelChunk);
     if (nb < 1) nb = 1;
     SelScratch sc;
