@@ -34,9 +34,10 @@ WORKLOAD_DESC = ("2M anchors / 8 levels / 2 km synthetic city grid, k=10, 1920x1
                  "120-pose zoom-out 10 m -> 2 km, FP32 decode")
 METRIC = "1080p FPS (frames/s)"
 # FP32 operations of one (pixel, Gaussian) blend evaluation of Eq. 2 with the rasterizer
-# conventions: offset (2), quadratic form (7), exp (2), clamp/skip (3), transmittance and
-# stop (3), weight and colour (4)
-OPS_PER_EVAL = 21
+# conventions (one ex2 and about fifteen FP32 operations: offset, quadratic form, skip and
+# clamp tests, transmittance and stop, weight and colour), counted over the tests the kernel
+# executes (its n_eval output)
+OPS_PER_EVAL = 16
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -191,6 +192,59 @@ def cpu_baseline(sc, mlp, cams, frames=8):
                       f"120-pose path ({dt:.1f} s, FP64 C oracle, OpenMP in blending)"}
 
 
+SINGLE_THREAD_POSES = (30, 90)
+
+
+def run_cpu_single(args):
+    """Times the oracle on one host thread (launched by the GPU arm with OMP_NUM_THREADS=1):
+    full 1080p frames of the city path; prints one JSON line."""
+    sc, mlp, cams = _workload()
+    sc, mlp = _as_f64(sc, mlp)
+    oracle_frame(sc, mlp, cams[0])
+    t0 = time.perf_counter()
+    for p in SINGLE_THREAD_POSES:
+        oracle_frame(sc, mlp, cams[p])
+    dt = time.perf_counter() - t0
+    print(json.dumps({"value": len(SINGLE_THREAD_POSES) / dt, "unit": "frames/s", "cores": 1,
+                      "s_per_frame": dt / len(SINGLE_THREAD_POSES),
+                      "sample": f"{len(SINGLE_THREAD_POSES)} full 1920x1080 frames at poses "
+                                f"{list(SINGLE_THREAD_POSES)} ({dt:.1f} s, one thread)"}))
+    return 0
+
+
+def cpu_baseline_single_thread():
+    """The oracle on one host thread, in a child process (the OpenMP thread count is fixed
+    when the oracle library loads)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-single"], env=env,
+                       capture_output=True, text=True, timeout=900)
+    if r.returncode != 0:
+        return {"error": r.stderr[-300:]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_train_view():
+    """One view of the batched training step (8M anchors, 10 levels, 1080p, L1 + D-SSIM) on
+    the oracle with every host core: training-mode forward, loss and analytic backward; a step
+    of 16 views is extrapolated x16."""
+    import oracle
+    import synth
+    sc, mlp, cams = synth.CONFIGS["city8M_1080p"]()
+    pose = 20                            # the 6th of the step's 16 views (every 4th pose)
+    cam = cams[pose]
+    target = np.random.default_rng(4).uniform(size=(3, cam.H, cam.W))
+    t0 = time.perf_counter()
+    fr = oracle.render(sc, mlp, cam, infer=False)
+    L, dimg = oracle.photometric_loss(fr.out["img"], target, 0.2)
+    oracle.render_grad(sc, mlp, cam, fr, dimg)
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / (16.0 * dt), "unit": "train-steps/s", "cores": os.cpu_count(),
+            "s_per_view": dt, "s_per_step_x16": 16.0 * dt, "kind": "oracle",
+            "sample": f"one of the 16 training views of a step (8M anchors, 1920x1080, pose "
+                      f"{pose}), forward + L1/D-SSIM + backward in FP64, {dt:.1f} s; the step "
+                      f"time is 16x that"}
+
+
 def _as_f64(sc, mlp):
     """One-time float64 copies so the oracle's per-call conversions are no-ops."""
     import synth
@@ -238,12 +292,15 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------
 
 # kernels each ABI call launches per frame
-LAUNCHES = {"lod_select": 3, "lod_select_gated": 4, "decode_project": 2, "sort": 4,
+LAUNCHES = {"lod_select": 2, "lod_select_gated": 3, "decode_project": 2, "sort": 4,
             "blend_fwd": 1}
 DPSNR_GATE_DB = 0.05
-# DRAM bytes (read + write) of one blend_fwd launch from an ncu capture of the same kernel
-# (pose 14 of the path, profiles/blend_fwd_city2M_1080p.md): 31.72 MB + 2.33 MB
+# DRAM bytes (read + write) of one blend_fwd launch and its issue-slot use, from an ncu
+# capture of the same kernel on this workload (pose 14 of the path, BF16 decode)
 BLEND_FWD_DRAM_BYTES = 34.05e6
+BLEND_FWD_ISSUE_FRAC = 0.82
+BLEND_FWD_TRAFFIC_NOTE = ("dram read + write bytes of one launch (pose 14) from ncu; the "
+                          "records written by the projection mostly stay in L2")
 
 
 def _time_form(rd, cams, pose, steps, warmup, gate, flush, clk_index):
@@ -318,6 +375,7 @@ def _explicit_bench(cams, pose, steps, warmup, flush, clk_index):
     attr = synth.explicit_attributes(sc, seed=0)
     W, H = cams[0].W, cams[0].H
     rd = Renderer(sc, None, W, H, sel_cap=200_000, pair_cap=6_000_000, explicit=attr)
+    rd.track_last = False
     for cam in cams:                      # size the buffers on every pose
         rd.render(cam)
     t, stages, clk = _time_form(rd, cams, pose, steps, warmup, None, flush, clk_index)
@@ -342,6 +400,7 @@ def _appearance_bench(cams, pose, steps, warmup, flush, clk_index):
     del sc
     W, H = cams[0].W, cams[0].H
     rd = Renderer(sa, ma, W, H, sel_cap=200_000, pair_cap=6_000_000, precision="bf16")
+    rd.track_last = False
     for cam in cams:                      # size the buffers on every pose
         rd.render(cam)
     t, stages, clk = _time_form(rd, cams, pose, steps, warmup, None, flush, clk_index)
@@ -529,10 +588,10 @@ POS_WEIGHT = 4.0
 def _train_proposal(rd, train_cams, test_cams, full_rd):
     """Trains the anchor-visibility proposal on the training poses (BCE with positives
     weighted, so dropping a visible anchor costs more than keeping an invisible one),
-    calibrates p* as the largest threshold whose WORST calibration pose stays within the
-    PSNR budget, and assesses it on the held-out poses against full-detail renders.  If the
-    held-out poses exceed the budget, the plain LOD path is used (the gate's fallback)."""
-    import torch
+    calibrates p* on every 5th training pose as the largest threshold whose pooled PSNR loss
+    stays within the budget, and assesses it on the held-out poses against full-detail renders
+    (pooled and per view).  If the held-out poses exceed the budget, the plain LOD path is used
+    (the gate's fallback)."""
     import synth
     from paper_2403_17898_gb300 import proposal
     t0 = time.perf_counter()
@@ -541,39 +600,27 @@ def _train_proposal(rd, train_cams, test_cams, full_rd):
     hist = proposal.train(net, rd, views, epochs=30, pos_weight=POS_WEIGHT)
     t_train = time.perf_counter() - t0
 
-    def assess(cams, p_star):
-        """Set-level PSNR loss (pixel MSE pooled over the views) of the gated BF16 form
-        against the full-detail render, relative to the plain FP32 path, plus per-view
-        figures and the kept anchor fraction."""
-        se_plain = se_gate = 0.0
-        dps, kept = [], []
-        for cam in cams:
-            full_rd.render(proposal.full_detail(cam))
-            ref = full_rd.img
-            rd.precision = "fp32"
-            c0 = rd.render(cam)
-            plain = rd.img.clone()
-            rd.precision = "bf16"
-            c1 = rd.render(cam, gate=(net.w, p_star))
-            rd.precision = "fp32"
-            m0 = float(torch.mean((plain - ref) ** 2).item())
-            m1 = float(torch.mean((rd.img - ref) ** 2).item())
-            se_plain += m0
-            se_gate += m1
-            dps.append(proposal.psnr(plain, ref) - proposal.psnr(rd.img, ref))
-            kept.append(c1.n_selected / max(c0.n_selected, 1))
-        pooled = 10.0 * math.log10(se_gate / se_plain) if se_plain > 0 else 0.0
-        return pooled, float(np.median(dps)), float(np.max(dps)), float(np.mean(kept))
-
     calib = train_cams[::5]
-    p_star, curve = 0.0, []
-    for cand in (0.001, 0.002, 0.005, 0.01, 0.02, 0.05, 0.1, 0.2, 0.3, 0.5):
-        r = assess(calib, cand)
-        curve.append([cand] + [round(x, 4) for x in r])
-        if r[0] <= DPSNR_GATE_DB:
-            p_star = cand
-    pooled, med, mx, kept = assess(test_cams, p_star) if p_star > 0 else (0.0, 0.0, 0.0, 1.0)
+    p_star, curve = proposal.calibrate(rd, full_rd, calib, net.w, DPSNR_GATE_DB)
+    held = proposal.assess(rd, full_rd, test_cams, (net.w, p_star)) if p_star > 0 else None
+    pooled = held.pooled_db if held is not None else 0.0
     use_gate = p_star > 0 and pooled <= DPSNR_GATE_DB
+    per_view = None
+    if held is not None:
+        d = held.dpsnr
+        worst = int(np.argmax(d))
+        per_view = {
+            "psnr_plain_db": [round(x, 3) for x in held.psnr_plain],
+            "psnr_gated_db": [round(x, 3) for x in held.psnr_gated],
+            "kept_frac": [round(x, 4) for x in held.kept],
+            "worst_view": {"index": worst, "psnr_plain_db": held.psnr_plain[worst],
+                           "psnr_gated_db": held.psnr_gated[worst], "dpsnr_db": d[worst]},
+            "psnr_plain_db_min": float(np.min(held.psnr_plain)),
+            "psnr_gated_db_min": float(np.min(held.psnr_gated))}
+    med = float(np.median(held.dpsnr)) if held is not None else 0.0
+    mx = float(np.max(held.dpsnr)) if held is not None else 0.0
+    kept = float(np.mean(held.kept)) if held is not None else 1.0
+    curve = [[round(x, 4) for x in row] for row in curve]
     info = {"train_poses": len(train_cams), "heldout_poses": len(test_cams),
             "epochs": len(hist), "bce_first_epoch": hist[0], "bce_last_epoch": hist[-1],
             "pos_weight": POS_WEIGHT, "train_s": t_train, "p_star": p_star,
@@ -581,6 +628,8 @@ def _train_proposal(rd, train_cams, test_cams, full_rd):
             "calibration_curve[p*, dPSNR set, dPSNR view median, dPSNR view max, kept]": curve,
             "heldout_dpsnr_db_set": pooled, "heldout_dpsnr_db_view_median": med,
             "heldout_dpsnr_db_view_max": mx, "heldout_kept_anchor_frac": kept,
+            "heldout_per_view": per_view,
+            "p_star_calibrated_on": f"{len(calib)} of the training poses (every 5th)",
             "gate_used": use_gate,
             "dpsnr_definition": "10 log10(sum_v MSE(gated BF16_v, full_v) / sum_v MSE(plain FP32_v, "
                                 "full_v)) over the views: the PSNR of the view set, full = "
@@ -616,6 +665,9 @@ def run_gpu(args):
     del full_rd
     torch.cuda.empty_cache()
     gate = (net.w, p_star) if use_gate else None
+    # inference frames: no backward follows, so the blend does not record each pixel's last
+    # blended entry (image and T are bit-identical either way)
+    rd.track_last = False
 
     # plain FP32 form
     rd.precision = "fp32"
@@ -688,9 +740,11 @@ def run_gpu(args):
         ach = evals * OPS_PER_EVAL / (mean_ms["blend_fwd"] * 1e-3) / 1e12
         roof = {"kernel": "blend_fwd", "bound": "alu", "achieved": ach, "peak": alu_peak,
                 "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": BLEND_FWD_DRAM_BYTES,
-                "traffic_note": "bytes per launch from one ncu capture (pose 14); records "
-                                "written by the projection mostly stay in L2",
-                "work": f"{evals:.4g} (pixel, Gaussian) evaluations x {OPS_PER_EVAL} FP32 ops",
+                "traffic_note": BLEND_FWD_TRAFFIC_NOTE,
+                "issue_active_frac_ncu": BLEND_FWD_ISSUE_FRAC,
+                "work": f"{evals:.4g} (pixel, Gaussian) tests executed per frame (n_eval: the "
+                        f"entries of each pixel's warp-block list up to its stop) x "
+                        f"{OPS_PER_EVAL} FP32 ops",
                 "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                f"{sm_max:.0f} MHz ({src} sm_max_mhz)"}
     else:
@@ -747,17 +801,29 @@ def run_gpu(args):
                                       + LAUNCHES["decode_project"] + LAUNCHES["sort"]
                                       + LAUNCHES["blend_fwd"]),
     }
+    def extra(fn, *a):
+        """An additional measurement; a failure is recorded in the line instead of losing it."""
+        try:
+            return fn(*a)
+        except Exception as e:                       # noqa: BLE001 - reported, not hidden
+            return {"error": f"{type(e).__name__}: {e}"[:300]}
+
     if ws == 1 and not args.no_train:
         del rd
         torch.cuda.empty_cache()
-        line["explicit_3dgs"] = _explicit_bench(cams, pose, min(args.steps, 600), args.warmup,
-                                                flush, local)
-        line["appearance_codes"] = _appearance_bench(cams, pose, min(args.steps, 600),
-                                                     args.warmup, flush, local)
-        line["train"] = _train_bench(local)
-        line["train"]["street500k_1600x900_appearance"] = _train_appearance_bench(local)
+        line["explicit_3dgs"] = extra(_explicit_bench, cams, pose, min(args.steps, 600),
+                                      args.warmup, flush, local)
+        line["appearance_codes"] = extra(_appearance_bench, cams, pose, min(args.steps, 600),
+                                         args.warmup, flush, local)
+        line["train"] = extra(_train_bench, local)
+        if "error" not in line["train"]:
+            line["train"]["street500k_1600x900_appearance"] = extra(_train_appearance_bench,
+                                                                    local)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(*_as_f64(sc, mlp), cams)
+        line["cpu_baseline"]["single_thread"] = extra(cpu_baseline_single_thread)
+        if not args.no_train:
+            line["cpu_baseline"]["train_step_city8M"] = extra(cpu_baseline_train_view)
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
@@ -832,7 +898,10 @@ def main():
     ap.add_argument("--train-workload", default="street500k_1600x900",
                     choices=["street500k_1600x900", "city8M_1080p"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
+    ap.add_argument("--cpu-single", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.cpu_single:
+        return run_cpu_single(args)
     if args.profile:
         return run_profile(args)
     if args.profile_train:

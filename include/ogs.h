@@ -274,7 +274,8 @@ ogs_status ogs_radix_sort_pairs(uint32_t* keys, uint32_t* vals, const uint32_t* 
  *   rec, pair_gauss, tile_range from the calls above
  *   bg: host float[3]
  *   img f32[3][H][W], T_final f32[H][W], n_last u32[H][W] (list entries up to and
- *   including the last blended one); img may be pinned host memory (page-locked, so its
+ *   including the last blended one; optional, may be NULL when no backward follows: the
+ *   kernel then skips tracking it); img may be pinned host memory (page-locked, so its
  *   address is valid on the device under unified addressing): the image then goes to the
  *   host while the kernel runs, with no separate copy
  *   n_eval (optional, may be NULL): u32[H][W], (pixel, Gaussian) tests the kernel made for

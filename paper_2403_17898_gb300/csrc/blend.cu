@@ -25,7 +25,7 @@ constexpr int kExitEvery = 128;  // records walked between two warp-wide saturat
 
 // One pixel's compositing step with Gaussian `idx - 1` of the list, branch-free.  Returns the
 // weight alpha T added to the pixel (0 when it skipped the Gaussian or saturated on it).
-template <bool kEval>
+template <bool kEval, bool kLast>
 __device__ __forceinline__ float composite(float p2, float o, float cr, float cg, float cb,
                                            float pskip2, int idx, bool& done, float& T,
                                            float& C0, float& C1, float& C2, int& last,
@@ -43,12 +43,12 @@ __device__ __forceinline__ float composite(float p2, float o, float cr, float cg
     C1 = fmaf(cg, wgt, C1);
     C2 = fmaf(cb, wgt, C2);
     T = apply ? Tn : T;
-    last = apply ? idx : last;
+    if (kLast) last = apply ? idx : last;
     done = done || sat;
     return wgt;
 }
 
-template <bool kMaxC, bool kEval>
+template <bool kMaxC, bool kEval, bool kLast>
 __global__ void __launch_bounds__(kThreads) blend_fwd_kernel(
     const float4* __restrict__ rec, const uint32_t* __restrict__ pair_gauss,
     const uint2* __restrict__ tile_range, int W, int H, int gx, float bg0, float bg1, float bg2,
@@ -105,9 +105,9 @@ __global__ void __launch_bounds__(kThreads) blend_fwd_kernel(
                 const float p0 = power2(ax, dx, dy0, A.w, B.x);
                 const float p1 = power2(ax, dx, dy1, A.w, B.x);
                 const int idx = b0 + j + 1;
-                const float c0 = composite<kEval>(p0, B.y, B.z, B.w, Cc.x, Cc.y, idx, done0, T0,
+                const float c0 = composite<kEval, kLast>(p0, B.y, B.z, B.w, Cc.x, Cc.y, idx, done0, T0,
                                                   C00, C01, C02, last0, tests0);
-                const float c1 = composite<kEval>(p1, B.y, B.z, B.w, Cc.x, Cc.y, idx, done1, T1,
+                const float c1 = composite<kEval, kLast>(p1, B.y, B.z, B.w, Cc.x, Cc.y, idx, done1, T1,
                                                   C10, C11, C12, last1, tests1);
                 if (kMaxC) {
                     // contributions are >= 0, so their float bits order like unsigned ints
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kThreads) blend_fwd_kernel(
         img[plane + pix] = C01 + T0 * bg1;
         img[2 * plane + pix] = C02 + T0 * bg2;
         T_final[pix] = T0;
-        n_last[pix] = (uint32_t)last0;
+        if (kLast) n_last[pix] = (uint32_t)last0;
         if (kEval) n_eval[pix] = (uint32_t)tests0;
     }
     if (in1) {
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kThreads) blend_fwd_kernel(
         img[plane + pix] = C11 + T1 * bg1;
         img[2 * plane + pix] = C12 + T1 * bg2;
         T_final[pix] = T1;
-        n_last[pix] = (uint32_t)last1;
+        if (kLast) n_last[pix] = (uint32_t)last1;
         if (kEval) n_eval[pix] = (uint32_t)tests1;
     }
 }
@@ -149,29 +149,28 @@ extern "C" ogs_status ogs_blend_fwd(const ogs_rec2d* rec, const uint32_t* pair_g
                                     const float* bg, float* img, float* T_final,
                                     uint32_t* n_last, uint32_t* n_eval, const uint32_t* sel_idx,
                                     int32_t k, uint32_t* maxc, void* stream) {
-    if (!rec || !pair_gauss || !tile_range || !bg || !img || !T_final || !n_last) return OGS_ERR_ARG;
+    if (!rec || !pair_gauss || !tile_range || !bg || !img || !T_final) return OGS_ERR_ARG;
     if (width <= 0 || height <= 0 || !aligned(rec, 16) || !aligned(tile_range, 8)) return OGS_ERR_ARG;
     if (maxc && (!sel_idx || k <= 0)) return OGS_ERR_ARG;
     const int gx = (width + kTile - 1) / kTile, gy = (height + kTile - 1) / kTile;
     cudaStream_t st = (cudaStream_t)stream;
     const float4* r = reinterpret_cast<const float4*>(rec);
     const uint2* tr = reinterpret_cast<const uint2*>(tile_range);
-    const dim3 grid(gx * gy);
-    if (maxc && n_eval)
-        launch_pdl(blend_fwd_kernel<true, true>, dim3(grid), dim3(blend::kThreads), 0, st,
-            r, pair_gauss, tr, width, height, gx, bg[0], bg[1], bg[2], img, T_final, n_last,
-            n_eval, sel_idx, k, maxc);
-    else if (maxc)
-        launch_pdl(blend_fwd_kernel<true, false>, dim3(grid), dim3(blend::kThreads), 0, st,
-            r, pair_gauss, tr, width, height, gx, bg[0], bg[1], bg[2], img, T_final, n_last,
-            nullptr, sel_idx, k, maxc);
-    else if (n_eval)
-        launch_pdl(blend_fwd_kernel<false, true>, dim3(grid), dim3(blend::kThreads), 0, st,
-            r, pair_gauss, tr, width, height, gx, bg[0], bg[1], bg[2], img, T_final, n_last,
-            n_eval, nullptr, 1, nullptr);
-    else
-        launch_pdl(blend_fwd_kernel<false, false>, dim3(grid), dim3(blend::kThreads), 0, st,
-            r, pair_gauss, tr, width, height, gx, bg[0], bg[1], bg[2], img, T_final, n_last,
-            nullptr, nullptr, 1, nullptr);
+    const dim3 grid(gx * gy), block(blend::kThreads);
+    const int variant = (maxc ? 4 : 0) | (n_eval ? 2 : 0) | (n_last ? 1 : 0);
+#define OGS_BLEND(M, E, L)                                                                     \
+    launch_pdl(blend_fwd_kernel<M, E, L>, grid, block, 0, st, r, pair_gauss, tr, width, height, \
+               gx, bg[0], bg[1], bg[2], img, T_final, n_last, n_eval, sel_idx, k, maxc)
+    switch (variant) {
+        case 0: OGS_BLEND(false, false, false); break;
+        case 1: OGS_BLEND(false, false, true); break;
+        case 2: OGS_BLEND(false, true, false); break;
+        case 3: OGS_BLEND(false, true, true); break;
+        case 4: OGS_BLEND(true, false, false); break;
+        case 5: OGS_BLEND(true, false, true); break;
+        case 6: OGS_BLEND(true, true, false); break;
+        default: OGS_BLEND(true, true, true); break;
+    }
+#undef OGS_BLEND
     return launch_status();
 }

@@ -68,6 +68,9 @@ class Renderer:
         # BF16 gate: scored inside the selection pass (ogs_lod_select_gated); False runs
         # ogs_lod_select and ogs_proposal_gate_bf16 as two calls
         self.fuse_gate = True
+        # inference renders also record each pixel's last blended entry (n_last, which only a
+        # backward reads); False skips it in inference mode (training forwards always keep it)
+        self.track_last = True
         self.k = k
         self.W, self.H = int(W), int(H)
         self.gx, self.gy = (self.W + TILE - 1) // TILE, (self.H + TILE - 1) // TILE
@@ -221,10 +224,11 @@ class Renderer:
             self.depth_key, self.rect, self.tiles, self.g_cap, -1, self.gx, self.gy,
             self.pair_gauss, self.tile_range, self.pair_cap, self.counts_t, self.sort_scratch,
             st, tile_count=self.tile_count))
+        n_last = self.n_last if (not infer or self.track_last) else None
         stage("blend_fwd", lambda: abi.blend_fwd(
             self.rec, self.pair_gauss, self.tile_range, self.W, self.H, bg,
             self.img if img is None else img, self.T,
-            self.n_last, sel, self.k, maxc, n_eval, st))
+            n_last, sel, self.k, maxc, n_eval, st))
 
     def backward(self, cam, dimg, grads, dmlp_struct, bg=(0.0, 0.0, 0.0), stream=None,
                  timers=None, on_drec=None):

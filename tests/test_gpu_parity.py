@@ -462,3 +462,18 @@ def test_render_grows_buffers_on_overflow(abi, torch):
     fr = oracle.render(sc, mlp, cams[0])
     ok = ~knife_pixel_mask(fr, 128, 128)
     assert np.abs(rd.img.cpu().numpy() - fr.out["img"])[:, ok].max() <= PIXEL_TOL
+
+
+def test_render_without_n_last_is_bit_identical(abi, torch):
+    """Inference without the last-entry output (track_last=False, n_last = NULL): the image
+    and T are bit for bit those of the full forward, on a 1080p city frame."""
+    from paper_2403_17898_gb300.render import Renderer
+    sc, mlp, cams = synth.CONFIGS["city2M_1080p"]()
+    rd = Renderer(sc, mlp, 1920, 1080, sel_cap=200_000, pair_cap=4_000_000, precision="bf16")
+    for pose in (7, 70):
+        rd.track_last = True
+        rd.render(cams[pose])
+        img, T = rd.img.clone(), rd.T.clone()
+        rd.track_last = False
+        rd.render(cams[pose])
+        assert torch.equal(rd.img, img) and torch.equal(rd.T, T)
