@@ -185,12 +185,16 @@ __global__ void __launch_bounds__(kLossThreads) ssim_fwd(const float* __restrict
             const float vx = exx - mx * mx, vy = eyy - my * my, vxy = exy - mx * my;
             const float A1 = 2.f * mx * my + kC1, A2 = 2.f * vxy + kC2;
             const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
-            const float S = (A1 * A2) / (B1 * B2);
+            // four fast reciprocals (a few ulp) in place of seven divisions: the epilogue
+            // would otherwise cost as much as the blurs
+            const float iA1 = __fdividef(1.f, A1), iA2 = __fdividef(1.f, A2);
+            const float iB1 = __fdividef(1.f, B1), iB2 = __fdividef(1.f, B2);
+            const float S = A1 * A2 * iB1 * iB2;
             local += S;
             const float sS = S * inv_n;
-            gp[i] = sS * (2.f * my / A1 - 2.f * my / A2 - 2.f * mx / B1 + 2.f * mx / B2);
-            gp[n + i] = -sS / B2;
-            gp[2 * n + i] = 2.f * sS / A2;
+            gp[i] = 2.f * sS * (my * (iA1 - iA2) + mx * (iB2 - iB1));
+            gp[n + i] = -sS * iB2;
+            gp[2 * n + i] = 2.f * sS * iA2;
         }
     }
     const float s = block_sum(local, red);
