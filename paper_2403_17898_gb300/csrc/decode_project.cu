@@ -258,9 +258,25 @@ __global__ void __launch_bounds__(kDpThreads, 3) decode_project_tc(DpArgs a) {
             __syncthreads();
             tc::fence_after_sync();
             // ---- project: Gaussian g of the round on thread g % 256 (the same trip count for
-            //      every lane of a warp, for the tile counting) ----
-#pragma unroll 1
-            for (int it = 0; it < (kRoundGauss + kDpThreads - 1) / kDpThreads; ++it) {
+            //      every lane of a warp, for the tile counting).  The offsets of the thread's
+            //      Gaussians (the only global reads of this phase) are all loaded first, so
+            //      their latencies overlap ----
+            constexpr int kIters = (kRoundGauss + kDpThreads - 1) / kDpThreads;
+            float Opre[kIters][3];
+#pragma unroll
+            for (int it = 0; it < kIters; ++it) {
+                const int gr = it * kDpThreads + t;
+                const int gl = kRoundGauss * round + gr;
+                const int rl = gl / kK, i = gl - rl * kK;
+                if (gr < kRoundGauss && tile * kTM + rl < M) {
+                    const uint32_t j = __float_as_uint(rows[rl * kRowWords]);
+                    const float* O = a.offs + ((size_t)j * kK + i) * 3;
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) Opre[it][q] = O[q];
+                }
+            }
+#pragma unroll
+            for (int it = 0; it < kIters; ++it) {
                 const int gr = it * kDpThreads + t;                 // Gaussian of the round
                 const int gl = kRoundGauss * round + gr;            // Gaussian of the tile
                 const int rl = gl / kK, i = gl - rl * kK;
@@ -285,9 +301,8 @@ __global__ void __launch_bounds__(kDpThreads, 3) decode_project_tc(DpArgs a) {
                         yc[q] = y[4 * kK + 7 * i + 3 + q] + sb2[4 * kK + 7 * i + 3 + q];
                     const float inv = act_qinv(yc);
                     const float4 qu = make_float4(yc[0] * inv, yc[1] * inv, yc[2] * inv, yc[3] * inv);
-                    const float* O = a.offs + ((size_t)j * kK + i) * 3;
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) mu[q] = act_mean(dv[q], O[q], lvv[q]);
+                    for (int q = 0; q < 3; ++q) mu[q] = act_mean(dv[q], Opre[it][q], lvv[q]);
                     const size_t gi = g_base + gl;
                     if (a.write_gauss) {
                         a.out.opac[gi] = o;
