@@ -297,10 +297,11 @@ LAUNCHES = {"lod_select": 2, "lod_select_gated": 3, "decode_project": 2, "sort":
 DPSNR_GATE_DB = 0.05
 # DRAM bytes (read + write) of one blend_fwd launch and its issue-slot use, from an ncu
 # capture of the same kernel on this workload (pose 14 of the path, BF16 decode)
-BLEND_FWD_DRAM_BYTES = 34.05e6
-BLEND_FWD_ISSUE_FRAC = 0.82
-BLEND_FWD_TRAFFIC_NOTE = ("dram read + write bytes of one launch (pose 14) from ncu; the "
-                          "records written by the projection mostly stay in L2")
+BLEND_FWD_DRAM_BYTES = 33.09e6
+BLEND_FWD_ISSUE_FRAC = 0.83
+BLEND_FWD_TRAFFIC_NOTE = ("dram read + write bytes of one launch (pose 14, the no-n_last "
+                          "variant the timed frames run) from ncu: 31.72 MB read, 1.38 MB "
+                          "written; the records written by the projection mostly stay in L2")
 
 
 def _time_form(rd, cams, pose, steps, warmup, gate, flush, clk_index):
@@ -840,6 +841,7 @@ def run_profile(args):
     sc, mlp, cams = _workload()
     rd = Renderer(sc, mlp, cams[0].W, cams[0].H, sel_cap=200_000, pair_cap=4_000_000,
                   precision=args.precision)
+    rd.track_last = False            # as the timed inference frames
     gate = None
     if args.gate:
         # an untrained proposal network at p* = 0.5: the gate kernel's cost, not its quality
