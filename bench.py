@@ -292,7 +292,7 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------
 
 # kernels each ABI call launches per frame
-LAUNCHES = {"lod_select": 2, "lod_select_gated": 3, "decode_project": 2, "sort": 4,
+LAUNCHES = {"lod_select": 2, "lod_select_gated": 3, "decode_project": 2, "sort": 5,
             "blend_fwd": 1}
 DPSNR_GATE_DB = 0.05
 # DRAM bytes (read + write) of one blend_fwd launch and its issue-slot use, from an ncu

@@ -252,8 +252,11 @@ bool radix_sort(uint32_t* keys, uint32_t* vals, const uint32_t* n_dev, int64_t n
 constexpr int kBinThreads = 256;
 constexpr int kBinItems = 4;
 constexpr int kBinTile = kBinThreads * kBinItems;
-constexpr int kSmallThreads = 128;
-constexpr int kSmallSort = 2048;         // lists up to this length: one small CTA, 16 KB of keys
+constexpr int kWarpSort = 512;           // lists up to this length: one warp, keys in registers
+constexpr int kWarpTiles = 4;            // warps of a warp-sort CTA, one tile at a time each
+constexpr int kWarpGrid = 8 * 152;       // warp-sort CTAs: 8 resident per SM
+constexpr int kSmallSort = 2048;         // longer lists up to this length: 16 KB of keys ..
+constexpr int kSmallGrid = 2 * 152;      // .. in CTAs of kLargeThreads looping over those lists
 constexpr int kLargeThreads = 512;
 constexpr int kLargeSort = 16384;        // longer lists: 128 KB of keys in dynamic shared memory
 constexpr int kLargeGrid = 152;          // CTAs looping over the long lists
@@ -344,8 +347,9 @@ __global__ void __launch_bounds__(kBinThreads) bin_count(const uint32_t* __restr
 // Exclusive scan of the tile counts: one CTA per kScanChunk consecutive tiles (one tile per
 // thread).  Each CTA sums every count itself (the total decides the overflow state; the part
 // before its chunk is its offset: a few thousand words from L2), then scans its chunk: tile
-// ranges, fill cursors cleared, and the chunk's tiles too long for the small sorter listed in
-// the chunk's slot of `big` (count in nbig[chunk]), so no counter needs clearing first.  CTA 0
+// ranges, fill cursors cleared, and the chunk's tiles too long for the warp sorter listed in
+// the chunk's slot of `mid` (up to kSmallSort entries) or `big` (longer), with their numbers
+// in nmid[chunk] and nbig[chunk], so no counter needs clearing first.  CTA 0
 // writes P and the overflow state.
 constexpr int kScanChunk = 1024;
 
@@ -353,16 +357,18 @@ __global__ void __launch_bounds__(kScanChunk) tile_scan(const uint32_t* __restri
                                                         int ntiles, int64_t pair_cap,
                                                         uint2* __restrict__ range,
                                                         uint32_t* __restrict__ cursor,
+                                                        uint32_t* __restrict__ mid,
+                                                        uint32_t* __restrict__ nmid,
                                                         uint32_t* __restrict__ big,
                                                         uint32_t* __restrict__ nbig,
                                                         ogs_counts* counts) {
     pdl_wait();
     pdl_trigger();
     __shared__ unsigned long long s_red[2][kScanChunk / 32];
-    __shared__ uint32_t s_nbig;
+    __shared__ uint32_t s_nmid, s_nbig;
     const int t = threadIdx.x, lane = (int)lane_id(), warp = t >> 5;
     const int c0 = blockIdx.x * kScanChunk;
-    if (t == 0) s_nbig = 0;
+    if (t == 0) s_nmid = s_nbig = 0;
     // totals: before the chunk, and over all tiles
     unsigned long long before = 0, all = 0;
     for (int b = t; b < ntiles; b += kScanChunk) {
@@ -407,9 +413,12 @@ __global__ void __launch_bounds__(kScanChunk) tile_scan(const uint32_t* __restri
         cursor[b] = 0;
         if (!over && v > (uint32_t)kSmallSort)
             big[c0 + atomicAdd(&s_nbig, 1u)] = (uint32_t)b;
+        else if (!over && v > (uint32_t)kWarpSort)
+            mid[c0 + atomicAdd(&s_nmid, 1u)] = (uint32_t)b;
     }
     __syncthreads();
     if (t == 0) {
+        nmid[blockIdx.x] = s_nmid;
         nbig[blockIdx.x] = s_nbig;
         if (blockIdx.x == 0) {
             counts->need_pairs = (uint32_t)(P > 0xFFFFFFFFull ? 0xFFFFFFFFull : P);
@@ -570,42 +579,285 @@ __device__ __forceinline__ void sort_in_smem(unsigned long long* s_k, uint2 r,
     for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) ids[r.x + i] = (uint32_t)s_k[i];
 }
 
-// one 128-thread CTA per tile; lists longer than kSmallSort are left to tile_sort_large
-__global__ void __launch_bounds__(kSmallThreads, 10) tile_sort_small(const uint2* __restrict__ range,
-                                                                 const ogs_counts* counts,
-                                                                 uint32_t* __restrict__ keys,
-                                                                 uint32_t* __restrict__ ids) {
-    pdl_wait();
-    pdl_trigger();
-    __shared__ unsigned long long s_k[kSmallSort];
-    if (counts->overflow & 2u) return;
-    const uint2 r = range[blockIdx.x];
-    const uint32_t cnt = r.y - r.x;
-    if (cnt <= 1 || cnt > (uint32_t)kSmallSort) return;
-    sort_in_smem(s_k, r, keys, ids);
+// The largest power of two <= x (x >= 1), at compile time.
+__host__ __device__ constexpr int top_bit(int x) { return x < 2 ? 1 : 2 * top_bit(x / 2); }
+
+// The lower of two slots keeps the smaller key: 32-bit keys by min / max, 64-bit ones by a
+// compare and selects.
+__device__ __forceinline__ void cx_pair(uint32_t& a, uint32_t& b) {
+    const uint32_t lo = min(a, b), hi = max(a, b);
+    a = lo;
+    b = hi;
+}
+__device__ __forceinline__ void cx_pair(unsigned long long& a, unsigned long long& b) {
+    const bool lt = a < b;
+    const unsigned long long lo = lt ? a : b, hi = lt ? b : a;
+    a = lo;
+    b = hi;
+}
+__device__ __forceinline__ uint32_t cx_keep(uint32_t a, uint32_t p, bool lower) {
+    return lower ? min(a, p) : max(a, p);
+}
+__device__ __forceinline__ unsigned long long cx_keep(unsigned long long a, unsigned long long p,
+                                                      bool lower) {
+    return ((a < p) == lower) ? a : p;
 }
 
-// kLargeGrid CTAs loop over the long tiles listed per scan chunk (chunk c: big[c * kScanChunk
-// .. + nbig[c]]), in chunk order
-__global__ void __launch_bounds__(kLargeThreads) tile_sort_large(const uint2* __restrict__ range,
-                                                                 const uint32_t* __restrict__ big,
-                                                                 const uint32_t* __restrict__ nbig,
-                                                                 int nchunks,
-                                                                 const ogs_counts* counts,
-                                                                 uint32_t* __restrict__ keys,
-                                                                 uint32_t* __restrict__ ids) {
+// One step of the flip bitonic network over the 32 kPer slots of a warp, slot e = lane * kPer + j
+// held in v[j] of that lane: slot e meets slot e ^ M and the lower of the two keeps the smaller
+// key (M = size - 1 for a block flip, a power of two for a half-cleaner).  M < kPer pairs two
+// registers of one lane; otherwise the partner lane is lane ^ (M / kPer) and the value
+// exchanged is its slot j ^ (M mod kPer), by shuffle.
+template <class T, int kPer, int M>
+__device__ __forceinline__ void warp_cx(T (&v)[kPer], uint32_t lane) {
+    if constexpr (M < kPer) {
+#pragma unroll
+        for (int j = 0; j < kPer; ++j)
+            if (!(j & top_bit(M))) cx_pair(v[j], v[j ^ M]);
+    } else {
+        constexpr int jm = M % kPer, lm = M / kPer;
+        const bool lower = !(lane & (uint32_t)top_bit(lm));
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            if (j <= (j ^ jm)) {            // slots j and j ^ jm together (read before written)
+                const T a = v[j], b = v[j ^ jm];
+                v[j] = cx_keep(a, __shfl_xor_sync(0xffffffffu, b, lm), lower);
+                if (jm) v[j ^ jm] = cx_keep(b, __shfl_xor_sync(0xffffffffu, a, lm), lower);
+            }
+        }
+    }
+}
+
+// merge of size S (a flip, then half-cleaners S/4 .. 1), then the merges above it up to 32 kPer
+template <class T, int kPer, int S>
+__device__ __forceinline__ void warp_merges(T (&v)[kPer], uint32_t lane) {
+    if constexpr (S <= 32 * kPer) {
+        warp_cx<T, kPer, S - 1>(v, lane);
+        if constexpr (S >= 4) warp_cx<T, kPer, S / 4>(v, lane);
+        if constexpr (S >= 8) warp_cx<T, kPer, S / 8>(v, lane);
+        if constexpr (S >= 16) warp_cx<T, kPer, S / 16>(v, lane);
+        if constexpr (S >= 32) warp_cx<T, kPer, S / 32>(v, lane);
+        if constexpr (S >= 64) warp_cx<T, kPer, S / 64>(v, lane);
+        if constexpr (S >= 128) warp_cx<T, kPer, S / 128>(v, lane);
+        if constexpr (S >= 256) warp_cx<T, kPer, S / 256>(v, lane);
+        if constexpr (S >= 512) warp_cx<T, kPer, S / 512>(v, lane);
+        warp_merges<T, kPer, 2 * S>(v, lane);
+    }
+}
+
+constexpr int kPosBits = 9;                // list positions < kWarpSort
+constexpr int kFixRounds = 8;              // odd-even rounds before the exact re-sort
+static_assert((1 << kPosBits) == kWarpSort, "position field");
+
+// Exact form for a list of 2 <= cnt <= kWarpSort entries: the 512-slot network on the 64-bit
+// keys (depth << 32 | id), read from and written back to the list in place (every read lands
+// in registers before the first write).  Called by a whole warp; kept out of line, since it is
+// the rare path and its code would otherwise crowd the instruction cache.
+__device__ __noinline__ void warp_sort_exact(const uint32_t* __restrict__ keys,
+                                             uint32_t* __restrict__ ids, uint32_t cnt,
+                                             uint32_t lane) {
+    constexpr int kPer = kWarpSort / 32;
+    unsigned long long w[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const uint32_t e = lane * kPer + j;
+        w[j] = e < cnt ? ((unsigned long long)keys[e] << 32) | ids[e] : ~0ull;
+    }
+    warp_merges<unsigned long long, kPer, 2>(w, lane);
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const uint32_t e = lane * kPer + j;
+        if (e < cnt) ids[e] = (uint32_t)w[j];
+    }
+}
+
+// Exact order of two list positions p, q (the low kPosBits of their 32-bit keys): by depth,
+// then id, read from the warp's buffers.
+template <int kPer>
+__device__ __forceinline__ bool exact_less(uint32_t p, uint32_t q, const uint32_t* sd,
+                                           const uint32_t* si) {
+    p &= (1u << kPosBits) - 1;
+    q &= (1u << kPosBits) - 1;
+    const uint32_t dp = sd[p + p / kPer], dq = sd[q + q / kPer];
+    return dp != dq ? dp < dq : si[p + p / kPer] < si[q + q / kPer];
+}
+
+// One round (even pairs, then odd pairs) of odd-even transposition over the first cnt of the
+// 32 kPer slots of a warp (slot e = lane * kPer + j in v[j]): neighbours that share a quantised
+// depth and are out of exact order swap (neighbours with different quantised depths are in
+// order already).  Returns whether anything moved in this lane.
+template <int kPer>
+__device__ __forceinline__ bool oe_round(uint32_t (&v)[kPer], uint32_t lane, uint32_t cnt,
+                                         const uint32_t* sd, const uint32_t* si) {
+    bool moved = false;
+#pragma unroll
+    for (int phase = 0; phase < 2; ++phase) {
+        if constexpr (kPer >= 2) {
+#pragma unroll
+            for (int j = phase; j + 1 < kPer; j += 2) {
+                const uint32_t a = v[j], b = v[j + 1];
+                if (lane * kPer + j + 1 < cnt && (a >> kPosBits) == (b >> kPosBits) &&
+                    exact_less<kPer>(b, a, sd, si)) {
+                    v[j] = b;
+                    v[j + 1] = a;
+                    moved = true;
+                }
+            }
+        }
+        if (kPer == 1 || phase == 1) {
+            // pairs across lanes: my last slot (lower) with the next lane's first (upper)
+            const uint32_t up = __shfl_down_sync(0xffffffffu, v[0], 1);
+            const uint32_t dn = __shfl_up_sync(0xffffffffu, v[kPer - 1], 1);
+            const bool as_lower = (kPer > 1 || (lane & 1u) == (uint32_t)phase) && lane < 31 &&
+                                  (lane + 1) * kPer < cnt;
+            const bool as_upper = (kPer > 1 || (lane & 1u) != (uint32_t)phase) && lane > 0 &&
+                                  lane * kPer < cnt;
+            const uint32_t last = v[kPer - 1], first = v[0];
+            if (as_lower && (last >> kPosBits) == (up >> kPosBits) &&
+                exact_less<kPer>(up, last, sd, si)) {
+                v[kPer - 1] = up;
+                moved = true;
+            }
+            if (as_upper && (dn >> kPosBits) == (first >> kPosBits) &&
+                exact_less<kPer>(first, dn, sd, si)) {
+                v[0] = dn;
+                moved = true;
+            }
+        }
+    }
+    return moved;
+}
+
+// A warp sorts one tile's list of 2 <= cnt <= 32 kPer entries by the unique key (depth, id).
+// The depths and ids go to the warp's shared buffers sd / si (slot e at e + e / kPer, which
+// makes the lane-major reads conflict-free).  The network then runs in registers on 32-bit
+// keys (quantised depth << kPosBits | list position), the depth quantised as (depth bits -
+// the list's smallest) >> shift with the shift that fits the list's depth span in the other
+// 23 bits: a monotone map, so the result is in (depth, id) order except inside runs that share
+// a quantised depth (an exact tie, or depths closer than the quantum).  When there are such
+// runs, the sorted slots go through rounds of odd-even transposition on the exact keys (depth,
+// id) until a round moves nothing (every neighbour then in order: the list is sorted; runs are
+// short, so one or two rounds usually do); after kFixRounds rounds the list is sorted again
+// from scratch on the exact keys (warp_sort_exact).  Padding slots hold ~0,
+// at or above every real key.
+template <int kPer>
+__device__ __forceinline__ void warp_sort_list(uint32_t* sd, uint32_t* si, uint2 r, uint32_t lane,
+                                               const uint32_t* __restrict__ keys,
+                                               uint32_t* __restrict__ ids) {
+    const uint32_t cnt = r.y - r.x;
+    uint32_t dmin = 0xFFFFFFFFu, dmax = 0;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const uint32_t e = q * 32 + lane;
+        if (e < cnt) {
+            const uint32_t d = keys[r.x + e];
+            sd[e + e / kPer] = d;
+            si[e + e / kPer] = ids[r.x + e];
+            dmin = min(dmin, d);
+            dmax = max(dmax, d);
+        }
+    }
+    dmin = __reduce_min_sync(0xffffffffu, dmin);
+    dmax = __reduce_max_sync(0xffffffffu, dmax);
+    const uint32_t wide = (dmax - dmin) >> (32 - kPosBits);
+    const uint32_t shift = wide ? 32 - __clz(wide) : 0;
+    __syncwarp();
+    uint32_t v[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const uint32_t e = lane * kPer + j;
+        v[j] = e < cnt ? (((sd[lane * (kPer + 1) + j] - dmin) >> shift) << kPosBits) | e
+                       : 0xFFFFFFFFu;
+    }
+    warp_merges<uint32_t, kPer, 2>(v, lane);
+    // neighbours with one quantised depth?
+    bool tie = false;
+#pragma unroll
+    for (int j = 0; j + 1 < kPer; ++j)
+        tie |= lane * kPer + j + 1 < cnt && (v[j] >> kPosBits) == (v[j + 1] >> kPosBits);
+    const uint32_t next = __shfl_down_sync(0xffffffffu, v[0], 1);
+    tie |= lane < 31 && (lane + 1) * kPer < cnt && (v[kPer - 1] >> kPosBits) == (next >> kPosBits);
+    if (__any_sync(0xffffffffu, tie)) {
+        int round = 0;
+        bool settled = true;
+        while (__any_sync(0xffffffffu, oe_round<kPer>(v, lane, cnt, sd, si))) {
+            if (++round == kFixRounds) {
+                settled = false;
+                break;
+            }
+        }
+        if (!settled) {                     // uniform over the warp
+            warp_sort_exact(keys + r.x, ids + r.x, cnt, lane);
+            return;
+        }
+    }
+    // slots < cnt hold real keys, whose positions are < cnt: their ids, lane-major, to sd
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const uint32_t e = v[j] & ((1u << kPosBits) - 1);
+        sd[lane * (kPer + 1) + j] = lane * kPer + j < cnt ? si[e + e / kPer] : 0u;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const uint32_t e = q * 32 + lane;
+        if (e < cnt) ids[r.x + e] = sd[e + e / kPer];
+    }
+}
+
+// each warp sorts the lists of 2 .. kWarpSort entries of tiles warp, warp + W, warp + 2W, ..
+// (W = every warp of the grid), the network sized to the list: 32, 64, .., 512 slots
+__global__ void __launch_bounds__(32 * kWarpTiles, 8) tile_sort_warp(const uint2* __restrict__ range,
+                                                                     int n_tiles,
+                                                                     const ogs_counts* counts,
+                                                                     const uint32_t* __restrict__ keys,
+                                                                     uint32_t* __restrict__ ids) {
+    pdl_wait();
+    pdl_trigger();
+    constexpr int kBuf = kWarpSort + kWarpSort / 16;
+    __shared__ uint32_t s_d[kWarpTiles][kBuf], s_i[kWarpTiles][kBuf];
+    if (counts->overflow & 2u) return;
+    const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+    uint32_t *sd = s_d[warp], *si = s_i[warp];
+    for (int tile = blockIdx.x * kWarpTiles + (int)warp; tile < n_tiles;
+         tile += gridDim.x * kWarpTiles) {
+        const uint2 r = range[tile];
+        const uint32_t cnt = r.y - r.x;
+        if (cnt <= 1 || cnt > (uint32_t)kWarpSort) continue;
+        if (cnt <= 32) warp_sort_list<1>(sd, si, r, lane, keys, ids);
+        else if (cnt <= 64) warp_sort_list<2>(sd, si, r, lane, keys, ids);
+        else if (cnt <= 128) warp_sort_list<4>(sd, si, r, lane, keys, ids);
+        else if (cnt <= 256) warp_sort_list<8>(sd, si, r, lane, keys, ids);
+        else warp_sort_list<16>(sd, si, r, lane, keys, ids);
+        __syncwarp();
+    }
+}
+
+// gridDim.x CTAs loop over the tiles listed per scan chunk (chunk c: list[c * kScanChunk ..
+// + nlist[c]]), in chunk order, each list sorted in shared memory (cap keys) or, beyond that,
+// on global memory
+template <int kT>
+__global__ void __launch_bounds__(kT) tile_sort_listed(const uint2* __restrict__ range,
+                                                       const uint32_t* __restrict__ list,
+                                                       const uint32_t* __restrict__ nlist,
+                                                       int nchunks, uint32_t cap,
+                                                       const ogs_counts* counts,
+                                                       uint32_t* __restrict__ keys,
+                                                       uint32_t* __restrict__ ids) {
     pdl_wait();
     pdl_trigger();
     extern __shared__ unsigned long long s_k[];
     if (counts->overflow & 2u) return;
     uint32_t n = 0;
-    for (int c = 0; c < nchunks; ++c) n += nbig[c];
+    for (int c = 0; c < nchunks; ++c) n += nlist[c];
     for (uint32_t q = blockIdx.x; q < n; q += gridDim.x) {
         uint32_t c = 0, i = q;
-        while (i >= nbig[c]) i -= nbig[c++];
-        const uint2 r = range[big[c * kScanChunk + i]];
+        while (i >= nlist[c]) i -= nlist[c++];
+        const uint2 r = range[list[c * kScanChunk + i]];
         const uint32_t cnt = r.y - r.x;
-        if (cnt <= (uint32_t)kLargeSort) {
+        if (cnt <= cap) {
             sort_in_smem(s_k, r, keys, ids);
         } else {
             // longer than shared memory holds: the same network on global memory
@@ -624,8 +876,10 @@ __global__ void __launch_bounds__(kLargeThreads) tile_sort_large(const uint2* __
 struct SortScratch {
     uint32_t* tcount;   // per-tile pair counts
     uint32_t* cursor;   // per-tile fill cursors
-    uint32_t* big;      // tiles whose lists exceed kSmallSort
-    uint32_t* nbig;     // their number
+    uint32_t* mid;      // tiles whose lists exceed kWarpSort but not kSmallSort, per scan chunk
+    uint32_t* nmid;     // their number per chunk
+    uint32_t* big;      // tiles whose lists exceed kSmallSort, per scan chunk
+    uint32_t* nbig;     // their number per chunk
     uint32_t* keys;     // depth key of every pair
 };
 
@@ -635,6 +889,8 @@ size_t sort_layout(int64_t pair_cap, int n_tiles, void* base, SortScratch* s) {
     t.tcount = cv.take<uint32_t>(n_tiles > 0 ? n_tiles : 1);
     t.cursor = cv.take<uint32_t>(n_tiles > 0 ? n_tiles : 1);
     const int nchunks = n_tiles > 0 ? (n_tiles + kScanChunk - 1) / kScanChunk : 1;
+    t.mid = cv.take<uint32_t>((size_t)nchunks * kScanChunk);
+    t.nmid = cv.take<uint32_t>(nchunks);
     t.big = cv.take<uint32_t>((size_t)nchunks * kScanChunk);
     t.nbig = cv.take<uint32_t>(nchunks);
     t.keys = cv.take<uint32_t>(pair_cap > 0 ? pair_cap : 1);
@@ -701,18 +957,22 @@ extern "C" ogs_status ogs_sort(const uint32_t* depth_key, const uint32_t* rect, 
     if (!tile_count) bin_count<<<nb, kBinThreads, 0, st>>>(tiles, rc, n_dev, n_cap, grid_x, s.tcount);
     const int nchunks = (n_tiles + kScanChunk - 1) / kScanChunk;
     launch_pdl(tile_scan, dim3(nchunks), dim3(kScanChunk), 0, st,
-               tile_count ? tile_count : s.tcount, n_tiles, pair_cap, range, s.cursor, s.big,
-               s.nbig, counts);
+               tile_count ? tile_count : s.tcount, n_tiles, pair_cap, range, s.cursor, s.mid,
+               s.nmid, s.big, s.nbig, counts);
     launch_pdl(bin_fill, dim3(nb), dim3(kBinThreads), 0, st, tiles, rc, depth_key, n_dev, n_cap,
                grid_x, range, s.cursor, counts, s.keys, pair_gauss);
-    launch_pdl(tile_sort_small, dim3(n_tiles), dim3(kSmallThreads), 0, st,
-               range, counts, s.keys, pair_gauss);
+    const int wgrid = std::min((n_tiles + kWarpTiles - 1) / kWarpTiles, kWarpGrid);
+    launch_pdl(tile_sort_warp, dim3(wgrid), dim3(32 * kWarpTiles), 0, st, range, n_tiles, counts,
+               (const uint32_t*)s.keys, pair_gauss);
+    launch_pdl(tile_sort_listed<kLargeThreads>, dim3(kSmallGrid), dim3(kLargeThreads),
+               sizeof(unsigned long long) * kSmallSort, st, range, s.mid, s.nmid, nchunks,
+               (uint32_t)kSmallSort, counts, s.keys, pair_gauss);
     const size_t smem = sizeof(unsigned long long) * kLargeSort;
-    if (cudaFuncSetAttribute(tile_sort_large, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(tile_sort_listed<kLargeThreads>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return OGS_ERR_CUDA;
-    launch_pdl(tile_sort_large, dim3(kLargeGrid), dim3(kLargeThreads), smem, st, range, s.big,
-               s.nbig, nchunks, counts, s.keys, pair_gauss);
+    launch_pdl(tile_sort_listed<kLargeThreads>, dim3(kLargeGrid), dim3(kLargeThreads), smem, st,
+               range, s.big, s.nbig, nchunks, (uint32_t)kLargeSort, counts, s.keys, pair_gauss);
     return launch_status();
 }
 

@@ -276,6 +276,44 @@ def test_sort_matches_oracle_lists(abi, torch, G, gx, gy, ext_counts):
     assert np.all(tr[~nonempty] == 0)
 
 
+@pytest.mark.parametrize("depths", ["ties", "coarse", "narrow"])
+def test_sort_list_length_classes(abi, torch, depths):
+    """Tile lists of exactly the lengths at every sorter's boundaries: the warp sorter's
+    register networks of 32, 64, 128, 256 and 512 slots, the shared-memory sorters of 513 ..
+    2048 entries and beyond.  depths: "ties" repeats 10% of the depths exactly; "coarse" puts
+    one depth of 1e30 in every list, so the warp sorter's quantised depths are too coarse to
+    tell most of the others apart (its exact fallback); "narrow" draws distinct depths from
+    [1, 1.008): one float step apart or more, a quantum of one step, no fallback)."""
+    lengths = [0, 1, 2, 3, 31, 32, 33, 63, 64, 65, 100, 127, 128, 129, 200, 255, 256, 257,
+               400, 511, 512, 513, 1000, 2047, 2048, 2049, 3000]
+    gx, gy = 9, 3
+    rng = np.random.default_rng(11)
+    tiles = np.repeat(np.arange(len(lengths)), lengths)
+    rng.shuffle(tiles)
+    G = len(tiles)
+    x0, y0 = tiles % gx, tiles // gx
+    rect = np.stack([x0, y0, x0 + 1, y0 + 1], 1).astype(np.int32)
+    if depths == "narrow":
+        base = np.float32(1.0).view(np.uint32)
+        depth = (base + rng.permutation(1 << 16)[:G].astype(np.uint32)).view(np.float32)
+    else:
+        depth = rng.uniform(0.3, 100.0, size=G).astype(np.float32)
+    if depths == "ties":
+        tie = rng.uniform(size=G) < 0.1
+        depth[tie] = depth[rng.integers(0, G, size=int(tie.sum()))]
+    if depths == "coarse":
+        for t in range(len(lengths)):
+            members = np.nonzero(tiles == t)[0]
+            if len(members):
+                depth[members[0]] = np.float32(1e30)
+    start, lst, _ = oracle.tile_lists(rect, depth.astype(np.float64), gx, gy)
+    assert np.array_equal(np.diff(start), lengths)
+    for ext in (False, True):
+        pg, tr, c, P = _gpu_sort(abi, torch, rect, depth, gx, gy, ext_counts=ext)
+        assert c["n_pairs"] == P == G and c["overflow"] == 0
+        assert np.array_equal(pg[:P], lst)
+
+
 def test_sort_pair_overflow(abi, torch):
     rect, depth = synth.random_rects_depths(9, 2000, 20, 20, max_span=6)
     pg, tr, c, P = _gpu_sort(abi, torch, rect, depth, 20, 20, pair_cap=100)
