@@ -9,6 +9,7 @@
 //   by one thread, written as per-block partials and summed by a deterministic reduction.
 #include "internal.cuh"
 #include "decode_bwd.cuh"
+#include "tc.cuh"
 
 namespace ogs {
 namespace {
@@ -384,8 +385,9 @@ __global__ void __launch_bounds__(kDbThreads, 3) decode_bwd_rows(DbArgs a) {
 
 // Weight pass: dW2 = dY^T H (block-diagonal), dW1 = dP^T Z, db2 = sum dY, db1 = sum dP over
 // the selected anchors.  Split over anchors: each CTA stages chunks of kWChunk rows in shared
-// memory and accumulates fixed output items in registers (4 columns per item: 2 shared loads
-// per 4 FMAs); its totals go to its partial row, summed across CTAs in a fixed order.
+// memory (double-buffered bulk copies) and accumulates fixed output items in registers (4
+// columns per item: 2 shared loads per 4 FMAs); its totals go to its partial row, summed
+// across CTAs in a fixed order.
 constexpr int kWThreads = 256;
 constexpr int kWChunk = 32;
 constexpr int kItemsW2 = kNOut * (kH / 4);                // 880
@@ -394,11 +396,32 @@ constexpr int kItems4 = kItemsW2 + kItemsW1;              // 1744
 constexpr int kPerThread4 = (kItems4 + kWThreads - 1) / kWThreads;   // 7
 constexpr int kItems1 = kNOut + kNB1;                     // 206 bias sums
 
+// Shared-memory stage of one chunk: the four row arrays back to back, each [kWChunk][row].
+constexpr int kWStageFloats = kWChunk * (kRowY + kRowH + kRowP + kRowZ);
+constexpr int kWSmemBytes = 2 * kWStageFloats * (int)sizeof(float);
+constexpr uint32_t kWWaitLimit = 1u << 24;
+
+// Bulk copies of chunk ch's rows (the first nv of them; every row is a multiple of 16 bytes and
+// the arrays start 256-byte aligned) into stage `st`, completing on mbar.
+__device__ __forceinline__ void weights_issue(const DbArgs& a, float* stage, uint32_t ch,
+                                              uint32_t M, uint64_t* mbar) {
+    const uint32_t r0 = ch * kWChunk;
+    const uint32_t nv = min((uint32_t)kWChunk, M - r0);
+    tc::mbar_expect_tx(mbar, nv * 4u * (kRowY + kRowH + kRowP + kRowZ));
+    tc::bulk_load(stage, a.rowY + (size_t)r0 * kRowY, nv * 4u * kRowY, mbar);
+    tc::bulk_load(stage + kWChunk * kRowY, a.rowH + (size_t)r0 * kRowH, nv * 4u * kRowH, mbar);
+    tc::bulk_load(stage + kWChunk * (kRowY + kRowH), a.rowP + (size_t)r0 * kRowP,
+                  nv * 4u * kRowP, mbar);
+    tc::bulk_load(stage + kWChunk * (kRowY + kRowH + kRowP), a.rowZ + (size_t)r0 * kRowZ,
+                  nv * 4u * kRowZ, mbar);
+}
+
+// The chunks arrive by bulk copies into two shared-memory stages: the copy of a CTA's next
+// chunk is issued before its current one is summed (the other stage was released by the
+// barrier that ended the previous chunk), so the CTA's loads overlap its arithmetic.
 __global__ void __launch_bounds__(kWThreads) decode_bwd_weights(DbArgs a) {
-    __shared__ __align__(16) float sY[kWChunk][kRowY];
-    __shared__ __align__(16) float sH[kWChunk][kRowH];
-    __shared__ __align__(16) float sP[kWChunk][kRowP];
-    __shared__ __align__(16) float sZ[kWChunk][kRowZ];
+    extern __shared__ __align__(16) float s_w[];
+    __shared__ __align__(8) uint64_t mbar[2];
     const uint32_t M = a.counts->n_selected;
     const int t = threadIdx.x;
     float4 acc[kPerThread4];
@@ -406,33 +429,39 @@ __global__ void __launch_bounds__(kWThreads) decode_bwd_weights(DbArgs a) {
     for (int q = 0; q < kPerThread4; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     float acc1 = 0.f;
     const uint32_t nchunks = (M + kWChunk - 1) / kWChunk;
-    for (uint32_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-        const uint32_t r0 = ch * kWChunk;
-        const int nv = (int)min((uint32_t)kWChunk, M - r0);
-        __syncthreads();
-        for (int e = t; e < kWChunk * (kRowY / 4); e += kWThreads) {
-            const int q = e / (kRowY / 4), c4 = e % (kRowY / 4);
-            reinterpret_cast<float4*>(sY[q])[c4] = q < nv
-                ? reinterpret_cast<const float4*>(a.rowY + (size_t)(r0 + q) * kRowY)[c4]
-                : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (t == 0) {
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
+        if (blockIdx.x < nchunks) weights_issue(a, s_w, blockIdx.x, M, &mbar[0]);
+    }
+    __syncthreads();
+    bool timed_out = false;
+    uint32_t i = 0;
+    for (uint32_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x, ++i) {
+        const uint32_t st = i & 1u;
+        float* stage = s_w + st * kWStageFloats;
+        if (t == 0 && ch + gridDim.x < nchunks)
+            weights_issue(a, s_w + (st ^ 1u) * kWStageFloats, ch + gridDim.x, M, &mbar[st ^ 1u]);
+        if (!tc::mbar_wait(&mbar[st], (i >> 1) & 1u, kWWaitLimit)) {
+            timed_out = true;
+            // the copies may still be landing: wait for them (bounded) before moving on
+            tc::mbar_wait(&mbar[st], (i >> 1) & 1u, kWWaitLimit);
         }
-        for (int e = t; e < kWChunk * (kRowH / 4); e += kWThreads) {
-            const int q = e / (kRowH / 4), c4 = e % (kRowH / 4);
-            const bool in = q < nv;
-            reinterpret_cast<float4*>(sH[q])[c4] = in
-                ? reinterpret_cast<const float4*>(a.rowH + (size_t)(r0 + q) * kRowH)[c4]
-                : make_float4(0.f, 0.f, 0.f, 0.f);
-            reinterpret_cast<float4*>(sP[q])[c4] = in
-                ? reinterpret_cast<const float4*>(a.rowP + (size_t)(r0 + q) * kRowP)[c4]
-                : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int nv = (int)min((uint32_t)kWChunk, M - ch * kWChunk);
+        float(*sY)[kRowY] = reinterpret_cast<float(*)[kRowY]>(stage);
+        float(*sH)[kRowH] = reinterpret_cast<float(*)[kRowH]>(stage + kWChunk * kRowY);
+        float(*sP)[kRowP] = reinterpret_cast<float(*)[kRowP]>(stage + kWChunk * (kRowY + kRowH));
+        float(*sZ)[kRowZ] =
+            reinterpret_cast<float(*)[kRowZ]>(stage + kWChunk * (kRowY + kRowH + kRowP));
+        if (nv < kWChunk) {                   // the last, partial chunk: zero the rows past it
+            for (int e = t; e < (kWChunk - nv) * kRowY; e += kWThreads) sY[nv + e / kRowY][e % kRowY] = 0.f;
+            for (int e = t; e < (kWChunk - nv) * kRowH; e += kWThreads) {
+                sH[nv + e / kRowH][e % kRowH] = 0.f;
+                sP[nv + e / kRowP][e % kRowP] = 0.f;
+            }
+            for (int e = t; e < (kWChunk - nv) * kRowZ; e += kWThreads) sZ[nv + e / kRowZ][e % kRowZ] = 0.f;
+            __syncthreads();
         }
-        for (int e = t; e < kWChunk * (kRowZ / 4); e += kWThreads) {
-            const int q = e / (kRowZ / 4), c4 = e % (kRowZ / 4);
-            reinterpret_cast<float4*>(sZ[q])[c4] = q < nv
-                ? reinterpret_cast<const float4*>(a.rowZ + (size_t)(r0 + q) * kRowZ)[c4]
-                : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        __syncthreads();
 #pragma unroll
         for (int q = 0; q < kPerThread4; ++q) {
             const int item = t + q * kWThreads;
@@ -471,7 +500,9 @@ __global__ void __launch_bounds__(kWThreads) decode_bwd_weights(DbArgs a) {
             }
             acc1 += s;
         }
+        __syncthreads();                      // this stage is free for the copy after next
     }
+    if (timed_out && t == 0) atomicExch(const_cast<uint32_t*>(&a.counts->timeout), 1u);
     // this CTA's totals -> its partial row (flat layout of the decoder gradients)
     float* out = a.partial + (size_t)blockIdx.x * kNWeights;
 #pragma unroll
@@ -659,7 +690,10 @@ __global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ p, float*
 
 cudaError_t db::launch_weight_pass(const DbArgs& a, const DbScratch& s, const ogs_mlp& dmlp,
                                    cudaStream_t st) {
-    decode_bwd_weights<<<kDbBlocks, kWThreads, 0, st>>>(a);
+    cudaError_t e = cudaFuncSetAttribute(decode_bwd_weights,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kWSmemBytes);
+    if (e != cudaSuccess) return e;
+    decode_bwd_weights<<<kDbBlocks, kWThreads, kWSmemBytes, st>>>(a);
     reduce_partials<<<(kNWeights + 31) / 32, 32 * kRedWarps, 0, st>>>(s.partial, kDbBlocks, dmlp);
     if (a.mlp.A > 0) {
         decode_bwd_app_weights<<<kDbBlocks, kAppItems, 0, st>>>(a, s.partial_app);
