@@ -254,6 +254,36 @@ ogs_status ogs_sort(const uint32_t* depth_key, const uint32_t* rect, const uint3
                     uint32_t* pair_gauss, uint32_t* tile_range, int64_t pair_cap,
                     ogs_counts* counts, void* scratch, size_t scratch_bytes, void* stream);
 
+/* Per-tile pair regions: tile t owns the entries [t * tile_cap, t * tile_cap + count_t) of
+ * pair_gauss (Gaussian id) and pair_key (its depth key).  Both arrays u32[n_tiles *
+ * tile_cap], caller-owned. */
+typedef struct ogs_tile_bins {
+    uint32_t* pair_key;
+    uint32_t* pair_gauss;
+    uint32_t tile_cap;
+} ogs_tile_bins;
+
+/* ---------------------------------------------------------------------------------------
+ * ogs_sort_bins — the tile lists of Sec. 3.1, as ogs_sort gives them (each tile's Gaussians
+ * ordered by (depth key, id)), but each list in its tile's fixed region instead of packed:
+ * one pass places every (Gaussian, tile) pair in its tile's region at the slot the atomic
+ * that counts it returns, then every region is sorted in place.  No prefix scan and no
+ * second pass over the pairs.
+ *   depth_key, rect, tiles, g_cap, n_gauss, grid_x, grid_y: as ogs_sort
+ *   bins: the regions (host struct); pair_gauss holds the sorted lists afterwards and
+ *   pair_key is clobbered
+ *   tile_range u32[n_tiles][2]: [t * tile_cap, t * tile_cap + count_t) of each tile
+ *   counts->n_pairs = the number of pairs.  If a tile has more than tile_cap pairs, overflow
+ *   bit 1 is set, need_pairs = the largest count (the tile_cap that fits) and every range is
+ *   empty.
+ *   scratch: ogs_sort_bins_scratch_bytes(n_tiles) bytes, 16-byte aligned.
+ * ------------------------------------------------------------------------------------- */
+size_t ogs_sort_bins_scratch_bytes(int32_t n_tiles);
+ogs_status ogs_sort_bins(const uint32_t* depth_key, const uint32_t* rect, const uint32_t* tiles,
+                         int64_t g_cap, int64_t n_gauss, int32_t grid_x, int32_t grid_y,
+                         const ogs_tile_bins* bins /* host struct */, uint32_t* tile_range,
+                         ogs_counts* counts, void* scratch, size_t scratch_bytes, void* stream);
+
 /* ---------------------------------------------------------------------------------------
  * ogs_radix_sort_pairs — a stable LSD radix sort of (key, value) pairs (the sort of the
  * cited rasterizer's global (tile, depth) key design; ogs_sort builds the same lists per tile

@@ -53,6 +53,11 @@ class Gaussians(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("means", "scales", "quats", "opac", "colors")]
 
 
+class TileBins(C.Structure):
+    """ogs_tile_bins: per-tile pair regions (pair_key, pair_gauss u32[n_tiles * tile_cap])."""
+    _fields_ = [("pair_key", C.c_void_p), ("pair_gauss", C.c_void_p), ("tile_cap", C.c_uint32)]
+
+
 _P = C.c_void_p
 _I64 = C.c_int64
 _I32 = C.c_int32
@@ -81,6 +86,9 @@ _SIGS = {
                                           C.POINTER(Camera), _P, _P, _I64, _P,
                                           C.POINTER(Gaussians), _P, _P, _P, _P, _P, _P, _SZ,
                                           _P]),
+    "ogs_sort_bins_scratch_bytes": (_SZ, [_I32]),
+    "ogs_sort_bins": (C.c_int, [_P, _P, _P, _I64, _I64, _I32, _I32, C.POINTER(TileBins), _P,
+                                _P, _P, _SZ, _P]),
     "ogs_sort_scratch_bytes": (_SZ, [_I64, _I64, _I32]),
     "ogs_sort": (C.c_int, [_P, _P, _P, _P, _I64, _I64, _I32, _I32, _P, _P, _I64, _P, _P, _SZ,
                            _P]),
@@ -305,6 +313,12 @@ def decode_project_scratch_bytes():
     return int(lib().ogs_decode_project_scratch_bytes())
 
 
+def tile_bins(pair_key, pair_gauss, tile_cap):
+    """ogs_tile_bins of two device u32 arrays of n_tiles * tile_cap entries."""
+    return TileBins(C.c_void_p(pair_key.data_ptr()), C.c_void_p(pair_gauss.data_ptr()),
+                    int(tile_cap))
+
+
 def decode_project_bf16(pos, feat, offs, lv, N, mlp, cam, sel_idx, sel_w, sel_cap, counts,
                         rec, depth_key, rect, tiles, scratch, out=None, tile_count=None,
                         stream=None):
@@ -319,6 +333,19 @@ def decode_project_bf16(pos, feat, offs, lv, N, mlp, cam, sel_idx, sel_w, sel_ca
         _ptr(sel_idx), _ptr(sel_w), int(sel_cap), _ptr(counts), g, _ptr(rec), _ptr(depth_key),
         _ptr(rect), _ptr(tiles), _ptr(tile_count), _ptr(scratch), scratch.numel(),
         _stream(stream)), "ogs_decode_project_bf16")
+
+
+def sort_bins_scratch_bytes(n_tiles):
+    return int(lib().ogs_sort_bins_scratch_bytes(int(n_tiles)))
+
+
+def sort_bins(depth_key, rect, tiles, g_cap, n_gauss, grid_x, grid_y, bins, tile_range, counts,
+              scratch, stream=None):
+    """ogs_sort_bins: the tile lists in per-tile regions (``bins``, a TileBins)."""
+    _check(lib().ogs_sort_bins(_ptr(depth_key), _ptr(rect), _ptr(tiles), int(g_cap),
+                               int(n_gauss), int(grid_x), int(grid_y), C.byref(bins),
+                               _ptr(tile_range), _ptr(counts), _ptr(scratch), scratch.numel(),
+                               _stream(stream)), "ogs_sort_bins")
 
 
 def sort_scratch_bytes(g_cap, pair_cap, n_tiles):

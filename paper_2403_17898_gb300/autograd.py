@@ -60,11 +60,7 @@ class RenderFn(torch.autograd.Function):
             c = rd.counts()
             if not c.overflow:
                 break
-            if c.overflow & 1:
-                rd.sel_cap = int(c.need_selected * 1.25) + 1024
-            if c.overflow & 2:
-                rd.pair_cap = int(c.need_pairs * 1.25) + 4096
-            rd._alloc()
+            rd.grow_for(c)
         else:
             raise abi.OgsError("buffers kept overflowing")
         ctx.rd, ctx.cam, ctx.bg, ctx.generation = rd, cam, tuple(bg), rd.generation

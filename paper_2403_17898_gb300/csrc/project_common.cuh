@@ -140,4 +140,71 @@ __device__ __forceinline__ void count_tiles(uint32_t* tc, int gx, uint2 rc, uint
     }
 }
 
+// count_tiles, and each pair placed at once: the atomic that counts a (Gaussian, tile) pair
+// returns its slot in the tile's region of cap entries, where the Gaussian's id and depth key
+// go (pair_gauss[t * cap + slot], pair_key[...]); slots at or past cap are counted, not
+// written (the caller sees the overflow in the counts).  g and dkey are the lane's Gaussian.
+// A lane issues all its atomics (up to kOwnTiles at a time) before the first store that needs
+// a slot, so their round trips overlap instead of adding up.
+__device__ __forceinline__ void bin_tiles(uint32_t* tc, int gx, uint2 rc, uint32_t ntiles,
+                                          uint32_t g, uint32_t dkey, uint32_t cap,
+                                          uint32_t* __restrict__ pair_key,
+                                          uint32_t* __restrict__ pair_gauss) {
+    const uint32_t x0 = rc.x & 0xFFFFu, y0 = rc.x >> 16, x1 = rc.y & 0xFFFFu;
+    const uint32_t w = x1 - x0;
+    auto put = [&](uint32_t t, uint32_t slot, uint32_t gg, uint32_t kk) {
+        if (slot < cap) {
+            const size_t o = (size_t)t * cap + slot;
+            pair_gauss[o] = gg;
+            pair_key[o] = kk;
+        }
+    };
+    const bool own = ntiles > 0 && ntiles <= kOwnTiles;
+    const uint32_t t0 = own ? y0 * (uint32_t)gx + x0 : 0xFFFFFFFFu;
+    const uint32_t peers = __match_any_sync(0xffffffffu, t0);
+    const uint32_t leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (own && lane_id() == leader) base = atomicAdd(tc + t0, (uint32_t)__popc(peers));
+    if (own) {
+        uint32_t tt[kOwnTiles], sl[kOwnTiles];
+#pragma unroll
+        for (uint32_t i = 1; i < kOwnTiles; ++i) {
+            if (i < ntiles) {
+                tt[i] = (y0 + i / w) * (uint32_t)gx + x0 + i % w;
+                sl[i] = atomicAdd(tc + tt[i], 1u);
+            }
+        }
+#pragma unroll
+        for (uint32_t i = 1; i < kOwnTiles; ++i)
+            if (i < ntiles) put(tt[i], sl[i], g, dkey);
+    }
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (own) put(t0, base + __popc(peers & lanemask_lt()), g, dkey);
+    uint32_t big = __ballot_sync(0xffffffffu, ntiles > kOwnTiles);
+    while (big) {
+        const int src = __ffs(big) - 1;
+        big &= big - 1;
+        const uint2 r = make_uint2(__shfl_sync(0xffffffffu, rc.x, src),
+                                   __shfl_sync(0xffffffffu, rc.y, src));
+        const uint32_t bg = __shfl_sync(0xffffffffu, g, src);
+        const uint32_t bk = __shfl_sync(0xffffffffu, dkey, src);
+        const uint32_t bx0 = r.x & 0xFFFFu, by0 = r.x >> 16, bw = (r.y & 0xFFFFu) - bx0;
+        const uint32_t bn = bw * ((r.y >> 16) - by0);
+        for (uint32_t i0 = 0; i0 < bn; i0 += 32 * kOwnTiles) {
+            uint32_t tt[kOwnTiles], sl[kOwnTiles];
+#pragma unroll
+            for (uint32_t j = 0; j < kOwnTiles; ++j) {
+                const uint32_t i = i0 + j * 32 + lane_id();
+                if (i < bn) {
+                    tt[j] = (by0 + i / bw) * (uint32_t)gx + bx0 + i % bw;
+                    sl[j] = atomicAdd(tc + tt[j], 1u);
+                }
+            }
+#pragma unroll
+            for (uint32_t j = 0; j < kOwnTiles; ++j)
+                if (i0 + j * 32 + lane_id() < bn) put(tt[j], sl[j], bg, bk);
+        }
+    }
+}
+
 }  // namespace ogs

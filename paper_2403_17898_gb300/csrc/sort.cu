@@ -19,6 +19,7 @@
 #include <mutex>
 
 #include "internal.cuh"
+#include "project_common.cuh"
 
 namespace ogs {
 namespace {
@@ -427,6 +428,107 @@ __global__ void __launch_bounds__(kScanChunk) tile_scan(const uint32_t* __restri
                 counts->n_pairs = 0;
             } else {
                 counts->n_pairs = (uint32_t)P;
+            }
+        }
+    }
+}
+
+// One pass over the Gaussians (one per thread, every lane of a warp calls bin_tiles):
+// each (Gaussian, tile) pair is counted by an atomic whose return value is its slot in the
+// tile's region, where its id and depth key are written.
+__global__ void __launch_bounds__(kBinThreads) bin_regions(const uint32_t* __restrict__ dkey,
+                                                           const uint2* __restrict__ rect,
+                                                           const uint32_t* __restrict__ tiles,
+                                                           const uint32_t* n_dev, int64_t n_cap,
+                                                           int gx, uint32_t* __restrict__ tc,
+                                                           uint32_t cap,
+                                                           uint32_t* __restrict__ keys,
+                                                           uint32_t* __restrict__ ids) {
+    pdl_wait();
+    pdl_trigger();
+    const uint32_t n = count_of(n_dev, n_cap);
+    const int64_t g = (int64_t)blockIdx.x * kBinThreads + threadIdx.x;
+    if ((int64_t)blockIdx.x * kBinThreads >= n) return;        // whole CTA out of range
+    uint32_t c = 0, k = 0xFFFFFFFFu;
+    uint2 rc = make_uint2(0, 0);
+    if (g < n) {
+        c = tiles[g];
+        if (c) {
+            rc = rect[g];
+            k = dkey[g];
+        }
+    }
+    bin_tiles(tc, gx, rc, c, (uint32_t)g, k, cap, keys, ids);
+}
+
+// Ranges of the binned lists: tile t owns [t cap, t cap + count_t).  One
+// CTA per kScanChunk tiles: every CTA reads all the counts itself (their total and largest
+// decide the pair count and the overflow state), then lists its chunk's tiles too long for
+// the warp sorter in `mid` (up to kSmallSort entries) or `big`, as tile_scan does.  CTA 0
+// writes P and the overflow state.
+__global__ void __launch_bounds__(kScanChunk) bins_scan(const uint32_t* __restrict__ tcount,
+                                                        int ntiles, uint32_t cap,
+                                                        uint2* __restrict__ range,
+                                                        uint32_t* __restrict__ mid,
+                                                        uint32_t* __restrict__ nmid,
+                                                        uint32_t* __restrict__ big,
+                                                        uint32_t* __restrict__ nbig,
+                                                        ogs_counts* counts) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ unsigned long long s_sum[kScanChunk / 32];
+    __shared__ uint32_t s_max[kScanChunk / 32];
+    __shared__ uint32_t s_nmid, s_nbig;
+    const int t = threadIdx.x, lane = (int)lane_id(), warp = t >> 5;
+    const int c0 = blockIdx.x * kScanChunk;
+    if (t == 0) s_nmid = s_nbig = 0;
+    unsigned long long all = 0;
+    uint32_t mx = 0;
+    for (int b = t; b < ntiles; b += kScanChunk) {
+        const uint32_t v = tcount[b];
+        all += v;
+        mx = max(mx, v);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        all += __shfl_xor_sync(0xffffffffu, all, o);
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if (lane == 0) {
+        s_sum[warp] = all;
+        s_max[warp] = mx;
+    }
+    __syncthreads();
+    unsigned long long P = 0;
+    uint32_t M = 0;
+#pragma unroll 8
+    for (int w = 0; w < kScanChunk / 32; ++w) {
+        P += s_sum[w];
+        M = max(M, s_max[w]);
+    }
+    const bool over = M > cap;
+    const int b = c0 + t;
+    if (b < ntiles) {
+        const uint32_t v = tcount[b];
+        const uint32_t st = (uint32_t)b * cap;
+        range[b] = over ? make_uint2(0, 0) : make_uint2(st, st + v);
+        if (!over && v > (uint32_t)kSmallSort)
+            big[c0 + atomicAdd(&s_nbig, 1u)] = (uint32_t)b;
+        else if (!over && v > (uint32_t)kWarpSort)
+            mid[c0 + atomicAdd(&s_nmid, 1u)] = (uint32_t)b;
+    }
+    __syncthreads();
+    if (t == 0) {
+        nmid[blockIdx.x] = s_nmid;
+        nbig[blockIdx.x] = s_nbig;
+        if (blockIdx.x == 0) {
+            if (over) {
+                atomicOr(&counts->overflow, 2u);
+                counts->need_pairs = M;
+                counts->n_pairs = 0;
+            } else {
+                counts->need_pairs = (uint32_t)(P > 0xFFFFFFFFull ? 0xFFFFFFFFull : P);
+                counts->n_pairs = (uint32_t)(P > 0xFFFFFFFFull ? 0xFFFFFFFFull : P);
             }
         }
     }
@@ -924,6 +1026,76 @@ extern "C" ogs_status ogs_radix_sort_pairs(uint32_t* keys, uint32_t* vals, const
 extern "C" size_t ogs_sort_scratch_bytes(int64_t g_cap, int64_t pair_cap, int32_t n_tiles) {
     (void)g_cap;
     return sort_layout(pair_cap < 0 ? 0 : pair_cap, n_tiles, nullptr, nullptr);
+}
+
+// scratch of ogs_sort_bins: the per-chunk lists of long tiles
+struct BinsScratch {
+    uint32_t *tcount, *mid, *nmid, *big, *nbig;
+};
+
+size_t bins_layout(int n_tiles, void* base, BinsScratch* s) {
+    Carver cv(base);
+    BinsScratch t;
+    const int nchunks = n_tiles > 0 ? (n_tiles + kScanChunk - 1) / kScanChunk : 1;
+    t.tcount = cv.take<uint32_t>(n_tiles > 0 ? n_tiles : 1);
+    t.mid = cv.take<uint32_t>((size_t)nchunks * kScanChunk);
+    t.nmid = cv.take<uint32_t>(nchunks);
+    t.big = cv.take<uint32_t>((size_t)nchunks * kScanChunk);
+    t.nbig = cv.take<uint32_t>(nchunks);
+    if (s) *s = t;
+    return cv.off + 256;
+}
+
+extern "C" size_t ogs_sort_bins_scratch_bytes(int32_t n_tiles) {
+    return bins_layout(n_tiles < 0 ? 0 : n_tiles, nullptr, nullptr);
+}
+
+extern "C" ogs_status ogs_sort_bins(const uint32_t* depth_key, const uint32_t* rect,
+                                    const uint32_t* tiles, int64_t g_cap, int64_t n_gauss,
+                                    int32_t grid_x, int32_t grid_y, const ogs_tile_bins* bins,
+                                    uint32_t* tile_range, ogs_counts* counts, void* scratch,
+                                    size_t scratch_bytes, void* stream) {
+    if (!depth_key || !rect || !tiles || !bins || !bins->pair_key || !bins->pair_gauss ||
+        !tile_range || !counts || !scratch || bins->tile_cap == 0)
+        return OGS_ERR_ARG;
+    if (g_cap < 0 || g_cap > 0xFFFFFFFFll || !aligned(rect, 8)) return OGS_ERR_ARG;
+    if (grid_x <= 0 || grid_y <= 0 || (int64_t)grid_x * grid_y > 65536 || grid_x > 65535)
+        return OGS_ERR_ARG;
+    const int n_tiles = grid_x * grid_y;
+    if ((uint64_t)n_tiles * bins->tile_cap > 0xFFFFFFFFull) return OGS_ERR_ARG;
+    if (scratch_bytes < ogs_sort_bins_scratch_bytes(n_tiles) || !aligned(scratch, 16) ||
+        !aligned(tile_range, 8))
+        return OGS_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    BinsScratch s;
+    bins_layout(n_tiles, scratch, &s);
+    uint2* range = reinterpret_cast<uint2*>(tile_range);
+    if (cudaMemsetAsync(s.tcount, 0, sizeof(uint32_t) * n_tiles, st) != cudaSuccess)
+        return OGS_ERR_CUDA;
+    // the Gaussian count is the device count written by the decoder, or the caller's n_gauss
+    const uint32_t* n_dev = n_gauss < 0 ? &counts->n_gaussians : nullptr;
+    const int64_t n_cap = n_gauss < 0 ? g_cap : (n_gauss < g_cap ? n_gauss : g_cap);
+    const int nb = n_cap > 0 ? (int)((n_cap + kBinThreads - 1) / kBinThreads) : 1;
+    launch_pdl(bin_regions, dim3(nb), dim3(kBinThreads), 0, st, depth_key,
+               reinterpret_cast<const uint2*>(rect), tiles, n_dev, n_cap, grid_x, s.tcount,
+               bins->tile_cap, bins->pair_key, bins->pair_gauss);
+    const int nchunks = (n_tiles + kScanChunk - 1) / kScanChunk;
+    launch_pdl(bins_scan, dim3(nchunks), dim3(kScanChunk), 0, st, (const uint32_t*)s.tcount, n_tiles,
+               bins->tile_cap, range, s.mid, s.nmid, s.big, s.nbig, counts);
+    const int wgrid = std::min((n_tiles + kWarpTiles - 1) / kWarpTiles, kWarpGrid);
+    launch_pdl(tile_sort_warp, dim3(wgrid), dim3(32 * kWarpTiles), 0, st, range, n_tiles, counts,
+               (const uint32_t*)bins->pair_key, bins->pair_gauss);
+    launch_pdl(tile_sort_listed<kLargeThreads>, dim3(kSmallGrid), dim3(kLargeThreads),
+               sizeof(unsigned long long) * kSmallSort, st, range, s.mid, s.nmid, nchunks,
+               (uint32_t)kSmallSort, counts, bins->pair_key, bins->pair_gauss);
+    const size_t smem = sizeof(unsigned long long) * kLargeSort;
+    if (cudaFuncSetAttribute(tile_sort_listed<kLargeThreads>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return OGS_ERR_CUDA;
+    launch_pdl(tile_sort_listed<kLargeThreads>, dim3(kLargeGrid), dim3(kLargeThreads), smem, st,
+               range, s.big, s.nbig, nchunks, (uint32_t)kLargeSort, counts, bins->pair_key,
+               bins->pair_gauss);
+    return launch_status();
 }
 
 extern "C" ogs_status ogs_sort(const uint32_t* depth_key, const uint32_t* rect, const uint32_t* tiles,

@@ -98,6 +98,11 @@ class Renderer:
         self._structs()
         self.sel_cap = int(sel_cap if sel_cap is not None else max(1024, self.N))
         self.pair_cap = int(pair_cap if pair_cap is not None else 1 << 20)
+        # the fused BF16 path's sort places every (tile, Gaussian) pair in its tile's region of
+        # tile_cap entries as it counts the pairs, then orders the regions in place
+        self.bin_lists = True
+        self.tile_cap = 4096
+        self._last_binned = False
         self.sel_scratch = torch.empty(abi.lod_select_gated_scratch_bytes(self.N),
                                        dtype=torch.uint8, device="cuda")
         self.counts_t = torch.zeros(8, dtype=torch.int32, device="cuda")
@@ -134,9 +139,15 @@ class Renderer:
         self.depth_key = torch.empty(G, dtype=torch.int32, device=dev)
         self.rect = torch.empty(G, 2, dtype=torch.int32, device=dev)
         self.tiles = torch.empty(G, dtype=torch.int32, device=dev)
-        self.pair_gauss = torch.empty(max(P, 1), dtype=torch.int32, device=dev)
-        self.sort_scratch = torch.empty(abi.sort_scratch_bytes(G, P, self.gx * self.gy),
-                                        dtype=torch.uint8, device=dev)
+        nt = self.gx * self.gy
+        self.pair_gauss = torch.empty(max(P, nt * self.tile_cap, 1), dtype=torch.int32,
+                                      device=dev)
+        self.pair_key = torch.empty(max(nt * self.tile_cap, 1), dtype=torch.int32, device=dev)
+        self.bins = abi.tile_bins(self.pair_key, self.pair_gauss, self.tile_cap)
+        self.sort_scratch = torch.empty(abi.sort_scratch_bytes(G, P, nt), dtype=torch.uint8,
+                                        device=dev)
+        self.bins_scratch = torch.empty(abi.sort_bins_scratch_bytes(nt), dtype=torch.uint8,
+                                        device=dev)
         self._grad_bufs_cap = None          # backward buffers follow the capacities
 
     def _grad_buffers(self):
@@ -199,14 +210,17 @@ class Renderer:
                     self.sel_w_g, None, self.gate_scratch, st, bf16=self.precision == "bf16"))
                 sel, selw = self.sel_idx_g, self.sel_w_g
         self.active_sel, self.active_selw = sel, selw
-        if self.explicit is None and self.precision == "bf16" and self.fuse_decode_project:
+        fused = self.explicit is None and self.precision == "bf16" and self.fuse_decode_project
+        binned = fused and self.bin_lists
+        self._last_binned = binned
+        if fused:
             # decoded Gaussians go straight to screen records; the Gaussian SoA is written only
             # when a backward pass will need it
             stage("decode_project", lambda: abi.decode_project_bf16(
                 self.pos, self.feat, self.offs, self.lv, self.N, self._mlp_struct, c, sel, selw,
                 self.sel_cap, self.counts_t, self.rec, self.depth_key, self.rect, self.tiles,
                 self.dp_scratch, out=None if infer else self._g_struct,
-                tile_count=self.tile_count, stream=st))
+                tile_count=None if binned else self.tile_count, stream=st))
         else:
             if self.explicit is not None:
                 stage("decode", lambda: abi.explicit_gaussians(
@@ -220,10 +234,15 @@ class Renderer:
             stage("project_bin", lambda: abi.project_bin(
                 self._g_struct, self.g_cap, 1, c, self.rec, self.depth_key, self.rect,
                 self.tiles, self.counts_t, st, tile_count=self.tile_count))
-        stage("sort", lambda: abi.sort(
-            self.depth_key, self.rect, self.tiles, self.g_cap, -1, self.gx, self.gy,
-            self.pair_gauss, self.tile_range, self.pair_cap, self.counts_t, self.sort_scratch,
-            st, tile_count=self.tile_count))
+        if binned:
+            stage("sort", lambda: abi.sort_bins(
+                self.depth_key, self.rect, self.tiles, self.g_cap, -1, self.gx, self.gy,
+                self.bins, self.tile_range, self.counts_t, self.bins_scratch, st))
+        else:
+            stage("sort", lambda: abi.sort(
+                self.depth_key, self.rect, self.tiles, self.g_cap, -1, self.gx, self.gy,
+                self.pair_gauss, self.tile_range, self.pair_cap, self.counts_t,
+                self.sort_scratch, st, tile_count=self.tile_count))
         n_last = self.n_last if (not infer or self.track_last) else None
         stage("blend_fwd", lambda: abi.blend_fwd(
             self.rec, self.pair_gauss, self.tile_range, self.W, self.H, bg,
@@ -345,6 +364,19 @@ class Renderer:
                 on_frame(j, host_imgs[b])
         return host_imgs
 
+    def grow_for(self, c):
+        """Enlarges the capacities a view overflowed (counts ``c``) and reallocates: the
+        selection, and the pair lists (their total, or with per-tile regions the longest
+        list, which is what need_pairs reports then)."""
+        if c.overflow & 1:
+            self.sel_cap = int(c.need_selected * 1.25) + 1024
+        if c.overflow & 2:
+            if self._last_binned:
+                self.tile_cap = int(c.need_pairs * 1.25) + 64
+            else:
+                self.pair_cap = int(c.need_pairs * 1.25) + 4096
+        self._alloc()
+
     def render(self, cam, infer=True, bg=(0.0, 0.0, 0.0), maxc=None, check=True, gate=None):
         """Renders one view; with ``check`` it synchronises, grows overflowing buffers and
         re-renders until everything fits."""
@@ -355,11 +387,7 @@ class Renderer:
             c = self.counts()
             if not c.overflow:
                 return c
-            if c.overflow & 1:
-                self.sel_cap = int(c.need_selected * 1.25) + 1024
-            if c.overflow & 2:
-                self.pair_cap = int(c.need_pairs * 1.25) + 4096
-            self._alloc()
+            self.grow_for(c)
             if maxc is not None:
                 maxc.zero_()
         raise abi.OgsError("buffers kept overflowing")

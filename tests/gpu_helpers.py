@@ -128,14 +128,19 @@ def tiles_to_pixels(tiles, W, H):
 
 
 def gpu_pairs(sel_gpu, tile_range, pair_gauss, k, T):
-    """GPU pairs as (tile, key) arrays in list order, keys = anchor * k + slot."""
+    """GPU pairs as (tile, key) arrays in list order, keys = anchor * k + slot.  The tile
+    ranges may be packed (the exclusive scan of the counts) or per-tile regions; either way
+    they must lie inside pair_gauss without overlapping."""
     tr = np.asarray(tile_range).reshape(-1, 2).astype(np.int64)
     cnt = tr[:, 1] - tr[:, 0]
-    ne = cnt > 0
-    # the GPU's tile ranges are the exclusive scan of its counts (tile-major pairs)
-    assert np.array_equal(tr[ne, 0], (np.cumsum(cnt) - cnt)[ne])
-    P = int(cnt.sum())
-    pg = np.asarray(pair_gauss)[:P].astype(np.int64)
+    ne = np.nonzero(cnt > 0)[0]
+    assert np.all(cnt >= 0) and np.all(tr[ne, 1] <= len(pair_gauss))
+    starts = tr[ne, 0]
+    order = np.argsort(starts, kind="stable")
+    assert np.all(tr[ne[order][1:], 0] >= tr[ne[order][:-1], 1])          # no overlap
+    pg_all = np.asarray(pair_gauss)
+    pg = (np.concatenate([pg_all[tr[t, 0]:tr[t, 1]] for t in ne]) if len(ne)
+          else pg_all[:0]).astype(np.int64)
     sel_gpu = np.asarray(sel_gpu).astype(np.int64)
     return np.repeat(np.arange(T), cnt), sel_gpu[pg // k] * k + pg % k, cnt
 

@@ -232,6 +232,31 @@ def test_radix_sort_device_count(abi, torch):
     assert np.array_equal(to_np_u32(vt)[12_345:], vals[12_345:])   # untouched beyond n
 
 
+def _gpu_sort_bins(abi, torch, rect, depth, gx, gy, tile_cap):
+    """ogs_sort_bins: the lists in per-tile regions of tile_cap entries; returns the lists
+    packed in tile order (for comparison with the oracle's), the ranges, the counts."""
+    G = len(depth)
+    area = np.maximum(rect[:, 2] - rect[:, 0], 0) * np.maximum(rect[:, 3] - rect[:, 1], 0)
+    dk = depth.astype(np.float32).view(np.uint32).copy()
+    dk[area == 0] = 0xFFFFFFFF
+    packed = np.stack([rect[:, 0] | (rect[:, 1] << 16), rect[:, 2] | (rect[:, 3] << 16)], 1)
+    packed = np.where(area[:, None] > 0, packed, 0).astype(np.uint32)
+    nt = gx * gy
+    pk = torch.zeros(nt * tile_cap, dtype=torch.int32, device="cuda")
+    pg = torch.zeros(nt * tile_cap, dtype=torch.int32, device="cuda")
+    tr = torch.zeros(nt, 2, dtype=torch.int32, device="cuda")
+    counts = torch.zeros(8, dtype=torch.int32, device="cuda")
+    scr = torch.empty(abi.sort_bins_scratch_bytes(nt), dtype=torch.uint8, device="cuda")
+    abi.sort_bins(cuda(dk.view(np.int32)), cuda(packed.view(np.int32)),
+                  cuda(area.astype(np.int32)), G, G, gx, gy, abi.tile_bins(pk, pg, tile_cap),
+                  tr, counts, scr)
+    torch.cuda.synchronize()
+    trn = to_np_u32(tr).reshape(-1, 2).astype(np.int64)
+    pgn = to_np_u32(pg)
+    lists = [pgn[a:b] for a, b in trn]
+    return (np.concatenate(lists) if lists else pgn[:0]), trn, _counts(abi, counts)
+
+
 def _gpu_sort(abi, torch, rect, depth, gx, gy, pair_cap=None, ext_counts=False):
     G = len(depth)
     area = np.maximum(rect[:, 2] - rect[:, 0], 0) * np.maximum(rect[:, 3] - rect[:, 1], 0)
@@ -312,6 +337,34 @@ def test_sort_list_length_classes(abi, torch, depths):
         pg, tr, c, P = _gpu_sort(abi, torch, rect, depth, gx, gy, ext_counts=ext)
         assert c["n_pairs"] == P == G and c["overflow"] == 0
         assert np.array_equal(pg[:P], lst)
+    got, tr, c = _gpu_sort_bins(abi, torch, rect, depth, gx, gy, 3000)
+    assert c["n_pairs"] == G and c["overflow"] == 0
+    assert np.array_equal(got, lst)
+
+
+@pytest.mark.parametrize("G,gx,gy", [(1, 3, 2), (3000, 9, 7), (60_000, 120, 68), (20_000, 4, 4)])
+def test_sort_bins_matches_oracle_lists(abi, torch, G, gx, gy):
+    """ogs_sort_bins: every tile's list in its region equals the oracle's list, the ranges
+    start at t * tile_cap, the pair count is the oracle's."""
+    rect, depth = synth.random_rects_depths(G, G, gx, gy, max_span=8, equal_depth_frac=0.05)
+    start, lst, _ = oracle.tile_lists(rect, depth.astype(np.float64), gx, gy)
+    cap = int(max(1, np.diff(start).max()))
+    got, tr, c = _gpu_sort_bins(abi, torch, rect, depth, gx, gy, cap)
+    assert c["n_pairs"] == len(lst) and c["overflow"] == 0
+    assert np.array_equal(tr[:, 0], np.arange(gx * gy) * cap)
+    assert np.array_equal(tr[:, 1] - tr[:, 0], np.diff(start))
+    assert np.array_equal(got, lst)
+
+
+def test_sort_bins_overflow(abi, torch):
+    """A tile with more pairs than tile_cap: overflow bit 1, need_pairs = the longest list,
+    every range empty."""
+    rect, depth = synth.random_rects_depths(9, 2000, 20, 20, max_span=6)
+    start, lst, _ = oracle.tile_lists(rect, depth.astype(np.float64), 20, 20)
+    longest = int(np.diff(start).max())
+    got, tr, c = _gpu_sort_bins(abi, torch, rect, depth, 20, 20, longest - 1)
+    assert c["overflow"] & 2 and c["need_pairs"] == longest and c["n_pairs"] == 0
+    assert np.all(tr == 0)
 
 
 def test_sort_pair_overflow(abi, torch):
