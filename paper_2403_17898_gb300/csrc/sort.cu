@@ -261,6 +261,8 @@ constexpr int kSmallGrid = 2 * 152;      // .. in CTAs of kLargeThreads looping 
 constexpr int kLargeThreads = 512;
 constexpr int kLargeSort = 16384;        // longer lists: 128 KB of keys in dynamic shared memory
 constexpr int kLargeGrid = 152;          // CTAs looping over the long lists
+constexpr int kBinsListSort = 4096;      // ogs_sort_bins: lists past kWarpSort, 32 KB of keys ..
+constexpr int kBinsListGrid = 4 * 152;   // .. in CTAs of kLargeThreads, four per SM
 
 __device__ __forceinline__ void rect_of(uint2 r, uint32_t& x0, uint32_t& y0, uint32_t& x1,
                                         uint32_t& y1) {
@@ -449,39 +451,36 @@ __global__ void __launch_bounds__(kBinThreads) bin_regions(const uint32_t* __res
     const uint32_t n = count_of(n_dev, n_cap);
     const int64_t g = (int64_t)blockIdx.x * kBinThreads + threadIdx.x;
     if ((int64_t)blockIdx.x * kBinThreads >= n) return;        // whole CTA out of range
+    // the three loads are independent (one round trip); rect and key are unused when c = 0
     uint32_t c = 0, k = 0xFFFFFFFFu;
     uint2 rc = make_uint2(0, 0);
     if (g < n) {
         c = tiles[g];
-        if (c) {
-            rc = rect[g];
-            k = dkey[g];
-        }
+        rc = rect[g];
+        k = dkey[g];
     }
+    if (c == 0) rc = make_uint2(0, 0);
     bin_tiles(tc, gx, rc, c, (uint32_t)g, k, cap, keys, ids);
 }
 
-// Ranges of the binned lists: tile t owns [t cap, t cap + count_t).  One
-// CTA per kScanChunk tiles: every CTA reads all the counts itself (their total and largest
-// decide the pair count and the overflow state), then lists its chunk's tiles too long for
-// the warp sorter in `mid` (up to kSmallSort entries) or `big`, as tile_scan does.  CTA 0
-// writes P and the overflow state.
+// Ranges of the binned lists: tile t owns [t cap, t cap + count_t).  One CTA per kScanChunk
+// tiles: every CTA reads all the counts itself (their total and largest decide the pair count
+// and the overflow state), then lists its chunk's tiles too long for the warp sorter in
+// `longl` (count in nlong[chunk]).  CTA 0 writes P and the overflow state.
 __global__ void __launch_bounds__(kScanChunk) bins_scan(const uint32_t* __restrict__ tcount,
                                                         int ntiles, uint32_t cap,
                                                         uint2* __restrict__ range,
-                                                        uint32_t* __restrict__ mid,
-                                                        uint32_t* __restrict__ nmid,
-                                                        uint32_t* __restrict__ big,
-                                                        uint32_t* __restrict__ nbig,
+                                                        uint32_t* __restrict__ longl,
+                                                        uint32_t* __restrict__ nlong,
                                                         ogs_counts* counts) {
     pdl_wait();
     pdl_trigger();
     __shared__ unsigned long long s_sum[kScanChunk / 32];
     __shared__ uint32_t s_max[kScanChunk / 32];
-    __shared__ uint32_t s_nmid, s_nbig;
+    __shared__ uint32_t s_nlong;
     const int t = threadIdx.x, lane = (int)lane_id(), warp = t >> 5;
     const int c0 = blockIdx.x * kScanChunk;
-    if (t == 0) s_nmid = s_nbig = 0;
+    if (t == 0) s_nlong = 0;
     unsigned long long all = 0;
     uint32_t mx = 0;
     for (int b = t; b < ntiles; b += kScanChunk) {
@@ -512,15 +511,11 @@ __global__ void __launch_bounds__(kScanChunk) bins_scan(const uint32_t* __restri
         const uint32_t v = tcount[b];
         const uint32_t st = (uint32_t)b * cap;
         range[b] = over ? make_uint2(0, 0) : make_uint2(st, st + v);
-        if (!over && v > (uint32_t)kSmallSort)
-            big[c0 + atomicAdd(&s_nbig, 1u)] = (uint32_t)b;
-        else if (!over && v > (uint32_t)kWarpSort)
-            mid[c0 + atomicAdd(&s_nmid, 1u)] = (uint32_t)b;
+        if (!over && v > (uint32_t)kWarpSort) longl[c0 + atomicAdd(&s_nlong, 1u)] = (uint32_t)b;
     }
     __syncthreads();
     if (t == 0) {
-        nmid[blockIdx.x] = s_nmid;
-        nbig[blockIdx.x] = s_nbig;
+        nlong[blockIdx.x] = s_nlong;
         if (blockIdx.x == 0) {
             if (over) {
                 atomicOr(&counts->overflow, 2u);
@@ -1030,7 +1025,7 @@ extern "C" size_t ogs_sort_scratch_bytes(int64_t g_cap, int64_t pair_cap, int32_
 
 // scratch of ogs_sort_bins: the per-chunk lists of long tiles
 struct BinsScratch {
-    uint32_t *tcount, *mid, *nmid, *big, *nbig;
+    uint32_t *tcount, *longl, *nlong;
 };
 
 size_t bins_layout(int n_tiles, void* base, BinsScratch* s) {
@@ -1038,10 +1033,8 @@ size_t bins_layout(int n_tiles, void* base, BinsScratch* s) {
     BinsScratch t;
     const int nchunks = n_tiles > 0 ? (n_tiles + kScanChunk - 1) / kScanChunk : 1;
     t.tcount = cv.take<uint32_t>(n_tiles > 0 ? n_tiles : 1);
-    t.mid = cv.take<uint32_t>((size_t)nchunks * kScanChunk);
-    t.nmid = cv.take<uint32_t>(nchunks);
-    t.big = cv.take<uint32_t>((size_t)nchunks * kScanChunk);
-    t.nbig = cv.take<uint32_t>(nchunks);
+    t.longl = cv.take<uint32_t>((size_t)nchunks * kScanChunk);
+    t.nlong = cv.take<uint32_t>(nchunks);
     if (s) *s = t;
     return cv.off + 256;
 }
@@ -1080,21 +1073,21 @@ extern "C" ogs_status ogs_sort_bins(const uint32_t* depth_key, const uint32_t* r
                reinterpret_cast<const uint2*>(rect), tiles, n_dev, n_cap, grid_x, s.tcount,
                bins->tile_cap, bins->pair_key, bins->pair_gauss);
     const int nchunks = (n_tiles + kScanChunk - 1) / kScanChunk;
-    launch_pdl(bins_scan, dim3(nchunks), dim3(kScanChunk), 0, st, (const uint32_t*)s.tcount, n_tiles,
-               bins->tile_cap, range, s.mid, s.nmid, s.big, s.nbig, counts);
+    launch_pdl(bins_scan, dim3(nchunks), dim3(kScanChunk), 0, st, (const uint32_t*)s.tcount,
+               n_tiles, bins->tile_cap, range, s.longl, s.nlong, counts);
     const int wgrid = std::min((n_tiles + kWarpTiles - 1) / kWarpTiles, kWarpGrid);
     launch_pdl(tile_sort_warp, dim3(wgrid), dim3(32 * kWarpTiles), 0, st, range, n_tiles, counts,
                (const uint32_t*)bins->pair_key, bins->pair_gauss);
-    launch_pdl(tile_sort_listed<kLargeThreads>, dim3(kSmallGrid), dim3(kLargeThreads),
-               sizeof(unsigned long long) * kSmallSort, st, range, s.mid, s.nmid, nchunks,
-               (uint32_t)kSmallSort, counts, bins->pair_key, bins->pair_gauss);
-    const size_t smem = sizeof(unsigned long long) * kLargeSort;
+    // every longer list in one launch: up to kBinsListSort keys in shared memory, the rare
+    // longer list by the same network on global memory
+    const size_t smem = sizeof(unsigned long long) * kBinsListSort;
     if (cudaFuncSetAttribute(tile_sort_listed<kLargeThreads>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(unsigned long long) * kLargeSort)) != cudaSuccess)
         return OGS_ERR_CUDA;
-    launch_pdl(tile_sort_listed<kLargeThreads>, dim3(kLargeGrid), dim3(kLargeThreads), smem, st,
-               range, s.big, s.nbig, nchunks, (uint32_t)kLargeSort, counts, bins->pair_key,
-               bins->pair_gauss);
+    launch_pdl(tile_sort_listed<kLargeThreads>, dim3(kBinsListGrid), dim3(kLargeThreads), smem,
+               st, range, s.longl, s.nlong, nchunks, (uint32_t)kBinsListSort, counts,
+               bins->pair_key, bins->pair_gauss);
     return launch_status();
 }
 
