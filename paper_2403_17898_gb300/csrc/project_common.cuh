@@ -167,12 +167,17 @@ __device__ __forceinline__ void bin_tiles(uint32_t* tc, int gx, uint2 rc, uint32
     if (own && lane_id() == leader) base = atomicAdd(tc + t0, (uint32_t)__popc(peers));
     if (own) {
         uint32_t tt[kOwnTiles], sl[kOwnTiles];
+        uint32_t kx = 0, t = t0;                    // walks the rectangle row by row
 #pragma unroll
         for (uint32_t i = 1; i < kOwnTiles; ++i) {
-            if (i < ntiles) {
-                tt[i] = (y0 + i / w) * (uint32_t)gx + x0 + i % w;
-                sl[i] = atomicAdd(tc + tt[i], 1u);
+            if (++kx == w) {
+                kx = 0;
+                t += (uint32_t)gx - w + 1;
+            } else {
+                ++t;
             }
+            tt[i] = t;
+            if (i < ntiles) sl[i] = atomicAdd(tc + t, 1u);
         }
 #pragma unroll
         for (uint32_t i = 1; i < kOwnTiles; ++i)
