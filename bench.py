@@ -497,6 +497,10 @@ def _train_bench(clk_index, steps_scale=1.0):
         res = {"workload": desc, "anchors": int(tr.N), "views_per_step": vps,
                "resolution": f"{W}x{H}", "ssim_lambda": lam, "steps": K, "warmup": Wm,
                "l2": "no flush: every step streams the dense Adam state (>= 1 GB) through L2",
+               "pipelined_views": "each view's loss and backward run on a second stream while "
+                                  "the next view's forward runs (two sets of per-view buffers), "
+                                  "so the per-stage times of a step overlap and add up to more "
+                                  "than the step",
                "max_selected": sel_max, "max_pairs": pair_max}
         # both forms start from the same parameters and optimiser state
         init = {n: t.clone() for n, t in tr._anchor_params().items()}

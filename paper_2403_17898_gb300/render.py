@@ -263,7 +263,8 @@ class Renderer:
         st = stream if stream is not None else torch.cuda.current_stream()
 
         def bb():
-            self.drec.zero_()
+            with torch.cuda.stream(st):
+                self.drec.zero_()
             abi.blend_bwd(self.rec, self.pair_gauss, self.tile_range, self.W, self.H, bg, self.T,
                           self.n_last, dimg, self.drec, st)
         _stage(timers, "blend_bwd", st, bb)
@@ -418,6 +419,15 @@ def progressive_schedule(NL, total, omega):
     return out
 
 
+# The per-view buffers a training view's forward writes and its backward reads: the
+# pipelined step keeps two sets of them, so that the forward of view v + 1 (on the caller's
+# stream) runs while the backward of view v (on a second stream) still reads its set.
+_VIEW_KEYS = ("sel_idx", "sel_w", "sel_idx_g", "sel_w_g", "gate_scratch", "dp_scratch", "g",
+              "_g_struct", "rec", "depth_key", "rect", "tiles", "pair_gauss", "pair_key", "bins",
+              "sort_scratch", "bins_scratch", "counts_t", "img", "T", "n_last", "tile_range",
+              "tile_count", "sel_scratch", "active_sel", "active_selw")
+
+
 class Trainer(Renderer):
     """One optimisation step over a batch of views: for each view the training-mode forward
     (no next-level anchors), the loss against its target, and the backward chain
@@ -472,6 +482,43 @@ class Trainer(Renderer):
             total, omega = progressive
             self.progressive = (int(total), progressive_schedule(self.NL, total, omega))
         self._grad_buffers()
+        # pipelined steps: the forward of the next view overlaps the backward of this one
+        self.pipeline = True
+        self._view_set = None            # the second set of per-view buffers, built lazily
+        self._view_set_sig = None
+        self._view_set_pending = False   # the second set holds views of the last step
+        self._bwd_stream = None
+
+    # -- two sets of per-view buffers for the pipelined step ---------------------------------
+    def _view_snapshot(self):
+        return {k: getattr(self, k, None) for k in _VIEW_KEYS}
+
+    @staticmethod
+    def _view_signature(d):
+        return tuple((k, v.data_ptr(), tuple(v.shape)) for k, v in d.items()
+                     if torch.is_tensor(v))
+
+    def _second_view_set(self, d):
+        """A set of per-view buffers shaped like ``d`` (the live set)."""
+        n = {}
+        for k, v in d.items():
+            n[k] = torch.empty_like(v) if torch.is_tensor(v) else v
+        n["counts_t"] = torch.zeros_like(d["counts_t"])
+        n["g"] = {name: torch.empty_like(t) for name, t in d["g"].items()}
+        n["_g_struct"] = abi.gaussians_struct(n["g"])
+        n["bins"] = abi.tile_bins(n["pair_key"], n["pair_gauss"], self.tile_cap)
+        n["active_sel"], n["active_selw"] = None, None
+        return n
+
+    def counts(self) -> FrameCounts:
+        """Counts of the view last enqueued; after a pipelined step the overflow and timeout
+        flags also cover the views of the second buffer set."""
+        c = super().counts()
+        if self._view_set is not None and self._view_set_pending:
+            v = self._view_set["counts_t"].cpu().numpy().view(np.uint32)
+            c.overflow |= int(v[3])
+            c.timeout |= int(v[6])
+        return c
 
     def _anchor_params(self):
         """Trainable per-anchor arrays: features, offsets and l_v of the neural form; offsets,
@@ -504,6 +551,7 @@ class Trainer(Renderer):
         return hit[1]
 
     def enqueue(self, cam, infer=True, *args, **kw):
+        self._view_set_pending = False
         super().enqueue(cam, infer, *args, **kw)
         if not infer:           # a training view: its anchors take the coming optimiser step
             abi.stamp_selected(self.active_sel, self.counts_t, self.stamp, self.step_count + 1,
@@ -578,17 +626,61 @@ class Trainer(Renderer):
         step; returns nothing (the summed per-view loss is left in ``self.loss``)."""
         self.loss.zero_()
         cap = self.active_level() if self.progressive is not None else None
-        for cam, tgt in zip(cams, targets):
-            self.enqueue(cam, infer=False, bg=bg, timers=timers, max_level=cap)
-            if self.track_view_frequency:
-                abi.count_selected(self.sel_idx, self.counts_t, self.sel_count)
-                self.n_views_seen += 1
-            if self.track_opacity:
-                abi.opacity_accumulate(self.g["opac"], self.sel_idx, self.counts_t, self.k,
-                                       self.opac_sum, self.opac_views)
-            self.backward_view(cam, tgt, bg, timers=timers)
+        if not self.pipeline or len(cams) < 2:
+            for cam, tgt in zip(cams, targets):
+                self._forward_view(cam, bg, timers, cap)
+                self.backward_view(cam, tgt, bg, timers=timers)
+        else:
+            self._pipelined_views(cams, targets, bg, timers, cap)
         if update:
             self.optimizer_step(timers=timers)
+
+    def _forward_view(self, cam, bg, timers, cap):
+        self.enqueue(cam, infer=False, bg=bg, timers=timers, max_level=cap)
+        if self.track_view_frequency:
+            abi.count_selected(self.sel_idx, self.counts_t, self.sel_count)
+            self.n_views_seen += 1
+        if self.track_opacity:
+            abi.opacity_accumulate(self.g["opac"], self.sel_idx, self.counts_t, self.k,
+                                   self.opac_sum, self.opac_views)
+
+    def _pipelined_views(self, cams, targets, bg, timers, cap):
+        """Views alternate between two sets of per-view buffers.  The forward of each view runs
+        on the caller's stream; its loss and backward on a second stream once that forward is
+        done, so the next view's forward overlaps them.  A set is reused only after the backward
+        that read it has finished; the backward passes run one after another in view order
+        (the gradients and the loss accumulate as in the sequential step), and the caller's
+        stream waits for the last of them."""
+        fwd = torch.cuda.current_stream()
+        if self._bwd_stream is None:
+            self._bwd_stream = torch.cuda.Stream()
+        bwd = self._bwd_stream
+        live = self._view_snapshot()
+        sig = self._view_signature(live)
+        if self._view_set is None or self._view_set_sig != sig:
+            self._view_set = self._second_view_set(live)
+            self._view_set_sig = sig
+        sets = [live, self._view_set]
+        done = [None, None]
+        try:
+            for v, (cam, tgt) in enumerate(zip(cams, targets)):
+                i = v & 1
+                self.__dict__.update(sets[i])
+                if done[i] is not None:
+                    fwd.wait_event(done[i])
+                self._forward_view(cam, bg, timers, cap)
+                ready = torch.cuda.Event()
+                ready.record(fwd)
+                bwd.wait_event(ready)
+                self.backward_view(cam, tgt, bg, stream=bwd, timers=timers)
+                done[i] = torch.cuda.Event()
+                done[i].record(bwd)
+                sets[i] = self._view_snapshot()
+            fwd.wait_stream(bwd)
+        finally:
+            self._view_set = sets[1]
+            self.__dict__.update(sets[0])
+        self._view_set_pending = True
 
     def _reset_opacity_stats(self):
         n = self.N if self.track_opacity else 0
