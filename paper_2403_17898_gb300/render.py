@@ -48,6 +48,15 @@ def _stage(timers, name, st, fn):
     timers.setdefault(name, []).append((e0, e1))
 
 
+# The per-view buffers a view's forward writes and its backward (or the copy of its image)
+# reads: pipelined sequences and training steps keep two sets of them, so that the work of
+# view v + 1 runs while view v's set is still in use.
+_VIEW_KEYS = ("sel_idx", "sel_w", "sel_idx_g", "sel_w_g", "gate_scratch", "dp_scratch", "g",
+              "_g_struct", "rec", "depth_key", "rect", "tiles", "pair_gauss", "pair_key", "bins",
+              "sort_scratch", "bins_scratch", "counts_t", "img", "T", "n_last", "tile_range",
+              "tile_count", "sel_scratch", "active_sel", "active_selw")
+
+
 class Renderer:
     """Renders views of one anchor set with one decoder at a fixed image size.
 
@@ -111,6 +120,9 @@ class Renderer:
         self.n_last = torch.empty(self.H, self.W, dtype=torch.int32, device="cuda")
         self.tile_range = torch.empty(self.gx * self.gy, 2, dtype=torch.int32, device="cuda")
         self.tile_count = torch.empty(self.gx * self.gy, dtype=torch.int32, device="cuda")
+        self._view_set = None            # the second set of per-view buffers, built lazily
+        self._view_set_sig = None
+        self._view_set_pending = False   # the second set holds views of the last sequence
         self._alloc()
 
     def _structs(self):
@@ -182,13 +194,15 @@ class Renderer:
         st = stream if stream is not None else torch.cuda.current_stream()
         # every forward overwrites the per-view buffers a backward reads
         self.generation = getattr(self, "generation", 0) + 1
+        self._view_set_pending = False
 
         def stage(name, fn):
             _stage(timers, name, st, fn)
 
         fused_gate = gate is not None and self.precision == "bf16" and self.fuse_gate
         if not fused_gate:               # the gated selection resets the counters itself
-            self.counts_t.zero_()
+            with torch.cuda.stream(st):
+                self.counts_t.zero_()
         sel, selw = self.sel_idx, self.sel_w
         assert max_level is None or gate is None, "a level cap is a training-time setting"
         NL = self.NL if max_level is None else max(1, min(self.NL, int(max_level) + 1))
@@ -287,9 +301,37 @@ class Renderer:
                 grads["feat"], grads["offs"], grads["lv"], dmlp_struct, self.db_scratch, st,
                 bf16=self.precision == "bf16"))
 
+    # -- two sets of per-view buffers for pipelined sequences and steps -----------------------
+    def _view_snapshot(self):
+        return {k: getattr(self, k, None) for k in _VIEW_KEYS}
+
+    @staticmethod
+    def _view_signature(d):
+        return tuple((k, v.data_ptr(), tuple(v.shape)) for k, v in d.items()
+                     if torch.is_tensor(v))
+
+    def _second_view_set(self, d):
+        """A set of per-view buffers shaped like ``d`` (the live set)."""
+        n = {}
+        for k, v in d.items():
+            n[k] = torch.empty_like(v) if torch.is_tensor(v) else v
+        n["counts_t"] = torch.zeros_like(d["counts_t"])
+        n["g"] = {name: torch.empty_like(t) for name, t in d["g"].items()}
+        n["_g_struct"] = abi.gaussians_struct(n["g"])
+        n["bins"] = abi.tile_bins(n["pair_key"], n["pair_gauss"], self.tile_cap)
+        n["active_sel"], n["active_selw"] = None, None
+        return n
+
     def counts(self) -> FrameCounts:
+        """Counts of the view last enqueued; after a pipelined sequence or step the overflow
+        and timeout flags also cover the views of the second buffer set."""
         v = self.counts_t.cpu().numpy().view(np.uint32)
-        return FrameCounts(*[int(x) for x in v])
+        c = FrameCounts(*[int(x) for x in v])
+        if self._view_set is not None and self._view_set_pending:
+            w = self._view_set["counts_t"].cpu().numpy().view(np.uint32)
+            c.overflow |= int(w[3])
+            c.timeout |= int(w[6])
+        return c
 
     def render_to_host(self, cam, host_img, infer=True, bg=(0.0, 0.0, 0.0), gate=None,
                        zero_copy=True):
@@ -314,8 +356,9 @@ class Renderer:
         on the device and copied to the host on a copy stream while view i + 1 renders; with
         ``zero_copy`` the blend of view i writes straight into its host buffer instead (no
         copy, but the blend's stores then cross the host link and lengthen it: slower when
-        views are pipelined, faster for one view at a time, see render_to_host).  Returns
-        when every image is on the host."""
+        views are pipelined, faster for one view at a time, see render_to_host).  In the
+        default form consecutive views also render concurrently, on two compute streams with
+        two sets of per-view buffers.  Returns when every image is on the host."""
         if zero_copy:
             done = [None, None]
             for i, cam in enumerate(cams):
@@ -334,35 +377,51 @@ class Renderer:
                 if on_frame is not None:
                     on_frame(j, host_imgs[b])
             return host_imgs
-        if not hasattr(self, "_seq_img"):
-            self._seq_img = torch.empty_like(self.img)
+        # two sets of per-view buffers, views alternating between them and between two
+        # compute streams: view i + 1 renders while view i is still rendering or being copied
+        if getattr(self, "_copy_stream", None) is None:
             self._copy_stream = torch.cuda.Stream()
-        dev_imgs = (self.img, self._seq_img)
-        comp = torch.cuda.current_stream()
-        ready = [torch.cuda.Event(), torch.cuda.Event()]
+            self._alt_stream = torch.cuda.Stream()
+        comps = (torch.cuda.current_stream(), self._alt_stream)
+        live = self._view_snapshot()
+        sig = self._view_signature(live)
+        if self._view_set is None or self._view_set_sig != sig:
+            self._view_set = self._second_view_set(live)
+            self._view_set_sig = sig
+        sets = [live, self._view_set]
         copied = [None, None]
-        for i, cam in enumerate(cams):
-            b = i % 2
-            if copied[b] is not None:
-                # the buffer pair's previous image: its copy must be done before the blend
-                # overwrites the device image and before the host buffer is handed out again
-                comp.wait_event(copied[b])
+        try:
+            for i, cam in enumerate(cams):
+                b = i & 1
+                self.__dict__.update(sets[b])
+                comp = comps[b]
+                if copied[b] is not None:
+                    # the set's previous view: its copy must be done before this view's blend
+                    # overwrites the device image and before the host buffer is handed out
+                    comp.wait_event(copied[b])
+                    copied[b].synchronize()
+                    if on_frame is not None:
+                        on_frame(i - 2, host_imgs[b])
+                self.enqueue(cam, True, bg, gate=gate, stream=comp)
+                ready = torch.cuda.Event()
+                ready.record(comp)
+                self._copy_stream.wait_event(ready)
+                with torch.cuda.stream(self._copy_stream):
+                    host_imgs[b].copy_(self.img, non_blocking=True)
+                    ev = torch.cuda.Event()
+                    ev.record(self._copy_stream)
+                copied[b] = ev
+                sets[b] = self._view_snapshot()
+            for j in range(max(len(cams) - 2, 0), len(cams)):
+                b = j & 1
                 copied[b].synchronize()
                 if on_frame is not None:
-                    on_frame(i - 2, host_imgs[b])
-            self.enqueue(cam, True, bg, gate=gate, img=dev_imgs[b])
-            ready[b].record(comp)
-            self._copy_stream.wait_event(ready[b])
-            with torch.cuda.stream(self._copy_stream):
-                host_imgs[b].copy_(dev_imgs[b], non_blocking=True)
-                ev = torch.cuda.Event()
-                ev.record(self._copy_stream)
-            copied[b] = ev
-        for j in range(max(len(cams) - 2, 0), len(cams)):
-            b = j % 2
-            copied[b].synchronize()
-            if on_frame is not None:
-                on_frame(j, host_imgs[b])
+                    on_frame(j, host_imgs[b])
+        finally:
+            self._view_set = sets[1]
+            self.__dict__.update(sets[0])
+            comps[0].wait_stream(comps[1])
+        self._view_set_pending = len(cams) > 1
         return host_imgs
 
     def grow_for(self, c):
@@ -417,15 +476,6 @@ def progressive_schedule(NL, total, omega):
         out.append((int(round(at)), i))
         at += unit * w
     return out
-
-
-# The per-view buffers a training view's forward writes and its backward reads: the
-# pipelined step keeps two sets of them, so that the forward of view v + 1 (on the caller's
-# stream) runs while the backward of view v (on a second stream) still reads its set.
-_VIEW_KEYS = ("sel_idx", "sel_w", "sel_idx_g", "sel_w_g", "gate_scratch", "dp_scratch", "g",
-              "_g_struct", "rec", "depth_key", "rect", "tiles", "pair_gauss", "pair_key", "bins",
-              "sort_scratch", "bins_scratch", "counts_t", "img", "T", "n_last", "tile_range",
-              "tile_count", "sel_scratch", "active_sel", "active_selw")
 
 
 class Trainer(Renderer):
@@ -484,41 +534,7 @@ class Trainer(Renderer):
         self._grad_buffers()
         # pipelined steps: the forward of the next view overlaps the backward of this one
         self.pipeline = True
-        self._view_set = None            # the second set of per-view buffers, built lazily
-        self._view_set_sig = None
-        self._view_set_pending = False   # the second set holds views of the last step
         self._bwd_stream = None
-
-    # -- two sets of per-view buffers for the pipelined step ---------------------------------
-    def _view_snapshot(self):
-        return {k: getattr(self, k, None) for k in _VIEW_KEYS}
-
-    @staticmethod
-    def _view_signature(d):
-        return tuple((k, v.data_ptr(), tuple(v.shape)) for k, v in d.items()
-                     if torch.is_tensor(v))
-
-    def _second_view_set(self, d):
-        """A set of per-view buffers shaped like ``d`` (the live set)."""
-        n = {}
-        for k, v in d.items():
-            n[k] = torch.empty_like(v) if torch.is_tensor(v) else v
-        n["counts_t"] = torch.zeros_like(d["counts_t"])
-        n["g"] = {name: torch.empty_like(t) for name, t in d["g"].items()}
-        n["_g_struct"] = abi.gaussians_struct(n["g"])
-        n["bins"] = abi.tile_bins(n["pair_key"], n["pair_gauss"], self.tile_cap)
-        n["active_sel"], n["active_selw"] = None, None
-        return n
-
-    def counts(self) -> FrameCounts:
-        """Counts of the view last enqueued; after a pipelined step the overflow and timeout
-        flags also cover the views of the second buffer set."""
-        c = super().counts()
-        if self._view_set is not None and self._view_set_pending:
-            v = self._view_set["counts_t"].cpu().numpy().view(np.uint32)
-            c.overflow |= int(v[3])
-            c.timeout |= int(v[6])
-        return c
 
     def _anchor_params(self):
         """Trainable per-anchor arrays: features, offsets and l_v of the neural form; offsets,
@@ -551,7 +567,6 @@ class Trainer(Renderer):
         return hit[1]
 
     def enqueue(self, cam, infer=True, *args, **kw):
-        self._view_set_pending = False
         super().enqueue(cam, infer, *args, **kw)
         if not infer:           # a training view: its anchors take the coming optimiser step
             abi.stamp_selected(self.active_sel, self.counts_t, self.stamp, self.step_count + 1,

@@ -1,6 +1,7 @@
 """End-to-end rendering into pinned host memory: Renderer.render_sequence_to_host, pipelined
 either by writing each image straight into its host buffer from the blend (zero copy) or by
-copying view i while view i + 1 renders, two buffers reused in turn; and the single-view
+copying view i while view i + 1 renders (consecutive views on two compute streams with two
+sets of per-view buffers), two host buffers reused in turn; and the single-view
 render_to_host in both forms.  Each host image is compared bit for bit with a separate
 single-view render of the same pose on the device."""
 import numpy as np
@@ -32,6 +33,8 @@ def test_sequence_to_host_matches_single_renders(abi, n, zero_copy):
                                on_frame=lambda i, h: got.__setitem__(i, h.numpy().copy()),
                                zero_copy=zero_copy)
     assert sorted(got) == list(range(n))
+    c = rd.counts()                    # both buffer sets of the pipelined form
+    assert c.overflow == 0 and c.timeout == 0
     for i, p in enumerate(poses):
         c = rd.render(cams[p])
         assert c.overflow == 0 and c.timeout == 0
