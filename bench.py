@@ -354,11 +354,13 @@ def _per_pose(rd, cams, gate=None):
 TRAIN_WORKLOADS = (
     ("city8M_1080p", 16, 0.2, 8, 3,
      "8M anchors / 10 levels / 4 km city grid, 16 views of 1920x1080 per step (every 4th pose "
-     "of a 64-pose zoom-out 8 m -> 4 km), 0.8 L1 + 0.2 D-SSIM vs seeded U[0,1] targets, "
-     "dense Adam over all anchors and decoder weights"),
+     "of a 64-pose zoom-out 8 m -> 4 km), 0.8 L1 + 0.2 D-SSIM, dense Adam over all anchors "
+     "and decoder weights; targets: the views rendered before N(0, 0.05) noise was added to "
+     "the anchor features"),
     ("street500k_1600x900", 1, 0.0, 60, 5,
      "500k anchors / 6 levels / 600 m street grid, one 1600x900 view per step (30-pose "
-     "zoom-out 8 m -> 250 m, cycled), L1 vs seeded U[0,1] targets, dense Adam"),
+     "zoom-out 8 m -> 250 m, cycled), L1, dense Adam; targets: the views rendered before "
+     "N(0, 0.05) noise was added to the anchor features"),
 )
 
 
@@ -416,6 +418,36 @@ def _appearance_bench(cams, pose, steps, warmup, flush, clk_index):
     return out
 
 
+FIT_SIGMA = 0.05     # N(0, 0.05) added to the N(0, 0.1) anchor features after the targets
+
+
+def _fit_targets(tr, cams, seed=1):
+    """Targets the training steps can fit: every view rendered (training mode, untimed) from
+    the scene as built, after which the anchor features get seeded N(0, FIT_SIGMA) noise, so
+    the steps pull the perturbed scene back towards images it can produce.  (Against noise
+    images, dense Adam at lr 1e-3 drives every decoded opacity below zero within two steps,
+    after which no Gaussian is drawn and a step does almost no work.)  Returns the targets and
+    the counts of every view before the perturbation (they also size the buffers)."""
+    import torch
+    targets, counts = [], []
+    for cam in cams:
+        c = tr.render(cam, infer=False)
+        assert c.overflow == 0 and c.timeout == 0, "size the buffers for the target renders"
+        targets.append(tr.img.clone())
+        counts.append(c)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    tr.feat.add_(FIT_SIGMA * torch.randn(tr.feat.shape, generator=gen, device="cuda"))
+    return targets, counts
+
+
+def _pairs_kept(tr, cams, pairs0):
+    """Pair count of the views after training over their count before it (untimed), so that a
+    step time measured on a scene that stopped drawing shows: such a time is not valid."""
+    now = [tr.render(cam, infer=False).n_pairs for cam in cams]
+    return round(float(sum(now)) / max(1, sum(pairs0)), 4)
+
+
 def _train_appearance_bench(clk_index, steps=60, warmup=5):
     """Training steps per second of the street workload (one 1600x900 view per step, L1,
     dense Adam) with an 8-value appearance code per anchor (Sec. 4.4), BF16: the codes and
@@ -428,13 +460,9 @@ def _train_appearance_bench(clk_index, steps=60, warmup=5):
     W, H = cams[0].W, cams[0].H
     tr = Trainer(sa, ma, W, H, sel_cap=400_000, pair_cap=8_000_000, precision="bf16")
     del sc, sa
-    gen = torch.Generator(device="cuda")
-    gen.manual_seed(1)
-    targets = [torch.rand(3, H, W, generator=gen, device="cuda") for _ in range(len(cams))]
-    sel_max = pair_max = 0
-    for cam in cams:
-        c = tr.render(cam, infer=False)
-        sel_max, pair_max = max(sel_max, c.n_selected), max(pair_max, c.n_pairs)
+    targets, cnt0 = _fit_targets(tr, cams)
+    sel_max = max(c.n_selected for c in cnt0)
+    pair_max = max(c.n_pairs for c in cnt0)
     tr.sel_cap, tr.pair_cap = int(sel_max * 1.2) + 1024, int(pair_max * 1.5) + 4096
     tr._alloc()
     batch = lambda i: ([cams[i % len(cams)]], [targets[i % len(cams)]])
@@ -453,8 +481,11 @@ def _train_appearance_bench(clk_index, steps=60, warmup=5):
     c = tr.counts()
     assert c.overflow == 0 and c.timeout == 0, "overflow or expired wait in training"
     ms = [a.elapsed_time(b) for a, b in ev]
+    kept = _pairs_kept(tr, cams, [c.n_pairs for c in cnt0])
     out = {"workload": "street500k_1600x900 with an 8-value appearance code per anchor "
-                       "(codes and code weights trained), BF16, L1, dense Adam",
+                       "(codes and code weights trained), BF16, L1, dense Adam; targets: the "
+                       "views rendered before N(0, 0.05) noise was added to the features",
+           "pairs_kept": kept, "valid": kept > 0.5, "loss_last_step": float(tr.loss.item()),
            "train_steps_per_s": 1e3 * steps / float(np.sum(ms)),
            "ms_per_step": float(np.mean(ms)), "steps": steps, "warmup": warmup,
            "stages_ms_per_step": {k: round(float(np.sum([a.elapsed_time(b) for a, b in v]))
@@ -483,15 +514,12 @@ def _train_bench(clk_index, steps_scale=1.0):
                      track_view_frequency=True, track_growth=True, track_opacity=True)
         voxel = synth.voxel_sizes(sc)
         del sc
-        gen = torch.Generator(device="cuda")
-        gen.manual_seed(1)
-        n_t = vps if vps > 1 else len(views)
-        targets = [torch.rand(3, H, W, generator=gen, device="cuda") for _ in range(n_t)]
-        # size the buffers on every view (training mode), with headroom for the updates
-        sel_max = pair_max = 0
-        for cam in views:
-            c = tr.render(cam, infer=False)
-            sel_max, pair_max = max(sel_max, c.n_selected), max(pair_max, c.n_pairs)
+        n_t = len(views)
+        # the targets (views rendered before the features are perturbed) also size the
+        # buffers, with headroom for the updates
+        targets, cnt0 = _fit_targets(tr, views)
+        sel_max = max(c.n_selected for c in cnt0)
+        pair_max = max(c.n_pairs for c in cnt0)
         tr.sel_cap, tr.pair_cap = int(sel_max * 1.2) + 1024, int(pair_max * 1.5) + 4096
         tr._alloc()
         res = {"workload": desc, "anchors": int(tr.N), "views_per_step": vps,
@@ -521,6 +549,8 @@ def _train_bench(clk_index, steps_scale=1.0):
                                [targets[(i * vps + v) % n_t] for v in range(vps)])
             for i in range(Wm):
                 tr.train_step(*batch(i))
+                if i == 0:
+                    loss_first = float(tr.loss.item())
             torch.cuda.synchronize()
             timers, ev = {}, []
             with ClockSampler(clk_index) as clk:
@@ -536,6 +566,8 @@ def _train_bench(clk_index, steps_scale=1.0):
             ms = [a.elapsed_time(b) for a, b in ev]
             stages = {k: round(float(np.sum([a.elapsed_time(b) for a, b in v])) / K, 4)
                       for k, v in timers.items()}
+            loss_last = float(tr.loss.item())
+            kept = _pairs_kept(tr, views, [c.n_pairs for c in cnt0])
             if precision == "bf16":
                 # view-frequency pruning (Sec. 4.2.2) after the counted training views
                 n_before, n_views = tr.N, tr.n_views_seen
@@ -576,11 +608,12 @@ def _train_bench(clk_index, steps_scale=1.0):
                     "seconds": time.perf_counter() - t0,
                     "note": "LOD-bias update, voxel-hash proposals, first-proposal-wins "
                             "compaction, appended rows with the parents' features and fresh "
-                            "Adam state, all on the GPU (random targets: the statistics are "
-                            "not those of a converging scene)"}
+                            "Adam state, all on the GPU (a few steps from a perturbed scene: "
+                            "the statistics are not those of a converged one)"}
             res[precision] = {"train_steps_per_s": 1e3 * K / float(np.sum(ms)),
                               "ms_per_step": float(np.mean(ms)), "stages_ms_per_step": stages,
-                              "loss_last_step": float(tr.loss.item()),
+                              "loss_first_step": loss_first, "loss_last_step": loss_last,
+                              "pairs_kept": kept, "valid": kept > 0.5,
                               "clocks": clk.summary()}
         out[name] = res
         del tr, targets
@@ -874,16 +907,16 @@ def run_profile_train(args):
     tr = Trainer(sc, mlp, W, H, ssim_lambda=0.2, sel_cap=100_000, pair_cap=2_000_000,
                  precision=args.precision, track_view_frequency=True, track_growth=True,
                  track_opacity=True)
-    gen = torch.Generator(device="cuda")
-    gen.manual_seed(1)
     views = cams[::4][:16] if args.train_workload == "city8M_1080p" else [cams[len(cams) // 2]]
-    tgts = [torch.rand(3, H, W, generator=gen, device="cuda") for _ in views]
-    for cam in views:
-        tr.render(cam, infer=False)
+    tgts, cnt0 = _fit_targets(tr, views)
     for _ in range(args.warmup + args.steps):
         tr.train_step(views, tgts)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_train_steps": args.warmup + args.steps, **tr.counts().__dict__}))
+    c = tr.counts()
+    assert c.overflow == 0 and c.timeout == 0
+    print(json.dumps({"profile_train_steps": args.warmup + args.steps,
+                      "pairs_kept": _pairs_kept(tr, views, [c.n_pairs for c in cnt0]),
+                      **c.__dict__}))
     return 0
 
 

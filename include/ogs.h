@@ -78,7 +78,7 @@ typedef struct ogs_counts {
     uint32_t need_selected;    /* selection size that was needed */
     uint32_t need_pairs;       /* pair count that was needed */
     uint32_t timeout;          /* nonzero if a bounded wait expired */
-    uint32_t n_visible;        /* Gaussians with a non-empty tile rectangle */
+    uint32_t reserved;         /* zero (pads the record to 32 bytes) */
 } ogs_counts;
 
 /* Decoder weights (device, f32), layout of the paper's three attribute MLPs (Sec. 3.2,

@@ -32,7 +32,7 @@ class Camera(C.Structure):
 
 class Counts(C.Structure):
     _fields_ = [(n, C.c_uint32) for n in ("n_selected", "n_gaussians", "n_pairs", "overflow",
-                                          "need_selected", "need_pairs", "timeout", "n_visible")]
+                                          "need_selected", "need_pairs", "timeout", "reserved")]
 
 
 COUNT_FIELDS = [f[0] for f in Counts._fields_]

@@ -33,7 +33,7 @@ class FrameCounts:
     need_selected: int
     need_pairs: int
     timeout: int
-    n_visible: int
+    reserved: int
 
 
 def _stage(timers, name, st, fn):
