@@ -268,7 +268,9 @@ typedef struct ogs_tile_bins {
  * ordered by (depth key, id)), but each list in its tile's fixed region instead of packed:
  * one pass places every (Gaussian, tile) pair in its tile's region at the slot the atomic
  * that counts it returns, then every region is sorted in place.  No prefix scan and no
- * second pass over the pairs.
+ * second pass over the pairs.  Rectangles of more than 8 tiles are handed on in chunks of
+ * 1024 tiles to a second pass whose warps share them out over the grid (the scratch holds
+ * 32 chunk entries per tile, at least 4096; chunks beyond that are placed by the first pass).
  *   depth_key, rect, tiles, g_cap, n_gauss, grid_x, grid_y: as ogs_sort
  *   bins: the regions (host struct); pair_gauss holds the sorted lists afterwards and
  *   pair_key is clobbered

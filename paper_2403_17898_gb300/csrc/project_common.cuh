@@ -140,23 +140,103 @@ __device__ __forceinline__ void count_tiles(uint32_t* tc, int gx, uint2 rc, uint
     }
 }
 
+// Rectangles of more than kOwnTiles tiles go through the whole warp in chunks of kChunkTiles
+// tiles.  bin_tiles hands each chunk to a list of deferred (Gaussian, chunk) entries that a
+// second pass spreads over the whole grid, so that a warp holding many large near-camera
+// Gaussians does not walk all their tiles alone; chunks that find the list full stay with
+// the warp.
+constexpr uint32_t kChunkTiles = 1024;
+
+// Places tiles [lo, hi) of rectangle r (row-major inside it) for Gaussian g with key k: every
+// lane of the warp takes one tile in 32, kFly atomics in flight before the stores.  All 32
+// lanes call it with the same arguments.
+template <uint32_t kFly>
+__device__ __forceinline__ void bin_rect_range(uint32_t* tc, int gx, uint2 r, uint32_t lo,
+                                               uint32_t hi, uint32_t g, uint32_t k,
+                                               uint32_t cap, uint32_t* __restrict__ pair_key,
+                                               uint32_t* __restrict__ pair_gauss) {
+    const uint32_t bx0 = r.x & 0xFFFFu, by0 = r.x >> 16, bw = (r.y & 0xFFFFu) - bx0;
+    for (uint32_t i0 = lo; i0 < hi; i0 += 32 * kFly) {
+        uint32_t tt[kFly], sl[kFly];
+#pragma unroll
+        for (uint32_t j = 0; j < kFly; ++j) {
+            const uint32_t i = i0 + j * 32 + lane_id();
+            if (i < hi) {
+                tt[j] = (by0 + i / bw) * (uint32_t)gx + bx0 + i % bw;
+                sl[j] = atomicAdd(tc + tt[j], 1u);
+            }
+        }
+#pragma unroll
+        for (uint32_t j = 0; j < kFly; ++j) {
+            const uint32_t i = i0 + j * 32 + lane_id();
+            if (i < hi && sl[j] < cap) {
+                const size_t o = (size_t)tt[j] * cap + sl[j];
+                pair_gauss[o] = g;
+                pair_key[o] = k;
+            }
+        }
+    }
+}
+
 // count_tiles, and each pair placed at once: the atomic that counts a (Gaussian, tile) pair
 // returns its slot in the tile's region of cap entries, where the Gaussian's id and depth key
 // go (pair_gauss[t * cap + slot], pair_key[...]); slots at or past cap are counted, not
 // written (the caller sees the overflow in the counts).  g and dkey are the lane's Gaussian.
 // A lane issues all its atomics (up to kOwnTiles at a time) before the first store that needs
-// a slot, so their round trips overlap instead of adding up.
+// a slot, so their round trips overlap instead of adding up.  A larger rectangle is cut into
+// chunks of kChunkTiles tiles, appended as (g, chunk) to `defer` (defer_cap entries, the
+// 64-bit counter n_defer counts every chunk offered); chunks past defer_cap are placed here.
 __device__ __forceinline__ void bin_tiles(uint32_t* tc, int gx, uint2 rc, uint32_t ntiles,
                                           uint32_t g, uint32_t dkey, uint32_t cap,
                                           uint32_t* __restrict__ pair_key,
-                                          uint32_t* __restrict__ pair_gauss) {
+                                          uint32_t* __restrict__ pair_gauss,
+                                          uint2* __restrict__ defer,
+                                          unsigned long long* n_defer, uint32_t defer_cap) {
     const uint32_t x0 = rc.x & 0xFFFFu, y0 = rc.x >> 16, x1 = rc.y & 0xFFFFu;
     const uint32_t w = x1 - x0;
-    auto put = [&](uint32_t t, uint32_t slot, uint32_t gg, uint32_t kk) {
+    const uint32_t lane = lane_id();
+    // large rectangles first (their list state is dead before the small ones' slots are live)
+    const bool is_big = ntiles > kOwnTiles;
+    if (__any_sync(0xffffffffu, is_big)) {
+        // chunks of the lane's rectangle, numbered across the warp by an inclusive scan
+        const uint32_t bn = is_big ? w * ((rc.y >> 16) - y0) : 0;
+        const uint32_t nch = (bn + kChunkTiles - 1) / kChunkTiles;
+        uint32_t incl = nch;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((int)lane >= o) incl += v;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned long long first = 0;
+        if (lane == 0) first = atomicAdd(n_defer, (unsigned long long)total);
+        first = __shfl_sync(0xffffffffu, first, 0);
+        const unsigned long long mine = first + (incl - nch);    // this lane's first entry
+        uint32_t kept = 0;                                       // chunks the list took
+        if (mine < (unsigned long long)defer_cap) {
+            const unsigned long long room = (unsigned long long)defer_cap - mine;
+            kept = room < nch ? (uint32_t)room : nch;
+        }
+        for (uint32_t c = 0; c < kept; ++c) defer[mine + c] = make_uint2(g, c);
+        // what the list could not take stays with the warp, one rectangle at a time (four
+        // atomics in flight per lane: this path is rare and keeps the kernel's registers low)
+        const uint32_t lo = kept * kChunkTiles;
+        uint32_t left = __ballot_sync(0xffffffffu, lo < bn);
+        while (left) {
+            const int src = __ffs(left) - 1;
+            left &= left - 1;
+            const uint2 r = make_uint2(__shfl_sync(0xffffffffu, rc.x, src),
+                                       __shfl_sync(0xffffffffu, rc.y, src));
+            bin_rect_range<4>(tc, gx, r, __shfl_sync(0xffffffffu, lo, src),
+                           __shfl_sync(0xffffffffu, bn, src), __shfl_sync(0xffffffffu, g, src),
+                           __shfl_sync(0xffffffffu, dkey, src), cap, pair_key, pair_gauss);
+        }
+    }
+    auto put = [&](uint32_t t, uint32_t slot) {
         if (slot < cap) {
             const size_t o = (size_t)t * cap + slot;
-            pair_gauss[o] = gg;
-            pair_key[o] = kk;
+            pair_gauss[o] = g;
+            pair_key[o] = dkey;
         }
     };
     const bool own = ntiles > 0 && ntiles <= kOwnTiles;
@@ -164,7 +244,7 @@ __device__ __forceinline__ void bin_tiles(uint32_t* tc, int gx, uint2 rc, uint32
     const uint32_t peers = __match_any_sync(0xffffffffu, t0);
     const uint32_t leader = __ffs(peers) - 1;
     uint32_t base = 0;
-    if (own && lane_id() == leader) base = atomicAdd(tc + t0, (uint32_t)__popc(peers));
+    if (own && lane == leader) base = atomicAdd(tc + t0, (uint32_t)__popc(peers));
     if (own) {
         uint32_t tt[kOwnTiles], sl[kOwnTiles];
         uint32_t kx = 0, t = t0;                    // walks the rectangle row by row
@@ -181,35 +261,10 @@ __device__ __forceinline__ void bin_tiles(uint32_t* tc, int gx, uint2 rc, uint32
         }
 #pragma unroll
         for (uint32_t i = 1; i < kOwnTiles; ++i)
-            if (i < ntiles) put(tt[i], sl[i], g, dkey);
+            if (i < ntiles) put(tt[i], sl[i]);
     }
     base = __shfl_sync(0xffffffffu, base, leader);
-    if (own) put(t0, base + __popc(peers & lanemask_lt()), g, dkey);
-    uint32_t big = __ballot_sync(0xffffffffu, ntiles > kOwnTiles);
-    while (big) {
-        const int src = __ffs(big) - 1;
-        big &= big - 1;
-        const uint2 r = make_uint2(__shfl_sync(0xffffffffu, rc.x, src),
-                                   __shfl_sync(0xffffffffu, rc.y, src));
-        const uint32_t bg = __shfl_sync(0xffffffffu, g, src);
-        const uint32_t bk = __shfl_sync(0xffffffffu, dkey, src);
-        const uint32_t bx0 = r.x & 0xFFFFu, by0 = r.x >> 16, bw = (r.y & 0xFFFFu) - bx0;
-        const uint32_t bn = bw * ((r.y >> 16) - by0);
-        for (uint32_t i0 = 0; i0 < bn; i0 += 32 * kOwnTiles) {
-            uint32_t tt[kOwnTiles], sl[kOwnTiles];
-#pragma unroll
-            for (uint32_t j = 0; j < kOwnTiles; ++j) {
-                const uint32_t i = i0 + j * 32 + lane_id();
-                if (i < bn) {
-                    tt[j] = (by0 + i / bw) * (uint32_t)gx + bx0 + i % bw;
-                    sl[j] = atomicAdd(tc + tt[j], 1u);
-                }
-            }
-#pragma unroll
-            for (uint32_t j = 0; j < kOwnTiles; ++j)
-                if (i0 + j * 32 + lane_id() < bn) put(tt[j], sl[j], bg, bk);
-        }
-    }
+    if (own) put(t0, base + __popc(peers & lanemask_lt()));
 }
 
 }  // namespace ogs

@@ -438,14 +438,17 @@ __global__ void __launch_bounds__(kScanChunk) tile_scan(const uint32_t* __restri
 // One pass over the Gaussians (one per thread, every lane of a warp calls bin_tiles):
 // each (Gaussian, tile) pair is counted by an atomic whose return value is its slot in the
 // tile's region, where its id and depth key are written.
-__global__ void __launch_bounds__(kBinThreads) bin_regions(const uint32_t* __restrict__ dkey,
+__global__ void __launch_bounds__(kBinThreads, 8) bin_regions(const uint32_t* __restrict__ dkey,
                                                            const uint2* __restrict__ rect,
                                                            const uint32_t* __restrict__ tiles,
                                                            const uint32_t* n_dev, int64_t n_cap,
                                                            int gx, uint32_t* __restrict__ tc,
                                                            uint32_t cap,
                                                            uint32_t* __restrict__ keys,
-                                                           uint32_t* __restrict__ ids) {
+                                                           uint32_t* __restrict__ ids,
+                                                           uint2* __restrict__ defer,
+                                                           unsigned long long* n_defer,
+                                                           uint32_t defer_cap) {
     pdl_wait();
     pdl_trigger();
     const uint32_t n = count_of(n_dev, n_cap);
@@ -460,7 +463,37 @@ __global__ void __launch_bounds__(kBinThreads) bin_regions(const uint32_t* __res
         k = dkey[g];
     }
     if (c == 0) rc = make_uint2(0, 0);
-    bin_tiles(tc, gx, rc, c, (uint32_t)g, k, cap, keys, ids);
+    bin_tiles(tc, gx, rc, c, (uint32_t)g, k, cap, keys, ids, defer, n_defer, defer_cap);
+}
+
+// The deferred chunks of large rectangles: one warp per (Gaussian, chunk) entry, the warps of
+// a fixed grid taking the entries in turn, so the tiles of the large near-camera Gaussians
+// are spread over every SM instead of staying with the warps that met them.
+constexpr int kDeferGrid = 4 * kSmCount;
+
+__global__ void __launch_bounds__(kBinThreads) bin_deferred(const uint32_t* __restrict__ dkey,
+                                                            const uint2* __restrict__ rect,
+                                                            int gx, uint32_t* __restrict__ tc,
+                                                            uint32_t cap,
+                                                            uint32_t* __restrict__ keys,
+                                                            uint32_t* __restrict__ ids,
+                                                            const uint2* __restrict__ defer,
+                                                            const unsigned long long* n_defer,
+                                                            uint32_t defer_cap) {
+    pdl_wait();
+    pdl_trigger();
+    const unsigned long long nd = *n_defer;
+    const uint32_t n = nd < (unsigned long long)defer_cap ? (uint32_t)nd : defer_cap;
+    const uint32_t nwarps = gridDim.x * (kBinThreads / 32);
+    for (uint32_t e = blockIdx.x * (kBinThreads / 32) + (threadIdx.x >> 5); e < n; e += nwarps) {
+        const uint2 en = defer[e];                   // the same entry in every lane
+        const uint2 r = rect[en.x];
+        const uint32_t bw = (r.y & 0xFFFFu) - (r.x & 0xFFFFu);
+        const uint32_t bn = bw * ((r.y >> 16) - (r.x >> 16));
+        const uint32_t lo = en.y * kChunkTiles;
+        const uint32_t hi = min(bn, lo + kChunkTiles);
+        bin_rect_range<kOwnTiles>(tc, gx, r, lo, hi, en.x, dkey[en.x], cap, keys, ids);
+    }
 }
 
 // Ranges of the binned lists: tile t owns [t cap, t cap + count_t).  One CTA per kScanChunk
@@ -1023,18 +1056,31 @@ extern "C" size_t ogs_sort_scratch_bytes(int64_t g_cap, int64_t pair_cap, int32_
     return sort_layout(pair_cap < 0 ? 0 : pair_cap, n_tiles, nullptr, nullptr);
 }
 
-// scratch of ogs_sort_bins: the per-chunk lists of long tiles
+// scratch of ogs_sort_bins: the tile counts behind the deferred-chunk counter (one memset
+// clears both), the deferred (Gaussian, chunk) entries and the per-chunk lists of long tiles
 struct BinsScratch {
+    unsigned long long* ndefer;
     uint32_t *tcount, *longl, *nlong;
+    uint2* defer;
+    uint32_t defer_cap;
 };
+
+inline uint32_t defer_cap_of(int n_tiles) {
+    const uint32_t c = 32u * (uint32_t)(n_tiles > 0 ? n_tiles : 0);
+    return c > 4096u ? c : 4096u;
+}
 
 size_t bins_layout(int n_tiles, void* base, BinsScratch* s) {
     Carver cv(base);
     BinsScratch t;
     const int nchunks = n_tiles > 0 ? (n_tiles + kScanChunk - 1) / kScanChunk : 1;
-    t.tcount = cv.take<uint32_t>(n_tiles > 0 ? n_tiles : 1);
+    uint32_t* head = cv.take<uint32_t>(2 + (size_t)(n_tiles > 0 ? n_tiles : 1));
+    t.ndefer = reinterpret_cast<unsigned long long*>(head);     // 256-byte aligned
+    t.tcount = head ? head + 2 : nullptr;
     t.longl = cv.take<uint32_t>((size_t)nchunks * kScanChunk);
     t.nlong = cv.take<uint32_t>(nchunks);
+    t.defer_cap = defer_cap_of(n_tiles);
+    t.defer = cv.take<uint2>(t.defer_cap);
     if (s) *s = t;
     return cv.off + 256;
 }
@@ -1063,7 +1109,8 @@ extern "C" ogs_status ogs_sort_bins(const uint32_t* depth_key, const uint32_t* r
     BinsScratch s;
     bins_layout(n_tiles, scratch, &s);
     uint2* range = reinterpret_cast<uint2*>(tile_range);
-    if (cudaMemsetAsync(s.tcount, 0, sizeof(uint32_t) * n_tiles, st) != cudaSuccess)
+    if (cudaMemsetAsync(s.ndefer, 0, sizeof(uint32_t) * (2 + (size_t)n_tiles), st) !=
+        cudaSuccess)
         return OGS_ERR_CUDA;
     // the Gaussian count is the device count written by the decoder, or the caller's n_gauss
     const uint32_t* n_dev = n_gauss < 0 ? &counts->n_gaussians : nullptr;
@@ -1071,7 +1118,12 @@ extern "C" ogs_status ogs_sort_bins(const uint32_t* depth_key, const uint32_t* r
     const int nb = n_cap > 0 ? (int)((n_cap + kBinThreads - 1) / kBinThreads) : 1;
     launch_pdl(bin_regions, dim3(nb), dim3(kBinThreads), 0, st, depth_key,
                reinterpret_cast<const uint2*>(rect), tiles, n_dev, n_cap, grid_x, s.tcount,
-               bins->tile_cap, bins->pair_key, bins->pair_gauss);
+               bins->tile_cap, bins->pair_key, bins->pair_gauss, s.defer, s.ndefer,
+               s.defer_cap);
+    launch_pdl(bin_deferred, dim3(kDeferGrid), dim3(kBinThreads), 0, st, depth_key,
+               reinterpret_cast<const uint2*>(rect), grid_x, s.tcount, bins->tile_cap,
+               bins->pair_key, bins->pair_gauss, (const uint2*)s.defer,
+               (const unsigned long long*)s.ndefer, s.defer_cap);
     const int nchunks = (n_tiles + kScanChunk - 1) / kScanChunk;
     launch_pdl(bins_scan, dim3(nchunks), dim3(kScanChunk), 0, st, (const uint32_t*)s.tcount,
                n_tiles, bins->tile_cap, range, s.longl, s.nlong, counts);

@@ -356,6 +356,22 @@ def test_sort_bins_matches_oracle_lists(abi, torch, G, gx, gy):
     assert np.array_equal(got, lst)
 
 
+@pytest.mark.parametrize("G,gx,gy,span", [(2000, 120, 68, 60), (60_000, 40, 40, 40)])
+def test_sort_bins_large_rectangles(abi, torch, G, gx, gy, span):
+    """Rectangles of up to span x span tiles.  Those of more than 8 tiles go to the deferred
+    list in chunks of 1024 tiles, several chunks for the largest (327 and 267 rectangles of
+    more than 1024 tiles).  In the second case the chunks offered (54,902) exceed the list
+    (32 entries per tile: 51,200), so the rest stay with the warps that met them.  The lists
+    equal the oracle's either way."""
+    rect, depth = synth.random_rects_depths(7, G, gx, gy, max_span=span, equal_depth_frac=0.05)
+    start, lst, _ = oracle.tile_lists(rect, depth.astype(np.float64), gx, gy)
+    cap = int(max(1, np.diff(start).max()))
+    got, tr, c = _gpu_sort_bins(abi, torch, rect, depth, gx, gy, cap)
+    assert c["n_pairs"] == len(lst) and c["overflow"] == 0
+    assert np.array_equal(tr[:, 1] - tr[:, 0], np.diff(start))
+    assert np.array_equal(got, lst)
+
+
 def test_sort_bins_overflow(abi, torch):
     """A tile with more pairs than tile_cap: overflow bit 1, need_pairs = the longest list,
     every range empty."""
