@@ -291,9 +291,9 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------------------
 
-# kernels each ABI call launches per frame (the timed form: fused BF16 decode + projection
-# binning the pairs into tile regions, then ogs_sort_bins)
-LAUNCHES = {"lod_select": 2, "lod_select_gated": 3, "decode_project": 2, "sort": 4,
+# kernels each ABI call launches per frame (the timed form: fused BF16 decode + projection,
+# then ogs_sort_bins: bin_regions, bin_deferred, bins_scan, tile_sort_warp, tile_sort_listed)
+LAUNCHES = {"lod_select": 2, "lod_select_gated": 3, "decode_project": 2, "sort": 5,
             "blend_fwd": 1}
 DPSNR_GATE_DB = 0.05
 # DRAM bytes (read + write) of one blend_fwd launch and its issue-slot use, from an ncu
