@@ -118,3 +118,27 @@ def test_counts_status_mapping(lib):
     assert abi.counts_status(c) == 3
     assert abi.counts_status(c, nonfinite=1) == 5
     assert abi.counts_status(np.zeros(8, np.uint32), nonfinite=4) == 5
+
+
+def test_sort_bins_scratch_and_host_checks(lib):
+    """ogs_sort_bins' scratch holds the tile counts behind an 8-byte chunk counter, the per
+    chunk lists of long tiles and 32 deferred (Gaussian, chunk) entries of 8 bytes per tile
+    (at least 4096); a scratch one byte short, a zero tile_cap or a grid of more than 65536
+    tiles is refused on the host (OGS_ERR_ARG) before anything is enqueued."""
+    from paper_2403_17898_gb300 import abi
+    L = abi.lib()
+    prev = 0
+    for nt in (1, 16, 128, 2209, 8160, 65536):
+        b = abi.sort_bins_scratch_bytes(nt)
+        chunks = -(-nt // 1024)
+        assert b >= 8 * max(4096, 32 * nt) + 4 * (nt + 2) + 4 * chunks * (1024 + 1)
+        assert b >= prev
+        prev = b
+    fake = ctypes.c_void_p(1 << 20)                 # never dereferenced: refused first
+    bins = abi.TileBins(fake, fake, 4096)
+    need = abi.sort_bins_scratch_bytes(120 * 68)
+    args = lambda gx, gy, sb, tb: (fake, fake, fake, 1000, -1, gx, gy, ctypes.byref(tb), fake,
+                                   fake, fake, sb, None)
+    assert L.ogs_sort_bins(*args(120, 68, need - 1, bins)) == 1
+    assert L.ogs_sort_bins(*args(257, 256, 1 << 40, bins)) == 1
+    assert L.ogs_sort_bins(*args(120, 68, need, abi.TileBins(fake, fake, 0))) == 1
